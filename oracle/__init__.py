@@ -1,0 +1,184 @@
+"""Oracle for the trace finder -- TEST INFRASTRUCTURE ONLY.
+
+A plain CPU restatement of the analysis in ``apo_oracle.cpp`` (C++, built with
+g++ into ``liboracle.so`` next to this file) plus thin numpy wrappers.  Only the
+test-suite, the smoke check and the CPU-baseline leg of the benchmark may use
+it; the library's product path never does.  It shares no code with the CUDA
+library.
+
+Parity unpinned: none -- every routine is pinned by ``tests/test_oracle_pins.py``
+(brute force on short strings, the paper's worked examples, published test
+vectors, invariants, and agreement of independent formulations).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "apo_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (host code only; builds on x86 and Arm)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        U64 = ctypes.c_uint64
+        L.ora_fnv1a64.restype = U64
+        L.ora_fnv1a64.argtypes = [P, U64]
+        L.ora_serialize_task.restype = U64
+        L.ora_serialize_task.argtypes = [U64, P, P, P, P, P, P, U64]
+        L.ora_hash_tasks.restype = None
+        L.ora_hash_tasks.argtypes = [U64, P, P, P, P, P, P]
+        for f in ("ora_suffix_array", "ora_suffix_array_doubling"):
+            getattr(L, f).restype = None
+            getattr(L, f).argtypes = [P, U64, P]
+        for f in ("ora_lcp_direct", "ora_lcp_kasai"):
+            getattr(L, f).restype = None
+            getattr(L, f).argtypes = [P, U64, P, P]
+        L.ora_candidates_raw.restype = U64
+        L.ora_candidates_raw.argtypes = [U64, P, P, P, P]
+        L.ora_greedy.restype = None
+        L.ora_greedy.argtypes = [U64, U64, P, P, P, ctypes.c_int]
+        L.ora_find_repeats.restype = None
+        L.ora_find_repeats.argtypes = [P, U64, P, P, ctypes.c_uint32, ctypes.c_int] + [P] * 10
+        L.ora_match.restype = U64
+        L.ora_match.argtypes = [P, P, U64, P, U64, ctypes.c_int, P, P, U64]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _tok(S) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(S).astype(np.uint64))
+
+
+def fnv1a64(data: bytes) -> int:
+    b = np.frombuffer(bytes(data), dtype=np.uint8).copy() if len(data) else np.zeros(1, np.uint8)
+    return int(lib().ora_fnv1a64(_p(b), len(data)))
+
+
+def serialize_task(ts, t: int) -> bytes:
+    arrs = [np.ascontiguousarray(x) for x in (ts.task_id, ts.arg_off, ts.region, ts.field_mask, ts.priv)]
+    n = lib().ora_serialize_task(t, *[_p(a) for a in arrs], None, 0)
+    out = np.zeros(max(1, n), dtype=np.uint8)
+    lib().ora_serialize_task(t, *[_p(a) for a in arrs], _p(out), n)
+    return out[:n].tobytes()
+
+
+def hash_tasks(ts) -> np.ndarray:
+    arrs = [np.ascontiguousarray(ts.task_id, dtype=np.uint32),
+            np.ascontiguousarray(ts.arg_off, dtype=np.uint32),
+            np.ascontiguousarray(ts.region, dtype=np.uint32),
+            np.ascontiguousarray(ts.field_mask, dtype=np.uint64),
+            np.ascontiguousarray(ts.priv, dtype=np.uint8)]
+    n = ts.n_tasks
+    out = np.zeros(n, dtype=np.uint64)
+    lib().ora_hash_tasks(n, *[_p(a) for a in arrs], _p(out))
+    return out
+
+
+def suffix_array(S, method: str = "direct") -> np.ndarray:
+    S = _tok(S)
+    sa = np.zeros(S.shape[0], dtype=np.uint32)
+    f = lib().ora_suffix_array if method == "direct" else lib().ora_suffix_array_doubling
+    f(_p(S), S.shape[0], _p(sa))
+    return sa
+
+
+def lcp(S, sa, method: str = "kasai") -> np.ndarray:
+    S = _tok(S)
+    sa = np.ascontiguousarray(sa, dtype=np.uint32)
+    out = np.zeros(S.shape[0], dtype=np.uint32)
+    f = lib().ora_lcp_kasai if method == "kasai" else lib().ora_lcp_direct
+    f(_p(S), S.shape[0], _p(sa), _p(out))
+    return out
+
+
+def candidates_raw(sa, lcp_arr):
+    sa = np.ascontiguousarray(sa, dtype=np.uint32)
+    lcp_arr = np.ascontiguousarray(lcp_arr, dtype=np.uint32)
+    n = sa.shape[0]
+    L = np.zeros(max(1, 2 * n), dtype=np.uint32)
+    Sx = np.zeros(max(1, 2 * n), dtype=np.uint32)
+    m = lib().ora_candidates_raw(n, _p(sa), _p(lcp_arr), _p(L), _p(Sx))
+    return L[:m], Sx[:m]
+
+
+def greedy(n: int, l, s, variant: int = 0) -> np.ndarray:
+    l = np.ascontiguousarray(l, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.uint32)
+    acc = np.zeros(max(1, l.shape[0]), dtype=np.uint8)
+    lib().ora_greedy(n, l.shape[0], _p(l), _p(s), _p(acc), variant)
+    return acc[:l.shape[0]]
+
+
+@dataclass
+class Repeats:
+    sa: np.ndarray
+    lcp: np.ndarray
+    cand_len: np.ndarray
+    cand_id: np.ndarray
+    cand_start: np.ndarray
+    accepted: np.ndarray
+    sel_start: np.ndarray
+    sel_len: np.ndarray
+    sel_trace: np.ndarray
+    trace_len: np.ndarray
+    trace_start: np.ndarray
+
+
+def find_repeats(S, min_len: int, greedy_variant: int = 0, sa_method: str = "direct",
+                 sa=None, lcp_arr=None) -> Repeats:
+    """Alg. 2 end to end on one window (SA, LCP, candidates, greedy, R)."""
+    S = _tok(S)
+    n = S.shape[0]
+    if sa is None:
+        sa = suffix_array(S, sa_method)
+    if lcp_arr is None:
+        lcp_arr = lcp(S, sa)
+    sa = np.ascontiguousarray(sa, dtype=np.uint32)
+    lcp_arr = np.ascontiguousarray(lcp_arr, dtype=np.uint32)
+    cap = max(1, 2 * n)
+    cl, ci, cs = (np.zeros(cap, np.uint32) for _ in range(3))
+    acc = np.zeros(cap, np.uint8)
+    ss, sl, st, tl, tst = (np.zeros(max(1, n), np.uint32) for _ in range(5))
+    counts = np.zeros(3, np.uint64)
+    lib().ora_find_repeats(_p(S), n, _p(sa), _p(lcp_arr), min_len, greedy_variant,
+                           _p(cl), _p(ci), _p(cs), _p(acc), _p(ss), _p(sl), _p(st), _p(tl), _p(tst),
+                           _p(counts))
+    m, k, t = (int(c) for c in counts)
+    return Repeats(sa, lcp_arr, cl[:m], ci[:m], cs[:m], acc[:m], ss[:k], sl[:k], st[:k], tl[:t], tst[:t])
+
+
+def match(pat_tokens, pat_off, stream, naive: bool = False):
+    """All (end, pattern) occurrences, sorted by (end, pattern)."""
+    pt = _tok(pat_tokens)
+    po = np.ascontiguousarray(pat_off, dtype=np.uint64)
+    st = _tok(stream)
+    P = po.shape[0] - 1
+    cnt = lib().ora_match(_p(pt), _p(po), P, _p(st), st.shape[0], int(naive), None, None, 0)
+    e = np.zeros(max(1, cnt), np.uint32)
+    i = np.zeros(max(1, cnt), np.uint32)
+    lib().ora_match(_p(pt), _p(po), P, _p(st), st.shape[0], int(naive), _p(e), _p(i), cnt)
+    return e[:cnt], i[:cnt]

@@ -1,0 +1,266 @@
+"""Pins for the oracle: brute force on short strings, the paper's worked
+examples, published test vectors, invariants and the agreement of independent
+formulations.  CPU only."""
+import itertools
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+# ---------------------------------------------------------------- brute force
+def bf_sa(S):
+    """Sort the materialised suffixes (Python list order: a proper prefix is smaller)."""
+    S = list(S)
+    return sorted(range(len(S)), key=lambda i: S[i:])
+
+
+def bf_lcp_pair(S, a, b):
+    k = 0
+    while a + k < len(S) and b + k < len(S) and S[a + k] == S[b + k]:
+        k += 1
+    return k
+
+
+def bf_nonoverlapping_repeats(S):
+    """All (length, start) with a second, non-overlapping occurrence."""
+    n = len(S)
+    out = set()
+    for l in range(1, n // 2 + 1):
+        for s in range(n - l + 1):
+            for t in range(n - l + 1):
+                if abs(s - t) >= l and S[s:s + l] == S[t:t + l]:
+                    out.add((l, s))
+                    break
+    return out
+
+
+def fnv1a64_py(data: bytes) -> int:
+    h = 0xCBF29CE484222325
+    for b in data:
+        h = ((h ^ b) * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def check_window(S, min_len):
+    """Every oracle output for S against its definition."""
+    S = list(S)
+    n = len(S)
+    sa = oracle.suffix_array(np.array(S, dtype=np.uint64)) if n else np.zeros(0, np.uint32)
+    assert list(sa) == bf_sa(S)
+    lc = oracle.lcp(np.array(S, dtype=np.uint64), sa)
+    for i in range(n - 1):
+        assert lc[i] == bf_lcp_pair(S, int(sa[i]), int(sa[i + 1]))
+    if n:
+        assert lc[n - 1] == 0
+    rl, rs = oracle.candidates_raw(sa, lc)
+    assert len(rl) == 2 * max(0, n - 1)
+    reps = bf_nonoverlapping_repeats(S)
+    for l, s in zip(rl, rs):
+        if l > 0:
+            assert (int(l), int(s)) in reps, (S, l, s)
+    r = oracle.find_repeats(np.array(S, dtype=np.uint64), min_len)
+    # candidate list: the filtered raw candidates, once each, in Alg. 2's order
+    want = sorted({(int(l), int(s)) for l, s in zip(rl, rs) if l >= min_len},
+                  key=lambda c: (-c[0], S[c[1]:c[1] + c[0]], c[1]))
+    got = list(zip(r.cand_len.tolist(), r.cand_start.tolist()))
+    assert got == want
+    # id = number of suffixes whose first l tokens are smaller than the sub-string
+    for l, s, cid in zip(r.cand_len.tolist(), r.cand_start.tolist(), r.cand_id.tolist()):
+        sub = S[s:s + l]
+        assert cid == sum(1 for j in range(n) if S[j:j + l] < sub)
+    # greedy: taken iff it meets no interval taken before it
+    acc = r.accepted.tolist()
+    for k, (l, s) in enumerate(got):
+        blocked = any(acc[j] and s < got[j][1] + got[j][0] and got[j][1] < s + l for j in range(k))
+        assert acc[k] == (not blocked)
+    for v in (1, 2):
+        assert oracle.greedy(n, r.cand_len, r.cand_start, v).tolist() == acc
+    # R in first-acceptance order; selected intervals by start
+    taken = [got[k] for k in range(len(got)) if acc[k]]
+    R = []
+    for l, s in taken:
+        if S[s:s + l] not in R:
+            R.append(S[s:s + l])
+    assert [list(S[s:s + l]) for l, s in zip(r.trace_len.tolist(), r.trace_start.tolist())] == R
+    for t, sub in enumerate(R):
+        starts = [s for l, s in taken if S[s:s + l] == sub]
+        assert r.trace_start[t] == min(starts)
+    sel = sorted((s, l) for l, s in taken)
+    assert list(zip(r.sel_start.tolist(), r.sel_len.tolist())) == sel
+    for s, l, t in zip(r.sel_start.tolist(), r.sel_len.tolist(), r.sel_trace.tolist()):
+        assert S[s:s + l] == R[t]
+    return r
+
+
+# ---------------------------------------------------------------- hashing
+def test_fnv1a64_published_vectors():
+    assert oracle.fnv1a64(b"") == 0xCBF29CE484222325
+    assert oracle.fnv1a64(b"a") == 0xAF63DC4C8601EC8C
+    assert oracle.fnv1a64(b"foobar") == 0x85944171F73967E8
+
+
+def test_task_serialisation_by_hand():
+    ts = W.TaskStream(task_id=np.array([0x01020304, 7], np.uint32),
+                      arg_off=np.array([0, 2, 3], np.uint32),
+                      region=np.array([0xA1B2C3D4, 5, 9], np.uint32),
+                      field_mask=np.array([0x1122334455667788, 1, 2], np.uint64),
+                      priv=np.array([3, 0, 1], np.uint8))
+    want0 = (struct.pack("<II", 0x01020304, 2)
+             + struct.pack("<IQB", 0xA1B2C3D4, 0x1122334455667788, 3)
+             + struct.pack("<IQB", 5, 1, 0))
+    want1 = struct.pack("<II", 7, 1) + struct.pack("<IQB", 9, 2, 1)
+    assert oracle.serialize_task(ts, 0) == want0
+    assert oracle.serialize_task(ts, 1) == want1
+    h = oracle.hash_tasks(ts)
+    assert int(h[0]) == fnv1a64_py(want0) and int(h[1]) == fnv1a64_py(want1)
+
+
+def test_hash_argument_order_and_fields_matter():
+    base = dict(task_id=np.array([1, 1, 1, 1, 1], np.uint32),
+                arg_off=np.array([0, 2, 4, 6, 8, 10], np.uint32))
+    # t0 base, t1 arguments swapped, t2 another field mask, t3 another privilege, t4 = t0
+    region = np.array([1, 2, 2, 1, 1, 2, 1, 2, 1, 2], np.uint32)
+    mask = np.array([1, 1, 1, 1, 3, 1, 1, 1, 1, 1], np.uint64)
+    priv = np.array([0, 1, 1, 0, 0, 1, 1, 1, 0, 1], np.uint8)
+    h = oracle.hash_tasks(W.TaskStream(region=region, field_mask=mask, priv=priv, **base))
+    # same regions in swapped order, a different field mask, a different privilege
+    assert len(set(h[:4].tolist())) == 4
+    assert h[0] == h[4]
+
+
+def test_jacobi_stream(golden):
+    g = golden("jacobi.json")
+    ts = W.jacobi_tasks(g["iterations"])
+    tok = oracle.hash_tasks(ts)
+    cls = g["token_classes"]
+    for i in range(len(cls)):
+        for j in range(len(cls)):
+            assert (tok[i] == tok[j]) == (cls[i] == cls[j])
+    r = oracle.find_repeats(tok, g["min_len"])
+    assert list(zip(r.sel_start.tolist(), r.sel_len.tolist())) == [tuple(x) for x in g["selected"]]
+    assert len(r.trace_len) == g["n_traces"]
+
+
+# ---------------------------------------------------------------- worked examples
+@pytest.mark.parametrize("name", ["aabcbcbaa.json", "ababab.json"])
+def test_worked_examples(golden, name):
+    g = golden(name)
+    S = [ord(c) for c in g["string"]]
+    for ml, res in g["results"].items():
+        r = check_window(S, int(ml))
+        assert r.sa.tolist() == g["sa"]
+        assert r.lcp.tolist() == g["lcp"]
+        assert list(zip(r.sel_start.tolist(), r.sel_len.tolist())) == [tuple(x) for x in res["selected"]]
+        got = ["".join(chr(S[s + k]) for k in range(l)) for l, s in zip(r.trace_len.tolist(), r.trace_start.tolist())]
+        assert got == res["traces"]
+
+
+def test_aabcbcbaa_raw_candidates(golden):
+    g = golden("aabcbcbaa.json")
+    S = [ord(c) for c in g["string"]]
+    sa = oracle.suffix_array(S)
+    rl, rs = oracle.candidates_raw(sa, oracle.lcp(S, sa))
+    want = [(c["l"], st) for c in g["raw_candidates_per_pair"] for st in c["starts"]]
+    assert list(zip(rl.tolist(), rs.tolist())) == want
+
+
+def test_longest_repeat_claim_does_not_hold(golden):
+    g = golden("abababa.json")
+    S = [ord(c) for c in g["string"]]
+    r = check_window(S, 1)
+    assert r.sa.tolist() == g["sa"] and r.lcp.tolist() == g["lcp"]
+    assert int(r.cand_len.max()) == g["max_candidate_length"]
+    assert max(l for l, _ in bf_nonoverlapping_repeats(S)) == g["longest_nonoverlapping_repeat"]
+
+
+# ---------------------------------------------------------------- brute force sweeps
+def test_all_binary_strings_up_to_10():
+    for n in range(0, 11):
+        for S in itertools.product(range(2), repeat=n):
+            check_window(S, 1 + (n % 3))
+
+
+def test_all_ternary_strings_up_to_7():
+    for n in range(1, 8):
+        for S in itertools.product(range(3), repeat=n):
+            check_window(S, 1 + (sum(S) % 2))
+
+
+def test_random_strings_up_to_12():
+    rng = W.uniform_int(77, 4000, 0, 1 << 30)
+    k = 0
+    for trial in range(400):
+        n = int(rng[k] % 12) + 1
+        sigma = int(rng[k + 1] % 4) + 1
+        k += 2
+        S = W.uniform_int(1000 + trial, n, 0, sigma - 1).tolist()
+        check_window(S, 1 + trial % 3)
+
+
+def test_unary_and_huge_tokens():
+    check_window([5] * 12, 1)
+    big = [0xFFFFFFFFFFFFFFFF, 0, 0xFFFFFFFFFFFFFFFF, 0, 1 << 63]
+    check_window(big, 1)
+
+
+# ---------------------------------------------------------------- larger cross-checks
+@pytest.mark.parametrize("kind", ["periodic", "random", "runs"])
+def test_sa_methods_and_lcp_methods_agree(kind):
+    if kind == "periodic":
+        S = W.config1_window(4096, seed=11)
+    elif kind == "random":
+        S = W.uniform_int(12, 4096, 0, 3)
+    else:
+        a, _ = W.config4_windows(3 * 1024)
+        S = a
+    S = np.asarray(S, dtype=np.uint64)
+    sa = oracle.suffix_array(S, "direct")
+    assert np.array_equal(np.sort(sa), np.arange(S.shape[0], dtype=np.uint32))
+    assert np.array_equal(sa, oracle.suffix_array(S, "doubling"))
+    assert np.array_equal(oracle.lcp(S, sa, "kasai"), oracle.lcp(S, sa, "direct"))
+
+
+def test_greedy_variants_agree_on_config1():
+    S = W.config1_window()
+    r = oracle.find_repeats(S, 5)
+    for v in (1, 2):
+        assert np.array_equal(oracle.greedy(S.shape[0], r.cand_len, r.cand_start, v), r.accepted)
+    # taken intervals are disjoint, the first candidate is the longest and is taken
+    ss, sl = r.sel_start.astype(np.int64), r.sel_len.astype(np.int64)
+    assert np.all(ss[1:] >= ss[:-1] + sl[:-1])
+    assert r.accepted[0] == 1 and r.cand_len[0] == r.cand_len.max()
+    assert sl.sum() <= S.shape[0]
+
+
+# ---------------------------------------------------------------- matching
+def test_ushers(golden):
+    g = golden("ushers.json")
+    toks, off = [], [0]
+    for p in g["patterns"]:
+        toks += [ord(c) for c in p]
+        off.append(len(toks))
+    text = [ord(c) for c in g["text"]]
+    for naive in (False, True):
+        e, i = oracle.match(toks, off, text, naive)
+        assert list(zip(e.tolist(), i.tolist())) == [tuple(x) for x in g["matches"]]
+
+
+def test_match_bruteforce_random():
+    for trial in range(30):
+        n = 200
+        text = W.uniform_int(500 + trial, n, 0, 2).tolist()
+        P = 12
+        lens = W.uniform_int(600 + trial, P, 1, 6).tolist()
+        pats = [W.uniform_int(700 + 31 * trial + p, lens[p], 0, 2).tolist() for p in range(P)]
+        pats.append(pats[0])  # duplicate pattern: reported under both ids
+        toks = [t for p in pats for t in p]
+        off = np.cumsum([0] + [len(p) for p in pats])
+        want = sorted((e, p) for p, pat in enumerate(pats) for e in range(len(pat) - 1, n)
+                      if text[e - len(pat) + 1:e + 1] == pat)
+        for naive in (False, True):
+            e, i = oracle.match(toks, off, text, naive)
+            assert list(zip(e.tolist(), i.tolist())) == want
