@@ -1,0 +1,189 @@
+/*
+ * apo.h -- C ABI of libapo, the GPU trace finder.
+ *
+ * The library computes the string analysis at the heart of automatic trace
+ * identification (Yadav et al., "Automatic Tracing in Task-Based Runtime
+ * Systems", ASPLOS 2025): task descriptors are hashed to tokens (Alg. 1,
+ * Sec. 4.1), a window of tokens is turned into non-overlapping repeated
+ * sub-strings (Alg. 2, Sec. 4.2), and the resulting candidate traces are
+ * matched against a token stream (Sec. 4.3).  All work runs in CUDA kernels
+ * on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller unless a
+ *     function says otherwise; the library never frees them.
+ *   - Calls are issued on the CUDA stream `stream` (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Functions that must learn a
+ *     data-dependent size before they can continue synchronise that stream;
+ *     each function documents whether it returns before the work finishes.
+ *   - Every function returns an apo_status.  On failure, apo_last_error()
+ *     returns a message for the calling thread.  Errors detected inside a
+ *     kernel (a device wait that gave up, an index out of range) are
+ *     reported by the next call that synchronises, as APO_ETIMEOUT or
+ *     APO_EDEVICE.
+ *   - Sizes: a window holds at most 2^31 - 1 tokens.
+ *   - A context owns the device scratch memory ("workspace") of the calls
+ *     made with it and grows it on demand with cudaMalloc; it is bound to
+ *     the device that was current when it was created.  A context must not
+ *     be used by two host threads at the same time.
+ */
+#ifndef APO_H
+#define APO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APO_OK = 0,
+  APO_EINVAL = -1,     /* a bad argument (null pointer, bad size or token width) */
+  APO_ENOMEM = -2,     /* device memory could not be allocated */
+  APO_ECAPACITY = -3,  /* an output array is too small; the needed count is still written */
+  APO_ECUDA = -4,      /* a CUDA runtime call failed */
+  APO_ETIMEOUT = -5,   /* a bounded device-side wait gave up (the results are invalid) */
+  APO_EDEVICE = -6     /* a kernel detected an inconsistency (the results are invalid) */
+} apo_status;
+
+typedef struct apo_ctx apo_ctx;
+
+/* Create a context on `device` (a CUDA ordinal).  The device becomes current
+ * for the calling thread. */
+int apo_create(apo_ctx **ctx, int device);
+
+/* Release a context and the workspace it owns.  NULL is accepted. */
+int apo_destroy(apo_ctx *ctx);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *apo_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int apo_version(void);
+
+/* ------------------------------------------------------------------------
+ * Task hashing -- Alg. 1 "Hash(T)", Sec. 4.1; what a task is: Sec. 2
+ * (a task id plus its ordered region arguments, whose regions, fields and
+ * privileges all affect the dependence analysis).
+ *
+ * token[t] = FNV-1a-64 over the little-endian bytes
+ *     task_id[t]:u32, nargs:u32,
+ *     then for a in arg_off[t] .. arg_off[t+1]-1:
+ *         region[a]:u32, field_mask[a]:u64, priv[a]:u8
+ * where nargs = arg_off[t+1] - arg_off[t].
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t n_tasks;           /* N */
+  const uint32_t *task_id;    /* [N] */
+  const uint32_t *arg_off;    /* [N+1], non-decreasing CSR offsets into the argument arrays */
+  const uint32_t *region;     /* [arg_off[N]] */
+  const uint64_t *field_mask; /* [arg_off[N]] */
+  const uint8_t *priv;        /* [arg_off[N]] */
+} apo_tasks;
+
+/* Hash N task descriptors to tokens_out[N] (device).  Asynchronous: returns
+ * after enqueueing.  N = 0 is a no-op.  APO_EINVAL if a pointer needed for
+ * N > 0 is NULL. */
+int apo_hash_tasks(apo_ctx *ctx, const apo_tasks *tasks, uint64_t *tokens_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Repeat finding -- Alg. 2 "FindRepeats(S)", Sec. 4.2.
+ *
+ * For one window S of n tokens (u32 or u64, compared as unsigned integers):
+ *   SA   suffix array; a suffix that is a proper prefix of another sorts first.
+ *   LCP  LCP[i] = longest common prefix of suffixes SA[i] and SA[i+1];
+ *        LCP[n-1] = 0.
+ *   candidates  for every adjacent pair i (s1 = SA[i], s2 = SA[i+1],
+ *        p = LCP[i]): if [s1, s1+p) and [s2, s2+p) are disjoint (|s1-s2| >= p)
+ *        the pair (p, s1), (p, s2); otherwise, with lo = min(s1, s2) and
+ *        d = |s1 - s2|, l = floor((p + d) / 2) - (floor((p + d) / 2) mod d)
+ *        and the pair (l, lo), (l, lo + l).  Candidates shorter than min_len
+ *        are dropped, identical (length, start) pairs are kept once, and the
+ *        rest are ordered by length descending, sub-string ascending
+ *        (lexicographic over the tokens), start ascending.  A candidate's
+ *        id is the SA index of the first suffix that starts with its
+ *        sub-string, so equal ids (at equal length) mean equal sub-strings
+ *        and id order is sub-string order.
+ *   greedy selection  candidates are visited in that order; one is accepted
+ *        iff [start, start+len) meets no interval accepted before it.
+ *   R    the distinct accepted sub-strings ("traces") in the order of their
+ *        first acceptance; trace_start = smallest accepted start of the trace.
+ *   selected intervals  the accepted intervals by increasing start, with the
+ *        index into R of their sub-string.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t n;          /* tokens in the window */
+  const void *tokens;  /* device, n tokens of token_bytes each */
+  int token_bytes;     /* 4 (uint32) or 8 (uint64) */
+} apo_window;
+
+typedef struct {
+  uint32_t min_len;    /* minimum trace length, >= 1 (Sec. 3: traces must be long enough
+                          to amortise the replay cost) */
+  uint32_t flags;      /* reserved, must be 0 */
+} apo_repeats_params;
+
+typedef struct {
+  /* Optional stage outputs; NULL skips the copy. */
+  uint32_t *sa;              /* [n] */
+  uint32_t *lcp;             /* [n] */
+  uint32_t *cand_len;        /* [cand_cap] candidates in greedy order */
+  uint32_t *cand_id;         /* [cand_cap] */
+  uint32_t *cand_start;      /* [cand_cap] */
+  uint8_t *cand_accepted;    /* [cand_cap] 1 = accepted by the greedy loop */
+  uint64_t cand_cap;
+  /* Results. */
+  uint32_t *sel_start;       /* [sel_cap] accepted intervals by increasing start */
+  uint32_t *sel_len;         /* [sel_cap] */
+  uint32_t *sel_trace;       /* [sel_cap] index into the trace arrays */
+  uint64_t sel_cap;
+  uint32_t *trace_len;       /* [trace_cap] R in first-acceptance order */
+  uint32_t *trace_start;     /* [trace_cap] smallest accepted start of the trace */
+  uint64_t trace_cap;
+  /* HOST array of 4 counts, written before the call returns:
+   * [0] candidates, [1] accepted intervals, [2] traces, [3] doubling rounds. */
+  uint64_t *counts;
+} apo_repeats_out;
+
+/* Run Alg. 2 on one window.  Synchronises `stream` (the suffix sorting loop
+ * and the output sizes are data-dependent); all outputs are complete when it
+ * returns APO_OK.  APO_ECAPACITY if cand_cap (when cand_* is requested),
+ * sel_cap or trace_cap is too small: counts are still written and nothing
+ * beyond a capacity is touched.  Capacities that always suffice:
+ * cand_cap = 2(n-1), sel_cap = trace_cap = floor(n / min_len).
+ * n = 0 or 1 gives no candidates. */
+int apo_find_repeats(apo_ctx *ctx, const apo_window *window, const apo_repeats_params *params,
+                     apo_repeats_out *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Candidate matching -- Sec. 4.3: the candidate traces are ingested into a
+ * trie, and pointers advanced through the trie as tokens arrive report a
+ * trace whenever one ends.  Computed here with an Aho-Corasick automaton
+ * (goto trie, failure and output links) over the whole stream at once.
+ *
+ * Reports every (end, id) with stream[end - len(id) + 1 .. end] == pattern id,
+ * for all patterns (overlapping occurrences included; a pattern listed twice
+ * is reported under both ids), sorted by (end, id).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t n_patterns;       /* P >= 1 */
+  const void *tokens;        /* device, pat_off[P] tokens */
+  int token_bytes;           /* 4 or 8, same width as the stream */
+  const uint64_t *pat_off;   /* HOST [P+1] CSR offsets; every pattern non-empty */
+} apo_patterns;
+
+/* Match `patterns` against stream[n] (device, same token width).  Writes up
+ * to `cap` matches to match_end/match_id (device) and the total number of
+ * matches to *count (HOST).  Synchronises `stream`.  APO_ECAPACITY if the
+ * total exceeds cap (the first cap matches in order are written).
+ * APO_EINVAL for an empty pattern, P = 0, or mismatched token widths. */
+int apo_match_candidates(apo_ctx *ctx, const apo_patterns *patterns, const void *stream_tokens,
+                         uint64_t n, uint32_t *match_end, uint32_t *match_id, uint64_t cap,
+                         uint64_t *count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APO_H */

@@ -1,0 +1,235 @@
+"""GPU trace finder: Python binding of libapo (argument marshalling only).
+
+Every step of the analysis runs in the CUDA kernels of ``libapo.so`` behind
+the C ABI declared in ``include/apo.h``; this module only moves torch
+tensors' device pointers and sizes across it.  There is no CPU fallback: if
+the library is missing, or no GPU is present, calls raise.
+
+    from paper_2406_18111_gb300 import Apo
+    apo = Apo(device=0)
+    tokens = apo.hash_tasks(task_id, arg_off, region, field_mask, priv)   # Alg. 1 Hash
+    res = apo.find_repeats(tokens, min_len=5)                              # Alg. 2
+    end, pid = apo.match_candidates(pat_tokens, pat_off, stream_tokens)    # Sec. 4.3
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapo.so")
+
+APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECAPACITY, APO_ECUDA, APO_ETIMEOUT, APO_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+_NAMES = {0: "APO_OK", -1: "APO_EINVAL", -2: "APO_ENOMEM", -3: "APO_ECAPACITY", -4: "APO_ECUDA",
+          -5: "APO_ETIMEOUT", -6: "APO_EDEVICE"}
+
+# Every symbol include/apo.h declares.
+EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_hash_tasks",
+           "apo_find_repeats", "apo_match_candidates")
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+
+
+class ApoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class apo_tasks(ctypes.Structure):
+    _fields_ = [("n_tasks", _U64), ("task_id", _P), ("arg_off", _P), ("region", _P),
+                ("field_mask", _P), ("priv", _P)]
+
+
+class apo_window(ctypes.Structure):
+    _fields_ = [("n", _U64), ("tokens", _P), ("token_bytes", ctypes.c_int)]
+
+
+class apo_repeats_params(ctypes.Structure):
+    _fields_ = [("min_len", _U32), ("flags", _U32)]
+
+
+class apo_repeats_out(ctypes.Structure):
+    _fields_ = [("sa", _P), ("lcp", _P), ("cand_len", _P), ("cand_id", _P), ("cand_start", _P),
+                ("cand_accepted", _P), ("cand_cap", _U64), ("sel_start", _P), ("sel_len", _P),
+                ("sel_trace", _P), ("sel_cap", _U64), ("trace_len", _P), ("trace_start", _P),
+                ("trace_cap", _U64), ("counts", _P)]
+
+
+class apo_patterns(ctypes.Structure):
+    _fields_ = [("n_patterns", _U64), ("tokens", _P), ("token_bytes", ctypes.c_int),
+                ("pat_off", _P)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libapo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2406_18111_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.apo_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+        L.apo_destroy.argtypes = [_P]
+        L.apo_last_error.restype = ctypes.c_char_p
+        L.apo_last_error.argtypes = []
+        L.apo_version.argtypes = []
+        L.apo_hash_tasks.argtypes = [_P, ctypes.POINTER(apo_tasks), _P, _P]
+        L.apo_find_repeats.argtypes = [_P, ctypes.POINTER(apo_window),
+                                       ctypes.POINTER(apo_repeats_params),
+                                       ctypes.POINTER(apo_repeats_out), _P]
+        L.apo_match_candidates.argtypes = [_P, ctypes.POINTER(apo_patterns), _P, _U64, _P, _P, _U64,
+                                           ctypes.POINTER(_U64), _P]
+        for f in EXPORTS:
+            if f not in ("apo_last_error",):
+                getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != APO_OK:
+        raise ApoError(code, lib().apo_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _token_bytes(t) -> int:
+    import torch
+    if t.dtype in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        return 4
+    if t.dtype in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        return 8
+    raise TypeError(f"tokens must be 32- or 64-bit integers, got {t.dtype}")
+
+
+@dataclass
+class Repeats:
+    """Outputs of Alg. 2 on one window (device tensors, unsigned values held
+    in int32 bit patterns)."""
+    sa: object
+    lcp: object
+    cand_len: object
+    cand_id: object
+    cand_start: object
+    cand_accepted: object
+    sel_start: object
+    sel_len: object
+    sel_trace: object
+    trace_len: object
+    trace_start: object
+    rounds: int
+
+
+class Apo:
+    """A library context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libapo needs a CUDA GPU; none is available")
+        self.device = device
+        h = _P()
+        _check(lib().apo_create(ctypes.byref(h), device))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- Alg. 1 Hash
+    def hash_tasks(self, task_id, arg_off, region, field_mask, priv, out=None, stream=None):
+        """Tokens (int64 tensor holding u64 bit patterns) of N task descriptors."""
+        import torch
+        n = int(task_id.shape[0])
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, device=task_id.device)
+        t = apo_tasks(n, _ptr(task_id), _ptr(arg_off), _ptr(region), _ptr(field_mask), _ptr(priv))
+        _check(lib().apo_hash_tasks(self._h, ctypes.byref(t), _ptr(out), _stream_handle(stream)))
+        return out
+
+    # -------------------------------------------------------------- Alg. 2
+    def find_repeats(self, tokens, min_len: int, stages: bool = True, stream=None) -> Repeats:
+        """Alg. 2 on one window of device tokens (int32 = u32, int64 = u64)."""
+        import torch
+        n = int(tokens.shape[0])
+        dev = tokens.device
+        u32 = torch.int32
+        M = max(1, 2 * (n - 1))
+        K = max(1, n // max(1, min_len))
+        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
+        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
+        cl = torch.empty(M, dtype=u32, device=dev) if stages else None
+        ci = torch.empty(M, dtype=u32, device=dev) if stages else None
+        cs = torch.empty(M, dtype=u32, device=dev) if stages else None
+        ca = torch.empty(M, dtype=torch.uint8, device=dev) if stages else None
+        ss, sl, st, tl, ts = (torch.empty(K, dtype=u32, device=dev) for _ in range(5))
+        counts = (ctypes.c_uint64 * 4)()
+        o = apo_repeats_out(_ptr(sa), _ptr(lcp), _ptr(cl), _ptr(ci), _ptr(cs), _ptr(ca),
+                            M if stages else 0, _ptr(ss), _ptr(sl), _ptr(st), K, _ptr(tl), _ptr(ts), K,
+                            ctypes.cast(counts, _P))
+        w = apo_window(n, _ptr(tokens), _token_bytes(tokens))
+        p = apo_repeats_params(int(min_len), 0)
+        _check(lib().apo_find_repeats(self._h, ctypes.byref(w), ctypes.byref(p), ctypes.byref(o),
+                                      _stream_handle(stream)))
+        m, k, t, rounds = (int(x) for x in counts)
+
+        def cut(x, c):
+            return None if x is None else x[:c]
+        return Repeats(cut(sa, n), cut(lcp, n), cut(cl, m), cut(ci, m), cut(cs, m), cut(ca, m),
+                       ss[:k], sl[:k], st[:k], tl[:t], ts[:t], rounds)
+
+    # -------------------------------------------------------------- Sec. 4.3
+    def match_candidates(self, pat_tokens, pat_off, stream_tokens, cap: int | None = None,
+                         stream=None):
+        """All (end, pattern id) occurrences, sorted; pat_off is a host array."""
+        import torch
+        po = np.ascontiguousarray(np.asarray(pat_off, dtype=np.uint64))
+        n = int(stream_tokens.shape[0])
+        if cap is None:
+            cap = max(1, 4 * n)
+        end = torch.empty(max(1, cap), dtype=torch.int32, device=stream_tokens.device)
+        pid = torch.empty(max(1, cap), dtype=torch.int32, device=stream_tokens.device)
+        cnt = _U64(0)
+        p = apo_patterns(po.shape[0] - 1, _ptr(pat_tokens), _token_bytes(pat_tokens),
+                         po.ctypes.data_as(_P).value)
+        code = lib().apo_match_candidates(self._h, ctypes.byref(p), _ptr(stream_tokens), n, _ptr(end),
+                                          _ptr(pid), cap, ctypes.byref(cnt), _stream_handle(stream))
+        if code == APO_ECAPACITY:
+            return self.match_candidates(pat_tokens, pat_off, stream_tokens, int(cnt.value), stream)
+        _check(code)
+        c = int(cnt.value)
+        return end[:c], pid[:c]
+
+
+def as_u32(t) -> np.ndarray:
+    """Device int32 tensor (u32 bit patterns) -> numpy uint32."""
+    return t.cpu().numpy().view(np.uint32)
+
+
+def as_u64(t) -> np.ndarray:
+    """Device int64 tensor (u64 bit patterns) -> numpy uint64."""
+    return t.cpu().numpy().view(np.uint64)

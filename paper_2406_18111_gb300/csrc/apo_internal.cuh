@@ -1,0 +1,155 @@
+// Internal declarations shared by the libapo translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/apo.h"
+
+namespace apo {
+
+// ---------------------------------------------------------------- errors
+// Device error word values (set by kernels, read by the host at sync points).
+enum : uint32_t {
+  kDevOk = 0,
+  kDevTimeout = 1,   // a bounded spin gave up
+  kDevRange = 2,     // an index fell outside its array
+};
+
+// Iterations after which a device-side spin wait gives up (with back-off this
+// bounds a wait to well under a second).
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+void set_error(const std::string &msg);
+
+#define APO_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::apo::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+      return APO_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+#define APO_TRY(expr)          \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != APO_OK) return r_; \
+  } while (0)
+
+// ---------------------------------------------------------------- workspace
+// A bump allocator over one device buffer owned by the context.  reserve()
+// grows the buffer (cudaMalloc) only between calls, never inside a stream's
+// pending work; take() hands out 256-byte aligned slices.
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  int reserve(size_t bytes);
+  void reset() { used = 0; }
+  void *take(size_t bytes);
+  template <class T>
+  T *take_n(size_t n) { return static_cast<T *>(take(n * sizeof(T))); }
+};
+
+// Layout of the context's small device counter buffer (u32 words).
+enum : int {
+  kCtrSortHist = 0,       // radix sort digit histograms, 12 x 256
+  kCtrSortTiles = 3072,   // radix sort tile tickets, 12
+  kCtrMisc = 3136,        // per-kernel tile tickets and totals, see kMisc*
+  kCtrWords = 4096,
+};
+enum : int {
+  kMiscRefreshTiles = 0, kMiscRefreshCount, kMiscCompactTiles, kMiscCompactCount,
+  kMiscCandCount, kMiscMaxLen, kMiscAccCount, kMiscTraceCount, kMiscMatchCount,
+  kMiscKeyOr = 16,        // u64, two words
+  kMiscCount = 64,
+};
+
+// Per-context persistent device state.
+struct Persistent {
+  uint32_t *err = nullptr;        // device error word
+  uint64_t *lookback = nullptr;   // decoupled look-back status words
+  size_t lookback_words = 0;
+  uint32_t *counters = nullptr;   // small scratch counters (tile ids, totals)
+  uint32_t epoch = 0;             // look-back epoch, bumped per launch
+};
+
+}  // namespace apo
+
+struct apo_ctx {
+  int device = 0;
+  int num_sms = 0;
+  apo::Arena arena;
+  apo::Persistent ps;
+  uint32_t *host_pinned = nullptr;  // small pinned staging buffer (counts)
+};
+
+namespace apo {
+
+// Next look-back epoch (30 bits, never 0).
+inline uint32_t next_epoch(apo_ctx *c) {
+  c->ps.epoch = (c->ps.epoch + 1) & 0x3fffffffu;
+  if (c->ps.epoch == 0) c->ps.epoch = 1;
+  return c->ps.epoch;
+}
+
+int ensure_lookback(apo_ctx *c, size_t words);
+int check_device_error(apo_ctx *c, cudaStream_t s);
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int bits_for(uint64_t v) {  // number of bits to represent values 0..v
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD sort of (key u64, value u32) pairs on the digits listed in
+// `shifts` (8-bit digits starting at each shift, least significant first).
+// The result lands in (*keys, *vals); the other buffer of each pair is
+// scratch.  `count_dev`, when non-null, is a device word holding the element
+// count (<= n_max) and n_max bounds the launch.
+struct SortBuffers {
+  uint64_t *keys[2];
+  uint32_t *vals[2];
+  int cur = 0;  // index of the buffer holding the current data
+};
+int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *shifts, int npass,
+                     cudaStream_t s);
+// OR of all keys (to learn how many digits are populated); result in *out_dev.
+void launch_key_or(const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
+
+// Plan the 8-bit digit shifts covering bits [lo, hi) of a key.
+int plan_digits(int lo, int hi, int *shifts, int start);
+int radix_sort_init();
+
+// ---------------------------------------------------------------- suffix array
+struct SuffixState {
+  uint32_t n;
+  uint32_t *sa;
+  uint32_t *rank;
+  uint32_t **snaps;  // host array of device pointers: rank after level k
+  int levels;        // number of snapshots written
+};
+int build_suffix_array(apo_ctx *c, const void *tokens, int token_bytes, uint32_t n,
+                       SuffixState &st, int max_levels, uint32_t *rounds_out, cudaStream_t s);
+int build_lcp(apo_ctx *c, const void *tokens, int token_bytes, const SuffixState &st,
+              uint32_t *lcp, cudaStream_t s);
+
+// ---------------------------------------------------------------- repeats
+int find_repeats_from_sa(apo_ctx *c, const void *tokens, int token_bytes, const SuffixState &st,
+                         const uint32_t *lcp, uint32_t min_len, apo_repeats_out *out,
+                         cudaStream_t s);
+
+// ---------------------------------------------------------------- hashing
+void launch_hash_tasks(const apo_tasks *t, uint64_t *out, cudaStream_t s, int sms);
+
+// ---------------------------------------------------------------- matching
+int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
+                   uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
+                   cudaStream_t s);
+
+}  // namespace apo

@@ -1,0 +1,246 @@
+// The C ABI of libapo: contexts, workspace, argument checks and the three
+// entry points (apo_hash_tasks, apo_find_repeats, apo_match_candidates).
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "apo_internal.cuh"
+
+namespace apo {
+
+size_t suffix_workspace_bytes(uint64_t n);
+size_t repeats_workspace_bytes(uint64_t n);
+size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t cap);
+int suffix_init();
+int repeats_init(int smem_optin);
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int Arena::reserve(size_t bytes) {
+  used = 0;
+  if (bytes <= cap) return APO_OK;
+  if (base) {
+    cudaDeviceSynchronize();
+    cudaFree(base);
+    base = nullptr;
+    cap = 0;
+  }
+  const size_t want = std::max<size_t>(bytes, (size_t)1 << 24);
+  if (cudaMalloc(&base, want) != cudaSuccess) {
+    cudaGetLastError();
+    base = nullptr;
+    set_error("workspace: cudaMalloc of " + std::to_string(want) + " bytes failed");
+    return APO_ENOMEM;
+  }
+  cap = want;
+  return APO_OK;
+}
+
+void *Arena::take(size_t bytes) {
+  const size_t a = (used + 255) & ~(size_t)255;
+  if (a + bytes > cap) return nullptr;
+  used = a + bytes;
+  return base + a;
+}
+
+int ensure_lookback(apo_ctx *c, size_t words) {
+  if (words <= c->ps.lookback_words) return APO_OK;
+  // Growing frees the old array: wait for launches that may still read it.
+  APO_CUDA_TRY(cudaDeviceSynchronize());
+  if (c->ps.lookback) cudaFree(c->ps.lookback);
+  c->ps.lookback = nullptr;
+  c->ps.lookback_words = 0;
+  const size_t w = std::max<size_t>(words, 1 << 16);
+  APO_CUDA_TRY(cudaMalloc(&c->ps.lookback, w * sizeof(uint64_t)));
+  APO_CUDA_TRY(cudaMemset(c->ps.lookback, 0, w * sizeof(uint64_t)));
+  c->ps.lookback_words = w;
+  return APO_OK;
+}
+
+int check_device_error(apo_ctx *c, cudaStream_t s) {
+  (void)s;
+  uint32_t e = 0;
+  APO_CUDA_TRY(cudaMemcpy(&e, c->ps.err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (e == kDevOk) return APO_OK;
+  APO_CUDA_TRY(cudaMemset(c->ps.err, 0, sizeof(uint32_t)));
+  if (e == kDevTimeout) {
+    set_error("a bounded device-side wait gave up");
+    return APO_ETIMEOUT;
+  }
+  set_error("a kernel detected an out-of-range index");
+  return APO_EDEVICE;
+}
+
+}  // namespace apo
+
+using namespace apo;
+
+extern "C" {
+
+int apo_version(void) { return 100; }
+
+const char *apo_last_error(void) { return g_last_error.c_str(); }
+
+int apo_create(apo_ctx **out, int device) {
+  if (!out) {
+    set_error("apo_create: null output pointer");
+    return APO_EINVAL;
+  }
+  *out = nullptr;
+  APO_CUDA_TRY(cudaSetDevice(device));
+  apo_ctx *c = new apo_ctx();
+  c->device = device;
+  int sms = 0, optin = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->num_sms = sms > 0 ? sms : 1;
+  int r = APO_OK;
+  if ((r = radix_sort_init()) != APO_OK || (r = suffix_init()) != APO_OK ||
+      (r = repeats_init(optin)) != APO_OK) {
+    delete c;
+    return r;
+  }
+  if (cudaMalloc(&c->ps.err, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->ps.counters, kCtrWords * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(&c->host_pinned, 64) != cudaSuccess) {
+    cudaGetLastError();
+    apo_destroy(c);
+    set_error("apo_create: device allocation failed");
+    return APO_ENOMEM;
+  }
+  cudaMemset(c->ps.err, 0, sizeof(uint32_t));
+  cudaMemset(c->ps.counters, 0, kCtrWords * sizeof(uint32_t));
+  if (ensure_lookback(c, 1 << 16) != APO_OK) {
+    apo_destroy(c);
+    return APO_ENOMEM;
+  }
+  *out = c;
+  return APO_OK;
+}
+
+int apo_destroy(apo_ctx *c) {
+  if (!c) return APO_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->arena.base) cudaFree(c->arena.base);
+  if (c->ps.err) cudaFree(c->ps.err);
+  if (c->ps.lookback) cudaFree(c->ps.lookback);
+  if (c->ps.counters) cudaFree(c->ps.counters);
+  if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  delete c;
+  return APO_OK;
+}
+
+int apo_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *tokens_out, void *stream) {
+  if (!c || !t) {
+    set_error("apo_hash_tasks: null context or task list");
+    return APO_EINVAL;
+  }
+  if (t->n_tasks == 0) return APO_OK;
+  if (!t->task_id || !t->arg_off || !tokens_out) {
+    set_error("apo_hash_tasks: null task_id, arg_off or output");
+    return APO_EINVAL;
+  }
+  launch_hash_tasks(t, tokens_out, static_cast<cudaStream_t>(stream), c->num_sms);
+  APO_CUDA_TRY(cudaGetLastError());
+  return APO_OK;
+}
+
+int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *p,
+                     apo_repeats_out *out, void *stream) {
+  if (!c || !w || !p || !out || !out->counts) {
+    set_error("apo_find_repeats: null argument");
+    return APO_EINVAL;
+  }
+  for (int k = 0; k < 4; ++k) out->counts[k] = 0;
+  if (w->token_bytes != 4 && w->token_bytes != 8) {
+    set_error("apo_find_repeats: token_bytes must be 4 or 8");
+    return APO_EINVAL;
+  }
+  if (p->min_len == 0 || p->flags != 0) {
+    set_error("apo_find_repeats: min_len must be >= 1 and flags 0");
+    return APO_EINVAL;
+  }
+  if (w->n > 0x7fffffffull) {
+    set_error("apo_find_repeats: a window holds at most 2^31 - 1 tokens");
+    return APO_EINVAL;
+  }
+  if (w->n > 0 && !w->tokens) {
+    set_error("apo_find_repeats: null tokens");
+    return APO_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t n = (uint32_t)w->n;
+  if (n == 0) return APO_OK;
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  APO_TRY(c->arena.reserve(suffix_workspace_bytes(n) + repeats_workspace_bytes(n) + (size_t)n * 16));
+  SuffixState st;
+  st.n = n;
+  st.sa = c->arena.take_n<uint32_t>(n);
+  st.rank = c->arena.take_n<uint32_t>(n);
+  const int max_levels = bits_for(n) + 2;
+  uint32_t *snap_base = c->arena.take_n<uint32_t>((size_t)max_levels * n);
+  uint32_t *lcp = c->arena.take_n<uint32_t>(n);
+  if (!st.sa || !st.rank || !snap_base || !lcp) {
+    set_error("apo_find_repeats: workspace too small");
+    return APO_ENOMEM;
+  }
+  uint32_t *snaps[40];
+  for (int k = 0; k < max_levels; ++k) snaps[k] = snap_base + (size_t)k * n;
+  st.snaps = snaps;
+  uint32_t rounds = 0;
+  APO_TRY(build_suffix_array(c, w->tokens, w->token_bytes, n, st, max_levels, &rounds, s));
+  APO_TRY(build_lcp(c, w->tokens, w->token_bytes, st, lcp, s));
+  if (out->sa) APO_CUDA_TRY(cudaMemcpyAsync(out->sa, st.sa, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  if (out->lcp) APO_CUDA_TRY(cudaMemcpyAsync(out->lcp, lcp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  const int r = find_repeats_from_sa(c, w->tokens, w->token_bytes, st, lcp, p->min_len, out, s);
+  out->counts[3] = rounds;
+  if (r == APO_OK) {
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    return check_device_error(c, s);
+  }
+  return r;
+}
+
+int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
+                         uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
+                         void *stream) {
+  if (!c || !p || !count || !p->pat_off) {
+    set_error("apo_match_candidates: null argument");
+    return APO_EINVAL;
+  }
+  *count = 0;
+  if (p->n_patterns == 0 || (p->token_bytes != 4 && p->token_bytes != 8)) {
+    set_error("apo_match_candidates: need at least one pattern and token_bytes 4 or 8");
+    return APO_EINVAL;
+  }
+  if (p->n_patterns >= 0xffffffffull || n >= 0xffffffffull) {
+    set_error("apo_match_candidates: too many patterns or stream tokens");
+    return APO_EINVAL;
+  }
+  for (uint64_t q = 0; q < p->n_patterns; ++q) {
+    if (p->pat_off[q + 1] <= p->pat_off[q]) {
+      set_error("apo_match_candidates: empty pattern or decreasing offsets");
+      return APO_EINVAL;
+    }
+  }
+  if (!p->tokens || (n > 0 && !stream_tokens) || (cap > 0 && (!match_end || !match_id))) {
+    set_error("apo_match_candidates: null tokens or outputs");
+    return APO_EINVAL;
+  }
+  if (p->pat_off[0] != 0) {
+    set_error("apo_match_candidates: pat_off[0] must be 0");
+    return APO_EINVAL;
+  }
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  const uint64_t total = p->pat_off[p->n_patterns];
+  APO_TRY(c->arena.reserve(match_workspace_bytes(total, p->n_patterns, n, cap)));
+  return match_patterns(c, p, stream_tokens, n, match_end, match_id, cap, count,
+                        static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

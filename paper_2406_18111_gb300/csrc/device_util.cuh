@@ -1,0 +1,132 @@
+// Device helpers: decoupled look-back status words and block-wide scans.
+//
+// Decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", NVIDIA TR 2016): each tile publishes its
+// aggregate, then walks back over its predecessors' status words until it
+// meets an inclusive prefix.  A status word packs the state in bits 63:62
+// (0 = not yet published, 1 = aggregate, 2 = inclusive prefix), a 30-bit
+// launch epoch in bits 61:32 and a 32-bit value, so one 64-bit store
+// publishes both the flag and the payload and the array never needs
+// clearing between launches (a word from another launch has another epoch).
+#pragma once
+
+#include <stdint.h>
+
+#include "apo_internal.cuh"
+
+namespace apo {
+
+enum : uint32_t { kLbNone = 0, kLbAggregate = 1, kLbInclusive = 2 };
+
+__device__ __forceinline__ uint64_t lb_pack(uint32_t state, uint32_t epoch, uint32_t value) {
+  return ((uint64_t)state << 62) | ((uint64_t)(epoch & 0x3fffffffu) << 32) | value;
+}
+
+__device__ __forceinline__ void lb_store(uint64_t *p, uint64_t w) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ uint64_t lb_load(const uint64_t *p) {
+  uint64_t w;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+
+struct OpSum {
+  __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; }
+};
+struct OpMax {
+  __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const { return a > b ? a : b; }
+};
+
+// Combine the published values of tiles t-1, t-2, ... (words at
+// status[j * stride]) until an inclusive one is found.  Bounded: after
+// kSpinLimit polls of a word that is not ready the wait gives up, records
+// kDevTimeout in *err and returns what it has (the launch's results are then
+// invalid and the host reports APO_ETIMEOUT).
+template <class Op>
+__device__ uint32_t lb_exclusive(const uint64_t *status, int stride, uint32_t t, uint32_t epoch,
+                                 Op op, uint32_t identity, uint32_t *err) {
+  uint32_t acc = identity;
+  long long j = (long long)t - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    uint64_t w = lb_load(status + (size_t)j * stride);
+    uint32_t st = (uint32_t)(w >> 62);
+    uint32_t ep = (uint32_t)(w >> 32) & 0x3fffffffu;
+    if (ep != epoch || st == kLbNone) {
+      if (++spins > kSpinLimit) {
+        atomicExch(err, kDevTimeout);
+        break;
+      }
+      if (spins > 32) __nanosleep(128);
+      continue;
+    }
+    acc = op(acc, (uint32_t)w);
+    if (st == kLbInclusive) break;
+    --j;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <class Op>
+__device__ __forceinline__ uint32_t warp_inclusive(uint32_t v, Op op) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v = op(v, o);
+  }
+  return v;
+}
+
+// Block-wide inclusive scan for blocks of NW warps; `scratch` holds NW words.
+// Returns the inclusive value; *total receives the block total.
+template <int NW, class Op>
+__device__ __forceinline__ uint32_t block_inclusive(uint32_t v, Op op, uint32_t identity,
+                                                    uint32_t *scratch, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = warp_inclusive(v, op);
+  if (lane == 31) scratch[warp] = inc;
+  __syncthreads();
+  uint32_t pre = identity, tot = identity;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    uint32_t x = scratch[w];
+    if (w < warp) pre = op(pre, x);
+    tot = op(tot, x);
+  }
+  __syncthreads();
+  *total = tot;
+  return op(pre, inc);
+}
+
+// Block-wide exclusive scan; *total receives the block total.
+template <int NW, class Op>
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, Op op, uint32_t identity,
+                                                    uint32_t *scratch, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_inclusive(v, op);
+  uint32_t wex = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) wex = identity;
+  if (lane == 31) scratch[warp] = inc;
+  __syncthreads();
+  uint32_t pre = identity, tot = identity;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t x = scratch[w];
+    if (w < warp) pre = op(pre, x);
+    tot = op(tot, x);
+  }
+  __syncthreads();
+  *total = tot;
+  return op(pre, wex);
+}
+
+}  // namespace apo

@@ -1,0 +1,571 @@
+// Alg. 2 after the suffix array: candidates, their order, the greedy
+// non-overlapping selection and the deduplicated result R.
+//
+//  candidates  one thread per adjacent SA pair (Alg. 2's first loop),
+//              candidates shorter than min_len dropped on the spot.
+//  ids         Sec. 4.2 replaces the sub-string in a candidate by a unique ID
+//              so that the sort and the deduplication are cheap.  The ID used
+//              here is the left end of the LCP interval that holds the pair:
+//              id = 1 + max{ j < i : LCP[j] < l } (0 if none), i.e. the SA index
+//              of the first suffix starting with the sub-string.  Equal-length
+//              distinct sub-strings occupy disjoint SA ranges in lexicographic
+//              order, so id order is sub-string order and the sort needs no
+//              token comparison.  The "previous smaller value" query walks a
+//              32-ary min-tree over LCP (up one level until a block with a
+//              smaller minimum lies to the left, then down into it).
+//  sort        (length desc, id asc, start asc): the onesweep radix sort over
+//              the start digits (value) then the (length, id) digits (key).
+//  dedup       identical (length, start) pairs are adjacent after the sort and
+//              are kept once (order-preserving compaction).
+//  greedy      the second loop of Alg. 2 is sequential by definition; it runs
+//              in one 1024-thread block with the mark array of Sec. 4.2 as a
+//              bitmap (in shared memory when the window fits).  Because the
+//              candidates come in non-increasing length, a candidate meets an
+//              accepted interval iff its first or last position is marked.
+//              Each round loads 1024 candidates, drops in parallel those whose
+//              ends are already marked, and one warp settles the few
+//              survivors in order, marking the accepted intervals.
+//  R           accepted candidates in order; a new trace starts where (length,
+//              id) changes; selected intervals are re-sorted by start.
+#include <algorithm>
+#include <cstring>
+
+#include "apo_internal.cuh"
+#include "device_util.cuh"
+
+namespace apo {
+
+namespace {
+
+constexpr int kMaxTree = 8;
+
+struct MinTree {
+  const uint32_t *lv[kMaxTree];
+  uint32_t cnt[kMaxTree];
+  int nlev;
+};
+
+__global__ void k_min32(const uint32_t *__restrict__ in, uint32_t nin, uint32_t *__restrict__ out,
+                        uint32_t nout) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nout; b += warps) {
+    const uint32_t i = b * 32 + lane;
+    uint32_t v = i < nin ? in[i] : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) out[b] = v;
+  }
+}
+
+__global__ void k_max_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t *out) {
+  uint32_t m = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, a[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// Largest j < k with level-0 value < l, or -1.
+__device__ long long prev_less(const MinTree &T, uint32_t k, uint32_t l, uint32_t *err) {
+  uint32_t x = k;
+  for (int lev = 0; lev < T.nlev; ++lev) {
+    const uint32_t *a = T.lv[lev];
+    const uint32_t lo = x & ~31u;
+    for (uint32_t j = x; j > lo;) {
+      --j;
+      if (a[j] < l) {
+        uint32_t idx = j;
+        for (int d = lev; d > 0; --d) {
+          const uint32_t *b = T.lv[d - 1];
+          const uint32_t first = idx * 32;
+          uint32_t jj = min(first + 32, T.cnt[d - 1]);
+          while (jj > first && b[jj - 1] >= l) --jj;
+          if (jj == first) {
+            atomicExch(err, kDevRange);
+            return -1;
+          }
+          idx = jj - 1;
+        }
+        return idx;
+      }
+    }
+    if (lo == 0) return -1;
+    x = lo >> 5;
+  }
+  return -1;
+}
+
+// Alg. 2 first loop.  Each kept pair writes two (key, start) entries with
+// key = ((lmax - l) << bi) | id.
+__global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ lcp,
+                           uint32_t n, uint32_t min_len, MinTree T, int bi, uint32_t lmax,
+                           uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                           uint32_t *count, uint32_t *err) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n - 1; base += stride) {
+    const uint32_t k = base + threadIdx.x;
+    bool ok = false;
+    uint32_t l = 0, a = 0, b = 0;
+    if (k < n - 1) {
+      const uint32_t s1 = sa[k], s2 = sa[k + 1], p = lcp[k];
+      const uint32_t lo = min(s1, s2), hi = max(s1, s2);
+      if (hi - lo >= p) {  // [s1, s1+p) and [s2, s2+p) are disjoint
+        l = p;
+        a = s1;
+        b = s2;
+      } else {             // the common prefix is a run of S[lo, lo + d)
+        const uint32_t d = hi - lo;
+        uint64_t h = ((uint64_t)p + d) / 2;
+        h -= h % d;
+        l = (uint32_t)h;
+        a = lo;
+        b = lo + l;
+      }
+      ok = l >= min_len && l > 0;
+    }
+    uint64_t key = 0;
+    if (ok) {
+      const long long j = prev_less(T, k, l, err);
+      key = ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1);
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+    if (bal == 0) continue;
+    const int leader = __ffs(bal) - 1;
+    uint32_t slot0 = 0;
+    if ((int)lane == leader) slot0 = atomicAdd(count, 2u * __popc(bal));
+    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+    if (ok) {
+      const uint32_t slot = slot0 + 2u * __popc(bal & lanemask_lt());
+      if (slot + 1 >= 2 * (n - 1)) {
+        atomicExch(err, kDevRange);
+        continue;
+      }
+      keys[slot] = key;
+      vals[slot] = a;
+      keys[slot + 1] = key;
+      vals[slot + 1] = b;
+    }
+  }
+}
+
+// Order-preserving compaction of the indices k < m with pred(k) (one
+// decoupled look-back sum-scan).
+constexpr int kCT = 256, kCI = 16, kCTile = kCT * kCI;
+
+struct PredFirstOfRun {  // k starts a run of identical (key, value) pairs
+  const uint64_t *keys;
+  const uint32_t *vals;
+  __device__ bool operator()(uint32_t k) const {
+    return k == 0 || keys[k] != keys[k - 1] || vals[k] != vals[k - 1];
+  }
+};
+struct PredFlag {
+  const uint8_t *f;
+  __device__ bool operator()(uint32_t k) const { return f[k] != 0; }
+};
+
+template <class Pred>
+__global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, uint32_t *__restrict__ out,
+                                                 uint32_t *count_out, uint64_t *status,
+                                                 uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+  __shared__ uint32_t s_tile, s_pre;
+  __shared__ uint32_t scr[kCT / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kCTile;
+  const uint64_t e0 = base + (uint64_t)tid * kCI;
+  uint32_t fb = 0;
+#pragma unroll
+  for (int i = 0; i < kCI; ++i)
+    if (e0 + i < m && pred((uint32_t)(e0 + i))) fb |= 1u << i;
+  uint32_t tot;
+  const uint32_t ex = block_exclusive<kCT / 32>(__popc(fb), OpSum(), 0u, scr, &tot);
+  if (tid == 0) {
+    lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
+    uint32_t pre = 0;
+    if (t > 0) {
+      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
+    }
+    s_pre = pre;
+    if (base + kCTile >= m) *count_out = pre + tot;
+  }
+  __syncthreads();
+  uint32_t r = s_pre + ex;
+#pragma unroll
+  for (int i = 0; i < kCI; ++i) {
+    if ((fb >> i) & 1u) {
+      if (r < m) out[r] = (uint32_t)(e0 + i); else atomicExch(err, kDevRange);
+      ++r;
+    }
+  }
+}
+
+__global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
+                              const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                              int bi, uint32_t lmax, uint32_t *__restrict__ cl,
+                              uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
+  const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+    const uint32_t k = sel[q];
+    const uint64_t key = keys[k];
+    cl[q] = lmax - (uint32_t)(key >> bi);
+    cid[q] = (uint32_t)(key & idmask);
+    cs[q] = vals[k];
+  }
+}
+
+// ---------------------------------------------------------------- greedy
+constexpr int kGT = 1024;
+
+template <bool kSmem>
+__device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
+  uint32_t w;
+  if (kSmem)
+    w = bits[x >> 5];
+  else
+    w = *(volatile const uint32_t *)(bits + (x >> 5));
+  return (w >> (x & 31)) & 1u;
+}
+
+template <bool kSmem>
+__global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ cl,
+                                                   const uint32_t *__restrict__ cs, uint32_t m,
+                                                   uint32_t n, uint32_t *gbits, uint8_t *acc,
+                                                   uint32_t *acc_count, uint32_t *err) {
+  extern __shared__ uint32_t sbits[];
+  __shared__ uint32_t s_l[kGT], s_s[kGT], s_k[kGT];
+  __shared__ uint32_t s_wc[32];
+  uint32_t *bits = kSmem ? sbits : gbits;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (kSmem) {
+    const uint32_t words = (n + 31) / 32;
+    for (uint32_t w = tid; w < words; w += kGT) sbits[w] = 0;
+  }
+  uint32_t nacc = 0;
+  uint32_t nl = 0, ns = 0;
+  if ((uint32_t)tid < m) {
+    nl = cl[tid];
+    ns = cs[tid];
+  }
+  __syncthreads();
+  for (uint32_t base = 0; base < m; base += kGT) {
+    const uint32_t k = base + tid;
+    const bool valid = k < m;
+    const uint32_t l = nl, s = ns;
+    if (k + kGT < m) {  // prefetch the next round
+      nl = cl[k + kGT];
+      ns = cs[k + kGT];
+    }
+    bool surv = false;
+    if (valid) {
+      acc[k] = 0;
+      if (l == 0 || (uint64_t)s + l > n) {
+        atomicExch(err, kDevRange);
+      } else {
+        surv = !marked<kSmem>(bits, s) && !marked<kSmem>(bits, s + l - 1);
+      }
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, surv);
+    if (lane == 0) s_wc[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+      const uint32_t c = s_wc[w];
+      off += w < warp ? c : 0;
+      total += c;
+    }
+    if (surv) {
+      const uint32_t q = off + __popc(bal & lanemask_lt());
+      s_l[q] = l;
+      s_s[q] = s;
+      s_k[q] = k;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (uint32_t q = 0; q < total; ++q) {
+        const uint32_t ql = s_l[q], qs = s_s[q], qe = qs + ql - 1;
+        if (!marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe)) {
+          const uint32_t w0 = qs >> 5, w1 = qe >> 5;
+          for (uint32_t w = w0 + lane; w <= w1; w += 32) {
+            uint32_t msk = 0xffffffffu;
+            if (w == w0) msk &= 0xffffffffu << (qs & 31);
+            if (w == w1) msk &= 0xffffffffu >> (31 - (qe & 31));
+            bits[w] |= msk;
+          }
+          if (lane == 0) {
+            acc[s_k[q]] = 1;
+            ++nacc;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *acc_count = nacc;
+}
+
+// Accepted candidates (compacted, in order) -> R and the keys of the
+// selected intervals.  One block; K is at most n / min_len.
+__global__ void __launch_bounds__(1024) k_traces(const uint32_t *__restrict__ accidx, uint32_t K,
+                                                 const uint32_t *__restrict__ cl,
+                                                 const uint32_t *__restrict__ cid,
+                                                 const uint32_t *__restrict__ cs,
+                                                 uint32_t *__restrict__ tl, uint32_t *__restrict__ ts,
+                                                 uint64_t *__restrict__ skeys,
+                                                 uint32_t *__restrict__ svals, uint32_t *tcount) {
+  __shared__ uint32_t scr[32];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < K; base += 1024) {
+    const uint32_t q = base + threadIdx.x;
+    uint32_t f = 0, k = 0;
+    if (q < K) {
+      k = accidx[q];
+      if (q == 0) {
+        f = 1;
+      } else {
+        const uint32_t kp = accidx[q - 1];
+        f = (cl[k] != cl[kp] || cid[k] != cid[kp]) ? 1u : 0u;
+      }
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive<32>(f, OpSum(), 0u, scr, &tot);
+    const uint32_t carry = s_carry;
+    if (q < K) {
+      const uint32_t tr = carry + ex + f - 1;  // index of this candidate's trace
+      if (f) {
+        tl[tr] = cl[k];
+        ts[tr] = cs[k];
+      }
+      skeys[q] = ((uint64_t)cs[k] << 32) | cl[k];
+      svals[q] = tr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *tcount = s_carry;
+}
+
+__global__ void k_sel_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                          uint32_t K, uint32_t *__restrict__ ss, uint32_t *__restrict__ sl,
+                          uint32_t *__restrict__ st) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+    const uint64_t key = keys[q];
+    ss[q] = (uint32_t)(key >> 32);
+    sl[q] = (uint32_t)key;
+    st[q] = vals[q];
+  }
+}
+
+int g_greedy_smem_max = 0;  // dynamic shared memory available to k_greedy<true>
+
+inline int grid_for(uint64_t n, int threads, int sms) {
+  long long b = (long long)((n + threads - 1) / threads);
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
+}
+
+int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  APO_TRY(check_device_error(c, s));
+  *host = c->host_pinned[0];
+  return APO_OK;
+}
+
+template <class Pred>
+int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_dev, cudaStream_t s) {
+  const int tiles = std::max(1, ceil_div(m, kCTile));
+  APO_TRY(ensure_lookback(c, tiles));
+  uint32_t *tctr = c->ps.counters + kCtrMisc + kMiscCompactTiles;
+  APO_CUDA_TRY(cudaMemsetAsync(tctr, 0, sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
+  k_compact<<<tiles, kCT, 0, s>>>(pred, m, out, count_dev, c->ps.lookback, tctr, next_epoch(c),
+                                  c->ps.err);
+  APO_CUDA_TRY(cudaGetLastError());
+  return APO_OK;
+}
+
+template <class T>
+int copy_out(T *dst, const T *src, uint64_t count, uint64_t cap, bool *over, cudaStream_t s) {
+  if (!dst) return APO_OK;
+  if (count > cap) *over = true;
+  const uint64_t k = std::min(count, cap);
+  if (k) APO_CUDA_TRY(cudaMemcpyAsync(dst, src, k * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  return APO_OK;
+}
+
+}  // namespace
+
+int repeats_init(int smem_optin) {
+  // static shared memory of k_greedy: 3 * 1024 + 32 words
+  g_greedy_smem_max = smem_optin - (3 * kGT + 64) * 4;
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    g_greedy_smem_max));
+  return APO_OK;
+}
+
+size_t repeats_workspace_bytes(uint64_t n) {
+  const uint64_t M = n ? 2 * (n - 1) : 0;
+  return (size_t)M * (2 * 8 + 2 * 4)  // sort buffers
+         + (size_t)M * (4 * 3 + 4 + 1)  // candidate arrays, compaction indices, flags
+         + (size_t)n * 20                // R and the selected intervals (5 arrays of <= n)
+         + (size_t)n * 4 / 16 + (size_t)n / 8 + 64 * 256;
+}
+
+int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixState &st,
+                         const uint32_t *lcp, uint32_t min_len, apo_repeats_out *out,
+                         cudaStream_t s) {
+  (void)tokens;
+  (void)tb;
+  const uint32_t n = st.n;
+  uint64_t *counts = out->counts;
+  counts[0] = counts[1] = counts[2] = 0;
+  if (n < 2) return APO_OK;
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  const int g = grid_for(n, 256, c->num_sms);
+
+  // bits of the (length, id) key
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMaxLen, 0, sizeof(uint32_t), s));
+  k_max_u32<<<g, 256, 0, s>>>(lcp, n, misc + kMiscMaxLen);
+  uint32_t maxlcp = 0;
+  APO_TRY(read_u32(c, misc + kMiscMaxLen, &maxlcp, s));
+  const int bl = std::max(1, bits_for(maxlcp));
+  const uint32_t lmax = (uint32_t)((1ull << bl) - 1);
+  const int bi = std::max(1, bits_for(n - 1));
+  const int bs = bi;
+
+  // 32-ary min-tree over LCP
+  MinTree T;
+  T.lv[0] = lcp;
+  T.cnt[0] = n;
+  T.nlev = 1;
+  while (T.cnt[T.nlev - 1] > 32) {
+    if (T.nlev >= kMaxTree) {
+      set_error("repeats: window too large for the LCP min-tree");
+      return APO_EINVAL;
+    }
+    const uint32_t nin = T.cnt[T.nlev - 1], nout = (nin + 31) / 32;
+    uint32_t *o = c->arena.take_n<uint32_t>(nout);
+    if (!o) return APO_ENOMEM;
+    k_min32<<<grid_for((uint64_t)nout * 32, 256, c->num_sms), 256, 0, s>>>(T.lv[T.nlev - 1], nin, o,
+                                                                           nout);
+    T.lv[T.nlev] = o;
+    T.cnt[T.nlev] = nout;
+    ++T.nlev;
+  }
+
+  // candidates
+  const uint64_t M = 2ull * (n - 1);
+  SortBuffers b;
+  b.keys[0] = c->arena.take_n<uint64_t>(M);
+  b.keys[1] = c->arena.take_n<uint64_t>(M);
+  b.vals[0] = c->arena.take_n<uint32_t>(M);
+  b.vals[1] = c->arena.take_n<uint32_t>(M);
+  uint32_t *sel = c->arena.take_n<uint32_t>(M);
+  uint32_t *cl = c->arena.take_n<uint32_t>(M);
+  uint32_t *cid = c->arena.take_n<uint32_t>(M);
+  uint32_t *cs = c->arena.take_n<uint32_t>(M);
+  uint8_t *acc = c->arena.take_n<uint8_t>(M);
+  uint32_t *gbits = c->arena.take_n<uint32_t>((n + 31) / 32 + 1);
+  if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !sel || !cl || !cid || !cs || !acc ||
+      !gbits) {
+    set_error("repeats: workspace too small");
+    return APO_ENOMEM;
+  }
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCandCount, 0, sizeof(uint32_t), s));
+  k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, lmax, b.keys[0], b.vals[0],
+                               misc + kMiscCandCount, c->ps.err);
+  APO_CUDA_TRY(cudaGetLastError());
+  uint32_t mraw = 0;
+  APO_TRY(read_u32(c, misc + kMiscCandCount, &mraw, s));
+  uint32_t m = 0;
+  if (mraw) {
+    int places[16];
+    int np = plan_digits(0, bs, places, 0);
+    for (int p = 0; p < np; ++p) places[p] |= 256;  // start digits come from the value
+    np = plan_digits(0, bi + bl, places, np);
+    b.cur = 0;
+    APO_TRY(radix_sort_pairs(c, b, mraw, places, np, s));
+    PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
+    APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCompactCount, s));
+    APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
+    k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur],
+                                                               b.vals[b.cur], bi, lmax, cl, cid, cs);
+  }
+
+  // greedy selection
+  uint32_t K = 0;
+  if (m) {
+    const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
+    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
+    if ((long long)bm_bytes <= g_greedy_smem_max) {
+      k_greedy<true><<<1, kGT, bm_bytes, s>>>(cl, cs, m, n, nullptr, acc, misc + kMiscAccCount,
+                                              c->ps.err);
+    } else {
+      APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, bm_bytes, s));
+      k_greedy<false><<<1, kGT, 0, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount, c->ps.err);
+    }
+    APO_CUDA_TRY(cudaGetLastError());
+    APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
+  }
+
+  // R and the selected intervals
+  uint32_t Tn = 0;
+  uint32_t *tl = c->arena.take_n<uint32_t>(std::max<uint32_t>(K, 1));
+  uint32_t *ts = c->arena.take_n<uint32_t>(std::max<uint32_t>(K, 1));
+  uint32_t *ss = c->arena.take_n<uint32_t>(std::max<uint32_t>(K, 1));
+  uint32_t *sl = c->arena.take_n<uint32_t>(std::max<uint32_t>(K, 1));
+  uint32_t *sq = c->arena.take_n<uint32_t>(std::max<uint32_t>(K, 1));
+  if (!tl || !ts || !ss || !sl || !sq) return APO_ENOMEM;
+  if (K) {
+    PredFlag pf{acc};
+    APO_TRY(compact(c, pf, m, sel, misc + kMiscCompactCount, s));
+    SortBuffers sb;
+    sb.keys[0] = b.keys[0];
+    sb.keys[1] = b.keys[1];
+    sb.vals[0] = b.vals[0];
+    sb.vals[1] = b.vals[1];
+    sb.cur = 0;
+    k_traces<<<1, 1024, 0, s>>>(sel, K, cl, cid, cs, tl, ts, sb.keys[0], sb.vals[0],
+                                misc + kMiscTraceCount);
+    int places[8];
+    const int np = plan_digits(32, 32 + bits_for(n - 1), places, 0);
+    APO_TRY(radix_sort_pairs(c, sb, K, places, np, s));
+    k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K,
+                                                           ss, sl, sq);
+    APO_CUDA_TRY(cudaGetLastError());
+    APO_TRY(read_u32(c, misc + kMiscTraceCount, &Tn, s));
+  }
+
+  bool over = false;
+  APO_TRY(copy_out(out->cand_len, cl, m, out->cand_cap, &over, s));
+  APO_TRY(copy_out(out->cand_id, cid, m, out->cand_cap, &over, s));
+  APO_TRY(copy_out(out->cand_start, cs, m, out->cand_cap, &over, s));
+  APO_TRY(copy_out(out->cand_accepted, acc, m, out->cand_cap, &over, s));
+  APO_TRY(copy_out(out->sel_start, ss, K, out->sel_cap, &over, s));
+  APO_TRY(copy_out(out->sel_len, sl, K, out->sel_cap, &over, s));
+  APO_TRY(copy_out(out->sel_trace, sq, K, out->sel_cap, &over, s));
+  APO_TRY(copy_out(out->trace_len, tl, Tn, out->trace_cap, &over, s));
+  APO_TRY(copy_out(out->trace_start, ts, Tn, out->trace_cap, &over, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  APO_TRY(check_device_error(c, s));
+  counts[0] = m;
+  counts[1] = K;
+  counts[2] = Tn;
+  if (over) {
+    set_error("find_repeats: an output capacity is too small (counts written)");
+    return APO_ECAPACITY;
+  }
+  return APO_OK;
+}
+
+}  // namespace apo

@@ -1,0 +1,343 @@
+// Suffix array by prefix doubling, and the LCP array by Phi / PLCP.
+//
+// Alg. 2 starts with SuffixArray(S) -> SA, LCP.  The suffix array is built
+// by prefix doubling (Manber & Myers 1993) on the GPU in the style of
+// Larsson & Sadakane: a suffix's rank is the SA position where its group of
+// suffixes with an equal 2^r-token prefix starts.  Round r sorts only the
+// suffixes whose group is not yet a singleton, by the key
+// (rank[i], rank[i+h] + 1) with h = 2^r (0 when i + h runs past the end, so
+// a proper prefix sorts first), with the onesweep radix sort.  The active
+// suffixes are kept in SA order, so the k-th sorted key takes the k-th
+// smallest active SA position: no segment bookkeeping is needed.  A single
+// refresh kernel then finds the new group heads, writes SA and ranks, and
+// compacts the suffixes that still share a group (one decoupled look-back
+// max-scan for the head positions, one sum-scan for the compaction).
+//
+// Each round's rank array is kept ("level" r ranks: equal iff the first 2^r
+// tokens are equal).  The LCP array follows Karkkainen, Manzini & Puglisi
+// (CPM 2009): Phi[SA[k]] = SA[k-1]; PLCP[i] = lcp(i, Phi[i]) >= PLCP[i-1] - 1
+// is computed in chunks with direct token comparison, and a match that keeps
+// going is finished in O(levels) steps by binary lifting over the kept ranks;
+// finally LCP[k] = PLCP[SA[k+1]] (LCP[k] pairs SA[k] with SA[k+1]).
+#include <algorithm>
+#include <cstring>
+
+#include "apo_internal.cuh"
+#include "device_util.cuh"
+
+namespace apo {
+
+namespace {
+
+constexpr int kRT = 256;            // refresh threads per block
+constexpr int kRI = 16;             // consecutive elements per thread
+constexpr int kRTile = kRT * kRI;   // 4096
+constexpr uint32_t kNone = 0xffffffffu;
+constexpr size_t kRefreshSmem = (size_t)(kRTile + 2) * 8 + (size_t)kRTile * 8;
+
+__global__ void k_init_keys(const void *__restrict__ tokens, int tb, uint32_t n,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    keys[i] = tb == 4 ? (uint64_t) static_cast<const uint32_t *>(tokens)[i]
+                      : static_cast<const uint64_t *>(tokens)[i];
+    vals[i] = i;
+  }
+}
+
+// Sorted (key, suffix) pairs of the active suffixes -> new group heads, SA,
+// ranks and the next active list.  actpos == nullptr means position = index
+// (the first call, where the sorted list is the whole SA).
+__global__ void __launch_bounds__(kRT) k_refresh(
+    const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx, uint32_t A,
+    const uint32_t *__restrict__ actpos, uint32_t *__restrict__ sa, uint32_t *__restrict__ rank,
+    uint32_t *__restrict__ act_next, uint32_t *__restrict__ pos_next, uint32_t n, uint32_t *count_out,
+    uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(smem);           // [kRTile + 2], key[base-1 ..]
+  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kRTile + 2);  // [kRTile]
+  uint32_t *sp = si + kRTile;                                     // [kRTile]
+  __shared__ uint32_t s_tile, s_pmax, s_psum;
+  __shared__ uint32_t scr[kRT / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kRTile;
+  const uint32_t cnt = (A - base) < (uint64_t)kRTile ? (uint32_t)(A - base) : (uint32_t)kRTile;
+  for (uint32_t q = tid; q < cnt + 2; q += kRT) {
+    const long long g = (long long)base - 1 + q;
+    sk[q] = (g >= 0 && g < (long long)A) ? keys[g] : 0;
+  }
+  for (uint32_t q = tid; q < cnt; q += kRT) {
+    si[q] = idx[base + q];
+    sp[q] = actpos ? actpos[base + q] : (uint32_t)(base + q);
+  }
+  __syncthreads();
+
+  const uint32_t e0 = tid * kRI;
+  uint32_t hb = 0;  // bit i: element e0+i starts a group (bit kRI: the element after)
+#pragma unroll
+  for (int i = 0; i <= kRI; ++i) {
+    const uint32_t local = e0 + i;
+    if (local <= cnt) {
+      const uint64_t g = base + local;
+      if (g == 0 || g == A || sk[local + 1] != sk[local]) hb |= 1u << i;
+    }
+  }
+  uint32_t tmax = 0, tcnt = 0;
+  bool thead = false;
+#pragma unroll
+  for (int i = 0; i < kRI; ++i) {
+    if (e0 + i < cnt) {
+      const bool h = (hb >> i) & 1u;
+      if (h) {
+        tmax = sp[e0 + i];
+        thead = true;
+      }
+      if (!(h && ((hb >> (i + 1)) & 1u))) ++tcnt;
+    }
+  }
+  uint32_t tot_max, tot_sum;
+  const uint32_t ex_max = block_exclusive<kRT / 32>(tmax, OpMax(), 0u, scr, &tot_max);
+  const uint32_t ex_sum = block_exclusive<kRT / 32>(tcnt, OpSum(), 0u, scr, &tot_sum);
+  const int any_head = __syncthreads_or(thead);
+  if (tid == 0) {
+    const bool incl = t == 0 || any_head;
+    lb_store(&st_max[t], lb_pack(incl ? kLbInclusive : kLbAggregate, epoch, tot_max));
+    uint32_t pm = 0;
+    if (t > 0) pm = lb_exclusive(st_max, 1, t, epoch, OpMax(), 0u, err);
+    if (!incl) lb_store(&st_max[t], lb_pack(kLbInclusive, epoch, max(pm, tot_max)));
+    s_pmax = pm;
+  }
+  if (tid == 32) {
+    lb_store(&st_sum[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot_sum));
+    uint32_t ps = 0;
+    if (t > 0) {
+      ps = lb_exclusive(st_sum, 1, t, epoch, OpSum(), 0u, err);
+      lb_store(&st_sum[t], lb_pack(kLbInclusive, epoch, ps + tot_sum));
+    }
+    s_psum = ps;
+    if (base + cnt == A) *count_out = ps + tot_sum;
+  }
+  __syncthreads();
+  uint32_t rm = max(s_pmax, ex_max);
+  uint32_t rs = s_psum + ex_sum;
+#pragma unroll
+  for (int i = 0; i < kRI; ++i) {
+    const uint32_t local = e0 + i;
+    if (local < cnt) {
+      const bool h = (hb >> i) & 1u;
+      const uint32_t p = sp[local];
+      if (h) rm = p;
+      const uint32_t id = si[local];
+      if (p >= n || id >= n) {
+        atomicExch(err, kDevRange);
+        continue;
+      }
+      sa[p] = id;
+      rank[id] = rm;
+      if (!(h && ((hb >> (i + 1)) & 1u))) {
+        if (rs < A) {
+          act_next[rs] = id;
+          pos_next[rs] = p;
+        } else {
+          atomicExch(err, kDevRange);
+        }
+        ++rs;
+      }
+    }
+  }
+}
+
+// key = (rank[i] << 32) | (i + h < n ? rank[i + h] + 1 : 0), value = i.
+__global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ rank,
+                       uint32_t n, uint64_t h, uint64_t *__restrict__ keys,
+                       uint32_t *__restrict__ vals) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < A; k += gridDim.x * blockDim.x) {
+    const uint32_t i = act[k];
+    const uint64_t j = i + h;
+    const uint32_t r2 = j < n ? rank[j] + 1u : 0u;
+    keys[k] = ((uint64_t)rank[i] << 32) | r2;
+    vals[k] = i;
+  }
+}
+
+__global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, uint32_t *__restrict__ phi) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    phi[sa[k]] = k ? sa[k - 1] : kNone;
+}
+
+template <class T>
+__device__ __forceinline__ bool long_match(const T *__restrict__ S, uint32_t n, uint32_t i,
+                                           uint32_t j, uint32_t &l) {
+  uint32_t steps = 0;
+  while (i + (uint64_t)l < n && j + (uint64_t)l < n && S[i + l] == S[j + l]) {
+    ++l;
+    if (++steps == 32) return true;
+  }
+  return false;
+}
+
+// PLCP[i] = lcp(i, Phi[i]) over chunks of consecutive i, kRChunk per thread.
+constexpr int kPChunk = 16;
+template <class T>
+__global__ void k_plcp(const T *__restrict__ S, uint32_t n, const uint32_t *__restrict__ phi,
+                       const uint32_t *__restrict__ snaps, int levels, uint32_t *__restrict__ plcp) {
+  const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPChunk;
+  if (i0 >= n) return;
+  const uint32_t iend = (i0 + kPChunk) < (uint64_t)n ? (uint32_t)(i0 + kPChunk) : n;
+  uint32_t l = 0;
+  for (uint32_t i = (uint32_t)i0; i < iend; ++i) {
+    const uint32_t j = phi[i];
+    if (j == kNone) {
+      plcp[i] = 0;
+      l = 0;
+      continue;
+    }
+    if (long_match(S, n, i, j, l)) {
+      // lift: level lev ranks are equal iff the next 2^lev tokens are equal
+      for (int lev = levels - 1; lev >= 0; --lev) {
+        const uint64_t a = (uint64_t)i + l, b = (uint64_t)j + l;
+        if (a < n && b < n && snaps[(size_t)lev * n + a] == snaps[(size_t)lev * n + b])
+          l += 1u << lev;
+      }
+    }
+    plcp[i] = l;
+    l = l ? l - 1 : 0;
+  }
+}
+
+__global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ plcp,
+                           uint32_t n, uint32_t *__restrict__ lcp) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    lcp[k] = k + 1 < n ? plcp[sa[k + 1]] : 0u;
+}
+
+inline int grid_for(uint64_t n, int threads, int sms) {
+  long long b = (long long)((n + threads - 1) / threads);
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
+}
+
+int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *actpos,
+            uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
+            uint32_t *count_host, cudaStream_t s) {
+  const int tiles = ceil_div(A, kRTile);
+  APO_TRY(ensure_lookback(c, (size_t)2 * tiles));
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRefreshTiles, 0, 2 * sizeof(uint32_t), s));
+  const uint32_t ep = next_epoch(c);
+  k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, sa, rank, act_next, pos_next,
+                                             n, misc + kMiscRefreshCount, c->ps.lookback,
+                                             c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
+                                             c->ps.err);
+  APO_CUDA_TRY(cudaGetLastError());
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscRefreshCount, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  APO_TRY(check_device_error(c, s));
+  *count_host = c->host_pinned[0];
+  return APO_OK;
+}
+
+}  // namespace
+
+int suffix_init() {
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_refresh, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kRefreshSmem));
+  return APO_OK;
+}
+
+size_t suffix_workspace_bytes(uint64_t n) {
+  const int levels = bits_for(n) + 2;
+  return (size_t)n * (2 * 8 + 2 * 4 + 4 * 4 + 4 + 4) + (size_t)levels * n * 4 + 16 * 256;
+}
+
+int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, SuffixState &st,
+                       int max_levels, uint32_t *rounds_out, cudaStream_t s) {
+  st.n = n;
+  st.levels = 0;
+  *rounds_out = 0;
+  if (n == 0) return APO_OK;
+  SortBuffers b;
+  b.keys[0] = c->arena.take_n<uint64_t>(n);
+  b.keys[1] = c->arena.take_n<uint64_t>(n);
+  b.vals[0] = c->arena.take_n<uint32_t>(n);
+  b.vals[1] = c->arena.take_n<uint32_t>(n);
+  uint32_t *act[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
+  uint32_t *pos[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
+  if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !act[0] || !act[1] || !pos[0] ||
+      !pos[1]) {
+    set_error("suffix array: workspace too small");
+    return APO_ENOMEM;
+  }
+  const int g = grid_for(n, 256, c->num_sms);
+  k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
+  // how many token bits are populated
+  uint64_t *kor = reinterpret_cast<uint64_t *>(c->ps.counters + kCtrMisc + kMiscKeyOr);
+  APO_CUDA_TRY(cudaMemsetAsync(kor, 0, sizeof(uint64_t), s));
+  launch_key_or(b.keys[0], n, kor, s);
+  uint64_t orv = 0;
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  memcpy(&orv, c->host_pinned, sizeof(uint64_t));
+  int places[16];
+  int np = plan_digits(0, bits_for(orv), places, 0);
+  APO_TRY(radix_sort_pairs(c, b, n, places, np, s));
+  uint32_t A = 0;
+  APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, st.sa, st.rank, act[0], pos[0], n,
+                  &A, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[0], st.rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  st.levels = 1;
+  int cur = 0;
+  uint32_t rounds = 0;
+  const int minor_bits = bits_for(n), major_bits = bits_for(n - 1);
+  for (uint64_t h = 1; A > 0; h <<= 1) {
+    if (st.levels >= max_levels) {
+      set_error("suffix array: too many doubling rounds");
+      return APO_EDEVICE;
+    }
+    b.cur = 0;
+    k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, b.keys[0],
+                                                          b.vals[0]);
+    np = plan_digits(0, minor_bits, places, 0);
+    np = plan_digits(32, 32 + major_bits, places, np);
+    APO_TRY(radix_sort_pairs(c, b, A, places, np, s));
+    uint32_t A2 = 0;
+    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], A, pos[cur], st.sa, st.rank, act[cur ^ 1],
+                    pos[cur ^ 1], n, &A2, s));
+    cur ^= 1;
+    A = A2;
+    ++rounds;
+    APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[st.levels], st.rank, (size_t)n * 4,
+                                 cudaMemcpyDeviceToDevice, s));
+    ++st.levels;
+  }
+  *rounds_out = rounds;
+  return APO_OK;
+}
+
+int build_lcp(apo_ctx *c, const void *tokens, int tb, const SuffixState &st, uint32_t *lcp,
+              cudaStream_t s) {
+  const uint32_t n = st.n;
+  if (n == 0) return APO_OK;
+  uint32_t *phi = c->arena.take_n<uint32_t>(n);
+  uint32_t *plcp = c->arena.take_n<uint32_t>(n);
+  if (!phi || !plcp) {
+    set_error("lcp: workspace too small");
+    return APO_ENOMEM;
+  }
+  const int g = grid_for(n, 256, c->num_sms);
+  k_phi<<<g, 256, 0, s>>>(st.sa, n, phi);
+  const int pb = ceil_div(ceil_div(n, kPChunk), 128);
+  if (tb == 4)
+    k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, phi, st.snaps[0],
+                                        st.levels, plcp);
+  else
+    k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, phi, st.snaps[0],
+                                        st.levels, plcp);
+  k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, lcp);
+  APO_CUDA_TRY(cudaGetLastError());
+  return APO_OK;
+}
+
+}  // namespace apo

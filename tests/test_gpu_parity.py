@@ -1,0 +1,250 @@
+"""GPU path vs the oracle, bit-exact, through the C ABI (via the binding).
+
+Sizes: short strings (brute-force territory), windows spanning many 4096-key
+tiles with ragged tails, and the full workload sizes (2^20 hashed tasks,
+2^24 adversarial windows)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("sa", "lcp", "cand_len", "cand_id", "cand_start", "sel_start", "sel_len", "sel_trace",
+          "trace_len", "trace_start")
+
+
+@pytest.fixture(scope="module")
+def apo():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_18111_gb300 import Apo
+    a = Apo(0)
+    yield a
+    a.close()
+
+
+def dev(a, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+
+
+def tokens_dev(S, tb):
+    S = np.asarray(S)
+    if tb == 4:
+        return dev(S.astype(np.uint32), np.int32)
+    return dev(S.astype(np.uint64), np.int64)
+
+
+def compare(apo, S, min_len, tb=4, sa_method="direct"):
+    from paper_2406_18111_gb300 import as_u32
+    S = np.asarray(S)
+    r = apo.find_repeats(tokens_dev(S, tb), min_len)
+    o = oracle.find_repeats(S.astype(np.uint64), min_len, sa_method=sa_method)
+    for f in FIELDS:
+        got = as_u32(getattr(r, f))
+        want = getattr(o, f)
+        if got.shape != want.shape or not np.array_equal(got, want):
+            bad = np.nonzero(got[:min(len(got), len(want))] != want[:min(len(got), len(want))])[0]
+            raise AssertionError(f"{f}: shapes {got.shape} vs {want.shape}, first diffs at {bad[:5]}")
+    assert np.array_equal(r.cand_accepted.cpu().numpy(), o.accepted)
+    return r, o
+
+
+# ---------------------------------------------------------------- hashing
+@pytest.mark.parametrize("n", [1, 1000, 1 << 14, 1 << 20])
+def test_hash_config2(apo, n):
+    from paper_2406_18111_gb300 import as_u64
+    ts = W.config2_tasks(n)
+    tok = apo.hash_tasks(dev(ts.task_id, np.int32), dev(ts.arg_off, np.int32), dev(ts.region, np.int32),
+                         dev(ts.field_mask, np.int64), dev(ts.priv, np.uint8))
+    assert np.array_equal(as_u64(tok), oracle.hash_tasks(ts))
+
+
+def test_hash_jacobi(apo):
+    from paper_2406_18111_gb300 import as_u64
+    ts = W.jacobi_tasks(6)
+    tok = apo.hash_tasks(dev(ts.task_id, np.int32), dev(ts.arg_off, np.int32), dev(ts.region, np.int32),
+                         dev(ts.field_mask, np.int64), dev(ts.priv, np.uint8))
+    assert np.array_equal(as_u64(tok), oracle.hash_tasks(ts))
+
+
+# ---------------------------------------------------------------- repeats, small
+def test_worked_examples(apo, golden):
+    for name in ("aabcbcbaa.json", "ababab.json"):
+        g = golden(name)
+        S = [ord(c) for c in g["string"]]
+        for ml in g["results"]:
+            r, o = compare(apo, S, int(ml))
+            assert o.sa.tolist() == g["sa"]
+
+
+def test_short_strings(apo):
+    k = 0
+    for n in range(2, 13):
+        for sigma in (1, 2, 3):
+            for rep in range(3):
+                S = W.uniform_int(9000 + k, n, 0, sigma - 1)
+                k += 1
+                compare(apo, S, 1 + rep, tb=4 if rep % 2 == 0 else 8)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_degenerate_sizes(apo, n):
+    compare(apo, np.arange(n) % 2, 1)
+
+
+def test_constant_run_and_huge_tokens(apo):
+    compare(apo, np.zeros(5000, dtype=np.uint32), 1)
+    compare(apo, np.full(4097, 0xFFFFFFFF, dtype=np.uint32), 3, tb=4)
+    big = W.splitmix64(3, 6000) | np.uint64(1 << 63)
+    big[::7] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    compare(apo, np.concatenate([big, big[:3000]]), 2, tb=8)
+
+
+# ---------------------------------------------------------------- repeats, workloads
+@pytest.mark.parametrize("min_len", [1, 5, 25])
+def test_config1(apo, min_len):
+    compare(apo, W.config1_window(), min_len)
+
+
+@pytest.mark.parametrize("n", [1 << 14, (1 << 16) + 123])
+def test_config2_tokens_scaled(apo, n):
+    tok = oracle.hash_tasks(W.config2_tasks(n))
+    compare(apo, tok, 5, tb=8)
+
+
+def test_config2_full(apo):
+    tok = oracle.hash_tasks(W.config2_tasks(1 << 20))
+    r, o = compare(apo, tok, 5, tb=8)
+    assert r.rounds >= 1
+
+
+def test_config3_windows(apo):
+    toks, off, periods = W.config3_windows(24)
+    order = np.argsort(np.diff(off.astype(np.int64)))
+    pick = list(order[:4]) + list(order[-3:])
+    pick += [w for w in range(24) if periods[w] > off[w + 1] - off[w]][:2]  # only noise repeats
+    for w in sorted(set(int(x) for x in pick)):
+        S = toks[int(off[w]):int(off[w + 1])]
+        compare(apo, S, 5)
+
+
+def test_config4_scaled(apo):
+    a, b = W.config4_windows(3 * (1 << 12) + 5)
+    compare(apo, a, 5, sa_method="doubling")
+    compare(apo, b, 5)
+    compare(apo, a, 1, sa_method="doubling")
+
+
+def test_config4_full(apo):
+    """2^24 tokens: the random window bit-exact; the adversarial window against
+    invariants and sampled direct checks (the oracle's direct comparison is
+    quadratic on a constant run of 5.6M tokens)."""
+    from paper_2406_18111_gb300 import as_u32
+    a, b = W.config4_windows()
+    compare(apo, b, 5)
+    r = apo.find_repeats(tokens_dev(a, 4), 5)
+    n = a.shape[0]
+    sa = as_u32(r.sa).astype(np.int64)
+    lcp = as_u32(r.lcp).astype(np.int64)
+    assert np.array_equal(np.sort(sa), np.arange(n))
+    A64 = a.astype(np.uint64)
+    rng = W.uniform_int(44, 400, 0, n - 2)
+    sub_sa = []
+    for k in rng:
+        x, y = int(sa[k]), int(sa[k + 1])
+        # direct LCP via block comparison, then the order of the next token
+        L = 0
+        step = 1 << 16
+        while x + L < n and y + L < n:
+            m = min(step, n - x - L, n - y - L)
+            eq = A64[x + L:x + L + m] == A64[y + L:y + L + m]
+            if eq.all():
+                L += m
+                continue
+            L += int(np.argmin(eq))
+            break
+        assert lcp[k] == L, (k, x, y, lcp[k], L)
+        if x + L < n and y + L < n:
+            assert A64[x + L] < A64[y + L]
+        else:
+            assert x + L == n  # a proper prefix comes first
+        sub_sa.append(k)
+    # candidates and the greedy selection: structure that holds at any size
+    cl = as_u32(r.cand_len).astype(np.int64)
+    cs = as_u32(r.cand_start).astype(np.int64)
+    acc = r.cand_accepted.cpu().numpy().astype(bool)
+    assert np.all(np.diff(cl) <= 0)
+    assert acc[0] and cl[0] == cl.max()
+    ss = as_u32(r.sel_start).astype(np.int64)
+    sl = as_u32(r.sel_len).astype(np.int64)
+    assert np.all(ss[1:] >= ss[:-1] + sl[:-1])
+    assert sorted(zip(cs[acc].tolist(), cl[acc].tolist())) == list(zip(ss.tolist(), sl.tolist()))
+    # every rejected candidate meets an accepted interval (sampled)
+    cover = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(cover, ss, 1)
+    np.add.at(cover, ss + sl, -1)
+    covered = np.cumsum(cover)[:n] > 0
+    rej = np.nonzero(~acc)[0]
+    for k in rej[:: max(1, len(rej) // 2000)]:
+        assert covered[cs[k]] or covered[cs[k] + cl[k] - 1]
+
+
+# ---------------------------------------------------------------- matching
+def test_match_ushers(apo, golden):
+    from paper_2406_18111_gb300 import as_u32
+    g = golden("ushers.json")
+    toks, off = [], [0]
+    for p in g["patterns"]:
+        toks += [ord(c) for c in p]
+        off.append(len(toks))
+    for tb in (4, 8):
+        e, i = apo.match_candidates(tokens_dev(toks, tb), np.array(off, np.uint64),
+                                    tokens_dev([ord(c) for c in g["text"]], tb))
+        assert list(zip(as_u32(e).tolist(), as_u32(i).tolist())) == [tuple(x) for x in g["matches"]]
+
+
+@pytest.mark.parametrize("tb", [4, 8])
+def test_match_random(apo, tb):
+    from paper_2406_18111_gb300 import as_u32
+    for trial in range(5):
+        n = 5000 + 37 * trial
+        text = W.uniform_int(300 + trial, n, 0, 2)
+        P = 60
+        lens = W.uniform_int(400 + trial, P, 1, 9)
+        pats = [W.uniform_int(500 + 13 * trial + p, int(lens[p]), 0, 2) for p in range(P)]
+        pats.append(pats[3])
+        off = np.zeros(len(pats) + 1, np.uint64)
+        off[1:] = np.cumsum([len(p) for p in pats])
+        pt = np.concatenate(pats)
+        e, i = apo.match_candidates(tokens_dev(pt, tb), off, tokens_dev(text, tb))
+        oe, oi = oracle.match(pt, off, text)
+        assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
+
+
+def test_match_config5_scaled(apo):
+    from paper_2406_18111_gb300 import as_u32
+    stream = W.match_stream(1 << 20, seed=7)
+    pt, off = W.match_patterns(stream, 400, 5, 2000, seed=7)
+    e, i = apo.match_candidates(tokens_dev(pt, 4), off, tokens_dev(stream, 4))
+    oe, oi = oracle.match(pt, off, stream)
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
+
+
+# ---------------------------------------------------------------- errors
+def test_invalid_arguments(apo):
+    import torch
+    from paper_2406_18111_gb300 import ApoError
+    t = tokens_dev(np.arange(10), 4)
+    with pytest.raises(ApoError):
+        apo.find_repeats(t, 0)
+    with pytest.raises((ApoError, TypeError)):
+        apo.find_repeats(t.to(torch.int16), 1)
+    with pytest.raises(ApoError):
+        apo.match_candidates(t, np.array([0, 2, 2], np.uint64), t)
