@@ -172,7 +172,7 @@ def find_repeats(S, min_len: int, greedy_variant: int = 0, sa_method: str = "dir
 
 
 def match(pat_tokens, pat_off, stream, naive: bool = False):
-    """All (end, pattern) occurrences, sorted by (end, pattern)."""
+    """All (end, pattern) occurrences by end, then pattern length descending, then id."""
     pt = _tok(pat_tokens)
     po = np.ascontiguousarray(pat_off, dtype=np.uint64)
     st = _tok(stream)

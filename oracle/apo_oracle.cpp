@@ -342,20 +342,23 @@ void ora_find_repeats(const uint64_t *S, uint64_t n, const uint32_t *sa, const u
   counts[2] = ntr;
 }
 
-// All (end, pattern) pairs with stream[end-len+1 .. end] == pattern, sorted by
-// (end, pattern).  naive != 0 tries every pattern at every position; otherwise
+// All (end, pattern) pairs with stream[end-len+1 .. end] == pattern, ordered
+// by end ascending, pattern length descending, pattern id ascending.  naive != 0 tries every pattern at every position; otherwise
 // only the patterns whose first token equals stream[pos].  Returns the count
 // (entries beyond cap are not written).
 uint64_t ora_match(const uint64_t *pat_tok, const uint64_t *pat_off, uint64_t P,
                    const uint64_t *stream, uint64_t n, int naive, uint32_t *end_out,
                    uint32_t *id_out, uint64_t cap) {
-  std::vector<std::pair<uint64_t, uint64_t>> hits;
+  struct Hit {
+    uint64_t end, len, p;
+  };
+  std::vector<Hit> hits;
   auto try_at = [&](uint64_t pos, uint64_t p) {
     uint64_t len = pat_off[p + 1] - pat_off[p];
     if (len == 0 || pos + len > n) return;
     for (uint64_t k = 0; k < len; ++k)
       if (stream[pos + k] != pat_tok[pat_off[p] + k]) return;
-    hits.push_back({pos + len - 1, p});
+    hits.push_back({pos + len - 1, len, p});
   };
   if (naive) {
     for (uint64_t pos = 0; pos < n; ++pos)
@@ -370,10 +373,14 @@ uint64_t ora_match(const uint64_t *pat_tok, const uint64_t *pat_off, uint64_t P,
       for (uint64_t p : it->second) try_at(pos, p);
     }
   }
-  std::sort(hits.begin(), hits.end());
+  std::sort(hits.begin(), hits.end(), [](const Hit &a, const Hit &b) {
+    if (a.end != b.end) return a.end < b.end;
+    if (a.len != b.len) return a.len > b.len;
+    return a.p < b.p;
+  });
   for (uint64_t k = 0; k < hits.size() && k < cap; ++k) {
-    end_out[k] = (uint32_t)hits[k].first;
-    id_out[k] = (uint32_t)hits[k].second;
+    end_out[k] = (uint32_t)hits[k].end;
+    id_out[k] = (uint32_t)hits[k].p;
   }
   return hits.size();
 }

@@ -259,8 +259,9 @@ def test_match_bruteforce_random():
         pats.append(pats[0])  # duplicate pattern: reported under both ids
         toks = [t for p in pats for t in p]
         off = np.cumsum([0] + [len(p) for p in pats])
-        want = sorted((e, p) for p, pat in enumerate(pats) for e in range(len(pat) - 1, n)
+        want = sorted((e, -len(pat), p) for p, pat in enumerate(pats) for e in range(len(pat) - 1, n)
                       if text[e - len(pat) + 1:e + 1] == pat)
+        want = [(e, p) for e, _, p in want]
         for naive in (False, True):
             e, i = oracle.match(toks, off, text, naive)
             assert list(zip(e.tolist(), i.tolist())) == want
