@@ -164,23 +164,51 @@ int apo_find_repeats(apo_ctx *ctx, const apo_window *window, const apo_repeats_p
  *
  * Reports every (end, id) with stream[end - len(id) + 1 .. end] == pattern id,
  * for all patterns (overlapping occurrences included; a pattern listed twice
- * is reported under both ids), sorted by (end, id).
+ * is reported under both ids), ordered by end ascending, then pattern length
+ * descending, then id ascending.  At most 2^32 - 1 matches per call.
  * ---------------------------------------------------------------------- */
 typedef struct {
   uint64_t n_patterns;       /* P >= 1 */
-  const void *tokens;        /* device, pat_off[P] tokens */
+  const void *tokens;        /* device token array the patterns are taken from */
   int token_bytes;           /* 4 or 8, same width as the stream */
-  const uint64_t *pat_off;   /* HOST [P+1] CSR offsets; every pattern non-empty */
+  /* Either CSR form: pattern p = tokens[pat_off[p] .. pat_off[p+1]) with
+   * pat_off a HOST array of P+1 offsets (pat_start/pat_len NULL) ... */
+  const uint64_t *pat_off;
+  /* ... or slice form (pat_off NULL): pattern p = tokens[pat_start[p] ..
+   * pat_start[p] + pat_len[p]) with DEVICE arrays, e.g. the trace_start /
+   * trace_len outputs of apo_find_repeats over the same tokens. */
+  const uint32_t *pat_start;
+  const uint32_t *pat_len;
 } apo_patterns;
 
-/* Match `patterns` against stream[n] (device, same token width).  Writes up
- * to `cap` matches to match_end/match_id (device) and the total number of
- * matches to *count (HOST).  Synchronises `stream`.  APO_ECAPACITY if the
- * total exceeds cap (the first cap matches in order are written).
- * APO_EINVAL for an empty pattern, P = 0, or mismatched token widths. */
+/* Match `patterns` against stream[n] (device, same token width).  Writes the
+ * matches to match_end/match_id (device, `cap` entries each) and their total
+ * number to *count (HOST).  Synchronises `stream`.  APO_ECAPACITY if the total
+ * exceeds cap (*count is exact, the arrays' contents are then unspecified).
+ * APO_EINVAL for an empty pattern, P = 0, or token_bytes not 4 or 8. */
 int apo_match_candidates(apo_ctx *ctx, const apo_patterns *patterns, const void *stream_tokens,
                          uint64_t n, uint32_t *match_end, uint32_t *match_id, uint64_t cap,
                          uint64_t *count, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to report per-kernel
+ * device time against the hardware roofline).
+ *
+ * Every kernel launch of the library is counted per kernel.  With timing
+ * enabled, each launch is also bracketed by two CUDA events recorded on its
+ * launch stream, and the elapsed device time is accumulated when the entry
+ * is read.  `units` accumulates the elements each launch processed (keys for
+ * a radix-sort pass, suffixes for a refresh, tokens for a match), from which
+ * a caller derives algorithmic bytes.
+ * ---------------------------------------------------------------------- */
+int apo_profile_enable(apo_ctx *ctx, int enable_timing);
+int apo_profile_reset(apo_ctx *ctx);
+/* Entry `index` (0-based): its kernel name (NUL-terminated, truncated to
+ * name_cap), launches, accumulated milliseconds (0 without timing) and units.
+ * Synchronises the events still pending.  APO_EINVAL when index is past the
+ * last entry. */
+int apo_profile_read(apo_ctx *ctx, int index, char *name, size_t name_cap, uint64_t *launches,
+                     double *ms, uint64_t *units);
 
 #ifdef __cplusplus
 }

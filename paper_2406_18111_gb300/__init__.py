@@ -28,7 +28,8 @@ _NAMES = {0: "APO_OK", -1: "APO_EINVAL", -2: "APO_ENOMEM", -3: "APO_ECAPACITY", 
 
 # Every symbol include/apo.h declares.
 EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_hash_tasks",
-           "apo_find_repeats", "apo_match_candidates")
+           "apo_find_repeats", "apo_match_candidates", "apo_profile_enable", "apo_profile_reset",
+           "apo_profile_read")
 
 _P = ctypes.c_void_p
 _U64 = ctypes.c_uint64
@@ -63,7 +64,7 @@ class apo_repeats_out(ctypes.Structure):
 
 class apo_patterns(ctypes.Structure):
     _fields_ = [("n_patterns", _U64), ("tokens", _P), ("token_bytes", ctypes.c_int),
-                ("pat_off", _P)]
+                ("pat_off", _P), ("pat_start", _P), ("pat_len", _P)]
 
 
 _lib = None
@@ -88,6 +89,11 @@ def lib():
                                        ctypes.POINTER(apo_repeats_out), _P]
         L.apo_match_candidates.argtypes = [_P, ctypes.POINTER(apo_patterns), _P, _U64, _P, _P, _U64,
                                            ctypes.POINTER(_U64), _P]
+        L.apo_profile_enable.argtypes = [_P, ctypes.c_int]
+        L.apo_profile_reset.argtypes = [_P]
+        L.apo_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
+                                       ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(_U64)]
         for f in EXPORTS:
             if f not in ("apo_last_error",):
                 getattr(L, f).restype = ctypes.c_int
@@ -204,25 +210,54 @@ class Apo:
 
     # -------------------------------------------------------------- Sec. 4.3
     def match_candidates(self, pat_tokens, pat_off, stream_tokens, cap: int | None = None,
-                         stream=None):
-        """All (end, pattern id) occurrences, sorted; pat_off is a host array."""
+                         stream=None, pat_start=None, pat_len=None):
+        """All (end, pattern id) occurrences in stream_tokens, sorted.  Patterns
+        are either a host CSR (pat_off) over pat_tokens, or device slices
+        (pat_start, pat_len, with pat_off None) of pat_tokens."""
         import torch
-        po = np.ascontiguousarray(np.asarray(pat_off, dtype=np.uint64))
         n = int(stream_tokens.shape[0])
         if cap is None:
             cap = max(1, 4 * n)
         end = torch.empty(max(1, cap), dtype=torch.int32, device=stream_tokens.device)
         pid = torch.empty(max(1, cap), dtype=torch.int32, device=stream_tokens.device)
         cnt = _U64(0)
-        p = apo_patterns(po.shape[0] - 1, _ptr(pat_tokens), _token_bytes(pat_tokens),
-                         po.ctypes.data_as(_P).value)
+        if pat_off is not None:
+            po = np.ascontiguousarray(np.asarray(pat_off, dtype=np.uint64))
+            p = apo_patterns(po.shape[0] - 1, _ptr(pat_tokens), _token_bytes(pat_tokens),
+                             po.ctypes.data_as(_P).value, None, None)
+        else:
+            p = apo_patterns(int(pat_start.shape[0]), _ptr(pat_tokens), _token_bytes(pat_tokens),
+                             None, _ptr(pat_start), _ptr(pat_len))
         code = lib().apo_match_candidates(self._h, ctypes.byref(p), _ptr(stream_tokens), n, _ptr(end),
                                           _ptr(pid), cap, ctypes.byref(cnt), _stream_handle(stream))
         if code == APO_ECAPACITY:
-            return self.match_candidates(pat_tokens, pat_off, stream_tokens, int(cnt.value), stream)
+            return self.match_candidates(pat_tokens, pat_off, stream_tokens, int(cnt.value), stream,
+                                         pat_start, pat_len)
         _check(code)
         c = int(cnt.value)
         return end[:c], pid[:c]
+
+    # -------------------------------------------------------------- instrumentation
+    def profile(self, enable_timing: bool = True):
+        _check(lib().apo_profile_enable(self._h, int(enable_timing)))
+
+    def profile_reset(self):
+        _check(lib().apo_profile_reset(self._h))
+
+    def profile_read(self) -> dict:
+        """{kernel: (launches, ms, units)} for every kernel launched so far."""
+        out = {}
+        name = ctypes.create_string_buffer(64)
+        i = 0
+        while True:
+            la, un, ms = _U64(0), _U64(0), ctypes.c_double(0)
+            if lib().apo_profile_read(self._h, i, name, 64, ctypes.byref(la), ctypes.byref(ms),
+                                      ctypes.byref(un)) != APO_OK:
+                break
+            if la.value:
+                out[name.value.decode()] = (int(la.value), float(ms.value), int(un.value))
+            i += 1
+        return out
 
 
 def as_u32(t) -> np.ndarray:

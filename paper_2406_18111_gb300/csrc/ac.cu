@@ -15,8 +15,13 @@
 //
 // Match.  A node's state depends only on the last (max pattern length)
 // tokens, so the stream is cut into chunks and each thread runs the
-// automaton over its chunk after a halo of (max length - 1) tokens.
-// Matches are appended as (end << 32 | id) and radix-sorted at the end.
+// automaton over its chunk after a halo of (max length - 1) tokens, writing
+// the state of every position.  The number of matches a state reports
+// (its own pattern ends plus those down its output chain) is precomputed per
+// node during the level-by-level link pass, so the output offsets are one
+// prefix sum over positions; a final kernel per position then writes its
+// matches.  Output order: end ascending, then pattern length descending (the
+// output chain's order), then pattern id ascending.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -69,14 +74,15 @@ __device__ __forceinline__ uint32_t to_sym(const void *tok, int tb, uint64_t i, 
   return (lo < sigma && dict[lo] == t) ? lo : kNil;
 }
 
-__global__ void k_trie_insert(const void *pat_tok, int tb, const uint64_t *__restrict__ pat_off,
-                              uint32_t P, const uint64_t *dict, uint32_t sigma, Goto g,
+__global__ void k_trie_insert(const void *pat_tok, int tb, const uint32_t *__restrict__ pstart,
+                              const uint32_t *__restrict__ plen, uint32_t P, const uint64_t *dict,
+                              uint32_t sigma, Goto g,
                               uint32_t *node_ctr, uint32_t *parent, uint32_t *depth, uint32_t *nsym,
                               uint32_t *end_node, uint32_t *err) {
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   uint32_t u = 0;
-  const uint64_t off = pat_off[p], len = pat_off[p + 1] - off;
+  const uint64_t off = pstart[p], len = plen[p];
   for (uint64_t d = 0; d < len; ++d) {
     const uint32_t c = to_sym(pat_tok, tb, off + d, dict, sigma);
     const uint64_t key = ((uint64_t)u << 32) | c;
@@ -120,6 +126,24 @@ __global__ void k_trie_insert(const void *pat_tok, int tb, const uint64_t *__res
   end_node[p] = u;
 }
 
+// max length, max end and total length of slice-form patterns; flags empty ones
+__global__ void k_slices(const uint32_t *__restrict__ pstart, const uint32_t *__restrict__ plen,
+                         uint32_t P, uint32_t *maxlen, uint32_t *maxend,
+                         unsigned long long *total, uint32_t *err) {
+  uint32_t ml = 0, me = 0;
+  unsigned long long tot = 0;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint32_t l = plen[p];
+    if (l == 0) atomicExch(err, kDevRange);
+    ml = max(ml, l);
+    me = max(me, pstart[p] + l);
+    tot += l;
+  }
+  atomicMax(maxlen, ml);
+  atomicMax(maxend, me);
+  atomicAdd(total, tot);
+}
+
 __global__ void k_depth_keys(const uint32_t *__restrict__ depth, uint32_t N, uint64_t *keys,
                              uint32_t *vals, uint32_t *level_cnt) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
@@ -147,7 +171,8 @@ __global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint
 __global__ void k_fail_level(const uint32_t *__restrict__ order, uint32_t lo, uint32_t hi,
                              uint32_t d, Goto g, const uint32_t *__restrict__ parent,
                              const uint32_t *__restrict__ nsym, const uint32_t *__restrict__ end_first,
-                             uint32_t *fail, uint32_t *outl) {
+                             const uint32_t *__restrict__ own, uint32_t *fail, uint32_t *outl,
+                             uint32_t *total) {
   for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
     const uint32_t v = order[i];
     uint32_t f = 0;
@@ -165,16 +190,24 @@ __global__ void k_fail_level(const uint32_t *__restrict__ order, uint32_t lo, ui
       }
     }
     fail[v] = f;
-    outl[v] = (f != 0 && end_first[f] != kNil) ? f : outl[f];
+    const uint32_t o = (f != 0 && end_first[f] != kNil) ? f : outl[f];
+    outl[v] = o;
+    total[v] = own[v] + total[o];  // matches reported when the automaton is in v
   }
 }
 
-__global__ void k_ac_match(const void *stream, int tb, uint64_t n, uint64_t chunk, uint64_t halo,
-                           const uint64_t *dict, uint32_t sigma, Goto g,
-                           const uint32_t *__restrict__ fail, const uint32_t *__restrict__ outl,
-                           const uint32_t *__restrict__ end_first, const uint64_t *__restrict__ ekeys,
-                           const uint32_t *__restrict__ evals, uint32_t P, uint64_t *buf,
-                           uint64_t cap, unsigned long long *count) {
+// own[v] = number of patterns ending exactly at node v.
+__global__ void k_own_counts(const uint64_t *__restrict__ skeys, uint32_t P, uint32_t *own) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x)
+    atomicAdd(&own[(uint32_t)skeys[k]], 1u);
+}
+
+// Pass A: automaton state after every stream position.  Thread t owns
+// positions [t*chunk, (t+1)*chunk) and starts from the root `halo` tokens
+// earlier (a state only depends on the last max-length tokens).
+__global__ void k_ac_states(const void *stream, int tb, uint64_t n, uint64_t chunk, uint64_t halo,
+                            const uint64_t *dict, uint32_t sigma, Goto g,
+                            const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
@@ -184,7 +217,7 @@ __global__ void k_ac_match(const void *stream, int tb, uint64_t n, uint64_t chun
   for (; x < ce; ++x) {
     const uint32_t c = to_sym(stream, tb, x, dict, sigma);
     while (true) {
-      const uint32_t nx = c == kNil && tb == 8 ? kNil : goto_lookup(g, state, c);
+      const uint32_t nx = (c == kNil && tb == 8) ? kNil : goto_lookup(g, state, c);
       if (nx != kNil) {
         state = nx;
         break;
@@ -192,24 +225,75 @@ __global__ void k_ac_match(const void *stream, int tb, uint64_t n, uint64_t chun
       if (state == 0) break;
       state = fail[state];
     }
-    if (x < cs) continue;
-    uint32_t v = end_first[state] != kNil ? state : outl[state];
-    while (v != 0) {
-      for (uint32_t k = end_first[v]; k < P && (uint32_t)ekeys[k] == v; ++k) {
-        const unsigned long long slot = atomicAdd(count, 1ull);
-        if (slot < cap) buf[slot] = (x << 32) | evals[k];
-      }
-      v = outl[v];
-    }
+    if (x >= cs) state_out[x] = state;
   }
 }
 
-__global__ void k_split_matches(const uint64_t *__restrict__ keys, uint64_t m, uint32_t *end,
-                                uint32_t *id) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    end[q] = (uint32_t)(keys[q] >> 32);
-    id[q] = (uint32_t)keys[q];
+// Exclusive prefix sum of total[state[x]] over stream positions (the first
+// output slot of each position), decoupled look-back.
+constexpr int kST = 256, kSI = 16, kSTile = kST * kSI;
+__global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restrict__ state,
+                                                       const uint32_t *__restrict__ total, uint32_t n,
+                                                       uint32_t *__restrict__ off, uint32_t *sum_out,
+                                                       uint64_t *status, uint32_t *tile_ctr,
+                                                       uint32_t epoch, uint32_t *err) {
+  __shared__ uint32_t s_tile, s_pre;
+  __shared__ uint32_t scr[kST / 32];
+  __shared__ uint32_t sv[kSTile];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kSTile;
+  for (int q = tid; q < kSTile; q += kST)
+    sv[q] = base + q < n ? total[state[base + q]] : 0u;
+  __syncthreads();
+  uint32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < kSI; ++i) run += sv[tid * kSI + i];
+  uint32_t tot;
+  const uint32_t ex = block_exclusive<kST / 32>(run, OpSum(), 0u, scr, &tot);
+  if (tid == 0) {
+    lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
+    uint32_t pre = 0;
+    if (t > 0) {
+      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
+    }
+    s_pre = pre;
+    if (base + kSTile >= n) *sum_out = pre + tot;
+  }
+  __syncthreads();
+  uint32_t r = s_pre + ex;
+#pragma unroll
+  for (int i = 0; i < kSI; ++i) {
+    const uint64_t x = base + (uint64_t)tid * kSI + i;
+    if (x < n) off[x] = r;
+    r += sv[tid * kSI + i];
+  }
+}
+
+// Pass B: the matches of position x, following the output chain from its
+// state (deepest first), ids ascending within a node.
+__global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
+                          const uint32_t *__restrict__ off, const uint32_t *__restrict__ outl,
+                          const uint32_t *__restrict__ end_first, const uint64_t *__restrict__ ekeys,
+                          const uint32_t *__restrict__ evals, uint32_t P, uint32_t *mend,
+                          uint32_t *mid, uint64_t cap) {
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    const uint32_t s0 = state[x];
+    uint64_t o = off[x];
+    uint32_t v = end_first[s0] != kNil ? s0 : outl[s0];
+    while (v != 0) {
+      for (uint32_t k = end_first[v]; k < P && (uint32_t)ekeys[k] == v; ++k) {
+        if (o < cap) {
+          mend[o] = x;
+          mid[o] = evals[k];
+        }
+        ++o;
+      }
+      v = outl[v];
+    }
   }
 }
 
@@ -240,8 +324,10 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   uint64_t tbl = 1;
   while (tbl < 2 * (total_tokens + 1)) tbl <<= 1;
   const uint64_t N = total_tokens + 1;
-  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, total_tokens), std::max<uint64_t>(P, cap));
-  return tbl * 12 + N * 4 * 7 + P * 24 + (P + 1) * 8 + total_tokens * 12 + M * 24 + 64 * 256;
+  (void)cap;
+  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, total_tokens), P);
+  return tbl * 12 + N * 4 * 9 + P * 24 + (P + 1) * 8 + total_tokens * 12 + M * 24 + n * 8 +
+         64 * 256;
 }
 
 int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint64_t n,
@@ -249,18 +335,50 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
                    cudaStream_t s) {
   const uint32_t P = (uint32_t)pp->n_patterns;
   const int tb = pp->token_bytes;
-  const uint64_t total = pp->pat_off[P];
-  uint64_t maxlen = 0;
-  for (uint32_t p = 0; p < P; ++p) maxlen = std::max(maxlen, pp->pat_off[p + 1] - pp->pat_off[p]);
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  unsigned long long *cnt64 = reinterpret_cast<unsigned long long *>(misc + kMiscKeyOr);
+  const int sms = c->num_sms;
+  // pattern p = tokens[pstart[p] .. pstart[p] + plen[p])
+  const uint32_t *pstart = pp->pat_start, *plen = pp->pat_len;
+  uint64_t total = 0, maxlen = 0, extent = 0;
+  uint32_t *hostbuf = nullptr;
+  if (pp->pat_off) {
+    for (uint32_t p = 0; p < P; ++p) maxlen = std::max(maxlen, pp->pat_off[p + 1] - pp->pat_off[p]);
+    total = pp->pat_off[P];
+    extent = total;
+  } else {
+    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMaxLen, 0, 2 * sizeof(uint32_t), s));
+    APO_CUDA_TRY(cudaMemsetAsync(cnt64, 0, 8, s));
+    {
+      Launch lp_(c, kKSlices, P, s);
+      k_slices<<<grid_for(P, 256, sms), 256, 0, s>>>(pstart, plen, P, misc + kMiscMaxLen,
+                                                      misc + kMiscMaxLen + 1, cnt64, c->ps.err);
+    }
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMaxLen, 8, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, cnt64, 8, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (check_device_error(c, s) != APO_OK) {
+      set_error("match_candidates: empty pattern");
+      return APO_EINVAL;
+    }
+    maxlen = c->host_pinned[0];
+    extent = c->host_pinned[1];
+    memcpy(&total, c->host_pinned + 2, 8);
+  }
+  (void)hostbuf;
+  if (total >= 0xffffffffull || extent >= 0xffffffffull) {
+    set_error("match_candidates: more than 2^32 - 1 pattern tokens");
+    return APO_EINVAL;
+  }
+  APO_TRY(c->arena.reserve(match_workspace_bytes(std::max(total, extent), P, n, cap)));
   const uint64_t N = total + 1;  // node bound (root included)
   uint64_t tbl = 1;
   while (tbl < 2 * N) tbl <<= 1;
-
   Goto g;
   g.keys = c->arena.take_n<uint64_t>(tbl);
   g.vals = c->arena.take_n<uint32_t>(tbl);
   g.mask = tbl - 1;
-  uint64_t *poff = c->arena.take_n<uint64_t>(P + 1);
+  uint32_t *pbuf = pp->pat_off ? c->arena.take_n<uint32_t>(2 * (size_t)P) : nullptr;
   uint32_t *parent = c->arena.take_n<uint32_t>(N);
   uint32_t *depth = c->arena.take_n<uint32_t>(N);
   uint32_t *nsym = c->arena.take_n<uint32_t>(N);
@@ -268,15 +386,17 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *outl = c->arena.take_n<uint32_t>(N);
   uint32_t *end_first = c->arena.take_n<uint32_t>(N);
   uint32_t *end_node = c->arena.take_n<uint32_t>(P);
+  uint32_t *own = c->arena.take_n<uint32_t>(N);
+  uint32_t *mtotal = c->arena.take_n<uint32_t>(N);
   uint32_t *levels = c->arena.take_n<uint32_t>(maxlen + 2);
-  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, total), std::max<uint64_t>(P, cap));
+  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, extent), P);
   SortBuffers b;
   b.keys[0] = c->arena.take_n<uint64_t>(M);
   b.keys[1] = c->arena.take_n<uint64_t>(M);
   b.vals[0] = c->arena.take_n<uint32_t>(M);
   b.vals[1] = c->arena.take_n<uint32_t>(M);
-  uint64_t *dict = c->arena.take_n<uint64_t>(std::max<uint64_t>(total, 1));
-  if (!g.keys || !g.vals || !poff || !parent || !depth || !nsym || !fail || !outl || !end_first ||
+  uint64_t *dict = c->arena.take_n<uint64_t>(std::max<uint64_t>(extent, 1));
+  if (!g.keys || !g.vals || (pp->pat_off && !pbuf) || !parent || !depth || !nsym || !fail || !outl || !end_first || !own || !mtotal ||
       !end_node || !levels || !b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !dict) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
@@ -285,34 +405,50 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     set_error("match: more than 2^32 - 1 nodes, stream tokens or matches");
     return APO_EINVAL;
   }
-  APO_CUDA_TRY(cudaMemcpyAsync(poff, pp->pat_off, (P + 1) * sizeof(uint64_t),
-                               cudaMemcpyHostToDevice, s));
+  if (pp->pat_off) {  // CSR on the host -> (start, len) on the device
+    std::vector<uint32_t> h(2 * (size_t)P);
+    for (uint32_t p = 0; p < P; ++p) {
+      h[p] = (uint32_t)pp->pat_off[p];
+      h[P + p] = (uint32_t)(pp->pat_off[p + 1] - pp->pat_off[p]);
+    }
+    APO_CUDA_TRY(cudaMemcpyAsync(pbuf, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    pstart = pbuf;
+    plen = pbuf + P;
+  }
   APO_CUDA_TRY(cudaMemsetAsync(g.keys, 0xff, tbl * sizeof(uint64_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(g.vals, 0, tbl * sizeof(uint32_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(end_first, 0xff, N * sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(own, 0, N * sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(mtotal, 0, N * sizeof(uint32_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(levels, 0, (maxlen + 2) * sizeof(uint32_t), s));
-  uint32_t *misc = c->ps.counters + kCtrMisc;
-  unsigned long long *cnt64 = reinterpret_cast<unsigned long long *>(misc + kMiscKeyOr);
-  const int sms = c->num_sms;
-
   // u64 tokens: dictionary of distinct pattern tokens
   uint32_t sigma = 0;
   if (tb == 8) {
-    k_u64_keys<<<grid_for(total, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens),
-                                                         total, b.keys[0], b.vals[0]);
+    {
+      Launch lp_(c, kKU64Keys, 0, s);
+      k_u64_keys<<<grid_for(extent, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens),
+                                                            extent, b.keys[0], b.vals[0]);
+    }
     b.cur = 0;
     int places[8];
     const int np = plan_digits(0, 64, places, 0);
-    APO_TRY(radix_sort_pairs(c, b, (uint32_t)total, places, np, s));
+    APO_TRY(radix_sort_pairs(c, b, (uint32_t)extent, places, np, s));
     APO_CUDA_TRY(cudaMemsetAsync(cnt64, 0, 8, s));
-    k_unique_u64<<<grid_for(total, 256, sms), 256, 0, s>>>(b.keys[b.cur], total, dict, cnt64);
+    {
+      Launch lp_(c, kKUnique, extent, s);
+      k_unique_u64<<<grid_for(extent, 256, sms), 256, 0, s>>>(b.keys[b.cur], extent, dict, cnt64);
+    }
     unsigned long long sg = 0;
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, cnt64, 8, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaStreamSynchronize(s));
     memcpy(&sg, c->host_pinned, 8);
     sigma = (uint32_t)sg;
     // distinct values were appended in arbitrary order: sort them
-    k_u64_keys<<<grid_for(sigma, 256, sms), 256, 0, s>>>(dict, sigma, b.keys[0], b.vals[0]);
+    {
+      Launch lp_(c, kKU64Keys, 0, s);
+      k_u64_keys<<<grid_for(sigma, 256, sms), 256, 0, s>>>(dict, sigma, b.keys[0], b.vals[0]);
+    }
     b.cur = 0;
     APO_TRY(radix_sort_pairs(c, b, sigma, places, np, s));
     APO_CUDA_TRY(cudaMemcpyAsync(dict, b.keys[b.cur], sigma * sizeof(uint64_t),
@@ -321,9 +457,12 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
 
   // trie
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMatchCount, 0, sizeof(uint32_t), s));
-  k_trie_insert<<<ceil_div(P, 128), 128, 0, s>>>(pp->tokens, tb, poff, P, dict, sigma, g,
-                                                 misc + kMiscMatchCount, parent, depth, nsym,
-                                                 end_node, c->ps.err);
+  {
+    Launch lp_(c, kKTrieInsert, total, s);
+    k_trie_insert<<<ceil_div(P, 128), 128, 0, s>>>(pp->tokens, tb, pstart, plen, P, dict, sigma, g,
+                                                   misc + kMiscMatchCount, parent, depth, nsym,
+                                                   end_node, c->ps.err);
+  }
   APO_CUDA_TRY(cudaGetLastError());
   uint32_t nodes = 0;
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMatchCount, 4, cudaMemcpyDeviceToHost, s));
@@ -334,7 +473,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   // pattern ends: (end node, pattern id) sorted by node
   uint64_t *ek;
   uint32_t *ev;
-  k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, b.keys[0], b.vals[0]);
+  {
+    Launch lp_(c, kKEndPairs, P, s);
+    k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, b.keys[0], b.vals[0]);
+  }
   b.cur = 0;
   {
     int places[8];
@@ -347,10 +489,20 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   if (!ek || !ev) return APO_ENOMEM;
   APO_CUDA_TRY(cudaMemcpyAsync(ek, b.keys[b.cur], P * 8, cudaMemcpyDeviceToDevice, s));
   APO_CUDA_TRY(cudaMemcpyAsync(ev, b.vals[b.cur], P * 4, cudaMemcpyDeviceToDevice, s));
-  k_mark_ends<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, end_first);
+  {
+    Launch lp_(c, kKMarkEnds, P, s);
+    k_mark_ends<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, end_first);
+  }
+  {
+    Launch lp_(c, kKOwn, P, s);
+    k_own_counts<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, own);
+  }
 
   // BFS order by depth
-  k_depth_keys<<<grid_for(nodes, 256, sms), 256, 0, s>>>(depth, nodes, b.keys[0], b.vals[0], levels);
+  {
+    Launch lp_(c, kKDepthKeys, nodes, s);
+    k_depth_keys<<<grid_for(nodes, 256, sms), 256, 0, s>>>(depth, nodes, b.keys[0], b.vals[0], levels);
+  }
   b.cur = 0;
   {
     int places[8];
@@ -366,47 +518,55 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t lo = lc[0];
   for (uint64_t d = 1; d <= maxlen; ++d) {
     const uint32_t hi = lo + lc[d];
-    if (hi > lo)
+    if (hi > lo) {
+      Launch lp_(c, kKFailLevel, hi - lo, s);
       k_fail_level<<<grid_for(hi - lo, 128, sms), 128, 0, s>>>(order, lo, hi, (uint32_t)d, g, parent,
-                                                              nsym, end_first, fail, outl);
+                                                              nsym, end_first, own, fail, outl,
+                                                              mtotal);
+    }
     lo = hi;
   }
   APO_CUDA_TRY(cudaGetLastError());
+  if (n == 0) return APO_OK;
 
-  // match
-  uint64_t *buf = b.keys[b.cur ^ 1];  // free sort buffer, M >= cap entries
+  // pass A: states
+  uint32_t *state = c->arena.take_n<uint32_t>(n);
+  uint32_t *off = c->arena.take_n<uint32_t>(n);
+  if (!state || !off) return APO_ENOMEM;
   const uint64_t halo = maxlen ? maxlen - 1 : 0;
-  const uint64_t chunk = std::max<uint64_t>(1024, 2 * halo);
+  const uint64_t chunk = std::max<uint64_t>(64, n / ((uint64_t)sms * 32));
   const uint64_t threads = (n + chunk - 1) / chunk;
-  APO_CUDA_TRY(cudaMemsetAsync(cnt64, 0, 8, s));
-  if (n)
-    k_ac_match<<<ceil_div(threads, 128), 128, 0, s>>>(stream, tb, n, chunk, halo, dict, sigma, g, fail,
-                                                      outl, end_first, ek, ev, P, buf, cap, cnt64);
+  {
+    Launch lp_(c, kKAcMatch, n, s);
+    k_ac_states<<<ceil_div(threads, 128), 128, 0, s>>>(stream, tb, n, chunk, halo, dict, sigma, g,
+                                                       fail, state);
+  }
+  // output offsets and total
+  const int tiles = ceil_div(n, kSTile);
+  APO_TRY(ensure_lookback(c, tiles));
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCompactTiles, 0, 2 * sizeof(uint32_t), s));
+  {
+    Launch lp_(c, kKMatchOffsets, n, s);
+    k_match_offsets<<<tiles, kST, 0, s>>>(state, mtotal, (uint32_t)n, off, misc + kMiscCompactCount,
+                                          c->ps.lookback, misc + kMiscCompactTiles, next_epoch(c),
+                                          c->ps.err);
+  }
   APO_CUDA_TRY(cudaGetLastError());
-  unsigned long long total_m = 0;
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, cnt64, 8, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscCompactCount, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   APO_TRY(check_device_error(c, s));
-  memcpy(&total_m, c->host_pinned, 8);
+  const uint64_t total_m = c->host_pinned[0];
   *count = total_m;
   if (total_m > cap) {
     set_error("match_candidates: more matches than cap (count written)");
     return APO_ECAPACITY;
   }
   if (total_m) {
-    SortBuffers mb;
-    mb.keys[0] = buf;
-    mb.keys[1] = b.keys[b.cur];
-    mb.vals[0] = b.vals[b.cur ^ 1];
-    mb.vals[1] = b.vals[b.cur];
-    mb.cur = 0;
-    int places[12];
-    int np = plan_digits(0, bits_for(P - 1), places, 0);
-    np = plan_digits(32, 32 + bits_for(n - 1), places, np);
-    APO_TRY(radix_sort_pairs(c, mb, (uint32_t)total_m, places, np, s));
-    k_split_matches<<<grid_for(total_m, 256, sms), 256, 0, s>>>(mb.keys[mb.cur], total_m, match_end,
-                                                               match_id);
+    Launch lp_(c, kKAcFill, n, s);
+    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, outl, end_first, ek, ev, P,
+                                                    match_end, match_id, cap);
   }
+  APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   return check_device_error(c, s);
 }

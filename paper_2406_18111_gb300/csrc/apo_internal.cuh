@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/apo.h"
 
@@ -77,6 +78,31 @@ struct Persistent {
   uint32_t epoch = 0;             // look-back epoch, bumped per launch
 };
 
+// ---------------------------------------------------------------- instrumentation
+enum KernelId : int {
+  kKHash, kKInitKeys, kKKeyOr, kKRsHist, kKRsOffsets, kKRsPass, kKRefresh, kKPack, kKPhi,
+  kKPlcp, kKLcpPerm, kKMin32, kKMax, kKCandGen, kKCompact, kKCandGather, kKGreedy, kKTraces,
+  kKSelOut, kKTrieInsert, kKDepthKeys, kKEndPairs, kKMarkEnds, kKFailLevel, kKAcMatch,
+  kKAcFill, kKU64Keys, kKUnique, kKSlices, kKMatchOffsets, kKOwn, kKCount
+};
+extern const char *const kKernelNames[kKCount];
+
+struct Profiler {
+  bool timing = false;
+  uint64_t launches[kKCount] = {};
+  uint64_t units[kKCount] = {};
+  double ms[kKCount] = {};
+  struct Pending {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  int resolve();
+  void release();
+};
+
 }  // namespace apo
 
 struct apo_ctx {
@@ -84,8 +110,29 @@ struct apo_ctx {
   int num_sms = 0;
   apo::Arena arena;
   apo::Persistent ps;
+  apo::Profiler prof;
   uint32_t *host_pinned = nullptr;  // small pinned staging buffer (counts)
 };
+
+namespace apo {
+
+// Counts one kernel launch and, with timing enabled, brackets it with CUDA
+// events on the launch stream.  Construct it right before the launch.
+class Launch {
+ public:
+  Launch(apo_ctx *c, int id, uint64_t units, cudaStream_t s);
+  ~Launch();
+  Launch(const Launch &) = delete;
+  Launch &operator=(const Launch &) = delete;
+
+ private:
+  apo_ctx *c_;
+  int id_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+}  // namespace apo
 
 namespace apo {
 
@@ -120,7 +167,7 @@ struct SortBuffers {
 int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *shifts, int npass,
                      cudaStream_t s);
 // OR of all keys (to learn how many digits are populated); result in *out_dev.
-void launch_key_or(const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
+void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
 
 // Plan the 8-bit digit shifts covering bits [lo, hi) of a key.
 int plan_digits(int lo, int hi, int *shifts, int start);
@@ -145,7 +192,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int token_bytes, const 
                          cudaStream_t s);
 
 // ---------------------------------------------------------------- hashing
-void launch_hash_tasks(const apo_tasks *t, uint64_t *out, cudaStream_t s, int sms);
+void launch_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- matching
 int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,

@@ -61,6 +61,59 @@ int ensure_lookback(apo_ctx *c, size_t words) {
   return APO_OK;
 }
 
+const char *const kKernelNames[kKCount] = {
+    "hash_tasks", "init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
+    "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
+    "traces", "sel_out", "trie_insert", "depth_keys", "end_pairs", "mark_ends", "fail_level",
+    "ac_states", "ac_fill", "u64_keys", "unique", "slices", "match_offsets", "own_counts"};
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int Profiler::resolve() {
+  for (auto &p : pending) {
+    float t = 0.f;
+    cudaEventSynchronize(p.b);
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.id] += t;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+  return APO_OK;
+}
+
+void Profiler::release() {
+  resolve();
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+
+Launch::Launch(apo_ctx *c, int id, uint64_t units, cudaStream_t s) : c_(c), id_(id), s_(s) {
+  c->prof.launches[id] += 1;
+  c->prof.units[id] += units;
+  if (c->prof.timing) {
+    if (c->prof.pending.size() > 8192) c->prof.resolve();
+    a_ = c->prof.get();
+    b_ = c->prof.get();
+    cudaEventRecord(a_, s);
+  }
+}
+
+Launch::~Launch() {
+  if (a_) {
+    cudaEventRecord(b_, s_);
+    c_->prof.pending.push_back({id_, a_, b_});
+  }
+}
+
 int check_device_error(apo_ctx *c, cudaStream_t s) {
   (void)s;
   uint32_t e = 0;
@@ -131,6 +184,7 @@ int apo_destroy(apo_ctx *c) {
   if (c->ps.lookback) cudaFree(c->ps.lookback);
   if (c->ps.counters) cudaFree(c->ps.counters);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  c->prof.release();
   delete c;
   return APO_OK;
 }
@@ -145,7 +199,7 @@ int apo_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *tokens_out, void *s
     set_error("apo_hash_tasks: null task_id, arg_off or output");
     return APO_EINVAL;
   }
-  launch_hash_tasks(t, tokens_out, static_cast<cudaStream_t>(stream), c->num_sms);
+  launch_hash_tasks(c, t, tokens_out, static_cast<cudaStream_t>(stream));
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
 }
@@ -209,7 +263,7 @@ int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *
 int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
                          uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
                          void *stream) {
-  if (!c || !p || !count || !p->pat_off) {
+  if (!c || !p || !count) {
     set_error("apo_match_candidates: null argument");
     return APO_EINVAL;
   }
@@ -222,25 +276,69 @@ int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_t
     set_error("apo_match_candidates: too many patterns or stream tokens");
     return APO_EINVAL;
   }
-  for (uint64_t q = 0; q < p->n_patterns; ++q) {
-    if (p->pat_off[q + 1] <= p->pat_off[q]) {
-      set_error("apo_match_candidates: empty pattern or decreasing offsets");
+  if (p->pat_off) {
+    if (p->pat_off[0] != 0) {
+      set_error("apo_match_candidates: pat_off[0] must be 0");
       return APO_EINVAL;
     }
+    for (uint64_t q = 0; q < p->n_patterns; ++q) {
+      if (p->pat_off[q + 1] <= p->pat_off[q]) {
+        set_error("apo_match_candidates: empty pattern or decreasing offsets");
+        return APO_EINVAL;
+      }
+    }
+  } else if (!p->pat_start || !p->pat_len) {
+    set_error("apo_match_candidates: give pat_off (host CSR) or pat_start and pat_len (device)");
+    return APO_EINVAL;
   }
   if (!p->tokens || (n > 0 && !stream_tokens) || (cap > 0 && (!match_end || !match_id))) {
     set_error("apo_match_candidates: null tokens or outputs");
     return APO_EINVAL;
   }
-  if (p->pat_off[0] != 0) {
-    set_error("apo_match_candidates: pat_off[0] must be 0");
-    return APO_EINVAL;
-  }
   APO_CUDA_TRY(cudaSetDevice(c->device));
-  const uint64_t total = p->pat_off[p->n_patterns];
-  APO_TRY(c->arena.reserve(match_workspace_bytes(total, p->n_patterns, n, cap)));
   return match_patterns(c, p, stream_tokens, n, match_end, match_id, cap, count,
                         static_cast<cudaStream_t>(stream));
+}
+
+int apo_profile_enable(apo_ctx *c, int enable) {
+  if (!c) {
+    set_error("apo_profile_enable: null context");
+    return APO_EINVAL;
+  }
+  c->prof.resolve();
+  c->prof.timing = enable != 0;
+  return APO_OK;
+}
+
+int apo_profile_reset(apo_ctx *c) {
+  if (!c) {
+    set_error("apo_profile_reset: null context");
+    return APO_EINVAL;
+  }
+  c->prof.resolve();
+  for (int k = 0; k < kKCount; ++k) {
+    c->prof.launches[k] = 0;
+    c->prof.units[k] = 0;
+    c->prof.ms[k] = 0;
+  }
+  return APO_OK;
+}
+
+int apo_profile_read(apo_ctx *c, int index, char *name, size_t name_cap, uint64_t *launches,
+                     double *ms, uint64_t *units) {
+  if (!c || index < 0 || index >= kKCount) {
+    set_error("apo_profile_read: null context or index out of range");
+    return APO_EINVAL;
+  }
+  c->prof.resolve();
+  if (name && name_cap) {
+    strncpy(name, kKernelNames[index], name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (launches) *launches = c->prof.launches[index];
+  if (ms) *ms = c->prof.ms[index];
+  if (units) *units = c->prof.units[index];
+  return APO_OK;
 }
 
 }  // extern "C"

@@ -50,11 +50,15 @@ __global__ void __launch_bounds__(256) k_hash_tasks(uint64_t N, const uint32_t *
 
 }  // namespace
 
-void launch_hash_tasks(const apo_tasks *t, uint64_t *out, cudaStream_t s, int sms) {
+void launch_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *out, cudaStream_t s) {
+  const int sms = c->num_sms;
   const uint64_t N = t->n_tasks;
   const long long blocks = std::min<long long>((long long)((N + 255) / 256), (long long)sms * 8);
-  k_hash_tasks<<<(int)std::max<long long>(1, blocks), 256, 0, s>>>(
-      N, t->task_id, t->arg_off, t->region, t->field_mask, t->priv, out);
+  {
+    Launch lp_(c, kKHash, N, s);
+    k_hash_tasks<<<(int)std::max<long long>(1, blocks), 256, 0, s>>>(
+        N, t->task_id, t->arg_off, t->region, t->field_mask, t->priv, out);
+  }
 }
 
 }  // namespace apo

@@ -190,9 +190,12 @@ int plan_digits(int lo, int hi, int *places, int start) {
   return n;
 }
 
-void launch_key_or(const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s) {
+void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s) {
   int blocks = n ? std::min(1024, ceil_div(n, 256 * 8)) : 1;
-  k_key_or<<<blocks, 256, 0, s>>>(keys, n, reinterpret_cast<unsigned long long *>(out_dev));
+  {
+    Launch lp_(c, kKKeyOr, n, s);
+    k_key_or<<<blocks, 256, 0, s>>>(keys, n, reinterpret_cast<unsigned long long *>(out_dev));
+  }
 }
 
 int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *places, int npass,
@@ -211,14 +214,23 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *places, 
   uint32_t *tctr = c->ps.counters + kCtrSortTiles;  // [kMaxPass]
   APO_CUDA_TRY(cudaMemsetAsync(hist, 0, (kMaxPass * kRadix + kMaxPass) * sizeof(uint32_t), s));
   const int hblocks = std::min(c->num_sms * 4, ceil_div(n, kThreads * 8));
-  k_rs_hist<<<hblocks, kThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, pl, hist);
-  k_rs_offsets<<<npass, kThreads, 0, s>>>(hist);
+  {
+    Launch lp_(c, kKRsHist, n, s);
+    k_rs_hist<<<hblocks, kThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, pl, hist);
+  }
+  {
+    Launch lp_(c, kKRsOffsets, npass, s);
+    k_rs_offsets<<<npass, kThreads, 0, s>>>(hist);
+  }
   for (int p = 0; p < npass; ++p) {
     const uint32_t ep = next_epoch(c);
-    k_rs_pass<<<tiles, kThreads, kPassSmem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
-                                                 b.vals[b.cur ^ 1], n, places[p],
-                                                 hist + p * kRadix, c->ps.lookback, tctr + p, ep,
-                                                 c->ps.err);
+    {
+      Launch lp_(c, kKRsPass, n, s);
+      k_rs_pass<<<tiles, kThreads, kPassSmem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
+                                                   b.vals[b.cur ^ 1], n, places[p],
+                                                   hist + p * kRadix, c->ps.lookback, tctr + p, ep,
+                                                   c->ps.err);
+    }
     b.cur ^= 1;
   }
   APO_CUDA_TRY(cudaGetLastError());

@@ -388,8 +388,11 @@ int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_de
   uint32_t *tctr = c->ps.counters + kCtrMisc + kMiscCompactTiles;
   APO_CUDA_TRY(cudaMemsetAsync(tctr, 0, sizeof(uint32_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
-  k_compact<<<tiles, kCT, 0, s>>>(pred, m, out, count_dev, c->ps.lookback, tctr, next_epoch(c),
-                                  c->ps.err);
+  {
+    Launch lp_(c, kKCompact, m, s);
+    k_compact<<<tiles, kCT, 0, s>>>(pred, m, out, count_dev, c->ps.lookback, tctr, next_epoch(c),
+                                    c->ps.err);
+  }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
 }
@@ -435,7 +438,10 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
 
   // bits of the (length, id) key
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMaxLen, 0, sizeof(uint32_t), s));
-  k_max_u32<<<g, 256, 0, s>>>(lcp, n, misc + kMiscMaxLen);
+  {
+    Launch lp_(c, kKMax, n, s);
+    k_max_u32<<<g, 256, 0, s>>>(lcp, n, misc + kMiscMaxLen);
+  }
   uint32_t maxlcp = 0;
   APO_TRY(read_u32(c, misc + kMiscMaxLen, &maxlcp, s));
   const int bl = std::max(1, bits_for(maxlcp));
@@ -456,8 +462,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     const uint32_t nin = T.cnt[T.nlev - 1], nout = (nin + 31) / 32;
     uint32_t *o = c->arena.take_n<uint32_t>(nout);
     if (!o) return APO_ENOMEM;
-    k_min32<<<grid_for((uint64_t)nout * 32, 256, c->num_sms), 256, 0, s>>>(T.lv[T.nlev - 1], nin, o,
-                                                                           nout);
+    {
+      Launch lp_(c, kKMin32, nin, s);
+      k_min32<<<grid_for((uint64_t)nout * 32, 256, c->num_sms), 256, 0, s>>>(T.lv[T.nlev - 1], nin, o,
+                                                                             nout);
+    }
     T.lv[T.nlev] = o;
     T.cnt[T.nlev] = nout;
     ++T.nlev;
@@ -482,8 +491,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     return APO_ENOMEM;
   }
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCandCount, 0, sizeof(uint32_t), s));
-  k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, lmax, b.keys[0], b.vals[0],
-                               misc + kMiscCandCount, c->ps.err);
+  {
+    Launch lp_(c, kKCandGen, n, s);
+    k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, lmax, b.keys[0], b.vals[0],
+                                 misc + kMiscCandCount, c->ps.err);
+  }
   APO_CUDA_TRY(cudaGetLastError());
   uint32_t mraw = 0;
   APO_TRY(read_u32(c, misc + kMiscCandCount, &mraw, s));
@@ -498,8 +510,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
     APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCompactCount, s));
     APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
-    k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur],
-                                                               b.vals[b.cur], bi, lmax, cl, cid, cs);
+    {
+      Launch lp_(c, kKCandGather, m, s);
+      k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur],
+                                                                 b.vals[b.cur], bi, lmax, cl, cid, cs);
+    }
   }
 
   // greedy selection
@@ -508,11 +523,17 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     if ((long long)bm_bytes <= g_greedy_smem_max) {
-      k_greedy<true><<<1, kGT, bm_bytes, s>>>(cl, cs, m, n, nullptr, acc, misc + kMiscAccCount,
-                                              c->ps.err);
+      {
+        Launch lp_(c, kKGreedy, m, s);
+        k_greedy<true><<<1, kGT, bm_bytes, s>>>(cl, cs, m, n, nullptr, acc, misc + kMiscAccCount,
+                                                c->ps.err);
+      }
     } else {
       APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, bm_bytes, s));
-      k_greedy<false><<<1, kGT, 0, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount, c->ps.err);
+      {
+        Launch lp_(c, kKGreedy, m, s);
+        k_greedy<false><<<1, kGT, 0, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount, c->ps.err);
+      }
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
@@ -535,13 +556,19 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     sb.vals[0] = b.vals[0];
     sb.vals[1] = b.vals[1];
     sb.cur = 0;
-    k_traces<<<1, 1024, 0, s>>>(sel, K, cl, cid, cs, tl, ts, sb.keys[0], sb.vals[0],
-                                misc + kMiscTraceCount);
+    {
+      Launch lp_(c, kKTraces, K, s);
+      k_traces<<<1, 1024, 0, s>>>(sel, K, cl, cid, cs, tl, ts, sb.keys[0], sb.vals[0],
+                                  misc + kMiscTraceCount);
+    }
     int places[8];
     const int np = plan_digits(32, 32 + bits_for(n - 1), places, 0);
     APO_TRY(radix_sort_pairs(c, sb, K, places, np, s));
-    k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K,
-                                                           ss, sl, sq);
+    {
+      Launch lp_(c, kKSelOut, K, s);
+      k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K,
+                                                             ss, sl, sq);
+    }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscTraceCount, &Tn, s));
   }

@@ -226,10 +226,13 @@ int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, c
   uint32_t *misc = c->ps.counters + kCtrMisc;
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRefreshTiles, 0, 2 * sizeof(uint32_t), s));
   const uint32_t ep = next_epoch(c);
-  k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, sa, rank, act_next, pos_next,
-                                             n, misc + kMiscRefreshCount, c->ps.lookback,
-                                             c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
-                                             c->ps.err);
+  {
+    Launch lp_(c, kKRefresh, A, s);
+    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, sa, rank, act_next, pos_next,
+                                               n, misc + kMiscRefreshCount, c->ps.lookback,
+                                               c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
+                                               c->ps.err);
+  }
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscRefreshCount, sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s));
@@ -271,11 +274,14 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     return APO_ENOMEM;
   }
   const int g = grid_for(n, 256, c->num_sms);
-  k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
+  {
+    Launch lp_(c, kKInitKeys, n, s);
+    k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
+  }
   // how many token bits are populated
   uint64_t *kor = reinterpret_cast<uint64_t *>(c->ps.counters + kCtrMisc + kMiscKeyOr);
   APO_CUDA_TRY(cudaMemsetAsync(kor, 0, sizeof(uint64_t), s));
-  launch_key_or(b.keys[0], n, kor, s);
+  launch_key_or(c, b.keys[0], n, kor, s);
   uint64_t orv = 0;
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -297,8 +303,11 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       return APO_EDEVICE;
     }
     b.cur = 0;
-    k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, b.keys[0],
-                                                          b.vals[0]);
+    {
+      Launch lp_(c, kKPack, A, s);
+      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, b.keys[0],
+                                                            b.vals[0]);
+    }
     np = plan_digits(0, minor_bits, places, 0);
     np = plan_digits(32, 32 + major_bits, places, np);
     APO_TRY(radix_sort_pairs(c, b, A, places, np, s));
@@ -327,15 +336,27 @@ int build_lcp(apo_ctx *c, const void *tokens, int tb, const SuffixState &st, uin
     return APO_ENOMEM;
   }
   const int g = grid_for(n, 256, c->num_sms);
-  k_phi<<<g, 256, 0, s>>>(st.sa, n, phi);
+  {
+    Launch lp_(c, kKPhi, n, s);
+    k_phi<<<g, 256, 0, s>>>(st.sa, n, phi);
+  }
   const int pb = ceil_div(ceil_div(n, kPChunk), 128);
   if (tb == 4)
-    k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, phi, st.snaps[0],
-                                        st.levels, plcp);
+    {
+      Launch lp_(c, kKPlcp, n, s);
+      k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, phi, st.snaps[0],
+                                          st.levels, plcp);
+    }
   else
-    k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, phi, st.snaps[0],
-                                        st.levels, plcp);
-  k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, lcp);
+    {
+      Launch lp_(c, kKPlcp, n, s);
+      k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, phi, st.snaps[0],
+                                          st.levels, plcp);
+    }
+  {
+    Launch lp_(c, kKLcpPerm, n, s);
+    k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, lcp);
+  }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
 }
