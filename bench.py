@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU trace finder: analysed tokens per second.
+
+One step = the whole hot path over one window of synthetic task descriptors:
+FNV-1a task hashing (Alg. 1 Hash) -> suffix array by prefix doubling -> LCP
+-> Alg. 2 candidates, ordering, greedy non-overlapping selection (min trace
+length 5) -> Aho-Corasick match of the traces found against the window's
+token stream (Sec. 4.3).  The window is 2^20 tasks with nested loop periods
+7 / 120 / 3000 and 1% of positions replaced by one of 2^16 random
+descriptors (1-8 region arguments each).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  `value` is device-timed throughput with the
+descriptors resident in HBM (L2 flushed between steps); `e2e` is the same
+step through the library's API with host (pinned) inputs and results copied
+back inside the timed region; `roofline` reports the dominant kernel's
+algorithmic bytes per launch over its event-timed launch duration against
+the measured HBM copy bandwidth.  With N > 1 (torchrun) every rank analyses
+its own window (weak scaling; windows are independent, no collective on
+the data path).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "analyzed tokens/s (SA+LCP+repeats) batched vs plain, % HBM roofline; p99 ms"
+UNIT = "tokens/s"
+MIN_LEN = 5
+N_TASKS = 1 << 20
+WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/3000, 1% noise "
+            "from 2^16 descriptors, 1-8 region args): hash -> SA -> LCP -> Alg. 2 repeats "
+            "(min_len 5) -> Aho-Corasick match of the traces found against the window")
+
+# Algorithmic bytes moved per unit of work, per kernel (unit = the element
+# count the library records for each launch).  rs_pass: read and write one
+# (u64 key, u32 value) pair; refresh: read key, suffix, position, write SA,
+# rank, next active suffix and position; pack: read suffix and two ranks,
+# write a pair; hash: descriptor bytes in, 8 out (per task, at the
+# workload's mean of 4.5 arguments); ac_states: one u64 token in, one u32
+# state out; ac_fill: one state and offset in, 8 bytes per match out
+# (unit = positions; matches counted separately).
+BYTES_PER_UNIT = {"rs_pass": 24, "refresh": 32, "pack": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
+                  "ac_states": 12, "plcp": 24, "cand_gen": 36, "greedy": 8, "compact": 16}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n-tasks", type=int, default=N_TASKS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def env_ranks():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n_tasks: int) -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload (one
+    full step on a smaller window of the same structure), single-threaded."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    ts = W.config2_tasks(n_tasks, seed=2)
+    t0 = time.perf_counter()
+    tok = oracle.hash_tasks(ts)
+    r = oracle.find_repeats(tok, MIN_LEN)
+    st, tl = r.trace_start.astype(np.int64), r.trace_len.astype(np.int64)
+    off = np.zeros(len(tl) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(tl)
+    pt = np.concatenate([tok[s:s + l] for s, l in zip(st, tl)]) if len(tl) else np.zeros(1, np.uint64)
+    e, _ = oracle.match(pt, off, tok) if len(tl) else (np.zeros(0), None)
+    dt = time.perf_counter() - t0
+    return {"value": n_tasks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full step (hash, SA, LCP, repeats, match) on a {n_tasks}-task window of "
+                      f"the same structure; {len(e)} matches; {dt:.2f} s single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    n = 1 << 16  # bounded sample per step so that warmup + steps end within minutes
+    times = []
+    for k in range(args.warmup + args.steps):
+        ts = W.config2_tasks(n, seed=2)
+        t0 = time.perf_counter()
+        tok = oracle.hash_tasks(ts)
+        r = oracle.find_repeats(tok, MIN_LEN)
+        import numpy as np
+        st, tl = r.trace_start.astype(np.int64), r.trace_len.astype(np.int64)
+        off = np.zeros(len(tl) + 1, dtype=np.uint64)
+        off[1:] = np.cumsum(tl)
+        if len(tl):
+            pt = np.concatenate([tok[s:s + l] for s, l in zip(st, tl)])
+            oracle.match(pt, off, tok)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n * len(times) / tot
+    sample = (f"each step: one full step (hash, SA, LCP, repeats, match) on a {n}-task window of "
+              f"the workload's structure, single-threaded oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tokens": n, "min_len": MIN_LEN},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    rank, world, local = env_ranks()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    n = args.n_tasks
+    ts = W.config2_tasks(n, seed=2 + rank)
+    host = [torch.from_numpy(np.ascontiguousarray(a).view(dt)).pin_memory()
+            for a, dt in ((ts.task_id, np.int32), (ts.arg_off, np.int32), (ts.region, np.int32),
+                          (ts.field_mask, np.int64), (ts.priv, np.uint8))]
+    dts = [h.to(dev) for h in host]
+    h2d_bytes = sum(h.numel() * h.element_size() for h in host)
+    tok = torch.empty(n, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    cap = [8 * n]
+
+    def step(inputs):
+        apo.hash_tasks(*inputs, out=tok)
+        r = apo.find_repeats(tok, MIN_LEN, stages=False)
+        e, i = apo.match_candidates(tok, None, tok, cap=cap[0], pat_start=r.trace_start,
+                                    pat_len=r.trace_len)
+        return r, e, i
+
+    r = None
+    for _ in range(args.warmup):
+        r, e, i = step(dts)
+        cap[0] = max(cap[0], int(e.shape[0] * 1.25) + 1)
+    torch.cuda.synchronize()
+    stats = {"candidates": None, "selected": int(r.sel_start.shape[0]), "traces": int(r.trace_len.shape[0]),
+             "matches": int(e.shape[0]), "rounds": r.rounds}
+
+    def launches():
+        return sum(v[0] for v in apo.profile_read().values())
+
+    def timed(inputs_fn, out_fn=None):
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = step(inputs_fn())
+            if out_fn is not None:
+                out_fn(res)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        return total / args.steps
+
+    # 1. device-resident inputs
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = launches()
+    t_wall = time.perf_counter()
+    ms = timed(lambda: dts)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    n_launch = launches() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    # 2. the same steps with per-kernel event timing (roofline)
+    apo.profile_reset()
+    apo.profile(True)
+    ms_prof = timed(lambda: dts)
+    prof = apo.profile_read()
+    apo.profile(False)
+    # 3. end to end: pinned host inputs in, results back to the host
+    d2h = [0]
+    pinned_out = {}
+
+    def to_host(res):
+        r_, e_, i_ = res
+        nb = 0
+        for name, t in (("ss", r_.sel_start), ("sl", r_.sel_len), ("st", r_.sel_trace),
+                        ("tl", r_.trace_len), ("ts", r_.trace_start), ("me", e_), ("mi", i_)):
+            buf = pinned_out.get(name)
+            if buf is None or buf.numel() < t.numel():
+                buf = torch.empty(max(1, int(t.numel() * 1.25)), dtype=t.dtype, pin_memory=True)
+                pinned_out[name] = buf
+            buf[:t.numel()].copy_(t, non_blocking=True)
+            nb += t.numel() * t.element_size()
+        d2h[0] = nb
+
+    def h2d():
+        for d_, h_ in zip(dts, host):
+            d_.copy_(h_, non_blocking=True)
+        return dts
+
+    ms_e2e = timed(h2d, to_host)
+    clk = clocks.stop()
+
+    mst = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(mst, op=torch.distributed.ReduceOp.MAX)
+    ms, ms_e2e = float(mst[0]), float(mst[1])
+    value = n * world / (ms / 1e3)
+    e2e_value = n * world / (ms_e2e / 1e3)
+
+    # roofline of the dominant kernel
+    peak, peak_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (la, kms, units) = dom
+    bpu = BYTES_PER_UNIT.get(name)
+    roof = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+            "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof,
+            "traffic": None}
+    if bpu is not None and kms > 0:
+        ach = bpu * units / (kms / 1e3) / 1e9
+        roof.update({"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": bpu * units / la,
+                     "ms_per_launch": kms / la})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(1 << 18)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tokens": n, "min_len": MIN_LEN,
+                   "l2": "flushed between steps (512 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                "d2h_bytes_per_step": d2h[0], "ms_per_step": ms_e2e},
+        "gpu_launches": n_launch,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+        "ms_per_step_profiled": ms_prof,
+        "step_stats": stats,
+        "kernels": kernels,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -248,3 +248,21 @@ def test_invalid_arguments(apo):
         apo.find_repeats(t.to(torch.int16), 1)
     with pytest.raises(ApoError):
         apo.match_candidates(t, np.array([0, 2, 2], np.uint64), t)
+
+
+def test_match_traces_slice_form(apo):
+    """The traces apo_find_repeats returns, matched as device slices of the
+    window against the window itself (the bench's pipeline)."""
+    from paper_2406_18111_gb300 import as_u32
+    tok = oracle.hash_tasks(W.config2_tasks(1 << 14))
+    t = tokens_dev(tok, 8)
+    r = apo.find_repeats(t, 5, stages=False)
+    e, i = apo.match_candidates(t, None, t, pat_start=r.trace_start, pat_len=r.trace_len)
+    o = oracle.find_repeats(tok, 5)
+    st, tl = o.trace_start.astype(np.int64), o.trace_len.astype(np.int64)
+    off = np.zeros(len(tl) + 1, np.uint64)
+    off[1:] = np.cumsum(tl)
+    pt = np.concatenate([tok[s:s + l] for s, l in zip(st, tl)])
+    oe, oi = oracle.match(pt, off, tok)
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
