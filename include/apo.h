@@ -191,6 +191,33 @@ int apo_match_candidates(apo_ctx *ctx, const apo_patterns *patterns, const void 
                          uint64_t *count, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Greedy selection without allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * running inside a task runtime that owns all device memory through its own
+ * pool, or on a latency-critical path that must not pay for cudaMalloc /
+ * cudaFree (which may synchronise the whole device).  It needs no context.
+ *
+ * It runs Alg. 2's second loop on candidates already in greedy order (the
+ * cand_len / cand_start outputs of apo_find_repeats for a window of n
+ * tokens): accepted[k] = 1 iff [cand_start[k], cand_start[k] + cand_len[k])
+ * meets no interval accepted before it, and *accepted_count (DEVICE u32)
+ * receives the number accepted.  All arguments are device pointers owned by
+ * the caller; the call only enqueues work on `stream` and returns.
+ *
+ * Its scratch is a fixed bitmap of APO_NOALLOC_MAX_WINDOW bits (512 KiB)
+ * compiled into the library as a static device array, which every GPU that
+ * loads the library holds until the process exits.  A window larger than
+ * that is rejected with APO_EINVAL.  The first call on a device looks up the
+ * array's device address (once per device, on the current device); make that
+ * first call before any stream capture.  Every call shares the array and it
+ * keeps the last call's contents (each call clears the part it uses first);
+ * calls whose work overlaps on the GPU race on it, so do not run two at once.
+ * ---------------------------------------------------------------------- */
+#define APO_NOALLOC_MAX_WINDOW (1u << 22)
+int apo_greedy_select_noalloc(const uint32_t *cand_len, const uint32_t *cand_start, uint64_t m,
+                              uint64_t n, uint8_t *accepted, uint32_t *accepted_count, void *stream);
+
+/* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to report per-kernel
  * device time against the hardware roofline).
  *

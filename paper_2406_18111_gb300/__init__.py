@@ -29,7 +29,10 @@ _NAMES = {0: "APO_OK", -1: "APO_EINVAL", -2: "APO_ENOMEM", -3: "APO_ECAPACITY", 
 # Every symbol include/apo.h declares.
 EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_hash_tasks",
            "apo_find_repeats", "apo_match_candidates", "apo_profile_enable", "apo_profile_reset",
-           "apo_profile_read")
+           "apo_profile_read", "apo_greedy_select_noalloc")
+
+# Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
+NOALLOC_MAX_WINDOW = 1 << 22
 
 _P = ctypes.c_void_p
 _U64 = ctypes.c_uint64
@@ -94,6 +97,7 @@ def lib():
         L.apo_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
                                        ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(_U64)]
+        L.apo_greedy_select_noalloc.argtypes = [_P, _P, _U64, _U64, _P, _P, _P]
         for f in EXPORTS:
             if f not in ("apo_last_error",):
                 getattr(L, f).restype = ctypes.c_int
@@ -258,6 +262,17 @@ class Apo:
                 out[name.value.decode()] = (int(la.value), float(ms.value), int(un.value))
             i += 1
         return out
+
+
+def greedy_select_noalloc(cand_len, cand_start, n: int, accepted, accepted_count, stream=None):
+    """apo_greedy_select_noalloc: Alg. 2's greedy loop with no device
+    allocation, for callers that cannot allocate (see include/apo.h).  All
+    tensors are caller-owned device buffers: cand_len / cand_start (int32,
+    m entries, greedy order), accepted (uint8, m) and accepted_count (int32,
+    1).  Only enqueues the work on `stream`."""
+    m = int(cand_len.shape[0])
+    _check(lib().apo_greedy_select_noalloc(_ptr(cand_len), _ptr(cand_start), m, int(n), _ptr(accepted),
+                                           _ptr(accepted_count), _stream_handle(stream)))
 
 
 def as_u32(t) -> np.ndarray:
