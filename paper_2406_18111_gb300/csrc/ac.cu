@@ -5,22 +5,29 @@
 // failure link per node (longest proper suffix that is also in the trie) and
 // an output link per node (nearest pattern end on the failure chain).
 //
-// Build.  Tokens become 32-bit symbols (u32 tokens as they are; u64 tokens
-// by their index in the sorted list of distinct pattern tokens, a stream
-// token outside that list matching nothing).  The goto function is one
-// open-addressed hash table keyed by (node << 32 | symbol); one thread per
-// pattern inserts its path, claiming slots with atomicCAS (a node id is
-// published after its parent/depth/symbol).  Nodes are ordered by depth with
-// the radix sort, and failure and output links are computed level by level.
+// Symbols.  u32 tokens are their own symbols.  u64 tokens are mapped to 32-bit
+// symbols through an open-addressed dictionary filled from the pattern tokens
+// (a token's symbol is its slot); a stream token missing from the dictionary
+// matches nothing.  Both the pattern source and the stream are mapped once,
+// in parallel, before any sequential work.
 //
-// Match.  A node's state depends only on the last (max pattern length)
-// tokens, so the stream is cut into chunks and each thread runs the
-// automaton over its chunk after a halo of (max length - 1) tokens, writing
-// the state of every position.  The number of matches a state reports
-// (its own pattern ends plus those down its output chain) is precomputed per
-// node during the level-by-level link pass, so the output offsets are one
-// prefix sum over positions; a final kernel per position then writes its
-// matches.  Output order: end ascending, then pattern length descending (the
+// Build.  One cooperative kernel builds the trie level by level: at level d
+// every pattern longer than d inserts its (d+1)-th node into the goto hash
+// table (keyed by node << 32 | symbol, slots claimed with atomicCAS, ids from a
+// counter so that each level's nodes get a contiguous id range), while the
+// nodes of depth d get their failure link, output link and match total
+// (own pattern ends plus those down the output chain).  A bounded grid
+// barrier separates levels.
+//
+// Match.  The stream is cut into short chunks and each thread runs the
+// automaton over its chunk from the root, writing the state of every
+// position (only the first chunk is exact).  Repair passes then restart each
+// chunk from its predecessor's end state and stop at the first position whose
+// state agrees with the recorded one -- from there on the deterministic
+// automaton repeats the recorded run.  When a pass changes no end state all
+// states are exact (after k passes chunks 0..k are, by induction).  The
+// per-node match totals turn the output offsets into one prefix sum over
+// positions; a final kernel per position writes its matches.  Output order: end ascending, then pattern length descending (the
 // output chain's order), then pattern id ascending.
 #include <algorithm>
 #include <cstring>
@@ -45,85 +52,71 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   return k;
 }
 
-struct Goto {
-  uint64_t *keys;
-  uint32_t *vals;
+// Open addressing with linear probing, capacity a power of two.  A goto entry
+// is 16 bytes (key, child id, pad) so that one 128-bit load reads both.
+struct Table {
+  uint64_t *keys;  // entry e: keys[2e] = key, keys[2e+1] low word = value
   uint64_t mask;
 };
 
-__device__ __forceinline__ uint32_t goto_lookup(const Goto &g, uint32_t u, uint32_t c) {
+__device__ __forceinline__ uint32_t goto_lookup(const Table &g, uint32_t u, uint32_t c) {
   const uint64_t key = ((uint64_t)u << 32) | c;
   uint64_t slot = mix64(key) & g.mask;
   while (true) {
-    const uint64_t k = g.keys[slot];
-    if (k == key) return g.vals[slot];
-    if (k == kEmpty) return kNil;
+    const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(g.keys + 2 * slot);
+    if (e.x == key) return (uint32_t)e.y;
+    if (e.x == kEmpty) return kNil;
     slot = (slot + 1) & g.mask;
   }
 }
 
-__device__ __forceinline__ uint32_t to_sym(const void *tok, int tb, uint64_t i, const uint64_t *dict,
-                                           uint32_t sigma) {
-  if (tb == 4) return static_cast<const uint32_t *>(tok)[i];
-  const uint64_t t = static_cast<const uint64_t *>(tok)[i];
-  uint32_t lo = 0, hi = sigma;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (dict[mid] < t) lo = mid + 1; else hi = mid;
+// ---------------------------------------------------------------- symbols
+struct Dict {
+  uint64_t *keys;  // a token's symbol is its slot
+  uint64_t mask;
+};
+
+__global__ void k_dict_insert(const uint64_t *__restrict__ tok, uint64_t m, Dict d) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = tok[i];
+    if (t == kEmpty) continue;  // mapped to a reserved symbol instead
+    uint64_t slot = mix64(t) & d.mask;
+    for (uint64_t probe = 0; probe <= d.mask; ++probe) {
+      uint64_t cur = d.keys[slot];
+      if (cur == t) break;
+      if (cur == kEmpty) {
+        cur = atomicCAS((unsigned long long *)&d.keys[slot], (unsigned long long)kEmpty,
+                        (unsigned long long)t);
+        if (cur == kEmpty || cur == t) break;
+      }
+      slot = (slot + 1) & d.mask;
+    }
   }
-  return (lo < sigma && dict[lo] == t) ? lo : kNil;
 }
 
-__global__ void k_trie_insert(const void *pat_tok, int tb, const uint32_t *__restrict__ pstart,
-                              const uint32_t *__restrict__ plen, uint32_t P, const uint64_t *dict,
-                              uint32_t sigma, Goto g,
-                              uint32_t *node_ctr, uint32_t *parent, uint32_t *depth, uint32_t *nsym,
-                              uint32_t *end_node, uint32_t *err) {
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  uint32_t u = 0;
-  const uint64_t off = pstart[p], len = plen[p];
-  for (uint64_t d = 0; d < len; ++d) {
-    const uint32_t c = to_sym(pat_tok, tb, off + d, dict, sigma);
-    const uint64_t key = ((uint64_t)u << 32) | c;
-    uint64_t slot = mix64(key) & g.mask;
-    uint32_t v = kNil;
-    for (uint64_t probe = 0; probe <= g.mask; ++probe) {
-      uint64_t cur = *(volatile uint64_t *)&g.keys[slot];
-      if (cur == kEmpty) {
-        cur = atomicCAS((unsigned long long *)&g.keys[slot], (unsigned long long)kEmpty,
-                        (unsigned long long)key);
-        if (cur == kEmpty) {  // this thread created the node
-          v = atomicAdd(node_ctr, 1u) + 1u;
-          parent[v] = u;
-          depth[v] = (uint32_t)d + 1;
-          nsym[v] = c;
-          __threadfence();
-          *(volatile uint32_t *)&g.vals[slot] = v;
+__global__ void k_dict_map(const uint64_t *__restrict__ tok, uint64_t m, Dict d,
+                           uint32_t *__restrict__ sym) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = tok[i];
+    uint32_t s = kNil;
+    if (t == kEmpty) {
+      s = (uint32_t)(d.mask + 1);  // reserved symbol of the all-ones token
+    } else {
+      uint64_t slot = mix64(t) & d.mask;
+      while (true) {
+        const uint64_t k = d.keys[slot];
+        if (k == t) {
+          s = (uint32_t)slot;
           break;
         }
+        if (k == kEmpty) break;
+        slot = (slot + 1) & d.mask;
       }
-      if (cur == key) {  // wait until the creator publishes the id
-        uint32_t spins = 0;
-        while ((v = *(volatile uint32_t *)&g.vals[slot]) == 0) {
-          if (++spins > kSpinLimit) {
-            atomicExch(err, kDevTimeout);
-            return;
-          }
-          __nanosleep(64);
-        }
-        __threadfence();
-        break;
-      }
-      slot = (slot + 1) & g.mask;
     }
-    if (v == kNil) {
-      atomicExch(err, kDevRange);
-      return;
-    }
-    u = v;
+    sym[i] = s;
   }
-  end_node[p] = u;
 }
 
 // max length, max end and total length of slice-form patterns; flags empty ones
@@ -144,13 +137,148 @@ __global__ void k_slices(const uint32_t *__restrict__ pstart, const uint32_t *__
   atomicAdd(total, tot);
 }
 
-__global__ void k_depth_keys(const uint32_t *__restrict__ depth, uint32_t N, uint64_t *keys,
-                             uint32_t *vals, uint32_t *level_cnt) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
-    const uint32_t d = v == 0 ? 0 : depth[v];
-    keys[v] = d;
-    vals[v] = v;
-    atomicAdd(&level_cnt[d], 1u);
+// ---------------------------------------------------------------- build
+struct GridBarrier {
+  uint32_t *count;
+  uint32_t *gen;
+};
+
+// All blocks of a cooperative launch meet here.  Bounded: a block that waits
+// too long records kDevTimeout and leaves (the caller then stops).
+__device__ void grid_sync(const GridBarrier &b, uint32_t *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t g0 = *(volatile uint32_t *)b.gen;
+    __threadfence();
+    if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
+      *(volatile uint32_t *)b.count = 0;
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      uint32_t spins = 0;
+      while (*(volatile uint32_t *)b.gen == g0) {
+        if (++spins > kSpinLimit) {
+          atomicExch(err, kDevTimeout);
+          break;
+        }
+        if (spins > 16) __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct BuildArgs {
+  const uint32_t *psym;    // symbols of the pattern source tokens
+  const uint32_t *pstart;  // pattern p = psym[pstart[p] .. pstart[p] + plen[p])
+  const uint32_t *plen;
+  uint32_t P;
+  uint32_t maxlen;
+  Table g;
+  uint32_t *cur;       // [P] node of each pattern at the current level
+  uint32_t *parent;    // [N]
+  uint32_t *nsym;      // [N] symbol on the edge into the node
+  uint32_t *fail;      // [N]
+  uint32_t *outl;      // [N]
+  uint32_t *own;       // [N] patterns ending exactly here
+  uint32_t *total;     // [N] matches reported in this state
+  uint32_t *end_node;  // [P]
+  uint32_t *node_ctr;
+  GridBarrier bar;
+  uint32_t *err;
+};
+
+constexpr int kBuildThreads = 512;
+
+__global__ void __launch_bounds__(kBuildThreads) k_ac_build(BuildArgs a) {
+  // the first half of the grid inserts, the second half computes links
+  const uint32_t half = gridDim.x * blockDim.x / 2;
+  const uint32_t gt0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool inserter = gt0 < half;
+  const uint32_t gt = inserter ? gt0 : gt0 - half;
+  const uint32_t nth = half;
+  uint32_t lo = 1, hi = 1;  // ids of the nodes of depth d
+  for (uint32_t d = 0; d <= a.maxlen; ++d) {
+    // (a) depth d+1 nodes of every pattern longer than d
+    for (uint32_t p = inserter ? gt : a.P; p < a.P; p += nth) {
+      if (d >= a.plen[p]) continue;
+      const uint32_t u = d ? a.cur[p] : 0u;
+      const uint32_t c = a.psym[a.pstart[p] + d];
+      const uint64_t key = ((uint64_t)u << 32) | c;
+      uint64_t slot = mix64(key) & a.g.mask;
+      uint32_t v = kNil;
+      for (uint64_t probe = 0; probe <= a.g.mask; ++probe) {
+        uint64_t *ek = a.g.keys + 2 * slot;
+        uint64_t cur = *(volatile uint64_t *)ek;
+        if (cur == kEmpty) {
+          cur = atomicCAS((unsigned long long *)ek, (unsigned long long)kEmpty,
+                          (unsigned long long)key);
+          if (cur == kEmpty) {  // this thread creates the node
+            v = atomicAdd(a.node_ctr, 1u) + 1u;
+            a.parent[v] = u;
+            a.nsym[v] = c;
+            __threadfence();
+            *(volatile uint64_t *)(ek + 1) = v;
+            break;
+          }
+        }
+        if (cur == key) {  // created by another thread of this level
+          uint32_t spins = 0;
+          while ((v = (uint32_t) * (volatile uint64_t *)(ek + 1)) == 0) {
+            if (++spins > kSpinLimit) {
+              atomicExch(a.err, kDevTimeout);
+              break;
+            }
+          }
+          __threadfence();
+          break;
+        }
+        slot = (slot + 1) & a.g.mask;
+      }
+      if (v == kNil || v == 0) {
+        atomicExch(a.err, kDevRange);
+        continue;
+      }
+      a.cur[p] = v;
+      if (d + 1 == a.plen[p]) {
+        a.end_node[p] = v;
+        atomicAdd(&a.own[v], 1u);
+      }
+    }
+    // (b) links of the depth-d nodes (all shallower nodes are complete)
+    for (uint32_t v = inserter ? hi : lo + gt; v < hi; v += nth) {
+      uint32_t f = 0;
+      if (d > 1) {
+        const uint32_t c = a.nsym[v];
+        uint32_t w = a.fail[a.parent[v]];
+        while (true) {
+          const uint32_t x = goto_lookup(a.g, w, c);
+          if (x != kNil) {
+            f = x;
+            break;
+          }
+          if (w == 0) break;
+          w = a.fail[w];
+        }
+      }
+      a.fail[v] = f;
+      const uint32_t o = (f != 0 && a.own[f] != 0) ? f : a.outl[f];
+      a.outl[v] = o;
+      a.total[v] = a.own[v] + a.total[o];
+    }
+    grid_sync(a.bar, a.err);
+    if (*(volatile uint32_t *)a.err != kDevOk) return;
+    lo = hi;
+    hi = *(volatile uint32_t *)a.node_ctr + 1;
+  }
+}
+
+__global__ void k_table_init(uint64_t *keys, uint64_t entries) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < entries;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    keys[2 * e] = kEmpty;
+    keys[2 * e + 1] = 0;
   }
 }
 
@@ -167,66 +295,62 @@ __global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint
     if (k == 0 || skeys[k] != skeys[k - 1]) end_first[(uint32_t)skeys[k]] = k;
 }
 
-// Failure and output links of the nodes order[lo, hi) (all of one depth).
-__global__ void k_fail_level(const uint32_t *__restrict__ order, uint32_t lo, uint32_t hi,
-                             uint32_t d, Goto g, const uint32_t *__restrict__ parent,
-                             const uint32_t *__restrict__ nsym, const uint32_t *__restrict__ end_first,
-                             const uint32_t *__restrict__ own, uint32_t *fail, uint32_t *outl,
-                             uint32_t *total) {
-  for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
-    const uint32_t v = order[i];
-    uint32_t f = 0;
-    if (d > 1) {
-      const uint32_t c = nsym[v];
-      uint32_t w = fail[parent[v]];
-      while (true) {
-        const uint32_t x = goto_lookup(g, w, c);
-        if (x != kNil) {
-          f = x;
-          break;
-        }
-        if (w == 0) break;
-        w = fail[w];
-      }
-    }
-    fail[v] = f;
-    const uint32_t o = (f != 0 && end_first[f] != kNil) ? f : outl[f];
-    outl[v] = o;
-    total[v] = own[v] + total[o];  // matches reported when the automaton is in v
+// ---------------------------------------------------------------- match
+__device__ __forceinline__ uint32_t ac_step(const Table &g, const uint32_t *__restrict__ fail,
+                                            uint32_t state, uint32_t c) {
+  while (true) {
+    const uint32_t nx = goto_lookup(g, state, c);
+    if (nx != kNil) return nx;
+    if (state == 0) return 0;
+    state = fail[state];
   }
 }
 
-// own[v] = number of patterns ending exactly at node v.
-__global__ void k_own_counts(const uint64_t *__restrict__ skeys, uint32_t P, uint32_t *own) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x)
-    atomicAdd(&own[(uint32_t)skeys[k]], 1u);
-}
-
-// Pass A: automaton state after every stream position.  Thread t owns
-// positions [t*chunk, (t+1)*chunk) and starts from the root `halo` tokens
-// earlier (a state only depends on the last max-length tokens).
-__global__ void k_ac_states(const void *stream, int tb, uint64_t n, uint64_t chunk, uint64_t halo,
-                            const uint64_t *dict, uint32_t sigma, Goto g,
-                            const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out) {
+// Pass A1: chunk t = positions [t*chunk, (t+1)*chunk) from the root state.
+// Chunk 0 is exact; the others may start in the wrong state.
+__global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Table g,
+                            const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out,
+                            uint32_t *__restrict__ end_state) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
   const uint64_t ce = min(n, cs + chunk);
-  uint64_t x = cs > halo ? cs - halo : 0;
   uint32_t state = 0;
-  for (; x < ce; ++x) {
-    const uint32_t c = to_sym(stream, tb, x, dict, sigma);
-    while (true) {
-      const uint32_t nx = (c == kNil && tb == 8) ? kNil : goto_lookup(g, state, c);
-      if (nx != kNil) {
-        state = nx;
-        break;
-      }
-      if (state == 0) break;
-      state = fail[state];
-    }
-    if (x >= cs) state_out[x] = state;
+  for (uint64_t x = cs; x < ce; ++x) {
+    state = ac_step(g, fail, state, ssym[x]);
+    state_out[x] = state;
   }
+  end_state[t] = state;
+}
+
+// Pass A2 (repeated until nothing changes): chunk t restarts from the end
+// state of chunk t-1 and re-runs until its state equals the recorded one
+// (the automaton is deterministic, so the rest of the chunk already agrees).
+// After k passes chunks 0..k are exact; the host stops when no end state
+// changed.
+__global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Table g,
+                         const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out,
+                         const uint32_t *__restrict__ end_in, uint32_t *__restrict__ end_out,
+                         uint32_t *changed) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t cs = t * chunk;
+  if (cs >= n) return;
+  if (t == 0) {
+    end_out[0] = end_in[0];
+    return;
+  }
+  const uint64_t ce = min(n, cs + chunk);
+  uint32_t state = end_in[t - 1];
+  for (uint64_t x = cs; x < ce; ++x) {
+    state = ac_step(g, fail, state, ssym[x]);
+    if (state_out[x] == state) {
+      end_out[t] = end_in[t];
+      return;
+    }
+    state_out[x] = state;
+  }
+  end_out[t] = state;
+  if (state != end_in[t]) atomicAdd(changed, 1u);
 }
 
 // Exclusive prefix sum of total[state[x]] over stream positions (the first
@@ -245,8 +369,7 @@ __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restric
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * kSTile;
-  for (int q = tid; q < kSTile; q += kST)
-    sv[q] = base + q < n ? total[state[base + q]] : 0u;
+  for (int q = tid; q < kSTile; q += kST) sv[q] = base + q < n ? total[state[base + q]] : 0u;
   __syncthreads();
   uint32_t run = 0;
 #pragma unroll
@@ -273,19 +396,20 @@ __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restric
   }
 }
 
-// Pass B: the matches of position x, following the output chain from its
-// state (deepest first), ids ascending within a node.
+// Pass B: the matches of position x, down the output chain from its state
+// (deepest first), ids ascending within a node.
 __global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
-                          const uint32_t *__restrict__ off, const uint32_t *__restrict__ outl,
-                          const uint32_t *__restrict__ end_first, const uint64_t *__restrict__ ekeys,
-                          const uint32_t *__restrict__ evals, uint32_t P, uint32_t *mend,
-                          uint32_t *mid, uint64_t cap) {
+                          const uint32_t *__restrict__ off, const uint32_t *__restrict__ own,
+                          const uint32_t *__restrict__ outl, const uint32_t *__restrict__ end_first,
+                          const uint32_t *__restrict__ evals, uint32_t *mend, uint32_t *mid,
+                          uint64_t cap) {
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     const uint32_t s0 = state[x];
     uint64_t o = off[x];
-    uint32_t v = end_first[s0] != kNil ? s0 : outl[s0];
+    uint32_t v = own[s0] != 0 ? s0 : outl[s0];
     while (v != 0) {
-      for (uint32_t k = end_first[v]; k < P && (uint32_t)ekeys[k] == v; ++k) {
+      const uint32_t k0 = end_first[v], k1 = k0 + own[v];
+      for (uint32_t k = k0; k < k1; ++k) {
         if (o < cap) {
           mend[o] = x;
           mid[o] = evals[k];
@@ -297,36 +421,33 @@ __global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
   }
 }
 
-__global__ void k_u64_keys(const uint64_t *__restrict__ t, uint64_t m, uint64_t *keys, uint32_t *vals) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    keys[q] = t[q];
-    vals[q] = 0;
-  }
-}
-
-__global__ void k_unique_u64(const uint64_t *__restrict__ s, uint64_t m, uint64_t *out,
-                             unsigned long long *cnt) {
-  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    if (q == 0 || s[q] != s[q - 1]) out[atomicAdd(cnt, 1ull)] = s[q];  // sorted again after
-  }
-}
-
 inline int grid_for(uint64_t n, int threads, int sms) {
   long long b = (long long)((n + threads - 1) / threads);
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
+int g_build_blocks = 0;  // co-resident blocks of k_ac_build for a cooperative launch
+
 }  // namespace
 
-size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t cap) {
+int match_init(int sms) {
+  // A small cooperative grid: the level barrier's cost grows with the number
+  // of arriving blocks, and 16K threads cover the patterns and the nodes of
+  // a level for the workloads at hand (larger sets loop).
+  int per_sm = 0;
+  APO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ac_build, kBuildThreads, 0));
+  g_build_blocks = std::max(1, std::min(32, per_sm * sms));
+  return APO_OK;
+}
+
+size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t extent) {
   uint64_t tbl = 1;
   while (tbl < 2 * (total_tokens + 1)) tbl <<= 1;
+  uint64_t dct = 1;
+  while (dct < 2 * (extent + 1)) dct <<= 1;
   const uint64_t N = total_tokens + 1;
-  (void)cap;
-  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, total_tokens), P);
-  return tbl * 12 + N * 4 * 9 + P * 24 + (P + 1) * 8 + total_tokens * 12 + M * 24 + n * 8 +
+  const uint64_t chunks = n / 32 + 2;
+  return tbl * 16 + dct * 12 + N * 4 * 8 + P * 48 + (extent + n) * 4 + n * 8 + chunks * 8 +
          64 * 256;
 }
 
@@ -341,7 +462,6 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   // pattern p = tokens[pstart[p] .. pstart[p] + plen[p])
   const uint32_t *pstart = pp->pat_start, *plen = pp->pat_len;
   uint64_t total = 0, maxlen = 0, extent = 0;
-  uint32_t *hostbuf = nullptr;
   if (pp->pat_off) {
     for (uint32_t p = 0; p < P; ++p) maxlen = std::max(maxlen, pp->pat_off[p + 1] - pp->pat_off[p]);
     total = pp->pat_off[P];
@@ -365,45 +485,38 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     extent = c->host_pinned[1];
     memcpy(&total, c->host_pinned + 2, 8);
   }
-  (void)hostbuf;
   if (total >= 0xffffffffull || extent >= 0xffffffffull) {
     set_error("match_candidates: more than 2^32 - 1 pattern tokens");
     return APO_EINVAL;
   }
-  APO_TRY(c->arena.reserve(match_workspace_bytes(std::max(total, extent), P, n, cap)));
+  APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent)));
   const uint64_t N = total + 1;  // node bound (root included)
   uint64_t tbl = 1;
   while (tbl < 2 * N) tbl <<= 1;
-  Goto g;
-  g.keys = c->arena.take_n<uint64_t>(tbl);
-  g.vals = c->arena.take_n<uint32_t>(tbl);
+
+  Table g;
+  g.keys = c->arena.take_n<uint64_t>(2 * tbl);
   g.mask = tbl - 1;
   uint32_t *pbuf = pp->pat_off ? c->arena.take_n<uint32_t>(2 * (size_t)P) : nullptr;
   uint32_t *parent = c->arena.take_n<uint32_t>(N);
-  uint32_t *depth = c->arena.take_n<uint32_t>(N);
   uint32_t *nsym = c->arena.take_n<uint32_t>(N);
   uint32_t *fail = c->arena.take_n<uint32_t>(N);
   uint32_t *outl = c->arena.take_n<uint32_t>(N);
-  uint32_t *end_first = c->arena.take_n<uint32_t>(N);
-  uint32_t *end_node = c->arena.take_n<uint32_t>(P);
   uint32_t *own = c->arena.take_n<uint32_t>(N);
   uint32_t *mtotal = c->arena.take_n<uint32_t>(N);
-  uint32_t *levels = c->arena.take_n<uint32_t>(maxlen + 2);
-  const uint64_t M = std::max<uint64_t>(std::max<uint64_t>(N, extent), P);
+  uint32_t *end_first = c->arena.take_n<uint32_t>(N);
+  uint32_t *cur = c->arena.take_n<uint32_t>(P);
+  uint32_t *end_node = c->arena.take_n<uint32_t>(P);
   SortBuffers b;
-  b.keys[0] = c->arena.take_n<uint64_t>(M);
-  b.keys[1] = c->arena.take_n<uint64_t>(M);
-  b.vals[0] = c->arena.take_n<uint32_t>(M);
-  b.vals[1] = c->arena.take_n<uint32_t>(M);
-  uint64_t *dict = c->arena.take_n<uint64_t>(std::max<uint64_t>(extent, 1));
-  if (!g.keys || !g.vals || (pp->pat_off && !pbuf) || !parent || !depth || !nsym || !fail || !outl || !end_first || !own || !mtotal ||
-      !end_node || !levels || !b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !dict) {
+  b.keys[0] = c->arena.take_n<uint64_t>(P);
+  b.keys[1] = c->arena.take_n<uint64_t>(P);
+  b.vals[0] = c->arena.take_n<uint32_t>(P);
+  b.vals[1] = c->arena.take_n<uint32_t>(P);
+  if (!g.keys || (pp->pat_off && !pbuf) || !parent || !nsym || !fail || !outl || !own ||
+      !mtotal || !end_first || !cur || !end_node || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
+      !b.vals[1]) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
-  }
-  if (M >= 0xffffffffull || N >= 0xffffffffull || n >= 0xffffffffull) {
-    set_error("match: more than 2^32 - 1 nodes, stream tokens or matches");
-    return APO_EINVAL;
   }
   if (pp->pat_off) {  // CSR on the host -> (start, len) on the device
     std::vector<uint32_t> h(2 * (size_t)P);
@@ -416,130 +529,120 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     pstart = pbuf;
     plen = pbuf + P;
   }
-  APO_CUDA_TRY(cudaMemsetAsync(g.keys, 0xff, tbl * sizeof(uint64_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(g.vals, 0, tbl * sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(end_first, 0xff, N * sizeof(uint32_t), s));
+  {  // every entry: key = empty, value = 0
+    Launch lp_(c, kKDepthKeys, tbl, s);
+    k_table_init<<<grid_for(tbl, 256, sms), 256, 0, s>>>(g.keys, tbl);
+  }
   APO_CUDA_TRY(cudaMemsetAsync(own, 0, N * sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(mtotal, 0, N * sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(levels, 0, (maxlen + 2) * sizeof(uint32_t), s));
-  // u64 tokens: dictionary of distinct pattern tokens
-  uint32_t sigma = 0;
-  if (tb == 8) {
+  APO_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(outl, 0, sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(mtotal, 0, sizeof(uint32_t), s));
+
+  // symbols of the pattern source and of the stream
+  const uint32_t *psym = nullptr, *ssym = nullptr;
+  if (tb == 4) {
+    psym = static_cast<const uint32_t *>(pp->tokens);
+    ssym = static_cast<const uint32_t *>(stream);
+  } else {
+    uint64_t dct = 1;
+    while (dct < 2 * (extent + 1)) dct <<= 1;
+    Dict d;
+    d.keys = c->arena.take_n<uint64_t>(dct);
+    d.mask = dct - 1;
+    const bool same = pp->tokens == stream && n >= extent;
+    uint32_t *ps = c->arena.take_n<uint32_t>(std::max<uint64_t>(same ? n : extent, 1));
+    uint32_t *ss = same ? ps : c->arena.take_n<uint32_t>(std::max<uint64_t>(n, 1));
+    if (!d.keys || !ps || !ss) return APO_ENOMEM;
+    APO_CUDA_TRY(cudaMemsetAsync(d.keys, 0xff, dct * sizeof(uint64_t), s));
+    const uint64_t *pt = static_cast<const uint64_t *>(pp->tokens);
     {
-      Launch lp_(c, kKU64Keys, 0, s);
-      k_u64_keys<<<grid_for(extent, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens),
-                                                            extent, b.keys[0], b.vals[0]);
+      Launch lp_(c, kKU64Keys, extent, s);
+      k_dict_insert<<<grid_for(extent, 256, sms), 256, 0, s>>>(pt, extent, d);
     }
-    b.cur = 0;
-    int places[8];
-    const int np = plan_digits(0, 64, places, 0);
-    APO_TRY(radix_sort_pairs(c, b, (uint32_t)extent, places, np, s));
-    APO_CUDA_TRY(cudaMemsetAsync(cnt64, 0, 8, s));
     {
-      Launch lp_(c, kKUnique, extent, s);
-      k_unique_u64<<<grid_for(extent, 256, sms), 256, 0, s>>>(b.keys[b.cur], extent, dict, cnt64);
+      Launch lp_(c, kKUnique, same ? n : extent, s);
+      k_dict_map<<<grid_for(same ? n : extent, 256, sms), 256, 0, s>>>(pt, same ? n : extent, d, ps);
     }
-    unsigned long long sg = 0;
-    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, cnt64, 8, cudaMemcpyDeviceToHost, s));
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    memcpy(&sg, c->host_pinned, 8);
-    sigma = (uint32_t)sg;
-    // distinct values were appended in arbitrary order: sort them
-    {
-      Launch lp_(c, kKU64Keys, 0, s);
-      k_u64_keys<<<grid_for(sigma, 256, sms), 256, 0, s>>>(dict, sigma, b.keys[0], b.vals[0]);
+    if (!same) {
+      Launch lp_(c, kKUnique, n, s);
+      k_dict_map<<<grid_for(n, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(stream), n, d, ss);
     }
-    b.cur = 0;
-    APO_TRY(radix_sort_pairs(c, b, sigma, places, np, s));
-    APO_CUDA_TRY(cudaMemcpyAsync(dict, b.keys[b.cur], sigma * sizeof(uint64_t),
-                                 cudaMemcpyDeviceToDevice, s));
+    psym = ps;
+    ssym = ss;
   }
 
-  // trie
-  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMatchCount, 0, sizeof(uint32_t), s));
+  // trie, failure / output links and match totals, level by level
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMatchCount, 0, 3 * sizeof(uint32_t), s));
   {
+    BuildArgs a;
+    a.psym = psym;
+    a.pstart = pstart;
+    a.plen = plen;
+    a.P = P;
+    a.maxlen = (uint32_t)maxlen;
+    a.g = g;
+    a.cur = cur;
+    a.parent = parent;
+    a.nsym = nsym;
+    a.fail = fail;
+    a.outl = outl;
+    a.own = own;
+    a.total = mtotal;
+    a.end_node = end_node;
+    a.node_ctr = misc + kMiscMatchCount;
+    a.bar.count = misc + kMiscMatchCount + 1;
+    a.bar.gen = misc + kMiscMatchCount + 2;
+    a.err = c->ps.err;
+    void *args[] = {&a};
     Launch lp_(c, kKTrieInsert, total, s);
-    k_trie_insert<<<ceil_div(P, 128), 128, 0, s>>>(pp->tokens, tb, pstart, plen, P, dict, sigma, g,
-                                                   misc + kMiscMatchCount, parent, depth, nsym,
-                                                   end_node, c->ps.err);
+    APO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_ac_build, g_build_blocks, kBuildThreads,
+                                             args, 0, s));
   }
   APO_CUDA_TRY(cudaGetLastError());
-  uint32_t nodes = 0;
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMatchCount, 4, cudaMemcpyDeviceToHost, s));
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
-  nodes = c->host_pinned[0] + 1;
-
-  // pattern ends: (end node, pattern id) sorted by node
-  uint64_t *ek;
-  uint32_t *ev;
+  // pattern ids grouped by end node
   {
     Launch lp_(c, kKEndPairs, P, s);
     k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, b.keys[0], b.vals[0]);
   }
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMatchCount, 4, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  APO_TRY(check_device_error(c, s));
+  const uint32_t nodes = c->host_pinned[0] + 1;
   b.cur = 0;
   {
     int places[8];
     const int np = plan_digits(0, bits_for(nodes), places, 0);
     APO_TRY(radix_sort_pairs(c, b, P, places, np, s));
   }
-  // keep the sorted end pairs where the depth sort below will not overwrite them
-  ek = c->arena.take_n<uint64_t>(P);
-  ev = c->arena.take_n<uint32_t>(P);
-  if (!ek || !ev) return APO_ENOMEM;
-  APO_CUDA_TRY(cudaMemcpyAsync(ek, b.keys[b.cur], P * 8, cudaMemcpyDeviceToDevice, s));
-  APO_CUDA_TRY(cudaMemcpyAsync(ev, b.vals[b.cur], P * 4, cudaMemcpyDeviceToDevice, s));
+  const uint64_t *ek = b.keys[b.cur];
+  const uint32_t *ev = b.vals[b.cur];
   {
     Launch lp_(c, kKMarkEnds, P, s);
     k_mark_ends<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, end_first);
   }
-  {
-    Launch lp_(c, kKOwn, P, s);
-    k_own_counts<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, own);
-  }
-
-  // BFS order by depth
-  {
-    Launch lp_(c, kKDepthKeys, nodes, s);
-    k_depth_keys<<<grid_for(nodes, 256, sms), 256, 0, s>>>(depth, nodes, b.keys[0], b.vals[0], levels);
-  }
-  b.cur = 0;
-  {
-    int places[8];
-    const int np = plan_digits(0, bits_for(maxlen), places, 0);
-    APO_TRY(radix_sort_pairs(c, b, nodes, places, np, s));
-  }
-  std::vector<uint32_t> lc(maxlen + 1);
-  APO_CUDA_TRY(cudaMemcpyAsync(lc.data(), levels, (maxlen + 1) * 4, cudaMemcpyDeviceToHost, s));
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  const uint32_t *order = b.vals[b.cur];
-  APO_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(outl, 0, sizeof(uint32_t), s));
-  uint32_t lo = lc[0];
-  for (uint64_t d = 1; d <= maxlen; ++d) {
-    const uint32_t hi = lo + lc[d];
-    if (hi > lo) {
-      Launch lp_(c, kKFailLevel, hi - lo, s);
-      k_fail_level<<<grid_for(hi - lo, 128, sms), 128, 0, s>>>(order, lo, hi, (uint32_t)d, g, parent,
-                                                              nsym, end_first, own, fail, outl,
-                                                              mtotal);
-    }
-    lo = hi;
-  }
-  APO_CUDA_TRY(cudaGetLastError());
   if (n == 0) return APO_OK;
 
-  // pass A: states
+  // pass A: states, chunked without a halo, then repaired until stable
   uint32_t *state = c->arena.take_n<uint32_t>(n);
   uint32_t *off = c->arena.take_n<uint32_t>(n);
-  if (!state || !off) return APO_ENOMEM;
-  const uint64_t halo = maxlen ? maxlen - 1 : 0;
-  const uint64_t chunk = std::max<uint64_t>(64, n / ((uint64_t)sms * 32));
-  const uint64_t threads = (n + chunk - 1) / chunk;
+  const uint64_t chunk = std::max<uint64_t>(32, n / ((uint64_t)sms * 64));
+  const uint64_t nch = (n + chunk - 1) / chunk;
+  uint32_t *ends[2] = {c->arena.take_n<uint32_t>(nch), c->arena.take_n<uint32_t>(nch)};
+  if (!state || !off || !ends[0] || !ends[1]) return APO_ENOMEM;
   {
     Launch lp_(c, kKAcMatch, n, s);
-    k_ac_states<<<ceil_div(threads, 128), 128, 0, s>>>(stream, tb, n, chunk, halo, dict, sigma, g,
-                                                       fail, state);
+    k_ac_states<<<ceil_div(nch, 128), 128, 0, s>>>(ssym, n, chunk, g, fail, state, ends[0]);
+  }
+  for (uint64_t pass = 0, e = 0; pass < nch; ++pass, e ^= 1) {
+    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
+    {
+      Launch lp_(c, kKFailLevel, n, s);
+      k_ac_fix<<<ceil_div(nch, 128), 128, 0, s>>>(ssym, n, chunk, g, fail, state, ends[e], ends[e ^ 1],
+                                                   misc + kMiscAccCount);
+    }
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->host_pinned[0] == 0) break;
   }
   // output offsets and total
   const int tiles = ceil_div(n, kSTile);
@@ -563,7 +666,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   if (total_m) {
     Launch lp_(c, kKAcFill, n, s);
-    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, outl, end_first, ek, ev, P,
+    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, own, outl, end_first, ev,
                                                     match_end, match_id, cap);
   }
   APO_CUDA_TRY(cudaGetLastError());

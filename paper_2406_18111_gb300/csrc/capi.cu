@@ -13,6 +13,7 @@ size_t repeats_workspace_bytes(uint64_t n);
 size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t cap);
 int suffix_init();
 int repeats_init(int smem_optin);
+int match_init(int sms);
 
 namespace {
 thread_local std::string g_last_error;
@@ -64,8 +65,8 @@ int ensure_lookback(apo_ctx *c, size_t words) {
 const char *const kKernelNames[kKCount] = {
     "hash_tasks", "init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
-    "traces", "sel_out", "trie_insert", "depth_keys", "end_pairs", "mark_ends", "fail_level",
-    "ac_states", "ac_fill", "u64_keys", "unique", "slices", "match_offsets", "own_counts"};
+    "traces", "sel_out", "ac_build", "table_init", "end_pairs", "mark_ends", "ac_fix",
+    "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "own_counts"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -152,8 +153,9 @@ int apo_create(apo_ctx **out, int device) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->num_sms = sms > 0 ? sms : 1;
   int r = APO_OK;
+  // (per-device kernel attributes and occupancy; cheap to redo per context)
   if ((r = radix_sort_init()) != APO_OK || (r = suffix_init()) != APO_OK ||
-      (r = repeats_init(optin)) != APO_OK) {
+      (r = repeats_init(optin)) != APO_OK || (r = match_init(c->num_sms)) != APO_OK) {
     delete c;
     return r;
   }

@@ -222,6 +222,9 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
 
 // ---------------------------------------------------------------- greedy
 constexpr int kGT = 1024;
+constexpr int kGI = 4;                // candidates per thread per round
+constexpr int kGRound = kGT * kGI;    // 4096
+constexpr int kGListBytes = kGRound * 12;
 
 template <bool kSmem>
 __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
@@ -233,82 +236,131 @@ __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
   return (w >> (x & 31)) & 1u;
 }
 
+// One block runs Alg. 2's second loop.  Each round takes the next 4096
+// candidates (candidate base + i*1024 + tid for item i of thread tid), drops
+// those whose first or last position is already marked, compacts the rest in
+// candidate order, and warp 0 settles them one by one, marking accepted
+// intervals.  The accepted flags must be zero on entry.
 template <bool kSmem>
 __global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ cl,
                                                    const uint32_t *__restrict__ cs, uint32_t m,
                                                    uint32_t n, uint32_t *gbits, uint8_t *acc,
                                                    uint32_t *acc_count, uint32_t *err) {
-  extern __shared__ uint32_t sbits[];
-  __shared__ uint32_t s_l[kGT], s_s[kGT], s_k[kGT];
-  __shared__ uint32_t s_wc[32];
-  uint32_t *bits = kSmem ? sbits : gbits;
+  extern __shared__ __align__(16) uint32_t gsm[];
+  const uint32_t words = kSmem ? ((n + 31) / 32 + 3) & ~3u : 0;
+  uint32_t *bits = kSmem ? gsm : gbits;
+  uint32_t *sl = gsm + words, *ss = sl + kGRound, *sk = ss + kGRound;
+  __shared__ uint32_t s_cnt[kGI][32], s_off[kGI][32], s_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (kSmem) {
-    const uint32_t words = (n + 31) / 32;
-    for (uint32_t w = tid; w < words; w += kGT) sbits[w] = 0;
-  }
+  if (kSmem)
+    for (uint32_t w = tid; w < words; w += kGT) gsm[w] = 0;
   uint32_t nacc = 0;
-  uint32_t nl = 0, ns = 0;
-  if ((uint32_t)tid < m) {
-    nl = cl[tid];
-    ns = cs[tid];
+  uint32_t nl[kGI], ns[kGI];
+#pragma unroll
+  for (int i = 0; i < kGI; ++i) {
+    const uint32_t k = i * kGT + tid;
+    nl[i] = k < m ? cl[k] : 0u;
+    ns[i] = k < m ? cs[k] : 0u;
   }
   __syncthreads();
-  for (uint32_t base = 0; base < m; base += kGT) {
-    const uint32_t k = base + tid;
-    const bool valid = k < m;
-    const uint32_t l = nl, s = ns;
-    if (k + kGT < m) {  // prefetch the next round
-      nl = cl[k + kGT];
-      ns = cs[k + kGT];
-    }
-    bool surv = false;
-    if (valid) {
-      acc[k] = 0;
-      if (l == 0 || (uint64_t)s + l > n) {
-        atomicExch(err, kDevRange);
-      } else {
-        surv = !marked<kSmem>(bits, s) && !marked<kSmem>(bits, s + l - 1);
+  for (uint32_t base = 0; base < m; base += kGRound) {
+    uint32_t l[kGI], s[kGI], bal[kGI];
+    bool surv[kGI];
+#pragma unroll
+    for (int i = 0; i < kGI; ++i) {
+      l[i] = nl[i];
+      s[i] = ns[i];
+      const uint64_t kn = (uint64_t)base + kGRound + i * kGT + tid;  // prefetch the next round
+      if (kn < m) {
+        nl[i] = cl[kn];
+        ns[i] = cs[kn];
       }
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, surv);
-    if (lane == 0) s_wc[warp] = __popc(bal);
-    __syncthreads();
-    uint32_t off = 0, total = 0;
-    for (int w = 0; w < 32; ++w) {
-      const uint32_t c = s_wc[w];
-      off += w < warp ? c : 0;
-      total += c;
+#pragma unroll
+    for (int i = 0; i < kGI; ++i) {
+      const uint32_t k = base + i * kGT + tid;
+      surv[i] = false;
+      if (k < m) {
+        if (l[i] == 0 || (uint64_t)s[i] + l[i] > n)
+          atomicExch(err, kDevRange);
+        else
+          surv[i] = !marked<kSmem>(bits, s[i]) && !marked<kSmem>(bits, s[i] + l[i] - 1);
+      }
+      bal[i] = __ballot_sync(0xffffffffu, surv[i]);
+      if (lane == 0) s_cnt[i][warp] = __popc(bal[i]);
     }
-    if (surv) {
-      const uint32_t q = off + __popc(bal & lanemask_lt());
-      s_l[q] = l;
-      s_s[q] = s;
-      s_k[q] = k;
+    __syncthreads();
+    if (warp == 0) {  // survivor offsets in (item, warp) order = candidate order
+      uint32_t carry = 0;
+#pragma unroll
+      for (int i = 0; i < kGI; ++i) {
+        const uint32_t c = s_cnt[i][lane];
+        const uint32_t inc = warp_inclusive(c, OpSum());
+        s_off[i][lane] = carry + inc - c;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) s_total = carry;
+    }
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kGI; ++i) {
+      if (surv[i]) {
+        const uint32_t q = s_off[i][warp] + __popc(bal[i] & lt);
+        sl[q] = l[i];
+        ss[q] = s[i];
+        sk[q] = base + i * kGT + tid;
+      }
     }
     __syncthreads();
     if (warp == 0) {
-      for (uint32_t q = 0; q < total; ++q) {
-        const uint32_t ql = s_l[q], qs = s_s[q], qe = qs + ql - 1;
-        if (!marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe)) {
-          const uint32_t w0 = qs >> 5, w1 = qe >> 5;
+      // Settle the survivors 32 at a time: lane j holds survivor q0 + j.  A
+      // lane is blocked if its ends are marked by earlier batches, or if it
+      // overlaps an earlier lane of its batch that is accepted; the second
+      // part is resolved in lane order with one mask per lane.
+      const uint32_t total = s_total;
+      for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const bool have = q < total;
+        uint32_t qs = 0, qe = 0;
+        bool free = false;
+        if (have) {
+          qs = ss[q];
+          qe = qs + sl[q] - 1;
+          free = !marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe);
+        }
+        uint32_t ov = 0;  // earlier lanes whose interval meets this lane's
+        for (int j = 0; j < 31; ++j) {
+          const uint32_t js = __shfl_sync(0xffffffffu, qs, j);
+          const uint32_t je = __shfl_sync(0xffffffffu, qe, j);
+          if (j < lane && js <= qe && qs <= je) ov |= 1u << j;
+        }
+        const uint32_t freem = __ballot_sync(0xffffffffu, free);
+        uint32_t accm = 0;
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t ovj = __shfl_sync(0xffffffffu, ov, j);
+          if (((freem >> j) & 1u) && (ovj & accm) == 0) accm |= 1u << j;
+        }
+        if ((accm >> lane) & 1u) acc[sk[q]] = 1;
+        for (uint32_t am = accm; am; am &= am - 1) {  // mark accepted intervals, warp-wide
+          const int j = __ffs(am) - 1;
+          const uint32_t js = __shfl_sync(0xffffffffu, qs, j);
+          const uint32_t je = __shfl_sync(0xffffffffu, qe, j);
+          const uint32_t w0 = js >> 5, w1 = je >> 5;
           for (uint32_t w = w0 + lane; w <= w1; w += 32) {
             uint32_t msk = 0xffffffffu;
-            if (w == w0) msk &= 0xffffffffu << (qs & 31);
-            if (w == w1) msk &= 0xffffffffu >> (31 - (qe & 31));
-            bits[w] |= msk;
-          }
-          if (lane == 0) {
-            acc[s_k[q]] = 1;
-            ++nacc;
+            if (w == w0) msk &= 0xffffffffu << (js & 31);
+            if (w == w1) msk &= 0xffffffffu >> (31 - (je & 31));
+            atomicOr(&bits[w], msk);
           }
         }
+        nacc += __popc(accm);
         __syncwarp();
       }
     }
     __syncthreads();
   }
-  if (tid == 0) *acc_count = nacc;
+  if (tid == 0) *acc_count = nacc;  // lane 0 of warp 0 counted every batch
 }
 
 // Accepted candidates (compacted, in order) -> R and the keys of the
@@ -409,10 +461,13 @@ int copy_out(T *dst, const T *src, uint64_t count, uint64_t cap, bool *over, cud
 }  // namespace
 
 int repeats_init(int smem_optin) {
-  // static shared memory of k_greedy: 3 * 1024 + 32 words
-  g_greedy_smem_max = smem_optin - (3 * kGT + 64) * 4;
+  // k_greedy: dynamic = bitmap (in the shared-memory variant) + survivor list;
+  // static = 2 * 4 * 32 + 1 words
+  g_greedy_smem_max = smem_optin - 2048;
   APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     g_greedy_smem_max));
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kGListBytes));
   return APO_OK;
 }
 
@@ -520,19 +575,22 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   // greedy selection
   uint32_t K = 0;
   if (m) {
-    const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
+    const size_t bm_bytes = (size_t)((((n + 31) / 32) + 3) & ~3u) * 4;
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
-    if ((long long)bm_bytes <= g_greedy_smem_max) {
+    APO_CUDA_TRY(cudaMemsetAsync(acc, 0, m, s));
+    if ((long long)(bm_bytes + kGListBytes) <= g_greedy_smem_max) {
       {
         Launch lp_(c, kKGreedy, m, s);
-        k_greedy<true><<<1, kGT, bm_bytes, s>>>(cl, cs, m, n, nullptr, acc, misc + kMiscAccCount,
+        k_greedy<true><<<1, kGT, bm_bytes + kGListBytes, s>>>(cl, cs, m, n, nullptr, acc,
+                                                              misc + kMiscAccCount,
                                                 c->ps.err);
       }
     } else {
       APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, bm_bytes, s));
       {
         Launch lp_(c, kKGreedy, m, s);
-        k_greedy<false><<<1, kGT, 0, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount, c->ps.err);
+        k_greedy<false><<<1, kGT, kGListBytes, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount,
+                                                    c->ps.err);
       }
     }
     APO_CUDA_TRY(cudaGetLastError());
