@@ -13,10 +13,10 @@
 //
 // Build.  One cooperative kernel builds the trie level by level: at level d
 // every pattern longer than d inserts its (d+1)-th node into the goto hash
-// table (keyed by node << 32 | symbol, slots claimed with atomicCAS, ids from a
-// counter so that each level's nodes get a contiguous id range), while the
-// nodes of depth d get their failure link, output link and match total
-// (own pattern ends plus those down the output chain).  A bounded grid
+// table (keyed by node << 32 | symbol, slots claimed with atomicCAS; a node's
+// id is its slot), while the depth-d nodes get their failure link, output
+// link and match total (own pattern ends plus those down the output chain),
+// each computed by the pattern that created the node.  A bounded grid
 // barrier separates levels.
 //
 // Match.  The stream is cut into short chunks and each thread runs the
@@ -145,132 +145,138 @@ struct GridBarrier {
 
 // All blocks of a cooperative launch meet here.  Bounded: a block that waits
 // too long records kDevTimeout and leaves (the caller then stops).
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ void grid_sync(const GridBarrier &b, uint32_t *err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const uint32_t g0 = *(volatile uint32_t *)b.gen;
-    __threadfence();
+    const uint32_t g0 = ld_acquire(b.gen);
+    __threadfence();  // this block's writes before its arrival
     if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
       *(volatile uint32_t *)b.count = 0;
       __threadfence();
       atomicAdd(b.gen, 1u);
     } else {
       uint32_t spins = 0;
-      while (*(volatile uint32_t *)b.gen == g0) {
+      while (ld_acquire(b.gen) == g0) {
         if (++spins > kSpinLimit) {
           atomicExch(err, kDevTimeout);
           break;
         }
-        if (spins > 16) __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
 
+// A node's id is the goto-table slot of the edge that leads to it (every
+// node but the root has exactly one incoming edge); the root's id is the
+// table capacity.  Node arrays therefore hold capacity + 1 entries.
 struct BuildArgs {
   const uint32_t *psym;    // symbols of the pattern source tokens
   const uint32_t *pstart;  // pattern p = psym[pstart[p] .. pstart[p] + plen[p])
   const uint32_t *plen;
   uint32_t P;
   uint32_t maxlen;
+  uint32_t root;
   Table g;
-  uint32_t *cur;       // [P] node of each pattern at the current level
-  uint32_t *parent;    // [N]
-  uint32_t *nsym;      // [N] symbol on the edge into the node
-  uint32_t *fail;      // [N]
-  uint32_t *outl;      // [N]
-  uint32_t *own;       // [N] patterns ending exactly here
-  uint32_t *total;     // [N] matches reported in this state
+  uint32_t *cur[2];    // [P] node of each pattern at depth d (parity of d)
+  uint8_t *made[2];    // [P] 1 if the pattern created that node
+  uint32_t *parent;    // [nodes]
+  uint32_t *nsym;      // [nodes] symbol on the edge into the node
+  uint32_t *fail;      // [nodes]
+  uint32_t *outl;      // [nodes] nearest pattern end on the failure chain (root = none)
+  uint32_t *own;       // [nodes] patterns ending exactly here
+  uint32_t *total;     // [nodes] matches reported in this state
   uint32_t *end_node;  // [P]
-  uint32_t *node_ctr;
   GridBarrier bar;
   uint32_t *err;
 };
 
 constexpr int kBuildThreads = 512;
 
+// Level d: inserter p creates or finds its depth-(d+1) node; linker p, if
+// pattern p created its depth-d node one level earlier, computes that node's
+// failure link, output link and match total (all shallower nodes and all
+// depth-d nodes exist after the previous barrier).
 __global__ void __launch_bounds__(kBuildThreads) k_ac_build(BuildArgs a) {
-  // the first half of the grid inserts, the second half computes links
   const uint32_t half = gridDim.x * blockDim.x / 2;
   const uint32_t gt0 = blockIdx.x * blockDim.x + threadIdx.x;
   const bool inserter = gt0 < half;
   const uint32_t gt = inserter ? gt0 : gt0 - half;
-  const uint32_t nth = half;
-  uint32_t lo = 1, hi = 1;  // ids of the nodes of depth d
+  const uint32_t root = a.root;
   for (uint32_t d = 0; d <= a.maxlen; ++d) {
-    // (a) depth d+1 nodes of every pattern longer than d
-    for (uint32_t p = inserter ? gt : a.P; p < a.P; p += nth) {
-      if (d >= a.plen[p]) continue;
-      const uint32_t u = d ? a.cur[p] : 0u;
-      const uint32_t c = a.psym[a.pstart[p] + d];
-      const uint64_t key = ((uint64_t)u << 32) | c;
-      uint64_t slot = mix64(key) & a.g.mask;
-      uint32_t v = kNil;
-      for (uint64_t probe = 0; probe <= a.g.mask; ++probe) {
-        uint64_t *ek = a.g.keys + 2 * slot;
-        uint64_t cur = *(volatile uint64_t *)ek;
-        if (cur == kEmpty) {
-          cur = atomicCAS((unsigned long long *)ek, (unsigned long long)kEmpty,
-                          (unsigned long long)key);
-          if (cur == kEmpty) {  // this thread creates the node
-            v = atomicAdd(a.node_ctr, 1u) + 1u;
-            a.parent[v] = u;
-            a.nsym[v] = c;
-            __threadfence();
-            *(volatile uint64_t *)(ek + 1) = v;
-            break;
-          }
-        }
-        if (cur == key) {  // created by another thread of this level
-          uint32_t spins = 0;
-          while ((v = (uint32_t) * (volatile uint64_t *)(ek + 1)) == 0) {
-            if (++spins > kSpinLimit) {
-              atomicExch(a.err, kDevTimeout);
+    const int par = d & 1;
+    for (uint32_t p = gt; p < a.P; p += half) {
+      const uint32_t L = a.plen[p];
+      if (inserter) {
+        if (d >= L) continue;
+        const uint32_t u = d ? a.cur[par][p] : root;
+        const uint32_t c = a.psym[a.pstart[p] + d];
+        const uint64_t key = ((uint64_t)u << 32) | c;
+        uint64_t slot = mix64(key) & a.g.mask;
+        uint32_t v = kNil;
+        uint8_t made = 0;
+        for (uint64_t probe = 0; probe <= a.g.mask; ++probe) {
+          uint64_t *ek = a.g.keys + 2 * slot;
+          uint64_t cur = *(volatile uint64_t *)ek;
+          if (cur == kEmpty) {
+            cur = atomicCAS((unsigned long long *)ek, (unsigned long long)kEmpty,
+                            (unsigned long long)key);
+            if (cur == kEmpty) {  // this pattern creates the node
+              v = (uint32_t)slot;
+              made = 1;
+              ek[1] = v;
+              a.parent[v] = u;
+              a.nsym[v] = c;
               break;
             }
           }
-          __threadfence();
-          break;
-        }
-        slot = (slot + 1) & a.g.mask;
-      }
-      if (v == kNil || v == 0) {
-        atomicExch(a.err, kDevRange);
-        continue;
-      }
-      a.cur[p] = v;
-      if (d + 1 == a.plen[p]) {
-        a.end_node[p] = v;
-        atomicAdd(&a.own[v], 1u);
-      }
-    }
-    // (b) links of the depth-d nodes (all shallower nodes are complete)
-    for (uint32_t v = inserter ? hi : lo + gt; v < hi; v += nth) {
-      uint32_t f = 0;
-      if (d > 1) {
-        const uint32_t c = a.nsym[v];
-        uint32_t w = a.fail[a.parent[v]];
-        while (true) {
-          const uint32_t x = goto_lookup(a.g, w, c);
-          if (x != kNil) {
-            f = x;
+          if (cur == key) {
+            v = (uint32_t)slot;
             break;
           }
-          if (w == 0) break;
-          w = a.fail[w];
+          slot = (slot + 1) & a.g.mask;
         }
+        if (v == kNil) {
+          atomicExch(a.err, kDevRange);
+          continue;
+        }
+        a.cur[par ^ 1][p] = v;
+        a.made[par ^ 1][p] = made;
+        if (d + 1 == L) {
+          a.end_node[p] = v;
+          atomicAdd(&a.own[v], 1u);
+        }
+      } else {
+        if (d == 0 || d > L || !a.made[par][p]) continue;
+        const uint32_t v = a.cur[par][p];
+        uint32_t f = root;
+        if (d > 1) {
+          const uint32_t c = a.nsym[v];
+          uint32_t w = a.fail[a.parent[v]];
+          while (true) {
+            const uint32_t x = goto_lookup(a.g, w, c);
+            if (x != kNil) {
+              f = x;
+              break;
+            }
+            if (w == root) break;
+            w = a.fail[w];
+          }
+        }
+        a.fail[v] = f;
+        const uint32_t o = (f != root && a.own[f] != 0) ? f : a.outl[f];
+        a.outl[v] = o;
+        a.total[v] = a.own[v] + a.total[o];
       }
-      a.fail[v] = f;
-      const uint32_t o = (f != 0 && a.own[f] != 0) ? f : a.outl[f];
-      a.outl[v] = o;
-      a.total[v] = a.own[v] + a.total[o];
     }
     grid_sync(a.bar, a.err);
     if (*(volatile uint32_t *)a.err != kDevOk) return;
-    lo = hi;
-    hi = *(volatile uint32_t *)a.node_ctr + 1;
   }
 }
 
@@ -298,10 +304,11 @@ __global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint
 // ---------------------------------------------------------------- match
 __device__ __forceinline__ uint32_t ac_step(const Table &g, const uint32_t *__restrict__ fail,
                                             uint32_t state, uint32_t c) {
+  const uint32_t root = (uint32_t)(g.mask + 1);
   while (true) {
     const uint32_t nx = goto_lookup(g, state, c);
     if (nx != kNil) return nx;
-    if (state == 0) return 0;
+    if (state == root) return root;
     state = fail[state];
   }
 }
@@ -315,7 +322,7 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
   const uint64_t ce = min(n, cs + chunk);
-  uint32_t state = 0;
+  uint32_t state = (uint32_t)(g.mask + 1);  // root
   for (uint64_t x = cs; x < ce; ++x) {
     state = ac_step(g, fail, state, ssym[x]);
     state_out[x] = state;
@@ -402,12 +409,12 @@ __global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
                           const uint32_t *__restrict__ off, const uint32_t *__restrict__ own,
                           const uint32_t *__restrict__ outl, const uint32_t *__restrict__ end_first,
                           const uint32_t *__restrict__ evals, uint32_t *mend, uint32_t *mid,
-                          uint64_t cap) {
+                          uint64_t cap, uint32_t root) {
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     const uint32_t s0 = state[x];
     uint64_t o = off[x];
     uint32_t v = own[s0] != 0 ? s0 : outl[s0];
-    while (v != 0) {
+    while (v != root) {
       const uint32_t k0 = end_first[v], k1 = k0 + own[v];
       for (uint32_t k = k0; k < k1; ++k) {
         if (o < cap) {
@@ -445,9 +452,9 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   while (tbl < 2 * (total_tokens + 1)) tbl <<= 1;
   uint64_t dct = 1;
   while (dct < 2 * (extent + 1)) dct <<= 1;
-  const uint64_t N = total_tokens + 1;
+  const uint64_t N = tbl + 1;
   const uint64_t chunks = n / 32 + 2;
-  return tbl * 16 + dct * 12 + N * 4 * 8 + P * 48 + (extent + n) * 4 + n * 8 + chunks * 8 +
+  return tbl * 16 + dct * 12 + N * 4 * 8 + P * 64 + (extent + n) * 4 + n * 8 + chunks * 8 +
          64 * 256;
 }
 
@@ -490,9 +497,11 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     return APO_EINVAL;
   }
   APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent)));
-  const uint64_t N = total + 1;  // node bound (root included)
+  const uint64_t N0 = total + 1;  // node bound (root included)
   uint64_t tbl = 1;
-  while (tbl < 2 * N) tbl <<= 1;
+  while (tbl < 2 * N0) tbl <<= 1;
+  const uint64_t N = tbl + 1;     // node ids are goto slots; the root is `tbl`
+  const uint32_t root = (uint32_t)tbl;
 
   Table g;
   g.keys = c->arena.take_n<uint64_t>(2 * tbl);
@@ -505,7 +514,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *own = c->arena.take_n<uint32_t>(N);
   uint32_t *mtotal = c->arena.take_n<uint32_t>(N);
   uint32_t *end_first = c->arena.take_n<uint32_t>(N);
-  uint32_t *cur = c->arena.take_n<uint32_t>(P);
+  uint32_t *cur = c->arena.take_n<uint32_t>(2 * (size_t)P);
+  uint8_t *made = c->arena.take_n<uint8_t>(2 * (size_t)P);
   uint32_t *end_node = c->arena.take_n<uint32_t>(P);
   SortBuffers b;
   b.keys[0] = c->arena.take_n<uint64_t>(P);
@@ -513,7 +523,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   b.vals[0] = c->arena.take_n<uint32_t>(P);
   b.vals[1] = c->arena.take_n<uint32_t>(P);
   if (!g.keys || (pp->pat_off && !pbuf) || !parent || !nsym || !fail || !outl || !own ||
-      !mtotal || !end_first || !cur || !end_node || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
+      !mtotal || !end_first || !cur || !made || !end_node || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
       !b.vals[1]) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
@@ -534,9 +544,13 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     k_table_init<<<grid_for(tbl, 256, sms), 256, 0, s>>>(g.keys, tbl);
   }
   APO_CUDA_TRY(cudaMemsetAsync(own, 0, N * sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(outl, 0, sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(mtotal, 0, sizeof(uint32_t), s));
+  {  // the root fails to itself, has no output link and reports nothing
+    const uint32_t rv[3] = {root, root, 0u};
+    APO_CUDA_TRY(cudaMemcpyAsync(fail + root, &rv[0], 4, cudaMemcpyHostToDevice, s));
+    APO_CUDA_TRY(cudaMemcpyAsync(outl + root, &rv[1], 4, cudaMemcpyHostToDevice, s));
+    APO_CUDA_TRY(cudaMemcpyAsync(mtotal + root, &rv[2], 4, cudaMemcpyHostToDevice, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+  }
 
   // symbols of the pattern source and of the stream
   const uint32_t *psym = nullptr, *ssym = nullptr;
@@ -581,7 +595,11 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.P = P;
     a.maxlen = (uint32_t)maxlen;
     a.g = g;
-    a.cur = cur;
+    a.root = root;
+    a.cur[0] = cur;
+    a.cur[1] = cur + P;
+    a.made[0] = made;
+    a.made[1] = made + P;
     a.parent = parent;
     a.nsym = nsym;
     a.fail = fail;
@@ -589,7 +607,6 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.own = own;
     a.total = mtotal;
     a.end_node = end_node;
-    a.node_ctr = misc + kMiscMatchCount;
     a.bar.count = misc + kMiscMatchCount + 1;
     a.bar.gen = misc + kMiscMatchCount + 2;
     a.err = c->ps.err;
@@ -604,14 +621,12 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     Launch lp_(c, kKEndPairs, P, s);
     k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, b.keys[0], b.vals[0]);
   }
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMatchCount, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   APO_TRY(check_device_error(c, s));
-  const uint32_t nodes = c->host_pinned[0] + 1;
   b.cur = 0;
   {
     int places[8];
-    const int np = plan_digits(0, bits_for(nodes), places, 0);
+    const int np = plan_digits(0, bits_for(root), places, 0);
     APO_TRY(radix_sort_pairs(c, b, P, places, np, s));
   }
   const uint64_t *ek = b.keys[b.cur];
@@ -667,7 +682,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   if (total_m) {
     Launch lp_(c, kKAcFill, n, s);
     k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, own, outl, end_first, ev,
-                                                    match_end, match_id, cap);
+                                                    match_end, match_id, cap, root);
   }
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaStreamSynchronize(s));

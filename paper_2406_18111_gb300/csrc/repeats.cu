@@ -313,33 +313,37 @@ __global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ 
       }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && s_total) {
       // Settle the survivors 32 at a time: lane j holds survivor q0 + j.  A
-      // lane is blocked if its ends are marked by earlier batches, or if it
-      // overlaps an earlier lane of its batch that is accepted; the second
-      // part is resolved in lane order with one mask per lane.
+      // lane is out if its ends are marked by an earlier batch; among the
+      // rest, a lane is accepted once no earlier lane that overlaps it is
+      // accepted or undecided, and rejected once one that overlaps it is
+      // accepted (the batch's greedy order, settled a few ballots at a time).
       const uint32_t total = s_total;
       for (uint32_t q0 = 0; q0 < total; q0 += 32) {
         const uint32_t q = q0 + lane;
-        const bool have = q < total;
+        const uint32_t nb = min(32u, total - q0);
         uint32_t qs = 0, qe = 0;
         bool free = false;
-        if (have) {
+        if (q < total) {
           qs = ss[q];
           qe = qs + sl[q] - 1;
           free = !marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe);
         }
-        uint32_t ov = 0;  // earlier lanes whose interval meets this lane's
-        for (int j = 0; j < 31; ++j) {
-          const uint32_t js = __shfl_sync(0xffffffffu, qs, j);
-          const uint32_t je = __shfl_sync(0xffffffffu, qe, j);
-          if (j < lane && js <= qe && qs <= je) ov |= 1u << j;
+        uint32_t ov = 0;  // earlier lanes of the batch whose interval meets this lane's
+        for (uint32_t j = 0; j < nb; ++j) {
+          const uint32_t js = ss[q0 + j];
+          const uint32_t je = js + sl[q0 + j] - 1;
+          if (j < (uint32_t)lane && js <= qe && qs <= je) ov |= 1u << j;
         }
-        const uint32_t freem = __ballot_sync(0xffffffffu, free);
-        uint32_t accm = 0;
-        for (int j = 0; j < 32; ++j) {
-          const uint32_t ovj = __shfl_sync(0xffffffffu, ov, j);
-          if (((freem >> j) & 1u) && (ovj & accm) == 0) accm |= 1u << j;
+        uint32_t und = __ballot_sync(0xffffffffu, free), accm = 0;
+        while (und) {
+          const bool mine = (und >> lane) & 1u;
+          const uint32_t take = __ballot_sync(0xffffffffu, mine && (ov & (und | accm)) == 0);
+          accm |= take;
+          und &= ~take;
+          const uint32_t drop = __ballot_sync(0xffffffffu, ((und >> lane) & 1u) && (ov & accm) != 0);
+          und &= ~drop;
         }
         if ((accm >> lane) & 1u) acc[sk[q]] = 1;
         for (uint32_t am = accm; am; am &= am - 1) {  // mark accepted intervals, warp-wide
