@@ -144,6 +144,12 @@ typedef struct {
   /* HOST array of 4 counts, written before the call returns:
    * [0] candidates, [1] accepted intervals, [2] traces, [3] doubling rounds. */
   uint64_t *counts;
+  /* Batched calls only (HOST, n_windows + 1 entries each, or NULL): where
+   * each window's candidates, selected intervals and traces start in the
+   * arrays above. */
+  uint64_t *cand_off;
+  uint64_t *sel_off;
+  uint64_t *trace_off;
 } apo_repeats_out;
 
 /* Run Alg. 2 on one window.  Synchronises `stream` (the suffix sorting loop
@@ -155,6 +161,34 @@ typedef struct {
  * n = 0 or 1 gives no candidates. */
 int apo_find_repeats(apo_ctx *ctx, const apo_window *window, const apo_repeats_params *params,
                      apo_repeats_out *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched repeat finding -- Alg. 2 applied to many independent windows in one
+ * call (Alg. 1 analyses many history slices asynchronously, Sec. 4.2 and 4.4).
+ *
+ * The windows are concatenated in `tokens`; window w is tokens[win_off[w] ..
+ * win_off[w+1]).  Every window gets exactly the results apo_find_repeats
+ * would give it alone: the suffix sorting, the candidates and the greedy
+ * selection never mix windows.  Outputs are concatenated window by window:
+ * sa/lcp (optional, sum of window lengths entries, values relative to the
+ * window start), candidates, selected intervals and traces (starts relative
+ * to their window, sel_trace relative to the window's first trace), with
+ * out->cand_off / sel_off / trace_off (HOST) giving each window's range.
+ * cand_id values are SA indices in the concatenated array (they order a
+ * window's sub-strings; only equality and order within a window matter).
+ * Synchronises `stream`.  Capacities that always suffice: cand_cap = 2 *
+ * total tokens, sel_cap = trace_cap = total tokens / min_len.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t n_windows;       /* W >= 1 */
+  const void *tokens;       /* device, win_off[W] tokens */
+  int token_bytes;          /* 4 or 8 */
+  const uint64_t *win_off;  /* HOST [W+1], win_off[0] = 0, non-decreasing; each window
+                               holds at most 2^31 - 1 tokens, all together < 2^31 */
+} apo_windows;
+
+int apo_find_repeats_batched(apo_ctx *ctx, const apo_windows *windows,
+                             const apo_repeats_params *params, apo_repeats_out *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * Candidate matching -- Sec. 4.3: the candidate traces are ingested into a

@@ -28,7 +28,8 @@ _NAMES = {0: "APO_OK", -1: "APO_EINVAL", -2: "APO_ENOMEM", -3: "APO_ECAPACITY", 
 
 # Every symbol include/apo.h declares.
 EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_hash_tasks",
-           "apo_find_repeats", "apo_match_candidates", "apo_profile_enable", "apo_profile_reset",
+           "apo_find_repeats", "apo_find_repeats_batched", "apo_match_candidates",
+           "apo_profile_enable", "apo_profile_reset",
            "apo_profile_read", "apo_greedy_select_noalloc")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
@@ -62,7 +63,12 @@ class apo_repeats_out(ctypes.Structure):
     _fields_ = [("sa", _P), ("lcp", _P), ("cand_len", _P), ("cand_id", _P), ("cand_start", _P),
                 ("cand_accepted", _P), ("cand_cap", _U64), ("sel_start", _P), ("sel_len", _P),
                 ("sel_trace", _P), ("sel_cap", _U64), ("trace_len", _P), ("trace_start", _P),
-                ("trace_cap", _U64), ("counts", _P)]
+                ("trace_cap", _U64), ("counts", _P), ("cand_off", _P), ("sel_off", _P),
+                ("trace_off", _P)]
+
+
+class apo_windows(ctypes.Structure):
+    _fields_ = [("n_windows", _U64), ("tokens", _P), ("token_bytes", ctypes.c_int), ("win_off", _P)]
 
 
 class apo_patterns(ctypes.Structure):
@@ -90,6 +96,9 @@ def lib():
         L.apo_find_repeats.argtypes = [_P, ctypes.POINTER(apo_window),
                                        ctypes.POINTER(apo_repeats_params),
                                        ctypes.POINTER(apo_repeats_out), _P]
+        L.apo_find_repeats_batched.argtypes = [_P, ctypes.POINTER(apo_windows),
+                                               ctypes.POINTER(apo_repeats_params),
+                                               ctypes.POINTER(apo_repeats_out), _P]
         L.apo_match_candidates.argtypes = [_P, ctypes.POINTER(apo_patterns), _P, _U64, _P, _P, _U64,
                                            ctypes.POINTER(_U64), _P]
         L.apo_profile_enable.argtypes = [_P, ctypes.c_int]
@@ -147,6 +156,29 @@ class Repeats:
     rounds: int
 
 
+@dataclass
+class BatchRepeats:
+    """Outputs of a batched call, concatenated window by window (starts are
+    window-relative, sel_trace indexes the window's traces); the *_off host
+    arrays give each window's range."""
+    sa: object
+    lcp: object
+    cand_len: object
+    cand_id: object
+    cand_start: object
+    cand_accepted: object
+    sel_start: object
+    sel_len: object
+    sel_trace: object
+    trace_len: object
+    trace_start: object
+    rounds: int
+    win_off: np.ndarray
+    cand_off: np.ndarray
+    sel_off: np.ndarray
+    trace_off: np.ndarray
+
+
 class Apo:
     """A library context bound to one CUDA device."""
 
@@ -200,7 +232,7 @@ class Apo:
         counts = (ctypes.c_uint64 * 4)()
         o = apo_repeats_out(_ptr(sa), _ptr(lcp), _ptr(cl), _ptr(ci), _ptr(cs), _ptr(ca),
                             M if stages else 0, _ptr(ss), _ptr(sl), _ptr(st), K, _ptr(tl), _ptr(ts), K,
-                            ctypes.cast(counts, _P))
+                            ctypes.cast(counts, _P), None, None, None)
         w = apo_window(n, _ptr(tokens), _token_bytes(tokens))
         p = apo_repeats_params(int(min_len), 0)
         _check(lib().apo_find_repeats(self._h, ctypes.byref(w), ctypes.byref(p), ctypes.byref(o),
@@ -211,6 +243,41 @@ class Apo:
             return None if x is None else x[:c]
         return Repeats(cut(sa, n), cut(lcp, n), cut(cl, m), cut(ci, m), cut(cs, m), cut(ca, m),
                        ss[:k], sl[:k], st[:k], tl[:t], ts[:t], rounds)
+
+    def find_repeats_batched(self, tokens, win_off, min_len: int, stages: bool = True,
+                             stream=None) -> "BatchRepeats":
+        """Alg. 2 on many windows at once: tokens holds the windows back to
+        back, window w = tokens[win_off[w]:win_off[w+1]] (win_off on the host)."""
+        import torch
+        wo = np.ascontiguousarray(np.asarray(win_off, dtype=np.uint64))
+        W = wo.shape[0] - 1
+        n = int(tokens.shape[0])
+        dev = tokens.device
+        u32 = torch.int32
+        M = max(1, 2 * n)
+        K = max(1, n // max(1, min_len))
+        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
+        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
+        cl = torch.empty(M, dtype=u32, device=dev) if stages else None
+        ci = torch.empty(M, dtype=u32, device=dev) if stages else None
+        cs = torch.empty(M, dtype=u32, device=dev) if stages else None
+        ca = torch.empty(M, dtype=torch.uint8, device=dev) if stages else None
+        ss, sl, st, tl, ts = (torch.empty(K, dtype=u32, device=dev) for _ in range(5))
+        counts = (ctypes.c_uint64 * 4)()
+        offs = [np.zeros(W + 1, dtype=np.uint64) for _ in range(3)]
+        o = apo_repeats_out(_ptr(sa), _ptr(lcp), _ptr(cl), _ptr(ci), _ptr(cs), _ptr(ca),
+                            M if stages else 0, _ptr(ss), _ptr(sl), _ptr(st), K, _ptr(tl), _ptr(ts), K,
+                            ctypes.cast(counts, _P), *[x.ctypes.data_as(_P).value for x in offs])
+        w = apo_windows(W, _ptr(tokens), _token_bytes(tokens), wo.ctypes.data_as(_P).value)
+        p = apo_repeats_params(int(min_len), 0)
+        _check(lib().apo_find_repeats_batched(self._h, ctypes.byref(w), ctypes.byref(p), ctypes.byref(o),
+                                              _stream_handle(stream)))
+        m, k, t, rounds = (int(x) for x in counts)
+
+        def cut(x, c):
+            return None if x is None else x[:c]
+        return BatchRepeats(cut(sa, n), cut(lcp, n), cut(cl, m), cut(ci, m), cut(cs, m), cut(ca, m),
+                            ss[:k], sl[:k], st[:k], tl[:t], ts[:t], rounds, wo, *offs)
 
     # -------------------------------------------------------------- Sec. 4.3
     def match_candidates(self, pat_tokens, pat_off, stream_tokens, cap: int | None = None,

@@ -173,13 +173,34 @@ void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_d
 int plan_digits(int lo, int hi, int *shifts, int start);
 int radix_sort_init();
 
+// ---------------------------------------------------------------- windows
+// Several windows analysed at once are concatenated; position i belongs to
+// window wid[i], which ends at wend[i] (exclusive, in concatenated
+// coordinates).  Null arrays mean one window spanning all positions.
+struct Windows {
+  uint32_t count = 1;
+  const uint32_t *wid = nullptr;    // [N]
+  const uint32_t *wend = nullptr;   // [N]
+  const uint64_t *off_host = nullptr;  // [count + 1] window offsets (host)
+  const uint32_t *off_dev = nullptr;   // [count + 1] window offsets (device)
+  uint32_t max_len = 0;             // longest window
+};
+
+__device__ __forceinline__ uint32_t win_end(const Windows &w, uint32_t i, uint32_t n) {
+  return w.wend ? w.wend[i] : n;
+}
+__device__ __forceinline__ uint32_t win_id(const Windows &w, uint32_t i) {
+  return w.wid ? w.wid[i] : 0u;
+}
+
 // ---------------------------------------------------------------- suffix array
 struct SuffixState {
-  uint32_t n;
-  uint32_t *sa;
+  uint32_t n;        // positions over all windows
+  uint32_t *sa;      // global SA: window w's suffixes occupy [off[w], off[w+1])
   uint32_t *rank;
   uint32_t **snaps;  // host array of device pointers: rank after level k
   int levels;        // number of snapshots written
+  Windows win;
 };
 int build_suffix_array(apo_ctx *c, const void *tokens, int token_bytes, uint32_t n,
                        SuffixState &st, int max_levels, uint32_t *rounds_out, cudaStream_t s);
@@ -187,9 +208,15 @@ int build_lcp(apo_ctx *c, const void *tokens, int token_bytes, const SuffixState
               uint32_t *lcp, cudaStream_t s);
 
 // ---------------------------------------------------------------- repeats
+// Per-window outputs of a batched call (HOST offset arrays, count + 1 each).
+struct BatchOffsets {
+  uint64_t *cand_off = nullptr;
+  uint64_t *sel_off = nullptr;
+  uint64_t *trace_off = nullptr;
+};
 int find_repeats_from_sa(apo_ctx *c, const void *tokens, int token_bytes, const SuffixState &st,
                          const uint32_t *lcp, uint32_t min_len, apo_repeats_out *out,
-                         cudaStream_t s);
+                         const BatchOffsets *boff, cudaStream_t s);
 
 // ---------------------------------------------------------------- hashing
 void launch_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *out, cudaStream_t s);

@@ -3,13 +3,14 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "apo_internal.cuh"
 
 namespace apo {
 
 size_t suffix_workspace_bytes(uint64_t n);
-size_t repeats_workspace_bytes(uint64_t n);
+size_t repeats_workspace_bytes(uint64_t n, uint64_t windows);
 size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t cap);
 int suffix_init();
 int repeats_init(int smem_optin);
@@ -206,34 +207,65 @@ int apo_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *tokens_out, void *s
   return APO_OK;
 }
 
-int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *p,
-                     apo_repeats_out *out, void *stream) {
-  if (!c || !w || !p || !out || !out->counts) {
-    set_error("apo_find_repeats: null argument");
-    return APO_EINVAL;
+}  // extern "C"
+
+namespace apo {
+namespace drv {
+
+__global__ void k_fill_windows(const uint32_t *__restrict__ off, uint32_t count, uint32_t *wid,
+                               uint32_t *wend) {
+  for (uint32_t w = blockIdx.x; w < count; w += gridDim.x) {
+    const uint32_t a = off[w], b = off[w + 1];
+    for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+      wid[i] = w;
+      wend[i] = b;
+    }
   }
+}
+
+__global__ void k_sa_relative(const uint32_t *__restrict__ sa, uint32_t n, const uint32_t *__restrict__ wid,
+                              const uint32_t *__restrict__ off, uint32_t *__restrict__ out) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    out[k] = sa[k] - off[wid[sa[k]]];
+}
+
+// Shared driver of apo_find_repeats (one window) and apo_find_repeats_batched.
+int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total,
+                        const uint64_t *win_off, uint32_t nwin, const apo_repeats_params *p,
+                        apo_repeats_out *out, cudaStream_t s) {
   for (int k = 0; k < 4; ++k) out->counts[k] = 0;
-  if (w->token_bytes != 4 && w->token_bytes != 8) {
-    set_error("apo_find_repeats: token_bytes must be 4 or 8");
+  if (tb != 4 && tb != 8) {
+    set_error("find_repeats: token_bytes must be 4 or 8");
     return APO_EINVAL;
   }
   if (p->min_len == 0 || p->flags != 0) {
-    set_error("apo_find_repeats: min_len must be >= 1 and flags 0");
+    set_error("find_repeats: min_len must be >= 1 and flags 0");
     return APO_EINVAL;
   }
-  if (w->n > 0x7fffffffull) {
-    set_error("apo_find_repeats: a window holds at most 2^31 - 1 tokens");
+  if (total > 0x7fffffffull) {
+    set_error("find_repeats: at most 2^31 - 1 tokens per call");
     return APO_EINVAL;
   }
-  if (w->n > 0 && !w->tokens) {
-    set_error("apo_find_repeats: null tokens");
+  if (total > 0 && !tokens) {
+    set_error("find_repeats: null tokens");
     return APO_EINVAL;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const uint32_t n = (uint32_t)w->n;
-  if (n == 0) return APO_OK;
+  const uint32_t n = (uint32_t)total;
+  BatchOffsets boff;
+  boff.cand_off = out->cand_off;
+  boff.sel_off = out->sel_off;
+  boff.trace_off = out->trace_off;
+  if (n == 0) {
+    for (uint32_t w = 0; w <= nwin; ++w) {
+      if (boff.cand_off) boff.cand_off[w] = 0;
+      if (boff.sel_off) boff.sel_off[w] = 0;
+      if (boff.trace_off) boff.trace_off[w] = 0;
+    }
+    return APO_OK;
+  }
   APO_CUDA_TRY(cudaSetDevice(c->device));
-  APO_TRY(c->arena.reserve(suffix_workspace_bytes(n) + repeats_workspace_bytes(n) + (size_t)n * 16));
+  APO_TRY(c->arena.reserve(suffix_workspace_bytes(n) + repeats_workspace_bytes(n, nwin) +
+                           (size_t)n * 24 + (size_t)(nwin + 1) * 4));
   SuffixState st;
   st.n = n;
   st.sa = c->arena.take_n<uint32_t>(n);
@@ -242,24 +274,98 @@ int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *
   uint32_t *snap_base = c->arena.take_n<uint32_t>((size_t)max_levels * n);
   uint32_t *lcp = c->arena.take_n<uint32_t>(n);
   if (!st.sa || !st.rank || !snap_base || !lcp) {
-    set_error("apo_find_repeats: workspace too small");
+    set_error("find_repeats: workspace too small");
     return APO_ENOMEM;
+  }
+  st.win.count = nwin;
+  if (nwin > 1) {
+    uint32_t *wid = c->arena.take_n<uint32_t>(n);
+    uint32_t *wend = c->arena.take_n<uint32_t>(n);
+    uint32_t *off = c->arena.take_n<uint32_t>(nwin + 1);
+    if (!wid || !wend || !off) return APO_ENOMEM;
+    std::vector<uint32_t> h(nwin + 1);
+    uint32_t maxlen = 0;
+    for (uint32_t w = 0; w <= nwin; ++w) {
+      h[w] = (uint32_t)win_off[w];
+      if (w) maxlen = std::max(maxlen, h[w] - h[w - 1]);
+    }
+    APO_CUDA_TRY(cudaMemcpyAsync(off, h.data(), (nwin + 1) * 4, cudaMemcpyHostToDevice, s));
+    {
+      Launch lp_(c, kKInitKeys, n, s);
+      k_fill_windows<<<std::min<uint32_t>(nwin, 4096), 256, 0, s>>>(off, nwin, wid, wend);
+    }
+    APO_CUDA_TRY(cudaStreamSynchronize(s));  // h goes out of scope
+    st.win.wid = wid;
+    st.win.wend = wend;
+    st.win.off_host = win_off;
+    st.win.off_dev = off;
+    st.win.max_len = maxlen;
+  } else {
+    st.win.max_len = n;
   }
   uint32_t *snaps[40];
   for (int k = 0; k < max_levels; ++k) snaps[k] = snap_base + (size_t)k * n;
   st.snaps = snaps;
   uint32_t rounds = 0;
-  APO_TRY(build_suffix_array(c, w->tokens, w->token_bytes, n, st, max_levels, &rounds, s));
-  APO_TRY(build_lcp(c, w->tokens, w->token_bytes, st, lcp, s));
-  if (out->sa) APO_CUDA_TRY(cudaMemcpyAsync(out->sa, st.sa, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  APO_TRY(build_suffix_array(c, tokens, tb, n, st, max_levels, &rounds, s));
+  APO_TRY(build_lcp(c, tokens, tb, st, lcp, s));
+  if (out->sa) {
+    if (nwin > 1) {
+      Launch lp_(c, kKSelOut, n, s);
+      k_sa_relative<<<std::max(1, std::min(ceil_div(n, 256), c->num_sms * 16)), 256, 0, s>>>(
+          st.sa, n, st.win.wid, st.win.off_dev, out->sa);
+    } else {
+      APO_CUDA_TRY(cudaMemcpyAsync(out->sa, st.sa, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+  }
   if (out->lcp) APO_CUDA_TRY(cudaMemcpyAsync(out->lcp, lcp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-  const int r = find_repeats_from_sa(c, w->tokens, w->token_bytes, st, lcp, p->min_len, out, s);
+  const int r = find_repeats_from_sa(c, tokens, tb, st, lcp, p->min_len, out, &boff, s);
   out->counts[3] = rounds;
   if (r == APO_OK) {
     APO_CUDA_TRY(cudaStreamSynchronize(s));
     return check_device_error(c, s);
   }
   return r;
+}
+
+}  // namespace drv
+}  // namespace apo
+
+extern "C" {
+
+int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *p,
+                     apo_repeats_out *out, void *stream) {
+  if (!c || !w || !p || !out || !out->counts) {
+    set_error("apo_find_repeats: null argument");
+    return APO_EINVAL;
+  }
+  const uint64_t off[2] = {0, w->n};
+  apo_repeats_out o = *out;
+  o.cand_off = o.sel_off = o.trace_off = nullptr;
+  const int r = drv::find_repeats_driver(c, w->tokens, w->token_bytes, w->n, off, 1, p, &o,
+                                    static_cast<cudaStream_t>(stream));
+  for (int k = 0; k < 4; ++k) out->counts[k] = o.counts[k];
+  return r;
+}
+
+int apo_find_repeats_batched(apo_ctx *c, const apo_windows *ws, const apo_repeats_params *p,
+                             apo_repeats_out *out, void *stream) {
+  if (!c || !ws || !p || !out || !out->counts || !ws->win_off) {
+    set_error("apo_find_repeats_batched: null argument");
+    return APO_EINVAL;
+  }
+  if (ws->n_windows == 0 || ws->n_windows > 0x7fffffffull || ws->win_off[0] != 0) {
+    set_error("apo_find_repeats_batched: need 1 <= n_windows and win_off[0] == 0");
+    return APO_EINVAL;
+  }
+  for (uint64_t w = 0; w < ws->n_windows; ++w) {
+    if (ws->win_off[w + 1] < ws->win_off[w]) {
+      set_error("apo_find_repeats_batched: win_off must be non-decreasing");
+      return APO_EINVAL;
+    }
+  }
+  return drv::find_repeats_driver(c, ws->tokens, ws->token_bytes, ws->win_off[ws->n_windows], ws->win_off,
+                             (uint32_t)ws->n_windows, p, out, static_cast<cudaStream_t>(stream));
 }
 
 int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,

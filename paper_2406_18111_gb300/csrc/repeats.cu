@@ -29,6 +29,7 @@
 //              id) changes; selected intervals are re-sorted by start.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "apo_internal.cuh"
 #include "device_util.cuh"
@@ -98,10 +99,11 @@ __device__ long long prev_less(const MinTree &T, uint32_t k, uint32_t l, uint32_
 }
 
 // Alg. 2 first loop.  Each kept pair writes two (key, start) entries with
-// key = ((lmax - l) << bi) | id.
+// key = (window << (bl + bi)) | ((lmax - l) << bi) | id.  Pairs that straddle
+// two windows have LCP 0 and are dropped with the other short candidates.
 __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ lcp,
-                           uint32_t n, uint32_t min_len, MinTree T, int bi, uint32_t lmax,
-                           uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                           uint32_t n, uint32_t min_len, MinTree T, int bi, int bl, uint32_t lmax,
+                           Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
                            uint32_t *count, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -129,7 +131,7 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
     uint64_t key = 0;
     if (ok) {
       const long long j = prev_less(T, k, l, err);
-      key = ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1);
+      key = ((uint64_t)win_id(W, a) << (bl + bi)) | ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1);
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, ok);
     if (bal == 0) continue;
@@ -208,23 +210,21 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, uint32_t
 
 __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
                               const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                              int bi, uint32_t lmax, uint32_t *__restrict__ cl,
+                              int bi, int bl, uint32_t lmax, uint32_t *__restrict__ cl,
                               uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
     const uint64_t key = keys[k];
-    cl[q] = lmax - (uint32_t)(key >> bi);
+    cl[q] = lmax - (uint32_t)((key >> bi) & lmax);
     cid[q] = (uint32_t)(key & idmask);
     cs[q] = vals[k];
   }
 }
 
 // ---------------------------------------------------------------- greedy
-constexpr int kGT = 1024;
-constexpr int kGI = 4;                // candidates per thread per round
-constexpr int kGRound = kGT * kGI;    // 4096
-constexpr int kGListBytes = kGRound * 12;
+constexpr int kGI = 4;  // candidates per thread per round
+constexpr int glist_bytes(int threads) { return threads * kGI * 12; }
 
 template <bool kSmem>
 __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
@@ -236,24 +236,40 @@ __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
   return (w >> (x & 31)) & 1u;
 }
 
-// One block runs Alg. 2's second loop.  Each round takes the next 4096
-// candidates (candidate base + i*1024 + tid for item i of thread tid), drops
-// those whose first or last position is already marked, compacts the rest in
-// candidate order, and warp 0 settles them one by one, marking accepted
-// intervals.  The accepted flags must be zero on entry.
-template <bool kSmem>
-__global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ cl,
-                                                   const uint32_t *__restrict__ cs, uint32_t m,
-                                                   uint32_t n, uint32_t *gbits, uint8_t *acc,
-                                                   uint32_t *acc_count, uint32_t *err) {
+// One block per window runs Alg. 2's second loop over the window's
+// candidates [cand_off[w], cand_off[w+1]).  Each round takes the next kT * 4
+// candidates (base + i*kT + tid for item i of thread tid), drops those whose
+// first or last position is already marked, compacts the rest in candidate
+// order, and warp 0 settles them 32 at a time, marking accepted intervals.
+// The accepted flags must be zero on entry.  The mark bitmap covers the
+// window in shared memory (positions relative to the window start), or all
+// positions in global memory (zeroed by the caller).
+template <int kT, bool kSmem>
+__global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
+                                               const uint32_t *__restrict__ cs,
+                                               const uint32_t *__restrict__ cand_off, uint32_t m,
+                                               const uint32_t *__restrict__ woff, uint32_t n,
+                                               uint32_t *gbits, uint8_t *acc, uint32_t *acc_count,
+                                               uint32_t *err) {
+  constexpr int kGT = kT;
+  constexpr int kGRound = kT * kGI;
   extern __shared__ __align__(16) uint32_t gsm[];
-  const uint32_t words = kSmem ? ((n + 31) / 32 + 3) & ~3u : 0;
+  const uint32_t w = blockIdx.x;
+  const uint32_t cb = cand_off ? cand_off[w] : 0u, ce = cand_off ? cand_off[w + 1] : m;
+  const uint32_t ws = woff ? woff[w] : 0u, we = woff ? woff[w + 1] : n;
+  const uint32_t shift = kSmem ? ws : 0u;  // bitmap coordinate = position - shift
+  const uint32_t words = kSmem ? ((we - ws + 31) / 32 + 3) & ~3u : 0;
   uint32_t *bits = kSmem ? gsm : gbits;
+  if (ce <= cb) return;
+  cl += cb;
+  cs += cb;
+  acc += cb;
+  m = ce - cb;
   uint32_t *sl = gsm + words, *ss = sl + kGRound, *sk = ss + kGRound;
   __shared__ uint32_t s_cnt[kGI][32], s_off[kGI][32], s_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (kSmem)
-    for (uint32_t w = tid; w < words; w += kGT) gsm[w] = 0;
+    for (uint32_t x = tid; x < words; x += kGT) gsm[x] = 0;
   uint32_t nacc = 0;
   uint32_t nl[kGI], ns[kGI];
 #pragma unroll
@@ -281,10 +297,12 @@ __global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ 
       const uint32_t k = base + i * kGT + tid;
       surv[i] = false;
       if (k < m) {
-        if (l[i] == 0 || (uint64_t)s[i] + l[i] > n)
+        if (l[i] == 0 || s[i] < ws || (uint64_t)s[i] + l[i] > we) {
           atomicExch(err, kDevRange);
-        else
+        } else {
+          s[i] -= shift;
           surv[i] = !marked<kSmem>(bits, s[i]) && !marked<kSmem>(bits, s[i] + l[i] - 1);
+        }
       }
       bal[i] = __ballot_sync(0xffffffffu, surv[i]);
       if (lane == 0) s_cnt[i][warp] = __popc(bal[i]);
@@ -294,7 +312,7 @@ __global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ 
       uint32_t carry = 0;
 #pragma unroll
       for (int i = 0; i < kGI; ++i) {
-        const uint32_t c = s_cnt[i][lane];
+        const uint32_t c = lane < kGT / 32 ? s_cnt[i][lane] : 0u;
         const uint32_t inc = warp_inclusive(c, OpSum());
         s_off[i][lane] = carry + inc - c;
         carry += __shfl_sync(0xffffffffu, inc, 31);
@@ -364,7 +382,7 @@ __global__ void __launch_bounds__(kGT, 1) k_greedy(const uint32_t *__restrict__ 
     }
     __syncthreads();
   }
-  if (tid == 0) *acc_count = nacc;  // lane 0 of warp 0 counted every batch
+  if (tid == 0) atomicAdd(acc_count, nacc);  // lane 0 of warp 0 counted every batch
 }
 
 // Accepted candidates (compacted, in order) -> R and the keys of the
@@ -422,7 +440,32 @@ __global__ void k_sel_out(const uint64_t *__restrict__ keys, const uint32_t *__r
   }
 }
 
-int g_greedy_smem_max = 0;  // dynamic shared memory available to k_greedy<true>
+// First index of each window in a list sorted by window (the window of entry
+// k is the window of position pos[k]); out[count] = m.
+__global__ void k_window_bounds(const uint32_t *__restrict__ pos, uint32_t m, Windows W,
+                                uint32_t *__restrict__ out) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= W.count; w += gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = m;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (win_id(W, pos[mid]) < w) lo = mid + 1; else hi = mid;
+    }
+    out[w] = lo;
+  }
+}
+
+// Window-relative outputs: starts minus the window start, trace indices
+// minus the window's first trace.
+__global__ void k_relativize(uint32_t *__restrict__ start, uint32_t *__restrict__ trace, uint32_t k,
+                             Windows W, const uint32_t *__restrict__ trace_off) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < k; q += gridDim.x * blockDim.x) {
+    const uint32_t w = win_id(W, start[q]);
+    if (trace) trace[q] -= trace_off[w];
+    start[q] -= W.off_dev ? W.off_dev[w] : 0u;
+  }
+}
+
+int g_greedy_smem_max = 0;  // dynamic shared memory available to k_greedy<*, true>
 
 inline int grid_for(uint64_t n, int threads, int sms) {
   long long b = (long long)((n + threads - 1) / threads);
@@ -465,37 +508,51 @@ int copy_out(T *dst, const T *src, uint64_t count, uint64_t cap, bool *over, cud
 }  // namespace
 
 int repeats_init(int smem_optin) {
-  // k_greedy: dynamic = bitmap (in the shared-memory variant) + survivor list;
+  // k_greedy: dynamic = bitmap (shared-memory variants) + survivor list;
   // static = 2 * 4 * 32 + 1 words
   g_greedy_smem_max = smem_optin - 2048;
-  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     g_greedy_smem_max));
-  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kGListBytes));
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<1024, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    glist_bytes(1024)));
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    g_greedy_smem_max));
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_greedy<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    glist_bytes(256)));
   return APO_OK;
 }
 
-size_t repeats_workspace_bytes(uint64_t n) {
+size_t repeats_workspace_bytes(uint64_t n, uint64_t windows) {
   const uint64_t M = n ? 2 * (n - 1) : 0;
   return (size_t)M * (2 * 8 + 2 * 4)  // sort buffers
          + (size_t)M * (4 * 3 + 4 + 1)  // candidate arrays, compaction indices, flags
          + (size_t)n * 20                // R and the selected intervals (5 arrays of <= n)
-         + (size_t)n * 4 / 16 + (size_t)n / 8 + 64 * 256;
+         + (size_t)n * 4 / 16 + (size_t)n / 8 + (size_t)(windows + 1) * 12 + 64 * 256;
 }
 
 int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixState &st,
                          const uint32_t *lcp, uint32_t min_len, apo_repeats_out *out,
-                         cudaStream_t s) {
+                         const BatchOffsets *boff, cudaStream_t s) {
   (void)tokens;
   (void)tb;
   const uint32_t n = st.n;
+  const Windows &W = st.win;
   uint64_t *counts = out->counts;
   counts[0] = counts[1] = counts[2] = 0;
+  auto zero_offsets = [&]() {
+    if (!boff) return;
+    for (uint32_t w = 0; w <= W.count; ++w) {
+      if (boff->cand_off) boff->cand_off[w] = 0;
+      if (boff->sel_off) boff->sel_off[w] = 0;
+      if (boff->trace_off) boff->trace_off[w] = 0;
+    }
+  };
+  zero_offsets();
   if (n < 2) return APO_OK;
   uint32_t *misc = c->ps.counters + kCtrMisc;
   const int g = grid_for(n, 256, c->num_sms);
 
-  // bits of the (length, id) key
+  // bits of the (window, length, id) key
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMaxLen, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKMax, n, s);
@@ -507,6 +564,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   const uint32_t lmax = (uint32_t)((1ull << bl) - 1);
   const int bi = std::max(1, bits_for(n - 1));
   const int bs = bi;
+  const int bw = W.count > 1 ? bits_for(W.count - 1) : 0;
+  if (bw + bl + bi > 64) {
+    set_error("repeats: windows, lengths and ids do not fit a 64-bit sort key");
+    return APO_EINVAL;
+  }
 
   // 32-ary min-tree over LCP
   MinTree T;
@@ -544,15 +606,18 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   uint32_t *cs = c->arena.take_n<uint32_t>(M);
   uint8_t *acc = c->arena.take_n<uint8_t>(M);
   uint32_t *gbits = c->arena.take_n<uint32_t>((n + 31) / 32 + 1);
+  uint32_t *cand_off = c->arena.take_n<uint32_t>(W.count + 1);
+  uint32_t *sel_off = c->arena.take_n<uint32_t>(W.count + 1);
+  uint32_t *trace_off = c->arena.take_n<uint32_t>(W.count + 1);
   if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !sel || !cl || !cid || !cs || !acc ||
-      !gbits) {
+      !gbits || !cand_off || !sel_off || !trace_off) {
     set_error("repeats: workspace too small");
     return APO_ENOMEM;
   }
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCandCount, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKCandGen, n, s);
-    k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, lmax, b.keys[0], b.vals[0],
+    k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, bl, lmax, W, b.keys[0], b.vals[0],
                                  misc + kMiscCandCount, c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
@@ -563,7 +628,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     int places[16];
     int np = plan_digits(0, bs, places, 0);
     for (int p = 0; p < np; ++p) places[p] |= 256;  // start digits come from the value
-    np = plan_digits(0, bi + bl, places, np);
+    np = plan_digits(0, bw + bl + bi, places, np);
     b.cur = 0;
     APO_TRY(radix_sort_pairs(c, b, mraw, places, np, s));
     PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
@@ -571,31 +636,42 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
     {
       Launch lp_(c, kKCandGather, m, s);
-      k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur],
-                                                                 b.vals[b.cur], bi, lmax, cl, cid, cs);
+      k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur], b.vals[b.cur],
+                                                                 bi, bl, lmax, cl, cid, cs);
     }
   }
 
-  // greedy selection
+  // greedy selection, one block per window
   uint32_t K = 0;
   if (m) {
-    const size_t bm_bytes = (size_t)((((n + 31) / 32) + 3) & ~3u) * 4;
+    {
+      Launch lp_(c, kKSlices, W.count + 1, s);
+      k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(cs, m, W, cand_off);
+    }
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     APO_CUDA_TRY(cudaMemsetAsync(acc, 0, m, s));
-    if ((long long)(bm_bytes + kGListBytes) <= g_greedy_smem_max) {
-      {
-        Launch lp_(c, kKGreedy, m, s);
-        k_greedy<true><<<1, kGT, bm_bytes + kGListBytes, s>>>(cl, cs, m, n, nullptr, acc,
-                                                              misc + kMiscAccCount,
-                                                c->ps.err);
-      }
-    } else {
-      APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, bm_bytes, s));
-      {
-        Launch lp_(c, kKGreedy, m, s);
-        k_greedy<false><<<1, kGT, kGListBytes, s>>>(cl, cs, m, n, gbits, acc, misc + kMiscAccCount,
-                                                    c->ps.err);
-      }
+    const uint32_t maxw = W.count > 1 ? W.max_len : n;
+    const size_t bm_bytes = (size_t)((((maxw + 31) / 32) + 3) & ~3u) * 4;
+    const bool big = W.count == 1;  // one window: one wide block
+    const size_t list = glist_bytes(big ? 1024 : 256);
+    const uint32_t *coff = W.count > 1 ? cand_off : nullptr;
+    const bool smem = (long long)(bm_bytes + list) <= g_greedy_smem_max;
+    if (!smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, (size_t)((n + 31) / 32) * 4, s));
+    {
+      Launch lp_(c, kKGreedy, m, s);
+      if (big && smem)
+        k_greedy<1024, true><<<1, 1024, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n, nullptr,
+                                                              acc, misc + kMiscAccCount, c->ps.err);
+      else if (big)
+        k_greedy<1024, false><<<1, 1024, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
+                                                     misc + kMiscAccCount, c->ps.err);
+      else if (smem)
+        k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n,
+                                                                  nullptr, acc, misc + kMiscAccCount,
+                                                                  c->ps.err);
+      else
+        k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
+                                                        misc + kMiscAccCount, c->ps.err);
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
@@ -628,11 +704,28 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     APO_TRY(radix_sort_pairs(c, sb, K, places, np, s));
     {
       Launch lp_(c, kKSelOut, K, s);
-      k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K,
-                                                             ss, sl, sq);
+      k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K, ss,
+                                                             sl, sq);
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscTraceCount, &Tn, s));
+    if (W.count > 1) {  // per-window offsets, then window-relative values
+      {
+        Launch lp_(c, kKSlices, W.count + 1, s);
+        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ss, K, W, sel_off);
+        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ts, Tn, W, trace_off);
+      }
+      {
+        Launch lp_(c, kKSelOut, K, s);
+        k_relativize<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(ss, sq, K, W, trace_off);
+        k_relativize<<<grid_for(Tn, 256, c->num_sms), 256, 0, s>>>(ts, nullptr, Tn, W, trace_off);
+      }
+    }
+  }
+  if (W.count > 1 && m && out->cand_start) {
+    // window-relative candidate starts for the caller (greedy is done with them)
+    Launch lp_(c, kKSelOut, m, s);
+    k_relativize<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(cs, nullptr, m, W, trace_off);
   }
 
   bool over = false;
@@ -645,6 +738,26 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_TRY(copy_out(out->sel_trace, sq, K, out->sel_cap, &over, s));
   APO_TRY(copy_out(out->trace_len, tl, Tn, out->trace_cap, &over, s));
   APO_TRY(copy_out(out->trace_start, ts, Tn, out->trace_cap, &over, s));
+  if (boff && W.count > 1) {
+    std::vector<uint32_t> h(3 * (size_t)(W.count + 1), 0);
+    if (m) APO_CUDA_TRY(cudaMemcpyAsync(h.data(), cand_off, (W.count + 1) * 4, cudaMemcpyDeviceToHost, s));
+    if (K) {
+      APO_CUDA_TRY(cudaMemcpyAsync(h.data() + (W.count + 1), sel_off, (W.count + 1) * 4,
+                                   cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaMemcpyAsync(h.data() + 2 * (W.count + 1), trace_off, (W.count + 1) * 4,
+                                   cudaMemcpyDeviceToHost, s));
+    }
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    for (uint32_t w = 0; w <= W.count; ++w) {
+      if (boff->cand_off) boff->cand_off[w] = h[w];
+      if (boff->sel_off) boff->sel_off[w] = h[(W.count + 1) + w];
+      if (boff->trace_off) boff->trace_off[w] = h[2 * (W.count + 1) + w];
+    }
+  } else if (boff) {
+    if (boff->cand_off) boff->cand_off[1] = m;
+    if (boff->sel_off) boff->sel_off[1] = K;
+    if (boff->trace_off) boff->trace_off[1] = Tn;
+  }
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   APO_TRY(check_device_error(c, s));
   counts[0] = m;

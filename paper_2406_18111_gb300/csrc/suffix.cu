@@ -149,27 +149,42 @@ __global__ void __launch_bounds__(kRT) k_refresh(
   }
 }
 
-// key = (rank[i] << 32) | (i + h < n ? rank[i + h] + 1 : 0), value = i.
+// key = (rank[i] << 32) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
+// value = i.
 __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ rank,
-                       uint32_t n, uint64_t h, uint64_t *__restrict__ keys,
+                       uint32_t n, uint64_t h, Windows W, uint64_t *__restrict__ keys,
                        uint32_t *__restrict__ vals) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < A; k += gridDim.x * blockDim.x) {
     const uint32_t i = act[k];
     const uint64_t j = i + h;
-    const uint32_t r2 = j < n ? rank[j] + 1u : 0u;
+    const uint32_t r2 = j < win_end(W, i, n) ? rank[j] + 1u : 0u;
     keys[k] = ((uint64_t)rank[i] << 32) | r2;
     vals[k] = i;
   }
 }
 
-__global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, uint32_t *__restrict__ phi) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    phi[sa[k]] = k ? sa[k - 1] : kNone;
+// Batched first round: key = (window << 32) | rank of the token among all
+// tokens, so that suffixes of different windows never share a group.
+__global__ void k_wkeys(const uint32_t *__restrict__ rank, Windows W, uint32_t n,
+                        uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    keys[i] = ((uint64_t)win_id(W, i) << 32) | rank[i];
+    vals[i] = i;
+  }
+}
+
+__global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, Windows W,
+                      uint32_t *__restrict__ phi) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t i = sa[k];
+    phi[i] = (k && win_id(W, sa[k - 1]) == win_id(W, i)) ? sa[k - 1] : kNone;
+  }
 }
 
 template <class T>
 __device__ __forceinline__ bool long_match(const T *__restrict__ S, uint32_t n, uint32_t i,
                                            uint32_t j, uint32_t &l) {
+  // i and j lie in the same window, which ends at n
   uint32_t steps = 0;
   while (i + (uint64_t)l < n && j + (uint64_t)l < n && S[i + l] == S[j + l]) {
     ++l;
@@ -181,8 +196,9 @@ __device__ __forceinline__ bool long_match(const T *__restrict__ S, uint32_t n, 
 // PLCP[i] = lcp(i, Phi[i]) over chunks of consecutive i, kRChunk per thread.
 constexpr int kPChunk = 16;
 template <class T>
-__global__ void k_plcp(const T *__restrict__ S, uint32_t n, const uint32_t *__restrict__ phi,
-                       const uint32_t *__restrict__ snaps, int levels, uint32_t *__restrict__ plcp) {
+__global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W,
+                       const uint32_t *__restrict__ phi, const uint32_t *__restrict__ snaps,
+                       int levels, uint32_t *__restrict__ plcp) {
   const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPChunk;
   if (i0 >= n) return;
   const uint32_t iend = (i0 + kPChunk) < (uint64_t)n ? (uint32_t)(i0 + kPChunk) : n;
@@ -194,11 +210,13 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, const uint32_t *__re
       l = 0;
       continue;
     }
-    if (long_match(S, n, i, j, l)) {
+    if (i > i0 && win_id(W, i) != win_id(W, i - 1)) l = 0;  // a new window starts
+    const uint32_t we = win_end(W, i, n);
+    if (long_match(S, we, i, j, l)) {
       // lift: level lev ranks are equal iff the next 2^lev tokens are equal
       for (int lev = levels - 1; lev >= 0; --lev) {
         const uint64_t a = (uint64_t)i + l, b = (uint64_t)j + l;
-        if (a < n && b < n && snaps[(size_t)lev * n + a] == snaps[(size_t)lev * n + b])
+        if (a < we && b < we && snaps[(size_t)lev * n + a] == snaps[(size_t)lev * n + b])
           l += 1u << lev;
       }
     }
@@ -208,9 +226,9 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, const uint32_t *__re
 }
 
 __global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ plcp,
-                           uint32_t n, uint32_t *__restrict__ lcp) {
+                           uint32_t n, Windows W, uint32_t *__restrict__ lcp) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    lcp[k] = k + 1 < n ? plcp[sa[k + 1]] : 0u;
+    lcp[k] = (k + 1 < n && win_id(W, sa[k + 1]) == win_id(W, sa[k])) ? plcp[sa[k + 1]] : 0u;
 }
 
 inline int grid_for(uint64_t n, int threads, int sms) {
@@ -292,6 +310,19 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   uint32_t A = 0;
   APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, st.sa, st.rank, act[0], pos[0], n,
                   &A, s));
+  if (st.win.count > 1) {
+    // group by (window, token): re-sort by the window id over the token ranks
+    {
+      Launch lp_(c, kKInitKeys, n, s);
+      k_wkeys<<<g, 256, 0, s>>>(st.rank, st.win, n, b.keys[0], b.vals[0]);
+    }
+    b.cur = 0;
+    np = plan_digits(0, bits_for(n - 1), places, 0);
+    np = plan_digits(32, 32 + bits_for(st.win.count - 1), places, np);
+    APO_TRY(radix_sort_pairs(c, b, n, places, np, s));
+    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, st.sa, st.rank, act[0], pos[0], n,
+                    &A, s));
+  }
   APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[0], st.rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   st.levels = 1;
   int cur = 0;
@@ -305,8 +336,8 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     b.cur = 0;
     {
       Launch lp_(c, kKPack, A, s);
-      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, b.keys[0],
-                                                            b.vals[0]);
+      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, st.win,
+                                                            b.keys[0], b.vals[0]);
     }
     np = plan_digits(0, minor_bits, places, 0);
     np = plan_digits(32, 32 + major_bits, places, np);
@@ -338,24 +369,26 @@ int build_lcp(apo_ctx *c, const void *tokens, int tb, const SuffixState &st, uin
   const int g = grid_for(n, 256, c->num_sms);
   {
     Launch lp_(c, kKPhi, n, s);
-    k_phi<<<g, 256, 0, s>>>(st.sa, n, phi);
+    k_phi<<<g, 256, 0, s>>>(st.sa, n, st.win, phi);
   }
   const int pb = ceil_div(ceil_div(n, kPChunk), 128);
   if (tb == 4)
     {
       Launch lp_(c, kKPlcp, n, s);
-      k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, phi, st.snaps[0],
+      k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, st.win, phi,
+                                          st.snaps[0],
                                           st.levels, plcp);
     }
   else
     {
       Launch lp_(c, kKPlcp, n, s);
-      k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, phi, st.snaps[0],
+      k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, st.win, phi,
+                                          st.snaps[0],
                                           st.levels, plcp);
     }
   {
     Launch lp_(c, kKLcpPerm, n, s);
-    k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, lcp);
+    k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, st.win, lcp);
   }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;

@@ -266,3 +266,66 @@ def test_match_traces_slice_form(apo):
     oe, oi = oracle.match(pt, off, tok)
     assert len(oe) > 0
     assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
+
+
+# ---------------------------------------------------------------- batched form
+def _window_slice(res, w, name, off_name):
+    from paper_2406_18111_gb300 import as_u32
+    off = getattr(res, off_name)
+    a = getattr(res, name)
+    x = a[int(off[w]):int(off[w + 1])]
+    return x.cpu().numpy() if name == "cand_accepted" else as_u32(x)
+
+
+def _check_batch_against(res, wins, per_window):
+    from paper_2406_18111_gb300 import as_u32
+    for w, S in enumerate(wins):
+        o = per_window(w, S)
+        a, b = int(res.win_off[w]), int(res.win_off[w + 1])
+        assert np.array_equal(as_u32(res.sa[a:b]), o.sa), ("sa", w)
+        assert np.array_equal(as_u32(res.lcp[a:b]), o.lcp), ("lcp", w)
+        for f in ("cand_len", "cand_start", "cand_accepted"):
+            want = o.accepted if f == "cand_accepted" else getattr(o, f)
+            assert np.array_equal(_window_slice(res, w, f, "cand_off"), want), (f, w)
+        for f in ("sel_start", "sel_len", "sel_trace"):
+            assert np.array_equal(_window_slice(res, w, f, "sel_off"), getattr(o, f)), (f, w)
+        for f in ("trace_len", "trace_start"):
+            assert np.array_equal(_window_slice(res, w, f, "trace_off"), getattr(o, f)), (f, w)
+
+
+def _concat(wins):
+    off = np.zeros(len(wins) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in wins])
+    return np.concatenate(wins).astype(np.uint32) if len(wins) else np.zeros(0, np.uint32), off
+
+
+def test_batched_config3_vs_oracle(apo):
+    toks, off, periods = W.config3_windows(24)
+    wins = [toks[int(off[w]):int(off[w + 1])] for w in range(24)]
+    wins += [np.zeros(0, np.uint32), np.array([7], np.uint32), np.array([3, 3, 3, 3, 3, 3], np.uint32)]
+    cat, o = _concat(wins)
+    res = apo.find_repeats_batched(tokens_dev(cat, 4), o, 5)
+    _check_batch_against(res, wins, lambda w, S: oracle.find_repeats(np.asarray(S, np.uint64), 5))
+
+
+def test_batched_equals_plain_and_u64(apo):
+    """Each window's bytes are the same alone (plain call) and in the batch."""
+    from paper_2406_18111_gb300 import as_u32
+    wins = [oracle.hash_tasks(W.config2_tasks(3000 + 977 * k, seed=20 + k)) for k in range(5)]
+    cat = np.concatenate(wins)
+    off = np.zeros(len(wins) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in wins])
+    res = apo.find_repeats_batched(tokens_dev(cat, 8), off, 5)
+
+    class Plain:
+        pass
+
+    def plain(w, S):
+        r = apo.find_repeats(tokens_dev(S, 8), 5)
+        p = Plain()
+        for f in FIELDS:
+            setattr(p, f, as_u32(getattr(r, f)))
+        p.accepted = p.cand_accepted = r.cand_accepted.cpu().numpy()
+        return p
+    _check_batch_against(res, wins, plain)
+    _check_batch_against(res, wins, lambda w, S: oracle.find_repeats(S, 5))
