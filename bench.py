@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="window", choices=["window", "batched"],
+                    help="window: the full path on one 2^20-task window (default); batched: "
+                         "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
+    ap.add_argument("--windows", type=int, default=512)
     return ap.parse_args()
 
 
@@ -178,11 +182,98 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_batched(args, rank, world, local):
+    """512 windows of log-uniform length 1,024..262,144 (period U{3..5000},
+    5% noise over 1,000 tokens): SA + LCP + Alg. 2 repeats for all of them in
+    one batched call, against one call per window (plain)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    toks, off, _ = W.config3_windows(args.windows, seed0=3 + 100000 * rank)
+    t = torch.from_numpy(toks.view(np.int32)).to(dev)
+    total = int(off[-1])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        r = apo.find_repeats_batched(t, off, MIN_LEN, stages=False)
+    torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    clocks = Clocks(local)
+    l0 = sum(v[0] for v in apo.profile_read().values())
+    ms = timed(lambda: apo.find_repeats_batched(t, off, MIN_LEN, stages=False), args.steps)
+    n_launch = sum(v[0] for v in apo.profile_read().values()) - l0
+    apo.profile_reset()
+    apo.profile(True)
+    ms_prof = timed(lambda: apo.find_repeats_batched(t, off, MIN_LEN, stages=False), args.steps)
+    prof = apo.profile_read()
+    apo.profile(False)
+
+    def plain():
+        for w in range(args.windows):
+            a, b = int(off[w]), int(off[w + 1])
+            apo.find_repeats(t[a:b], MIN_LEN, stages=False)
+    plain_steps = max(1, min(3, args.steps))
+    ms_plain = timed(plain, plain_steps)
+    clk = clocks.stop()
+    peak, peak_kind = peaks()
+    name, (la, kms, units) = max(prof.items(), key=lambda kv: kv[1][1])
+    bpu = BYTES_PER_UNIT.get(name)
+    roof = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+            "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof, "traffic": None}
+    if bpu is not None and kms > 0:
+        ach = bpu * units / (kms / 1e3) / 1e9
+        roof.update({"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": bpu * units / la,
+                     "ms_per_launch": kms / la})
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": total * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched: {args.windows} windows, log-uniform 1,024..262,144 tokens, "
+                                   "periods U{3..5000}, 5% noise; SA+LCP+repeats (min_len 5)",
+                       "n_tokens": total, "windows": args.windows, "min_len": MIN_LEN,
+                       "l2": "flushed between steps"},
+            "plain": {"value": total / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
+                      "form": "one apo_find_repeats call per window, same stream", "steps": plain_steps},
+            "batched_over_plain": ms_plain / ms,
+            "gpu_launches": n_launch, "roofline": roof, "clocks": clk, "kernels": kernels}))
+
+
 def main():
     args = parse()
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        import torch
+        torch.cuda.set_device(local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        import __graft_entry__
+        if rank == 0:
+            __graft_entry__.build()
+        if world > 1:
+            torch.distributed.barrier()
+        return run_batched(args, rank, world, local)
     import numpy as np
     import torch
     torch.cuda.set_device(local)
