@@ -63,10 +63,13 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
+    ap.add_argument("--duration", type=float, default=3.0, help="served: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served: mean requests per second")
+    ap.add_argument("--lanes", type=int, default=2, help="served: batches in flight")
     return ap.parse_args()
 
 
@@ -257,12 +260,65 @@ def run_batched(args, rank, world, local):
             "gpu_launches": n_launch, "roofline": roof, "clocks": clk, "kernels": kernels}))
 
 
+def run_served(args, rank, world, local):
+    """Poisson analysis requests (mean `rate`/s for `duration` s, window
+    lengths log-uniform 4,096..2^20 tokens, periodic content with 5% noise)
+    submitted in real time to a continuous-batching server; p50/p99 latency
+    from submission to results and tokens/s served."""
+    import threading
+
+    import numpy as np
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Server
+    t_arr, L, P = W.served_requests(args.duration, args.rate, seed=5 + rank)
+    pool_n = 96  # distinct windows, replayed by the arrivals (content does not change the timing model)
+    pool = [W.served_window(k, int(L[k]), int(P[k])) for k in range(min(pool_n, len(L)))]
+    reqs = [pool[k % len(pool)] for k in range(len(t_arr))]
+    srv = Server(local, min_len=MIN_LEN, token_bytes=4, max_batch_tokens=1 << 24, max_batch_windows=256,
+                 lanes=args.lanes)
+    for k in range(min(8, len(pool))):  # warm the lanes
+        srv.wait(srv.submit(pool[k]))
+    clocks = Clocks(local)
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for k, S in enumerate(reqs):
+            delay = t_arr[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = srv.submit(S)
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = [srv.wait(i) for i in ids]
+    clk = clocks.stop()
+    srv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
+    tokens = sum(r.n for r in res)
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    bw = np.array([r.batch_windows for r in res])
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": tokens / span, "unit": UNIT, "n_gpus": world,
+            "steps": len(res), "warmup": 8, "ms_per_step": float(np.mean(lat)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served: Poisson {args.rate}/s for {args.duration} s, windows log-uniform "
+                                   "4,096..2^20 tokens, periods U{3..5000}, 5% noise; SA+LCP+repeats "
+                                   "(min_len 5), continuous batching",
+                       "requests": len(res), "offered_tokens_per_s": tokens / args.duration,
+                       "lanes": args.lanes, "max_batch_tokens": 1 << 24},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch_windows": float(bw.mean()), "clocks": clk}))
+
+
 def main():
     args = parse()
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload == "batched":
+    if args.workload in ("batched", "served"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -273,6 +329,8 @@ def main():
             __graft_entry__.build()
         if world > 1:
             torch.distributed.barrier()
+        if args.workload == "served":
+            return run_served(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch

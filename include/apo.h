@@ -44,7 +44,8 @@ typedef enum {
   APO_ECAPACITY = -3,  /* an output array is too small; the needed count is still written */
   APO_ECUDA = -4,      /* a CUDA runtime call failed */
   APO_ETIMEOUT = -5,   /* a bounded device-side wait gave up (the results are invalid) */
-  APO_EDEVICE = -6     /* a kernel detected an inconsistency (the results are invalid) */
+  APO_EDEVICE = -6,    /* a kernel detected an inconsistency (the results are invalid) */
+  APO_EAGAIN = -7      /* not ready yet (a served request still in flight) */
 } apo_status;
 
 typedef struct apo_ctx apo_ctx;
@@ -189,6 +190,58 @@ typedef struct {
 
 int apo_find_repeats_batched(apo_ctx *ctx, const apo_windows *windows,
                              const apo_repeats_params *params, apo_repeats_out *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Served repeat finding -- Alg. 1 launches an asynchronous FindRepeats for
+ * each history slice while the application keeps issuing tasks, and ingests
+ * each result when it completes (Sec. 4.2, 4.3).  A server accepts such
+ * analysis requests at any time and batches them continuously: each of its
+ * `lanes` (a context and a stream of its own) repeatedly takes the requests
+ * that are waiting, in arrival order, up to max_batch_tokens tokens (the
+ * admission budget: a batch's device footprint grows with its tokens) and
+ * max_batch_windows requests, runs apo_find_repeats_batched on them and
+ * publishes each request's results.  Batches of different lanes overlap on
+ * the device; requests that arrive meanwhile join the next batch a lane forms.
+ * A request's results are the ones apo_find_repeats gives its window alone.
+ * ---------------------------------------------------------------------- */
+typedef struct apo_server apo_server;
+
+typedef struct {
+  uint32_t min_len;            /* as apo_repeats_params */
+  int token_bytes;             /* 4 or 8 */
+  uint64_t max_batch_tokens;   /* admission budget per batch (a larger request runs alone) */
+  uint32_t max_batch_windows;  /* most requests per batch */
+  uint32_t lanes;              /* batches in flight at once, >= 1 */
+} apo_server_config;
+
+typedef struct {
+  int status;                  /* APO_OK or the batch's error */
+  uint64_t n;                  /* tokens of the request */
+  uint64_t n_selected, n_traces;
+  const uint32_t *sel_start;   /* HOST, owned by the server until apo_server_release */
+  const uint32_t *sel_len;
+  const uint32_t *sel_trace;
+  const uint32_t *trace_len;
+  const uint32_t *trace_start;
+  double t_submit, t_start, t_done;  /* seconds on the server's steady clock */
+  uint64_t batch_windows;      /* requests in the batch that served it */
+} apo_request_result;
+
+/* Start a server on `device` with cfg->lanes worker threads. */
+int apo_server_create(apo_server **srv, int device, const apo_server_config *cfg);
+/* Queue a request; `tokens` (HOST, n tokens) is copied before the call
+ * returns.  *id identifies the request. */
+int apo_server_submit(apo_server *srv, const void *tokens, uint64_t n, uint64_t *id);
+/* APO_OK and *out filled if request `id` is done, APO_EAGAIN if not yet. */
+int apo_server_poll(apo_server *srv, uint64_t id, apo_request_result *out);
+/* Block until request `id` is done, then as apo_server_poll. */
+int apo_server_wait(apo_server *srv, uint64_t id, apo_request_result *out);
+/* Drop a finished request's results (its pointers become invalid). */
+int apo_server_release(apo_server *srv, uint64_t id);
+/* Seconds on the server's steady clock (the clock of the t_* fields). */
+double apo_server_now(apo_server *srv);
+/* Finish the queued requests, stop the lanes and free everything. */
+int apo_server_destroy(apo_server *srv);
 
 /* ------------------------------------------------------------------------
  * Candidate matching -- Sec. 4.3: the candidate traces are ingested into a

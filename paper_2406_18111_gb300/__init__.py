@@ -23,14 +23,17 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libapo.so")
 
 APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECAPACITY, APO_ECUDA, APO_ETIMEOUT, APO_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+APO_EAGAIN = -7
 _NAMES = {0: "APO_OK", -1: "APO_EINVAL", -2: "APO_ENOMEM", -3: "APO_ECAPACITY", -4: "APO_ECUDA",
-          -5: "APO_ETIMEOUT", -6: "APO_EDEVICE"}
+          -5: "APO_ETIMEOUT", -6: "APO_EDEVICE", -7: "APO_EAGAIN"}
 
 # Every symbol include/apo.h declares.
 EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_hash_tasks",
            "apo_find_repeats", "apo_find_repeats_batched", "apo_match_candidates",
            "apo_profile_enable", "apo_profile_reset",
-           "apo_profile_read", "apo_greedy_select_noalloc")
+           "apo_profile_read", "apo_greedy_select_noalloc", "apo_server_create", "apo_server_submit",
+           "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
+           "apo_server_destroy")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -65,6 +68,18 @@ class apo_repeats_out(ctypes.Structure):
                 ("sel_trace", _P), ("sel_cap", _U64), ("trace_len", _P), ("trace_start", _P),
                 ("trace_cap", _U64), ("counts", _P), ("cand_off", _P), ("sel_off", _P),
                 ("trace_off", _P)]
+
+
+class apo_server_config(ctypes.Structure):
+    _fields_ = [("min_len", _U32), ("token_bytes", ctypes.c_int), ("max_batch_tokens", _U64),
+                ("max_batch_windows", _U32), ("lanes", _U32)]
+
+
+class apo_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n", _U64), ("n_selected", _U64), ("n_traces", _U64),
+                ("sel_start", _P), ("sel_len", _P), ("sel_trace", _P), ("trace_len", _P),
+                ("trace_start", _P), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batch_windows", _U64)]
 
 
 class apo_windows(ctypes.Structure):
@@ -107,9 +122,17 @@ def lib():
                                        ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(_U64)]
         L.apo_greedy_select_noalloc.argtypes = [_P, _P, _U64, _U64, _P, _P, _P]
+        L.apo_server_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(apo_server_config)]
+        L.apo_server_submit.argtypes = [_P, _P, _U64, ctypes.POINTER(_U64)]
+        L.apo_server_poll.argtypes = [_P, _U64, ctypes.POINTER(apo_request_result)]
+        L.apo_server_wait.argtypes = [_P, _U64, ctypes.POINTER(apo_request_result)]
+        L.apo_server_release.argtypes = [_P, _U64]
+        L.apo_server_now.argtypes = [_P]
+        L.apo_server_destroy.argtypes = [_P]
         for f in EXPORTS:
-            if f not in ("apo_last_error",):
+            if f not in ("apo_last_error", "apo_server_now"):
                 getattr(L, f).restype = ctypes.c_int
+        L.apo_server_now.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -329,6 +352,84 @@ class Apo:
                 out[name.value.decode()] = (int(la.value), float(ms.value), int(un.value))
             i += 1
         return out
+
+
+@dataclass
+class ServedResult:
+    n: int
+    sel_start: np.ndarray
+    sel_len: np.ndarray
+    sel_trace: np.ndarray
+    trace_len: np.ndarray
+    trace_start: np.ndarray
+    t_submit: float
+    t_start: float
+    t_done: float
+    batch_windows: int
+
+
+class Server:
+    """Continuous batching of repeat-finding requests (apo_server_*): submit
+    host token windows at any time; lanes batch whatever is waiting, up to
+    max_batch_tokens tokens and max_batch_windows requests, and run them on
+    the GPU, several batches in flight at once."""
+
+    def __init__(self, device: int = 0, min_len: int = 5, token_bytes: int = 4,
+                 max_batch_tokens: int = 1 << 24, max_batch_windows: int = 512, lanes: int = 2):
+        self.token_bytes = token_bytes
+        self._dt = np.uint32 if token_bytes == 4 else np.uint64
+        h = _P()
+        cfg = apo_server_config(min_len, token_bytes, max_batch_tokens, max_batch_windows, lanes)
+        _check(lib().apo_server_create(ctypes.byref(h), device, ctypes.byref(cfg)))
+        self._h = h
+
+    def submit(self, tokens) -> int:
+        a = np.ascontiguousarray(np.asarray(tokens).astype(self._dt, copy=False))
+        rid = _U64(0)
+        _check(lib().apo_server_submit(self._h, a.ctypes.data_as(_P).value, a.shape[0], ctypes.byref(rid)))
+        return int(rid.value)
+
+    @staticmethod
+    def _arr(p, k):
+        if k == 0:
+            return np.zeros(0, np.uint32)
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_uint32)), shape=(k,)).copy()
+
+    def _take(self, rid, r) -> ServedResult:
+        _check(r.status)
+        out = ServedResult(int(r.n), self._arr(r.sel_start, r.n_selected), self._arr(r.sel_len, r.n_selected),
+                           self._arr(r.sel_trace, r.n_selected), self._arr(r.trace_len, r.n_traces),
+                           self._arr(r.trace_start, r.n_traces), r.t_submit, r.t_start, r.t_done,
+                           int(r.batch_windows))
+        _check(lib().apo_server_release(self._h, rid))
+        return out
+
+    def poll(self, rid: int):
+        r = apo_request_result()
+        code = lib().apo_server_poll(self._h, rid, ctypes.byref(r))
+        if code == APO_EAGAIN:
+            return None
+        _check(code)
+        return self._take(rid, r)
+
+    def wait(self, rid: int) -> ServedResult:
+        r = apo_request_result()
+        _check(lib().apo_server_wait(self._h, rid, ctypes.byref(r)))
+        return self._take(rid, r)
+
+    def now(self) -> float:
+        return float(lib().apo_server_now(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apo_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def greedy_select_noalloc(cand_len, cand_start, n: int, accepted, accepted_count, stream=None):

@@ -27,8 +27,9 @@
 // automaton repeats the recorded run.  When a pass changes no end state all
 // states are exact (after k passes chunks 0..k are, by induction).  The
 // per-node match totals turn the output offsets into one prefix sum over
-// positions; a final kernel per position writes its matches.  Output order: end ascending, then pattern length descending (the
-// output chain's order), then pattern id ascending.
+// positions; a final kernel per position writes its matches.  Output order:
+// end ascending, then pattern length descending (the output chain's order),
+// then pattern id ascending.
 #include <algorithm>
 #include <cstring>
 #include <vector>

@@ -329,3 +329,25 @@ def test_batched_equals_plain_and_u64(apo):
         return p
     _check_batch_against(res, wins, plain)
     _check_batch_against(res, wins, lambda w, S: oracle.find_repeats(S, 5))
+
+
+# ---------------------------------------------------------------- served form
+def test_served_results_equal_alone(apo):
+    """Requests submitted together are batched by the server; every result
+    equals what the same window gives alone (plain call) and the oracle."""
+    from paper_2406_18111_gb300 import Server, as_u32
+    srv = Server(0, min_len=5, token_bytes=4, max_batch_tokens=300000, max_batch_windows=8, lanes=2)
+    wins = []
+    for r in range(14):
+        L = [5000, 60000, 1, 0, 12345, 100000, 4096][r % 7] + r
+        wins.append(W.periodic_window(L, 3 + (r * 977) % 4000, 0.05, 1000, seed=900 + r))
+    ids = [srv.submit(S) for S in wins]
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    assert max(x.batch_windows for x in res) > 1  # some requests shared a batch
+    for S, got in zip(wins, res):
+        alone = apo.find_repeats(tokens_dev(S, 4), 5, stages=False)
+        o = oracle.find_repeats(S.astype(np.uint64), 5)
+        for f in ("sel_start", "sel_len", "sel_trace", "trace_len", "trace_start"):
+            assert np.array_equal(getattr(got, f), as_u32(getattr(alone, f))), f
+            assert np.array_equal(getattr(got, f), getattr(o, f)), f
