@@ -1,10 +1,11 @@
 // Onesweep LSD radix sort of (u64 key, u32 value) pairs.
 //
 // After Adinets & Merrill, "Onesweep: A Faster Least Significant Digit Radix
-// Sort for GPUs" (2022): one upsweep kernel histograms every digit place in a
-// single read of the keys; then each digit place is scattered by one kernel
-// whose tiles learn their global digit offsets through decoupled look-back
-// instead of a separate scan pass.  Within a tile, keys are ranked per warp
+// Sort for GPUs" (2022): each digit place is scattered by one kernel whose
+// tiles learn their global digit offsets through decoupled look-back instead
+// of a separate scan pass.  Only the first place's histogram needs its own
+// read of the keys; every pass counts the next place's digits of the keys it
+// already holds, and each tile turns a histogram into offsets itself.  Within a tile, keys are ranked per warp
 // with __match_any_sync (stable: a warp's items are visited in input order),
 // staged in shared memory in digit order and written out in runs, so global
 // writes are coalesced per digit.
@@ -21,10 +22,12 @@ namespace apo {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;              // histogram / offsets kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // 4096 pairs per tile
+constexpr int kPT = 512;                   // digit-pass kernel: threads per block
+constexpr int kPW = kPT / 32;
+constexpr int kItems = 8;                  // pairs per thread
+constexpr int kTile = kPT * kItems;        // 4096 pairs per tile
 constexpr int kRadix = 256;
 constexpr int kMaxPass = 12;
 
@@ -38,48 +41,60 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t v, int place) 
   return (place & 256) ? ((v >> sh) & 255u) : (uint32_t)((k >> sh) & 255u);
 }
 
+// Every place's digit histogram in one read of the keys.  When all lanes of
+// a warp hold the same digit (common for the high digits of sorted ranks)
+// one add counts the whole warp, so skewed digits do not serialise on one
+// shared-memory counter.
 __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint64_t *__restrict__ keys,
                                                       const uint32_t *__restrict__ vals, uint32_t n,
                                                       Places pl, uint32_t *__restrict__ hist) {
   __shared__ uint32_t sh[kMaxPass * kRadix];
   for (int i = threadIdx.x; i < pl.n * kRadix; i += kThreads) sh[i] = 0;
   __syncthreads();
-  const uint32_t stride = gridDim.x * kThreads;
-  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
-    const uint64_t k = keys[i];
-    const uint32_t v = vals[i];
-    for (int p = 0; p < pl.n; ++p) atomicAdd(&sh[p * kRadix + digit_of(k, v, pl.p[p])], 1u);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u); b0 < n; b0 += stride) {
+    const uint64_t i = b0 + lane;
+    const bool valid = i < n;
+    const uint64_t k = valid ? keys[i] : 0;
+    const uint32_t v = valid ? vals[i] : 0;
+    for (int p = 0; p < pl.n; ++p) {
+      const uint32_t d = valid ? digit_of(k, v, pl.p[p]) : 256u;
+      const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+      if (__all_sync(0xffffffffu, d == d0 && d0 < 256u)) {
+        if (lane == 0) atomicAdd(&sh[p * kRadix + d0], 32u);
+      } else if (valid) {
+        atomicAdd(&sh[p * kRadix + d], 1u);
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < pl.n * kRadix; i += kThreads)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// hist[p][d] -> exclusive prefix over d, in place (one block per place).
-__global__ void __launch_bounds__(kThreads) k_rs_offsets(uint32_t *hist) {
-  __shared__ uint32_t scratch[kWarps];
-  uint32_t *h = hist + blockIdx.x * kRadix;
-  const uint32_t c = h[threadIdx.x];
-  uint32_t tot;
-  const uint32_t inc = block_inclusive<kWarps>(c, OpSum(), 0u, scratch, &tot);
-  h[threadIdx.x] = inc - c;
-}
-
-__global__ void __launch_bounds__(kThreads) k_rs_pass(
+// One digit place.  `gcnt` is this place's global digit histogram (the
+// tile turns it into digit offsets itself); when next_place >= 0 the tile
+// also counts the next place's digits of its keys into next_cnt, so no
+// separate histogram read is needed for any place but the first.
+__global__ void __launch_bounds__(kPT, 2) k_rs_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, uint32_t n, int place, const uint32_t *__restrict__ offs,
-    uint64_t *status, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+    uint32_t *__restrict__ vout, uint32_t n, int place, const uint32_t *__restrict__ gcnt,
+    int next_place, uint32_t *__restrict__ next_cnt, uint64_t *status, uint32_t *tile_ctr,
+    uint32_t epoch, uint32_t *err) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kTile);
-  uint32_t *wc = sv + kTile;            // [kWarps][256] per-warp digit counts, then prefixes
-  uint32_t *tex = wc + kWarps * kRadix;  // [256] exclusive digit prefix within the tile
+  uint32_t *wc = sv + kTile;            // [kPW][256] per-warp digit counts, then prefixes
+  uint32_t *tex = wc + kPW * kRadix;     // [256] exclusive digit prefix within the tile
   uint32_t *gof = tex + kRadix;          // [256] global offset of the tile's digit run, minus tex
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t scratch[kWarps];
+  __shared__ uint32_t scratch[kPW];
+  __shared__ uint32_t s_next[kRadix];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < kWarps * kRadix; i += kThreads) wc[i] = 0;
+  for (int i = tid; i < kPW * kRadix; i += kPT) wc[i] = 0;
+  if (tid < kRadix) s_next[tid] = 0;
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
@@ -102,6 +117,19 @@ __global__ void __launch_bounds__(kThreads) k_rs_pass(
   }
   uint32_t *mywc = wc + warp * kRadix;
   const uint32_t lt = lanemask_lt();
+  if (next_place >= 0) {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const bool valid = seg + j * 32 + lane < n;
+      const uint32_t dn = valid ? digit_of(k[j], v[j], next_place) : 256u;
+      const uint32_t d0 = __shfl_sync(0xffffffffu, dn, 0);
+      if (__all_sync(0xffffffffu, dn == d0 && d0 < 256u)) {
+        if (lane == 0) atomicAdd(&s_next[d0], 32u);
+      } else if (valid) {
+        atomicAdd(&s_next[dn], 1u);
+      }
+    }
+  }
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const bool valid = seg + j * 32 + lane < n;
@@ -118,26 +146,35 @@ __global__ void __launch_bounds__(kThreads) k_rs_pass(
   }
   __syncthreads();
 
-  // Thread d owns digit d: warp prefixes, tile count, publication, look-back.
+  // Thread d < 256 owns digit d: warp prefixes, tile count, publication,
+  // look-back (threads 256.. only join the block scan with zero).
   const int d = tid;
+  const bool owner = d < kRadix;
   uint32_t tcnt = 0;
+  if (owner) {
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = wc[w * kRadix + d];
-    wc[w * kRadix + d] = tcnt;
-    tcnt += c;
+    for (int w = 0; w < kPW; ++w) {
+      const uint32_t c = wc[w * kRadix + d];
+      wc[w * kRadix + d] = tcnt;
+      tcnt += c;
+    }
   }
   uint64_t *st = status + (size_t)t * kRadix;
-  lb_store(&st[d], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tcnt));
+  if (owner) lb_store(&st[d], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tcnt));
   uint32_t tot;
-  const uint32_t inc = block_inclusive<kWarps>(tcnt, OpSum(), 0u, scratch, &tot);
-  tex[d] = inc - tcnt;
-  uint32_t excl = 0;
-  if (t > 0) {
-    excl = lb_exclusive(status + d, kRadix, t, epoch, OpSum(), 0u, err);
-    lb_store(&st[d], lb_pack(kLbInclusive, epoch, excl + tcnt));
+  const uint32_t gc = owner ? gcnt[d] : 0u;
+  const uint32_t ginc = block_inclusive<kPW>(gc, OpSum(), 0u, scratch, &tot);
+  if (owner && next_place >= 0 && s_next[d]) atomicAdd(&next_cnt[d], s_next[d]);
+  const uint32_t inc = block_inclusive<kPW>(tcnt, OpSum(), 0u, scratch, &tot);
+  if (owner) {
+    tex[d] = inc - tcnt;
+    uint32_t excl = 0;
+    if (t > 0) {
+      excl = lb_exclusive(status + d, kRadix, t, epoch, OpSum(), 0u, err);
+      lb_store(&st[d], lb_pack(kLbInclusive, epoch, excl + tcnt));
+    }
+    gof[d] = (ginc - gc) + excl - (inc - tcnt);
   }
-  gof[d] = offs[d] + excl - (inc - tcnt);
   __syncthreads();
 
 #pragma unroll
@@ -151,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_rs_pass(
   }
   __syncthreads();
   const uint32_t cnt = (n - base) < (uint64_t)kTile ? (uint32_t)(n - base) : (uint32_t)kTile;
-  for (uint32_t q = tid; q < cnt; q += kThreads) {
+  for (uint32_t q = tid; q < cnt; q += kPT) {
     const uint64_t kk = sk[q];
     const uint32_t vv = sv[q];
     const uint32_t pos = gof[digit_of(kk, vv, place)] + q;
@@ -174,7 +211,7 @@ __global__ void k_key_or(const uint64_t *__restrict__ keys, uint32_t n, unsigned
 }
 
 constexpr size_t kPassSmem =
-    (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4;
+    (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kPW * kRadix * 4 + 2 * kRadix * 4;
 
 }  // namespace
 
@@ -216,20 +253,19 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *places, 
   const int hblocks = std::min(c->num_sms * 4, ceil_div(n, kThreads * 8));
   {
     Launch lp_(c, kKRsHist, n, s);
-    k_rs_hist<<<hblocks, kThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, pl, hist);
-  }
-  {
-    Launch lp_(c, kKRsOffsets, npass, s);
-    k_rs_offsets<<<npass, kThreads, 0, s>>>(hist);
+    Places first = pl;
+    first.n = 1;
+    k_rs_hist<<<hblocks, kThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, first, hist);
   }
   for (int p = 0; p < npass; ++p) {
     const uint32_t ep = next_epoch(c);
+    const int nxt = p + 1 < npass ? places[p + 1] : -1;
     {
       Launch lp_(c, kKRsPass, n, s);
-      k_rs_pass<<<tiles, kThreads, kPassSmem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
+      k_rs_pass<<<tiles, kPT, kPassSmem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
                                                    b.vals[b.cur ^ 1], n, places[p],
-                                                   hist + p * kRadix, c->ps.lookback, tctr + p, ep,
-                                                   c->ps.err);
+                                                   hist + p * kRadix, nxt, hist + (p + 1) * kRadix,
+                                                   c->ps.lookback, tctr + p, ep, c->ps.err);
     }
     b.cur ^= 1;
   }

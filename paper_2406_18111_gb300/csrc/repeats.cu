@@ -386,35 +386,62 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
 }
 
 // Accepted candidates (compacted, in order) -> R and the keys of the
-// selected intervals.  One block; K is at most n / min_len.
-__global__ void __launch_bounds__(1024) k_traces(const uint32_t *__restrict__ accidx, uint32_t K,
-                                                 const uint32_t *__restrict__ cl,
-                                                 const uint32_t *__restrict__ cid,
-                                                 const uint32_t *__restrict__ cs,
-                                                 uint32_t *__restrict__ tl, uint32_t *__restrict__ ts,
-                                                 uint64_t *__restrict__ skeys,
-                                                 uint32_t *__restrict__ svals, uint32_t *tcount) {
-  __shared__ uint32_t scr[32];
-  __shared__ uint32_t s_carry;
-  if (threadIdx.x == 0) s_carry = 0;
+// selected intervals.  A new trace starts wherever (length, id) changes; the
+// trace index of an accepted candidate is the number of such starts up to it,
+// minus one (a decoupled look-back sum over tiles of 4096).
+__global__ void __launch_bounds__(kCT) k_traces(const uint32_t *__restrict__ accidx, uint32_t K,
+                                                const uint32_t *__restrict__ cl,
+                                                const uint32_t *__restrict__ cid,
+                                                const uint32_t *__restrict__ cs,
+                                                uint32_t *__restrict__ tl, uint32_t *__restrict__ ts,
+                                                uint64_t *__restrict__ skeys,
+                                                uint32_t *__restrict__ svals, uint32_t *tcount,
+                                                uint64_t *status, uint32_t *tile_ctr, uint32_t epoch,
+                                                uint32_t *err) {
+  __shared__ uint32_t s_tile, s_pre;
+  __shared__ uint32_t scr[kCT / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
-  for (uint32_t base = 0; base < K; base += 1024) {
-    const uint32_t q = base + threadIdx.x;
-    uint32_t f = 0, k = 0;
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kCTile;
+  const uint64_t e0 = base + (uint64_t)tid * kCI;
+  uint32_t fb = 0;
+#pragma unroll
+  for (int i = 0; i < kCI; ++i) {
+    const uint64_t q = e0 + i;
     if (q < K) {
-      k = accidx[q];
-      if (q == 0) {
-        f = 1;
-      } else {
+      const uint32_t k = accidx[q];
+      bool f = q == 0;
+      if (!f) {
         const uint32_t kp = accidx[q - 1];
-        f = (cl[k] != cl[kp] || cid[k] != cid[kp]) ? 1u : 0u;
+        f = cl[k] != cl[kp] || cid[k] != cid[kp];
       }
+      if (f) fb |= 1u << i;
     }
-    uint32_t tot;
-    const uint32_t ex = block_exclusive<32>(f, OpSum(), 0u, scr, &tot);
-    const uint32_t carry = s_carry;
+  }
+  uint32_t tot;
+  const uint32_t ex = block_exclusive<kCT / 32>(__popc(fb), OpSum(), 0u, scr, &tot);
+  if (tid == 0) {
+    lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
+    uint32_t pre = 0;
+    if (t > 0) {
+      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
+    }
+    s_pre = pre;
+    if (base + kCTile >= K) *tcount = pre + tot;
+  }
+  __syncthreads();
+  uint32_t run = s_pre + ex;  // trace starts before element e0
+#pragma unroll
+  for (int i = 0; i < kCI; ++i) {
+    const uint64_t q = e0 + i;
     if (q < K) {
-      const uint32_t tr = carry + ex + f - 1;  // index of this candidate's trace
+      const uint32_t k = accidx[q];
+      const bool f = (fb >> i) & 1u;
+      run += f;
+      const uint32_t tr = run - 1;  // index of this candidate's trace
       if (f) {
         tl[tr] = cl[k];
         ts[tr] = cs[k];
@@ -422,11 +449,7 @@ __global__ void __launch_bounds__(1024) k_traces(const uint32_t *__restrict__ ac
       skeys[q] = ((uint64_t)cs[k] << 32) | cl[k];
       svals[q] = tr;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry = carry + tot;
-    __syncthreads();
   }
-  if (threadIdx.x == 0) *tcount = s_carry;
 }
 
 __global__ void k_sel_out(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
@@ -695,9 +718,13 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     sb.vals[1] = b.vals[1];
     sb.cur = 0;
     {
+      const int tiles = ceil_div(K, kCTile);
+      APO_TRY(ensure_lookback(c, tiles));
+      APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCompactTiles, 0, sizeof(uint32_t), s));
       Launch lp_(c, kKTraces, K, s);
-      k_traces<<<1, 1024, 0, s>>>(sel, K, cl, cid, cs, tl, ts, sb.keys[0], sb.vals[0],
-                                  misc + kMiscTraceCount);
+      k_traces<<<tiles, kCT, 0, s>>>(sel, K, cl, cid, cs, tl, ts, sb.keys[0], sb.vals[0],
+                                     misc + kMiscTraceCount, c->ps.lookback,
+                                     misc + kMiscCompactTiles, next_epoch(c), c->ps.err);
     }
     int places[8];
     const int np = plan_digits(32, 32 + bits_for(n - 1), places, 0);

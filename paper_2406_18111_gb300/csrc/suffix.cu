@@ -149,16 +149,16 @@ __global__ void __launch_bounds__(kRT) k_refresh(
   }
 }
 
-// key = (rank[i] << 32) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
-// value = i.
+// key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
+// value = i, with sh = bits of n (the second part is at most n).
 __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ rank,
-                       uint32_t n, uint64_t h, Windows W, uint64_t *__restrict__ keys,
+                       uint32_t n, uint64_t h, int sh, Windows W, uint64_t *__restrict__ keys,
                        uint32_t *__restrict__ vals) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < A; k += gridDim.x * blockDim.x) {
     const uint32_t i = act[k];
     const uint64_t j = i + h;
     const uint32_t r2 = j < win_end(W, i, n) ? rank[j] + 1u : 0u;
-    keys[k] = ((uint64_t)rank[i] << 32) | r2;
+    keys[k] = ((uint64_t)rank[i] << sh) | r2;
     vals[k] = i;
   }
 }
@@ -336,11 +336,10 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     b.cur = 0;
     {
       Launch lp_(c, kKPack, A, s);
-      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, st.win,
-                                                            b.keys[0], b.vals[0]);
+      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, minor_bits,
+                                                            st.win, b.keys[0], b.vals[0]);
     }
-    np = plan_digits(0, minor_bits, places, 0);
-    np = plan_digits(32, 32 + major_bits, places, np);
+    np = plan_digits(0, minor_bits + major_bits, places, 0);
     APO_TRY(radix_sort_pairs(c, b, A, places, np, s));
     uint32_t A2 = 0;
     APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], A, pos[cur], st.sa, st.rank, act[cur ^ 1],
