@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=3.0, help="served: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: mean requests per second")
     ap.add_argument("--lanes", type=int, default=2, help="served: batches in flight")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="window workload: skip the short batched and served measurements")
     return ap.parse_args()
 
 
@@ -185,7 +187,7 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def run_batched(args, rank, world, local):
+def run_batched(args, rank, world, local, emit=True, plain_steps=3):
     """512 windows of log-uniform length 1,024..262,144 (period U{3..5000},
     5% noise over 1,000 tokens): SA + LCP + Alg. 2 repeats for all of them in
     one batched call, against one call per window (plain)."""
@@ -231,7 +233,7 @@ def run_batched(args, rank, world, local):
         for w in range(args.windows):
             a, b = int(off[w]), int(off[w + 1])
             apo.find_repeats(t[a:b], MIN_LEN, stages=False)
-    plain_steps = max(1, min(3, args.steps))
+    plain_steps = max(1, min(plain_steps, args.steps))
     ms_plain = timed(plain, plain_steps)
     clk = clocks.stop()
     peak, peak_kind = peaks()
@@ -245,8 +247,7 @@ def run_batched(args, rank, world, local):
                      "ms_per_launch": kms / la})
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
-    if rank == 0:
-        print(json.dumps({
+    out = ({
             "metric": METRIC, "value": total * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -257,10 +258,13 @@ def run_batched(args, rank, world, local):
             "plain": {"value": total / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                       "form": "one apo_find_repeats call per window, same stream", "steps": plain_steps},
             "batched_over_plain": ms_plain / ms,
-            "gpu_launches": n_launch, "roofline": roof, "clocks": clk, "kernels": kernels}))
+            "gpu_launches": n_launch, "roofline": roof, "clocks": clk, "kernels": kernels})
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
 
 
-def run_served(args, rank, world, local):
+def run_served(args, rank, world, local, emit=True):
     """Poisson analysis requests (mean `rate`/s for `duration` s, window
     lengths log-uniform 4,096..2^20 tokens, periodic content with 5% noise)
     submitted in real time to a continuous-batching server; p50/p99 latency
@@ -299,8 +303,7 @@ def run_served(args, rank, world, local):
     tokens = sum(r.n for r in res)
     span = max(r.t_done for r in res) - min(r.t_submit for r in res)
     bw = np.array([r.batch_windows for r in res])
-    if rank == 0:
-        print(json.dumps({
+    out = ({
             "metric": METRIC, "value": tokens / span, "unit": UNIT, "n_gpus": world,
             "steps": len(res), "warmup": 8, "ms_per_step": float(np.mean(lat)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -310,7 +313,10 @@ def run_served(args, rank, world, local):
                        "requests": len(res), "offered_tokens_per_s": tokens / args.duration,
                        "lanes": args.lanes, "max_batch_tokens": 1 << 24},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_batch_windows": float(bw.mean()), "clocks": clk}))
+            "mean_batch_windows": float(bw.mean()), "clocks": clk})
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
 
 
 def main():
@@ -482,6 +488,20 @@ def main():
         "step_stats": stats,
         "kernels": kernels,
     }
+    if world == 1 and not args.no_forms:
+        # The batched and served forms, measured briefly
+        # on their own workloads; their own modes (--workload) give the full runs.
+        import copy
+        a2 = copy.copy(args)
+        a2.steps, a2.warmup = min(args.steps, 5), 2
+        bt = run_batched(a2, rank, world, local, emit=False, plain_steps=1)
+        line["batched"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "config", "plain",
+                                               "batched_over_plain", "roofline")}
+        a3 = copy.copy(args)
+        a3.duration = 2.0
+        sv = run_served(a3, rank, world, local, emit=False)
+        line["served"] = {k: sv[k] for k in ("value", "unit", "p50_ms", "p99_ms", "config",
+                                              "mean_batch_windows")}
     print(json.dumps(line))
 
 

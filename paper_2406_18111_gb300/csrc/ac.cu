@@ -303,16 +303,9 @@ __global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint
 }
 
 // ---------------------------------------------------------------- match
-__device__ __forceinline__ uint32_t ac_step(const Table &g, const uint32_t *__restrict__ fail,
-                                            uint32_t state, uint32_t c) {
-  const uint32_t root = (uint32_t)(g.mask + 1);
-  while (true) {
-    const uint32_t nx = goto_lookup(g, state, c);
-    if (nx != kNil) return nx;
-    if (state == root) return root;
-    state = fail[state];
-  }
-}
+// One goto probe or one failure step per loop iteration, so that the lanes
+// of a warp advance through their chunks independently instead of waiting at
+// every token for the lane with the longest failure chain.
 
 // Pass A1: chunk t = positions [t*chunk, (t+1)*chunk) from the root state.
 // Chunk 0 is exact; the others may start in the wrong state.
@@ -323,10 +316,20 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
   const uint64_t ce = min(n, cs + chunk);
-  uint32_t state = (uint32_t)(g.mask + 1);  // root
-  for (uint64_t x = cs; x < ce; ++x) {
-    state = ac_step(g, fail, state, ssym[x]);
-    state_out[x] = state;
+  const uint32_t root = (uint32_t)(g.mask + 1);
+  uint32_t state = root, cur = root;  // cur: where the transition for x is being looked up
+  uint64_t x = cs;
+  uint32_t c = ssym[x];
+  while (x < ce) {
+    const uint32_t nx = goto_lookup(g, cur, c);
+    if (nx != kNil || cur == root) {
+      state = nx != kNil ? nx : root;
+      state_out[x] = state;
+      cur = state;
+      if (++x < ce) c = ssym[x];
+    } else {
+      cur = fail[cur];
+    }
   }
   end_state[t] = state;
 }
@@ -348,14 +351,24 @@ __global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t
     return;
   }
   const uint64_t ce = min(n, cs + chunk);
-  uint32_t state = end_in[t - 1];
-  for (uint64_t x = cs; x < ce; ++x) {
-    state = ac_step(g, fail, state, ssym[x]);
-    if (state_out[x] == state) {
-      end_out[t] = end_in[t];
-      return;
+  const uint32_t root = (uint32_t)(g.mask + 1);
+  uint32_t state = end_in[t - 1], cur = state;
+  uint64_t x = cs;
+  uint32_t c = ssym[x];
+  while (x < ce) {
+    const uint32_t nx = goto_lookup(g, cur, c);
+    if (nx != kNil || cur == root) {
+      state = nx != kNil ? nx : root;
+      if (state_out[x] == state) {
+        end_out[t] = end_in[t];
+        return;
+      }
+      state_out[x] = state;
+      cur = state;
+      if (++x < ce) c = ssym[x];
+    } else {
+      cur = fail[cur];
     }
-    state_out[x] = state;
   }
   end_out[t] = state;
   if (state != end_in[t]) atomicAdd(changed, 1u);
@@ -647,13 +660,13 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   if (!state || !off || !ends[0] || !ends[1]) return APO_ENOMEM;
   {
     Launch lp_(c, kKAcMatch, n, s);
-    k_ac_states<<<ceil_div(nch, 128), 128, 0, s>>>(ssym, n, chunk, g, fail, state, ends[0]);
+    k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, g, fail, state, ends[0]);
   }
   for (uint64_t pass = 0, e = 0; pass < nch; ++pass, e ^= 1) {
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     {
       Launch lp_(c, kKFailLevel, n, s);
-      k_ac_fix<<<ceil_div(nch, 128), 128, 0, s>>>(ssym, n, chunk, g, fail, state, ends[e], ends[e ^ 1],
+      k_ac_fix<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, g, fail, state, ends[e], ends[e ^ 1],
                                                    misc + kMiscAccCount);
     }
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));

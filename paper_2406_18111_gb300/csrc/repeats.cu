@@ -349,10 +349,10 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
           free = !marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe);
         }
         uint32_t ov = 0;  // earlier lanes of the batch whose interval meets this lane's
-        for (uint32_t j = 0; j < nb; ++j) {
-          const uint32_t js = ss[q0 + j];
-          const uint32_t je = js + sl[q0 + j] - 1;
-          if (j < (uint32_t)lane && js <= qe && qs <= je) ov |= 1u << j;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t js = ss[q0 + j], je = js + sl[q0 + j] - 1;  // list has room past total
+          if (j < lane && (uint32_t)j < nb && js <= qe && qs <= je) ov |= 1u << j;
         }
         uint32_t und = __ballot_sync(0xffffffffu, free), accm = 0;
         while (und) {
@@ -363,8 +363,24 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
           const uint32_t drop = __ballot_sync(0xffffffffu, ((und >> lane) & 1u) && (ov & accm) != 0);
           und &= ~drop;
         }
-        if ((accm >> lane) & 1u) acc[sk[q]] = 1;
-        for (uint32_t am = accm; am; am &= am - 1) {  // mark accepted intervals, warp-wide
+        // mark accepted intervals: short ones by their own lane, long ones warp-wide
+        const bool mine = (accm >> lane) & 1u;
+        bool lng = false;
+        if (mine) {
+          acc[sk[q]] = 1;
+          const uint32_t w0 = qs >> 5, w1 = qe >> 5;
+          if (w1 - w0 < 8) {
+            for (uint32_t w = w0; w <= w1; ++w) {
+              uint32_t msk = 0xffffffffu;
+              if (w == w0) msk &= 0xffffffffu << (qs & 31);
+              if (w == w1) msk &= 0xffffffffu >> (31 - (qe & 31));
+              atomicOr(&bits[w], msk);
+            }
+          } else {
+            lng = true;
+          }
+        }
+        for (uint32_t am = __ballot_sync(0xffffffffu, lng); am; am &= am - 1) {
           const int j = __ffs(am) - 1;
           const uint32_t js = __shfl_sync(0xffffffffu, qs, j);
           const uint32_t je = __shfl_sync(0xffffffffu, qe, j);
