@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched", "served"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
@@ -319,12 +319,69 @@ def run_served(args, rank, world, local, emit=True):
     return out
 
 
+def run_match(args, rank, world, local, emit=True):
+    """Aho-Corasick matching (Sec. 4.3) of 10,000 candidate traces (lengths
+    log-uniform 5..2000; half copied from the stream, half random) against a
+    2^26-token stream of periodic segments: stream tokens per second, with
+    the automaton built inside every timed call."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    stream_np = W.match_stream(1 << 26, seed=5 + rank)
+    pt, off = W.match_patterns(stream_np, 10000, 5, 2000, seed=5 + rank)
+    st = torch.from_numpy(stream_np.view(np.int32)).to(dev)
+    ptd = torch.from_numpy(pt.view(np.int32)).to(dev)
+    cap = [1 << 20]
+    for _ in range(max(1, args.warmup)):
+        e, i = apo.match_candidates(ptd, off, st, cap=cap[0])
+        cap[0] = max(cap[0], int(e.shape[0] * 1.1) + 1)
+    matches = int(e.shape[0])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    clocks = Clocks(local)
+    apo.profile_reset()
+    apo.profile(True)
+    tot = 0.0
+    steps = max(1, min(args.steps, 10))
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        apo.match_candidates(ptd, off, st, cap=cap[0])
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    prof = apo.profile_read()
+    apo.profile(False)
+    clk = clocks.stop()
+    ms = tot / steps
+    n = int(stream_np.shape[0])
+    kernels = {k: {"launches_per_step": v[0] / steps, "ms_per_step": v[1] / steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    out = {"metric": "matched stream tokens/s (Aho-Corasick, build included)", "value": n * world / (ms / 1e3),
+           "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic",
+           "config": {"workload": "2^26-token stream of periodic segments; 10,000 patterns, lengths "
+                                  "log-uniform 5..2000, half stream substrings, half random",
+                      "n_tokens": n, "patterns": 10000, "pattern_tokens": int(off[-1]),
+                      "matches": matches, "l2": "flushed between steps"},
+           "clocks": clk, "kernels": kernels}
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in ("batched", "served"):
+    if args.workload in ("batched", "served", "match"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -337,6 +394,8 @@ def main():
             torch.distributed.barrier()
         if args.workload == "served":
             return run_served(args, rank, world, local)
+        if args.workload == "match":
+            return run_match(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch

@@ -271,9 +271,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_ac_build(BuildArgs a) {
           }
         }
         a.fail[v] = f;
-        const uint32_t o = (f != root && a.own[f] != 0) ? f : a.outl[f];
-        a.outl[v] = o;
-        a.total[v] = a.own[v] + a.total[o];
+        // total[f] = own[f] + total[outl[f]], so whichever of f and outl[f]
+        // is v's output link, the matches reported down it number total[f]
+        const uint32_t of = a.own[f];
+        a.outl[v] = (f != root && of != 0) ? f : a.outl[f];
+        a.total[v] = a.own[v] + a.total[f];
       }
     }
     grid_sync(a.bar, a.err);
@@ -447,17 +449,16 @@ inline int grid_for(uint64_t n, int threads, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
-int g_build_blocks = 0;  // co-resident blocks of k_ac_build for a cooperative launch
+int g_build_blocks = 0;  // most co-resident blocks of k_ac_build for a cooperative launch
 
 }  // namespace
 
 int match_init(int sms) {
-  // A small cooperative grid: the level barrier's cost grows with the number
-  // of arriving blocks, and 16K threads cover the patterns and the nodes of
-  // a level for the workloads at hand (larger sets loop).
+  // The level barrier's cost grows with the number of arriving blocks, so
+  // launches use no more blocks than the pattern count needs.
   int per_sm = 0;
   APO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ac_build, kBuildThreads, 0));
-  g_build_blocks = std::max(1, std::min(32, per_sm * sms));
+  g_build_blocks = std::max(1, per_sm * sms);
   return APO_OK;
 }
 
@@ -626,8 +627,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.err = c->ps.err;
     void *args[] = {&a};
     Launch lp_(c, kKTrieInsert, total, s);
-    APO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_ac_build, g_build_blocks, kBuildThreads,
-                                             args, 0, s));
+    // one inserter and one linker thread per pattern where possible, at least
+    // 32 blocks, at most what is co-resident (larger sets loop)
+    const int blocks = std::min<int>(g_build_blocks, std::max<int>(32, ceil_div(2ull * P, kBuildThreads)));
+    APO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_ac_build, blocks, kBuildThreads, args, 0, s));
   }
   APO_CUDA_TRY(cudaGetLastError());
   // pattern ids grouped by end node
@@ -654,7 +657,9 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   // pass A: states, chunked without a halo, then repaired until stable
   uint32_t *state = c->arena.take_n<uint32_t>(n);
   uint32_t *off = c->arena.take_n<uint32_t>(n);
-  const uint64_t chunk = std::max<uint64_t>(32, n / ((uint64_t)sms * 64));
+  // short chunks: a chunk is a chain of dependent lookups, so its length is
+  // the pass time; repair passes cost little once chunks end in a reset
+  const uint64_t chunk = std::max<uint64_t>(32, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
   const uint64_t nch = (n + chunk - 1) / chunk;
   uint32_t *ends[2] = {c->arena.take_n<uint32_t>(nch), c->arena.take_n<uint32_t>(nch)};
   if (!state || !off || !ends[0] || !ends[1]) return APO_ENOMEM;

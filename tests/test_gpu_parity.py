@@ -227,10 +227,11 @@ def test_match_random(apo, tb):
         assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
 
 
-def test_match_config5_scaled(apo):
+@pytest.mark.parametrize("n,P", [(1 << 20, 400), (1 << 22, 2000)])
+def test_match_config5_scaled(apo, n, P):
     from paper_2406_18111_gb300 import as_u32
-    stream = W.match_stream(1 << 20, seed=7)
-    pt, off = W.match_patterns(stream, 400, 5, 2000, seed=7)
+    stream = W.match_stream(n, seed=7)
+    pt, off = W.match_patterns(stream, P, 5, 2000, seed=7)
     e, i = apo.match_candidates(tokens_dev(pt, 4), off, tokens_dev(stream, 4))
     oe, oi = oracle.match(pt, off, stream)
     assert len(oe) > 0
@@ -351,3 +352,14 @@ def test_served_results_equal_alone(apo):
         for f in ("sel_start", "sel_len", "sel_trace", "trace_len", "trace_start"):
             assert np.array_equal(getattr(got, f), as_u32(getattr(alone, f))), f
             assert np.array_equal(getattr(got, f), getattr(o, f)), f
+
+
+def test_match_config5_full(apo):
+    """Full-size matching workload: 2^26-token stream, 10,000 patterns."""
+    from paper_2406_18111_gb300 import as_u32
+    stream = W.match_stream(1 << 26, seed=5)
+    pt, off = W.match_patterns(stream, 10000, 5, 2000, seed=5)
+    e, i = apo.match_candidates(tokens_dev(pt, 4), off, tokens_dev(stream, 4))
+    oe, oi = oracle.match(pt, off, stream)
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
