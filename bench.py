@@ -55,6 +55,53 @@ BYTES_PER_UNIT = {"rs_pass": 24, "refresh": 32, "pack": 24, "rs_hist": 12, "hash
                   "ac_states": 12, "plcp": 24, "cand_gen": 36, "greedy": 8, "compact": 16}
 
 
+# The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
+# with their radix sorts and rank refreshes) and the Phi/PLCP LCP.
+SA_LCP_KERNELS = ("init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack", "phi",
+                  "plcp", "lcp_perm")
+
+
+def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:
+    """Algorithmic bytes of the SA+LCP path for one call (all windows):
+    rank init n(w+28); per doubling round r >= 1, 36 bytes per active suffix,
+    where A_r = #{i : max LCP of i with its SA neighbours >= 2^(r-1)} (a
+    property of the input, not of the implementation); SA write 4n; LCP
+    n(28+2w).  `lcp` is the pair-convention LCP (LCP[i] of SA[i], SA[i+1]),
+    zero across window boundaries."""
+    import torch
+    n = int(lcp.numel())
+    lc = lcp.to(torch.int64)
+    if win_off is not None:
+        # the pair straddling a window boundary has LCP 0 by definition
+        ends = torch.as_tensor([int(x) - 1 for x in win_off[1:-1]], dtype=torch.int64, device=lc.device)
+        lc[ends] = 0
+    lc[n - 1] = 0
+    left = torch.cat([torch.zeros(1, dtype=torch.int64, device=lc.device), lc[:-1]])
+    mx = torch.maximum(left, lc)
+    a_r = []
+    h = 1
+    while True:
+        a = int((mx >= h).sum())
+        if a == 0:
+            break
+        a_r.append(a)
+        h <<= 1
+    total = n * (w + 28) + 36 * sum(a_r) + 4 * n + n * (28 + 2 * w)
+    return float(total), a_r
+
+
+def sa_lcp_roofline(prof: dict, steps: int, b_alg: float, a_r: list, peak: float, peak_kind: str) -> dict:
+    """Algorithmic fraction of the HBM roofline for the SA+LCP path: its
+    algorithmic bytes per call over the summed event time of its kernels."""
+    ms = sum(prof[k][1] for k in SA_LCP_KERNELS if k in prof) / steps
+    launches = sum(prof[k][0] for k in SA_LCP_KERNELS if k in prof) / steps
+    ach = b_alg / (ms / 1e3) / 1e9 if ms > 0 else None
+    return {"bound": "hbm", "unit": "GB/s", "kernels": list(SA_LCP_KERNELS), "launches_per_step": launches,
+            "ms_per_step": ms, "algorithmic_bytes": b_alg, "active_per_round": a_r, "achieved": ach,
+            "peak": peak, "peak_kind": peak_kind, "frac": (ach / peak) if ach else None,
+            "traffic": None}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -247,6 +294,10 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
                      "ms_per_launch": kms / la})
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    full = apo.find_repeats_batched(t, off, MIN_LEN, stages=True)
+    b_alg, a_r = sa_lcp_bytes(full.lcp, off, 4)
+    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind)
+    del full
     out = ({
             "metric": METRIC, "value": total * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -258,7 +309,8 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
             "plain": {"value": total / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                       "form": "one apo_find_repeats call per window, same stream", "steps": plain_steps},
             "batched_over_plain": ms_plain / ms,
-            "gpu_launches": n_launch, "roofline": roof, "clocks": clk, "kernels": kernels})
+            "gpu_launches": n_launch, "roofline": roof, "sa_lcp_roofline": sa_lcp, "clocks": clk,
+            "kernels": kernels})
     if emit and rank == 0:
         print(json.dumps(out))
     return out
@@ -524,6 +576,11 @@ def main():
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    full = apo.find_repeats(tok, MIN_LEN, stages=True)
+    b_alg, a_r = sa_lcp_bytes(full.lcp, None, 8)
+    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind)
+    del full
+
     if rank != 0:
         return
     cpu = None
@@ -540,6 +597,7 @@ def main():
                 "d2h_bytes_per_step": d2h[0], "ms_per_step": ms_e2e},
         "gpu_launches": n_launch,
         "roofline": roof,
+        "sa_lcp_roofline": sa_lcp,
         "cpu_baseline": cpu,
         "clocks": clk,
         "wall_s_timed": t_wall,
@@ -548,14 +606,14 @@ def main():
         "kernels": kernels,
     }
     if world == 1 and not args.no_forms:
-        # The batched and served forms, measured briefly
-        # on their own workloads; their own modes (--workload) give the full runs.
+        # The batched and served forms, measured briefly on their own
+        # workloads; their own modes (--workload) give the full runs.
         import copy
         a2 = copy.copy(args)
         a2.steps, a2.warmup = min(args.steps, 5), 2
         bt = run_batched(a2, rank, world, local, emit=False, plain_steps=1)
         line["batched"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "config", "plain",
-                                               "batched_over_plain", "roofline")}
+                                               "batched_over_plain", "roofline", "sa_lcp_roofline")}
         a3 = copy.copy(args)
         a3.duration = 2.0
         sv = run_served(a3, rank, world, local, emit=False)

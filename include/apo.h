@@ -313,7 +313,10 @@ int apo_greedy_select_noalloc(const uint32_t *cand_len, const uint32_t *cand_sta
  * launch stream, and the elapsed device time is accumulated when the entry
  * is read.  `units` accumulates the elements each launch processed (keys for
  * a radix-sort pass, suffixes for a refresh, tokens for a match), from which
- * a caller derives algorithmic bytes.
+ * a caller derives algorithmic bytes.  Kernels that apo_match_candidates
+ * launches to build the suffix array and LCP of its pattern text are kept
+ * apart from the entries of the same kernels on other paths: their names
+ * carry the prefix "ac.".
  * ---------------------------------------------------------------------- */
 int apo_profile_enable(apo_ctx *ctx, int enable_timing);
 int apo_profile_reset(apo_ctx *ctx);

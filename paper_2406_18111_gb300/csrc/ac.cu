@@ -5,19 +5,39 @@
 // failure link per node (longest proper suffix that is also in the trie) and
 // an output link per node (nearest pattern end on the failure chain).
 //
-// Symbols.  u32 tokens are their own symbols.  u64 tokens are mapped to 32-bit
-// symbols through an open-addressed dictionary filled from the pattern tokens
-// (a token's symbol is its slot); a stream token missing from the dictionary
-// matches nothing.  Both the pattern source and the stream are mapped once,
-// in parallel, before any sequential work.
+// Symbols.  Tokens (u32 or u64) are mapped to dense 32-bit symbols through an
+// open-addressed dictionary filled from the pattern tokens (a token's symbol
+// is its slot); a stream token missing from the dictionary matches nothing.
 //
-// Build.  One cooperative kernel builds the trie level by level: at level d
-// every pattern longer than d inserts its (d+1)-th node into the goto hash
-// table (keyed by node << 32 | symbol, slots claimed with atomicCAS; a node's
-// id is its slot), while the depth-d nodes get their failure link, output
-// link and match total (own pattern ends plus those down the output chain),
-// each computed by the pattern that created the node.  A bounded grid
-// barrier separates levels.
+// Build without a level-by-level walk.  The patterns are laid out as one
+// text T = P_0 #_0 P_1 #_1 ... whose separators #_p are distinct and smaller
+// than every symbol, and T gets a suffix array and an LCP array (the same
+// prefix-doubling and Phi/PLCP kernels as the window analysis).  With that:
+//
+//  nodes   a trie node is a distinct pattern prefix x.  Its id is the
+//          position in T of the last symbol of x inside the first pattern,
+//          in suffix order, that starts with x.  Pattern starts in suffix
+//          order, with slcp[j] = lcp(start j-1, start j), give that pattern
+//          as rep(j, |x|) = the largest j' <= j with slcp[j'] < |x|.  So the
+//          prefix of length d of the pattern at start j is its own node iff
+//          d > slcp[j], and a node's child on its own next symbol is simply
+//          the next position of T ("primary" edge, stored nowhere).  Only
+//          the depth slcp[j] + 1 node of each pattern hangs off another
+//          pattern's node, so the goto hash table holds at most one edge per
+//          pattern.
+//  fail    M(q) = the longest common prefix of suffix q with any pattern
+//          start (the nearer start on either side in suffix order, two
+//          segmented min-scans over LCP).  The suffix of length k of the
+//          node ending at e is a node iff M(e - k) >= k, so the failure depth
+//          of that node is e - q* with q* the first position after the
+//          pattern's start whose reach q + M(q) is >= e: a binary search over
+//          the segmented running maximum of the reach.  Its node id follows
+//          from a pattern start that shares that prefix (the nearer start on
+//          the side where M was attained) and rep().
+//  totals  match count per node = own pattern ends + the failure link's
+//          count, and the output link, by pointer jumping along failure
+//          links (a fixed number of in-place rounds: the chain shrinks by at
+//          least half per round).
 //
 // Match.  The stream is cut into short chunks and each thread runs the
 // automaton over its chunk from the root, writing the state of every
@@ -41,8 +61,10 @@ namespace apo {
 
 namespace {
 
-constexpr uint32_t kNil = 0xffffffffu;
+constexpr uint32_t kNil = 0xffffffffu;  // no node; also the symbol of a token no pattern has
+constexpr uint32_t kSep = 0xfffffffeu;  // symbol slot of a pattern separator in T
 constexpr uint64_t kEmpty = ~0ull;
+constexpr uint32_t kFlag = 0x80000000u;  // segment-start flag of a packed scan value
 
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;
@@ -60,7 +82,7 @@ struct Table {
   uint64_t mask;
 };
 
-__device__ __forceinline__ uint32_t goto_lookup(const Table &g, uint32_t u, uint32_t c) {
+__device__ __forceinline__ uint32_t table_lookup(const Table &g, uint32_t u, uint32_t c) {
   const uint64_t key = ((uint64_t)u << 32) | c;
   uint64_t slot = mix64(key) & g.mask;
   while (true) {
@@ -71,16 +93,25 @@ __device__ __forceinline__ uint32_t goto_lookup(const Table &g, uint32_t u, uint
   }
 }
 
+// goto(v, c): the primary edge when T continues with c after v, else the
+// branch table.
+__device__ __forceinline__ uint32_t ac_goto(const uint32_t *__restrict__ tsym, const Table &g,
+                                            uint32_t v, uint32_t c, uint32_t root) {
+  if (v != root && tsym[v + 1] == c) return v + 1;
+  return table_lookup(g, v, c);
+}
+
 // ---------------------------------------------------------------- symbols
 struct Dict {
   uint64_t *keys;  // a token's symbol is its slot
   uint64_t mask;
 };
 
-__global__ void k_dict_insert(const uint64_t *__restrict__ tok, uint64_t m, Dict d) {
+template <class T>
+__global__ void k_dict_insert(const T *__restrict__ tok, uint64_t m, Dict d) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t t = tok[i];
+    const uint64_t t = (uint64_t)tok[i];
     if (t == kEmpty) continue;  // mapped to a reserved symbol instead
     uint64_t slot = mix64(t) & d.mask;
     for (uint64_t probe = 0; probe <= d.mask; ++probe) {
@@ -96,28 +127,24 @@ __global__ void k_dict_insert(const uint64_t *__restrict__ tok, uint64_t m, Dict
   }
 }
 
-__global__ void k_dict_map(const uint64_t *__restrict__ tok, uint64_t m, Dict d,
-                           uint32_t *__restrict__ sym) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t t = tok[i];
-    uint32_t s = kNil;
-    if (t == kEmpty) {
-      s = (uint32_t)(d.mask + 1);  // reserved symbol of the all-ones token
-    } else {
-      uint64_t slot = mix64(t) & d.mask;
-      while (true) {
-        const uint64_t k = d.keys[slot];
-        if (k == t) {
-          s = (uint32_t)slot;
-          break;
-        }
-        if (k == kEmpty) break;
-        slot = (slot + 1) & d.mask;
-      }
-    }
-    sym[i] = s;
+template <class T>
+__device__ __forceinline__ uint32_t dict_symbol(const Dict &d, T tok) {
+  const uint64_t t = (uint64_t)tok;
+  if (t == kEmpty) return (uint32_t)(d.mask + 1);  // reserved symbol of the all-ones token
+  uint64_t slot = mix64(t) & d.mask;
+  while (true) {
+    const uint64_t k = d.keys[slot];
+    if (k == t) return (uint32_t)slot;
+    if (k == kEmpty) return kNil;
+    slot = (slot + 1) & d.mask;
   }
+}
+
+template <class T>
+__global__ void k_dict_map(const T *__restrict__ tok, uint64_t m, Dict d, uint32_t *__restrict__ sym) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    sym[i] = dict_symbol(d, tok[i]);
 }
 
 // max length, max end and total length of slice-form patterns; flags empty ones
@@ -138,148 +165,320 @@ __global__ void k_slices(const uint32_t *__restrict__ pstart, const uint32_t *__
   atomicAdd(total, tot);
 }
 
-// ---------------------------------------------------------------- build
-struct GridBarrier {
-  uint32_t *count;
-  uint32_t *gen;
-};
-
-// All blocks of a cooperative launch meet here.  Bounded: a block that waits
-// too long records kDevTimeout and leaves (the caller then stops).
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ void grid_sync(const GridBarrier &b, uint32_t *err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint32_t g0 = ld_acquire(b.gen);
-    __threadfence();  // this block's writes before its arrival
-    if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
-      *(volatile uint32_t *)b.count = 0;
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      uint32_t spins = 0;
-      while (ld_acquire(b.gen) == g0) {
-        if (++spins > kSpinLimit) {
-          atomicExch(err, kDevTimeout);
-          break;
-        }
+// ---------------------------------------------------------------- pattern text
+// T position of pattern p's first symbol: tstart[p] = sum of earlier lengths + p.
+// One warp per pattern writes its symbols and its separator: tsym (symbol,
+// kSep at the separator) and tkey (the suffix-sort token: separator p -> p,
+// symbol c -> P + c, so separators are distinct and below every symbol).
+template <class T>
+__global__ void k_pat_layout(const T *__restrict__ tok, const uint32_t *__restrict__ pstart,
+                             const uint32_t *__restrict__ plen, const uint32_t *__restrict__ tstart,
+                             uint32_t P, uint32_t N, Dict d, uint32_t *__restrict__ tsym,
+                             uint64_t *__restrict__ tkey) {
+  if (blockIdx.x == 0 && threadIdx.x < 2) tsym[N + threadIdx.x] = kSep;  // past the last separator
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < P; p += warps) {
+    const uint32_t src = pstart[p], len = plen[p], dst = tstart[p];
+    for (uint32_t k = lane; k <= len; k += 32) {
+      uint32_t c = kSep;
+      uint64_t key = p;
+      if (k < len) {
+        c = dict_symbol(d, tok[src + k]);
+        key = (uint64_t)P + c;
       }
+      tsym[dst + k] = c;
+      tkey[dst + k] = key;
     }
   }
-  __syncthreads();
 }
 
-// A node's id is the goto-table slot of the edge that leads to it (every
-// node but the root has exactly one incoming edge); the root's id is the
-// table capacity.  Node arrays therefore hold capacity + 1 entries.
-struct BuildArgs {
-  const uint32_t *psym;    // symbols of the pattern source tokens
-  const uint32_t *pstart;  // pattern p = psym[pstart[p] .. pstart[p] + plen[p])
-  const uint32_t *plen;
+// ---------------------------------------------------------------- segmented scans
+// Packed value: bit 31 = "a segment starts in this range", bits 30:0 = value.
+struct OpSegMin {  // running minimum since the last segment start
+  __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const {
+    if (b & kFlag) return b;
+    return (a & kFlag) | min(a & ~kFlag, b);
+  }
+};
+struct OpSegMax {  // running maximum since the last segment start
+  __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const {
+    if (b & kFlag) return b;
+    return (a & kFlag) | max(a & ~kFlag, b);
+  }
+};
+constexpr uint32_t kSegMinId = 0x7fffffffu, kSegMaxId = 0u;
+
+// Element k of the left scan over suffix order: lcp(SA[k-1], SA[k]), a
+// segment start when SA[k-1] is a pattern start.  Output: the lcp of SA[k]
+// with the nearest pattern start before it in suffix order (0 if none).
+struct SrcLeft {
+  const uint32_t *lcp;
+  const uint8_t *is_start;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+    if (k == 0) return kSegMinId;
+    return (is_start[k - 1] ? kFlag : 0u) | lcp[k - 1];
+  }
+};
+// Element k of the right scan (run from the end): lcp(SA[k], SA[k+1]), a
+// segment start when SA[k+1] is a pattern start.
+struct SrcRight {
+  const uint32_t *lcp;
+  const uint8_t *is_start;
+  uint32_t n;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+    if (k + 1 >= n) return kSegMinId;
+    return (is_start[k + 1] ? kFlag : 0u) | lcp[k];
+  }
+};
+struct DstFlagged {  // value where a segment start was seen, else 0
+  uint32_t *out;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const {
+    out[k] = (v & kFlag) ? (v & ~kFlag) : 0u;
+  }
+};
+// Element q of the reach scan over T: reach(q) = q + M(q), M(q) the longer of
+// the two lcps of suffix q with its nearest pattern starts; a segment starts
+// (with value 0) at each pattern's first position.
+struct SrcReach {
+  const uint64_t *tkey;
+  const uint32_t *rank, *left, *right;
   uint32_t P;
-  uint32_t maxlen;
-  uint32_t root;
+  __device__ __forceinline__ uint32_t operator()(uint32_t q) const {
+    if (q == 0 || tkey[q - 1] < P) return kFlag;
+    const uint32_t r = rank[q];
+    return q + max(left[r], right[r]);
+  }
+};
+struct DstValue {
+  uint32_t *out;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const { out[k] = v & ~kFlag; }
+};
+
+// Inclusive scan over n elements (in reverse index order when kReverse), one
+// 4096-element tile per block, tiles chained by decoupled look-back.
+constexpr int kGT = 256, kGI = 16, kGTile = kGT * kGI;
+template <bool kReverse, class Src, class Op, class Dst>
+__global__ void __launch_bounds__(kGT) k_seg_scan(Src src, Dst dst, uint32_t n, Op op, uint32_t ident,
+                                                  uint64_t *status, uint32_t *tile_ctr, uint32_t epoch,
+                                                  uint32_t *err) {
+  __shared__ uint32_t s_tile, s_pre;
+  __shared__ uint32_t scr[kGT / 32];
+  __shared__ uint32_t sv[kGTile];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kGTile;
+  for (int q = tid; q < kGTile; q += kGT) {
+    const uint64_t i = base + q;
+    sv[q] = i < n ? src(kReverse ? (uint32_t)(n - 1 - i) : (uint32_t)i) : ident;
+  }
+  __syncthreads();
+  uint32_t run = ident;
+#pragma unroll
+  for (int i = 0; i < kGI; ++i) run = op(run, sv[tid * kGI + i]);
+  uint32_t tot;
+  const uint32_t ex = block_exclusive<kGT / 32>(run, op, ident, scr, &tot);
+  if (tid == 0) {
+    lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
+    uint32_t pre = ident;
+    if (t > 0) {
+      pre = lb_exclusive(status, 1, t, epoch, op, ident, err);
+      lb_store(&status[t], lb_pack(kLbInclusive, epoch, op(pre, tot)));
+    }
+    s_pre = pre;
+  }
+  __syncthreads();
+  uint32_t r = op(s_pre, ex);
+#pragma unroll
+  for (int i = 0; i < kGI; ++i) {
+    r = op(r, sv[tid * kGI + i]);
+    sv[tid * kGI + i] = r;
+  }
+  __syncthreads();
+  for (int q = tid; q < kGTile; q += kGT) {
+    const uint64_t i = base + q;
+    if (i < n) dst(kReverse ? (uint32_t)(n - 1 - i) : (uint32_t)i, sv[q]);
+  }
+}
+
+// ---------------------------------------------------------------- pattern starts
+// (rank of pattern p's first suffix, p) for the sort into suffix order.
+__global__ void k_start_keys(const uint32_t *__restrict__ tstart, const uint32_t *__restrict__ rank,
+                             uint32_t P, uint64_t *keys, uint32_t *vals) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    keys[p] = rank[tstart[p]];
+    vals[p] = p;
+  }
+}
+
+// After the sort: sorted start j is SA index sr[j] of pattern sp[j].  Marks
+// the start suffixes and records each pattern's position j.
+__global__ void k_start_mark(const uint64_t *__restrict__ skeys, const uint32_t *__restrict__ svals,
+                             uint32_t P, uint32_t *sr, uint32_t *jpos, uint8_t *is_start) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)skeys[j];
+    sr[j] = r;
+    jpos[svals[j]] = j;
+    is_start[r] = 1;
+  }
+}
+
+// slcp[j] = lcp(start j-1, start j) in suffix order (0 for j = 0): the left
+// scan's value at the start's own SA index.
+__global__ void k_slcp(const uint32_t *__restrict__ sr, const uint32_t *__restrict__ left, uint32_t P,
+                       uint32_t *slcp) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += gridDim.x * blockDim.x)
+    slcp[j] = j ? left[sr[j]] : 0u;
+}
+
+// Sparse table of minima over windows ending at j: lev l, entry j =
+// min(slcp[max(0, j - 2^l + 1) .. j]).
+__global__ void k_sparse_level(const uint32_t *__restrict__ prev, uint32_t P, uint32_t half,
+                               uint32_t *__restrict__ next) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += gridDim.x * blockDim.x)
+    next[j] = j >= half ? min(prev[j], prev[j - half]) : prev[j];
+}
+
+constexpr int kMaxSparse = 33;
+struct Sparse {
+  const uint32_t *lev[kMaxSparse];
+  int nlev;
+};
+
+// rep(j, d): the largest j' <= j with slcp[j'] < d (d >= 1; slcp[0] = 0).
+__device__ __forceinline__ uint32_t rep_of(const Sparse &S, uint32_t j, uint32_t d) {
+  if (S.lev[0][j] < d) return j;
+  long long y = (long long)j - 1;  // every entry in (y, j] is >= d
+  for (int l = S.nlev - 1; l >= 0; --l) {
+    const long long w = 1ll << l;
+    if (y - w + 1 >= 0 && S.lev[l][y] >= d) y -= w;
+  }
+  return (uint32_t)max(0ll, y);
+}
+
+// ---------------------------------------------------------------- nodes and links
+struct NodeArgs {
+  const uint32_t *tstart, *plen, *tsym;
+  const uint32_t *jpos, *sp, *sr;  // sorted starts: pattern sp[j] at SA index sr[j]
+  const uint32_t *rank, *left, *reach;
+  Sparse S;  // minima over slcp
+  uint32_t P, root;
   Table g;
-  uint32_t *cur[2];    // [P] node of each pattern at depth d (parity of d)
-  uint8_t *made[2];    // [P] 1 if the pattern created that node
-  uint32_t *parent;    // [nodes]
-  uint32_t *nsym;      // [nodes] symbol on the edge into the node
-  uint32_t *fail;      // [nodes]
-  uint32_t *outl;      // [nodes] nearest pattern end on the failure chain (root = none)
-  uint32_t *own;       // [nodes] patterns ending exactly here
-  uint32_t *total;     // [nodes] matches reported in this state
-  uint32_t *end_node;  // [P]
-  GridBarrier bar;
+  uint32_t *fail, *own, *end_node;
   uint32_t *err;
 };
 
-constexpr int kBuildThreads = 512;
+__device__ __forceinline__ void table_insert(const Table &g, uint32_t u, uint32_t c, uint32_t v,
+                                             uint32_t *err) {
+  const uint64_t key = ((uint64_t)u << 32) | c;
+  uint64_t slot = mix64(key) & g.mask;
+  for (uint64_t probe = 0; probe <= g.mask; ++probe) {
+    uint64_t *ek = g.keys + 2 * slot;
+    const uint64_t cur = atomicCAS((unsigned long long *)ek, (unsigned long long)kEmpty,
+                                   (unsigned long long)key);
+    if (cur == kEmpty) {
+      ek[1] = v;
+      return;
+    }
+    slot = (slot + 1) & g.mask;
+  }
+  atomicExch(err, kDevRange);
+}
 
-// Level d: inserter p creates or finds its depth-(d+1) node; linker p, if
-// pattern p created its depth-d node one level earlier, computes that node's
-// failure link, output link and match total (all shallower nodes and all
-// depth-d nodes exist after the previous barrier).
-__global__ void __launch_bounds__(kBuildThreads) k_ac_build(BuildArgs a) {
-  const uint32_t half = gridDim.x * blockDim.x / 2;
-  const uint32_t gt0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool inserter = gt0 < half;
-  const uint32_t gt = inserter ? gt0 : gt0 - half;
-  const uint32_t root = a.root;
-  for (uint32_t d = 0; d <= a.maxlen; ++d) {
-    const int par = d & 1;
-    for (uint32_t p = gt; p < a.P; p += half) {
-      const uint32_t L = a.plen[p];
-      if (inserter) {
-        if (d >= L) continue;
-        const uint32_t u = d ? a.cur[par][p] : root;
-        const uint32_t c = a.psym[a.pstart[p] + d];
-        const uint64_t key = ((uint64_t)u << 32) | c;
-        uint64_t slot = mix64(key) & a.g.mask;
-        uint32_t v = kNil;
-        uint8_t made = 0;
-        for (uint64_t probe = 0; probe <= a.g.mask; ++probe) {
-          uint64_t *ek = a.g.keys + 2 * slot;
-          uint64_t cur = *(volatile uint64_t *)ek;
-          if (cur == kEmpty) {
-            cur = atomicCAS((unsigned long long *)ek, (unsigned long long)kEmpty,
-                            (unsigned long long)key);
-            if (cur == kEmpty) {  // this pattern creates the node
-              v = (uint32_t)slot;
-              made = 1;
-              ek[1] = v;
-              a.parent[v] = u;
-              a.nsym[v] = c;
-              break;
-            }
+// Node id of the pattern prefix of length d shared with sorted start j.
+__device__ __forceinline__ uint32_t node_of(const NodeArgs &a, uint32_t j, uint32_t d) {
+  return a.tstart[a.sp[rep_of(a.S, j, d)]] + d - 1;
+}
+
+// One warp per pattern, one lane per depth d = 1 .. len + 1 (len + 1 is the
+// separator after the pattern).  A depth-d prefix that is its own node gets
+// its failure link, and the branch edge into it when it hangs off another
+// pattern's node; the pattern's end node counts one more pattern end.
+__global__ void k_ac_nodes(NodeArgs a) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.P; i += warps) {
+    const uint32_t S = a.tstart[i], len = a.plen[i], j = a.jpos[i];
+    const uint32_t sl = a.S.lev[0][j];
+    for (uint32_t d = lane + 1; d <= len + 1; d += 32) {
+      const uint32_t v = S + d - 1;
+      uint32_t f = a.root;
+      if (d <= len && d > sl) {
+        const uint32_t e = S + d;
+        if (d >= 2 && a.reach[e - 1] >= e) {
+          uint32_t lo = S + 1, hi = e - 1;  // first q in (S, e) with reach >= e
+          while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo) >> 1);
+            if (a.reach[mid] >= e) hi = mid;
+            else lo = mid + 1;
           }
-          if (cur == key) {
-            v = (uint32_t)slot;
-            break;
+          const uint32_t fd = e - lo, k = a.rank[lo];
+          uint32_t cnt = 0, hi2 = a.P;  // starts before SA index k
+          while (cnt < hi2) {
+            const uint32_t mid = (cnt + hi2) >> 1;
+            if (a.sr[mid] < k) cnt = mid + 1;
+            else hi2 = mid;
           }
-          slot = (slot + 1) & a.g.mask;
-        }
-        if (v == kNil) {
-          atomicExch(a.err, kDevRange);
-          continue;
-        }
-        a.cur[par ^ 1][p] = v;
-        a.made[par ^ 1][p] = made;
-        if (d + 1 == L) {
-          a.end_node[p] = v;
-          atomicAdd(&a.own[v], 1u);
-        }
-      } else {
-        if (d == 0 || d > L || !a.made[par][p]) continue;
-        const uint32_t v = a.cur[par][p];
-        uint32_t f = root;
-        if (d > 1) {
-          const uint32_t c = a.nsym[v];
-          uint32_t w = a.fail[a.parent[v]];
-          while (true) {
-            const uint32_t x = goto_lookup(a.g, w, c);
-            if (x != kNil) {
-              f = x;
-              break;
-            }
-            if (w == root) break;
-            w = a.fail[w];
+          const uint32_t jj = (a.left[k] >= fd) ? cnt - 1 : cnt;
+          if (jj >= a.P) {
+            atomicExch(a.err, kDevRange);
+          } else {
+            f = node_of(a, jj, fd);
           }
         }
-        a.fail[v] = f;
-        // total[f] = own[f] + total[outl[f]], so whichever of f and outl[f]
-        // is v's output link, the matches reported down it number total[f]
-        const uint32_t of = a.own[f];
-        a.outl[v] = (f != root && of != 0) ? f : a.outl[f];
-        a.total[v] = a.own[v] + a.total[f];
+        if (d == sl + 1) {
+          const uint32_t parent = d == 1 ? a.root : node_of(a, j, d - 1);
+          table_insert(a.g, parent, a.tsym[v], v, a.err);
+        }
+      }
+      a.fail[v] = f;
+      if (d == len) {
+        const uint32_t en = node_of(a, j, len);
+        a.end_node[i] = en;
+        atomicAdd(&a.own[en], 1u);
       }
     }
-    grid_sync(a.bar, a.err);
-    if (*(volatile uint32_t *)a.err != kDevOk) return;
+  }
+}
+
+// Pointer jumping along failure links, in place.  w[v] = (pointer << 32) |
+// sum of own over the chain from v up to the pointer (exclusive); jl[v] =
+// the first node with own > 0 found so far on the chain after v.  Every
+// value read is a valid state of its owner, so a round may see another
+// node's update of the same round.  The last round writes the totals and
+// output links.
+__global__ void k_ac_jump(uint64_t *w, uint32_t *jl, const uint32_t *__restrict__ own, uint32_t nodes,
+                          uint32_t root, int last, uint32_t *total, uint32_t *outl, uint32_t *err) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nodes; v += gridDim.x * blockDim.x) {
+    uint64_t x = w[v];
+    uint32_t p = (uint32_t)(x >> 32);
+    if (p != root) {
+      const uint64_t y = *(volatile uint64_t *)&w[p];
+      x = (y & 0xffffffff00000000ull) | (uint32_t)((uint32_t)x + (uint32_t)y);
+      w[v] = x;
+      p = (uint32_t)(x >> 32);
+    }
+    uint32_t o = jl[v];
+    if (o != root && own[o] == 0) {
+      o = *(volatile uint32_t *)&jl[o];
+      jl[v] = o;
+    }
+    if (last) {
+      if (p != root || (o != root && own[o] == 0)) atomicExch(err, kDevRange);
+      total[v] = (uint32_t)x;
+      outl[v] = o;
+    }
+  }
+}
+
+__global__ void k_jump_init(const uint32_t *__restrict__ fail, const uint32_t *__restrict__ own,
+                            uint32_t nodes, uint32_t root, uint64_t *w, uint32_t *jl) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nodes; v += gridDim.x * blockDim.x) {
+    const uint32_t f = v == root ? root : fail[v];
+    w[v] = ((uint64_t)f << 32) | own[v];
+    jl[v] = f;
   }
 }
 
@@ -308,29 +507,34 @@ __global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint
 // One goto probe or one failure step per loop iteration, so that the lanes
 // of a warp advance through their chunks independently instead of waiting at
 // every token for the lane with the longest failure chain.
+struct Automaton {
+  const uint32_t *tsym;
+  Table g;
+  const uint32_t *fail;
+  uint32_t root;
+};
 
 // Pass A1: chunk t = positions [t*chunk, (t+1)*chunk) from the root state.
 // Chunk 0 is exact; the others may start in the wrong state.
-__global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Table g,
-                            const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out,
-                            uint32_t *__restrict__ end_state) {
+__global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
+                            uint32_t *__restrict__ state_out, uint32_t *__restrict__ end_state) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
   const uint64_t ce = min(n, cs + chunk);
-  const uint32_t root = (uint32_t)(g.mask + 1);
+  const uint32_t root = A.root;
   uint32_t state = root, cur = root;  // cur: where the transition for x is being looked up
   uint64_t x = cs;
   uint32_t c = ssym[x];
   while (x < ce) {
-    const uint32_t nx = goto_lookup(g, cur, c);
+    const uint32_t nx = ac_goto(A.tsym, A.g, cur, c, root);
     if (nx != kNil || cur == root) {
       state = nx != kNil ? nx : root;
       state_out[x] = state;
       cur = state;
       if (++x < ce) c = ssym[x];
     } else {
-      cur = fail[cur];
+      cur = A.fail[cur];
     }
   }
   end_state[t] = state;
@@ -341,10 +545,9 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
 // (the automaton is deterministic, so the rest of the chunk already agrees).
 // After k passes chunks 0..k are exact; the host stops when no end state
 // changed.
-__global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Table g,
-                         const uint32_t *__restrict__ fail, uint32_t *__restrict__ state_out,
-                         const uint32_t *__restrict__ end_in, uint32_t *__restrict__ end_out,
-                         uint32_t *changed) {
+__global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
+                         uint32_t *__restrict__ state_out, const uint32_t *__restrict__ end_in,
+                         uint32_t *__restrict__ end_out, uint32_t *changed) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
@@ -353,12 +556,12 @@ __global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t
     return;
   }
   const uint64_t ce = min(n, cs + chunk);
-  const uint32_t root = (uint32_t)(g.mask + 1);
+  const uint32_t root = A.root;
   uint32_t state = end_in[t - 1], cur = state;
   uint64_t x = cs;
   uint32_t c = ssym[x];
   while (x < ce) {
-    const uint32_t nx = goto_lookup(g, cur, c);
+    const uint32_t nx = ac_goto(A.tsym, A.g, cur, c, root);
     if (nx != kNil || cur == root) {
       state = nx != kNil ? nx : root;
       if (state_out[x] == state) {
@@ -369,7 +572,7 @@ __global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t
       cur = state;
       if (++x < ce) c = ssym[x];
     } else {
-      cur = fail[cur];
+      cur = A.fail[cur];
     }
   }
   end_out[t] = state;
@@ -429,7 +632,7 @@ __global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     const uint32_t s0 = state[x];
     uint64_t o = off[x];
-    uint32_t v = own[s0] != 0 ? s0 : outl[s0];
+    uint32_t v = s0 != root && own[s0] != 0 ? s0 : outl[s0];
     while (v != root) {
       const uint32_t k0 = end_first[v], k1 = k0 + own[v];
       for (uint32_t k = k0; k < k1; ++k) {
@@ -449,29 +652,73 @@ inline int grid_for(uint64_t n, int threads, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
-int g_build_blocks = 0;  // most co-resident blocks of k_ac_build for a cooperative launch
-
 }  // namespace
 
 int match_init(int sms) {
-  // The level barrier's cost grows with the number of arriving blocks, so
-  // launches use no more blocks than the pattern count needs.
-  int per_sm = 0;
-  APO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ac_build, kBuildThreads, 0));
-  g_build_blocks = std::max(1, per_sm * sms);
+  (void)sms;
   return APO_OK;
 }
 
-size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t extent) {
-  uint64_t tbl = 1;
-  while (tbl < 2 * (total_tokens + 1)) tbl <<= 1;
-  uint64_t dct = 1;
-  while (dct < 2 * (extent + 1)) dct <<= 1;
-  const uint64_t N = tbl + 1;
-  const uint64_t chunks = n / 32 + 2;
-  return tbl * 16 + dct * 12 + N * 4 * 8 + P * 64 + (extent + n) * 4 + n * 8 + chunks * 8 +
-         64 * 256;
+size_t suffix_workspace_bytes(uint64_t n);
+
+namespace {
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t t = 1;
+  while (t < x) t <<= 1;
+  return t;
 }
+int sa_levels(uint64_t maxlen) { return bits_for(maxlen + 1) + 3; }
+}  // namespace
+
+size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t extent,
+                             uint64_t maxlen) {
+  const uint64_t N = total_tokens + P;  // pattern text with separators
+  const uint64_t tbl = pow2_at_least(2 * (P + 1));
+  const uint64_t dct = pow2_at_least(2 * (extent + 1));
+  const uint64_t chunks = n / 32 + 2;
+  const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
+  return suffix_workspace_bytes(N) + (uint64_t)sa_levels(maxlen) * N * 4 +
+         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + 2) * (4 + 4 + 8 + 4 + 4 + 4 + 4) +
+         tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + chunks * 8 +
+         96 * 256;
+}
+
+namespace {
+
+// Launches counted under the "ac." scope while alive.
+struct ScopeGuard {
+  apo_ctx *c;
+  int prev;
+  explicit ScopeGuard(apo_ctx *c_) : c(c_), prev(c_->prof.scope) { c->prof.scope = 1; }
+  ~ScopeGuard() { c->prof.scope = prev; }
+};
+
+// Exclusive prefix of plen[p] + 1 (pattern p's first position in T).
+struct SrcPlen {
+  const uint32_t *plen;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const { return plen[k] + 1; }
+};
+struct DstTstart {
+  const uint32_t *plen;
+  uint32_t *out;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const { out[k] = v - plen[k] - 1; }
+};
+
+template <bool kReverse, class Src, class Op, class Dst>
+int seg_scan(apo_ctx *c, Src src, Dst dst, uint32_t n, Op op, uint32_t ident, cudaStream_t s) {
+  if (n == 0) return APO_OK;
+  const int tiles = ceil_div(n, kGTile);
+  APO_TRY(ensure_lookback(c, tiles));
+  uint32_t *ctr = c->ps.counters + kCtrMisc + kMiscCompactTiles;
+  APO_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), s));
+  Launch lp_(c, kKSegScan, n, s);
+  k_seg_scan<kReverse><<<tiles, kGT, 0, s>>>(src, dst, n, op, ident, c->ps.lookback, ctr, next_epoch(c),
+                                             c->ps.err);
+  APO_CUDA_TRY(cudaGetLastError());
+  return APO_OK;
+}
+
+}  // namespace
 
 int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint64_t n,
                    uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
@@ -507,39 +754,58 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     extent = c->host_pinned[1];
     memcpy(&total, c->host_pinned + 2, 8);
   }
-  if (total >= 0xffffffffull || extent >= 0xffffffffull) {
-    set_error("match_candidates: more than 2^32 - 1 pattern tokens");
+  // T positions and reach values live in 31 bits; dictionary slots below 2^31
+  if (total + P >= 0x7fffffffull || extent >= (1ull << 30)) {
+    set_error("match_candidates: at most 2^30 pattern source tokens and 2^31 - 1 pattern tokens "
+              "plus patterns");
     return APO_EINVAL;
   }
-  APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent)));
-  const uint64_t N0 = total + 1;  // node bound (root included)
-  uint64_t tbl = 1;
-  while (tbl < 2 * N0) tbl <<= 1;
-  const uint64_t N = tbl + 1;     // node ids are goto slots; the root is `tbl`
-  const uint32_t root = (uint32_t)tbl;
+  APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent, maxlen)));
+  const uint32_t N = (uint32_t)(total + P);  // pattern text with separators
+  const uint32_t root = N;                   // node ids are T positions; the root is N
+  const uint64_t tbl = pow2_at_least(2 * (P + 1));
+  const uint64_t dct = pow2_at_least(2 * (extent + 1));
+  const int levels = sa_levels(maxlen);
+  const int nsparse = std::max(1, bits_for(P));
 
-  Table g;
-  g.keys = c->arena.take_n<uint64_t>(2 * tbl);
-  g.mask = tbl - 1;
+  Table g{c->arena.take_n<uint64_t>(2 * tbl), tbl - 1};
+  Dict d{c->arena.take_n<uint64_t>(dct), dct - 1};
   uint32_t *pbuf = pp->pat_off ? c->arena.take_n<uint32_t>(2 * (size_t)P) : nullptr;
-  uint32_t *parent = c->arena.take_n<uint32_t>(N);
-  uint32_t *nsym = c->arena.take_n<uint32_t>(N);
-  uint32_t *fail = c->arena.take_n<uint32_t>(N);
-  uint32_t *outl = c->arena.take_n<uint32_t>(N);
-  uint32_t *own = c->arena.take_n<uint32_t>(N);
-  uint32_t *mtotal = c->arena.take_n<uint32_t>(N);
-  uint32_t *end_first = c->arena.take_n<uint32_t>(N);
-  uint32_t *cur = c->arena.take_n<uint32_t>(2 * (size_t)P);
-  uint8_t *made = c->arena.take_n<uint8_t>(2 * (size_t)P);
+  uint32_t *tstart = c->arena.take_n<uint32_t>(P);
+  uint32_t *tsym = c->arena.take_n<uint32_t>((size_t)N + 2);
+  uint64_t *tkey = c->arena.take_n<uint64_t>(N);
+  uint32_t *lcp = c->arena.take_n<uint32_t>(N);
+  uint8_t *is_start = c->arena.take_n<uint8_t>(N);
+  uint32_t *left = c->arena.take_n<uint32_t>(N);
+  uint32_t *right = c->arena.take_n<uint32_t>(N);
+  uint32_t *reach = c->arena.take_n<uint32_t>(N);
+  uint32_t *fail = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *own = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint64_t *wj = c->arena.take_n<uint64_t>((size_t)N + 1);
+  uint32_t *jl = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *mtotal = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *outl = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *end_first = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *sr = c->arena.take_n<uint32_t>(P);
+  uint32_t *jpos = c->arena.take_n<uint32_t>(P);
   uint32_t *end_node = c->arena.take_n<uint32_t>(P);
-  SortBuffers b;
-  b.keys[0] = c->arena.take_n<uint64_t>(P);
-  b.keys[1] = c->arena.take_n<uint64_t>(P);
-  b.vals[0] = c->arena.take_n<uint32_t>(P);
-  b.vals[1] = c->arena.take_n<uint32_t>(P);
-  if (!g.keys || (pp->pat_off && !pbuf) || !parent || !nsym || !fail || !outl || !own ||
-      !mtotal || !end_first || !cur || !made || !end_node || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
-      !b.vals[1]) {
+  uint32_t *sparse = c->arena.take_n<uint32_t>((size_t)nsparse * P);
+  SuffixState st;
+  st.n = N;
+  st.sa = c->arena.take_n<uint32_t>(N);
+  st.rank = c->arena.take_n<uint32_t>(N);
+  uint32_t *snap_base = c->arena.take_n<uint32_t>((size_t)levels * N);
+  SortBuffers b, be;
+  for (SortBuffers *x : {&b, &be}) {
+    x->keys[0] = c->arena.take_n<uint64_t>(P);
+    x->keys[1] = c->arena.take_n<uint64_t>(P);
+    x->vals[0] = c->arena.take_n<uint32_t>(P);
+    x->vals[1] = c->arena.take_n<uint32_t>(P);
+  }
+  if (!g.keys || !d.keys || (pp->pat_off && !pbuf) || !tstart || !tsym || !tkey || !lcp || !is_start ||
+      !left || !right || !reach || !fail || !own || !wj || !jl || !mtotal || !outl || !end_first || !sr ||
+      !jpos || !end_node || !sparse || !st.sa || !st.rank || !snap_base || !b.keys[0] || !b.keys[1] ||
+      !b.vals[0] || !b.vals[1] || !be.keys[0] || !be.keys[1] || !be.vals[0] || !be.vals[1]) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
   }
@@ -554,107 +820,152 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     pstart = pbuf;
     plen = pbuf + P;
   }
-  {  // every entry: key = empty, value = 0
-    Launch lp_(c, kKDepthKeys, tbl, s);
-    k_table_init<<<grid_for(tbl, 256, sms), 256, 0, s>>>(g.keys, tbl);
-  }
-  APO_CUDA_TRY(cudaMemsetAsync(own, 0, N * sizeof(uint32_t), s));
-  {  // the root fails to itself, has no output link and reports nothing
-    const uint32_t rv[3] = {root, root, 0u};
-    APO_CUDA_TRY(cudaMemcpyAsync(fail + root, &rv[0], 4, cudaMemcpyHostToDevice, s));
-    APO_CUDA_TRY(cudaMemcpyAsync(outl + root, &rv[1], 4, cudaMemcpyHostToDevice, s));
-    APO_CUDA_TRY(cudaMemcpyAsync(mtotal + root, &rv[2], 4, cudaMemcpyHostToDevice, s));
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-  }
 
-  // symbols of the pattern source and of the stream
-  const uint32_t *psym = nullptr, *ssym = nullptr;
-  if (tb == 4) {
-    psym = static_cast<const uint32_t *>(pp->tokens);
-    ssym = static_cast<const uint32_t *>(stream);
-  } else {
-    uint64_t dct = 1;
-    while (dct < 2 * (extent + 1)) dct <<= 1;
-    Dict d;
-    d.keys = c->arena.take_n<uint64_t>(dct);
-    d.mask = dct - 1;
-    const bool same = pp->tokens == stream && n >= extent;
-    uint32_t *ps = c->arena.take_n<uint32_t>(std::max<uint64_t>(same ? n : extent, 1));
-    uint32_t *ss = same ? ps : c->arena.take_n<uint32_t>(std::max<uint64_t>(n, 1));
-    if (!d.keys || !ps || !ss) return APO_ENOMEM;
-    APO_CUDA_TRY(cudaMemsetAsync(d.keys, 0xff, dct * sizeof(uint64_t), s));
-    const uint64_t *pt = static_cast<const uint64_t *>(pp->tokens);
-    {
-      Launch lp_(c, kKU64Keys, extent, s);
-      k_dict_insert<<<grid_for(extent, 256, sms), 256, 0, s>>>(pt, extent, d);
-    }
-    {
-      Launch lp_(c, kKUnique, same ? n : extent, s);
-      k_dict_map<<<grid_for(same ? n : extent, 256, sms), 256, 0, s>>>(pt, same ? n : extent, d, ps);
-    }
-    if (!same) {
-      Launch lp_(c, kKUnique, n, s);
-      k_dict_map<<<grid_for(n, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(stream), n, d, ss);
-    }
-    psym = ps;
-    ssym = ss;
-  }
-
-  // trie, failure / output links and match totals, level by level
-  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMatchCount, 0, 3 * sizeof(uint32_t), s));
+  // symbols: the dictionary of pattern tokens, the pattern text, the stream
+  APO_CUDA_TRY(cudaMemsetAsync(d.keys, 0xff, dct * sizeof(uint64_t), s));
+  uint32_t *ssym = c->arena.take_n<uint32_t>(std::max<uint64_t>(n, 1));
+  if (!ssym) return APO_ENOMEM;
+  APO_TRY(seg_scan<false>(c, SrcPlen{plen}, DstTstart{plen, tstart}, P, OpSum(), 0u, s));
   {
-    BuildArgs a;
-    a.psym = psym;
-    a.pstart = pstart;
-    a.plen = plen;
-    a.P = P;
-    a.maxlen = (uint32_t)maxlen;
-    a.g = g;
-    a.root = root;
-    a.cur[0] = cur;
-    a.cur[1] = cur + P;
-    a.made[0] = made;
-    a.made[1] = made + P;
-    a.parent = parent;
-    a.nsym = nsym;
-    a.fail = fail;
-    a.outl = outl;
-    a.own = own;
-    a.total = mtotal;
-    a.end_node = end_node;
-    a.bar.count = misc + kMiscMatchCount + 1;
-    a.bar.gen = misc + kMiscMatchCount + 2;
-    a.err = c->ps.err;
-    void *args[] = {&a};
-    Launch lp_(c, kKTrieInsert, total, s);
-    // one inserter and one linker thread per pattern where possible, at least
-    // 32 blocks, at most what is co-resident (larger sets loop)
-    const int blocks = std::min<int>(g_build_blocks, std::max<int>(32, ceil_div(2ull * P, kBuildThreads)));
-    APO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_ac_build, blocks, kBuildThreads, args, 0, s));
+    Launch lp_(c, kKDictInsert, extent, s);
+    if (tb == 4)
+      k_dict_insert<<<grid_for(extent, 256, sms), 256, 0, s>>>(static_cast<const uint32_t *>(pp->tokens),
+                                                                extent, d);
+    else
+      k_dict_insert<<<grid_for(extent, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens),
+                                                                extent, d);
+  }
+  {
+    Launch lp_(c, kKPatLayout, N, s);
+    const int blocks = std::max(1, std::min(ceil_div(P, 8), sms * 16));
+    if (tb == 4)
+      k_pat_layout<<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(pp->tokens), pstart, plen, tstart,
+                                          P, N, d, tsym, tkey);
+    else
+      k_pat_layout<<<blocks, 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens), pstart, plen, tstart,
+                                          P, N, d, tsym, tkey);
+  }
+  if (n) {
+    Launch lp_(c, kKDictMap, n, s);
+    if (tb == 4)
+      k_dict_map<<<grid_for(n, 256, sms), 256, 0, s>>>(static_cast<const uint32_t *>(stream), n, d, ssym);
+    else
+      k_dict_map<<<grid_for(n, 256, sms), 256, 0, s>>>(static_cast<const uint64_t *>(stream), n, d, ssym);
   }
   APO_CUDA_TRY(cudaGetLastError());
-  // pattern ids grouped by end node
+
+  // suffix array and LCP of the pattern text
   {
-    Launch lp_(c, kKEndPairs, P, s);
-    k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, b.keys[0], b.vals[0]);
+    ScopeGuard scope(c);
+    uint32_t *snaps[64];
+    for (int k = 0; k < levels; ++k) snaps[k] = snap_base + (size_t)k * N;
+    st.snaps = snaps;
+    uint32_t rounds = 0;
+    APO_TRY(build_suffix_array(c, tkey, 8, N, st, levels, &rounds, s));
+    APO_TRY(build_lcp(c, tkey, 8, st, lcp, s));
   }
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
+
+  // pattern starts in suffix order
+  {
+    Launch lp_(c, kKStarts, P, s);
+    k_start_keys<<<grid_for(P, 256, sms), 256, 0, s>>>(tstart, st.rank, P, b.keys[0], b.vals[0]);
+  }
   b.cur = 0;
   {
     int places[8];
-    const int np = plan_digits(0, bits_for(root), places, 0);
+    const int np = plan_digits(0, bits_for(N - 1), places, 0);
     APO_TRY(radix_sort_pairs(c, b, P, places, np, s));
   }
-  const uint64_t *ek = b.keys[b.cur];
-  const uint32_t *ev = b.vals[b.cur];
+  const uint32_t *sp = b.vals[b.cur];
+  APO_CUDA_TRY(cudaMemsetAsync(is_start, 0, N, s));
+  {
+    Launch lp_(c, kKStarts, P, s);
+    k_start_mark<<<grid_for(P, 256, sms), 256, 0, s>>>(b.keys[b.cur], sp, P, sr, jpos, is_start);
+  }
+  // lcp with the nearest pattern start on each side in suffix order, the
+  // start-to-start lcps, and the running maximum of the reach over T
+  APO_TRY(seg_scan<false>(c, SrcLeft{lcp, is_start}, DstFlagged{left}, N, OpSegMin(), kSegMinId, s));
+  {
+    Launch lp_(c, kKStarts, P, s);
+    k_slcp<<<grid_for(P, 256, sms), 256, 0, s>>>(sr, left, P, sparse);
+  }
+  APO_TRY(seg_scan<true>(c, SrcRight{lcp, is_start, N}, DstFlagged{right}, N, OpSegMin(), kSegMinId, s));
+  APO_TRY(seg_scan<false>(c, SrcReach{tkey, st.rank, left, right, P}, DstValue{reach}, N, OpSegMax(),
+                          kSegMaxId, s));
+  Sparse S;
+  S.nlev = nsparse;
+  S.lev[0] = sparse;
+  for (int l = 1; l < nsparse; ++l) {
+    uint32_t *lv = sparse + (size_t)l * P;
+    Launch lp_(c, kKSparse, P, s);
+    k_sparse_level<<<grid_for(P, 256, sms), 256, 0, s>>>(S.lev[l - 1], P, 1u << (l - 1), lv);
+    S.lev[l] = lv;
+  }
+
+  // nodes: failure links, branch edges, pattern ends
+  {
+    Launch lp_(c, kKTableInit, tbl, s);
+    k_table_init<<<grid_for(tbl, 256, sms), 256, 0, s>>>(g.keys, tbl);
+  }
+  APO_CUDA_TRY(cudaMemsetAsync(own, 0, ((size_t)N + 1) * sizeof(uint32_t), s));
+  {
+    NodeArgs a;
+    a.tstart = tstart;
+    a.plen = plen;
+    a.tsym = tsym;
+    a.jpos = jpos;
+    a.sp = sp;
+    a.sr = sr;
+    a.rank = st.rank;
+    a.left = left;
+    a.reach = reach;
+    a.S = S;
+    a.P = P;
+    a.root = root;
+    a.g = g;
+    a.fail = fail;
+    a.own = own;
+    a.end_node = end_node;
+    a.err = c->ps.err;
+    Launch lp_(c, kKAcNodes, N, s);
+    k_ac_nodes<<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
+  }
+  // match totals and output links
+  {
+    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
+    k_jump_init<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(fail, own, N + 1, root, wj, jl);
+  }
+  const int jumps = bits_for(maxlen) + 1;
+  for (int r = 0; r < jumps; ++r) {
+    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
+    k_ac_jump<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(wj, jl, own, N + 1, root, r == jumps - 1,
+                                                                  mtotal, outl, c->ps.err);
+  }
+  // pattern ids grouped by end node
+  {
+    Launch lp_(c, kKEndPairs, P, s);
+    k_end_pairs<<<grid_for(P, 256, sms), 256, 0, s>>>(end_node, P, be.keys[0], be.vals[0]);
+  }
+  be.cur = 0;
+  {
+    int places[8];
+    const int np = plan_digits(0, bits_for(root), places, 0);
+    APO_TRY(radix_sort_pairs(c, be, P, places, np, s));
+  }
+  const uint64_t *ek = be.keys[be.cur];
+  const uint32_t *ev = be.vals[be.cur];
   {
     Launch lp_(c, kKMarkEnds, P, s);
     k_mark_ends<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, end_first);
   }
-  if (n == 0) return APO_OK;
+  APO_CUDA_TRY(cudaGetLastError());
+  if (n == 0) {
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    return check_device_error(c, s);
+  }
 
   // pass A: states, chunked without a halo, then repaired until stable
+  Automaton A{tsym, g, fail, root};
   uint32_t *state = c->arena.take_n<uint32_t>(n);
   uint32_t *off = c->arena.take_n<uint32_t>(n);
   // short chunks: a chunk is a chain of dependent lookups, so its length is
@@ -664,14 +975,14 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *ends[2] = {c->arena.take_n<uint32_t>(nch), c->arena.take_n<uint32_t>(nch)};
   if (!state || !off || !ends[0] || !ends[1]) return APO_ENOMEM;
   {
-    Launch lp_(c, kKAcMatch, n, s);
-    k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, g, fail, state, ends[0]);
+    Launch lp_(c, kKAcStates, n, s);
+    k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state, ends[0]);
   }
   for (uint64_t pass = 0, e = 0; pass < nch; ++pass, e ^= 1) {
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     {
-      Launch lp_(c, kKFailLevel, n, s);
-      k_ac_fix<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, g, fail, state, ends[e], ends[e ^ 1],
+      Launch lp_(c, kKAcFix, n, s);
+      k_ac_fix<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state, ends[e], ends[e ^ 1],
                                                    misc + kMiscAccCount);
     }
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));

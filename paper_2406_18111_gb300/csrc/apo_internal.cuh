@@ -82,16 +82,23 @@ struct Persistent {
 enum KernelId : int {
   kKHash, kKInitKeys, kKKeyOr, kKRsHist, kKRsOffsets, kKRsPass, kKRefresh, kKPack, kKPhi,
   kKPlcp, kKLcpPerm, kKMin32, kKMax, kKCandGen, kKCompact, kKCandGather, kKGreedy, kKTraces,
-  kKSelOut, kKTrieInsert, kKDepthKeys, kKEndPairs, kKMarkEnds, kKFailLevel, kKAcMatch,
-  kKAcFill, kKU64Keys, kKUnique, kKSlices, kKMatchOffsets, kKOwn, kKCount
+  kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
+  kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
+  kKAcNodes, kKAcJump, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
+// Launch records are kept per scope: scope 0 is the call's own path; scope 1
+// holds the suffix array and LCP of the pattern text built while matching
+// (reported with an "ac." prefix), so that the two never mix.
+constexpr int kScopes = 2;
+
 struct Profiler {
   bool timing = false;
-  uint64_t launches[kKCount] = {};
-  uint64_t units[kKCount] = {};
-  double ms[kKCount] = {};
+  int scope = 0;
+  uint64_t launches[kScopes * kKCount] = {};
+  uint64_t units[kScopes * kKCount] = {};
+  double ms[kScopes * kKCount] = {};
   struct Pending {
     int id;
     cudaEvent_t a, b;

@@ -11,7 +11,6 @@ namespace apo {
 
 size_t suffix_workspace_bytes(uint64_t n);
 size_t repeats_workspace_bytes(uint64_t n, uint64_t windows);
-size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t cap);
 int suffix_init();
 int repeats_init(int smem_optin);
 int match_init(int sms);
@@ -66,8 +65,9 @@ int ensure_lookback(apo_ctx *c, size_t words) {
 const char *const kKernelNames[kKCount] = {
     "hash_tasks", "init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
-    "traces", "sel_out", "ac_build", "table_init", "end_pairs", "mark_ends", "ac_fix",
-    "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "own_counts"};
+    "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
+    "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
+    "starts", "sparse", "ac_nodes", "ac_jump"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -98,9 +98,10 @@ void Profiler::release() {
   pool.clear();
 }
 
-Launch::Launch(apo_ctx *c, int id, uint64_t units, cudaStream_t s) : c_(c), id_(id), s_(s) {
-  c->prof.launches[id] += 1;
-  c->prof.units[id] += units;
+Launch::Launch(apo_ctx *c, int id, uint64_t units, cudaStream_t s)
+    : c_(c), id_(id + c->prof.scope * kKCount), s_(s) {
+  c->prof.launches[id_] += 1;
+  c->prof.units[id_] += units;
   if (c->prof.timing) {
     if (c->prof.pending.size() > 8192) c->prof.resolve();
     a_ = c->prof.get();
@@ -424,7 +425,7 @@ int apo_profile_reset(apo_ctx *c) {
     return APO_EINVAL;
   }
   c->prof.resolve();
-  for (int k = 0; k < kKCount; ++k) {
+  for (int k = 0; k < kScopes * kKCount; ++k) {
     c->prof.launches[k] = 0;
     c->prof.units[k] = 0;
     c->prof.ms[k] = 0;
@@ -434,13 +435,14 @@ int apo_profile_reset(apo_ctx *c) {
 
 int apo_profile_read(apo_ctx *c, int index, char *name, size_t name_cap, uint64_t *launches,
                      double *ms, uint64_t *units) {
-  if (!c || index < 0 || index >= kKCount) {
+  if (!c || index < 0 || index >= kScopes * kKCount) {
     set_error("apo_profile_read: null context or index out of range");
     return APO_EINVAL;
   }
   c->prof.resolve();
   if (name && name_cap) {
-    strncpy(name, kKernelNames[index], name_cap - 1);
+    const std::string nm = std::string(index >= kKCount ? "ac." : "") + kKernelNames[index % kKCount];
+    strncpy(name, nm.c_str(), name_cap - 1);
     name[name_cap - 1] = 0;
   }
   if (launches) *launches = c->prof.launches[index];

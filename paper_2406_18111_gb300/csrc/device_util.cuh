@@ -40,7 +40,8 @@ struct OpMax {
 };
 
 // Combine the published values of tiles t-1, t-2, ... (words at
-// status[j * stride]) until an inclusive one is found.  Bounded: after
+// status[j * stride]) until an inclusive one is found, in index order (the
+// operator need not commute).  Bounded: after
 // kSpinLimit polls of a word that is not ready the wait gives up, records
 // kDevTimeout in *err and returns what it has (the launch's results are then
 // invalid and the host reports APO_ETIMEOUT).
@@ -62,7 +63,7 @@ __device__ uint32_t lb_exclusive(const uint64_t *status, int stride, uint32_t t,
       if (spins > 32) __nanosleep(128);
       continue;
     }
-    acc = op(acc, (uint32_t)w);
+    acc = op((uint32_t)w, acc);  // tile j precedes the tiles already combined
     if (st == kLbInclusive) break;
     --j;
   }
@@ -81,7 +82,7 @@ __device__ __forceinline__ uint32_t warp_inclusive(uint32_t v, Op op) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
-    if (lane >= d) v = op(v, o);
+    if (lane >= d) v = op(o, v);  // lane - d precedes this lane
   }
   return v;
 }
