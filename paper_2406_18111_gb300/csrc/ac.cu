@@ -65,6 +65,7 @@ constexpr uint32_t kNil = 0xffffffffu;  // no node; also the symbol of a token n
 constexpr uint32_t kSep = 0xfffffffeu;  // symbol slot of a pattern separator in T
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kFlag = 0x80000000u;  // segment-start flag of a packed scan value
+constexpr int kTsymPad = 40;            // separators after the pattern text (warp-wide reads)
 
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;
@@ -175,7 +176,7 @@ __global__ void k_pat_layout(const T *__restrict__ tok, const uint32_t *__restri
                              const uint32_t *__restrict__ plen, const uint32_t *__restrict__ tstart,
                              uint32_t P, uint32_t N, Dict d, uint32_t *__restrict__ tsym,
                              uint64_t *__restrict__ tkey) {
-  if (blockIdx.x == 0 && threadIdx.x < 2) tsym[N + threadIdx.x] = kSep;  // past the last separator
+  if (blockIdx.x == 0 && threadIdx.x < kTsymPad) tsym[N + threadIdx.x] = kSep;  // past the text
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < P; p += warps) {
@@ -367,6 +368,7 @@ struct NodeArgs {
   uint32_t P, root;
   Table g;
   uint32_t *fail, *own, *end_node;
+  uint8_t *has_branch;  // [nodes] 1 if a branch-table edge leaves the node
   uint32_t *err;
 };
 
@@ -431,6 +433,7 @@ __global__ void k_ac_nodes(NodeArgs a) {
         if (d == sl + 1) {
           const uint32_t parent = d == 1 ? a.root : node_of(a, j, d - 1);
           table_insert(a.g, parent, a.tsym[v], v, a.err);
+          a.has_branch[parent] = 1;
         }
       }
       a.fail[v] = f;
@@ -447,11 +450,29 @@ __global__ void k_ac_nodes(NodeArgs a) {
 // sum of own over the chain from v up to the pointer (exclusive); jl[v] =
 // the first node with own > 0 found so far on the chain after v.  Every
 // value read is a valid state of its owner, so a round may see another
-// node's update of the same round.  The last round writes the totals and
-// output links.
-__global__ void k_ac_jump(uint64_t *w, uint32_t *jl, const uint32_t *__restrict__ own, uint32_t nodes,
-                          uint32_t root, int last, uint32_t *total, uint32_t *outl, uint32_t *err) {
+// node's update of the same round.  The last round writes the totals, each
+// node's first output record and each record's successor (the record of the
+// output link).
+// Skip links for matching: sk[v] = the first node u on v's failure chain that
+// could have a transition v's own primary symbol cannot rule out, i.e. the
+// root, a node with branch-table edges, or a node whose primary symbol
+// differs from v's.  A failure step is only taken after v's primary edge did
+// not match, so the nodes skipped (no branch edges, the same primary symbol)
+// cannot match either.  sk[u] of a skipped u has the same criterion as sk[v],
+// which makes the jumps composable.
+__global__ void k_ac_jump(uint64_t *w, uint32_t *jl, uint32_t *sk, const uint32_t *__restrict__ own,
+                          const uint32_t *__restrict__ tsym, const uint8_t *__restrict__ has_branch,
+                          uint32_t nodes, uint32_t root, int last, uint32_t *total,
+                          const uint32_t *__restrict__ recidx, uint32_t *firstrec, uint4 *rec, uint32_t *err) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nodes; v += gridDim.x * blockDim.x) {
+    uint32_t u = sk[v];
+    const uint32_t a = v != root ? tsym[v + 1] : kNil;
+    const bool skippable = u != root && !has_branch[u] && tsym[u + 1] == a;
+    if (skippable) {
+      u = *(volatile uint32_t *)&sk[u];
+      sk[v] = u;
+    }
+    if (last && u != root && !has_branch[u] && tsym[u + 1] == a) atomicExch(err, kDevRange);
     uint64_t x = w[v];
     uint32_t p = (uint32_t)(x >> 32);
     if (p != root) {
@@ -468,15 +489,23 @@ __global__ void k_ac_jump(uint64_t *w, uint32_t *jl, const uint32_t *__restrict_
     if (last) {
       if (p != root || (o != root && own[o] == 0)) atomicExch(err, kDevRange);
       total[v] = (uint32_t)x;
-      outl[v] = o;
+      const uint32_t ro = o != root ? recidx[o] : kNil;  // output record of the output link
+      if (v != root && own[v] != 0) {
+        const uint32_t r = recidx[v];
+        rec[r].z = ro;
+        firstrec[v] = r;
+      } else {
+        firstrec[v] = ro;
+      }
     }
   }
 }
 
 __global__ void k_jump_init(const uint32_t *__restrict__ fail, const uint32_t *__restrict__ own,
-                            uint32_t nodes, uint32_t root, uint64_t *w, uint32_t *jl) {
+                            uint32_t nodes, uint32_t root, uint64_t *w, uint32_t *jl, uint32_t *sk) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nodes; v += gridDim.x * blockDim.x) {
     const uint32_t f = v == root ? root : fail[v];
+    sk[v] = f;
     w[v] = ((uint64_t)f << 32) | own[v];
     jl[v] = f;
   }
@@ -498,26 +527,138 @@ __global__ void k_end_pairs(const uint32_t *__restrict__ end_node, uint32_t P, u
   }
 }
 
-__global__ void k_mark_ends(const uint64_t *__restrict__ skeys, uint32_t P, uint32_t *end_first) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x)
-    if (k == 0 || skeys[k] != skeys[k - 1]) end_first[(uint32_t)skeys[k]] = k;
-}
-
-// ---------------------------------------------------------------- match
-// One goto probe or one failure step per loop iteration, so that the lanes
-// of a warp advance through their chunks independently instead of waiting at
-// every token for the lane with the longest failure chain.
-struct Automaton {
-  const uint32_t *tsym;
-  Table g;
-  const uint32_t *fail;
-  uint32_t root;
+// Output records: one per node where patterns end, in node order after the
+// sort of (end node, pattern id): rec = (first sorted index, patterns ending
+// there, next record down the output chain); recidx[node] = its record.
+struct SrcRunStart {
+  const uint64_t *keys;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+    return (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+  }
+};
+struct DstRecord {
+  const uint64_t *keys;
+  const uint32_t *own;
+  uint32_t *recidx;
+  uint4 *rec;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const {
+    if (k == 0 || keys[k] != keys[k - 1]) {
+      const uint32_t node = (uint32_t)keys[k];
+      recidx[node] = v - 1;
+      rec[v - 1] = make_uint4(k, own[node], kNil, 0u);
+    }
+  }
 };
 
-// Pass A1: chunk t = positions [t*chunk, (t+1)*chunk) from the root state.
-// Chunk 0 is exact; the others may start in the wrong state.
+// ---------------------------------------------------------------- match
+// One warp runs the automaton over one chunk.  Along a primary edge the next
+// state is the next position of T, so the warp compares up to 32 stream
+// symbols with the 32 symbols of T after the current state at once and
+// takes the whole agreeing run in one step; a mismatch is settled by one
+// lane with the goto table and the failure chain.
+struct Automaton {
+  const uint32_t *tsym;  // padded with kTsymPad separators past the text
+  Table g;
+  const uint32_t *skip;  // failure steps taken after the primary edge did not match
+  uint32_t root;
+};
+constexpr int kStateWarps = 4;
+
+// Runs positions [x, x1) from state v.  With `recorded`, stops at the first
+// position whose new state equals the state already stored there (the run
+// from there on is the stored one) and returns true.  *v_out: the state after
+// the last position run.
+template <bool kCheck>
+__device__ __forceinline__ bool run_chunk(const uint32_t *__restrict__ ssym, uint64_t x, uint64_t x1,
+                                          uint32_t v, const Automaton &A, uint32_t *__restrict__ state,
+                                          uint32_t *v_out) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t root = A.root;
+  while (x < x1) {
+    uint32_t m = 0;
+    if (v != root) {
+      const uint64_t xi = x + lane;
+      const bool ok = xi < x1 && ssym[xi] == A.tsym[v + 1 + lane];
+      const uint32_t miss = __ballot_sync(0xffffffffu, !ok);
+      m = miss ? (uint32_t)(__ffs(miss) - 1) : 32u;
+    }
+    else {
+      // from the root: positions whose symbol starts no pattern stay at the
+      // root, so the first of the next 32 that does is found at once
+      const uint64_t xi = x + lane;
+      uint32_t r = kNil;
+      if (xi < x1) r = table_lookup(A.g, root, ssym[xi]);
+      const uint32_t hit = __ballot_sync(0xffffffffu, r != kNil || xi >= x1);
+      const uint32_t h = hit ? (uint32_t)(__ffs(hit) - 1) : 32u;  // positions staying at the root
+      if (h > 0) {
+        if (kCheck) {
+          const uint32_t ab = __ballot_sync(0xffffffffu, lane < h && state[xi] == root);
+          if (ab) {
+            const uint32_t first = __ffs(ab) - 1;
+            if (lane < first) state[xi] = root;
+            return true;
+          }
+        }
+        if (lane < h) state[xi] = root;
+        x += h;
+        continue;
+      }
+      // position x leaves the root on its own symbol
+      const uint32_t nv = __shfl_sync(0xffffffffu, r, 0);
+      if (kCheck && __shfl_sync(0xffffffffu, lane == 0 ? state[x] : 0u, 0) == nv) return true;
+      if (lane == 0) state[x] = nv;
+      v = nv;
+      ++x;
+      continue;
+    }
+    if (m > 0) {
+      if (kCheck) {
+        const bool agree = lane < m && state[x + lane] == v + 1 + lane;
+        const uint32_t ab = __ballot_sync(0xffffffffu, agree);
+        if (ab) {
+          const uint32_t first = __ffs(ab) - 1;
+          if (lane < first) state[x + lane] = v + 1 + lane;
+          return true;
+        }
+      }
+      if (lane < m) state[x + lane] = v + 1 + lane;
+      v += m;
+      x += m;
+      continue;
+    }
+    uint32_t nv = root;
+    if (lane == 0) {
+      const uint32_t c = ssym[x];
+      uint32_t cur = v;
+      while (true) {
+        const uint32_t nx = ac_goto(A.tsym, A.g, cur, c, root);
+        if (nx != kNil) {
+          nv = nx;
+          break;
+        }
+        if (cur == root) break;
+        cur = A.skip[cur];
+      }
+      if (kCheck && state[x] == nv) nv = kNil;  // agreement
+      else state[x] = nv;
+    }
+    nv = __shfl_sync(0xffffffffu, nv, 0);
+    if (kCheck && nv == kNil) return true;
+    v = nv;
+    ++x;
+  }
+  *v_out = v;
+  return false;
+}
+
+// Pass A1: chunk t = positions [t*chunk, (t+1)*chunk) from the root state,
+// one lane per chunk (short chunks, many of them: the first pass is mostly
+// short runs and failure steps, which independent lanes overlap best).  One
+// goto probe or one failure step per loop iteration, so that the lanes of a
+// warp advance through their chunks independently.  Chunk 0 is exact; the
+// others may start in the wrong state.
 __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
-                            uint32_t *__restrict__ state_out, uint32_t *__restrict__ end_state) {
+                            uint32_t *__restrict__ state_out) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t cs = t * chunk;
   if (cs >= n) return;
@@ -534,49 +675,40 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
       cur = state;
       if (++x < ce) c = ssym[x];
     } else {
-      cur = A.fail[cur];
+      cur = A.skip[cur];
     }
   }
-  end_state[t] = state;
 }
 
-// Pass A2 (repeated until nothing changes): chunk t restarts from the end
-// state of chunk t-1 and re-runs until its state equals the recorded one
-// (the automaton is deterministic, so the rest of the chunk already agrees).
-// After k passes chunks 0..k are exact; the host stops when no end state
-// changed.
-__global__ void k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
-                         uint32_t *__restrict__ state_out, const uint32_t *__restrict__ end_in,
-                         uint32_t *__restrict__ end_out, uint32_t *changed) {
-  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t cs = t * chunk;
-  if (cs >= n) return;
-  if (t == 0) {
-    end_out[0] = end_in[0];
-    return;
-  }
-  const uint64_t ce = min(n, cs + chunk);
-  const uint32_t root = A.root;
-  uint32_t state = end_in[t - 1], cur = state;
-  uint64_t x = cs;
-  uint32_t c = ssym[x];
-  while (x < ce) {
-    const uint32_t nx = ac_goto(A.tsym, A.g, cur, c, root);
-    if (nx != kNil || cur == root) {
-      state = nx != kNil ? nx : root;
-      if (state_out[x] == state) {
-        end_out[t] = end_in[t];
-        return;
-      }
-      state_out[x] = state;
-      cur = state;
-      if (++x < ce) c = ssym[x];
-    } else {
-      cur = A.fail[cur];
+// Pass A2 (repeated until nothing changes), one warp per group of kGroup
+// consecutive first-pass chunks: the group restarts from the state stored at
+// its predecessor's last position, and each of its chunks re-runs until its
+// state equals the stored one (the rest of that chunk was stored by a
+// continuous run, so it already agrees), then the next chunk continues from
+// the stored end state.  The start state may be read while the predecessor
+// is still rewriting it; then the predecessor's end state changes in this
+// pass and the host runs another.  When no group's end state changes, every
+// group continues its predecessor exactly and all states are exact.
+constexpr int kGroup = 4;
+__global__ void __launch_bounds__(32 * kStateWarps)
+    k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
+             uint32_t *__restrict__ state, uint32_t *changed) {
+  const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t g0 = t * chunk * kGroup;
+  if (g0 >= n) return;
+  const uint64_t ce = min(n, g0 + chunk * kGroup);
+  const uint64_t cs = g0 == 0 ? chunk : g0;  // the first chunk of all is exact
+  if (cs >= ce) return;
+  const uint32_t rec_end = state[ce - 1];
+  uint32_t v = *(volatile uint32_t *)&state[cs - 1];
+  for (uint64_t fs = cs; fs < ce; fs += chunk) {
+    const uint64_t fe = min(ce, fs + chunk);
+    if (run_chunk<true>(ssym, fs, fe, v, A, state, &v)) {
+      __syncwarp();
+      v = state[fe - 1];
     }
   }
-  end_out[t] = state;
-  if (state != end_in[t]) atomicAdd(changed, 1u);
+  if ((threadIdx.x & 31) == 0 && v != rec_end) atomicAdd(changed, 1u);
 }
 
 // Exclusive prefix sum of total[state[x]] over stream positions (the first
@@ -623,26 +755,24 @@ __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restric
 }
 
 // Pass B: the matches of position x, down the output chain from its state
-// (deepest first), ids ascending within a node.
-__global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n,
-                          const uint32_t *__restrict__ off, const uint32_t *__restrict__ own,
-                          const uint32_t *__restrict__ outl, const uint32_t *__restrict__ end_first,
-                          const uint32_t *__restrict__ evals, uint32_t *mend, uint32_t *mid,
-                          uint64_t cap, uint32_t root) {
+// (deepest first), ids ascending within a node.  The chain is walked over
+// the compact output records (one 16-byte load per node that ends patterns).
+__global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n, const uint32_t *__restrict__ off,
+                          const uint32_t *__restrict__ firstrec, const uint4 *__restrict__ rec,
+                          const uint32_t *__restrict__ evals, uint32_t *mend, uint32_t *mid, uint64_t cap) {
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    const uint32_t s0 = state[x];
+    uint32_t r = firstrec[state[x]];
     uint64_t o = off[x];
-    uint32_t v = s0 != root && own[s0] != 0 ? s0 : outl[s0];
-    while (v != root) {
-      const uint32_t k0 = end_first[v], k1 = k0 + own[v];
-      for (uint32_t k = k0; k < k1; ++k) {
+    while (r != kNil) {
+      const uint4 q = rec[r];
+      for (uint32_t k = q.x; k < q.x + q.y; ++k) {
         if (o < cap) {
           mend[o] = x;
           mid[o] = evals[k];
         }
         ++o;
       }
-      v = outl[v];
+      r = q.z;
     }
   }
 }
@@ -675,11 +805,10 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   const uint64_t N = total_tokens + P;  // pattern text with separators
   const uint64_t tbl = pow2_at_least(2 * (P + 1));
   const uint64_t dct = pow2_at_least(2 * (extent + 1));
-  const uint64_t chunks = n / 32 + 2;
-  const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
+    const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
   return suffix_workspace_bytes(N) + (uint64_t)sa_levels(maxlen) * N * 4 +
-         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + 2) * (4 + 4 + 8 + 4 + 4 + 4 + 4) +
-         tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + chunks * 8 +
+         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * 16 +
+         tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 +
          96 * 256;
 }
 
@@ -772,7 +901,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   Dict d{c->arena.take_n<uint64_t>(dct), dct - 1};
   uint32_t *pbuf = pp->pat_off ? c->arena.take_n<uint32_t>(2 * (size_t)P) : nullptr;
   uint32_t *tstart = c->arena.take_n<uint32_t>(P);
-  uint32_t *tsym = c->arena.take_n<uint32_t>((size_t)N + 2);
+  uint32_t *tsym = c->arena.take_n<uint32_t>((size_t)N + kTsymPad);
   uint64_t *tkey = c->arena.take_n<uint64_t>(N);
   uint32_t *lcp = c->arena.take_n<uint32_t>(N);
   uint8_t *is_start = c->arena.take_n<uint8_t>(N);
@@ -784,8 +913,11 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint64_t *wj = c->arena.take_n<uint64_t>((size_t)N + 1);
   uint32_t *jl = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint32_t *mtotal = c->arena.take_n<uint32_t>((size_t)N + 1);
-  uint32_t *outl = c->arena.take_n<uint32_t>((size_t)N + 1);
-  uint32_t *end_first = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *skip = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint8_t *has_branch = c->arena.take_n<uint8_t>((size_t)N + 1);
+  uint32_t *recidx = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint32_t *firstrec = c->arena.take_n<uint32_t>((size_t)N + 1);
+  uint4 *rec = c->arena.take_n<uint4>(P);
   uint32_t *sr = c->arena.take_n<uint32_t>(P);
   uint32_t *jpos = c->arena.take_n<uint32_t>(P);
   uint32_t *end_node = c->arena.take_n<uint32_t>(P);
@@ -803,7 +935,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     x->vals[1] = c->arena.take_n<uint32_t>(P);
   }
   if (!g.keys || !d.keys || (pp->pat_off && !pbuf) || !tstart || !tsym || !tkey || !lcp || !is_start ||
-      !left || !right || !reach || !fail || !own || !wj || !jl || !mtotal || !outl || !end_first || !sr ||
+      !left || !right || !reach || !fail || !own || !wj || !jl || !mtotal || !skip || !has_branch || !recidx || !firstrec || !rec || !sr ||
       !jpos || !end_node || !sparse || !st.sa || !st.rank || !snap_base || !b.keys[0] || !b.keys[1] ||
       !b.vals[0] || !b.vals[1] || !be.keys[0] || !be.keys[1] || !be.vals[0] || !be.vals[1]) {
     set_error("match: workspace too small");
@@ -908,6 +1040,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     k_table_init<<<grid_for(tbl, 256, sms), 256, 0, s>>>(g.keys, tbl);
   }
   APO_CUDA_TRY(cudaMemsetAsync(own, 0, ((size_t)N + 1) * sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(has_branch, 0, (size_t)N + 1, s));
   {
     NodeArgs a;
     a.tstart = tstart;
@@ -926,20 +1059,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.fail = fail;
     a.own = own;
     a.end_node = end_node;
+    a.has_branch = has_branch;
     a.err = c->ps.err;
     Launch lp_(c, kKAcNodes, N, s);
     k_ac_nodes<<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
-  }
-  // match totals and output links
-  {
-    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
-    k_jump_init<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(fail, own, N + 1, root, wj, jl);
-  }
-  const int jumps = bits_for(maxlen) + 1;
-  for (int r = 0; r < jumps; ++r) {
-    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
-    k_ac_jump<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(wj, jl, own, N + 1, root, r == jumps - 1,
-                                                                  mtotal, outl, c->ps.err);
   }
   // pattern ids grouped by end node
   {
@@ -954,9 +1077,18 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   const uint64_t *ek = be.keys[be.cur];
   const uint32_t *ev = be.vals[be.cur];
+  APO_TRY(seg_scan<false>(c, SrcRunStart{ek}, DstRecord{ek, own, recidx, rec}, P, OpSum(), 0u, s));
+  // match totals and output links
   {
-    Launch lp_(c, kKMarkEnds, P, s);
-    k_mark_ends<<<grid_for(P, 256, sms), 256, 0, s>>>(ek, P, end_first);
+    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
+    k_jump_init<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(fail, own, N + 1, root, wj, jl, skip);
+  }
+  const int jumps = bits_for(maxlen) + 1;
+  for (int r = 0; r < jumps; ++r) {
+    Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
+    k_ac_jump<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(wj, jl, skip, own, tsym, has_branch, N + 1,
+                                                                  root, r == jumps - 1, mtotal, recidx,
+                                                                  firstrec, rec, c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
   if (n == 0) {
@@ -965,25 +1097,27 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
 
   // pass A: states, chunked without a halo, then repaired until stable
-  Automaton A{tsym, g, fail, root};
+  Automaton A{tsym, g, skip, root};
   uint32_t *state = c->arena.take_n<uint32_t>(n);
   uint32_t *off = c->arena.take_n<uint32_t>(n);
-  // short chunks: a chunk is a chain of dependent lookups, so its length is
-  // the pass time; repair passes cost little once chunks end in a reset
-  const uint64_t chunk = std::max<uint64_t>(32, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
+  // a chunk per lane in the first pass, about 64 per SM; a repair pass
+  // moves exact states one chunk further
+  // a chunk per lane in the first pass, about 64 per SM; a repair pass moves
+  // exact states one group of chunks further
+  const uint64_t chunk = std::max<uint64_t>(64, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
   const uint64_t nch = (n + chunk - 1) / chunk;
-  uint32_t *ends[2] = {c->arena.take_n<uint32_t>(nch), c->arena.take_n<uint32_t>(nch)};
-  if (!state || !off || !ends[0] || !ends[1]) return APO_ENOMEM;
+  const uint64_t nch2 = (nch + kGroup - 1) / kGroup;
+  if (!state || !off) return APO_ENOMEM;
   {
     Launch lp_(c, kKAcStates, n, s);
-    k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state, ends[0]);
+    k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state);
   }
-  for (uint64_t pass = 0, e = 0; pass < nch; ++pass, e ^= 1) {
+  for (uint64_t pass = 0; pass < nch2; ++pass) {
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     {
       Launch lp_(c, kKAcFix, n, s);
-      k_ac_fix<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state, ends[e], ends[e ^ 1],
-                                                   misc + kMiscAccCount);
+      k_ac_fix<<<ceil_div(nch2, kStateWarps), 32 * kStateWarps, 0, s>>>(ssym, n, chunk, A, state,
+                                                                          misc + kMiscAccCount);
     }
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1011,8 +1145,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   if (total_m) {
     Launch lp_(c, kKAcFill, n, s);
-    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, own, outl, end_first, ev,
-                                                    match_end, match_id, cap, root);
+    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, firstrec, rec, ev, match_end,
+                                                    match_id, cap);
   }
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaStreamSynchronize(s));
