@@ -90,6 +90,13 @@ def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:
     return float(total), a_r
 
 
+def tuning_summary(apo) -> list:
+    """Radix-sort shapes chosen so far: [log2 size class, key bits, threads,
+    pairs per thread, digit bits, trial ms of the chosen / default shape]."""
+    return [[t["size_log2"], t["key_bits"], t["threads"], t["items"], t["digit_bits"],
+             round(t["best_ms"], 4), round(t["default_ms"], 4)] for t in apo.sort_tuning_read()]
+
+
 def sa_lcp_roofline(prof: dict, steps: int, b_alg: float, a_r: list, peak: float, peak_kind: str) -> dict:
     """Algorithmic fraction of the HBM roofline for the SA+LCP path: its
     algorithmic bytes per call over the summed event time of its kernels."""
@@ -119,6 +126,8 @@ def parse():
     ap.add_argument("--lanes", type=int, default=2, help="served: batches in flight")
     ap.add_argument("--no-forms", action="store_true",
                     help="window workload: skip the short batched and served measurements")
+    ap.add_argument("--sort-tuning", type=int, default=0, choices=[0, 1],
+                    help="0: radix-sort shapes timed per size class on first use; 1: default shape only")
     return ap.parse_args()
 
 
@@ -245,6 +254,7 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
     from paper_2406_18111_gb300 import Apo
     dev = torch.device("cuda", local)
     apo = Apo(local)
+    apo.sort_tuning(args.sort_tuning)
     toks, off, _ = W.config3_windows(args.windows, seed0=3 + 100000 * rank)
     t = torch.from_numpy(toks.view(np.int32)).to(dev)
     total = int(off[-1])
@@ -310,7 +320,7 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
                       "form": "one apo_find_repeats call per window, same stream", "steps": plain_steps},
             "batched_over_plain": ms_plain / ms,
             "gpu_launches": n_launch, "roofline": roof, "sa_lcp_roofline": sa_lcp, "clocks": clk,
-            "kernels": kernels})
+            "kernels": kernels, "sort_tuning": tuning_summary(apo)})
     if emit and rank == 0:
         print(json.dumps(out))
     return out
@@ -383,6 +393,7 @@ def run_match(args, rank, world, local, emit=True):
     from paper_2406_18111_gb300 import Apo
     dev = torch.device("cuda", local)
     apo = Apo(local)
+    apo.sort_tuning(args.sort_tuning)
     stream_np = W.match_stream(1 << 26, seed=5 + rank)
     pt, off = W.match_patterns(stream_np, 10000, 5, 2000, seed=5 + rank)
     st = torch.from_numpy(stream_np.view(np.int32)).to(dev)
@@ -464,6 +475,7 @@ def main():
     from paper_2406_18111_gb300 import Apo
     dev = torch.device("cuda", local)
     apo = Apo(local)
+    apo.sort_tuning(args.sort_tuning)
     n = args.n_tasks
     ts = W.config2_tasks(n, seed=2 + rank)
     host = [torch.from_numpy(np.ascontiguousarray(a).view(dt)).pin_memory()
@@ -604,6 +616,7 @@ def main():
         "ms_per_step_profiled": ms_prof,
         "step_stats": stats,
         "kernels": kernels,
+        "sort_tuning": tuning_summary(apo),
     }
     if world == 1 and not args.no_forms:
         # The batched and served forms, measured briefly on their own

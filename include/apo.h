@@ -327,6 +327,33 @@ int apo_profile_reset(apo_ctx *ctx);
 int apo_profile_read(apo_ctx *ctx, int index, char *name, size_t name_cap, uint64_t *launches,
                      double *ms, uint64_t *units);
 
+/* ------------------------------------------------------------------------
+ * Radix-sort launch shapes (no counterpart in the paper: a property of this
+ * GPU implementation).
+ *
+ * Every sort (the prefix-doubling rounds, the candidate order, the pattern
+ * starts) runs the onesweep digit pass in one of several shapes: threads per
+ * block, pairs per thread and digit width (8 or 9 bits).  In mode 0 (the
+ * default) the first sort of each size class (n rounded up to a power of
+ * two, 2^10 .. 2^23 and above) and key width on a device times every shape
+ * on synthetic keys of that size (at most 2^22 pairs) and width, on the
+ * call's stream, and keeps the fastest for the process's lifetime; that
+ * first call is slower by the trials.  Mode 1 always uses the default shape
+ * (512 threads, 8 pairs each, 8-bit digits) and never times anything.
+ * The choices are kept per device and shared by every context of the
+ * process (a served lane benefits from another lane's trials); the mode is
+ * per context.
+ * Results never depend on the shape: the sort is stable and exact.
+ * ---------------------------------------------------------------------- */
+int apo_sort_tuning(apo_ctx *ctx, int mode);
+/* Tuned entry `index` (0-based, in class then key-width order): size class
+ * (log2 of the class's largest n), key bits, trial size, the chosen shape
+ * and the trial times (ms per sort) of the chosen and the default shape.
+ * APO_EINVAL when index is past the last tuned entry. */
+int apo_sort_tuning_read(apo_ctx *ctx, int index, uint32_t *size_log2, uint32_t *key_bits,
+                         uint32_t *trial_n, int *threads, int *items, int *digit_bits, double *best_ms,
+                         double *default_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_profile_enable", "apo_profile_reset",
            "apo_profile_read", "apo_greedy_select_noalloc", "apo_server_create", "apo_server_submit",
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
-           "apo_server_destroy")
+           "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -330,6 +330,30 @@ class Apo:
         _check(code)
         c = int(cnt.value)
         return end[:c], pid[:c]
+
+    # -------------------------------------------------------------- sort tuning
+    def sort_tuning(self, mode: int):
+        """0: time the radix-sort shapes per size class and key width on first
+        use (default); 1: always the default shape."""
+        _check(lib().apo_sort_tuning(self._h, int(mode)))
+
+    def sort_tuning_read(self) -> list:
+        """The shapes chosen so far, one dict per (size class, key bits)."""
+        out = []
+        i = 0
+        while True:
+            sl, kb, tn = _U32(0), _U32(0), _U32(0)
+            th, it, db = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+            bm, dm = ctypes.c_double(0), ctypes.c_double(0)
+            if lib().apo_sort_tuning_read(self._h, i, ctypes.byref(sl), ctypes.byref(kb), ctypes.byref(tn),
+                                          ctypes.byref(th), ctypes.byref(it), ctypes.byref(db),
+                                          ctypes.byref(bm), ctypes.byref(dm)) != APO_OK:
+                break
+            out.append({"size_log2": sl.value, "key_bits": kb.value, "trial_n": tn.value,
+                        "threads": th.value, "items": it.value, "digit_bits": db.value,
+                        "best_ms": bm.value, "default_ms": dm.value})
+            i += 1
+        return out
 
     # -------------------------------------------------------------- instrumentation
     def profile(self, enable_timing: bool = True):

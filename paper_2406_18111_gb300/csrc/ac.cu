@@ -1004,9 +1004,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   b.cur = 0;
   {
-    int places[8];
-    const int np = plan_digits(0, bits_for(N - 1), places, 0);
-    APO_TRY(radix_sort_pairs(c, b, P, places, np, s));
+    const DigitRange r{0, bits_for(N - 1), false};
+    APO_TRY(radix_sort_pairs(c, b, P, &r, 1, s));
   }
   const uint32_t *sp = b.vals[b.cur];
   APO_CUDA_TRY(cudaMemsetAsync(is_start, 0, N, s));
@@ -1071,9 +1070,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   be.cur = 0;
   {
-    int places[8];
-    const int np = plan_digits(0, bits_for(root), places, 0);
-    APO_TRY(radix_sort_pairs(c, be, P, places, np, s));
+    const DigitRange r{0, bits_for(root), false};
+    APO_TRY(radix_sort_pairs(c, be, P, &r, 1, s));
   }
   const uint64_t *ek = be.keys[be.cur];
   const uint32_t *ev = be.vals[be.cur];

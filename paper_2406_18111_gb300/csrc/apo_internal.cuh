@@ -57,10 +57,10 @@ struct Arena {
 
 // Layout of the context's small device counter buffer (u32 words).
 enum : int {
-  kCtrSortHist = 0,       // radix sort digit histograms, 12 x 256
-  kCtrSortTiles = 3072,   // radix sort tile tickets, 12
-  kCtrMisc = 3136,        // per-kernel tile tickets and totals, see kMisc*
-  kCtrWords = 4096,
+  kCtrSortHist = 0,       // radix sort digit histograms, 12 places x 512 digits
+  kCtrSortTiles = 6144,   // radix sort tile tickets, 12
+  kCtrMisc = 6208,        // per-kernel tile tickets and totals, see kMisc*
+  kCtrWords = 8192,
 };
 enum : int {
   kMiscRefreshTiles = 0, kMiscRefreshCount, kMiscCompactTiles, kMiscCompactCount,
@@ -84,7 +84,7 @@ enum KernelId : int {
   kKPlcp, kKLcpPerm, kKMin32, kKMax, kKCandGen, kKCompact, kKCandGather, kKGreedy, kKTraces,
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
-  kKAcNodes, kKAcJump, kKCount
+  kKAcNodes, kKAcJump, kKRsTune, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
@@ -112,12 +112,44 @@ struct Profiler {
 
 }  // namespace apo
 
+namespace apo {
+
+// Radix-sort launch shape per (size class, key bits): chosen by timing every
+// shape the first time a class is sorted on a device (mode 0), or always the
+// default shape (mode 1).  The choices are shared by all contexts of the
+// process on the same device (sort_table()).
+constexpr int kTuneMinBits = 10, kTuneMaxBits = 23;  // size classes: n <= 2^10 .. n > 2^22
+constexpr int kTuneClasses = kTuneMaxBits - kTuneMinBits + 1;
+constexpr int kTuneBits = 97;  // sorted bits 0..96 (key and value digits together)
+struct SortTable {
+  int8_t choice[kTuneClasses][kTuneBits];
+  float best_ms[kTuneClasses][kTuneBits] = {};
+  float default_ms[kTuneClasses][kTuneBits] = {};
+  uint32_t trial_n[kTuneClasses][kTuneBits] = {};
+  SortTable() {
+    for (auto &row : choice)
+      for (auto &x : row) x = -1;
+  }
+};
+// The device's table; `lock` guards every read and write of it.
+SortTable &sort_table(int device);
+void sort_table_lock(bool lock);
+struct SortTuner {
+  int mode = 0;
+  void *scratch = nullptr;  // trial pairs
+  size_t scratch_bytes = 0;
+  static int size_class(uint32_t n);
+};
+
+}  // namespace apo
+
 struct apo_ctx {
   int device = 0;
   int num_sms = 0;
   apo::Arena arena;
   apo::Persistent ps;
   apo::Profiler prof;
+  apo::SortTuner tuner;
   uint32_t *host_pinned = nullptr;  // small pinned staging buffer (counts)
 };
 
@@ -161,24 +193,26 @@ inline int bits_for(uint64_t v) {  // number of bits to represent values 0..v
 }
 
 // ---------------------------------------------------------------- radix sort
-// Stable LSD sort of (key u64, value u32) pairs on the digits listed in
-// `shifts` (8-bit digits starting at each shift, least significant first).
-// The result lands in (*keys, *vals); the other buffer of each pair is
-// scratch.  `count_dev`, when non-null, is a device word holding the element
-// count (<= n_max) and n_max bounds the launch.
+// Stable LSD sort of (key u64, value u32) pairs on the bit ranges listed in
+// `ranges`, least significant first (a range of value bits sorts by the
+// value).  The result lands in (*keys, *vals); the other buffer of each pair
+// is scratch.  The digit width and tile shape come from the context's tuner.
 struct SortBuffers {
   uint64_t *keys[2];
   uint32_t *vals[2];
   int cur = 0;  // index of the buffer holding the current data
 };
-int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const int *shifts, int npass,
+struct DigitRange {
+  int lo, hi;       // bits [lo, hi) of the key (or of the value)
+  bool from_value;
+};
+constexpr int kFromValue = 256;  // place flag: the digit comes from the value
+int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
                      cudaStream_t s);
 // OR of all keys (to learn how many digits are populated); result in *out_dev.
 void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
-
-// Plan the 8-bit digit shifts covering bits [lo, hi) of a key.
-int plan_digits(int lo, int hi, int *shifts, int start);
 int radix_sort_init();
+int sort_shape_info(int id, int *threads, int *items, int *bits);
 
 // ---------------------------------------------------------------- windows
 // Several windows analysed at once are concatenated; position i belongs to

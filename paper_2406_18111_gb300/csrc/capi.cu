@@ -67,7 +67,7 @@ const char *const kKernelNames[kKCount] = {
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
-    "starts", "sparse", "ac_nodes", "ac_jump"};
+    "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -188,6 +188,7 @@ int apo_destroy(apo_ctx *c) {
   if (c->ps.lookback) cudaFree(c->ps.lookback);
   if (c->ps.counters) cudaFree(c->ps.counters);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  if (c->tuner.scratch) cudaFree(c->tuner.scratch);
   c->prof.release();
   delete c;
   return APO_OK;
@@ -449,6 +450,47 @@ int apo_profile_read(apo_ctx *c, int index, char *name, size_t name_cap, uint64_
   if (ms) *ms = c->prof.ms[index];
   if (units) *units = c->prof.units[index];
   return APO_OK;
+}
+
+int apo_sort_tuning(apo_ctx *c, int mode) {
+  if (!c || (mode != 0 && mode != 1)) {
+    set_error("apo_sort_tuning: null context or mode not 0 or 1");
+    return APO_EINVAL;
+  }
+  c->tuner.mode = mode;
+  return APO_OK;
+}
+
+int apo_sort_tuning_read(apo_ctx *c, int index, uint32_t *size_log2, uint32_t *key_bits, uint32_t *trial_n,
+                         int *threads, int *items, int *digit_bits, double *best_ms, double *default_ms) {
+  if (!c || index < 0) {
+    set_error("apo_sort_tuning_read: null context or negative index");
+    return APO_EINVAL;
+  }
+  int k = 0;
+  const SortTable &tb = sort_table(c->device);
+  sort_table_lock(true);
+  for (int cls = 0; cls < kTuneClasses; ++cls)
+    for (int bits = 0; bits < kTuneBits; ++bits) {
+      const int id = tb.choice[cls][bits];
+      if (id < 0) continue;
+      if (k++ != index) continue;
+      int th = 0, it = 0, db = 0;
+      sort_shape_info(id, &th, &it, &db);
+      if (size_log2) *size_log2 = (uint32_t)(cls + kTuneMinBits);
+      if (key_bits) *key_bits = (uint32_t)bits;
+      if (trial_n) *trial_n = tb.trial_n[cls][bits];
+      if (threads) *threads = th;
+      if (items) *items = it;
+      if (digit_bits) *digit_bits = db;
+      if (best_ms) *best_ms = tb.best_ms[cls][bits];
+      if (default_ms) *default_ms = tb.default_ms[cls][bits];
+      sort_table_lock(false);
+      return APO_OK;
+    }
+  sort_table_lock(false);
+  set_error("apo_sort_tuning_read: index past the last tuned entry");
+  return APO_EINVAL;
 }
 
 }  // extern "C"

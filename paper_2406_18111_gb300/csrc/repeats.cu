@@ -224,6 +224,7 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
 
 // ---------------------------------------------------------------- greedy
 constexpr int kGI = 4;  // candidates per thread per round
+constexpr uint32_t kGreedyFirstPhase = 1u << 15;  // candidates settled before the first drop
 constexpr int glist_bytes(int threads) { return threads * kGI * 12; }
 
 template <bool kSmem>
@@ -244,12 +245,18 @@ __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
 // The accepted flags must be zero on entry.  The mark bitmap covers the
 // window in shared memory (positions relative to the window start), or all
 // positions in global memory (zeroed by the caller).
+//
+// Single window, in phases: `corig` maps list positions to candidate indices
+// (null: the identity) when the list is a compacted remainder, and with
+// `persist` the shared-memory bitmap is loaded from gbits at the start and
+// stored back at the end, so that a later phase continues the same marks.
 template <int kT, bool kSmem>
 __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
                                                const uint32_t *__restrict__ cs,
                                                const uint32_t *__restrict__ cand_off, uint32_t m,
                                                const uint32_t *__restrict__ woff, uint32_t n,
                                                uint32_t *gbits, uint8_t *acc, uint32_t *acc_count,
+                                               const uint32_t *__restrict__ corig, int persist,
                                                uint32_t *err) {
   constexpr int kGT = kT;
   constexpr int kGRound = kT * kGI;
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
   __shared__ uint32_t s_cnt[kGI][32], s_off[kGI][32], s_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (kSmem)
-    for (uint32_t x = tid; x < words; x += kGT) gsm[x] = 0;
+    for (uint32_t x = tid; x < words; x += kGT) gsm[x] = persist ? gbits[x] : 0u;
   uint32_t nacc = 0;
   uint32_t nl[kGI], ns[kGI];
 #pragma unroll
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
         const uint32_t q = s_off[i][warp] + __popc(bal[i] & lt);
         sl[q] = l[i];
         ss[q] = s[i];
-        sk[q] = base + i * kGT + tid;
+        sk[q] = corig ? corig[base + i * kGT + tid] : base + i * kGT + tid;
       }
     }
     __syncthreads();
@@ -399,6 +406,36 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
     __syncthreads();
   }
   if (tid == 0) atomicAdd(acc_count, nacc);  // lane 0 of warp 0 counted every batch
+  if (kSmem && persist) {
+    __syncthreads();
+    for (uint32_t x = tid; x < words; x += kGT) gbits[x] = gsm[x];
+  }
+}
+
+// Candidates of the list remainder [from, len) whose first and last
+// positions are both unmarked (the others can never be accepted: marks only
+// accumulate, and a candidate meets an accepted interval iff an end of it is
+// marked).
+struct PredUnmarked {
+  const uint32_t *l, *s, *bits;
+  uint32_t from;
+  __device__ bool operator()(uint32_t k) const {
+    const uint32_t a = s[from + k], b = a + l[from + k] - 1;
+    return !((bits[a >> 5] >> (a & 31)) & 1u) && !((bits[b >> 5] >> (b & 31)) & 1u);
+  }
+};
+
+// New list = the kept remainder entries, in order.
+__global__ void k_list_gather(const uint32_t *__restrict__ keep, uint32_t cnt, uint32_t from,
+                              const uint32_t *__restrict__ l, const uint32_t *__restrict__ st,
+                              const uint32_t *__restrict__ orig, uint32_t *__restrict__ l2,
+                              uint32_t *__restrict__ s2, uint32_t *__restrict__ o2) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    const uint32_t k = from + keep[q];
+    l2[q] = l[k];
+    s2[q] = st[k];
+    o2[q] = orig ? orig[k] : k;
+  }
 }
 
 // Accepted candidates (compacted, in order) -> R and the keys of the
@@ -565,8 +602,9 @@ size_t repeats_workspace_bytes(uint64_t n, uint64_t windows) {
   const uint64_t M = n ? 2 * (n - 1) : 0;
   return (size_t)M * (2 * 8 + 2 * 4)  // sort buffers
          + (size_t)M * (4 * 3 + 4 + 1)  // candidate arrays, compaction indices, flags
+         + (size_t)M * (4 * 7)           // single window: greedy lists (two of three arrays) and drops
          + (size_t)n * 20                // R and the selected intervals (5 arrays of <= n)
-         + (size_t)n * 4 / 16 + (size_t)n / 8 + (size_t)(windows + 1) * 12 + 64 * 256;
+         + (size_t)n * 4 / 16 + (size_t)n / 8 + 16 + (size_t)(windows + 1) * 12 + 64 * 256;
 }
 
 int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixState &st,
@@ -644,7 +682,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   uint32_t *cid = c->arena.take_n<uint32_t>(M);
   uint32_t *cs = c->arena.take_n<uint32_t>(M);
   uint8_t *acc = c->arena.take_n<uint8_t>(M);
-  uint32_t *gbits = c->arena.take_n<uint32_t>((n + 31) / 32 + 1);
+  const size_t gwords = (size_t)(n + 31) / 32 + 4;  // the shared-memory bitmap rounds up to 4 words
+  uint32_t *gbits = c->arena.take_n<uint32_t>(gwords);
   uint32_t *cand_off = c->arena.take_n<uint32_t>(W.count + 1);
   uint32_t *sel_off = c->arena.take_n<uint32_t>(W.count + 1);
   uint32_t *trace_off = c->arena.take_n<uint32_t>(W.count + 1);
@@ -664,12 +703,10 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_TRY(read_u32(c, misc + kMiscCandCount, &mraw, s));
   uint32_t m = 0;
   if (mraw) {
-    int places[16];
-    int np = plan_digits(0, bs, places, 0);
-    for (int p = 0; p < np; ++p) places[p] |= 256;  // start digits come from the value
-    np = plan_digits(0, bw + bl + bi, places, np);
+    // start digits (the value) first, then the (window, length, id) key
+    const DigitRange r[2] = {{0, bs, true}, {0, bw + bl + bi, false}};
     b.cur = 0;
-    APO_TRY(radix_sort_pairs(c, b, mraw, places, np, s));
+    APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
     PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
     APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCompactCount, s));
     APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
@@ -695,22 +732,62 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     const size_t list = glist_bytes(big ? 1024 : 256);
     const uint32_t *coff = W.count > 1 ? cand_off : nullptr;
     const bool smem = (long long)(bm_bytes + list) <= g_greedy_smem_max;
-    if (!smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, (size_t)((n + 31) / 32) * 4, s));
-    {
+    if (!smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
+    uint32_t *keep = nullptr, *glist[2][3] = {};
+    if (big) {
+      keep = c->arena.take_n<uint32_t>(m);
+      for (auto &g : glist)
+        for (auto &a : g) a = c->arena.take_n<uint32_t>(m);
+      if (!keep || !glist[1][2]) return APO_ENOMEM;
+    }
+    if (big) {
+      // Phases: the one block settles a prefix of the list; then every
+      // remaining candidate with a marked end is dropped by the whole GPU
+      // and the survivors form the next list.  Long candidates come first,
+      // so a short prefix marks most of the window.
+      if (smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
+      const uint32_t *pl = cl, *ps = cs, *po = nullptr;
+      uint32_t len = m, prefix = kGreedyFirstPhase;
+      for (int phase = 0;; ++phase) {
+        const uint32_t take = std::min(prefix, len);
+        {
+          Launch lp_(c, kKGreedy, take, s);
+          if (smem)
+            k_greedy<1024, true><<<1, 1024, bm_bytes + list, s>>>(pl, ps, nullptr, take, W.off_dev, n, gbits,
+                                                                  acc, misc + kMiscAccCount, po, 1,
+                                                                  c->ps.err);
+          else
+            k_greedy<1024, false><<<1, 1024, list, s>>>(pl, ps, nullptr, take, W.off_dev, n, gbits, acc,
+                                                         misc + kMiscAccCount, po, 0, c->ps.err);
+        }
+        APO_CUDA_TRY(cudaGetLastError());
+        if (take == len) break;
+        PredUnmarked pu{pl, ps, gbits, take};
+        APO_TRY(compact(c, pu, len - take, keep, misc + kMiscCompactCount, s));
+        uint32_t kept = 0;
+        APO_TRY(read_u32(c, misc + kMiscCompactCount, &kept, s));
+        if (kept == 0) break;
+        uint32_t *l2 = glist[phase & 1][0], *s2 = glist[phase & 1][1], *o2 = glist[phase & 1][2];
+        {
+          Launch lp_(c, kKCandGather, kept, s);
+          k_list_gather<<<grid_for(kept, 256, c->num_sms), 256, 0, s>>>(keep, kept, take, pl, ps, po, l2, s2,
+                                                                        o2);
+        }
+        pl = l2;
+        ps = s2;
+        po = o2;
+        len = kept;
+        prefix *= 4;
+      }
+    } else {
       Launch lp_(c, kKGreedy, m, s);
-      if (big && smem)
-        k_greedy<1024, true><<<1, 1024, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n, nullptr,
-                                                              acc, misc + kMiscAccCount, c->ps.err);
-      else if (big)
-        k_greedy<1024, false><<<1, 1024, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
-                                                     misc + kMiscAccCount, c->ps.err);
-      else if (smem)
+      if (smem)
         k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n,
                                                                   nullptr, acc, misc + kMiscAccCount,
-                                                                  c->ps.err);
+                                                                  nullptr, 0, c->ps.err);
       else
         k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
-                                                        misc + kMiscAccCount, c->ps.err);
+                                                        misc + kMiscAccCount, nullptr, 0, c->ps.err);
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
@@ -742,9 +819,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
                                      misc + kMiscTraceCount, c->ps.lookback,
                                      misc + kMiscCompactTiles, next_epoch(c), c->ps.err);
     }
-    int places[8];
-    const int np = plan_digits(32, 32 + bits_for(n - 1), places, 0);
-    APO_TRY(radix_sort_pairs(c, sb, K, places, np, s));
+    const DigitRange r{32, 32 + bits_for(n - 1), false};
+    APO_TRY(radix_sort_pairs(c, sb, K, &r, 1, s));
     {
       Launch lp_(c, kKSelOut, K, s);
       k_sel_out<<<grid_for(K, 256, c->num_sms), 256, 0, s>>>(sb.keys[sb.cur], sb.vals[sb.cur], K, ss,

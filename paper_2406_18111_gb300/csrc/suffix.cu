@@ -46,12 +46,17 @@ __global__ void k_init_keys(const void *__restrict__ tokens, int tb, uint32_t n,
 
 // Sorted (key, suffix) pairs of the active suffixes -> new group heads, SA,
 // ranks and the next active list.  actpos == nullptr means position = index
-// (the first call, where the sorted list is the whole SA).
+// (the first call, where the sorted list is the whole SA).  Only a suffix
+// whose group became a singleton has reached its final SA position, so only
+// it writes SA; a rank is written only when it changed (with old_sh >= 0 the
+// old rank is key >> old_sh; a group's first subgroup keeps its start).
+// Both cut scattered 4-byte writes, each of which costs a whole sector.
 __global__ void __launch_bounds__(kRT) k_refresh(
     const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx, uint32_t A,
-    const uint32_t *__restrict__ actpos, uint32_t *__restrict__ sa, uint32_t *__restrict__ rank,
-    uint32_t *__restrict__ act_next, uint32_t *__restrict__ pos_next, uint32_t n, uint32_t *count_out,
-    uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+    const uint32_t *__restrict__ actpos, int old_sh, uint32_t *__restrict__ sa,
+    uint32_t *__restrict__ rank, uint32_t *__restrict__ act_next, uint32_t *__restrict__ pos_next,
+    uint32_t n, uint32_t *count_out, uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr,
+    uint32_t epoch, uint32_t *err) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem);           // [kRTile + 2], key[base-1 ..]
   uint32_t *si = reinterpret_cast<uint32_t *>(sk + kRTile + 2);  // [kRTile]
@@ -134,9 +139,10 @@ __global__ void __launch_bounds__(kRT) k_refresh(
         atomicExch(err, kDevRange);
         continue;
       }
-      sa[p] = id;
-      rank[id] = rm;
-      if (!(h && ((hb >> (i + 1)) & 1u))) {
+      const bool single = h && ((hb >> (i + 1)) & 1u);
+      if (single) sa[p] = id;
+      if (old_sh < 0 || (uint32_t)(sk[local + 1] >> old_sh) != rm) rank[id] = rm;
+      if (!single) {
         if (rs < A) {
           act_next[rs] = id;
           pos_next[rs] = p;
@@ -237,7 +243,7 @@ inline int grid_for(uint64_t n, int threads, int sms) {
 }
 
 int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *actpos,
-            uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
+            int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
             uint32_t *count_host, cudaStream_t s) {
   const int tiles = ceil_div(A, kRTile);
   APO_TRY(ensure_lookback(c, (size_t)2 * tiles));
@@ -246,7 +252,7 @@ int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, c
   const uint32_t ep = next_epoch(c);
   {
     Launch lp_(c, kKRefresh, A, s);
-    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, sa, rank, act_next, pos_next,
+    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, old_sh, sa, rank, act_next, pos_next,
                                                n, misc + kMiscRefreshCount, c->ps.lookback,
                                                c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
                                                c->ps.err);
@@ -304,11 +310,12 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   memcpy(&orv, c->host_pinned, sizeof(uint64_t));
-  int places[16];
-  int np = plan_digits(0, bits_for(orv), places, 0);
-  APO_TRY(radix_sort_pairs(c, b, n, places, np, s));
+  {
+    const DigitRange r{0, bits_for(orv), false};
+    APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
+  }
   uint32_t A = 0;
-  APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, st.sa, st.rank, act[0], pos[0], n,
+  APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
                   &A, s));
   if (st.win.count > 1) {
     // group by (window, token): re-sort by the window id over the token ranks
@@ -317,10 +324,9 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       k_wkeys<<<g, 256, 0, s>>>(st.rank, st.win, n, b.keys[0], b.vals[0]);
     }
     b.cur = 0;
-    np = plan_digits(0, bits_for(n - 1), places, 0);
-    np = plan_digits(32, 32 + bits_for(st.win.count - 1), places, np);
-    APO_TRY(radix_sort_pairs(c, b, n, places, np, s));
-    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, st.sa, st.rank, act[0], pos[0], n,
+    const DigitRange r[2] = {{0, bits_for(n - 1), false}, {32, 32 + bits_for(st.win.count - 1), false}};
+    APO_TRY(radix_sort_pairs(c, b, n, r, 2, s));
+    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
                     &A, s));
   }
   APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[0], st.rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
@@ -339,10 +345,10 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, minor_bits,
                                                             st.win, b.keys[0], b.vals[0]);
     }
-    np = plan_digits(0, minor_bits + major_bits, places, 0);
-    APO_TRY(radix_sort_pairs(c, b, A, places, np, s));
+    const DigitRange r{0, minor_bits + major_bits, false};
+    APO_TRY(radix_sort_pairs(c, b, A, &r, 1, s));
     uint32_t A2 = 0;
-    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], A, pos[cur], st.sa, st.rank, act[cur ^ 1],
+    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], A, pos[cur], minor_bits, st.sa, st.rank, act[cur ^ 1],
                     pos[cur ^ 1], n, &A2, s));
     cur ^= 1;
     A = A2;

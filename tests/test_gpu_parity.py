@@ -332,6 +332,27 @@ def test_batched_equals_plain_and_u64(apo):
     _check_batch_against(res, wins, lambda w, S: oracle.find_repeats(S, 5))
 
 
+# ---------------------------------------------------------------- sort shapes
+def test_sort_shapes_give_identical_results(apo):
+    """Every radix-sort shape the tuner may pick gives the same bytes: the
+    same windows with tuning off (default shape) and on (timed shapes), and
+    against the oracle; the tuner reports what it chose."""
+    from paper_2406_18111_gb300 import Apo, as_u32
+    S = oracle.hash_tasks(W.config2_tasks((1 << 16) + 321, seed=31))
+    want = oracle.find_repeats(S, 5)
+    for mode in (1, 0):
+        a = Apo(0)
+        a.sort_tuning(mode)
+        r = a.find_repeats(tokens_dev(S, 8), 5)
+        for f in FIELDS:
+            assert np.array_equal(as_u32(getattr(r, f)), getattr(want, f)), (mode, f)
+        if mode == 0:
+            tab = a.sort_tuning_read()
+            assert tab and all(t["threads"] in (256, 512) and t["digit_bits"] in (8, 9) for t in tab)
+            assert all(t["best_ms"] <= t["default_ms"] + 1e-9 for t in tab)
+        a.close()
+
+
 # ---------------------------------------------------------------- served form
 def test_served_results_equal_alone(apo):
     """Requests submitted together are batched by the server; every result
