@@ -90,6 +90,25 @@ def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:
     return float(total), a_r
 
 
+class _Range:
+    """NVTX range around each timed step (lets a profiler select exactly the
+    steady-state launches); a no-op where NVTX is unavailable."""
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push("step")
+            self.ok = True
+        except Exception:
+            self.ok = False
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            import torch
+            torch.cuda.nvtx.range_pop()
+
+
 def tuning_summary(apo) -> list:
     """Radix-sort shapes chosen so far: [log2 size class, key bits, threads,
     pairs per thread, digit bits, trial ms of the chosen / default shape]."""
@@ -126,8 +145,9 @@ def parse():
     ap.add_argument("--lanes", type=int, default=2, help="served: batches in flight")
     ap.add_argument("--no-forms", action="store_true",
                     help="window workload: skip the short batched and served measurements")
-    ap.add_argument("--sort-tuning", type=int, default=0, choices=[0, 1],
-                    help="0: radix-sort shapes timed per size class on first use; 1: default shape only")
+    ap.add_argument("--sort-tuning", type=int, default=0, choices=range(0, 8),
+                    help="0: radix-sort shapes timed per size class on first use; 1: default shape "
+                         "only; 2 + k: shape k only")
     return ap.parse_args()
 
 
@@ -270,7 +290,8 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            fn()
+            with _Range():
+                fn()
             b.record(stream)
             b.synchronize()
             tot += a.elapsed_time(b)
@@ -343,8 +364,22 @@ def run_served(args, rank, world, local, emit=True):
     reqs = [pool[k % len(pool)] for k in range(len(t_arr))]
     srv = Server(local, min_len=MIN_LEN, token_bytes=4, max_batch_tokens=1 << 24, max_batch_windows=256,
                  lanes=args.lanes)
-    for k in range(min(8, len(pool))):  # warm the lanes
-        srv.wait(srv.submit(pool[k]))
+    # Warm-up, untimed: every pool window once, then one second of the same
+    # arrival process, so that the lanes' first-use work (workspace growth,
+    # the radix-sort shape trials of each batch size class) is done before
+    # the measured arrivals.
+    for i in [srv.submit(S) for S in pool]:
+        srv.wait(i)
+    t_w, _, _ = W.served_requests(1.0, args.rate, seed=1005 + rank)
+    tw0 = time.perf_counter()
+    wids = []
+    for k, ta in enumerate(t_w):
+        delay = ta - (time.perf_counter() - tw0)
+        if delay > 0:
+            time.sleep(delay)
+        wids.append(srv.submit(pool[k % len(pool)]))
+    for i in wids:
+        srv.wait(i)
     clocks = Clocks(local)
     ids = [None] * len(reqs)
     t0 = time.perf_counter()
@@ -512,9 +547,10 @@ def main():
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            res = step(inputs_fn())
-            if out_fn is not None:
-                out_fn(res)
+            with _Range():
+                res = step(inputs_fn())
+                if out_fn is not None:
+                    out_fn(res)
             b.record(stream)
             b.synchronize()
             total += a.elapsed_time(b)

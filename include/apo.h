@@ -339,7 +339,10 @@ int apo_profile_read(apo_ctx *ctx, int index, char *name, size_t name_cap, uint6
  * on synthetic keys of that size (at most 2^22 pairs) and width, on the
  * call's stream, and keeps the fastest for the process's lifetime; that
  * first call is slower by the trials.  Mode 1 always uses the default shape
- * (512 threads, 8 pairs each, 8-bit digits) and never times anything.
+ * (512 threads, 8 pairs each, 8-bit digits) and never times anything; mode
+ * 2 + k always uses shape k (0: 512 x 8 pairs, 8-bit; 1: 256 x 8, 8-bit;
+ * 2: 512 x 4, 8-bit; 3: 256 x 4, 8-bit; 4: 512 x 8, 9-bit; 5: 512 x 4,
+ * 9-bit), for reproducible profiles.  Other modes: APO_EINVAL.
  * The choices are kept per device and shared by every context of the
  * process (a served lane benefits from another lane's trials); the mode is
  * per context.

@@ -334,7 +334,7 @@ class Apo:
     # -------------------------------------------------------------- sort tuning
     def sort_tuning(self, mode: int):
         """0: time the radix-sort shapes per size class and key width on first
-        use (default); 1: always the default shape."""
+        use (default); 1: always the default shape; 2 + k: always shape k."""
         _check(lib().apo_sort_tuning(self._h, int(mode)))
 
     def sort_tuning_read(self) -> list:

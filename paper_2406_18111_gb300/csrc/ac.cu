@@ -66,6 +66,7 @@ constexpr uint32_t kSep = 0xfffffffeu;  // symbol slot of a pattern separator in
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kFlag = 0x80000000u;  // segment-start flag of a packed scan value
 constexpr int kTsymPad = 40;            // separators after the pattern text (warp-wide reads)
+constexpr uint64_t kMaxFlat = 1ull << 28;  // longest flattened output chains (entries)
 
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;
@@ -540,15 +541,104 @@ struct DstRecord {
   const uint64_t *keys;
   const uint32_t *own;
   uint32_t *recidx;
-  uint4 *rec;
+  uint4 *rec;      // (first sorted index, patterns ending there, next record, node)
+  uint32_t P;
+  uint32_t *count;  // number of records
   __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const {
     if (k == 0 || keys[k] != keys[k - 1]) {
       const uint32_t node = (uint32_t)keys[k];
       recidx[node] = v - 1;
-      rec[v - 1] = make_uint4(k, own[node], kNil, 0u);
+      rec[v - 1] = make_uint4(k, own[node], kNil, node);
     }
+    if (k == P - 1) *count = v;
   }
 };
+
+// Flattened output chains: record r's chain (all its matches, in report
+// order) is flat[flat_off[r] .. + rtot[r]).  rtot[r] = the match total of
+// the record's node.
+__global__ void k_rec_totals(const uint4 *__restrict__ rec, const uint32_t *__restrict__ total, uint32_t R,
+                             uint32_t *rtot) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+    rtot[r] = total[rec[r].w];
+}
+
+struct SrcU32 {
+  const uint32_t *a;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const { return a[k]; }
+};
+struct DstExclusive {  // out[k] = inclusive - a[k]; *sum = the grand total
+  const uint32_t *a;
+  uint32_t *out, *sum;
+  uint32_t n;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const {
+    out[k] = v - a[k];
+    if (k == n - 1) *sum = v;
+  }
+};
+
+// One warp per record walks its chain and writes the ids.
+__global__ void k_flat_chains(const uint4 *__restrict__ rec, uint32_t R, const uint32_t *__restrict__ flat_off,
+                              const uint32_t *__restrict__ evals, uint32_t *__restrict__ flat) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R; r += warps) {
+    uint32_t o = flat_off[r];
+    uint32_t cur = r;
+    while (cur != kNil) {
+      const uint4 q = rec[cur];
+      for (uint32_t k = lane; k < q.y; k += 32) flat[o + k] = evals[q.x + k];
+      o += q.y;
+      cur = q.z;
+    }
+  }
+}
+
+// Pass B over flattened chains: one warp per 32 positions; lane j fetches
+// position x0+j's chain; short chains are copied by their own lane, long ones
+// by the whole warp in position order (contiguous reads and writes).
+constexpr uint32_t kFillOwn = 4;
+__global__ void k_ac_fill_flat(const uint32_t *__restrict__ state, uint32_t n, const uint32_t *__restrict__ off,
+                               const uint32_t *__restrict__ firstrec, const uint32_t *__restrict__ rtot,
+                               const uint32_t *__restrict__ flat_off, const uint32_t *__restrict__ flat,
+                               uint32_t *mend, uint32_t *mid, uint64_t cap) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint64_t x0 = (uint64_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; x0 < n;
+       x0 += (uint64_t)warps * 32) {
+    const uint64_t x = x0 + lane;
+    uint32_t cnt = 0, src = 0, dst = 0;
+    if (x < n) {
+      const uint32_t r = firstrec[state[x]];
+      if (r != kNil) {
+        cnt = rtot[r];
+        src = flat_off[r];
+        dst = off[x];
+      }
+    }
+    if (cnt <= kFillOwn) {  // short chains: each lane copies its own
+      for (uint32_t k = 0; k < cnt; ++k) {
+        if (dst + (uint64_t)k < cap) {
+          mend[dst + k] = (uint32_t)x;
+          mid[dst + k] = flat[src + k];
+        }
+      }
+    }
+    for (uint32_t busy = __ballot_sync(0xffffffffu, cnt > kFillOwn); busy; busy &= busy - 1) {
+      const int j = __ffs(busy) - 1;
+      const uint32_t c = __shfl_sync(0xffffffffu, cnt, j);
+      const uint32_t sj = __shfl_sync(0xffffffffu, src, j);
+      const uint64_t dj = __shfl_sync(0xffffffffu, dst, j);
+      const uint32_t xj = (uint32_t)(x0 + j);
+      for (uint32_t k = lane; k < c; k += 32) {
+        if (dj + k < cap) {
+          mend[dj + k] = xj;
+          mid[dj + k] = flat[sj + k];
+        }
+      }
+    }
+  }
+}
 
 // ---------------------------------------------------------------- match
 // One warp runs the automaton over one chunk.  Along a primary edge the next
@@ -807,7 +897,7 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   const uint64_t dct = pow2_at_least(2 * (extent + 1));
     const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
   return suffix_workspace_bytes(N) + (uint64_t)sa_levels(maxlen) * N * 4 +
-         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * 16 +
+         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * (16 + 8) +
          tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 +
          96 * 256;
 }
@@ -1075,7 +1165,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   const uint64_t *ek = be.keys[be.cur];
   const uint32_t *ev = be.vals[be.cur];
-  APO_TRY(seg_scan<false>(c, SrcRunStart{ek}, DstRecord{ek, own, recidx, rec}, P, OpSum(), 0u, s));
+  APO_TRY(seg_scan<false>(c, SrcRunStart{ek}, DstRecord{ek, own, recidx, rec, P, misc + kMiscTraceCount},
+                          P, OpSum(), 0u, s));
   // match totals and output links
   {
     Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
@@ -1133,6 +1224,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscCompactCount, 4, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 1, misc + kMiscTraceCount, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   APO_TRY(check_device_error(c, s));
   const uint64_t total_m = c->host_pinned[0];
@@ -1142,9 +1234,41 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     return APO_ECAPACITY;
   }
   if (total_m) {
-    Launch lp_(c, kKAcFill, n, s);
-    k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, firstrec, rec, ev, match_end,
-                                                    match_id, cap);
+    // flatten each output record's chain once (sum over records of their
+    // chain lengths, usually far below the match count), then copy chains
+    // per position; very long flattened chains fall back to walking
+    const uint32_t R = c->host_pinned[1];
+    uint32_t *rtot = c->arena.take_n<uint32_t>(R), *flat_off = c->arena.take_n<uint32_t>(R);
+    uint64_t flat_total = ~0ull;
+    if (rtot && flat_off && R) {
+      {
+        Launch lp_(c, kKMarkEnds, R, s);
+        k_rec_totals<<<grid_for(R, 256, sms), 256, 0, s>>>(rec, mtotal, R, rtot);
+      }
+      APO_TRY(seg_scan<false>(c, SrcU32{rtot}, DstExclusive{rtot, flat_off, misc + kMiscAccCount, R}, R, OpSum(),
+                              0u, s));
+      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaStreamSynchronize(s));
+      flat_total = c->host_pinned[0];
+    }
+    uint32_t *flat = nullptr;
+    if (flat_total <= kMaxFlat) {
+      APO_TRY(ensure_side(c, std::max<uint64_t>(flat_total, 1) * 4, s));
+      flat = static_cast<uint32_t *>(c->side);
+    }
+    if (flat) {
+      {
+        Launch lp_(c, kKAcFill, flat_total, s);
+        k_flat_chains<<<std::max(1, std::min(ceil_div(R, 8), sms * 16)), 256, 0, s>>>(rec, R, flat_off, ev, flat);
+      }
+      Launch lp_(c, kKAcFill, n, s);
+      k_ac_fill_flat<<<std::max(1, std::min(ceil_div(n, 256), sms * 32)), 256, 0, s>>>(
+          state, (uint32_t)n, off, firstrec, rtot, flat_off, flat, match_end, match_id, cap);
+    } else {
+      Launch lp_(c, kKAcFill, n, s);
+      k_ac_fill<<<grid_for(n, 256, sms), 256, 0, s>>>(state, (uint32_t)n, off, firstrec, rec, ev, match_end,
+                                                      match_id, cap);
+    }
   }
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaStreamSynchronize(s));

@@ -115,8 +115,8 @@ struct Profiler {
 namespace apo {
 
 // Radix-sort launch shape per (size class, key bits): chosen by timing every
-// shape the first time a class is sorted on a device (mode 0), or always the
-// default shape (mode 1).  The choices are shared by all contexts of the
+// shape the first time a class is sorted on a device (mode 0), always the
+// default shape (mode 1), or always shape k (mode 2 + k).  The choices are shared by all contexts of the
 // process on the same device (sort_table()).
 constexpr int kTuneMinBits = 10, kTuneMaxBits = 23;  // size classes: n <= 2^10 .. n > 2^22
 constexpr int kTuneClasses = kTuneMaxBits - kTuneMinBits + 1;
@@ -151,6 +151,8 @@ struct apo_ctx {
   apo::Profiler prof;
   apo::SortTuner tuner;
   uint32_t *host_pinned = nullptr;  // small pinned staging buffer (counts)
+  void *side = nullptr;             // grow-only buffer for sizes known only mid-call
+  size_t side_bytes = 0;
 };
 
 namespace apo {
@@ -183,6 +185,8 @@ inline uint32_t next_epoch(apo_ctx *c) {
 }
 
 int ensure_lookback(apo_ctx *c, size_t words);
+// Grows the context's side buffer to `bytes` (waits for the stream first).
+int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s);
 int check_device_error(apo_ctx *c, cudaStream_t s);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -213,6 +217,7 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *r
 void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
 int radix_sort_init();
 int sort_shape_info(int id, int *threads, int *items, int *bits);
+int sort_shape_count();
 
 // ---------------------------------------------------------------- windows
 // Several windows analysed at once are concatenated; position i belongs to

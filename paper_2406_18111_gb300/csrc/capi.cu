@@ -62,6 +62,18 @@ int ensure_lookback(apo_ctx *c, size_t words) {
   return APO_OK;
 }
 
+int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s) {
+  if (bytes <= c->side_bytes) return APO_OK;
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  if (c->side) cudaFree(c->side);
+  c->side = nullptr;
+  c->side_bytes = 0;
+  const size_t want = std::max<size_t>(bytes + bytes / 4, (size_t)1 << 20);
+  APO_CUDA_TRY(cudaMalloc(&c->side, want));
+  c->side_bytes = want;
+  return APO_OK;
+}
+
 const char *const kKernelNames[kKCount] = {
     "hash_tasks", "init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
@@ -189,6 +201,7 @@ int apo_destroy(apo_ctx *c) {
   if (c->ps.counters) cudaFree(c->ps.counters);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->tuner.scratch) cudaFree(c->tuner.scratch);
+  if (c->side) cudaFree(c->side);
   c->prof.release();
   delete c;
   return APO_OK;
@@ -453,8 +466,8 @@ int apo_profile_read(apo_ctx *c, int index, char *name, size_t name_cap, uint64_
 }
 
 int apo_sort_tuning(apo_ctx *c, int mode) {
-  if (!c || (mode != 0 && mode != 1)) {
-    set_error("apo_sort_tuning: null context or mode not 0 or 1");
+  if (!c || mode < 0 || mode >= 2 + sort_shape_count()) {
+    set_error("apo_sort_tuning: null context or mode not 0, 1 or 2 + a shape index");
     return APO_EINVAL;
   }
   c->tuner.mode = mode;

@@ -412,7 +412,7 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *r
     set_error("radix sort: more than 96 bits to sort on");
     return APO_EINVAL;
   }
-  int shape_id = 0;
+  int shape_id = c->tuner.mode >= 2 ? c->tuner.mode - 2 : 0;  // mode 2 + k: always shape k
   if (c->tuner.mode == 0) {
     const int cls = SortTuner::size_class(n);
     SortTable &tb = sort_table(c->device);
@@ -435,6 +435,8 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *r
   }
   return sort_with(c, kShapes[shape_id], b, n, pl, true, s);
 }
+
+int sort_shape_count() { return kNumShapes; }
 
 int sort_shape_info(int id, int *threads, int *items, int *bits) {
   if (id < 0 || id >= kNumShapes) return APO_EINVAL;
