@@ -48,11 +48,10 @@ WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/30
 # (u64 key, u32 value) pair; refresh: read key, suffix, position, write SA,
 # rank, next active suffix and position; pack: read suffix and two ranks,
 # write a pair; hash: descriptor bytes in, 8 out (per task, at the
-# workload's mean of 4.5 arguments); ac_states: one u64 token in, one u32
-# state out; ac_fill: one state and offset in, 8 bytes per match out
-# (unit = positions; matches counted separately).
+# workload's mean of 4.5 arguments).  The greedy loop and the automaton
+# passes are chains of dependent accesses (latency-bound) and have no entry.
 BYTES_PER_UNIT = {"rs_pass": 24, "refresh": 32, "pack": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
-                  "ac_states": 12, "plcp": 24, "cand_gen": 36, "greedy": 8, "compact": 16}
+                  "plcp": 24, "cand_gen": 36, "compact": 16}
 
 
 # The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
@@ -107,6 +106,25 @@ class _Range:
         if self.ok:
             import torch
             torch.cuda.nvtx.range_pop()
+
+
+def traffic_for(workload: str, kernel: str, units_per_launch: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu figures
+    (profiles/traffic.txt), or None when there are none or the kernel's
+    source changed since they were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) != 5 or line.startswith("#") or f[0] != workload or f[1] != kernel:
+            continue
+        src = os.path.join(ROOT, f[3])
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != f[4]:
+            return None
+        return float(f[2]) * units_per_launch
+    return None
 
 
 def tuning_summary(apo) -> list:
@@ -315,10 +333,13 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
     ms_plain = timed(plain, plain_steps)
     clk = clocks.stop()
     peak, peak_kind = peaks()
-    name, (la, kms, units) = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (la, kms, units) = max(((k, v) for k, v in prof.items() if k in BYTES_PER_UNIT),
+                                 key=lambda kv: kv[1][1])
     bpu = BYTES_PER_UNIT.get(name)
     roof = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
-            "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof, "traffic": None}
+            "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof,
+            "traffic": traffic_for("batched", name, units / la) if la else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
     if bpu is not None and kms > 0:
         ach = bpu * units / (kms / 1e3) / 1e9
         roof.update({"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": bpu * units / la,
@@ -607,20 +628,25 @@ def main():
     value = n * world / (ms / 1e3)
     e2e_value = n * world / (ms_e2e / 1e3)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel with a byte model (the kernels without
+    # one are latency-bound chains: the greedy loop, automaton passes)
     peak, peak_kind = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    dom = max(((k, v) for k, v in prof.items() if k in BYTES_PER_UNIT), key=lambda kv: kv[1][1])
     name, (la, kms, units) = dom
     bpu = BYTES_PER_UNIT.get(name)
     roof = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
             "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof,
-            "traffic": None}
+            "traffic": traffic_for("window", name, units / la) if la else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
     if bpu is not None and kms > 0:
         ach = bpu * units / (kms / 1e3) / 1e9
         roof.update({"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": bpu * units / la,
                      "ms_per_launch": kms / la})
     else:
         roof.update({"achieved": None, "frac": None})
+    roof["top_kernel"] = {"kernel": top[0], "share_of_step": top[1][1] / args.steps / ms_prof,
+                          "bound": "hbm" if top[0] in BYTES_PER_UNIT else "latency"}
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
