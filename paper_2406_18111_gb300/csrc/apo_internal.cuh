@@ -66,6 +66,7 @@ enum : int {
   kMiscRefreshTiles = 0, kMiscRefreshCount, kMiscCompactTiles, kMiscCompactCount,
   kMiscCandCount, kMiscMaxLen, kMiscAccCount, kMiscTraceCount, kMiscMatchCount,
   kMiscKeyOr = 16,        // u64, two words
+  kMiscRound = 20,        // two words: active-suffix counts of consecutive doubling rounds
   kMiscCount = 64,
 };
 
@@ -153,6 +154,7 @@ struct apo_ctx {
   uint32_t *host_pinned = nullptr;  // small pinned staging buffer (counts)
   void *side = nullptr;             // grow-only buffer for sizes known only mid-call
   size_t side_bytes = 0;
+  cudaEvent_t round_ev[2] = {nullptr, nullptr};  // doubling-round count read-backs
 };
 
 namespace apo {
@@ -211,8 +213,10 @@ struct DigitRange {
   bool from_value;
 };
 constexpr int kFromValue = 256;  // place flag: the digit comes from the value
+// With n_dev, the element count is the device word *n_dev and n only bounds
+// the launch (so a sort can be queued before its count reaches the host).
 int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
-                     cudaStream_t s);
+                     cudaStream_t s, const uint32_t *n_dev = nullptr);
 // OR of all keys (to learn how many digits are populated); result in *out_dev.
 void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
 int radix_sort_init();

@@ -181,6 +181,13 @@ int apo_create(apo_ctx **out, int device) {
     set_error("apo_create: device allocation failed");
     return APO_ENOMEM;
   }
+  if (cudaEventCreateWithFlags(&c->round_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->round_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    apo_destroy(c);
+    set_error("apo_create: event creation failed");
+    return APO_ECUDA;
+  }
   cudaMemset(c->ps.err, 0, sizeof(uint32_t));
   cudaMemset(c->ps.counters, 0, kCtrWords * sizeof(uint32_t));
   if (ensure_lookback(c, 1 << 16) != APO_OK) {
@@ -202,6 +209,8 @@ int apo_destroy(apo_ctx *c) {
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->tuner.scratch) cudaFree(c->tuner.scratch);
   if (c->side) cudaFree(c->side);
+  for (auto e : c->round_ev)
+    if (e) cudaEventDestroy(e);
   c->prof.release();
   delete c;
   return APO_OK;

@@ -53,8 +53,10 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t v, int place) 
 template <int BITS>
 __global__ void __launch_bounds__(kHistThreads) k_rs_hist(const uint64_t *__restrict__ keys,
                                                           const uint32_t *__restrict__ vals, uint32_t n,
-                                                          int place, uint32_t *__restrict__ hist) {
+                                                          const uint32_t *__restrict__ n_dev, int place,
+                                                          uint32_t *__restrict__ hist) {
   constexpr int R = 1 << BITS;
+  if (n_dev) n = min(n, *n_dev);
   __shared__ uint32_t sh[R];
   for (int i = threadIdx.x; i < R; i += kHistThreads) sh[i] = 0;
   __syncthreads();
@@ -92,10 +94,11 @@ struct PassShape {
 template <int TPB, int ITEMS, int BITS>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, uint32_t n, int place, const uint32_t *__restrict__ gcnt,
-    int next_place, uint32_t *__restrict__ next_cnt, uint64_t *status, uint32_t *tile_ctr,
-    uint32_t epoch, uint32_t *err) {
+    uint32_t *__restrict__ vout, uint32_t n, const uint32_t *__restrict__ n_dev, int place,
+    const uint32_t *__restrict__ gcnt, int next_place, uint32_t *__restrict__ next_cnt, uint64_t *status,
+    uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
   using S = PassShape<TPB, ITEMS, BITS>;
+  if (n_dev) n = min(n, *n_dev);  // the launch is sized for an upper bound
   constexpr int R = S::kRadix, NW = S::kWarps, TILE = S::kTile;
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * TILE;
+  if (base >= n) return;  // a tile past the device-side count (no later tile looks at it)
   const uint64_t seg = base + (uint64_t)warp * (ITEMS * 32);
 
   uint64_t k[ITEMS];
@@ -240,9 +244,9 @@ __global__ void k_rs_trial_keys(uint64_t *keys, uint32_t *vals, uint32_t n, int 
 }
 
 // ---------------------------------------------------------------- shapes
-using PassFn = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, uint32_t, int,
-                        const uint32_t *, int, uint32_t *, uint64_t *, uint32_t *, uint32_t, uint32_t *);
-using HistFn = void (*)(const uint64_t *, const uint32_t *, uint32_t, int, uint32_t *);
+using PassFn = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, uint32_t, const uint32_t *,
+                        int, const uint32_t *, int, uint32_t *, uint64_t *, uint32_t *, uint32_t, uint32_t *);
+using HistFn = void (*)(const uint64_t *, const uint32_t *, uint32_t, const uint32_t *, int, uint32_t *);
 
 struct Shape {
   int threads, items, bits;
@@ -275,8 +279,8 @@ int plan(const Shape &sh, const DigitRange *ranges, int nranges, Places *pl) {
 }
 
 // All passes of one sort with one shape (b.cur flips once per pass).
-int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const Places &pl, bool count,
-              cudaStream_t s) {
+int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const uint32_t *n_dev, const Places &pl,
+              bool count, cudaStream_t s) {
   const int R = 1 << sh.bits;
   const int tile = sh.threads * sh.items;
   const int tiles = ceil_div(n, tile);
@@ -287,7 +291,7 @@ int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const Pla
   const int hblocks = std::max(1, std::min(c->num_sms * 4, ceil_div(n, kHistThreads * 8)));
   {
     Launch lp_(c, count ? kKRsHist : kKRsTune, n, s);
-    sh.hist<<<hblocks, kHistThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, pl.p[0], hist);
+    sh.hist<<<hblocks, kHistThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, n_dev, pl.p[0], hist);
   }
   for (int p = 0; p < pl.n; ++p) {
     const uint32_t ep = next_epoch(c);
@@ -295,7 +299,7 @@ int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const Pla
     {
       Launch lp_(c, count ? kKRsPass : kKRsTune, n, s);
       sh.pass<<<tiles, sh.threads, sh.smem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
-                                                 b.vals[b.cur ^ 1], n, pl.p[p], hist + p * kMaxRadix, nxt,
+                                                 b.vals[b.cur ^ 1], n, n_dev, pl.p[p], hist + p * kMaxRadix, nxt,
                                                  hist + (p + 1) * kMaxRadix, c->ps.lookback, tctr + p, ep,
                                                  c->ps.err);
     }
@@ -368,7 +372,7 @@ int tune(apo_ctx *c, uint32_t n, int bits, int cls, cudaStream_t s) {
                                                                                   std::min(bits, 64), 0x5eedull + rep);
       b.cur = 0;
       APO_CUDA_TRY(cudaEventRecord(e0, s));
-      APO_TRY(sort_with(c, kShapes[i], b, nt, pl, false, s));
+      APO_TRY(sort_with(c, kShapes[i], b, nt, nullptr, pl, false, s));
       APO_CUDA_TRY(cudaEventRecord(e1, s));
       APO_CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -404,7 +408,7 @@ void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_d
 }
 
 int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
-                     cudaStream_t s) {
+                     cudaStream_t s, const uint32_t *n_dev) {
   int bits = 0;
   for (int r = 0; r < nranges; ++r) bits += std::max(0, ranges[r].hi - ranges[r].lo);
   if (n <= 1 || bits == 0) return APO_OK;
@@ -433,7 +437,7 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *r
     set_error("radix sort: too many digit places");
     return APO_EINVAL;
   }
-  return sort_with(c, kShapes[shape_id], b, n, pl, true, s);
+  return sort_with(c, kShapes[shape_id], b, n, n_dev, pl, true, s);
 }
 
 int sort_shape_count() { return kNumShapes; }

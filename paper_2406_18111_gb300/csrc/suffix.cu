@@ -53,10 +53,10 @@ __global__ void k_init_keys(const void *__restrict__ tokens, int tb, uint32_t n,
 // Both cut scattered 4-byte writes, each of which costs a whole sector.
 __global__ void __launch_bounds__(kRT) k_refresh(
     const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx, uint32_t A,
-    const uint32_t *__restrict__ actpos, int old_sh, uint32_t *__restrict__ sa,
-    uint32_t *__restrict__ rank, uint32_t *__restrict__ act_next, uint32_t *__restrict__ pos_next,
-    uint32_t n, uint32_t *count_out, uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr,
-    uint32_t epoch, uint32_t *err) {
+    const uint32_t *__restrict__ A_dev, const uint32_t *__restrict__ actpos, int old_sh,
+    uint32_t *__restrict__ sa, uint32_t *__restrict__ rank, uint32_t *__restrict__ act_next,
+    uint32_t *__restrict__ pos_next, uint32_t n, uint32_t *count_out, uint64_t *st_max, uint64_t *st_sum,
+    uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem);           // [kRTile + 2], key[base-1 ..]
   uint32_t *si = reinterpret_cast<uint32_t *>(sk + kRTile + 2);  // [kRTile]
@@ -64,10 +64,12 @@ __global__ void __launch_bounds__(kRT) k_refresh(
   __shared__ uint32_t s_tile, s_pmax, s_psum;
   __shared__ uint32_t scr[kRT / 32];
   const int tid = threadIdx.x;
+  if (A_dev) A = min(A, *A_dev);  // the launch is sized for an upper bound
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * kRTile;
+  if (base >= A) return;  // past the device-side count: no later tile looks at it
   const uint32_t cnt = (A - base) < (uint64_t)kRTile ? (uint32_t)(A - base) : (uint32_t)kRTile;
   for (uint32_t q = tid; q < cnt + 2; q += kRT) {
     const long long g = (long long)base - 1 + q;
@@ -157,9 +159,10 @@ __global__ void __launch_bounds__(kRT) k_refresh(
 
 // key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
 // value = i, with sh = bits of n (the second part is at most n).
-__global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ rank,
-                       uint32_t n, uint64_t h, int sh, Windows W, uint64_t *__restrict__ keys,
-                       uint32_t *__restrict__ vals) {
+__global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ A_dev,
+                       const uint32_t *__restrict__ rank, uint32_t n, uint64_t h, int sh, Windows W,
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  if (A_dev) A = min(A, *A_dev);
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < A; k += gridDim.x * blockDim.x) {
     const uint32_t i = act[k];
     const uint64_t j = i + h;
@@ -242,24 +245,35 @@ inline int grid_for(uint64_t n, int threads, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
-int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *actpos,
-            int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
-            uint32_t *count_host, cudaStream_t s) {
-  const int tiles = ceil_div(A, kRTile);
+// Launches the refresh of the (at most A, exactly *A_dev when given) sorted
+// active suffixes; the number still active lands in *count_dev (zeroed
+// first, so a launch with nothing to do leaves 0).
+int refresh_launch(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *A_dev,
+                   const uint32_t *actpos, int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next,
+                   uint32_t *pos_next, uint32_t n, uint32_t *count_dev, cudaStream_t s) {
+  const int tiles = std::max(1, ceil_div(A, kRTile));
   APO_TRY(ensure_lookback(c, (size_t)2 * tiles));
   uint32_t *misc = c->ps.counters + kCtrMisc;
-  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRefreshTiles, 0, 2 * sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRefreshTiles, 0, sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
   const uint32_t ep = next_epoch(c);
   {
     Launch lp_(c, kKRefresh, A, s);
-    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, actpos, old_sh, sa, rank, act_next, pos_next,
-                                               n, misc + kMiscRefreshCount, c->ps.lookback,
-                                               c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
-                                               c->ps.err);
+    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, A_dev, actpos, old_sh, sa, rank, act_next, pos_next,
+                                               n, count_dev, c->ps.lookback, c->ps.lookback + tiles,
+                                               misc + kMiscRefreshTiles, ep, c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscRefreshCount, sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, s));
+  return APO_OK;
+}
+
+// Refresh with the count read back at once (the first rounds).
+int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *actpos,
+            int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
+            uint32_t *count_host, cudaStream_t s) {
+  uint32_t *cnt = c->ps.counters + kCtrMisc + kMiscRefreshCount;
+  APO_TRY(refresh_launch(c, keys, idx, A, nullptr, actpos, old_sh, sa, rank, act_next, pos_next, n, cnt, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   APO_TRY(check_device_error(c, s));
   *count_host = c->host_pinned[0];
@@ -334,29 +348,50 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   int cur = 0;
   uint32_t rounds = 0;
   const int minor_bits = bits_for(n), major_bits = bits_for(n - 1);
-  for (uint64_t h = 1; A > 0; h <<= 1) {
+  // Round r reads its active count from a device word and writes the next
+  // one; the host queues round r+1 before it has read round r's count (an
+  // upper bound sizes the launches), and stops one round after the count
+  // reaches 0 (that round's kernels find nothing to do and return).
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  uint32_t *rc = misc + kMiscRound;
+  uint32_t ub = A;  // upper bound on the current round's input count
+  for (uint32_t r = 0; A > 0; ++r) {
     if (st.levels >= max_levels) {
       set_error("suffix array: too many doubling rounds");
       return APO_EDEVICE;
     }
+    const uint32_t *in = r == 0 ? misc + kMiscRefreshCount : rc + ((r - 1) & 1);
+    uint32_t *out = rc + (r & 1);
+    const uint64_t h = 1ull << r;
     b.cur = 0;
     {
-      Launch lp_(c, kKPack, A, s);
-      k_pack<<<grid_for(A, 256, c->num_sms), 256, 0, s>>>(act[cur], A, st.rank, n, h, minor_bits,
-                                                            st.win, b.keys[0], b.vals[0]);
+      Launch lp_(c, kKPack, ub, s);
+      k_pack<<<grid_for(ub, 256, c->num_sms), 256, 0, s>>>(act[cur], ub, in, st.rank, n, h, minor_bits,
+                                                             st.win, b.keys[0], b.vals[0]);
     }
-    const DigitRange r{0, minor_bits + major_bits, false};
-    APO_TRY(radix_sort_pairs(c, b, A, &r, 1, s));
-    uint32_t A2 = 0;
-    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], A, pos[cur], minor_bits, st.sa, st.rank, act[cur ^ 1],
-                    pos[cur ^ 1], n, &A2, s));
+    const DigitRange dr{0, minor_bits + major_bits, false};
+    APO_TRY(radix_sort_pairs(c, b, ub, &dr, 1, s, in));
+    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], ub, in, pos[cur], minor_bits, st.sa, st.rank,
+                           act[cur ^ 1], pos[cur ^ 1], n, out, s));
     cur ^= 1;
-    A = A2;
-    ++rounds;
     APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[st.levels], st.rank, (size_t)n * 4,
                                  cudaMemcpyDeviceToDevice, s));
     ++st.levels;
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 4 + (r & 1), out, 4, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaEventRecord(c->round_ev[r & 1], s));
+    if (r > 0) {
+      APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
+      const uint32_t a = c->host_pinned[4 + ((r - 1) & 1)];  // round r's input count
+      if (a == 0) {  // round r had nothing to do
+        --st.levels;
+        break;
+      }
+      ub = a;
+    }
+    ++rounds;
   }
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  APO_TRY(check_device_error(c, s));
   *rounds_out = rounds;
   return APO_OK;
 }
