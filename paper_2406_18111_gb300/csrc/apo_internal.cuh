@@ -67,6 +67,7 @@ enum : int {
   kMiscCandCount, kMiscMaxLen, kMiscAccCount, kMiscTraceCount, kMiscMatchCount,
   kMiscKeyOr = 16,        // u64, two words
   kMiscRound = 20,        // two words: active-suffix counts of consecutive doubling rounds
+  kMiscDict = 22,         // two words: distinct tokens, dictionary overflow flag
   kMiscCount = 64,
 };
 
@@ -251,6 +252,7 @@ struct SuffixState {
   uint32_t **snaps;  // host array of device pointers: rank after level k
   int levels;        // number of snapshots written
   Windows win;
+  uint32_t h0 = 1;   // tokens per initial key: level k ranks are equal iff h0 * 2^k tokens are
 };
 int build_suffix_array(apo_ctx *c, const void *tokens, int token_bytes, uint32_t n,
                        SuffixState &st, int max_levels, uint32_t *rounds_out, cudaStream_t s);

@@ -157,6 +157,105 @@ __global__ void __launch_bounds__(kRT) k_refresh(
   }
 }
 
+// ---------------------------------------------------------------- initial keys
+// The first sort groups suffixes by their first h0 tokens at once: each
+// token gets an order-preserving code 1..sigma (0 = past the window's end),
+// h0 codes of cb bits are packed into one key under the window id, so the
+// doubling starts at h = h0 instead of 1.  Codes: the token + 1 when the
+// tokens are small integers; otherwise the rank of the token among the
+// distinct tokens, through a hash dictionary of the distinct tokens.
+constexpr uint64_t kDictEmpty = ~0ull;
+constexpr uint32_t kDictMaxLog = 23;  // dictionary capacity at most 2^23 slots (sigma <= 2^22)
+
+__device__ __forceinline__ uint64_t dmix(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ uint64_t token_at(const void *tokens, int tb, uint32_t i) {
+  return tb == 4 ? (uint64_t) static_cast<const uint32_t *>(tokens)[i] : static_cast<const uint64_t *>(tokens)[i];
+}
+
+// Inserts every token (a token equal to the empty marker gets the last code
+// by itself, see k_code_map); counts distinct tokens and gives up (flag)
+// past `limit` of them.
+__global__ void k_dict_tokens(const void *__restrict__ tokens, int tb, uint32_t n, uint64_t *keys, uint64_t mask,
+                              uint32_t limit, uint32_t *distinct, uint32_t *over) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (*(volatile uint32_t *)over) return;
+    const uint64_t t = token_at(tokens, tb, i);
+    if (t == kDictEmpty) continue;
+    uint64_t slot = dmix(t) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      uint64_t cur = keys[slot];
+      if (cur == t) break;
+      if (cur == kDictEmpty) {
+        cur = atomicCAS((unsigned long long *)&keys[slot], (unsigned long long)kDictEmpty,
+                        (unsigned long long)t);
+        if (cur == kDictEmpty) {
+          if (atomicAdd(distinct, 1u) >= limit) atomicExch(over, 1u);
+          break;
+        }
+        if (cur == t) break;
+      }
+      slot = (slot + 1) & mask;
+    }
+  }
+}
+
+// (token, slot) of every occupied slot, in any order (sorted next).
+__global__ void k_dict_list(const uint64_t *__restrict__ keys, uint64_t cap, uint64_t *lk, uint32_t *lv,
+                            uint32_t *count) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cap; e += (uint64_t)gridDim.x * blockDim.x) {
+    if (keys[e] == kDictEmpty) continue;
+    const uint32_t q = atomicAdd(count, 1u);
+    lk[q] = keys[e];
+    lv[q] = (uint32_t)e;
+  }
+}
+
+// code of slot = its token's rank among the distinct tokens + 1
+__global__ void k_code_scatter(const uint32_t *__restrict__ sorted_slots, uint32_t sigma, uint32_t *code) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < sigma; q += gridDim.x * blockDim.x)
+    code[sorted_slots[q]] = q + 1;
+}
+
+__global__ void k_code_map(const void *__restrict__ tokens, int tb, uint32_t n, const uint64_t *__restrict__ keys,
+                           uint64_t mask, const uint32_t *__restrict__ slot_code, uint32_t top,
+                           uint32_t *__restrict__ codes) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t t = token_at(tokens, tb, i);
+    uint32_t cd = top;  // the all-ones token: larger than every other token
+    if (t != kDictEmpty) {
+      uint64_t slot = dmix(t) & mask;
+      while (keys[slot] != t) slot = (slot + 1) & mask;
+      cd = slot_code[slot];
+    }
+    codes[i] = cd;
+  }
+}
+
+// key(i) = (window << (h0 * cb)) | code(i) code(i+1) .. code(i+h0-1), value i.
+__global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t *__restrict__ codes, uint32_t n,
+                        uint32_t h0, int cb, Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t we = win_end(W, i, n);
+    uint64_t key = 0;
+    for (uint32_t j = 0; j < h0; ++j) {
+      uint64_t cd = 0;
+      if (i + j < we) cd = codes ? codes[i + j] : token_at(tokens, tb, i + j) + 1;
+      key = (key << cb) | cd;
+    }
+    if (W.count > 1) key |= (uint64_t)win_id(W, i) << (h0 * cb);
+    keys[i] = key;
+    vals[i] = i;
+  }
+}
+
 // key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
 // value = i, with sh = bits of n (the second part is at most n).
 __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ A_dev,
@@ -207,7 +306,7 @@ constexpr int kPChunk = 16;
 template <class T>
 __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W,
                        const uint32_t *__restrict__ phi, const uint32_t *__restrict__ snaps,
-                       int levels, uint32_t *__restrict__ plcp) {
+                       int levels, uint32_t h0, uint32_t *__restrict__ plcp) {
   const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPChunk;
   if (i0 >= n) return;
   const uint32_t iend = (i0 + kPChunk) < (uint64_t)n ? (uint32_t)(i0 + kPChunk) : n;
@@ -222,12 +321,15 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W,
     if (i > i0 && win_id(W, i) != win_id(W, i - 1)) l = 0;  // a new window starts
     const uint32_t we = win_end(W, i, n);
     if (long_match(S, we, i, j, l)) {
-      // lift: level lev ranks are equal iff the next 2^lev tokens are equal
+      // lift: level lev ranks are equal iff the next h0 * 2^lev tokens are
+      // equal; what remains is shorter than h0 and is compared directly
       for (int lev = levels - 1; lev >= 0; --lev) {
         const uint64_t a = (uint64_t)i + l, b = (uint64_t)j + l;
         if (a < we && b < we && snaps[(size_t)lev * n + a] == snaps[(size_t)lev * n + b])
-          l += 1u << lev;
+          l += h0 << lev;
       }
+      for (uint32_t k = 1; k < h0 && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]; ++k)
+        ++l;
     }
     plcp[i] = l;
     l = l ? l - 1 : 0;
@@ -280,6 +382,65 @@ int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, c
   return APO_OK;
 }
 
+uint64_t dict_capacity(uint32_t n) {
+  uint64_t cap = 1;
+  while (cap < 2ull * n && cap < (1ull << kDictMaxLog)) cap <<= 1;
+  return cap;
+}
+
+// Order-preserving dense codes of the tokens (1 .. sigma, sigma + 1 for the
+// all-ones u64 token) through a dictionary of the distinct tokens; *codes_out
+// stays null when there are more than half the dictionary's capacity.
+int dictionary_codes(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tbits, uint32_t **codes_out,
+                     int *cb_out, cudaStream_t s) {
+  *codes_out = nullptr;
+  const uint64_t cap = dict_capacity(n);
+  const uint32_t limit = (uint32_t)(cap / 2);
+  uint64_t *keys = c->arena.take_n<uint64_t>(cap);
+  uint32_t *slot_code = c->arena.take_n<uint32_t>(cap);
+  uint32_t *codes = c->arena.take_n<uint32_t>(n);
+  SortBuffers lb;
+  lb.keys[0] = c->arena.take_n<uint64_t>(limit);
+  lb.keys[1] = c->arena.take_n<uint64_t>(limit);
+  lb.vals[0] = c->arena.take_n<uint32_t>(limit);
+  lb.vals[1] = c->arena.take_n<uint32_t>(limit);
+  if (!keys || !slot_code || !codes || !lb.keys[0] || !lb.keys[1] || !lb.vals[0] || !lb.vals[1]) return APO_OK;
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  APO_CUDA_TRY(cudaMemsetAsync(keys, 0xff, cap * sizeof(uint64_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, 2 * sizeof(uint32_t), s));
+  const int g = grid_for(n, 256, c->num_sms);
+  {
+    Launch lp_(c, kKDictInsert, n, s);
+    k_dict_tokens<<<g, 256, 0, s>>>(tokens, tb, n, keys, cap - 1, limit, misc + kMiscDict, misc + kMiscDict + 1);
+  }
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscDict, 8, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t sigma = c->host_pinned[0];
+  if (c->host_pinned[1] || sigma > limit) return APO_OK;
+  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, sizeof(uint32_t), s));
+  {
+    Launch lp_(c, kKDictMap, cap, s);
+    k_dict_list<<<grid_for(cap, 256, c->num_sms), 256, 0, s>>>(keys, cap, lb.keys[0], lb.vals[0],
+                                                               misc + kMiscDict);
+  }
+  lb.cur = 0;
+  const DigitRange r{0, tbits, false};
+  APO_TRY(radix_sort_pairs(c, lb, sigma, &r, 1, s));
+  {
+    Launch lp_(c, kKDictMap, sigma, s);
+    k_code_scatter<<<grid_for(std::max<uint32_t>(sigma, 1), 256, c->num_sms), 256, 0, s>>>(lb.vals[lb.cur], sigma,
+                                                                                           slot_code);
+  }
+  {
+    Launch lp_(c, kKDictMap, n, s);
+    k_code_map<<<g, 256, 0, s>>>(tokens, tb, n, keys, cap - 1, slot_code, sigma + 1, codes);
+  }
+  APO_CUDA_TRY(cudaGetLastError());
+  *codes_out = codes;
+  *cb_out = bits_for(sigma + 1);
+  return APO_OK;
+}
+
 }  // namespace
 
 int suffix_init() {
@@ -290,7 +451,9 @@ int suffix_init() {
 
 size_t suffix_workspace_bytes(uint64_t n) {
   const int levels = bits_for(n) + 2;
-  return (size_t)n * (2 * 8 + 2 * 4 + 4 * 4 + 4 + 4) + (size_t)levels * n * 4 + 16 * 256;
+  const uint64_t cap = dict_capacity((uint32_t)std::min<uint64_t>(n, 0xffffffffull));
+  return (size_t)n * (2 * 8 + 2 * 4 + 4 * 4 + 4 + 4) + (size_t)levels * n * 4 + 16 * 256 +
+         (size_t)(cap * 12 + (cap / 2) * 24 + n * 4 + 8 * 256);  // token dictionary
 }
 
 int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, SuffixState &st,
@@ -317,32 +480,66 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
   }
   // how many token bits are populated
-  uint64_t *kor = reinterpret_cast<uint64_t *>(c->ps.counters + kCtrMisc + kMiscKeyOr);
+  uint32_t *misc = c->ps.counters + kCtrMisc;
+  uint64_t *kor = reinterpret_cast<uint64_t *>(misc + kMiscKeyOr);
   APO_CUDA_TRY(cudaMemsetAsync(kor, 0, sizeof(uint64_t), s));
   launch_key_or(c, b.keys[0], n, kor, s);
   uint64_t orv = 0;
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   memcpy(&orv, c->host_pinned, sizeof(uint64_t));
-  {
-    const DigitRange r{0, bits_for(orv), false};
-    APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
+
+  // codes for the packed first keys: token + 1, or dictionary ranks when
+  // that packs more tokens per key
+  const int wb = st.win.count > 1 ? bits_for(st.win.count - 1) : 0;
+  const int tbits = bits_for(orv);
+  int cb = tbits <= 32 ? bits_for(orv + 1) : 0;
+  uint32_t h0 = cb ? (uint32_t)((64 - wb) / cb) : 0;
+  const uint32_t *codes = nullptr;
+  if (h0 < 4 && n >= 4096) {
+    uint32_t *code_arr = nullptr;
+    int cb_dict = 0;
+    APO_TRY(dictionary_codes(c, tokens, tb, n, tbits, &code_arr, &cb_dict, s));
+    if (code_arr && (uint32_t)((64 - wb) / cb_dict) > h0) {
+      codes = code_arr;
+      cb = cb_dict;
+      h0 = (uint32_t)((64 - wb) / cb);
+    }
   }
   uint32_t A = 0;
-  APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
-                  &A, s));
-  if (st.win.count > 1) {
-    // group by (window, token): re-sort by the window id over the token ranks
+  if (h0 >= 2) {
+    h0 = std::min<uint32_t>(h0, 32);
     {
       Launch lp_(c, kKInitKeys, n, s);
-      k_wkeys<<<g, 256, 0, s>>>(st.rank, st.win, n, b.keys[0], b.vals[0]);
+      k_pack0<<<g, 256, 0, s>>>(tokens, tb, codes, n, h0, cb, st.win, b.keys[0], b.vals[0]);
     }
     b.cur = 0;
-    const DigitRange r[2] = {{0, bits_for(n - 1), false}, {32, 32 + bits_for(st.win.count - 1), false}};
-    APO_TRY(radix_sort_pairs(c, b, n, r, 2, s));
+    const DigitRange r{0, wb + (int)h0 * cb, false};
+    APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
     APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
                     &A, s));
+  } else {
+    h0 = 1;
+    {
+      const DigitRange r{0, tbits, false};
+      APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
+    }
+    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
+                    &A, s));
+    if (st.win.count > 1) {
+      // group by (window, token): re-sort by the window id over the token ranks
+      {
+        Launch lp_(c, kKInitKeys, n, s);
+        k_wkeys<<<g, 256, 0, s>>>(st.rank, st.win, n, b.keys[0], b.vals[0]);
+      }
+      b.cur = 0;
+      const DigitRange r[2] = {{0, bits_for(n - 1), false}, {32, 32 + wb, false}};
+      APO_TRY(radix_sort_pairs(c, b, n, r, 2, s));
+      APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
+                      &A, s));
+    }
   }
+  st.h0 = h0;
   APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[0], st.rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   st.levels = 1;
   int cur = 0;
@@ -352,7 +549,6 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   // one; the host queues round r+1 before it has read round r's count (an
   // upper bound sizes the launches), and stops one round after the count
   // reaches 0 (that round's kernels find nothing to do and return).
-  uint32_t *misc = c->ps.counters + kCtrMisc;
   uint32_t *rc = misc + kMiscRound;
   uint32_t ub = A;  // upper bound on the current round's input count
   for (uint32_t r = 0; A > 0; ++r) {
@@ -362,7 +558,7 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     }
     const uint32_t *in = r == 0 ? misc + kMiscRefreshCount : rc + ((r - 1) & 1);
     uint32_t *out = rc + (r & 1);
-    const uint64_t h = 1ull << r;
+    const uint64_t h = (uint64_t)h0 << r;
     b.cur = 0;
     {
       Launch lp_(c, kKPack, ub, s);
@@ -417,14 +613,14 @@ int build_lcp(apo_ctx *c, const void *tokens, int tb, const SuffixState &st, uin
       Launch lp_(c, kKPlcp, n, s);
       k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, st.win, phi,
                                           st.snaps[0],
-                                          st.levels, plcp);
+                                          st.levels, st.h0, plcp);
     }
   else
     {
       Launch lp_(c, kKPlcp, n, s);
       k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, st.win, phi,
                                           st.snaps[0],
-                                          st.levels, plcp);
+                                          st.levels, st.h0, plcp);
     }
   {
     Launch lp_(c, kKLcpPerm, n, s);
