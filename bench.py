@@ -546,9 +546,9 @@ def main():
 
     def step(inputs):
         apo.hash_tasks(*inputs, out=tok)
-        r = apo.find_repeats(tok, MIN_LEN, stages=False)
+        r = apo.find_repeats(tok, MIN_LEN, stages=False, sa_lcp=True)
         e, i = apo.match_candidates(tok, None, tok, cap=cap[0], pat_start=r.trace_start,
-                                    pat_len=r.trace_len)
+                                    pat_len=r.trace_len, src_sa=r.sa, src_lcp=r.lcp)
         return r, e, i
 
     r = None

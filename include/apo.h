@@ -266,6 +266,17 @@ typedef struct {
    * trace_len outputs of apo_find_repeats over the same tokens. */
   const uint32_t *pat_start;
   const uint32_t *pat_len;
+  /* Optional, slice form only: the suffix array and LCP array of the
+   * pattern source tokens[0 .. src_n) (DEVICE arrays of src_n entries, as
+   * apo_find_repeats writes them for one window: lcp[k] pairs sa[k] with
+   * sa[k+1], lcp[src_n-1] = 0).  Every slice must lie inside the source.
+   * With them the trie, failure links and match totals are read off the
+   * source's suffix array; without them (NULL) the library builds one over
+   * the patterns.  The results are the same; APO_EINVAL if src_n does not
+   * cover the slices, APO_EDEVICE if sa is not a permutation. */
+  const uint32_t *src_sa;
+  const uint32_t *src_lcp;
+  uint64_t src_n;
 } apo_patterns;
 
 /* Match `patterns` against stream[n] (device, same token width).  Writes the

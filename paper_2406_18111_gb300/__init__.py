@@ -88,7 +88,8 @@ class apo_windows(ctypes.Structure):
 
 class apo_patterns(ctypes.Structure):
     _fields_ = [("n_patterns", _U64), ("tokens", _P), ("token_bytes", ctypes.c_int),
-                ("pat_off", _P), ("pat_start", _P), ("pat_len", _P)]
+                ("pat_off", _P), ("pat_start", _P), ("pat_len", _P), ("src_sa", _P), ("src_lcp", _P),
+                ("src_n", _U64)]
 
 
 _lib = None
@@ -237,16 +238,19 @@ class Apo:
         return out
 
     # -------------------------------------------------------------- Alg. 2
-    def find_repeats(self, tokens, min_len: int, stages: bool = True, stream=None) -> Repeats:
-        """Alg. 2 on one window of device tokens (int32 = u32, int64 = u64)."""
+    def find_repeats(self, tokens, min_len: int, stages: bool = True, stream=None,
+                     sa_lcp: bool = False) -> Repeats:
+        """Alg. 2 on one window of device tokens (int32 = u32, int64 = u64).
+        stages: also return SA, LCP and the candidates; sa_lcp: SA and LCP
+        only (what match_candidates can reuse)."""
         import torch
         n = int(tokens.shape[0])
         dev = tokens.device
         u32 = torch.int32
         M = max(1, 2 * (n - 1))
         K = max(1, n // max(1, min_len))
-        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
-        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
+        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None
+        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None
         cl = torch.empty(M, dtype=u32, device=dev) if stages else None
         ci = torch.empty(M, dtype=u32, device=dev) if stages else None
         cs = torch.empty(M, dtype=u32, device=dev) if stages else None
@@ -304,10 +308,12 @@ class Apo:
 
     # -------------------------------------------------------------- Sec. 4.3
     def match_candidates(self, pat_tokens, pat_off, stream_tokens, cap: int | None = None,
-                         stream=None, pat_start=None, pat_len=None):
+                         stream=None, pat_start=None, pat_len=None, src_sa=None, src_lcp=None):
         """All (end, pattern id) occurrences in stream_tokens, sorted.  Patterns
         are either a host CSR (pat_off) over pat_tokens, or device slices
-        (pat_start, pat_len, with pat_off None) of pat_tokens."""
+        (pat_start, pat_len, with pat_off None) of pat_tokens; for slices,
+        src_sa / src_lcp (the suffix and LCP arrays of pat_tokens, as
+        find_repeats returns them) let the automaton be read off them."""
         import torch
         n = int(stream_tokens.shape[0])
         if cap is None:
@@ -321,12 +327,13 @@ class Apo:
                              po.ctypes.data_as(_P).value, None, None)
         else:
             p = apo_patterns(int(pat_start.shape[0]), _ptr(pat_tokens), _token_bytes(pat_tokens),
-                             None, _ptr(pat_start), _ptr(pat_len))
+                             None, _ptr(pat_start), _ptr(pat_len), _ptr(src_sa), _ptr(src_lcp),
+                             int(pat_tokens.shape[0]) if src_sa is not None else 0)
         code = lib().apo_match_candidates(self._h, ctypes.byref(p), _ptr(stream_tokens), n, _ptr(end),
                                           _ptr(pid), cap, ctypes.byref(cnt), _stream_handle(stream))
         if code == APO_ECAPACITY:
             return self.match_candidates(pat_tokens, pat_off, stream_tokens, int(cnt.value), stream,
-                                         pat_start, pat_len)
+                                         pat_start, pat_len, src_sa, src_lcp)
         _check(code)
         c = int(cnt.value)
         return end[:c], pid[:c]

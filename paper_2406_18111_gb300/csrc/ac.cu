@@ -56,6 +56,7 @@
 
 #include "apo_internal.cuh"
 #include "device_util.cuh"
+#include "lcp_tree.cuh"
 
 namespace apo {
 
@@ -176,7 +177,7 @@ template <class T>
 __global__ void k_pat_layout(const T *__restrict__ tok, const uint32_t *__restrict__ pstart,
                              const uint32_t *__restrict__ plen, const uint32_t *__restrict__ tstart,
                              uint32_t P, uint32_t N, Dict d, uint32_t *__restrict__ tsym,
-                             uint64_t *__restrict__ tkey) {
+                             uint64_t *__restrict__ tkey, uint32_t *__restrict__ tpid) {
   if (blockIdx.x == 0 && threadIdx.x < kTsymPad) tsym[N + threadIdx.x] = kSep;  // past the text
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -191,6 +192,7 @@ __global__ void k_pat_layout(const T *__restrict__ tok, const uint32_t *__restri
       }
       tsym[dst + k] = c;
       tkey[dst + k] = key;
+      tpid[dst + k] = p;
     }
   }
 }
@@ -360,6 +362,111 @@ __device__ __forceinline__ uint32_t rep_of(const Sparse &S, uint32_t j, uint32_t
   return (uint32_t)max(0ll, y);
 }
 
+// ---------------------------------------------------------------- source mode
+// The patterns are slices of a source whose suffix array and LCP array are
+// given.  A pattern's key is (left end of its string's LCP interval in the
+// source, length): sorting by it is sorting the pattern strings (disjoint
+// intervals are in string order; a proper prefix has the enclosing interval
+// and sorts first at an equal left end).
+__global__ void k_isa(const uint32_t *__restrict__ sa, uint32_t n, uint32_t *__restrict__ rank, uint32_t *err) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t i = sa[k];
+    if (i < n) rank[i] = k;
+    else atomicExch(err, kDevRange);
+  }
+}
+
+__global__ void k_src_pat_keys(const uint32_t *__restrict__ pstart, const uint32_t *__restrict__ plen, uint32_t P,
+                               const uint32_t *__restrict__ rank, MinTree T, int lenbits, uint64_t *keys,
+                               uint32_t *vals, uint32_t *startlen, uint32_t *err) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint32_t st = pstart[p], len = plen[p];
+    const long long j = prev_less(T, rank[st], len, err);
+    keys[p] = ((uint64_t)(j + 1) << lenbits) | len;
+    vals[p] = p;
+    atomicMax(&startlen[st], len);
+  }
+}
+
+// slcp[j] = lcp of the sorted patterns j-1 and j (direct comparison, one
+// warp per j); jpos[p] = sorted position of pattern p.
+template <class T>
+__global__ void k_src_slcp(const T *__restrict__ tok, const uint32_t *__restrict__ pstart,
+                           const uint32_t *__restrict__ plen, const uint32_t *__restrict__ sp, uint32_t P,
+                           uint32_t *slcp, uint32_t *jpos) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < P; j += warps) {
+    const uint32_t b = sp[j];
+    if (lane == 0) jpos[b] = j;
+    uint32_t l = 0;
+    if (j > 0) {
+      const uint32_t a = sp[j - 1];
+      const uint32_t m = min(plen[a], plen[b]);
+      const T *x = tok + pstart[a], *y = tok + pstart[b];
+      for (uint32_t k0 = 0; k0 < m; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const uint32_t miss = __ballot_sync(0xffffffffu, k < m && x[k] != y[k]);
+        if (miss) {
+          l = k0 + __ffs(miss) - 1;
+          break;
+        }
+        l = min(m, k0 + 32);
+      }
+    }
+    if (lane == 0) slcp[j] = l;
+  }
+}
+
+// F(k) = max over pattern starts at suffix ranks <= k (resp. >= k) of
+// min(pattern length, LCP of the two suffixes): the scan element of rank k is
+// the map x -> max(s_k, min(x, l_k)) (s_k: longest pattern starting at SA[k],
+// l_k: the LCP towards the previous rank), and these maps compose into maps
+// of the same form, (s, l) then (s', l') = (max(s', min(s, l')), min(l, l')).
+// Both parts are clamped to 16 bits (to the longest pattern, below 2^16).
+struct OpClampCompose {
+  __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const {
+    const uint32_t as = a >> 16, al = a & 0xffffu, bs = b >> 16, bl = b & 0xffffu;
+    return (max(bs, min(as, bl)) << 16) | min(al, bl);
+  }
+};
+constexpr uint32_t kClampId = 0x0000ffffu;
+struct SrcFnLeft {
+  const uint32_t *sa, *lcp, *startlen;
+  uint32_t cap;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+    const uint32_t sv = min(startlen[sa[k]], cap), lv = k ? min(lcp[k - 1], cap) : 0u;
+    return (sv << 16) | lv;
+  }
+};
+struct SrcFnRight {
+  const uint32_t *sa, *lcp, *startlen;
+  uint32_t cap, n;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+    const uint32_t sv = min(startlen[sa[k]], cap), lv = k + 1 < n ? min(lcp[k], cap) : 0u;
+    return (sv << 16) | lv;
+  }
+};
+struct DstFnLeft {
+  uint32_t *out;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const { out[k] = v >> 16; }
+};
+struct DstFnRight {  // M of source position SA[k] = the better of both sides
+  const uint32_t *sa, *left;
+  uint32_t *mw;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t v) const { mw[sa[k]] = max(left[k], v >> 16); }
+};
+// reach(q) = q + M(q) over T, M(q) = min(the pattern's remaining length,
+// M of the source position), a segment starting at each pattern
+struct SrcReachSrc {
+  const uint32_t *tsym, *tpid, *tstart, *plen, *pstart, *mw;
+  __device__ __forceinline__ uint32_t operator()(uint32_t q) const {
+    if (q == 0 || tsym[q - 1] == kSep) return kFlag;
+    const uint32_t p = tpid[q], o = q - tstart[p], rem = plen[p] - o;
+    return q + (rem ? min(rem, mw[pstart[p] + o]) : 0u);
+  }
+};
+
 // ---------------------------------------------------------------- nodes and links
 struct NodeArgs {
   const uint32_t *tstart, *plen, *tsym;
@@ -371,6 +478,13 @@ struct NodeArgs {
   uint32_t *fail, *own, *end_node;
   uint8_t *has_branch;  // [nodes] 1 if a branch-table edge leaves the node
   uint32_t *err;
+  // source mode (the patterns are slices of a source with a known suffix
+  // array): failure nodes are found through the source's LCP intervals
+  bool src;
+  const uint32_t *pstart, *src_rank;
+  const uint64_t *skey;  // sorted pattern keys (LCP-interval left end << lenbits | length)
+  MinTree T;             // over the source LCP
+  int lenbits;
 };
 
 __device__ __forceinline__ void table_insert(const Table &g, uint32_t u, uint32_t c, uint32_t v,
@@ -417,18 +531,34 @@ __global__ void k_ac_nodes(NodeArgs a) {
             if (a.reach[mid] >= e) hi = mid;
             else lo = mid + 1;
           }
-          const uint32_t fd = e - lo, k = a.rank[lo];
-          uint32_t cnt = 0, hi2 = a.P;  // starts before SA index k
-          while (cnt < hi2) {
-            const uint32_t mid = (cnt + hi2) >> 1;
-            if (a.sr[mid] < k) cnt = mid + 1;
-            else hi2 = mid;
-          }
-          const uint32_t jj = (a.left[k] >= fd) ? cnt - 1 : cnt;
-          if (jj >= a.P) {
-            atomicExch(a.err, kDevRange);
+          const uint32_t fd = e - lo;
+          if (a.src) {
+            // the string's LCP interval in the source; the first pattern in
+            // sorted order whose key is not below (left end, fd) starts with it
+            const uint32_t r = a.src_rank[a.pstart[i] + (lo - S)];
+            const uint64_t key = ((uint64_t)(prev_less(a.T, r, fd, a.err) + 1) << a.lenbits) | fd;
+            uint32_t jl = 0, jh = a.P;
+            while (jl < jh) {
+              const uint32_t mid = (jl + jh) >> 1;
+              if (a.skey[mid] < key) jl = mid + 1;
+              else jh = mid;
+            }
+            if (jl >= a.P) atomicExch(a.err, kDevRange);
+            else f = a.tstart[a.sp[jl]] + fd - 1;
           } else {
-            f = node_of(a, jj, fd);
+            const uint32_t k = a.rank[lo];
+            uint32_t cnt = 0, hi2 = a.P;  // starts before SA index k
+            while (cnt < hi2) {
+              const uint32_t mid = (cnt + hi2) >> 1;
+              if (a.sr[mid] < k) cnt = mid + 1;
+              else hi2 = mid;
+            }
+            const uint32_t jj = (a.left[k] >= fd) ? cnt - 1 : cnt;
+            if (jj >= a.P) {
+              atomicExch(a.err, kDevRange);
+            } else {
+              f = node_of(a, jj, fd);
+            }
           }
         }
         if (d == sl + 1) {
@@ -891,15 +1021,19 @@ int sa_levels(uint64_t maxlen) { return bits_for(maxlen + 1) + 3; }
 }  // namespace
 
 size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint64_t extent,
-                             uint64_t maxlen) {
+                             uint64_t maxlen, uint64_t src_n) {
   const uint64_t N = total_tokens + P;  // pattern text with separators
   const uint64_t tbl = pow2_at_least(2 * (P + 1));
   const uint64_t dct = pow2_at_least(2 * (extent + 1));
-    const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
-  return suffix_workspace_bytes(N) + (uint64_t)sa_levels(maxlen) * N * 4 +
-         N * (4 + 8 + 4 + 4 + 4 + 1 + 4 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * (16 + 8) +
-         tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 +
-         96 * 256;
+  const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
+  // pattern text (symbols, sort tokens, pattern ids, reach) and the per-node arrays
+  uint64_t bytes = N * (8 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * (16 + 8) +
+                   tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + 96 * 256;
+  if (src_n)  // source ranks, start lengths, both interval scans, the LCP min-tree
+    bytes += src_n * 16 + (src_n / 31 + 1) * 4 + kMaxTree * 256;
+  else  // the suffix array, LCP and nearest-start scans of the pattern text
+    bytes += suffix_workspace_bytes(N) + (uint64_t)sa_levels(maxlen) * N * 4 + N * (4 + 1 + 4 + 4);
+  return bytes;
 }
 
 namespace {
@@ -979,7 +1113,15 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
               "plus patterns");
     return APO_EINVAL;
   }
-  APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent, maxlen)));
+  // source mode: the slices' source comes with its suffix and LCP arrays
+  bool srcm = !pp->pat_off && pp->src_sa && pp->src_lcp;
+  if (srcm && (pp->src_n < extent || pp->src_n >= 0xffffffffull)) {
+    set_error("match_candidates: src_n does not cover the pattern slices");
+    return APO_EINVAL;
+  }
+  if (srcm && maxlen >= 0xffff) srcm = false;  // the interval scans hold lengths in 16 bits
+  const uint32_t src_n = srcm ? (uint32_t)pp->src_n : 0u;
+  APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent, maxlen, src_n)));
   const uint32_t N = (uint32_t)(total + P);  // pattern text with separators
   const uint32_t root = N;                   // node ids are T positions; the root is N
   const uint64_t tbl = pow2_at_least(2 * (P + 1));
@@ -993,11 +1135,18 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *tstart = c->arena.take_n<uint32_t>(P);
   uint32_t *tsym = c->arena.take_n<uint32_t>((size_t)N + kTsymPad);
   uint64_t *tkey = c->arena.take_n<uint64_t>(N);
-  uint32_t *lcp = c->arena.take_n<uint32_t>(N);
-  uint8_t *is_start = c->arena.take_n<uint8_t>(N);
-  uint32_t *left = c->arena.take_n<uint32_t>(N);
-  uint32_t *right = c->arena.take_n<uint32_t>(N);
+  uint32_t *tpid = c->arena.take_n<uint32_t>(N);
   uint32_t *reach = c->arena.take_n<uint32_t>(N);
+  // pattern-text suffix array (not in source mode)
+  uint32_t *lcp = srcm ? nullptr : c->arena.take_n<uint32_t>(N);
+  uint8_t *is_start = srcm ? nullptr : c->arena.take_n<uint8_t>(N);
+  uint32_t *left = srcm ? nullptr : c->arena.take_n<uint32_t>(N);
+  uint32_t *right = srcm ? nullptr : c->arena.take_n<uint32_t>(N);
+  // source mode
+  uint32_t *src_rank = srcm ? c->arena.take_n<uint32_t>(src_n) : nullptr;
+  uint32_t *startlen = srcm ? c->arena.take_n<uint32_t>(src_n) : nullptr;
+  uint32_t *fl = srcm ? c->arena.take_n<uint32_t>(src_n) : nullptr;
+  uint32_t *mw = srcm ? c->arena.take_n<uint32_t>(src_n) : nullptr;
   uint32_t *fail = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint32_t *own = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint64_t *wj = c->arena.take_n<uint64_t>((size_t)N + 1);
@@ -1014,9 +1163,9 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *sparse = c->arena.take_n<uint32_t>((size_t)nsparse * P);
   SuffixState st;
   st.n = N;
-  st.sa = c->arena.take_n<uint32_t>(N);
-  st.rank = c->arena.take_n<uint32_t>(N);
-  uint32_t *snap_base = c->arena.take_n<uint32_t>((size_t)levels * N);
+  st.sa = srcm ? nullptr : c->arena.take_n<uint32_t>(N);
+  st.rank = srcm ? nullptr : c->arena.take_n<uint32_t>(N);
+  uint32_t *snap_base = srcm ? nullptr : c->arena.take_n<uint32_t>((size_t)levels * N);
   SortBuffers b, be;
   for (SortBuffers *x : {&b, &be}) {
     x->keys[0] = c->arena.take_n<uint64_t>(P);
@@ -1024,10 +1173,12 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     x->vals[0] = c->arena.take_n<uint32_t>(P);
     x->vals[1] = c->arena.take_n<uint32_t>(P);
   }
-  if (!g.keys || !d.keys || (pp->pat_off && !pbuf) || !tstart || !tsym || !tkey || !lcp || !is_start ||
-      !left || !right || !reach || !fail || !own || !wj || !jl || !mtotal || !skip || !has_branch || !recidx || !firstrec || !rec || !sr ||
-      !jpos || !end_node || !sparse || !st.sa || !st.rank || !snap_base || !b.keys[0] || !b.keys[1] ||
-      !b.vals[0] || !b.vals[1] || !be.keys[0] || !be.keys[1] || !be.vals[0] || !be.vals[1]) {
+  const bool sa_mode_ok = srcm || (lcp && is_start && left && right && st.sa && st.rank && snap_base);
+  const bool src_mode_ok = !srcm || (src_rank && startlen && fl && mw);
+  if (!g.keys || !d.keys || (pp->pat_off && !pbuf) || !tstart || !tsym || !tkey || !tpid || !reach ||
+      !sa_mode_ok || !src_mode_ok || !fail || !own || !wj || !jl || !mtotal || !skip || !has_branch || !recidx ||
+      !firstrec || !rec || !sr || !jpos || !end_node || !sparse || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
+      !b.vals[1] || !be.keys[0] || !be.keys[1] || !be.vals[0] || !be.vals[1]) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
   }
@@ -1062,10 +1213,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     const int blocks = std::max(1, std::min(ceil_div(P, 8), sms * 16));
     if (tb == 4)
       k_pat_layout<<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(pp->tokens), pstart, plen, tstart,
-                                          P, N, d, tsym, tkey);
+                                          P, N, d, tsym, tkey, tpid);
     else
       k_pat_layout<<<blocks, 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens), pstart, plen, tstart,
-                                          P, N, d, tsym, tkey);
+                                          P, N, d, tsym, tkey, tpid);
   }
   if (n) {
     Launch lp_(c, kKDictMap, n, s);
@@ -1076,43 +1227,88 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   APO_CUDA_TRY(cudaGetLastError());
 
-  // suffix array and LCP of the pattern text
-  {
-    ScopeGuard scope(c);
-    uint32_t *snaps[64];
-    for (int k = 0; k < levels; ++k) snaps[k] = snap_base + (size_t)k * N;
-    st.snaps = snaps;
-    uint32_t rounds = 0;
-    APO_TRY(build_suffix_array(c, tkey, 8, N, st, levels, &rounds, s));
-    APO_TRY(build_lcp(c, tkey, 8, st, lcp, s));
-  }
+  const uint32_t *sp = nullptr;
+  const uint64_t *skey = nullptr;
+  MinTree src_tree;
+  const int lenbits = std::max(1, bits_for(maxlen));
+  if (srcm) {
+    // the patterns in string order by their LCP intervals in the source, the
+    // start-to-start lcps, and M over the source positions
+    const int g = grid_for(src_n, 256, sms);
+    {
+      Launch lp_(c, kKStarts, src_n, s);
+      k_isa<<<g, 256, 0, s>>>(pp->src_sa, src_n, src_rank, c->ps.err);
+    }
+    APO_TRY(build_min_tree(c, pp->src_lcp, src_n, &src_tree, s));
+    APO_CUDA_TRY(cudaMemsetAsync(startlen, 0, (size_t)src_n * 4, s));
+    {
+      Launch lp_(c, kKStarts, P, s);
+      k_src_pat_keys<<<grid_for(P, 256, sms), 256, 0, s>>>(pstart, plen, P, src_rank, src_tree, lenbits,
+                                                           b.keys[0], b.vals[0], startlen, c->ps.err);
+    }
+    b.cur = 0;
+    {
+      const DigitRange r{0, bits_for(src_n - 1) + lenbits, false};
+      APO_TRY(radix_sort_pairs(c, b, P, &r, 1, s));
+    }
+    sp = b.vals[b.cur];
+    skey = b.keys[b.cur];
+    {
+      Launch lp_(c, kKStarts, P, s);
+      const int blocks = std::max(1, std::min(ceil_div(P, 8), sms * 16));
+      if (tb == 4)
+        k_src_slcp<<<blocks, 256, 0, s>>>(static_cast<const uint32_t *>(pp->tokens), pstart, plen, sp, P, sparse,
+                                          jpos);
+      else
+        k_src_slcp<<<blocks, 256, 0, s>>>(static_cast<const uint64_t *>(pp->tokens), pstart, plen, sp, P, sparse,
+                                          jpos);
+    }
+    const uint32_t capv = (uint32_t)maxlen;
+    APO_TRY(seg_scan<false>(c, SrcFnLeft{pp->src_sa, pp->src_lcp, startlen, capv}, DstFnLeft{fl}, src_n,
+                            OpClampCompose(), kClampId, s));
+    APO_TRY(seg_scan<true>(c, SrcFnRight{pp->src_sa, pp->src_lcp, startlen, capv, src_n},
+                           DstFnRight{pp->src_sa, fl, mw}, src_n, OpClampCompose(), kClampId, s));
+    APO_TRY(seg_scan<false>(c, SrcReachSrc{tsym, tpid, tstart, plen, pstart, mw}, DstValue{reach}, N,
+                            OpSegMax(), kSegMaxId, s));
+  } else {
+    // suffix array and LCP of the pattern text
+    {
+      ScopeGuard scope(c);
+      uint32_t *snaps[64];
+      for (int k = 0; k < levels; ++k) snaps[k] = snap_base + (size_t)k * N;
+      st.snaps = snaps;
+      uint32_t rounds = 0;
+      APO_TRY(build_suffix_array(c, tkey, 8, N, st, levels, &rounds, s));
+      APO_TRY(build_lcp(c, tkey, 8, st, lcp, s));
+    }
 
-  // pattern starts in suffix order
-  {
-    Launch lp_(c, kKStarts, P, s);
-    k_start_keys<<<grid_for(P, 256, sms), 256, 0, s>>>(tstart, st.rank, P, b.keys[0], b.vals[0]);
+    // pattern starts in suffix order
+    {
+      Launch lp_(c, kKStarts, P, s);
+      k_start_keys<<<grid_for(P, 256, sms), 256, 0, s>>>(tstart, st.rank, P, b.keys[0], b.vals[0]);
+    }
+    b.cur = 0;
+    {
+      const DigitRange r{0, bits_for(N - 1), false};
+      APO_TRY(radix_sort_pairs(c, b, P, &r, 1, s));
+    }
+    sp = b.vals[b.cur];
+    APO_CUDA_TRY(cudaMemsetAsync(is_start, 0, N, s));
+    {
+      Launch lp_(c, kKStarts, P, s);
+      k_start_mark<<<grid_for(P, 256, sms), 256, 0, s>>>(b.keys[b.cur], sp, P, sr, jpos, is_start);
+    }
+    // lcp with the nearest pattern start on each side in suffix order, the
+    // start-to-start lcps, and the running maximum of the reach over T
+    APO_TRY(seg_scan<false>(c, SrcLeft{lcp, is_start}, DstFlagged{left}, N, OpSegMin(), kSegMinId, s));
+    {
+      Launch lp_(c, kKStarts, P, s);
+      k_slcp<<<grid_for(P, 256, sms), 256, 0, s>>>(sr, left, P, sparse);
+    }
+    APO_TRY(seg_scan<true>(c, SrcRight{lcp, is_start, N}, DstFlagged{right}, N, OpSegMin(), kSegMinId, s));
+    APO_TRY(seg_scan<false>(c, SrcReach{tkey, st.rank, left, right, P}, DstValue{reach}, N, OpSegMax(),
+                            kSegMaxId, s));
   }
-  b.cur = 0;
-  {
-    const DigitRange r{0, bits_for(N - 1), false};
-    APO_TRY(radix_sort_pairs(c, b, P, &r, 1, s));
-  }
-  const uint32_t *sp = b.vals[b.cur];
-  APO_CUDA_TRY(cudaMemsetAsync(is_start, 0, N, s));
-  {
-    Launch lp_(c, kKStarts, P, s);
-    k_start_mark<<<grid_for(P, 256, sms), 256, 0, s>>>(b.keys[b.cur], sp, P, sr, jpos, is_start);
-  }
-  // lcp with the nearest pattern start on each side in suffix order, the
-  // start-to-start lcps, and the running maximum of the reach over T
-  APO_TRY(seg_scan<false>(c, SrcLeft{lcp, is_start}, DstFlagged{left}, N, OpSegMin(), kSegMinId, s));
-  {
-    Launch lp_(c, kKStarts, P, s);
-    k_slcp<<<grid_for(P, 256, sms), 256, 0, s>>>(sr, left, P, sparse);
-  }
-  APO_TRY(seg_scan<true>(c, SrcRight{lcp, is_start, N}, DstFlagged{right}, N, OpSegMin(), kSegMinId, s));
-  APO_TRY(seg_scan<false>(c, SrcReach{tkey, st.rank, left, right, P}, DstValue{reach}, N, OpSegMax(),
-                          kSegMaxId, s));
   Sparse S;
   S.nlev = nsparse;
   S.lev[0] = sparse;
@@ -1150,6 +1346,12 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.end_node = end_node;
     a.has_branch = has_branch;
     a.err = c->ps.err;
+    a.src = srcm;
+    a.pstart = pstart;
+    a.src_rank = src_rank;
+    a.skey = skey;
+    a.T = src_tree;
+    a.lenbits = lenbits;
     Launch lp_(c, kKAcNodes, N, s);
     k_ac_nodes<<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
   }

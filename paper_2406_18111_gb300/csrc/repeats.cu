@@ -33,31 +33,11 @@
 
 #include "apo_internal.cuh"
 #include "device_util.cuh"
+#include "lcp_tree.cuh"
 
 namespace apo {
 
 namespace {
-
-constexpr int kMaxTree = 8;
-
-struct MinTree {
-  const uint32_t *lv[kMaxTree];
-  uint32_t cnt[kMaxTree];
-  int nlev;
-};
-
-__global__ void k_min32(const uint32_t *__restrict__ in, uint32_t nin, uint32_t *__restrict__ out,
-                        uint32_t nout) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nout; b += warps) {
-    const uint32_t i = b * 32 + lane;
-    uint32_t v = i < nin ? in[i] : 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) out[b] = v;
-  }
-}
 
 __global__ void k_max_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t *out) {
   uint32_t m = 0;
@@ -66,36 +46,6 @@ __global__ void k_max_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t *
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-}
-
-// Largest j < k with level-0 value < l, or -1.
-__device__ long long prev_less(const MinTree &T, uint32_t k, uint32_t l, uint32_t *err) {
-  uint32_t x = k;
-  for (int lev = 0; lev < T.nlev; ++lev) {
-    const uint32_t *a = T.lv[lev];
-    const uint32_t lo = x & ~31u;
-    for (uint32_t j = x; j > lo;) {
-      --j;
-      if (a[j] < l) {
-        uint32_t idx = j;
-        for (int d = lev; d > 0; --d) {
-          const uint32_t *b = T.lv[d - 1];
-          const uint32_t first = idx * 32;
-          uint32_t jj = min(first + 32, T.cnt[d - 1]);
-          while (jj > first && b[jj - 1] >= l) --jj;
-          if (jj == first) {
-            atomicExch(err, kDevRange);
-            return -1;
-          }
-          idx = jj - 1;
-        }
-        return idx;
-      }
-    }
-    if (lo == 0) return -1;
-    x = lo >> 5;
-  }
-  return -1;
 }
 
 // Alg. 2 first loop.  Each kept pair writes two (key, start) entries with
@@ -583,6 +533,44 @@ int copy_out(T *dst, const T *src, uint64_t count, uint64_t cap, bool *over, cud
 
 }  // namespace
 
+__global__ void k_min32(const uint32_t *__restrict__ in, uint32_t nin, uint32_t *__restrict__ out,
+                        uint32_t nout) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nout; b += warps) {
+    const uint32_t i = b * 32 + lane;
+    uint32_t v = i < nin ? in[i] : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) out[b] = v;
+  }
+}
+
+int build_min_tree(apo_ctx *c, const uint32_t *lcp, uint32_t n, MinTree *T, cudaStream_t s) {
+  T->lv[0] = lcp;
+  T->cnt[0] = n;
+  T->nlev = 1;
+  while (T->cnt[T->nlev - 1] > 32) {
+    if (T->nlev >= kMaxTree) {
+      set_error("LCP min-tree: array too large");
+      return APO_EINVAL;
+    }
+    const uint32_t nin = T->cnt[T->nlev - 1], nout = (nin + 31) / 32;
+    uint32_t *o = c->arena.take_n<uint32_t>(nout);
+    if (!o) return APO_ENOMEM;
+    {
+      Launch lp_(c, kKMin32, nin, s);
+      const int blocks = std::max(1, std::min(ceil_div((long long)nout * 32, 256), c->num_sms * 16));
+      k_min32<<<blocks, 256, 0, s>>>(T->lv[T->nlev - 1], nin, o, nout);
+    }
+    T->lv[T->nlev] = o;
+    T->cnt[T->nlev] = nout;
+    ++T->nlev;
+  }
+  APO_CUDA_TRY(cudaGetLastError());
+  return APO_OK;
+}
+
 int repeats_init(int smem_optin) {
   // k_greedy: dynamic = bitmap (shared-memory variants) + survivor list;
   // static = 2 * 4 * 32 + 1 words
@@ -649,26 +637,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
 
   // 32-ary min-tree over LCP
   MinTree T;
-  T.lv[0] = lcp;
-  T.cnt[0] = n;
-  T.nlev = 1;
-  while (T.cnt[T.nlev - 1] > 32) {
-    if (T.nlev >= kMaxTree) {
-      set_error("repeats: window too large for the LCP min-tree");
-      return APO_EINVAL;
-    }
-    const uint32_t nin = T.cnt[T.nlev - 1], nout = (nin + 31) / 32;
-    uint32_t *o = c->arena.take_n<uint32_t>(nout);
-    if (!o) return APO_ENOMEM;
-    {
-      Launch lp_(c, kKMin32, nin, s);
-      k_min32<<<grid_for((uint64_t)nout * 32, 256, c->num_sms), 256, 0, s>>>(T.lv[T.nlev - 1], nin, o,
-                                                                             nout);
-    }
-    T.lv[T.nlev] = o;
-    T.cnt[T.nlev] = nout;
-    ++T.nlev;
-  }
+  APO_TRY(build_min_tree(c, lcp, n, &T, s));
 
   // candidates
   const uint64_t M = 2ull * (n - 1);

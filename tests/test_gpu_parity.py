@@ -269,6 +269,47 @@ def test_match_traces_slice_form(apo):
     assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
 
 
+@pytest.mark.parametrize("n,tb", [(1 << 14, 8), ((1 << 16) + 77, 8), (20000, 4)])
+def test_match_source_mode(apo, n, tb):
+    """Slices matched with the source's suffix and LCP arrays given (the
+    automaton read off the source's suffix array): the same matches as the
+    oracle, and as the call that builds a suffix array of the patterns; also
+    arbitrary overlapping, nested and duplicate slices."""
+    from paper_2406_18111_gb300 import as_u32
+    import torch
+    if tb == 8:
+        tok = oracle.hash_tasks(W.config2_tasks(n, seed=9))
+    else:
+        tok, _, _ = W.config3_windows(1, seed0=41)
+        tok = tok[:n].astype(np.uint64)
+    t = tokens_dev(tok, tb)
+    r = apo.find_repeats(t, 5, stages=False, sa_lcp=True)
+    starts = [as_u32(r.trace_start).astype(np.int64)]
+    lens = [as_u32(r.trace_len).astype(np.int64)]
+    rng = np.random.default_rng(n)
+    k = 300
+    a = rng.integers(0, len(tok) - 1, k)
+    l = np.minimum(rng.integers(1, 400, k), len(tok) - a)
+    starts.append(a)
+    lens.append(l)
+    starts.append(starts[0][:20])  # duplicates
+    lens.append(lens[0][:20])
+    ps = np.concatenate(starts)
+    pl = np.concatenate(lens)
+    dps = dev(ps.astype(np.uint32), np.int32)
+    dpl = dev(pl.astype(np.uint32), np.int32)
+    e1, i1 = apo.match_candidates(t, None, t, pat_start=dps, pat_len=dpl, src_sa=r.sa, src_lcp=r.lcp)
+    e2, i2 = apo.match_candidates(t, None, t, pat_start=dps, pat_len=dpl)
+    assert np.array_equal(as_u32(e1), as_u32(e2)) and np.array_equal(as_u32(i1), as_u32(i2))
+    off = np.zeros(len(pl) + 1, np.uint64)
+    off[1:] = np.cumsum(pl)
+    pt = np.concatenate([tok[x:x + y] for x, y in zip(ps, pl)])
+    oe, oi = oracle.match(pt, off, tok)
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e1), oe) and np.array_equal(as_u32(i1), oi)
+    del torch
+
+
 # ---------------------------------------------------------------- batched form
 def _window_slice(res, w, name, off_name):
     from paper_2406_18111_gb300 import as_u32
