@@ -244,6 +244,55 @@ double apo_server_now(apo_server *srv);
 int apo_server_destroy(apo_server *srv);
 
 /* ------------------------------------------------------------------------
+ * Online trace finder -- Alg. 1's TraceFinder with Sec. 4.4's sampling of
+ * the history buffer by the exponentiated ruler function.
+ *
+ * Tokens arrive in issue order (apo_finder_push, any chunk sizes).  The
+ * finder keeps the most recent `buffer_tokens` of them.  After every `unit`
+ * tokens (analysis point i = 1, 2, ...) it hands the most recent
+ * unit * 2^ruler(i) tokens (ruler(i): how many times 2 divides i), at most
+ * the buffer and at most what has arrived, to the server as one
+ * asynchronous FindRepeats (Alg. 2) request.  Completed analyses come back
+ * in analysis order through apo_finder_poll, with trace starts in stream
+ * coordinates (token index since the first push).  Total tokens analysed
+ * over a stream of n tokens grow as n log(buffer/unit), so the work is
+ * O(n log^2 n) for Alg. 2's O(n log n) per slice (Sec. 4.4).
+ * ---------------------------------------------------------------------- */
+typedef struct apo_finder apo_finder;
+
+typedef struct {
+  uint64_t buffer_tokens;  /* history buffer size (the paper uses 5000) */
+  uint64_t unit;           /* analysis period and smallest slice (250 or 500) */
+} apo_finder_config;
+
+typedef struct {
+  uint64_t index;          /* analysis point i (1-based) */
+  uint64_t slice_start;    /* stream position of the slice's first token */
+  uint64_t slice_len;
+  int status;              /* the request's status */
+  uint64_t n_traces;
+  const uint32_t *trace_len;    /* HOST, valid until the next poll or destroy */
+  const uint64_t *trace_start;  /* stream coordinates */
+  double t_submit, t_done;      /* server clock */
+} apo_finder_result;
+
+/* A finder feeding `server` (tokens of the server's token width, min_len of
+ * the server).  APO_EINVAL for unit = 0 or buffer_tokens < unit. */
+int apo_finder_create(apo_finder **out, apo_server *server, const apo_finder_config *cfg);
+/* Append n tokens (HOST, copied); submits the analyses whose points are
+ * reached.  *submitted (optional) receives how many were submitted. */
+int apo_finder_push(apo_finder *f, const void *tokens, uint64_t n, uint64_t *submitted);
+/* The oldest submitted analysis not yet returned: APO_OK and *out filled
+ * if it is done, APO_EAGAIN if it is still running, APO_ECAPACITY if there
+ * is none outstanding.  With wait != 0, blocks until it is done. */
+int apo_finder_poll(apo_finder *f, int wait, apo_finder_result *out);
+/* Totals so far: tokens pushed, analyses submitted, tokens analysed. */
+int apo_finder_stats(apo_finder *f, uint64_t *pushed, uint64_t *analyses, uint64_t *analysed_tokens);
+/* Releases the outstanding requests (waiting for them) and frees the finder;
+ * the server stays. */
+int apo_finder_destroy(apo_finder *f);
+
+/* ------------------------------------------------------------------------
  * Candidate matching -- Sec. 4.3: the candidate traces are ingested into a
  * trie, and pointers advanced through the trie as tokens arrive report a
  * trace whenever one ends.  Computed here with an Aho-Corasick automaton

@@ -182,3 +182,38 @@ def match(pat_tokens, pat_off, stream, naive: bool = False):
     i = np.zeros(max(1, cnt), np.uint32)
     lib().ora_match(_p(pt), _p(po), P, _p(st), st.shape[0], int(naive), _p(e), _p(i), cnt)
     return e[:cnt], i[:cnt]
+
+
+def ruler(i: int) -> int:
+    """The ruler function of Sec. 4.4: how many times 2 divides i (i >= 1)."""
+    r = 0
+    while i % 2 == 0:
+        i //= 2
+        r += 1
+    return r
+
+
+def ruler_schedule(n_tokens: int, unit: int, buffer: int):
+    """The analysis slices of Sec. 4.4's sampling over a stream of n_tokens:
+    after every `unit` tokens (point i = 1, 2, ...), the most recent
+    unit * 2^ruler(i) tokens, at most the buffer and what has arrived.
+    Returns [(i, start, length)]."""
+    out = []
+    for i in range(1, n_tokens // unit + 1):
+        end = i * unit
+        length = min(unit * 2 ** ruler(i), buffer, end)
+        out.append((i, end - length, length))
+    return out
+
+
+def online_traces(S, unit: int, buffer: int, min_len: int):
+    """Alg. 1's TraceFinder with the ruler sampling: Alg. 2 on every slice
+    of ruler_schedule, traces in stream coordinates.  Returns
+    [(i, start, length, trace_len, trace_start)]."""
+    S = np.asarray(S)
+    out = []
+    for i, start, length in ruler_schedule(len(S), unit, buffer):
+        r = find_repeats(S[start:start + length].astype(np.uint64), min_len)
+        out.append((i, start, length, r.trace_len.astype(np.uint32),
+                    r.trace_start.astype(np.uint64) + np.uint64(start)))
+    return out

@@ -33,7 +33,8 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_profile_enable", "apo_profile_reset",
            "apo_profile_read", "apo_greedy_select_noalloc", "apo_server_create", "apo_server_submit",
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
-           "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read")
+           "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read", "apo_finder_create",
+           "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -397,6 +398,86 @@ class ServedResult:
     t_start: float
     t_done: float
     batch_windows: int
+
+
+class apo_finder_config(ctypes.Structure):
+    _fields_ = [("buffer_tokens", _U64), ("unit", _U64)]
+
+
+class apo_finder_result(ctypes.Structure):
+    _fields_ = [("index", _U64), ("slice_start", _U64), ("slice_len", _U64), ("status", ctypes.c_int),
+                ("n_traces", _U64), ("trace_len", _P), ("trace_start", _P), ("t_submit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+@dataclass
+class FinderResult:
+    index: int
+    slice_start: int
+    slice_len: int
+    trace_len: np.ndarray
+    trace_start: np.ndarray
+    t_submit: float
+    t_done: float
+
+
+class Finder:
+    """Alg. 1's online TraceFinder with Sec. 4.4's ruler-function sampling
+    (apo_finder_*): push tokens as they are issued; every `unit` tokens the
+    most recent unit * 2^ruler(i) tokens (at most `buffer_tokens`) go to the
+    server as one asynchronous analysis; poll returns them in order."""
+
+    def __init__(self, server: "Server", buffer_tokens: int = 5000, unit: int = 250):
+        self.server = server
+        h = _P()
+        cfg = apo_finder_config(buffer_tokens, unit)
+        _check(lib().apo_finder_create(ctypes.byref(h), server._h, ctypes.byref(cfg)))
+        self._h = h
+
+    def push(self, tokens) -> int:
+        a = np.ascontiguousarray(np.asarray(tokens).astype(self.server._dt, copy=False))
+        subs = _U64(0)
+        _check(lib().apo_finder_push(self._h, a.ctypes.data_as(_P).value, a.shape[0], ctypes.byref(subs)))
+        return int(subs.value)
+
+    def poll(self, wait: bool = False):
+        """The next analysis in order, or None (still running / none left)."""
+        r = apo_finder_result()
+        code = lib().apo_finder_poll(self._h, int(wait), ctypes.byref(r))
+        if code in (APO_EAGAIN, APO_ECAPACITY):
+            return None
+        _check(code)
+        _check(r.status)
+        k = int(r.n_traces)
+        tl = (np.ctypeslib.as_array(ctypes.cast(r.trace_len, ctypes.POINTER(ctypes.c_uint32)), shape=(k,)).copy()
+              if k else np.zeros(0, np.uint32))
+        ts = (np.ctypeslib.as_array(ctypes.cast(r.trace_start, ctypes.POINTER(ctypes.c_uint64)), shape=(k,)).copy()
+              if k else np.zeros(0, np.uint64))
+        return FinderResult(int(r.index), int(r.slice_start), int(r.slice_len), tl, ts, r.t_submit, r.t_done)
+
+    def drain(self) -> list:
+        out = []
+        while True:
+            r = self.poll(wait=True)
+            if r is None:
+                return out
+            out.append(r)
+
+    def stats(self) -> dict:
+        a, b, c = _U64(0), _U64(0), _U64(0)
+        _check(lib().apo_finder_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"pushed": int(a.value), "analyses": int(b.value), "analysed_tokens": int(c.value)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().apo_finder_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

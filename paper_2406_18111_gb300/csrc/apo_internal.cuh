@@ -273,6 +273,9 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int token_bytes, const 
 // ---------------------------------------------------------------- hashing
 void launch_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *out, cudaStream_t s);
 
+// ---------------------------------------------------------------- served form
+int server_token_bytes(apo_server *s);
+
 // ---------------------------------------------------------------- matching
 int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
                    uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,

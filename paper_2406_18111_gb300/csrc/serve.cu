@@ -204,6 +204,10 @@ void fill(const Request &r, apo_request_result *o) {
 
 }  // namespace
 
+namespace apo {
+int server_token_bytes(apo_server *s) { return s->cfg.token_bytes; }
+}  // namespace apo
+
 extern "C" {
 
 int apo_server_create(apo_server **out, int device, const apo_server_config *cfg) {

@@ -425,3 +425,39 @@ def test_match_config5_full(apo):
     oe, oi = oracle.match(pt, off, stream)
     assert len(oe) > 0
     assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
+
+
+# ---------------------------------------------------------------- online finder (Sec. 4.4)
+@pytest.mark.parametrize("unit,buffer,tb", [(250, 5000, 8), (100, 1000, 4)])
+def test_finder_ruler_sampling_equals_oracle(apo, unit, buffer, tb):
+    """Tokens pushed in uneven chunks: the analyses are the ruler-function
+    slices, each with the oracle's traces (stream coordinates), in order."""
+    from paper_2406_18111_gb300 import Finder, Server
+    if tb == 8:
+        S = oracle.hash_tasks(W.config2_tasks(12000, seed=17))
+    else:
+        S = (np.arange(9000) % 37).astype(np.uint32)
+        S[W.uniform_int(18, 300, 0, 8999)] = 500
+    srv = Server(0, min_len=5, token_bytes=tb, max_batch_tokens=1 << 20, max_batch_windows=64, lanes=2)
+    f = Finder(srv, buffer_tokens=buffer, unit=unit)
+    rng = np.random.default_rng(unit)
+    pos = 0
+    got = []
+    while pos < len(S):
+        k = int(rng.integers(1, 3 * unit))
+        f.push(S[pos:pos + k])
+        pos += k
+        r = f.poll()
+        if r is not None:
+            got.append(r)
+    got += f.drain()
+    want = oracle.online_traces(S, unit, buffer, 5)
+    assert len(got) == len(want) == len(S) // unit
+    for g, (i, start, length, tl, ts) in zip(got, want):
+        assert (g.index, g.slice_start, g.slice_len) == (i, start, length)
+        assert np.array_equal(g.trace_len, tl) and np.array_equal(g.trace_start, ts), i
+    st = f.stats()
+    assert st["analyses"] == len(want)
+    assert st["analysed_tokens"] == sum(w[2] for w in want)
+    f.close()
+    srv.close()

@@ -265,3 +265,46 @@ def test_match_bruteforce_random():
         for naive in (False, True):
             e, i = oracle.match(toks, off, text, naive)
             assert list(zip(e.tolist(), i.tolist())) == want
+
+
+# ---------------------------------------------------------------- Sec. 4.4 sampling
+def test_ruler_function_values():
+    # Sec. 4.4: applied to 1, 2, 3, 4, ... the ruler function gives 0, 1, 0, 2, ...
+    assert [oracle.ruler(i) for i in range(1, 9)] == [0, 1, 0, 2, 0, 1, 0, 3]
+    # its powers of two: 1, 2, 1, 4, ...
+    assert [2 ** oracle.ruler(i) for i in range(1, 5)] == [1, 2, 1, 4]
+
+
+def test_ruler_schedule_paper_examples():
+    # Sec. 4.4: with a buffer of four, the first task, the first two, the
+    # third, then all four
+    assert oracle.ruler_schedule(4, 1, 4) == [(1, 0, 1), (2, 0, 2), (3, 2, 1), (4, 0, 4)]
+    # Fig. (buffer of size 8): after task i, the slice labelled i ends at i
+    # with 2^ruler(i) tasks
+    sched = oracle.ruler_schedule(8, 1, 8)
+    assert [l for _, _, l in sched] == [1, 2, 1, 4, 1, 2, 1, 8]
+    assert all(s + l == i for i, s, l in sched)
+    # the buffer caps a slice, and so do the tokens that have arrived
+    assert oracle.ruler_schedule(32, 1, 8)[15] == (16, 8, 8)
+    assert oracle.ruler_schedule(1000, 250, 5000)[3] == (4, 0, 1000)
+
+
+def test_ruler_schedule_total_work():
+    # tokens analysed grow as n log(buffer / unit): per analysis point the
+    # mean slice is unit * (1 + log2(buffer/unit) / 2) at most (Sec. 4.4)
+    import math
+    unit, buffer = 250, 5000
+    for n in (10 ** 4, 10 ** 5, 10 ** 6):
+        sched = oracle.ruler_schedule(n, unit, buffer)
+        total = sum(l for _, _, l in sched)
+        assert total <= n * (1 + math.log2(buffer / unit) / 2 + 1)
+        assert total >= n  # every token is analysed at least once
+
+
+def test_online_traces_slices():
+    S = [j % 7 for j in range(3000)]
+    res = oracle.online_traces(S, 250, 1000, 5)
+    assert [r[:3] for r in res] == oracle.ruler_schedule(3000, 250, 1000)
+    for i, start, length, tl, ts in res:
+        # every trace lies inside its slice
+        assert np.all(ts >= start) and np.all(ts + tl <= start + length)
