@@ -154,7 +154,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
@@ -437,6 +437,69 @@ def run_served(args, rank, world, local, emit=True):
     return out
 
 
+def run_finder(args, rank, world, local, emit=True):
+    """Alg. 1's online TraceFinder with Sec. 4.4's ruler-function sampling
+    (history buffer 5000 tokens, unit 250) over a stream of 2^20 hashed task
+    descriptors pushed in chunks of 1000 as fast as the host issues them;
+    every analysis is an asynchronous request of the served form."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo, Finder, Server
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    n = args.n_tasks
+    ts = W.config2_tasks(n, seed=2 + rank)
+    dts = [torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(dev)
+           for a, dt in ((ts.task_id, np.int32), (ts.arg_off, np.int32), (ts.region, np.int32),
+                         (ts.field_mask, np.int64), (ts.priv, np.uint8))]
+    tok = apo.hash_tasks(*dts).cpu().numpy().view(np.uint64)
+    unit, buffer, chunk = 250, 5000, 1000
+    srv = Server(local, min_len=MIN_LEN, token_bytes=8, max_batch_tokens=1 << 22, max_batch_windows=256,
+                 lanes=args.lanes)
+    warm = Finder(srv, buffer_tokens=buffer, unit=unit)  # first-use work (workspace, shape trials)
+    warm.push(tok[:200000])
+    warm.drain()
+    warm.close()
+    clocks = Clocks(local)
+    f = Finder(srv, buffer_tokens=buffer, unit=unit)
+    res = []
+    t0 = time.perf_counter()
+    for a in range(0, n, chunk):
+        f.push(tok[a:a + chunk])
+        while True:
+            r = f.poll()
+            if r is None:
+                break
+            res.append(r)
+    t_push = time.perf_counter() - t0
+    res += f.drain()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = f.stats()
+    f.close()
+    srv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res]) * 1e3
+    import math
+    out = {"metric": "online trace finder: stream tokens/s (ruler-sampled analyses, Sec. 4.4)",
+           "value": n * world / wall, "unit": UNIT, "n_gpus": world, "steps": len(res), "warmup": 1,
+           "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": f"{n} hashed task descriptors (config-2 structure) pushed {chunk} at a time; "
+                                  f"history buffer {buffer}, unit {unit}; analyses on the served form "
+                                  f"({args.lanes} lanes)",
+                      "analyses": st["analyses"], "analysed_tokens": st["analysed_tokens"],
+                      "analysed_per_token": st["analysed_tokens"] / n,
+                      "log2_buffer_over_unit": math.log2(buffer / unit)},
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "push_s": t_push, "wall_s": wall, "traces_found": int(sum(len(r.trace_len) for r in res)),
+           "clocks": clk}
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
+
+
 def run_match(args, rank, world, local, emit=True):
     """Aho-Corasick matching (Sec. 4.3) of 10,000 candidate traces (lengths
     log-uniform 5..2000; half copied from the stream, half random) against a
@@ -500,7 +563,7 @@ def main():
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in ("batched", "served", "match"):
+    if args.workload in ("batched", "served", "match", "finder"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -515,6 +578,8 @@ def main():
             return run_served(args, rank, world, local)
         if args.workload == "match":
             return run_match(args, rank, world, local)
+        if args.workload == "finder":
+            return run_finder(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch
@@ -694,6 +759,8 @@ def main():
         sv = run_served(a3, rank, world, local, emit=False)
         line["served"] = {k: sv[k] for k in ("value", "unit", "p50_ms", "p99_ms", "config",
                                               "mean_batch_windows")}
+        fd = run_finder(args, rank, world, local, emit=False)
+        line["finder"] = {k: fd[k] for k in ("metric", "value", "unit", "p50_ms", "p99_ms", "config")}
     print(json.dumps(line))
 
 
