@@ -191,6 +191,9 @@ int ensure_lookback(apo_ctx *c, size_t words);
 // Grows the context's side buffer to `bytes` (waits for the stream first).
 int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s);
 int check_device_error(apo_ctx *c, cudaStream_t s);
+// Pinned slot that receives the device error word alongside a count read.
+constexpr int kPinnedErr = 15;
+int device_error_status(apo_ctx *c, cudaStream_t s);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline int bits_for(uint64_t v) {  // number of bits to represent values 0..v

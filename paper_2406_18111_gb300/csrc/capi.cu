@@ -129,12 +129,23 @@ Launch::~Launch() {
   }
 }
 
+// Reads the device error word on the call's stream (after everything queued
+// before it); clears it when set.
 int check_device_error(apo_ctx *c, cudaStream_t s) {
-  (void)s;
-  uint32_t e = 0;
-  APO_CUDA_TRY(cudaMemcpy(&e, c->ps.err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  return device_error_status(c, s);
+}
+
+// The error word already copied to the pinned slot by the caller's last
+// synchronised read.
+int device_error_status(apo_ctx *c, cudaStream_t s) {
+  const uint32_t e = c->host_pinned[kPinnedErr];
   if (e == kDevOk) return APO_OK;
-  APO_CUDA_TRY(cudaMemset(c->ps.err, 0, sizeof(uint32_t)));
+  c->host_pinned[kPinnedErr] = kDevOk;
+  APO_CUDA_TRY(cudaMemsetAsync(c->ps.err, 0, sizeof(uint32_t), s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
   if (e == kDevTimeout) {
     set_error("a bounded device-side wait gave up");
     return APO_ETIMEOUT;

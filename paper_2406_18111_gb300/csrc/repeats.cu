@@ -39,14 +39,6 @@ namespace apo {
 
 namespace {
 
-__global__ void k_max_u32(const uint32_t *__restrict__ a, uint32_t n, uint32_t *out) {
-  uint32_t m = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    m = max(m, a[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-}
 
 // Alg. 2 first loop.  Each kept pair writes two (key, start) entries with
 // key = (window << (bl + bi)) | ((lmax - l) << bi) | id.  Pairs that straddle
@@ -498,10 +490,13 @@ inline int grid_for(uint64_t n, int threads, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
+// A device count and the error word in one synchronisation.
 int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
+  APO_TRY(device_error_status(c, s));
   *host = c->host_pinned[0];
   return APO_OK;
 }
@@ -617,15 +612,10 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   uint32_t *misc = c->ps.counters + kCtrMisc;
   const int g = grid_for(n, 256, c->num_sms);
 
-  // bits of the (window, length, id) key
-  APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscMaxLen, 0, sizeof(uint32_t), s));
-  {
-    Launch lp_(c, kKMax, n, s);
-    k_max_u32<<<g, 256, 0, s>>>(lcp, n, misc + kMiscMaxLen);
-  }
-  uint32_t maxlcp = 0;
-  APO_TRY(read_u32(c, misc + kMiscMaxLen, &maxlcp, s));
-  const int bl = std::max(1, bits_for(maxlcp));
+  // bits of the (window, length, id) key: after the last doubling round no
+  // two suffixes share h0 * 2^rounds tokens, so every LCP is below that
+  const uint64_t lcp_bound = ((uint64_t)st.h0 << std::max(0, st.levels - 1)) - 1;
+  const int bl = std::max(1, bits_for(std::min<uint64_t>(lcp_bound, n)));
   const uint32_t lmax = (uint32_t)((1ull << bl) - 1);
   const int bi = std::max(1, bits_for(n - 1));
   const int bs = bi;
