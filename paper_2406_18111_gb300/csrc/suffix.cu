@@ -389,54 +389,70 @@ uint64_t dict_capacity(uint32_t n) {
 }
 
 // Order-preserving dense codes of the tokens (1 .. sigma, sigma + 1 for the
-// all-ones u64 token) through a dictionary of the distinct tokens; *codes_out
-// stays null when there are more than half the dictionary's capacity.
-int dictionary_codes(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tbits, uint32_t **codes_out,
-                     int *cb_out, cudaStream_t s) {
-  *codes_out = nullptr;
-  const uint64_t cap = dict_capacity(n);
-  const uint32_t limit = (uint32_t)(cap / 2);
-  uint64_t *keys = c->arena.take_n<uint64_t>(cap);
-  uint32_t *slot_code = c->arena.take_n<uint32_t>(cap);
-  uint32_t *codes = c->arena.take_n<uint32_t>(n);
+// all-ones u64 token) through a dictionary of the distinct tokens.  begin
+// queues the inserts and the read-back of the distinct count and overflow
+// flag (pinned words 2 and 3); finish, after the caller's synchronisation,
+// leaves *codes_out null when there are more than half the dictionary's
+// capacity of distinct tokens.
+struct DictCodes {
+  uint64_t cap = 0;
+  uint64_t *keys = nullptr;
+  uint32_t *slot_code = nullptr, *codes = nullptr;
   SortBuffers lb;
-  lb.keys[0] = c->arena.take_n<uint64_t>(limit);
-  lb.keys[1] = c->arena.take_n<uint64_t>(limit);
-  lb.vals[0] = c->arena.take_n<uint32_t>(limit);
-  lb.vals[1] = c->arena.take_n<uint32_t>(limit);
-  if (!keys || !slot_code || !codes || !lb.keys[0] || !lb.keys[1] || !lb.vals[0] || !lb.vals[1]) return APO_OK;
+  bool ok = false;
+};
+
+int dictionary_begin(apo_ctx *c, const void *tokens, int tb, uint32_t n, DictCodes *d, cudaStream_t s) {
+  d->cap = dict_capacity(n);
+  const uint32_t limit = (uint32_t)(d->cap / 2);
+  d->keys = c->arena.take_n<uint64_t>(d->cap);
+  d->slot_code = c->arena.take_n<uint32_t>(d->cap);
+  d->codes = c->arena.take_n<uint32_t>(n);
+  d->lb.keys[0] = c->arena.take_n<uint64_t>(limit);
+  d->lb.keys[1] = c->arena.take_n<uint64_t>(limit);
+  d->lb.vals[0] = c->arena.take_n<uint32_t>(limit);
+  d->lb.vals[1] = c->arena.take_n<uint32_t>(limit);
+  d->ok = d->keys && d->slot_code && d->codes && d->lb.keys[0] && d->lb.keys[1] && d->lb.vals[0] && d->lb.vals[1];
+  if (!d->ok) return APO_OK;
   uint32_t *misc = c->ps.counters + kCtrMisc;
-  APO_CUDA_TRY(cudaMemsetAsync(keys, 0xff, cap * sizeof(uint64_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(d->keys, 0xff, d->cap * sizeof(uint64_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, 2 * sizeof(uint32_t), s));
-  const int g = grid_for(n, 256, c->num_sms);
   {
     Launch lp_(c, kKDictInsert, n, s);
-    k_dict_tokens<<<g, 256, 0, s>>>(tokens, tb, n, keys, cap - 1, limit, misc + kMiscDict, misc + kMiscDict + 1);
+    k_dict_tokens<<<grid_for(n, 256, c->num_sms), 256, 0, s>>>(tokens, tb, n, d->keys, d->cap - 1, limit,
+                                                               misc + kMiscDict, misc + kMiscDict + 1);
   }
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscDict, 8, cudaMemcpyDeviceToHost, s));
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  const uint32_t sigma = c->host_pinned[0];
-  if (c->host_pinned[1] || sigma > limit) return APO_OK;
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, misc + kMiscDict, 8, cudaMemcpyDeviceToHost, s));
+  return APO_OK;
+}
+
+int dictionary_finish(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tbits, DictCodes *d,
+                      uint32_t **codes_out, int *cb_out, cudaStream_t s) {
+  *codes_out = nullptr;
+  const uint32_t sigma = c->host_pinned[2];
+  if (!d->ok || c->host_pinned[3] || sigma > d->cap / 2) return APO_OK;
+  uint32_t *misc = c->ps.counters + kCtrMisc;
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, sizeof(uint32_t), s));
   {
-    Launch lp_(c, kKDictMap, cap, s);
-    k_dict_list<<<grid_for(cap, 256, c->num_sms), 256, 0, s>>>(keys, cap, lb.keys[0], lb.vals[0],
-                                                               misc + kMiscDict);
+    Launch lp_(c, kKDictMap, d->cap, s);
+    k_dict_list<<<grid_for(d->cap, 256, c->num_sms), 256, 0, s>>>(d->keys, d->cap, d->lb.keys[0], d->lb.vals[0],
+                                                                  misc + kMiscDict);
   }
-  lb.cur = 0;
+  d->lb.cur = 0;
   const DigitRange r{0, tbits, false};
-  APO_TRY(radix_sort_pairs(c, lb, sigma, &r, 1, s));
+  APO_TRY(radix_sort_pairs(c, d->lb, sigma, &r, 1, s));
   {
     Launch lp_(c, kKDictMap, sigma, s);
-    k_code_scatter<<<grid_for(std::max<uint32_t>(sigma, 1), 256, c->num_sms), 256, 0, s>>>(lb.vals[lb.cur], sigma,
-                                                                                           slot_code);
+    k_code_scatter<<<grid_for(std::max<uint32_t>(sigma, 1), 256, c->num_sms), 256, 0, s>>>(d->lb.vals[d->lb.cur],
+                                                                                           sigma, d->slot_code);
   }
   {
     Launch lp_(c, kKDictMap, n, s);
-    k_code_map<<<g, 256, 0, s>>>(tokens, tb, n, keys, cap - 1, slot_code, sigma + 1, codes);
+    k_code_map<<<grid_for(n, 256, c->num_sms), 256, 0, s>>>(tokens, tb, n, d->keys, d->cap - 1, d->slot_code,
+                                                            sigma + 1, d->codes);
   }
   APO_CUDA_TRY(cudaGetLastError());
-  *codes_out = codes;
+  *codes_out = d->codes;
   *cb_out = bits_for(sigma + 1);
   return APO_OK;
 }
@@ -479,11 +495,15 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     Launch lp_(c, kKInitKeys, n, s);
     k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
   }
-  // how many token bits are populated
+  // how many token bits are populated (for u64 tokens the dictionary of
+  // distinct tokens is filled in the same round trip)
   uint32_t *misc = c->ps.counters + kCtrMisc;
   uint64_t *kor = reinterpret_cast<uint64_t *>(misc + kMiscKeyOr);
   APO_CUDA_TRY(cudaMemsetAsync(kor, 0, sizeof(uint64_t), s));
   launch_key_or(c, b.keys[0], n, kor, s);
+  DictCodes dict;
+  const bool dict_early = tb == 8 && n >= 4096;
+  if (dict_early) APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
   uint64_t orv = 0;
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -499,7 +519,11 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   if (h0 < 4 && n >= 4096) {
     uint32_t *code_arr = nullptr;
     int cb_dict = 0;
-    APO_TRY(dictionary_codes(c, tokens, tb, n, tbits, &code_arr, &cb_dict, s));
+    if (!dict_early) {
+      APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
+      APO_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    APO_TRY(dictionary_finish(c, tokens, tb, n, tbits, &dict, &code_arr, &cb_dict, s));
     if (code_arr && (uint32_t)((64 - wb) / cb_dict) > h0) {
       codes = code_arr;
       cb = cb_dict;
@@ -516,16 +540,18 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     b.cur = 0;
     const DigitRange r{0, wb + (int)h0 * cb, false};
     APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
-    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
-                    &A, s));
+    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
+                           pos[0], n, misc + kMiscRefreshCount, s));
+    A = n;  // an upper bound: the count stays on the device
   } else {
     h0 = 1;
     {
       const DigitRange r{0, tbits, false};
       APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
     }
-    APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
-                    &A, s));
+    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
+                           pos[0], n, misc + kMiscRefreshCount, s));
+    A = n;  // an upper bound: the count stays on the device
     if (st.win.count > 1) {
       // group by (window, token): re-sort by the window id over the token ranks
       {
@@ -535,8 +561,9 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       b.cur = 0;
       const DigitRange r[2] = {{0, bits_for(n - 1), false}, {32, 32 + wb, false}};
       APO_TRY(radix_sort_pairs(c, b, n, r, 2, s));
-      APO_TRY(refresh(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, -1, st.sa, st.rank, act[0], pos[0], n,
-                      &A, s));
+      APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
+                           pos[0], n, misc + kMiscRefreshCount, s));
+    A = n;  // an upper bound: the count stays on the device
     }
   }
   st.h0 = h0;
@@ -573,10 +600,17 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[st.levels], st.rank, (size_t)n * 4,
                                  cudaMemcpyDeviceToDevice, s));
     ++st.levels;
+    if (r == 0)  // round 0's input count, also unknown on the host so far
+      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 6, in, 4, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 4 + (r & 1), out, 4, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaEventRecord(c->round_ev[r & 1], s));
     if (r > 0) {
       APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
+      if (r == 1 && c->host_pinned[6] == 0) {  // the first sort left no group: rounds 0 and 1 idle
+        st.levels -= 2;
+        rounds = 0;
+        break;
+      }
       const uint32_t a = c->host_pinned[4 + ((r - 1) & 1)];  // round r's input count
       if (a == 0) {  // round r had nothing to do
         --st.levels;
@@ -586,8 +620,6 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     }
     ++rounds;
   }
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
   *rounds_out = rounds;
   return APO_OK;
 }
