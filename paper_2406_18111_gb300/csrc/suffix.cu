@@ -30,8 +30,8 @@ namespace apo {
 namespace {
 
 constexpr int kRT = 256;            // refresh threads per block
-constexpr int kRI = 16;             // consecutive elements per thread
-constexpr int kRTile = kRT * kRI;   // 4096
+constexpr int kRI = 4;              // consecutive elements per thread
+constexpr int kRTile = kRT * kRI;   // 1024
 constexpr uint32_t kNone = 0xffffffffu;
 constexpr size_t kRefreshSmem = (size_t)(kRTile + 2) * 8 + (size_t)kRTile * 8;
 
