@@ -261,7 +261,7 @@ struct DstValue {
 
 // Inclusive scan over n elements (in reverse index order when kReverse), one
 // 4096-element tile per block, tiles chained by decoupled look-back.
-constexpr int kGT = 256, kGI = 16, kGTile = kGT * kGI;
+constexpr int kGT = 256, kGI = 8, kGTile = kGT * kGI;
 template <bool kReverse, class Src, class Op, class Dst>
 __global__ void __launch_bounds__(kGT) k_seg_scan(Src src, Dst dst, uint32_t n, Op op, uint32_t ident,
                                                   uint64_t *status, uint32_t *tile_ctr, uint32_t epoch,
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(32 * kStateWarps)
 
 // Exclusive prefix sum of total[state[x]] over stream positions (the first
 // output slot of each position), decoupled look-back.
-constexpr int kST = 256, kSI = 16, kSTile = kST * kSI;
+constexpr int kST = 256, kSI = 8, kSTile = kST * kSI;
 __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restrict__ state,
                                                        const uint32_t *__restrict__ total, uint32_t n,
                                                        uint32_t *__restrict__ off, uint32_t *sum_out,

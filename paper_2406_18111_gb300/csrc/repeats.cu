@@ -97,7 +97,7 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
 
 // Order-preserving compaction of the indices k < m with pred(k) (one
 // decoupled look-back sum-scan).
-constexpr int kCT = 256, kCI = 16, kCTile = kCT * kCI;
+constexpr int kCT = 256, kCI = 8, kCTile = kCT * kCI;
 
 struct PredFirstOfRun {  // k starts a run of identical (key, value) pairs
   const uint64_t *keys;
