@@ -297,13 +297,16 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
           qe = qs + sl[q] - 1;
           free = !marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe);
         }
-        uint32_t ov = 0;  // earlier lanes of the batch whose interval meets this lane's
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const uint32_t js = ss[q0 + j], je = js + sl[q0 + j] - 1;  // list has room past total
-          if (j < lane && (uint32_t)j < nb && js <= qe && qs <= je) ov |= 1u << j;
-        }
         uint32_t und = __ballot_sync(0xffffffffu, free), accm = 0;
+        if (und == 0) continue;  // every survivor of the batch met an accepted interval meanwhile
+        uint32_t ov = 0;  // earlier lanes of the batch whose interval meets this lane's
+        if (und & (und - 1)) {  // a single free lane needs no overlap test
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const uint32_t js = ss[q0 + j], je = js + sl[q0 + j] - 1;  // list has room past total
+            if (j < lane && (uint32_t)j < nb && js <= qe && qs <= je) ov |= 1u << j;
+          }
+        }
         while (und) {
           const bool mine = (und >> lane) & 1u;
           const uint32_t take = __ballot_sync(0xffffffffu, mine && (ov & (und | accm)) == 0);
