@@ -249,6 +249,36 @@ def test_invalid_arguments(apo):
         apo.find_repeats(t.to(torch.int16), 1)
     with pytest.raises(ApoError):
         apo.match_candidates(t, np.array([0, 2, 2], np.uint64), t)
+    # source mode: the source arrays must cover the slices
+    r = apo.find_repeats(t, 1, stages=False, sa_lcp=True)
+    ps = dev(np.array([0, 5], np.uint32), np.int32)
+    pl = dev(np.array([3, 5], np.uint32), np.int32)
+    with pytest.raises(ApoError):
+        apo.match_candidates(t[:6], None, t, pat_start=ps, pat_len=pl, src_sa=r.sa[:6], src_lcp=r.lcp[:6])
+    # sort-shape modes: 0, 1 and 2 + k for the six shapes, nothing else
+    for bad in (-1, 8):
+        with pytest.raises(ApoError):
+            apo.sort_tuning(bad)
+
+
+def test_match_source_mode_edges(apo):
+    """Source mode at the edges: one-token patterns, a pattern that is the
+    whole source, patterns ending at the source's end, a constant source."""
+    from paper_2406_18111_gb300 import as_u32
+    for S in (np.array([3, 1, 4, 1, 5, 9, 2, 6, 5, 3, 5], np.uint32), np.full(40, 7, np.uint32),
+              (np.arange(50) % 3).astype(np.uint32)):
+        n = len(S)
+        t = tokens_dev(S, 4)
+        r = apo.find_repeats(t, 1, stages=False, sa_lcp=True)
+        starts = np.array([0, n - 1, 0, n - 3, 1, 2, 2], np.uint32)
+        lens = np.array([1, 1, n, 3, 2, n - 2, 1], np.uint32)
+        e1, i1 = apo.match_candidates(t, None, t, pat_start=dev(starts, np.int32), pat_len=dev(lens, np.int32),
+                                      src_sa=r.sa, src_lcp=r.lcp)
+        off = np.zeros(len(lens) + 1, np.uint64)
+        off[1:] = np.cumsum(lens)
+        pt = np.concatenate([S[a:a + l] for a, l in zip(starts, lens)]).astype(np.uint64)
+        oe, oi = oracle.match(pt, off, S.astype(np.uint64))
+        assert np.array_equal(as_u32(e1), oe) and np.array_equal(as_u32(i1), oi)
 
 
 def test_match_traces_slice_form(apo):
