@@ -221,6 +221,20 @@ constexpr int kFromValue = 256;  // place flag: the digit comes from the value
 // the launch (so a sort can be queued before its count reaches the host).
 int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
                      cudaStream_t s, const uint32_t *n_dev = nullptr);
+// The same in two steps, for a caller that counts the first digit place
+// while it writes the keys: sort_plan picks the shape (tuning it if needed)
+// and the places; the caller clears sort_first_hist() (sort_first_hist_clear),
+// adds the counts of place[0] (digit width `bits`) into it, and runs
+// radix_sort_planned with hist_ready.
+struct SortPlan {
+  int shape = -1, bits = 8, places = 0;
+  int place[12];
+};
+int sort_plan(apo_ctx *c, uint32_t n, const DigitRange *ranges, int nranges, SortPlan *out, cudaStream_t s);
+int sort_first_hist_clear(apo_ctx *c, cudaStream_t s);
+uint32_t *sort_first_hist(apo_ctx *c);
+int radix_sort_planned(apo_ctx *c, SortBuffers &b, uint32_t n, const SortPlan &sp, cudaStream_t s,
+                       const uint32_t *n_dev, bool hist_ready);
 // OR of all keys (to learn how many digits are populated); result in *out_dev.
 void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
 int radix_sort_init();

@@ -280,16 +280,18 @@ int plan(const Shape &sh, const DigitRange *ranges, int nranges, Places *pl) {
 
 // All passes of one sort with one shape (b.cur flips once per pass).
 int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const uint32_t *n_dev, const Places &pl,
-              bool count, cudaStream_t s) {
+              bool count, cudaStream_t s, bool hist_ready = false) {
   const int R = 1 << sh.bits;
   const int tile = sh.threads * sh.items;
   const int tiles = ceil_div(n, tile);
   APO_TRY(ensure_lookback(c, (size_t)tiles * R));
   uint32_t *hist = c->ps.counters + kCtrSortHist;   // [kMaxPass][kMaxRadix]
   uint32_t *tctr = c->ps.counters + kCtrSortTiles;  // [kMaxPass]
-  APO_CUDA_TRY(cudaMemsetAsync(hist, 0, (kMaxPass * kMaxRadix + kMaxPass) * sizeof(uint32_t), s));
-  const int hblocks = std::max(1, std::min(c->num_sms * 4, ceil_div(n, kHistThreads * 8)));
-  {
+  if (hist_ready) {  // the first place's counts are in; clear the others and the tile tickets
+    APO_CUDA_TRY(cudaMemsetAsync(hist + kMaxRadix, 0, ((kMaxPass - 1) * kMaxRadix + kMaxPass) * sizeof(uint32_t), s));
+  } else {
+    APO_CUDA_TRY(cudaMemsetAsync(hist, 0, (kMaxPass * kMaxRadix + kMaxPass) * sizeof(uint32_t), s));
+    const int hblocks = std::max(1, std::min(c->num_sms * 4, ceil_div(n, kHistThreads * 8)));
     Launch lp_(c, count ? kKRsHist : kKRsTune, n, s);
     sh.hist<<<hblocks, kHistThreads, 0, s>>>(b.keys[b.cur], b.vals[b.cur], n, n_dev, pl.p[0], hist);
   }
@@ -407,8 +409,8 @@ void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_d
   }
 }
 
-int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
-                     cudaStream_t s, const uint32_t *n_dev) {
+int sort_plan(apo_ctx *c, uint32_t n, const DigitRange *ranges, int nranges, SortPlan *out, cudaStream_t s) {
+  out->shape = -1;
   int bits = 0;
   for (int r = 0; r < nranges; ++r) bits += std::max(0, ranges[r].hi - ranges[r].lo);
   if (n <= 1 || bits == 0) return APO_OK;
@@ -437,7 +439,34 @@ int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *r
     set_error("radix sort: too many digit places");
     return APO_EINVAL;
   }
-  return sort_with(c, kShapes[shape_id], b, n, n_dev, pl, true, s);
+  out->shape = shape_id;
+  out->bits = kShapes[shape_id].bits;
+  out->places = pl.n;
+  for (int p = 0; p < pl.n; ++p) out->place[p] = pl.p[p];
+  return APO_OK;
+}
+
+int sort_first_hist_clear(apo_ctx *c, cudaStream_t s) {
+  APO_CUDA_TRY(cudaMemsetAsync(c->ps.counters + kCtrSortHist, 0, kMaxRadix * sizeof(uint32_t), s));
+  return APO_OK;
+}
+
+uint32_t *sort_first_hist(apo_ctx *c) { return c->ps.counters + kCtrSortHist; }
+
+int radix_sort_planned(apo_ctx *c, SortBuffers &b, uint32_t n, const SortPlan &sp, cudaStream_t s,
+                       const uint32_t *n_dev, bool hist_ready) {
+  if (sp.shape < 0) return APO_OK;
+  Places pl;
+  pl.n = sp.places;
+  for (int p = 0; p < sp.places; ++p) pl.p[p] = sp.place[p];
+  return sort_with(c, kShapes[sp.shape], b, n, n_dev, pl, true, s, hist_ready);
+}
+
+int radix_sort_pairs(apo_ctx *c, SortBuffers &b, uint32_t n, const DigitRange *ranges, int nranges,
+                     cudaStream_t s, const uint32_t *n_dev) {
+  SortPlan sp;
+  APO_TRY(sort_plan(c, n, ranges, nranges, &sp, s));
+  return radix_sort_planned(c, b, n, sp, s, n_dev, false);
 }
 
 int sort_shape_count() { return kNumShapes; }

@@ -258,17 +258,40 @@ __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t 
 
 // key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
 // value = i, with sh = bits of n (the second part is at most n).
+// Also counts the digits of the sort's first place (key bits [shift,
+// shift + dbits)) into hist, which saves the sort its own pass over the keys.
 __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ A_dev,
                        const uint32_t *__restrict__ rank, uint32_t n, uint64_t h, int sh, Windows W,
-                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *hist, int shift,
+                       int dbits) {
+  __shared__ uint32_t cnt[512];
+  const uint32_t R = 1u << dbits, lane = threadIdx.x & 31;
+  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) cnt[q] = 0;
+  __syncthreads();
   if (A_dev) A = min(A, *A_dev);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < A; k += gridDim.x * blockDim.x) {
-    const uint32_t i = act[k];
-    const uint64_t j = i + h;
-    const uint32_t r2 = j < win_end(W, i, n) ? rank[j] + 1u : 0u;
-    keys[k] = ((uint64_t)rank[i] << sh) | r2;
-    vals[k] = i;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t k0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < A; k0 += stride) {
+    const uint32_t k = k0 + lane;
+    uint32_t d = R;
+    if (k < A) {
+      const uint32_t i = act[k];
+      const uint64_t j = i + h;
+      const uint32_t r2 = j < win_end(W, i, n) ? rank[j] + 1u : 0u;
+      const uint64_t key = ((uint64_t)rank[i] << sh) | r2;
+      keys[k] = key;
+      vals[k] = i;
+      d = (uint32_t)(key >> shift) & (R - 1);
+    }
+    const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+    if (__all_sync(0xffffffffu, d == d0 && d0 < R)) {
+      if (lane == 0) atomicAdd(&cnt[d0], 32u);
+    } else if (d < R) {
+      atomicAdd(&cnt[d], 1u);
+    }
   }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
+    if (cnt[q]) atomicAdd(&hist[q], cnt[q]);
 }
 
 // Batched first round: key = (window << 32) | rank of the token among all
@@ -587,13 +610,17 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     uint32_t *out = rc + (r & 1);
     const uint64_t h = (uint64_t)h0 << r;
     b.cur = 0;
+    const DigitRange dr{0, minor_bits + major_bits, false};
+    SortPlan sp;
+    APO_TRY(sort_plan(c, ub, &dr, 1, &sp, s));
+    APO_TRY(sort_first_hist_clear(c, s));
     {
       Launch lp_(c, kKPack, ub, s);
-      k_pack<<<grid_for(ub, 256, c->num_sms), 256, 0, s>>>(act[cur], ub, in, st.rank, n, h, minor_bits,
-                                                             st.win, b.keys[0], b.vals[0]);
+      const int blocks = std::max(1, std::min(ceil_div(ub, 256), c->num_sms * 4));
+      k_pack<<<blocks, 256, 0, s>>>(act[cur], ub, in, st.rank, n, h, minor_bits, st.win, b.keys[0], b.vals[0],
+                                    sort_first_hist(c), sp.shape >= 0 ? (sp.place[0] & 255) : 0, sp.bits);
     }
-    const DigitRange dr{0, minor_bits + major_bits, false};
-    APO_TRY(radix_sort_pairs(c, b, ub, &dr, 1, s, in));
+    APO_TRY(radix_sort_planned(c, b, ub, sp, s, in, true));
     APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], ub, in, pos[cur], minor_bits, st.sa, st.rank,
                            act[cur ^ 1], pos[cur ^ 1], n, out, s));
     cur ^= 1;
