@@ -72,8 +72,14 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
     }
     uint64_t key = 0;
     if (ok) {
+      // with several windows, the id and the start are relative to the
+      // window (its suffixes occupy a contiguous SA range starting at its
+      // offset), which keeps the key and value digits to the longest window
+      const uint32_t w = win_id(W, a), wbase = W.off_dev ? W.off_dev[w] : 0u;
       const long long j = prev_less(T, k, l, err);
-      key = ((uint64_t)win_id(W, a) << (bl + bi)) | ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1);
+      key = ((uint64_t)w << (bl + bi)) | ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1 - wbase);
+      a -= wbase;
+      b -= wbase;
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, ok);
     if (bal == 0) continue;
@@ -152,15 +158,16 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, uint32_t
 
 __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
                               const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                              int bi, int bl, uint32_t lmax, uint32_t *__restrict__ cl,
-                              uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
+                              int bi, int bl, uint32_t lmax, const uint32_t *__restrict__ woff,
+                              uint32_t *__restrict__ cl, uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
     const uint64_t key = keys[k];
+    const uint32_t base = woff ? woff[(uint32_t)(key >> (bl + bi))] : 0u;  // back to global positions
     cl[q] = lmax - (uint32_t)((key >> bi) & lmax);
-    cid[q] = (uint32_t)(key & idmask);
-    cs[q] = vals[k];
+    cid[q] = (uint32_t)(key & idmask) + base;
+    cs[q] = vals[k] + base;
   }
 }
 
@@ -620,7 +627,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   const uint64_t lcp_bound = ((uint64_t)st.h0 << std::max(0, st.levels - 1)) - 1;
   const int bl = std::max(1, bits_for(std::min<uint64_t>(lcp_bound, n)));
   const uint32_t lmax = (uint32_t)((1ull << bl) - 1);
-  const int bi = std::max(1, bits_for(n - 1));
+  // ids and starts are window-relative with several windows
+  const int bi = std::max(1, bits_for((W.count > 1 ? W.max_len : n) - 1));
   const int bs = bi;
   const int bw = W.count > 1 ? bits_for(W.count - 1) : 0;
   if (bw + bl + bi > 64) {
@@ -675,7 +683,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     {
       Launch lp_(c, kKCandGather, m, s);
       k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur], b.vals[b.cur],
-                                                                 bi, bl, lmax, cl, cid, cs);
+                                                                 bi, bl, lmax, W.count > 1 ? W.off_dev : nullptr,
+                                                                 cl, cid, cs);
     }
   }
 
