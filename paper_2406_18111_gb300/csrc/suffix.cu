@@ -256,8 +256,10 @@ __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t 
   }
 }
 
-// key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0),
-// value = i, with sh = bits of n (the second part is at most n).
+// key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0)
+// (the second part relative to the window's SA range with several windows),
+// value = i, with sh = bits of the longest window (the second part is at
+// most its length).
 // Also counts the digits of the sort's first place (key bits [shift,
 // shift + dbits)) into hist, which saves the sort its own pass over the keys.
 __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ A_dev,
@@ -276,7 +278,10 @@ __global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint3
     if (k < A) {
       const uint32_t i = act[k];
       const uint64_t j = i + h;
-      const uint32_t r2 = j < win_end(W, i, n) ? rank[j] + 1u : 0u;
+      // the second rank is only compared within a group, i.e. within one
+      // window, so it is taken relative to the window's SA range
+      uint32_t r2 = 0;
+      if (j < win_end(W, i, n)) r2 = rank[j] + 1u - (W.count > 1 ? W.off_dev[W.wid[i]] : 0u);
       const uint64_t key = ((uint64_t)rank[i] << sh) | r2;
       keys[k] = key;
       vals[k] = i;
@@ -594,7 +599,8 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   st.levels = 1;
   int cur = 0;
   uint32_t rounds = 0;
-  const int minor_bits = bits_for(n), major_bits = bits_for(n - 1);
+  // second rank + 1 <= the longest window; first rank < n
+  const int minor_bits = bits_for(st.win.count > 1 ? st.win.max_len : n), major_bits = bits_for(n - 1);
   // Round r reads its active count from a device word and writes the next
   // one; the host queues round r+1 before it has read round r's count (an
   // upper bound sizes the launches), and stops one round after the count
