@@ -61,6 +61,8 @@ def lib():
         L.ora_find_repeats.argtypes = [P, U64, P, P, ctypes.c_uint32, ctypes.c_int] + [P] * 10
         L.ora_match.restype = U64
         L.ora_match.argtypes = [P, P, U64, P, U64, ctypes.c_int, P, P, U64]
+        L.ora_replay.restype = U64
+        L.ora_replay.argtypes = [P, U64, U64, P, P, P] + [U64] * 5 + [P, P, P, U64, P]
         _lib = L
     return _lib
 
@@ -217,3 +219,34 @@ def online_traces(S, unit: int, buffer: int, min_len: int):
         out.append((i, start, length, r.trace_len.astype(np.uint32),
                     r.trace_start.astype(np.uint64) + np.uint64(start)))
     return out
+
+
+@dataclass
+class Replay:
+    end: np.ndarray      # task index where each replayed trace ends
+    length: np.ndarray   # its length
+    trace: np.ndarray    # smallest piece number with its string
+    traced: np.ndarray   # u8 per task: 1 = inside a replay
+
+
+def replay(S, tr_start, tr_len, tr_ingest, max_len: int = 0, cap: int = 0, half_life: int = 0,
+           bonus=(1, 1)) -> Replay:
+    """Alg. 1's TraceReplayer (Sec. 4.3), task by task: candidate trace q is
+    S[tr_start[q] : tr_start[q] + tr_len[q]] and enters the trie at task
+    tr_ingest[q]; see ora_replay for the steps and the score."""
+    S = _tok(S)
+    n = S.shape[0]
+    st = np.ascontiguousarray(tr_start, dtype=np.uint64)
+    ln = np.ascontiguousarray(tr_len, dtype=np.uint64)
+    ig = np.ascontiguousarray(tr_ingest, dtype=np.uint64)
+    P = st.shape[0]
+    assert ln.shape[0] == P and ig.shape[0] == P
+    assert all(int(l) >= 1 and int(a) + int(l) <= n for a, l in zip(st, ln))
+    cap_r = n + 1
+    e = np.zeros(cap_r, np.uint32)
+    l = np.zeros(cap_r, np.uint32)
+    t = np.zeros(cap_r, np.uint32)
+    traced = np.zeros(max(1, n), np.uint8)
+    r = lib().ora_replay(_p(S), n, P, _p(st), _p(ln), _p(ig), max_len, cap, half_life, bonus[0], bonus[1],
+                         _p(e), _p(l), _p(t), cap_r, _p(traced))
+    return Replay(e[:r], l[:r], t[:r], traced[:n])

@@ -22,6 +22,10 @@
 //   ora_match                      every occurrence of every candidate trace in
 //                                  a stream (Sec. 4.3: a pointer that reaches the
 //                                  end of a trace in the trie is a match).
+//   ora_replay                     Alg. 1 "TraceReplayer" (Sec. 4.3) task by
+//                                  task: a growing trie, pointers advanced per
+//                                  task, completed candidates scored, the best
+//                                  one replayed.
 //
 // Parity notes (readings where the paper is silent):
 //   * a suffix that is a proper prefix of another sorts first;
@@ -383,6 +387,134 @@ uint64_t ora_match(const uint64_t *pat_tok, const uint64_t *pat_off, uint64_t P,
     id_out[k] = (uint32_t)hits[k].p;
   }
   return hits.size();
+}
+
+// Alg. 1 "TraceReplayer" with Sec. 4.3's trie, pointers and scoring, one
+// task at a time.  Candidate trace q is the slice S[tr_start[q] ..
+// tr_start[q] + tr_len[q]) and enters the trie when task tr_ingest[q] is
+// processed (IngestCandidates runs first in TraceReplayer).  A trace longer
+// than max_len (0 = no limit) enters as consecutive pieces of max_len tokens,
+// the last one shorter (the maximum trace length of Sec. 6.2); pieces are
+// numbered in input order, and a replay reports the smallest piece number
+// with its string.  For task k (token S[k]):
+//   AdvanceActiveCandidates / FilterInvalidCandidates: every pointer moves
+//     along the edge S[k] if the trie has it and is dropped otherwise; a new
+//     pointer starts at the root and moves along S[k] the same way;
+//   FilterCompletedCandidates: D = the pointers standing at the end of a
+//     trace; every trace in D counts one more appearance;
+//   SelectReplayTrace: if D is not empty, the trace with the highest score
+//     (the longer one on a tie) is replayed -- it ends at k -- and
+//   ExecuteAndReplay: the tasks before it run untraced, its tasks are the
+//     replay, and every pointer is dropped (each one has consumed task k,
+//     which the replay took).
+// score = (len * min(count, cap) * (replayed before ? bonus_num : bonus_den))
+//         >> ((k - previous appearance) / half_life)
+// with count including this appearance; no shift at a trace's first
+// appearance or with half_life = 0, a shift of 64 or more gives 0, cap = 0
+// means no cap.  Writes up to rcap replays (end task, length, trace number)
+// and traced[k] = 1 for the tasks inside replays; returns the replay count.
+uint64_t ora_replay(const uint64_t *S, uint64_t n, uint64_t P, const uint64_t *tr_start,
+                    const uint64_t *tr_len, const uint64_t *tr_ingest, uint64_t max_len, uint64_t cap,
+                    uint64_t half_life, uint64_t bonus_num, uint64_t bonus_den, uint32_t *rep_end,
+                    uint32_t *rep_len, uint32_t *rep_trace, uint64_t rcap, uint8_t *traced) {
+  struct Piece {
+    uint64_t start, len, ingest, id;
+  };
+  std::vector<Piece> pieces;
+  for (uint64_t q = 0; q < P; ++q) {
+    uint64_t off = 0;
+    do {
+      uint64_t l = tr_len[q] - off;
+      if (max_len && l > max_len) l = max_len;
+      pieces.push_back({tr_start[q] + off, l, tr_ingest[q], (uint64_t)pieces.size()});
+      off += l;
+    } while (off < tr_len[q]);
+  }
+  // smallest piece number per string
+  std::map<std::vector<uint64_t>, uint64_t> first_id;
+  for (const Piece &pc : pieces) {
+    std::vector<uint64_t> str(S + pc.start, S + pc.start + pc.len);
+    auto it = first_id.find(str);
+    if (it == first_id.end()) first_id.emplace(std::move(str), pc.id);
+  }
+  struct Node {
+    std::map<uint64_t, uint32_t> child;
+    int64_t trace = -1;  // trace number if a trace ends here
+    uint64_t len = 0, count = 0;
+    int64_t last = -1;
+    bool replayed = false;
+  };
+  std::vector<Node> trie(1);
+  auto ingest = [&](const Piece &pc) {
+    uint32_t v = 0;
+    for (uint64_t j = 0; j < pc.len; ++j) {
+      const uint64_t c = S[pc.start + j];
+      auto it = trie[v].child.find(c);
+      if (it == trie[v].child.end()) {
+        trie.emplace_back();
+        const uint32_t w = (uint32_t)(trie.size() - 1);
+        trie[v].child.emplace(c, w);
+        v = w;
+      } else {
+        v = it->second;
+      }
+    }
+    if (trie[v].trace < 0) {
+      std::vector<uint64_t> str(S + pc.start, S + pc.start + pc.len);
+      trie[v].trace = (int64_t)first_id[str];
+      trie[v].len = pc.len;
+    }
+  };
+  std::vector<uint64_t> order(pieces.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint64_t a, uint64_t b) { return pieces[a].ingest < pieces[b].ingest; });
+  uint64_t next_piece = 0, nrep = 0;
+  std::vector<uint32_t> A, A2;  // pointers: trie nodes (a node's depth fixes its start)
+  for (uint64_t k = 0; k < n; ++k) {
+    traced[k] = 0;
+    while (next_piece < order.size() && pieces[order[next_piece]].ingest <= k) ingest(pieces[order[next_piece++]]);
+    A2.clear();
+    for (uint32_t v : A) {
+      auto it = trie[v].child.find(S[k]);
+      if (it != trie[v].child.end()) A2.push_back(it->second);
+    }
+    {
+      auto it = trie[0].child.find(S[k]);
+      if (it != trie[0].child.end()) A2.push_back(it->second);
+    }
+    A.swap(A2);
+    int64_t best = -1;
+    uint64_t best_score = 0;
+    for (uint32_t v : A) {
+      Node &t = trie[v];
+      if (t.trace < 0) continue;
+      uint64_t shift = 0;
+      if (t.last >= 0 && half_life) shift = (k - (uint64_t)t.last) / half_life;
+      t.count += 1;
+      t.last = (int64_t)k;
+      const uint64_t c = cap ? std::min(t.count, cap) : t.count;
+      const uint64_t x = t.len * c * (t.replayed ? bonus_num : bonus_den);
+      const uint64_t score = shift >= 64 ? 0 : (x >> shift);
+      if (best < 0 || score > best_score || (score == best_score && t.len > trie[best].len)) {
+        best = v;
+        best_score = score;
+      }
+    }
+    if (best >= 0) {
+      Node &t = trie[best];
+      t.replayed = true;
+      if (nrep < rcap) {
+        rep_end[nrep] = (uint32_t)k;
+        rep_len[nrep] = (uint32_t)t.len;
+        rep_trace[nrep] = (uint32_t)t.trace;
+      }
+      ++nrep;
+      for (uint64_t j = k + 1 - t.len; j <= k; ++j) traced[j] = 1;
+      A.clear();
+    }
+  }
+  return nrep;
 }
 
 }  // extern "C"

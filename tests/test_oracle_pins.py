@@ -308,3 +308,189 @@ def test_online_traces_slices():
     for i, start, length, tl, ts in res:
         # every trace lies inside its slice
         assert np.all(ts >= start) and np.all(ts + tl <= start + length)
+
+
+# ---------------------------------------------------------------- TraceReplayer
+# Sec. 4.3: traces enter a trie, pointers follow the stream through it, a
+# pointer at the end of a trace completes it, the completed trace with the
+# best score (length x capped appearance count, decayed by the tasks since
+# its previous appearance, raised for a trace already replayed) is replayed.
+# Expected values below are worked by hand from that description.
+_TOK = {ch: i + 1 for i, ch in enumerate("abcdexy")}
+
+
+def _s(text):
+    return np.array([_TOK[ch] for ch in text], dtype=np.uint64)
+
+
+def _rep(r):
+    return list(zip(r.end.tolist(), r.length.tolist(), r.trace.tolist()))
+
+
+def test_replay_periodic_single_trace():
+    r = oracle.replay(_s("abc" * 5), [0], [3], [0])
+    assert _rep(r) == [(2, 3, 0), (5, 3, 0), (8, 3, 0), (11, 3, 0), (14, 3, 0)]
+    assert r.traced.tolist() == [1] * 15
+
+
+def test_replay_waits_for_ingestion():
+    # the trace enters at task 4: no pointer can follow it before, and the
+    # pointers started at tasks 4 and 5 meet no edge of the trie
+    r = oracle.replay(_s("abc" * 5), [0], [3], [4])
+    assert _rep(r) == [(8, 3, 0), (11, 3, 0), (14, 3, 0)]
+    assert r.traced.tolist() == [0] * 6 + [1] * 9
+
+
+def test_replay_prefix_trace_completes_first():
+    # "ab" ends one task before "abc": it is replayed and takes the pointer
+    # that was on its way to "abc"
+    r = oracle.replay(_s("abcabc"), [0, 0], [2, 3], [0, 0])
+    assert _rep(r) == [(1, 2, 0), (4, 2, 0)]
+    assert r.traced.tolist() == [1, 1, 0, 1, 1, 0]
+
+
+def test_replay_longer_of_two_completed_traces():
+    # "bc" (piece 0) and "abc" (piece 1) complete together: 3 x 1 > 2 x 1
+    r = oracle.replay(_s("abcabc"), [1, 0], [2, 3], [0, 0])
+    assert _rep(r) == [(2, 3, 1), (5, 3, 1)]
+
+
+def test_replay_growing_trie():
+    # "abd" is in the trie from the start, "abc" enters at task 2; the
+    # pointer started at task 0 stands at "ab" then and continues into "abc"
+    r = oracle.replay(_s("abcxabd"), [4, 0], [3, 3], [0, 2])
+    assert _rep(r) == [(2, 3, 1), (6, 3, 0)]
+    # with "axd" instead, that pointer died at task 1 ("a" has no edge b)
+    r = oracle.replay(_s("abcxaxd"), [4, 0], [3, 3], [0, 2])
+    assert _rep(r) == [(6, 3, 0)]
+
+
+_BC_ABC = _s("xbc" * 4 + "abc" * 3)
+
+
+def test_replay_appearance_count_and_cap():
+    # "bc" appears alone four times, then with "abc" at tasks 14, 17, 20
+    # no cap: bc scores 2 x 5, 2 x 6, 2 x 7 against abc's 3, 6, 9
+    r = oracle.replay(_BC_ABC, [1, 12], [2, 3], [0, 0])
+    assert r.length.tolist() == [2] * 7
+    assert r.end.tolist() == [2, 5, 8, 11, 14, 17, 20]
+    # cap 2: bc scores 2 x 2 = 4 against abc's 3 x 1, then 3 x 2 = 6 twice
+    r = oracle.replay(_BC_ABC, [1, 12], [2, 3], [0, 0], cap=2)
+    assert r.length.tolist() == [2, 2, 2, 2, 2, 3, 3]
+    assert r.traced.tolist() == [0, 1, 1] * 4 + [0, 1, 1] + [1] * 6
+
+
+def test_replay_decay():
+    # half-life 1 task: the score is shifted right by the tasks since the
+    # previous appearance.  Task 14: abc 3 (first appearance) > bc 10 >> 3;
+    # task 17: abc 6 >> 3 = 0 < bc 12 >> 3 = 1; task 20: 9 >> 3 = 14 >> 3,
+    # the tie goes to the longer abc
+    r = oracle.replay(_BC_ABC, [1, 12], [2, 3], [0, 0], half_life=1)
+    assert r.length.tolist() == [2, 2, 2, 2, 3, 2, 3]
+    assert r.end.tolist() == [2, 5, 8, 11, 14, 17, 20]
+    # a half-life of 4 tasks shifts by 3 // 4 = 0: as without decay
+    r = oracle.replay(_BC_ABC, [1, 12], [2, 3], [0, 0], half_life=4)
+    assert r.length.tolist() == [2] * 7
+
+
+def test_replay_bonus_for_replayed_trace():
+    # "cd" replayed at tasks 3 and 7; at task 11 abcd (4 x 1) meets cd
+    # (2 x min(3, 2) = 4): a tie the longer trace wins, unless the bonus
+    # (2 against 1) lifts the already replayed cd to 8.  Task 15: abcd
+    # 4 x 2 = 8 against cd 4 (x 2 with the bonus): a tie again
+    S = _s("xycd" * 2 + "abcd" * 2)
+    r = oracle.replay(S, [2, 8], [2, 4], [0, 0], cap=2)
+    assert r.length.tolist() == [2, 2, 4, 4]
+    r = oracle.replay(S, [2, 8], [2, 4], [0, 0], cap=2, bonus=(2, 1))
+    assert r.length.tolist() == [2, 2, 2, 4]
+    assert r.end.tolist() == [3, 7, 11, 15]
+
+
+def test_replay_maximum_trace_length():
+    # a 5-task trace with a maximum length of 2 enters as ab, cd, e
+    r = oracle.replay(_s("abcde" * 2), [0], [5], [0], max_len=2)
+    assert _rep(r) == [(1, 2, 0), (3, 2, 1), (4, 1, 2), (6, 2, 0), (8, 2, 1), (9, 1, 2)]
+    # equal strings report the smallest piece number
+    r = oracle.replay(_s("abcabc"), [3, 0], [3, 3], [0, 0])
+    assert _rep(r) == [(2, 3, 0), (5, 3, 0)]
+
+
+def _replay_by_occurrences(S, starts, lens, ingest, max_len, cap, half_life, bonus):
+    """The same replay decisions formulated over occurrences instead of
+    pointers: an occurrence [s, e] of trace t is followed by a pointer iff
+    s >= need(t) = max over j < |t| of (B(t[:j]) - j + 1) and E(t) - |t| + 1,
+    with B(u) the earliest ingestion of a piece starting with u and E(t) the
+    earliest of t itself (the pointer stands at t[:j] while task s + j - 1 is
+    processed, and completes t at task s + |t| - 1); replays end where the
+    first such occurrence starting after the previous replay ends."""
+    S = [int(x) for x in S]
+    n = len(S)
+    pieces = []
+    for a, l, g in zip(starts, lens, ingest):
+        off = 0
+        while off < l:
+            m = l - off if not max_len else min(max_len, l - off)
+            pieces.append((tuple(S[a + off:a + off + m]), int(g)))
+            off += m
+    first = {}
+    for pid, (u, _) in enumerate(pieces):
+        first.setdefault(u, pid)
+
+    def birth(u):
+        return min(g for v, g in pieces if v[:len(u)] == u)
+
+    def own(u):  # the trace itself ends a pointer only once it is in the trie
+        return min(g for v, g in pieces if v == u)
+
+    need = {u: max([birth(u[:j]) - j + 1 for j in range(1, len(u))] + [own(u) - len(u) + 1]) for u in first}
+    occ = {}  # end -> [(start, string)]
+    for u in first:
+        L = len(u)
+        for s in range(0, n - L + 1):
+            if tuple(S[s:s + L]) == u and s >= need[u]:
+                occ.setdefault(s + L - 1, []).append((s, u))
+    state = {u: [0, -1, False] for u in first}  # count, last, replayed
+    out, traced, c = [], [0] * n, 0
+    for e in range(n):
+        D = [(s, u) for s, u in occ.get(e, []) if s >= c]
+        if not D:
+            continue
+        best = None
+        for s, u in D:
+            cnt, last, rep = state[u]
+            sh = (e - last) // half_life if (last >= 0 and half_life) else 0
+            cnt += 1
+            state[u][0], state[u][1] = cnt, e
+            x = len(u) * (min(cnt, cap) if cap else cnt) * (bonus[0] if rep else bonus[1])
+            sc = 0 if sh >= 64 else x >> sh
+            if best is None or (sc, len(u)) > best[0]:
+                best = ((sc, len(u)), u)
+        u = best[1]
+        state[u][2] = True
+        out.append((e, len(u), first[u]))
+        for j in range(e - len(u) + 1, e + 1):
+            traced[j] = 1
+        c = e + 1
+    return out, traced
+
+
+def test_replay_agrees_with_occurrence_formulation():
+    rng = np.random.default_rng(7)
+    for case in range(400):
+        n = int(rng.integers(1, 80))
+        per = int(rng.integers(1, 7))
+        S = rng.integers(0, 3, size=per)[np.arange(n) % per]
+        flip = rng.random(n) < 0.1
+        S = np.where(flip, rng.integers(0, 3, size=n), S).astype(np.uint64)
+        P = int(rng.integers(0, 6))
+        lens = rng.integers(1, min(n, 8) + 1, size=P)
+        starts = np.array([rng.integers(0, n - l + 1) for l in lens], dtype=np.int64)
+        ingest = rng.integers(0, n + 3, size=P)
+        max_len = int(rng.choice([0, 0, 2, 3]))
+        cap = int(rng.choice([0, 1, 2, 4]))
+        half_life = int(rng.choice([0, 1, 3]))
+        bonus = [(1, 1), (2, 1), (17, 16), (1, 2)][int(rng.integers(0, 4))]
+        r = oracle.replay(S, starts, lens, ingest, max_len, cap, half_life, bonus)
+        exp, traced = _replay_by_occurrences(S, starts, lens, ingest, max_len, cap, half_life, bonus)
+        assert _rep(r) == exp, case
+        assert r.traced.tolist() == traced, case
