@@ -338,6 +338,72 @@ int apo_match_candidates(apo_ctx *ctx, const apo_patterns *patterns, const void 
                          uint64_t *count, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Trace replay -- Alg. 1 "TraceReplayer", Sec. 4.3, for a whole stream.
+ *
+ * The replayer the paper runs per task: candidate traces are ingested into
+ * a trie; each task advances every live pointer along its token (dropping
+ * those the trie does not continue) and starts a new one at the root; a
+ * pointer standing at the end of a trace completes it, which counts one
+ * appearance of that trace; when traces complete, the one with the highest
+ * score is replayed -- it ends at the current task, the tasks before it run
+ * untraced -- and every pointer is dropped (each has consumed the replayed
+ * task).  Score of a completed trace t at task k:
+ *     (len(t) * min(count(t), count_cap) * (t replayed before ? bonus_num : bonus_den))
+ *         >> ((k - previous appearance of t) / half_life)
+ * in unsigned 64-bit arithmetic (wrapping), count(t) including this
+ * appearance; no shift at a first appearance or with half_life = 0; a shift
+ * of 64 or more gives 0; count_cap = 0 means no cap; a tie goes to the longer
+ * trace.  (The paper names these ingredients -- length times a capped count,
+ * exponential decay with the tasks since the trace last appeared, a small
+ * raise for a trace already replayed -- without constants; the halving per
+ * half_life tasks and the integer form are this library's.)
+ *
+ * Trace q is the slice stream[start[q] .. start[q] + len[q]) and enters the
+ * trie when task ingest[q] is processed (before that task's token; at
+ * ingest >= n never).  A trace longer than max_trace_len (0 = no limit)
+ * enters as consecutive pieces of max_trace_len tokens, the last one shorter
+ * (the maximum trace length of Sec. 6.2).  Pieces are numbered in trace
+ * order; a replay reports the smallest piece number with its string.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t n_traces;       /* P (0 allowed: nothing is replayed) */
+  const uint32_t *start;   /* [P] device */
+  const uint32_t *len;     /* [P] device, >= 1, start + len <= n */
+  const uint32_t *ingest;  /* [P] device: task index at which the trace enters the trie */
+} apo_replay_traces;
+
+typedef struct {
+  uint32_t max_trace_len;  /* 0 = no limit */
+  uint32_t count_cap;      /* 0 = no cap */
+  uint32_t half_life;      /* tasks per halving of the score; 0 = no decay */
+  uint32_t bonus_num;      /* factor for a trace replayed before, 1 .. 65535 */
+  uint32_t bonus_den;      /* factor otherwise, 1 .. 65535 */
+  uint32_t window;         /* curve window in tasks (0 = every task so far) */
+} apo_replay_params;
+
+typedef struct {
+  uint32_t *rep_end;       /* [rep_cap] device: task where each replay ends, ascending */
+  uint32_t *rep_len;       /* [rep_cap] its length */
+  uint32_t *rep_trace;     /* [rep_cap] the smallest piece number of its string */
+  uint64_t rep_cap;
+  uint8_t *traced;         /* [n] device or NULL: 1 for a task inside a replay */
+  uint32_t *curve;         /* [n] device or NULL: traced tasks among the `window`
+                              tasks ending at each task (the paper's Fig. 10 view) */
+  /* HOST array of 8 counts, written before the call returns: [0] replays,
+   * [1] traced tasks, [2] pieces, [3] occurrences of the pieces, [4]
+   * appearances, [5] replay tasks not decided by the lower/upper score
+   * bound, [6] rounds of the fixed-point selection, [7] jump levels. */
+  uint64_t *counts;
+} apo_replay_out;
+
+/* Replay decisions for stream[n] (device tokens of token_bytes 4 or 8).
+ * Synchronises `stream`.  APO_EINVAL for a bad argument or trace;
+ * APO_ECAPACITY if the replays exceed rep_cap (counts are still written). */
+int apo_replay(apo_ctx *ctx, const void *stream_tokens, uint64_t n, int token_bytes,
+               const apo_replay_traces *traces, const apo_replay_params *params, apo_replay_out *out,
+               void *stream);
+
+/* ------------------------------------------------------------------------
  * Greedy selection without allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
  * running inside a task runtime that owns all device memory through its own

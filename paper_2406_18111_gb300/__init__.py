@@ -34,7 +34,8 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_profile_read", "apo_greedy_select_noalloc", "apo_server_create", "apo_server_submit",
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
            "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read", "apo_finder_create",
-           "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy")
+           "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy",
+           "apo_replay")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -96,6 +97,20 @@ class apo_patterns(ctypes.Structure):
 _lib = None
 
 
+class apo_replay_traces(ctypes.Structure):
+    _fields_ = [("n_traces", _U64), ("start", _P), ("len", _P), ("ingest", _P)]
+
+
+class apo_replay_params(ctypes.Structure):
+    _fields_ = [("max_trace_len", _U32), ("count_cap", _U32), ("half_life", _U32), ("bonus_num", _U32),
+                ("bonus_den", _U32), ("window", _U32)]
+
+
+class apo_replay_out(ctypes.Structure):
+    _fields_ = [("rep_end", _P), ("rep_len", _P), ("rep_trace", _P), ("rep_cap", _U64), ("traced", _P),
+                ("curve", _P), ("counts", _P)]
+
+
 def lib():
     """Load libapo.so (raises if it has not been built)."""
     global _lib
@@ -131,6 +146,8 @@ def lib():
         L.apo_server_release.argtypes = [_P, _U64]
         L.apo_server_now.argtypes = [_P]
         L.apo_server_destroy.argtypes = [_P]
+        L.apo_replay.argtypes = [_P, _P, _U64, ctypes.c_int, ctypes.POINTER(apo_replay_traces),
+                                 ctypes.POINTER(apo_replay_params), ctypes.POINTER(apo_replay_out), _P]
         for f in EXPORTS:
             if f not in ("apo_last_error", "apo_server_now"):
                 getattr(L, f).restype = ctypes.c_int
@@ -338,6 +355,33 @@ class Apo:
         _check(code)
         c = int(cnt.value)
         return end[:c], pid[:c]
+
+    def replay(self, stream_tokens, start, length, ingest, max_trace_len: int = 0, count_cap: int = 0,
+               half_life: int = 0, bonus=(1, 1), window: int = 0, traced: bool = True, curve: bool = False,
+               rep_cap: int | None = None, stream=None):
+        """Alg. 1's TraceReplayer over stream_tokens (device): trace q is
+        stream_tokens[start[q] : start[q] + length[q]] and enters the trie at
+        task ingest[q] (all device u32 tensors).  Returns (end, len, trace)
+        of the replays, the traced flags (u8 per task) or None, the curve
+        (traced tasks among the last `window`) or None, and the counts."""
+        import torch
+        n = int(stream_tokens.shape[0])
+        dev = stream_tokens.device
+        cap = max(1, n if rep_cap is None else rep_cap)
+        end = torch.empty(cap, dtype=torch.int32, device=dev)
+        ln = torch.empty(cap, dtype=torch.int32, device=dev)
+        tr = torch.empty(cap, dtype=torch.int32, device=dev)
+        tf = torch.empty(max(1, n), dtype=torch.uint8, device=dev) if traced else None
+        cv = torch.empty(max(1, n), dtype=torch.int32, device=dev) if curve else None
+        counts = np.zeros(8, dtype=np.uint64)
+        t = apo_replay_traces(int(start.shape[0]), _ptr(start), _ptr(length), _ptr(ingest))
+        p = apo_replay_params(max_trace_len, count_cap, half_life, bonus[0], bonus[1], window)
+        o = apo_replay_out(_ptr(end), _ptr(ln), _ptr(tr), cap, _ptr(tf), _ptr(cv), counts.ctypes.data_as(_P).value)
+        _check(lib().apo_replay(self._h, _ptr(stream_tokens), n, _token_bytes(stream_tokens), ctypes.byref(t),
+                                ctypes.byref(p), ctypes.byref(o), _stream_handle(stream)))
+        r = int(counts[0])
+        return (end[:r], ln[:r], tr[:r], None if tf is None else tf[:n], None if cv is None else cv[:n],
+                [int(x) for x in counts])
 
     # -------------------------------------------------------------- sort tuning
     def sort_tuning(self, mode: int):

@@ -86,7 +86,8 @@ enum KernelId : int {
   kKPlcp, kKLcpPerm, kKMin32, kKMax, kKCandGen, kKCompact, kKCandGather, kKGreedy, kKTraces,
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
-  kKAcNodes, kKAcJump, kKRsTune, kKCount
+  kKAcNodes, kKAcJump, kKRsTune, kKRpPieces, kKRpNeed, kKRpChain, kKRpAppear, kKRpSelect, kKRpOut,
+  kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
@@ -111,6 +112,10 @@ struct Profiler {
   int resolve();
   void release();
 };
+
+// ---------------------------------------------------------------- trace replay
+int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
+                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
 
 }  // namespace apo
 
@@ -143,6 +148,10 @@ struct SortTuner {
   static int size_class(uint32_t n);
 };
 
+// ---------------------------------------------------------------- trace replay
+int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
+                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+
 }  // namespace apo
 
 struct apo_ctx {
@@ -156,6 +165,9 @@ struct apo_ctx {
   void *side = nullptr;             // grow-only buffer for sizes known only mid-call
   size_t side_bytes = 0;
   cudaEvent_t round_ev[2] = {nullptr, nullptr};  // doubling-round count read-backs
+  void *rp[3] = {nullptr, nullptr, nullptr};     // trace replay buffers (grow-only)
+  size_t rp_bytes[3] = {0, 0, 0};
+  uint64_t rp_cap = 0;                            // occurrences the replay buffers hold
 };
 
 namespace apo {
@@ -175,6 +187,10 @@ class Launch {
   cudaStream_t s_;
   cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+
+// ---------------------------------------------------------------- trace replay
+int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
+                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
 
 }  // namespace apo
 
@@ -294,8 +310,16 @@ void launch_hash_tasks(apo_ctx *c, const apo_tasks *t, uint64_t *out, cudaStream
 int server_token_bytes(apo_server *s);
 
 // ---------------------------------------------------------------- matching
+// With aux_order / aux_slcp (device, P entries each) it also returns the
+// patterns in string order (aux_order[j] = pattern id; equal strings by
+// increasing id) and aux_slcp[j] = lcp of the patterns at j - 1 and j
+// (aux_slcp[0] = 0).
 int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
                    uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
-                   cudaStream_t s);
+                   cudaStream_t s, uint32_t *aux_order = nullptr, uint32_t *aux_slcp = nullptr);
+
+// ---------------------------------------------------------------- trace replay
+int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
+                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
 
 }  // namespace apo

@@ -79,7 +79,8 @@ const char *const kKernelNames[kKCount] = {
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
-    "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune"};
+    "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
+    "rp_appear", "rp_select", "rp_out"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -220,6 +221,8 @@ int apo_destroy(apo_ctx *c) {
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->tuner.scratch) cudaFree(c->tuner.scratch);
   if (c->side) cudaFree(c->side);
+  for (void *p : c->rp)
+    if (p) cudaFree(p);
   for (auto e : c->round_ev)
     if (e) cudaEventDestroy(e);
   c->prof.release();
@@ -441,6 +444,33 @@ int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_t
   APO_CUDA_TRY(cudaSetDevice(c->device));
   return match_patterns(c, p, stream_tokens, n, match_end, match_id, cap, count,
                         static_cast<cudaStream_t>(stream));
+}
+
+int apo_replay(apo_ctx *c, const void *stream_tokens, uint64_t n, int token_bytes,
+               const apo_replay_traces *tr, const apo_replay_params *prm, apo_replay_out *out, void *stream) {
+  if (!c || !tr || !prm || !out || !out->counts) {
+    set_error("apo_replay: null context, traces, params or outputs");
+    return APO_EINVAL;
+  }
+  if (token_bytes != 4 && token_bytes != 8) {
+    set_error("apo_replay: token_bytes must be 4 or 8");
+    return APO_EINVAL;
+  }
+  if (n >= 0x7fffffffull || tr->n_traces >= 0x7fffffffull) {
+    set_error("apo_replay: at most 2^31 - 2 tasks and 2^31 - 2 traces");
+    return APO_EINVAL;
+  }
+  if (prm->bonus_num < 1 || prm->bonus_num > 65535 || prm->bonus_den < 1 || prm->bonus_den > 65535) {
+    set_error("apo_replay: bonus_num and bonus_den must lie in 1 .. 65535");
+    return APO_EINVAL;
+  }
+  if ((n > 0 && !stream_tokens) || (tr->n_traces > 0 && (!tr->start || !tr->len || !tr->ingest)) ||
+      (out->rep_cap > 0 && (!out->rep_end || !out->rep_len || !out->rep_trace))) {
+    set_error("apo_replay: null stream, trace arrays or replay outputs");
+    return APO_EINVAL;
+  }
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  return replay_stream(c, stream_tokens, n, token_bytes, tr, prm, out, static_cast<cudaStream_t>(stream));
 }
 
 int apo_profile_enable(apo_ctx *c, int enable) {

@@ -491,3 +491,138 @@ def test_finder_ruler_sampling_equals_oracle(apo, unit, buffer, tb):
     assert st["analysed_tokens"] == sum(w[2] for w in want)
     f.close()
     srv.close()
+
+
+# ---------------------------------------------------------------- trace replay
+def _replay_both(apo, S, starts, lens, ingest, tb=4, max_len=0, cap=0, half_life=0, bonus=(1, 1), window=0):
+    S = np.asarray(S)
+    starts = np.asarray(starts, dtype=np.uint32)
+    lens = np.asarray(lens, dtype=np.uint32)
+    ingest = np.asarray(ingest, dtype=np.uint32)
+    o = oracle.replay(S.astype(np.uint64), starts, lens, ingest, max_len, cap, half_life, bonus)
+    end, ln, tr, traced, curve, counts = apo.replay(
+        tokens_dev(S, tb), dev(starts, np.int32), dev(lens, np.int32), dev(ingest, np.int32),
+        max_trace_len=max_len, count_cap=cap, half_life=half_life, bonus=bonus, window=window, curve=True)
+    got = (end.cpu().numpy().view(np.uint32), ln.cpu().numpy().view(np.uint32), tr.cpu().numpy().view(np.uint32))
+    assert np.array_equal(got[0], o.end), "replay ends"
+    assert np.array_equal(got[1], o.length), "replay lengths"
+    assert np.array_equal(got[2], o.trace), "replay traces"
+    n = S.shape[0]
+    assert np.array_equal(traced.cpu().numpy(), o.traced)
+    pre = np.concatenate([[0], np.cumsum(o.traced.astype(np.int64))])
+    w = window if window else n
+    want_curve = pre[1:] - pre[np.maximum(0, np.arange(1, n + 1) - w)]
+    assert np.array_equal(curve.cpu().numpy().astype(np.int64), want_curve)
+    assert counts[0] == len(o.end) and counts[1] == int(o.traced.sum())
+    return o, counts
+
+
+_TOKS = {ch: i + 1 for i, ch in enumerate("abcdexy")}
+
+
+def _txt(t):
+    return np.array([_TOKS[ch] for ch in t], dtype=np.uint32)
+
+
+def test_replay_hand_cases(apo):
+    # the oracle's hand-worked cases (tests/test_oracle_pins.py), GPU = oracle
+    bc_abc = _txt("xbc" * 4 + "abc" * 3)
+    cases = [
+        (_txt("abc" * 5), [0], [3], [0], {}),
+        (_txt("abc" * 5), [0], [3], [4], {}),
+        (_txt("abcabc"), [0, 0], [2, 3], [0, 0], {}),
+        (_txt("abcabc"), [1, 0], [2, 3], [0, 0], {}),
+        (_txt("abcxabd"), [4, 0], [3, 3], [0, 2], {}),
+        (_txt("abcxaxd"), [4, 0], [3, 3], [0, 2], {}),
+        (bc_abc, [1, 12], [2, 3], [0, 0], {}),
+        (bc_abc, [1, 12], [2, 3], [0, 0], {"cap": 2}),
+        (bc_abc, [1, 12], [2, 3], [0, 0], {"half_life": 1}),
+        (_txt("xycd" * 2 + "abcd" * 2), [2, 8], [2, 4], [0, 0], {"cap": 2, "bonus": (2, 1)}),
+        (_txt("abcde" * 2), [0], [5], [0], {"max_len": 2}),
+        (_txt("abcabc"), [3, 0], [3, 3], [0, 0], {}),
+    ]
+    for S, st, ln, ig, kw in cases:
+        for tb in (4, 8):
+            _replay_both(apo, S, st, ln, ig, tb=tb, **kw)
+
+
+def test_replay_random_small(apo):
+    rng = np.random.default_rng(11)
+    for case in range(250):
+        n = int(rng.integers(1, 80))
+        per = int(rng.integers(1, 7))
+        S = rng.integers(0, 3, size=per)[np.arange(n) % per]
+        S = np.where(rng.random(n) < 0.1, rng.integers(0, 3, size=n), S).astype(np.uint32)
+        P = int(rng.integers(0, 7))
+        lens = rng.integers(1, min(n, 8) + 1, size=P)
+        starts = np.array([rng.integers(0, n - l + 1) for l in lens], dtype=np.int64)
+        ingest = rng.integers(0, n + 3, size=P)
+        _replay_both(apo, S, starts, lens, ingest, max_len=int(rng.choice([0, 0, 2, 3])),
+                     cap=int(rng.choice([0, 1, 2, 4])), half_life=int(rng.choice([0, 1, 3])),
+                     bonus=[(1, 1), (2, 1), (17, 16), (1, 2)][int(rng.integers(0, 4))],
+                     window=int(rng.choice([0, 1, 7])))
+
+
+def _online_inputs(S, unit=250, buffer=5000, min_len=5):
+    st, ln, ig = [], [], []
+    for i, _, _, tl, ts in oracle.online_traces(S, unit, buffer, min_len):
+        st += ts.tolist()
+        ln += tl.tolist()
+        ig += [(i + 1) * unit] * len(tl)  # ingested one analysis period after its point
+    return np.array(st, np.uint32), np.array(ln, np.uint32), np.array(ig, np.uint32)
+
+
+@pytest.mark.parametrize("n,kw", [
+    (1 << 16, {}),
+    (1 << 16, {"max_len": 16, "cap": 8, "half_life": 1000, "bonus": (17, 16), "window": 5000}),
+    ((1 << 17) + 321, {"cap": 2, "half_life": 50, "bonus": (2, 1), "window": 1000}),
+])
+def test_replay_online_finder_traces(apo, n, kw):
+    S = W.replay_stream(n, seed=6)
+    st, ln, ig = _online_inputs(S)
+    _, counts = _replay_both(apo, S, st, ln, ig, **kw)
+    assert counts[0] > 100  # the stream does replay
+
+
+@pytest.mark.parametrize("tb", [4, 8])
+def test_replay_random_slices(apo, tb):
+    n = (1 << 17) + 77
+    S = W.replay_stream(n, seed=7)
+    st, ln, ig = W.replay_random_traces(n, 4000, seed=8)
+    _replay_both(apo, S, st, ln, ig, tb=tb, cap=4, half_life=200, bonus=(9, 8))
+
+
+def test_replay_full_size(apo):
+    # the replay workload's size: 2^20 tasks with every trace the online
+    # finder (ruler sampling, unit 250, buffer 5000) reports over them
+    S = W.replay_stream(1 << 20, seed=6)
+    st, ln, ig = _online_inputs(S)
+    _replay_both(apo, S, st, ln, ig, cap=8, half_life=1000, bonus=(17, 16), window=5000)
+
+
+def test_replay_edges(apo):
+    from paper_2406_18111_gb300 import ApoError
+    S = _txt("abcabcabc")
+    # no traces; traces that never enter; one-token pieces; all traces equal
+    _replay_both(apo, S, [], [], [])
+    _replay_both(apo, S, [0, 3], [3, 2], [9, 100])
+    _replay_both(apo, S, [0], [9], [0], max_len=1)
+    _replay_both(apo, S, [0, 3, 6, 3], [3, 3, 3, 3], [5, 2, 0, 7], cap=1)
+    _replay_both(apo, S[:1], [0], [1], [0])
+    # the whole stream as one trace: it can never repeat inside it
+    _replay_both(apo, S, [0], [9], [0])
+    # a constant stream with nested traces
+    C = np.zeros(500, np.uint32)
+    _replay_both(apo, C, [0, 0, 0, 7], [1, 5, 50, 13], [0, 10, 3, 100], cap=3, half_life=2, bonus=(3, 2))
+    # errors: empty trace, trace past the end, bad bonus, bad token width
+    import torch
+    t = tokens_dev(S, 4)
+    one = dev(np.array([0], np.uint32), np.int32)
+    for st, ln, kw in [([0], [0], {}), ([7], [3], {}), ([0], [3], {"bonus": (0, 1)}), ([0], [3], {"bonus": (1, 70000)})]:
+        with pytest.raises(ApoError):
+            apo.replay(t, dev(np.array(st, np.uint32), np.int32), dev(np.array(ln, np.uint32), np.int32), one, **kw)
+    with pytest.raises(TypeError):
+        apo.replay(t.view(torch.int16), one, one, one)
+    # too small a replay array: APO_ECAPACITY
+    with pytest.raises(ApoError):
+        apo.replay(t, one, dev(np.array([3], np.uint32), np.int32), one, rep_cap=1)

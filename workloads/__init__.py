@@ -283,3 +283,37 @@ def served_requests(duration_s: float = 30.0, rate: float = 2000.0, lo: int = 40
 def served_window(r: int, L: int, P: int, seed: int = 5) -> np.ndarray:
     """Tokens of served request r (see served_requests)."""
     return periodic_window(int(L), int(P), 0.05, 1000, seed * 1000033 + r)
+
+
+# --------------------------------------------------------------------------
+# Trace replay inputs
+# --------------------------------------------------------------------------
+
+def replay_stream(n: int = 1 << 20, seed: int = 6) -> np.ndarray:
+    """A task stream whose loop structure changes over time: back-to-back
+    phases (length log-uniform in [2^14, 2^17]), each a period-P loop
+    (P uniform on 20..600) with 1% noise over 2^16 tokens.  uint32[n]."""
+    out = np.empty(n, dtype=np.uint32)
+    pos, w = 0, 0
+    while pos < n:
+        s = seed * 1000003 + w
+        L = int(log_uniform_int(uniform01(s, 1, stream=70), 1 << 14, 1 << 17)[0])
+        P = int(uniform_int(s, 1, 20, 600, stream=71)[0])
+        L = min(L, n - pos)
+        out[pos:pos + L] = periodic_window(L, P, 0.01, 1 << 16, s)
+        pos += L
+        w += 1
+    return out
+
+
+def replay_random_traces(n: int, n_traces: int, seed: int, lo: int = 1, hi: int = 300):
+    """Candidate traces as random slices of a length-n stream: lengths
+    log-uniform in [lo, min(hi, n)], starts uniform, ingestion tasks uniform
+    on [0, n + n // 8] (some never enter).  Returns (start, length, ingest)
+    as uint32 arrays."""
+    hi = max(lo, min(hi, n))
+    L = log_uniform_int(uniform01(seed, n_traces, stream=80), lo, hi).astype(np.int64)
+    u = uniform01(seed, n_traces, stream=81)
+    start = np.floor(u * (n - L + 1)).astype(np.int64)
+    ingest = uniform_int(seed, n_traces, 0, n + n // 8, stream=82)
+    return start.astype(np.uint32), L.astype(np.uint32), ingest.astype(np.uint32)
