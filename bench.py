@@ -154,7 +154,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder", "replay"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
@@ -500,6 +500,121 @@ def run_finder(args, rank, world, local, emit=True):
     return out
 
 
+def run_replay(args, rank, world, local, emit=True, cpu_leg=True):
+    """Alg. 1's TraceReplayer (Sec. 4.3) over a 2^20-task stream whose loop
+    structure changes over time: the candidate traces are what the online
+    finder (ruler sampling, buffer 5000, unit 250; this library's served
+    form) reports over that stream, each ingested one analysis period after
+    its analysis point.  Replay decisions for the whole stream per step."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo, Finder, Server
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    apo.sort_tuning(args.sort_tuning)
+    n = args.n_tasks
+    S = W.replay_stream(n, seed=6 + rank)
+    unit, buffer = 250, 5000
+    srv = Server(local, min_len=MIN_LEN, token_bytes=4, max_batch_tokens=1 << 22, max_batch_windows=256,
+                 lanes=args.lanes)
+    f = Finder(srv, buffer_tokens=buffer, unit=unit)
+    st_l, ln_l, ig_l = [], [], []
+    for a in range(0, n, 1 << 16):
+        f.push(S[a:a + (1 << 16)])
+    for r in f.drain():
+        st_l.append(np.asarray(r.trace_start, dtype=np.uint64))
+        ln_l.append(np.asarray(r.trace_len, dtype=np.uint32))
+        ig_l.append(np.full(len(r.trace_len), (r.index + 1) * unit, dtype=np.uint64))
+    f.close()
+    srv.close()
+    h_st = np.concatenate(st_l).astype(np.uint32)
+    h_ln = np.concatenate(ln_l).astype(np.uint32)
+    h_ig = np.minimum(np.concatenate(ig_l), 0xffffffff).astype(np.uint32)
+    P = int(h_st.shape[0])
+    params = dict(count_cap=8, half_life=1000, bonus=(17, 16), window=5000)
+    d_S = torch.from_numpy(S.view(np.int32)).to(dev)
+    d_st, d_ln, d_ig = (torch.from_numpy(x.view(np.int32)).to(dev) for x in (h_st, h_ln, h_ig))
+    for _ in range(max(3, args.warmup)):
+        rep = apo.replay(d_S, d_st, d_ln, d_ig, curve=True, **params)
+    counts = rep[5]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    clocks = Clocks(local)
+    steps = max(1, min(args.steps, 10))
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with _Range():
+            apo.replay(d_S, d_st, d_ln, d_ig, curve=True, **params)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    ms = tot / steps
+    # per-kernel times from separate profiled steps (events around every launch)
+    apo.profile_reset()
+    apo.profile(True)
+    for _ in range(steps):
+        flush.zero_()
+        apo.replay(d_S, d_st, d_ln, d_ig, curve=True, **params)
+    torch.cuda.synchronize()
+    prof = apo.profile_read()
+    apo.profile(False)
+    # end to end: host stream and traces in, replays out
+    pin = [torch.from_numpy(x.view(np.int32)).pin_memory() for x in (S, h_st, h_ln, h_ig)]
+    dst = [torch.empty_like(x, device=dev) for x in pin]
+    tot_e2e, d2h = 0.0, 0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for d_, h_ in zip(dst, pin):
+            d_.copy_(h_, non_blocking=True)
+        e, l, t, _, _, _ = apo.replay(dst[0], dst[1], dst[2], dst[3], traced=False, **params)
+        out = [x.cpu() for x in (e, l, t)]
+        b.record(stream)
+        b.synchronize()
+        tot_e2e += a.elapsed_time(b)
+        d2h = sum(x.numel() * 4 for x in out)
+    clk = clocks.stop()
+    ms_e2e = tot_e2e / steps
+    kernels = {k: {"launches_per_step": v[0] / steps, "ms_per_step": v[1] / steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    ksum = sum(v["ms_per_step"] for v in kernels.values()) or 1.0
+    top = next(iter(kernels.items())) if kernels else ("", {"ms_per_step": 0.0, "launches_per_step": 0})
+    out = {"metric": "replayed stream tasks/s (TraceReplayer, Alg. 1 / Sec. 4.3, whole stream per step)",
+           "value": n * world / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": f"{n}-task stream of changing loops (periods 20..600, 1% noise); "
+                                  f"{P} traces from the online finder (buffer {buffer}, unit {unit}), "
+                                  f"ingested one period after their analysis point",
+                      "n_tasks": n, "traces": P, **{k: v for k, v in params.items()},
+                      "l2": "flushed between steps"},
+           "e2e": {"value": n * world / (ms_e2e / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(x.numel() * 4 for x in pin)), "d2h_bytes_per_step": d2h},
+           "replays": counts[0], "traced_fraction": counts[1] / n, "pieces": counts[2],
+           "occurrences": counts[3], "appearances": counts[4], "undecided": counts[5],
+           "selection_rounds": counts[6],
+           "top_kernel": {"kernel": top[0], "share_of_kernel_time": top[1]["ms_per_step"] / ksum},
+           "kernels": kernels, "clocks": clk}
+    if cpu_leg and rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        o = oracle.replay(S.astype(np.uint64), h_st, h_ln, h_ig, 0, params["count_cap"], params["half_life"],
+                          params["bonus"])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the whole step (the same stream and traces), {dt:.2f} s "
+                                         f"single-threaded; {len(o.end)} replays"}
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
+
+
 def run_match(args, rank, world, local, emit=True):
     """Aho-Corasick matching (Sec. 4.3) of 10,000 candidate traces (lengths
     log-uniform 5..2000; half copied from the stream, half random) against a
@@ -525,8 +640,6 @@ def run_match(args, rank, world, local, emit=True):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     clocks = Clocks(local)
-    apo.profile_reset()
-    apo.profile(True)
     tot = 0.0
     steps = max(1, min(args.steps, 10))
     for _ in range(steps):
@@ -537,10 +650,17 @@ def run_match(args, rank, world, local, emit=True):
         b.record(stream)
         b.synchronize()
         tot += a.elapsed_time(b)
-    prof = apo.profile_read()
-    apo.profile(False)
     clk = clocks.stop()
     ms = tot / steps
+    # per-kernel times from separate profiled steps (events around every launch)
+    apo.profile_reset()
+    apo.profile(True)
+    for _ in range(steps):
+        flush.zero_()
+        apo.match_candidates(ptd, off, st, cap=cap[0])
+    torch.cuda.synchronize()
+    prof = apo.profile_read()
+    apo.profile(False)
     n = int(stream_np.shape[0])
     kernels = {k: {"launches_per_step": v[0] / steps, "ms_per_step": v[1] / steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -563,7 +683,7 @@ def main():
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in ("batched", "served", "match", "finder"):
+    if args.workload in ("batched", "served", "match", "finder", "replay"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -580,6 +700,8 @@ def main():
             return run_match(args, rank, world, local)
         if args.workload == "finder":
             return run_finder(args, rank, world, local)
+        if args.workload == "replay":
+            return run_replay(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch
@@ -761,6 +883,9 @@ def main():
                                               "mean_batch_windows")}
         fd = run_finder(args, rank, world, local, emit=False)
         line["finder"] = {k: fd[k] for k in ("metric", "value", "unit", "p50_ms", "p99_ms", "config")}
+        rp = run_replay(a2, rank, world, local, emit=False, cpu_leg=False)
+        line["replay"] = {k: rp[k] for k in ("metric", "value", "unit", "ms_per_step", "e2e", "replays",
+                                              "traced_fraction", "top_kernel", "config")}
     print(json.dumps(line))
 
 

@@ -146,6 +146,16 @@ def lib():
         L.apo_server_release.argtypes = [_P, _U64]
         L.apo_server_now.argtypes = [_P]
         L.apo_server_destroy.argtypes = [_P]
+        L.apo_sort_tuning.argtypes = [_P, ctypes.c_int]
+        _I = ctypes.POINTER(ctypes.c_int)
+        _D = ctypes.POINTER(ctypes.c_double)
+        _U = ctypes.POINTER(_U32)
+        L.apo_sort_tuning_read.argtypes = [_P, ctypes.c_int, _U, _U, _U, _I, _I, _I, _D, _D]
+        L.apo_finder_create.argtypes = [ctypes.POINTER(_P), _P, ctypes.POINTER(apo_finder_config)]
+        L.apo_finder_push.argtypes = [_P, _P, _U64, ctypes.POINTER(_U64)]
+        L.apo_finder_poll.argtypes = [_P, ctypes.c_int, ctypes.POINTER(apo_finder_result)]
+        L.apo_finder_stats.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
+        L.apo_finder_destroy.argtypes = [_P]
         L.apo_replay.argtypes = [_P, _P, _U64, ctypes.c_int, ctypes.POINTER(apo_replay_traces),
                                  ctypes.POINTER(apo_replay_params), ctypes.POINTER(apo_replay_out), _P]
         for f in EXPORTS:

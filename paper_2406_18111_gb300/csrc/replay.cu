@@ -225,12 +225,16 @@ __device__ __forceinline__ bool followed(uint32_t e, uint32_t t, const uint32_t 
   return s >= need[t];
 }
 
-// ms1[e] = 1 + the largest start of a followed occurrence ending at e (0: none)
+// ms1[e] = 1 + the largest start of a followed occurrence ending at e (0: none);
+// first[e] = index of the first occurrence ending at e (occurrences come
+// sorted by end; entries of tasks without one are not written).
 __global__ void k_valid_ends(const uint32_t *__restrict__ oend, const uint32_t *__restrict__ oid, uint32_t O,
                              const uint32_t *__restrict__ canon, const uint32_t *__restrict__ need,
-                             const uint32_t *__restrict__ plen, uint32_t *__restrict__ ms1) {
+                             const uint32_t *__restrict__ plen, uint32_t *__restrict__ ms1,
+                             uint32_t *__restrict__ first) {
   RP_FOR(i, O) {
     const uint32_t e = oend[i];
+    if (i == 0 || oend[i - 1] != e) first[e] = (uint32_t)i;
     uint32_t s;
     if (followed(e, oid[i], canon, need, plen, &s)) atomicMax(&ms1[e], s + 1);
   }
@@ -261,7 +265,8 @@ __global__ void k_jump_level(const uint32_t *__restrict__ Jp, uint32_t n, uint32
 }
 
 // The chain from node 0 at stride 2^K, walked by one thread (each step moves
-// at least 2^K nodes ahead, so at most (n + 1) / 2^K + 1 steps).
+// at least 2^K nodes ahead, so at most (n + 1) / 2^K + 1 steps; K is chosen
+// to keep that near 2^8).
 __global__ void k_chain_top(const uint32_t *__restrict__ JK, uint32_t n, uint32_t *__restrict__ list,
                             uint32_t *__restrict__ len_out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -289,26 +294,18 @@ __global__ void k_chain_refine(const uint32_t *__restrict__ lin, const uint32_t 
 
 // ---------------------------------------------------------------- appearances
 // Replay r (0-based) ends at task chain[r + 1] - 1; the appearances are the
-// followed occurrences ending there and starting at chain[r] or later.
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t n, uint32_t v) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
+// followed occurrences ending there and starting at chain[r] or later (a
+// replay task always has an occurrence, so first[] is written there).
 template <bool kWrite>
-__global__ void k_appear(const uint32_t *__restrict__ chain, uint32_t R, const uint32_t *__restrict__ oend,
+__global__ void k_appear(const uint32_t *__restrict__ chain, uint32_t R, const uint32_t *__restrict__ first,
+                         const uint32_t *__restrict__ oend,
                          const uint32_t *__restrict__ oid, uint32_t O, const uint32_t *__restrict__ canon,
                          const uint32_t *__restrict__ need, const uint32_t *__restrict__ plen,
                          uint32_t *__restrict__ acnt, const uint32_t *__restrict__ aoff,
                          uint32_t *__restrict__ app_t, uint32_t *__restrict__ app_r) {
   RP_FOR(r, R) {
     const uint32_t e = chain[r + 1] - 1, c = chain[r];
-    uint32_t k = lower_bound_u32(oend, O, e), cnt = 0;
+    uint32_t k = first[e], cnt = 0;
     uint32_t w = kWrite ? aoff[r] : 0u;
     for (; k < O && oend[k] == e; ++k) {
       uint32_t s;
@@ -540,7 +537,7 @@ struct Carve {
 
 struct Ws1 {
   uint32_t *pstart, *plen, *ptau, *sp, *slcp, *tau_sorted, *lev, *canon, *need, *first_dec, *fu;
-  uint32_t *ms1, *pm, *J, *la, *lb, *acnt, *aoff, *winner, *und, *wcur, *wnew, *pre, *small;
+  uint32_t *ms1, *pm, *first, *J, *la, *lb, *acnt, *aoff, *winner, *und, *wcur, *wnew, *pre, *small;
   uint8_t *traced;
 };
 
@@ -559,6 +556,7 @@ Ws1 carve1(Carve &cv, uint64_t n, uint32_t Q, int nlev, int K) {
   w.fu = cv.take<uint32_t>(Q);
   w.ms1 = cv.take<uint32_t>(n + 1);
   w.pm = cv.take<uint32_t>(n + 1);
+  w.first = cv.take<uint32_t>(n + 1);
   w.J = cv.take<uint32_t>((size_t)(K + 1) * (n + 2));
   w.la = cv.take<uint32_t>(n + 2);
   w.lb = cv.take<uint32_t>(n + 2);
@@ -644,7 +642,7 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
     return APO_EINVAL;
   }
   const int nlev = std::max(1, bits_for(Q));
-  const int K = std::max(0, bits_for(n + 1) - 12);
+  const int K = std::max(0, bits_for(n + 1) - 8);  // the top-level walk takes at most ~2^8 steps
   Carve sz{nullptr};
   carve1(sz, n, Q, nlev, K);
   APO_TRY(ensure_rp(c, 1, sz.used, s));
@@ -716,7 +714,8 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
   APO_CUDA_TRY(cudaMemsetAsync(w.ms1, 0, n * 4, s));
   if (O32) {
     Launch lp_(c, kKRpChain, O32, s);
-    k_valid_ends<<<grid_for(O32, 256, sms), 256, 0, s>>>(v.oend, v.oid, O32, w.canon, w.need, w.plen, w.ms1);
+    k_valid_ends<<<grid_for(O32, 256, sms), 256, 0, s>>>(v.oend, v.oid, O32, w.canon, w.need, w.plen, w.ms1,
+                                                         w.first);
   }
   APO_TRY(seg_scan<false>(c, SrcU32{w.ms1}, DstU32{w.pm}, nn, OpMax(), 0u, s));
   {
@@ -757,13 +756,15 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
     // appearances: the set D of each replay task
     {
       Launch lp_(c, kKRpAppear, R, s);
-      k_appear<false><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, v.oend, v.oid, O32, w.canon, w.need, w.plen,
+      k_appear<false><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, w.first, v.oend, v.oid, O32, w.canon, w.need,
+                                                            w.plen,
                                                             w.acnt, nullptr, nullptr, nullptr);
     }
     APO_TRY(seg_scan<false>(c, SrcU32{w.acnt}, DstExclusive{w.acnt, w.aoff, R}, R, OpSum(), 0u, s));
     {
       Launch lp_(c, kKRpAppear, R, s);
-      k_appear<true><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, v.oend, v.oid, O32, w.canon, w.need, w.plen,
+      k_appear<true><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, w.first, v.oend, v.oid, O32, w.canon, w.need,
+                                                           w.plen,
                                                            nullptr, w.aoff, v.app_t, v.app_r);
     }
     // count and previous appearance per trace: stable sort by trace

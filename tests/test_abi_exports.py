@@ -33,6 +33,11 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, s), s
     import paper_2406_18111_gb300 as P
     assert set(P.EXPORTS) == set(declared_symbols())
+    # every entry point has its argument types declared: ctypes would
+    # otherwise pass a Python int (a host pointer, a 64-bit size) as a C int
+    L = P.lib()
+    for s in P.EXPORTS:
+        assert getattr(L, s).argtypes is not None, s
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
