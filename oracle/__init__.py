@@ -61,6 +61,8 @@ def lib():
         L.ora_find_repeats.argtypes = [P, U64, P, P, ctypes.c_uint32, ctypes.c_int] + [P] * 10
         L.ora_match.restype = U64
         L.ora_match.argtypes = [P, P, U64, P, U64, ctypes.c_int, P, P, U64]
+        L.ora_optimum.restype = U64
+        L.ora_optimum.argtypes = [P, U64, U64, P, P, P]
         L.ora_replay.restype = U64
         L.ora_replay.argtypes = [P, U64, U64, P, P, P] + [U64] * 5 + [P, P, P, U64, P]
         _lib = L
@@ -250,3 +252,16 @@ def replay(S, tr_start, tr_len, tr_ingest, max_len: int = 0, cap: int = 0, half_
     r = lib().ora_replay(_p(S), n, P, _p(st), _p(ln), _p(ig), max_len, cap, half_life, bonus[0], bonus[1],
                          _p(e), _p(l), _p(t), cap_r, _p(traced))
     return Replay(e[:r], l[:r], t[:r], traced[:n])
+
+
+def optimum(S, min_len: int):
+    """Sec. 3's optimisation problem with repeated traces, by exhaustive
+    enumeration (small n only): ((coverage, intervals, |T|), [(start, len)])
+    of one optimal interval set."""
+    S = _tok(S)
+    n = S.shape[0]
+    best = np.zeros(3, np.uint64)
+    ws = np.zeros(max(1, n), np.uint32)
+    wl = np.zeros(max(1, n), np.uint32)
+    k = lib().ora_optimum(_p(S), n, min_len, _p(best), _p(ws), _p(wl))
+    return (int(best[0]), int(best[1]), int(best[2])), list(zip(ws[:k].tolist(), wl[:k].tolist()))

@@ -26,6 +26,9 @@
 //                                  task: a growing trie, pointers advanced per
 //                                  task, completed candidates scored, the best
 //                                  one replayed.
+//   ora_optimum                    the optimisation problem of Sec. 3 (with
+//                                  every trace repeated) by exhaustive
+//                                  enumeration of the interval sets.
 //
 // Parity notes (readings where the paper is silent):
 //   * a suffix that is a proper prefix of another sorts first;
@@ -40,6 +43,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <set>
@@ -515,6 +519,62 @@ uint64_t ora_replay(const uint64_t *S, uint64_t n, uint64_t P, const uint64_t *t
     }
   }
   return nrep;
+}
+
+// Sec. 3's problem: traces T (sub-strings of S of length >= min_len) and
+// for each trace a set of intervals of S holding it, all intervals disjoint;
+// maximise the coverage (sum of interval lengths), then the number of
+// intervals, then minimise |T|.  As stated the problem is solved by T = {S}
+// (one interval covering everything), so every trace is required to match at
+// least two intervals: the traces must repeat.  Exhaustive: every set of
+// disjoint intervals of length >= min_len is enumerated (positions left to
+// right: uncovered, or the start of an interval of each admissible length);
+// a set is feasible iff each of its distinct strings occurs in it at least
+// twice, and T is then its set of distinct strings.  Writes the optimum
+// (coverage, intervals, |T|) and one optimal set (the first met in the
+// enumeration order; wstart/wlen, n entries each) and returns its size.
+uint64_t ora_optimum(const uint64_t *S, uint64_t n, uint64_t min_len, uint64_t *best3, uint32_t *wstart,
+                     uint32_t *wlen) {
+  std::vector<std::pair<uint64_t, uint64_t>> cur, best;
+  int64_t bcov = -1, bcnt = -1, bdist = -1;
+  auto evaluate = [&]() {
+    std::map<std::vector<uint64_t>, int> groups;
+    int64_t cov = 0;
+    for (auto &iv : cur) {
+      groups[std::vector<uint64_t>(S + iv.first, S + iv.first + iv.second)] += 1;
+      cov += (int64_t)iv.second;
+    }
+    for (auto &g : groups)
+      if (g.second < 2) return;
+    const int64_t cnt = (int64_t)cur.size(), dist = (int64_t)groups.size();
+    if (cov > bcov || (cov == bcov && (cnt > bcnt || (cnt == bcnt && dist < bdist)))) {
+      bcov = cov;
+      bcnt = cnt;
+      bdist = dist;
+      best = cur;
+    }
+  };
+  std::function<void(uint64_t)> go = [&](uint64_t p) {
+    if (p >= n) {
+      evaluate();
+      return;
+    }
+    go(p + 1);  // position p uncovered
+    for (uint64_t L = std::max<uint64_t>(min_len, 1); p + L <= n; ++L) {
+      cur.push_back({p, L});
+      go(p + L);
+      cur.pop_back();
+    }
+  };
+  go(0);
+  best3[0] = (uint64_t)bcov;
+  best3[1] = (uint64_t)bcnt;
+  best3[2] = (uint64_t)bdist;
+  for (uint64_t k = 0; k < best.size(); ++k) {
+    wstart[k] = (uint32_t)best[k].first;
+    wlen[k] = (uint32_t)best[k].second;
+  }
+  return best.size();
 }
 
 }  // extern "C"

@@ -494,3 +494,111 @@ def test_replay_agrees_with_occurrence_formulation():
         exp, traced = _replay_by_occurrences(S, starts, lens, ingest, max_len, cap, half_life, bonus)
         assert _rep(r) == exp, case
         assert r.traced.tolist() == traced, case
+
+
+# ---------------------------------------------------------------- Sec. 3 optimum
+# The optimisation problem of Sec. 3 with every trace repeated (as stated, one
+# trace equal to S would cover everything).  Hand-derived optima:
+#   abab        ab|ab                          coverage 4, 2 intervals, 1 trace
+#   abcab       ab at 0 and 3                  4, 2, 1
+#   abababab    ab x 4 beats abab x 2 on intervals  8, 4, 1
+#   abcd        nothing repeats                0, 0, 0
+#   abcabcxabc  x occurs once and is never covered; abc x 3   9, 3, 1
+#   aabaab      aab x 2                        6, 2, 1
+def test_optimum_hand_cases():
+    cases = {"abab": (4, 2, 1), "abcab": (4, 2, 1), "abababab": (8, 4, 1), "abcd": (0, 0, 0),
+             "abcabcxabc": (9, 3, 1), "aabaab": (6, 2, 1), "aaaa": (4, 2, 1)}
+    for text, want in cases.items():
+        (cov, cnt, dist), _ = oracle.optimum(_s(text), 2)
+        assert (cov, cnt, dist) == want, text
+    # min length 3: "abab" has no repeat of length 3 that fits twice
+    assert oracle.optimum(_s("abab"), 3)[0] == (0, 0, 0)
+    # xyabxyab: xy|ab|xy|ab (4 intervals, 2 traces) beats xyab x 2 (2
+    # intervals, 1 trace): more intervals come before fewer traces
+    assert oracle.optimum(_s("xyabxyab"), 2)[0] == (8, 4, 2)
+
+
+def _check_witness(S, m, best, wit):
+    S = [int(x) for x in S]
+    last = -1
+    groups = {}
+    for a, l in wit:
+        assert a > last and l >= m and a + l <= len(S)
+        last = a + l - 1
+        groups.setdefault(tuple(S[a:a + l]), []).append(a)
+    assert all(len(v) >= 2 for v in groups.values())
+    assert best == (sum(l for _, l in wit), len(wit), len(groups))
+
+
+def _optimum_mask_first(S, m):
+    """The same optimum enumerated another way: every set of covered
+    positions, then every split of its maximal runs into pieces >= m."""
+    S = [int(x) for x in S]
+    n = len(S)
+    best = (0, 0, 0)
+
+    def splits(a, b):
+        if a == b:
+            yield []
+            return
+        for L in range(m, b - a + 1):
+            for rest in splits(a + L, b):
+                yield [(a, L)] + rest
+
+    for mask in range(1 << n):
+        runs, j = [], 0
+        while j < n:
+            if mask >> j & 1:
+                k = j
+                while k < n and mask >> k & 1:
+                    k += 1
+                runs.append((j, k))
+                j = k
+            else:
+                j += 1
+        if any(b - a < m for a, b in runs):
+            continue
+        parts = [list(splits(a, b)) for a, b in runs]
+        for combo in itertools.product(*parts):
+            ivs = [iv for part in combo for iv in part]
+            g = {}
+            for a, l in ivs:
+                g[tuple(S[a:a + l])] = g.get(tuple(S[a:a + l]), 0) + 1
+            if any(c < 2 for c in g.values()):
+                continue
+            key = (sum(l for _, l in ivs), len(ivs), -len(g))
+            if key > (best[0], best[1], -best[2]):
+                best = (key[0], key[1], -key[2])
+    return best
+
+
+def test_optimum_invariants_and_second_enumeration():
+    rng = np.random.default_rng(5)
+    for case in range(120):
+        n = int(rng.integers(1, 11))
+        m = int(rng.integers(1, 4)) if n <= 8 else int(rng.integers(2, 4))
+        S = rng.integers(0, int(rng.integers(1, 4)), size=n).astype(np.uint64)
+        best, wit = oracle.optimum(S, m)
+        _check_witness(S, m, best, wit)
+        assert best == _optimum_mask_first(S, m), (S.tolist(), m)
+        # reversal and renaming of the alphabet keep the optimum
+        assert oracle.optimum(S[::-1].copy(), m)[0] == best
+        assert oracle.optimum((S * 7 + 3) % 11, m)[0] == best
+        # a solution for a prefix is a solution for S
+        if n > 1:
+            assert oracle.optimum(S[:-1], m)[0][0] <= best[0]
+
+
+def test_alg2_feasible_part_never_beats_the_optimum():
+    rng = np.random.default_rng(6)
+    for case in range(60):
+        n = int(rng.integers(4, 15))
+        per = int(rng.integers(2, 5))
+        S = rng.integers(0, 3, size=per)[np.arange(n) % per]
+        S = np.where(rng.random(n) < 0.15, rng.integers(0, 3, size=n), S).astype(np.uint64)
+        r = oracle.find_repeats(S, 2)
+        groups = {}
+        for a, l in zip(r.sel_start.tolist(), r.sel_len.tolist()):
+            groups.setdefault(tuple(S[a:a + l].tolist()), []).append(l)
+        feasible = sum(sum(v) for v in groups.values() if len(v) >= 2)
+        assert feasible <= oracle.optimum(S, 2)[0][0]
