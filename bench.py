@@ -154,7 +154,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder", "replay"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder", "replay", "quality"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
@@ -615,6 +615,81 @@ def run_replay(args, rank, world, local, emit=True, cpu_leg=True):
     return out
 
 
+def run_quality(args, rank, world, local, emit=True):
+    """Alg. 2 against the exact optimum of Sec. 3's problem (traces required
+    to repeat) on 2^16 windows of 20 tokens, min length 2: the optimum by
+    exhaustive search (apo_optimum_batched, timed: windows/s), Alg. 2 by the
+    batched form on the same windows, and how far the heuristic falls short."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    count, n, m = 1 << 16, 20, 2
+    q = W.quality_windows(count, n, seed=9 + rank)
+    off = np.arange(count + 1, dtype=np.uint64) * n
+    dq = torch.from_numpy(q.view(np.int32)).to(dev)
+    for _ in range(max(1, args.warmup)):
+        best, ws_, wl, wc = apo.optimum_batched(dq, off, m)
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    steps = max(1, min(args.steps, 5))
+    tot = 0.0
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        best, ws_, wl, wc = apo.optimum_batched(dq, off, m)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    clk = clocks.stop()
+    ms = tot / steps
+    opt = best.cpu().numpy().astype(np.int64)
+    r = apo.find_repeats_batched(dq, off, m)
+    sel_start = r.sel_start.cpu().numpy().view(np.uint32).astype(np.int64)
+    sel_len = r.sel_len.cpu().numpy().view(np.uint32).astype(np.int64)
+    sel_off = np.asarray(r.sel_off, dtype=np.int64)
+    raw = np.zeros(count, np.int64)
+    feas = np.zeros(count, np.int64)
+    qq = q.reshape(count, n)
+    for w in range(count):
+        groups = {}
+        for k in range(sel_off[w], sel_off[w + 1]):
+            a, l = int(sel_start[k]), int(sel_len[k])
+            groups.setdefault(qq[w, a:a + l].tobytes(), []).append(l)
+            raw[w] += l
+        feas[w] = sum(sum(v) for v in groups.values() if len(v) >= 2)
+    gap = opt[:, 0] - feas
+    out = {"metric": "exact Sec. 3 optimum: windows/s (exhaustive search, one thread per window)",
+           "value": count * world / (ms / 1e3), "unit": "windows/s", "n_gpus": world, "steps": steps,
+           "warmup": max(1, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": f"{count} windows of {n} tokens (half random over 2..4 tokens, half periodic "
+                                  f"with 10% noise), min length {m}", "windows": count, "n": n, "min_len": m},
+           "study": {"optimum_coverage_mean": float(opt[:, 0].mean() / n),
+                     "alg2_coverage_mean": float(raw.mean() / n),
+                     "alg2_repeated_coverage_mean": float(feas.mean() / n),
+                     "alg2_optimal_fraction": float((gap == 0).mean()),
+                     "gap_mean_tokens": float(gap.mean()), "gap_max_tokens": int(gap.max()),
+                     "gap_histogram": {str(g): int((gap == g).sum()) for g in range(0, int(gap.max()) + 1)
+                                       if int((gap == g).sum())}},
+           "clocks": clk}
+    if rank == 0:
+        import oracle
+        k = 50
+        t0 = time.perf_counter()
+        for w in range(k):
+            oracle.optimum(qq[w].astype(np.uint64), m)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k / dt, "unit": "windows/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the first {k} windows, {dt:.2f} s single-threaded (plain enumeration)"}
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
+
+
 def run_match(args, rank, world, local, emit=True):
     """Aho-Corasick matching (Sec. 4.3) of 10,000 candidate traces (lengths
     log-uniform 5..2000; half copied from the stream, half random) against a
@@ -683,7 +758,7 @@ def main():
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in ("batched", "served", "match", "finder", "replay"):
+    if args.workload in ("batched", "served", "match", "finder", "replay", "quality"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -702,6 +777,8 @@ def main():
             return run_finder(args, rank, world, local)
         if args.workload == "replay":
             return run_replay(args, rank, world, local)
+        if args.workload == "quality":
+            return run_quality(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch

@@ -404,6 +404,31 @@ int apo_replay(apo_ctx *ctx, const void *stream_tokens, uint64_t n, int token_by
                void *stream);
 
 /* ------------------------------------------------------------------------
+ * Optimal trace selection for short windows -- the optimisation problem of
+ * Sec. 3, the yardstick for Alg. 2 (a heuristic, Sec. 4.2).
+ *
+ * For each window S: choose traces T (sub-strings of S, length >= min_len)
+ * and for each trace a set of intervals of S holding it, all intervals
+ * disjoint, every trace matching at least two intervals (as stated in the
+ * paper the problem is solved by T = {S}, one interval over everything; the
+ * traces must repeat).  Maximise the coverage (summed interval lengths),
+ * then the number of intervals, then minimise |T|.
+ *
+ * Exhaustive search per window (one GPU thread each), positions left to
+ * right, each uncovered or starting an interval of length min_len,
+ * min_len + 1, ...; the witness is the first optimal set in that order.
+ * Windows hold at most 24 tokens, and the number of interval sets of the
+ * longest window at this min_len must not exceed 2^24 (e.g. 24 tokens at
+ * min_len 2, 16 at min_len 1); APO_EINVAL otherwise.
+ * ---------------------------------------------------------------------- */
+/* best: [3 * n_windows] device: coverage, intervals, |T| per window.
+ * wit_start / wit_len: [win_off[n_windows]] device: window w's optimal
+ * intervals at [win_off[w], win_off[w] + wit_count[w]), by start, in
+ * window coordinates.  wit_count: [n_windows] device.  Synchronises. */
+int apo_optimum_batched(apo_ctx *ctx, const apo_windows *windows, uint32_t min_len, uint32_t *best,
+                        uint32_t *wit_start, uint32_t *wit_len, uint32_t *wit_count, void *stream);
+
+/* ------------------------------------------------------------------------
  * Greedy selection without allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
  * running inside a task runtime that owns all device memory through its own

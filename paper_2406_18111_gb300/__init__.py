@@ -35,7 +35,7 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
            "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read", "apo_finder_create",
            "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy",
-           "apo_replay")
+           "apo_replay", "apo_optimum_batched")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -156,6 +156,7 @@ def lib():
         L.apo_finder_poll.argtypes = [_P, ctypes.c_int, ctypes.POINTER(apo_finder_result)]
         L.apo_finder_stats.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
         L.apo_finder_destroy.argtypes = [_P]
+        L.apo_optimum_batched.argtypes = [_P, ctypes.POINTER(apo_windows), _U32, _P, _P, _P, _P, _P]
         L.apo_replay.argtypes = [_P, _P, _U64, ctypes.c_int, ctypes.POINTER(apo_replay_traces),
                                  ctypes.POINTER(apo_replay_params), ctypes.POINTER(apo_replay_out), _P]
         for f in EXPORTS:
@@ -392,6 +393,26 @@ class Apo:
         r = int(counts[0])
         return (end[:r], ln[:r], tr[:r], None if tf is None else tf[:n], None if cv is None else cv[:n],
                 [int(x) for x in counts])
+
+    def optimum_batched(self, tokens, win_off, min_len: int, stream=None):
+        """Sec. 3's optimum (traces required to repeat) for every window of
+        the concatenated device tokens (host offsets win_off): per window
+        (coverage, intervals, |T|) as an int32 [W, 3] tensor, and the
+        witness intervals (start, len) at each window's offset with their
+        counts."""
+        import torch
+        wo = np.ascontiguousarray(np.asarray(win_off, dtype=np.uint64))
+        W = wo.shape[0] - 1
+        dev = tokens.device
+        best = torch.empty((max(1, W), 3), dtype=torch.int32, device=dev)
+        n = int(tokens.shape[0])
+        ws_ = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+        wl = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+        wc = torch.empty(max(1, W), dtype=torch.int32, device=dev)
+        w = apo_windows(W, _ptr(tokens), _token_bytes(tokens), wo.ctypes.data_as(_P).value)
+        _check(lib().apo_optimum_batched(self._h, ctypes.byref(w), min_len, _ptr(best), _ptr(ws_), _ptr(wl),
+                                         _ptr(wc), _stream_handle(stream)))
+        return best[:W], ws_[:n], wl[:n], wc[:W]
 
     # -------------------------------------------------------------- sort tuning
     def sort_tuning(self, mode: int):

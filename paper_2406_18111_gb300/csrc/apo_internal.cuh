@@ -87,7 +87,7 @@ enum KernelId : int {
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
   kKAcNodes, kKAcJump, kKRsTune, kKRpPieces, kKRpNeed, kKRpChain, kKRpAppear, kKRpSelect, kKRpOut,
-  kKCount
+  kKOptimum, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
@@ -116,6 +116,10 @@ struct Profiler {
 // ---------------------------------------------------------------- trace replay
 int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
                   const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- Sec. 3 optimum
+int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
+                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
 
 }  // namespace apo
 
@@ -151,6 +155,10 @@ struct SortTuner {
 // ---------------------------------------------------------------- trace replay
 int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
                   const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- Sec. 3 optimum
+int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
+                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
 
 }  // namespace apo
 
@@ -191,6 +199,10 @@ class Launch {
 // ---------------------------------------------------------------- trace replay
 int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
                   const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- Sec. 3 optimum
+int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
+                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
 
 }  // namespace apo
 
@@ -321,5 +333,9 @@ int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens,
 // ---------------------------------------------------------------- trace replay
 int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
                   const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- Sec. 3 optimum
+int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
+                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
 
 }  // namespace apo

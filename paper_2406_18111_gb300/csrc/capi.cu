@@ -80,7 +80,7 @@ const char *const kKernelNames[kKCount] = {
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
-    "rp_appear", "rp_select", "rp_out"};
+    "rp_appear", "rp_select", "rp_out", "optimum"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -471,6 +471,34 @@ int apo_replay(apo_ctx *c, const void *stream_tokens, uint64_t n, int token_byte
   }
   APO_CUDA_TRY(cudaSetDevice(c->device));
   return replay_stream(c, stream_tokens, n, token_bytes, tr, prm, out, static_cast<cudaStream_t>(stream));
+}
+
+int apo_optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wit_start,
+                        uint32_t *wit_len, uint32_t *wit_count, void *stream) {
+  if (!c || !ws || !ws->win_off || !best || !wit_start || !wit_len || !wit_count) {
+    set_error("apo_optimum_batched: null context, windows or outputs");
+    return APO_EINVAL;
+  }
+  if (ws->token_bytes != 4 && ws->token_bytes != 8) {
+    set_error("apo_optimum_batched: token_bytes must be 4 or 8");
+    return APO_EINVAL;
+  }
+  if (ws->n_windows == 0 || ws->n_windows > 0x7fffffffull || ws->win_off[0] != 0 || min_len == 0) {
+    set_error("apo_optimum_batched: need 1 <= n_windows, win_off[0] == 0 and min_len >= 1");
+    return APO_EINVAL;
+  }
+  for (uint64_t w = 0; w < ws->n_windows; ++w) {
+    if (ws->win_off[w + 1] < ws->win_off[w]) {
+      set_error("apo_optimum_batched: win_off must be non-decreasing");
+      return APO_EINVAL;
+    }
+  }
+  if (ws->win_off[ws->n_windows] >= 0x7fffffffull || (ws->win_off[ws->n_windows] > 0 && !ws->tokens)) {
+    set_error("apo_optimum_batched: null tokens or too many tokens");
+    return APO_EINVAL;
+  }
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  return optimum_batched(c, ws, min_len, best, wit_start, wit_len, wit_count, static_cast<cudaStream_t>(stream));
 }
 
 int apo_profile_enable(apo_ctx *c, int enable) {

@@ -626,3 +626,50 @@ def test_replay_edges(apo):
     # too small a replay array: APO_ECAPACITY
     with pytest.raises(ApoError):
         apo.replay(t, one, dev(np.array([3], np.uint32), np.int32), one, rep_cap=1)
+
+
+# ---------------------------------------------------------------- Sec. 3 optimum
+def _optimum_both(apo, wins, m, tb=4):
+    toks = np.concatenate([np.asarray(w, dtype=np.uint64) for w in wins]) if wins else np.zeros(0, np.uint64)
+    off = np.zeros(len(wins) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(w) for w in wins])
+    t = tokens_dev(toks if len(toks) else np.zeros(1, np.uint64), tb)[:len(toks)]
+    best, ws_, wl, wc = apo.optimum_batched(t, off, m)
+    best, ws_, wl, wc = (x.cpu().numpy() for x in (best, ws_, wl, wc))
+    for k, w in enumerate(wins):
+        want, wit = oracle.optimum(np.asarray(w, dtype=np.uint64), m)
+        assert tuple(best[k].tolist()) == want, (list(w), m)
+        a = int(off[k])
+        got = list(zip(ws_[a:a + wc[k]].tolist(), wl[a:a + wc[k]].tolist()))
+        assert got == wit, (list(w), m)  # the first optimal set in the same order
+
+
+def test_optimum_hand_and_random(apo):
+    T = {c: i + 1 for i, c in enumerate("abcdxy")}
+    hand = ["abab", "abcab", "abababab", "abcd", "abcabcxabc", "aabaab", "aaaa", "xyabxyab", "", "a"]
+    _optimum_both(apo, [[T[c] for c in h] for h in hand], 2)
+    rng = np.random.default_rng(21)
+    for m, nmax, count in ((1, 11, 150), (2, 16, 250), (3, 20, 200), (5, 24, 100)):
+        wins = []
+        for _ in range(count):
+            n = int(rng.integers(0, nmax + 1))
+            if rng.random() < 0.5:
+                w = rng.integers(0, int(rng.integers(1, 5)), size=n)
+            else:
+                per = int(rng.integers(1, 6))
+                w = rng.integers(0, 4, size=per)[np.arange(n) % per]
+                w = np.where(rng.random(n) < 0.1, rng.integers(0, 4, size=n), w)
+            wins.append(w.astype(np.uint64))
+        _optimum_both(apo, wins, m, 4)
+        _optimum_both(apo, wins[:40], m, 8)
+
+
+def test_optimum_limits(apo):
+    from paper_2406_18111_gb300 import ApoError
+    t = tokens_dev(np.zeros(25, np.uint32), 4)
+    with pytest.raises(ApoError):  # a window past 24 tokens
+        apo.optimum_batched(t, [0, 25], 2)
+    with pytest.raises(ApoError):  # 2^24 interval sets exceeded (20 tokens, min_len 1)
+        apo.optimum_batched(t[:20], [0, 20], 1)
+    with pytest.raises(ApoError):
+        apo.optimum_batched(t[:4], [0, 4], 0)

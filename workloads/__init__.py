@@ -317,3 +317,25 @@ def replay_random_traces(n: int, n_traces: int, seed: int, lo: int = 1, hi: int 
     start = np.floor(u * (n - L + 1)).astype(np.int64)
     ingest = uniform_int(seed, n_traces, 0, n + n // 8, stream=82)
     return start.astype(np.uint32), L.astype(np.uint32), ingest.astype(np.uint32)
+
+
+def quality_windows(count: int = 1 << 16, n: int = 20, seed: int = 9):
+    """Short windows for the comparison with the exact optimum: half random
+    strings over alphabets of 2..4 tokens, half periodic (period U{2..6} over
+    4 tokens) with 10% of positions redrawn.  Returns uint32[count * n]."""
+    out = np.empty((count, n), dtype=np.uint32)
+    kind = uniform_int(seed, count, 0, 1, stream=90)
+    sigma = uniform_int(seed, count, 2, 4, stream=91)
+    per = uniform_int(seed, count, 2, 6, stream=92)
+    u = uniform01(seed, count * n, stream=93).reshape(count, n)
+    body = uniform_int(seed, count * 6, 0, 3, stream=94).reshape(count, 6)
+    noise = uniform01(seed, count * n, stream=95).reshape(count, n)
+    redraw = uniform_int(seed, count * n, 0, 3, stream=96).reshape(count, n)
+    j = np.arange(n)
+    for w in range(count):
+        if kind[w] == 0:
+            out[w] = np.floor(u[w] * sigma[w]).astype(np.uint32)
+        else:
+            s = body[w, j % per[w]]
+            out[w] = np.where(noise[w] < 0.1, redraw[w], s).astype(np.uint32)
+    return out.reshape(-1)
