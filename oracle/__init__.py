@@ -265,3 +265,23 @@ def optimum(S, min_len: int):
     wl = np.zeros(max(1, n), np.uint32)
     k = lib().ora_optimum(_p(S), n, min_len, _p(best), _p(ws), _p(wl))
     return (int(best[0]), int(best[1]), int(best[2])), list(zip(ws[:k].tolist(), wl[:k].tolist()))
+
+
+def ingestion_points(submit, ready, lag0: int, growth: int = 2):
+    """Sec. 4.5's agreed ingestion across nodes, sequentially: analysis j,
+    submitted at operation submit[j], is ingested when operation
+    submit[j] + lag_j is reached on every node; ready[r][j] is the operation
+    count at which node r has the result (it waits at the ingestion point if
+    that is later); if any node waited, the lag of the next analysis grows by
+    `growth` (lag_0 = lag0).  Returns (points, waited, lags)."""
+    points, waited, lags = [], [], []
+    lag = lag0
+    for j, s in enumerate(submit):
+        p = int(s) + lag
+        w = any(int(r[j]) > p for r in ready)
+        points.append(p)
+        waited.append(w)
+        lags.append(lag)
+        if w:
+            lag *= growth
+    return points, waited, lags

@@ -339,3 +339,14 @@ def quality_windows(count: int = 1 << 16, n: int = 20, seed: int = 9):
             s = body[w, j % per[w]]
             out[w] = np.where(noise[w] < 0.1, redraw[w], s).astype(np.uint32)
     return out.reshape(-1)
+
+
+def analysis_ready_ops(submit, slice_len, node: int, seed: int = 10, ops_per_token: float = 0.05,
+                       jitter: int = 400):
+    """Operation count at which node `node` has each asynchronous analysis
+    back: submit op + slice_len * ops_per_token * (1 + node / 2) (nodes
+    differ in speed) + a uniform jitter in [0, jitter).  int64 array."""
+    submit = np.asarray(submit, dtype=np.int64)
+    L = np.asarray(slice_len, dtype=np.float64)
+    j = uniform_int(seed * 7 + node, len(submit), 0, max(0, jitter - 1), stream=100)
+    return submit + np.ceil(L * ops_per_token * (1.0 + node / 2.0)).astype(np.int64) + j
