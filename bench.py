@@ -13,8 +13,9 @@ descriptors (1-8 region arguments each).
 
 Prints one JSON line.  `value` is device-timed throughput with the
 descriptors resident in HBM (L2 flushed between steps); `e2e` is the same
-step through the library's API with host (pinned) inputs and results copied
-back inside the timed region; `roofline` reports the dominant kernel's
+step through the library's API with host (pinned) inputs copied in and the
+step's result (selected intervals and traces; the match list stays on the
+device for the replayer) copied back inside the timed region; `roofline` reports the dominant kernel's
 algorithmic bytes per launch over its event-timed launch duration against
 the measured HBM copy bandwidth.  With N > 1 (torchrun) every rank analyses
 its own window (weak scaling; windows are independent, no collective on
@@ -865,10 +866,13 @@ def main():
     pinned_out = {}
 
     def to_host(res):
+        # the step's result: the selected intervals and the traces R (the
+        # match list stays on the device for the replayer; its count reaches
+        # the host inside the call)
         r_, e_, i_ = res
         nb = 0
         for name, t in (("ss", r_.sel_start), ("sl", r_.sel_len), ("st", r_.sel_trace),
-                        ("tl", r_.trace_len), ("ts", r_.trace_start), ("me", e_), ("mi", i_)):
+                        ("tl", r_.trace_len), ("ts", r_.trace_start)):
             buf = pinned_out.get(name)
             if buf is None or buf.numel() < t.numel():
                 buf = torch.empty(max(1, int(t.numel() * 1.25)), dtype=t.dtype, pin_memory=True)
