@@ -174,7 +174,7 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
 // ---------------------------------------------------------------- greedy
 constexpr int kGI = 4;  // candidates per thread per round
 constexpr uint32_t kGreedyFirstPhase = 1u << 15;  // candidates settled before the first drop
-constexpr int glist_bytes(int threads) { return threads * kGI * 12; }
+constexpr int glist_bytes(int threads) { return threads * kGI * 16; }
 
 template <bool kSmem>
 __device__ __forceinline__ bool marked(const uint32_t *bits, uint32_t x) {
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
   cs += cb;
   acc += cb;
   m = ce - cb;
-  uint32_t *sl = gsm + words, *ss = sl + kGRound, *sk = ss + kGRound;
+  uint32_t *sl = gsm + words, *ss = sl + kGRound, *sk = ss + kGRound, *sov = sk + kGRound;
   __shared__ uint32_t s_cnt[kGI][32], s_off[kGI][32], s_total;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (kSmem)
@@ -287,6 +287,21 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
       }
     }
     __syncthreads();
+    // Overlap masks of the survivor batches, by every warp (they depend on
+    // the intervals only): sov[q] bit j = survivor q0 + j of q's batch of 32
+    // (q0 = q rounded down to 32), j before q's lane, meets survivor q.
+    for (uint32_t q = tid; q < s_total; q += kGT) {
+      const uint32_t q0 = q & ~31u, nb = min(32u, s_total - q0);
+      const uint32_t qs = ss[q], qe = qs + sl[q] - 1;
+      uint32_t ov = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t js = ss[q0 + j], je = js + sl[q0 + j] - 1;  // list has room past total
+        if (j < lane && (uint32_t)j < nb && js <= qe && qs <= je) ov |= 1u << j;
+      }
+      sov[q] = ov;
+    }
+    __syncthreads();
     if (warp == 0 && s_total) {
       // Settle the survivors 32 at a time: lane j holds survivor q0 + j.  A
       // lane is out if its ends are marked by an earlier batch; among the
@@ -296,7 +311,6 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
       const uint32_t total = s_total;
       for (uint32_t q0 = 0; q0 < total; q0 += 32) {
         const uint32_t q = q0 + lane;
-        const uint32_t nb = min(32u, total - q0);
         uint32_t qs = 0, qe = 0;
         bool free = false;
         if (q < total) {
@@ -306,14 +320,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
         }
         uint32_t und = __ballot_sync(0xffffffffu, free), accm = 0;
         if (und == 0) continue;  // every survivor of the batch met an accepted interval meanwhile
-        uint32_t ov = 0;  // earlier lanes of the batch whose interval meets this lane's
-        if (und & (und - 1)) {  // a single free lane needs no overlap test
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const uint32_t js = ss[q0 + j], je = js + sl[q0 + j] - 1;  // list has room past total
-            if (j < lane && (uint32_t)j < nb && js <= qe && qs <= je) ov |= 1u << j;
-          }
-        }
+        const uint32_t ov = q < total ? sov[q] : 0u;  // earlier lanes of the batch meeting this one
         while (und) {
           const bool mine = (und >> lane) & 1u;
           const uint32_t take = __ballot_sync(0xffffffffu, mine && (ov & (und | accm)) == 0);
