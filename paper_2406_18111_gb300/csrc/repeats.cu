@@ -41,10 +41,12 @@ namespace {
 
 
 // Alg. 2 first loop.  Each kept pair writes two (key, start) entries with
-// key = (window << (bl + bi)) | ((lmax - l) << bi) | id.  Pairs that straddle
+// key = (window << (bl + bi)) | ((lmax - l) << bi) | id, shifted left by ks
+// with the start in the low ks bits when everything fits one 64-bit key
+// (ks = 0 otherwise: the start is sorted as the value).  Pairs that straddle
 // two windows have LCP 0 and are dropped with the other short candidates.
 __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ lcp,
-                           uint32_t n, uint32_t min_len, MinTree T, int bi, int bl, uint32_t lmax,
+                           uint32_t n, uint32_t min_len, MinTree T, int bi, int bl, uint32_t lmax, int ks,
                            Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
                            uint32_t *count, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
@@ -93,9 +95,9 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
         atomicExch(err, kDevRange);
         continue;
       }
-      keys[slot] = key;
+      keys[slot] = ks ? (key << ks) | a : key;
       vals[slot] = a;
-      keys[slot + 1] = key;
+      keys[slot + 1] = ks ? (key << ks) | b : key;
       vals[slot + 1] = b;
     }
   }
@@ -158,12 +160,12 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, uint32_t
 
 __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
                               const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                              int bi, int bl, uint32_t lmax, const uint32_t *__restrict__ woff,
+                              int bi, int bl, uint32_t lmax, int ks, const uint32_t *__restrict__ woff,
                               uint32_t *__restrict__ cl, uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
-    const uint64_t key = keys[k];
+    const uint64_t key = keys[k] >> ks;
     const uint32_t base = woff ? woff[(uint32_t)(key >> (bl + bi))] : 0u;  // back to global positions
     cl[q] = lmax - (uint32_t)((key >> bi) & lmax);
     cid[q] = (uint32_t)(key & idmask) + base;
@@ -642,6 +644,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     set_error("repeats: windows, lengths and ids do not fit a 64-bit sort key");
     return APO_EINVAL;
   }
+  // the start joins the key when it fits: one digit range instead of two
+  const int ks = bw + bl + bi + bs <= 64 ? bs : 0;
 
   // 32-ary min-tree over LCP
   MinTree T;
@@ -672,7 +676,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCandCount, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKCandGen, n, s);
-    k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, bl, lmax, W, b.keys[0], b.vals[0],
+    k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, bl, lmax, ks, W, b.keys[0], b.vals[0],
                                  misc + kMiscCandCount, c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
@@ -680,17 +684,22 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_TRY(read_u32(c, misc + kMiscCandCount, &mraw, s));
   uint32_t m = 0;
   if (mraw) {
-    // start digits (the value) first, then the (window, length, id) key
+    // (window, length, id, start): one key, or start digits (the value)
+    // first and then the (window, length, id) key
     const DigitRange r[2] = {{0, bs, true}, {0, bw + bl + bi, false}};
+    const DigitRange rk{0, bw + bl + bi + bs, false};
     b.cur = 0;
-    APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
+    if (ks)
+      APO_TRY(radix_sort_pairs(c, b, mraw, &rk, 1, s));
+    else
+      APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
     PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
     APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCompactCount, s));
     APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
     {
       Launch lp_(c, kKCandGather, m, s);
       k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur], b.vals[b.cur],
-                                                                 bi, bl, lmax, W.count > 1 ? W.off_dev : nullptr,
+                                                                 bi, bl, lmax, ks, W.count > 1 ? W.off_dev : nullptr,
                                                                  cl, cid, cs);
     }
   }
