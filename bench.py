@@ -52,13 +52,13 @@ WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/30
 # workload's mean of 4.5 arguments).  The greedy loop and the automaton
 # passes are chains of dependent accesses (latency-bound) and have no entry.
 BYTES_PER_UNIT = {"rs_pass": 24, "refresh": 32, "pack": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
-                  "plcp": 24, "cand_gen": 36, "compact": 16}
+                  "plcp": 24, "rep.cand_gen": 36, "rep.compact": 16}
 
 
 # The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
 # with their radix sorts and rank refreshes) and the Phi/PLCP LCP.
-SA_LCP_KERNELS = ("init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack", "phi",
-                  "plcp", "lcp_perm")
+SA_LCP_KERNELS = ("init_keys", "key_or", "sa_dict", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
+                  "phi", "plcp", "lcp_perm")
 
 
 def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:
@@ -121,8 +121,13 @@ def traffic_for(workload: str, kernel: str, units_per_launch: float):
         f = line.split()
         if len(f) != 5 or line.startswith("#") or f[0] != workload or f[1] != kernel:
             continue
-        src = os.path.join(ROOT, f[3])
-        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != f[4]:
+        h = hashlib.sha256()
+        for rel in f[3].split(","):  # one or more source files, hashed in order
+            src = os.path.join(ROOT, rel)
+            if not os.path.exists(src):
+                return None
+            h.update(open(src, "rb").read())
+        if h.hexdigest() != f[4]:
             return None
         return float(f[2]) * units_per_launch
     return None
@@ -135,16 +140,21 @@ def tuning_summary(apo) -> list:
              round(t["best_ms"], 4), round(t["default_ms"], 4)] for t in apo.sort_tuning_read()]
 
 
-def sa_lcp_roofline(prof: dict, steps: int, b_alg: float, a_r: list, peak: float, peak_kind: str) -> dict:
-    """Algorithmic fraction of the HBM roofline for the SA+LCP path: its
-    algorithmic bytes per call over the summed event time of its kernels."""
+def sa_lcp_roofline(prof: dict, steps: int, b_alg: float, a_r: list, peak: float, peak_kind: str,
+                    traffic_step=None) -> dict:
+    """The SA+LCP path against the HBM roofline, over the summed event time
+    of its kernels: `achieved`/`frac` from its algorithmic bytes per call
+    (work efficiency), `dram_achieved`/`dram_frac` from the DRAM bytes ncu
+    measured for the same launches (`traffic`, per step; null when the
+    kernels' sources changed since)."""
     ms = sum(prof[k][1] for k in SA_LCP_KERNELS if k in prof) / steps
     launches = sum(prof[k][0] for k in SA_LCP_KERNELS if k in prof) / steps
     ach = b_alg / (ms / 1e3) / 1e9 if ms > 0 else None
+    dram = traffic_step / (ms / 1e3) / 1e9 if (traffic_step and ms > 0) else None
     return {"bound": "hbm", "unit": "GB/s", "kernels": list(SA_LCP_KERNELS), "launches_per_step": launches,
             "ms_per_step": ms, "algorithmic_bytes": b_alg, "active_per_round": a_r, "achieved": ach,
             "peak": peak, "peak_kind": peak_kind, "frac": (ach / peak) if ach else None,
-            "traffic": None}
+            "traffic": traffic_step, "dram_achieved": dram, "dram_frac": (dram / peak) if dram else None}
 
 
 def parse():
@@ -349,7 +359,7 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     full = apo.find_repeats_batched(t, off, MIN_LEN, stages=True)
     b_alg, a_r = sa_lcp_bytes(full.lcp, off, 4)
-    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind)
+    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind, traffic_for("batched", "sa_lcp", 1.0))
     del full
     out = ({
             "metric": METRIC, "value": total * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
@@ -920,7 +930,7 @@ def main():
 
     full = apo.find_repeats(tok, MIN_LEN, stages=True)
     b_alg, a_r = sa_lcp_bytes(full.lcp, None, 8)
-    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind)
+    sa_lcp = sa_lcp_roofline(prof, args.steps, b_alg, a_r, peak, peak_kind, traffic_for("window", "sa_lcp", 1.0))
     del full
 
     if rank != 0:

@@ -464,10 +464,13 @@ int apo_greedy_select_noalloc(const uint32_t *cand_len, const uint32_t *cand_sta
  * launch stream, and the elapsed device time is accumulated when the entry
  * is read.  `units` accumulates the elements each launch processed (keys for
  * a radix-sort pass, suffixes for a refresh, tokens for a match), from which
- * a caller derives algorithmic bytes.  Kernels that apo_match_candidates
- * launches to build the suffix array and LCP of its pattern text are kept
- * apart from the entries of the same kernels on other paths: their names
- * carry the prefix "ac.".
+ * a caller derives algorithmic bytes.  The same kernel on different stages
+ * is kept in separate entries: everything the matcher launches (including
+ * the suffix array of its pattern text) carries the prefix "ac.", the
+ * repeat selection after the LCP (candidates, their sort, the greedy loop,
+ * R) the prefix "rep."; unprefixed entries are the call's own path (task
+ * hashing, the suffix array and LCP of the analysed windows with its token
+ * dictionary "sa_dict", the replayer).
  * ---------------------------------------------------------------------- */
 int apo_profile_enable(apo_ctx *ctx, int enable_timing);
 int apo_profile_reset(apo_ctx *ctx);

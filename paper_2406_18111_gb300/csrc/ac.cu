@@ -991,13 +991,6 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
 
 namespace {
 
-// Launches counted under the "ac." scope while alive.
-struct ScopeGuard {
-  apo_ctx *c;
-  int prev;
-  explicit ScopeGuard(apo_ctx *c_) : c(c_), prev(c_->prof.scope) { c->prof.scope = 1; }
-  ~ScopeGuard() { c->prof.scope = prev; }
-};
 
 // Exclusive prefix of plen[p] + 1 (pattern p's first position in T).
 struct SrcPlen {
@@ -1016,6 +1009,7 @@ struct DstTstart {
 int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint64_t n,
                    uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
                    cudaStream_t s, uint32_t *aux_order, uint32_t *aux_slcp) {
+  ScopeGuard scope_(c, kScopeMatch);
   const uint32_t P = (uint32_t)pp->n_patterns;
   const int tb = pp->token_bytes;
   uint32_t *misc = c->ps.counters + kCtrMisc;
@@ -1213,7 +1207,6 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   } else {
     // suffix array and LCP of the pattern text
     {
-      ScopeGuard scope(c);
       uint32_t *snaps[64];
       for (int k = 0; k < levels; ++k) snaps[k] = snap_base + (size_t)k * N;
       st.snaps = snaps;

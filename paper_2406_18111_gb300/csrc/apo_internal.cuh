@@ -87,14 +87,17 @@ enum KernelId : int {
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
   kKAcNodes, kKAcJump, kKRsTune, kKRpPieces, kKRpNeed, kKRpChain, kKRpAppear, kKRpSelect, kKRpOut,
-  kKOptimum, kKCount
+  kKOptimum, kKSaDict, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
-// Launch records are kept per scope: scope 0 is the call's own path; scope 1
-// holds the suffix array and LCP of the pattern text built while matching
-// (reported with an "ac." prefix), so that the two never mix.
-constexpr int kScopes = 2;
+// Launch records are kept per scope, so that the same kernel on different
+// stages never mixes: scope 0 is the call's own path (hashing, the suffix
+// array and LCP of the analysed windows, the replayer), scope 1 everything
+// the matcher launches ("ac." prefix), scope 2 the repeat selection after
+// the LCP ("rep." prefix: candidates, their sort, greedy loop, R).
+constexpr int kScopes = 3;
+enum : int { kScopeOwn = 0, kScopeMatch = 1, kScopeRepeats = 2 };
 
 struct Profiler {
   bool timing = false;
@@ -179,6 +182,16 @@ struct apo_ctx {
 };
 
 namespace apo {
+
+// Launches counted under `scope` while alive (restores the previous scope).
+struct ScopeGuard {
+  apo_ctx *c;
+  int prev;
+  ScopeGuard(apo_ctx *c_, int scope);
+  ~ScopeGuard();
+  ScopeGuard(const ScopeGuard &) = delete;
+  ScopeGuard &operator=(const ScopeGuard &) = delete;
+};
 
 // Counts one kernel launch and, with timing enabled, brackets it with CUDA
 // events on the launch stream.  Construct it right before the launch.

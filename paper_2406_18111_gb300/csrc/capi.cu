@@ -74,13 +74,16 @@ int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s) {
   return APO_OK;
 }
 
+ScopeGuard::ScopeGuard(apo_ctx *c_, int scope) : c(c_), prev(c_->prof.scope) { c->prof.scope = scope; }
+ScopeGuard::~ScopeGuard() { c->prof.scope = prev; }
+
 const char *const kKernelNames[kKCount] = {
     "hash_tasks", "init_keys", "key_or", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
     "phi", "plcp", "lcp_perm", "min32", "max", "cand_gen", "compact", "cand_gather", "greedy",
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
-    "rp_appear", "rp_select", "rp_out", "optimum"};
+    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -533,7 +536,8 @@ int apo_profile_read(apo_ctx *c, int index, char *name, size_t name_cap, uint64_
   }
   c->prof.resolve();
   if (name && name_cap) {
-    const std::string nm = std::string(index >= kKCount ? "ac." : "") + kKernelNames[index % kKCount];
+    static const char *const kPrefix[kScopes] = {"", "ac.", "rep."};
+    const std::string nm = std::string(kPrefix[index / kKCount]) + kKernelNames[index % kKCount];
     strncpy(name, nm.c_str(), name_cap - 1);
     name[name_cap - 1] = 0;
   }

@@ -612,6 +612,7 @@ size_t repeats_workspace_bytes(uint64_t n, uint64_t windows) {
 int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixState &st,
                          const uint32_t *lcp, uint32_t min_len, apo_repeats_out *out,
                          const BatchOffsets *boff, cudaStream_t s) {
+  ScopeGuard scope_(c, kScopeRepeats);
   (void)tokens;
   (void)tb;
   const uint32_t n = st.n;

@@ -446,7 +446,7 @@ int dictionary_begin(apo_ctx *c, const void *tokens, int tb, uint32_t n, DictCod
   APO_CUDA_TRY(cudaMemsetAsync(d->keys, 0xff, d->cap * sizeof(uint64_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, 2 * sizeof(uint32_t), s));
   {
-    Launch lp_(c, kKDictInsert, n, s);
+    Launch lp_(c, kKSaDict, n, s);
     k_dict_tokens<<<grid_for(n, 256, c->num_sms), 256, 0, s>>>(tokens, tb, n, d->keys, d->cap - 1, limit,
                                                                misc + kMiscDict, misc + kMiscDict + 1);
   }
@@ -462,7 +462,7 @@ int dictionary_finish(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tb
   uint32_t *misc = c->ps.counters + kCtrMisc;
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, sizeof(uint32_t), s));
   {
-    Launch lp_(c, kKDictMap, d->cap, s);
+    Launch lp_(c, kKSaDict, d->cap, s);
     k_dict_list<<<grid_for(d->cap, 256, c->num_sms), 256, 0, s>>>(d->keys, d->cap, d->lb.keys[0], d->lb.vals[0],
                                                                   misc + kMiscDict);
   }
@@ -470,12 +470,12 @@ int dictionary_finish(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tb
   const DigitRange r{0, tbits, false};
   APO_TRY(radix_sort_pairs(c, d->lb, sigma, &r, 1, s));
   {
-    Launch lp_(c, kKDictMap, sigma, s);
+    Launch lp_(c, kKSaDict, sigma, s);
     k_code_scatter<<<grid_for(std::max<uint32_t>(sigma, 1), 256, c->num_sms), 256, 0, s>>>(d->lb.vals[d->lb.cur],
                                                                                            sigma, d->slot_code);
   }
   {
-    Launch lp_(c, kKDictMap, n, s);
+    Launch lp_(c, kKSaDict, n, s);
     k_code_map<<<grid_for(n, 256, c->num_sms), 256, 0, s>>>(tokens, tb, n, d->keys, d->cap - 1, d->slot_code,
                                                             sigma + 1, d->codes);
   }
