@@ -65,7 +65,7 @@ enum : int {
 enum : int {
   kMiscRefreshTiles = 0, kMiscRefreshCount, kMiscCompactTiles, kMiscCompactCount,
   kMiscCandCount, kMiscMaxLen, kMiscAccCount, kMiscTraceCount, kMiscMatchCount,
-  kMiscKeyOr = 16,        // u64, two words
+  kMiscKeyOr = 16,        // two u64 (four words): OR and maximum of keys
   kMiscRound = 20,        // two words: active-suffix counts of consecutive doubling rounds
   kMiscDict = 22,         // two words: distinct tokens, dictionary overflow flag
   kMiscCount = 64,
@@ -276,7 +276,8 @@ int sort_first_hist_clear(apo_ctx *c, cudaStream_t s);
 uint32_t *sort_first_hist(apo_ctx *c);
 int radix_sort_planned(apo_ctx *c, SortBuffers &b, uint32_t n, const SortPlan &sp, cudaStream_t s,
                        const uint32_t *n_dev, bool hist_ready);
-// OR of all keys (to learn how many digits are populated); result in *out_dev.
+// OR of all keys (how many digits are populated) in out_dev[0] and their
+// maximum in out_dev[1]; both words must be zero on entry.
 void launch_key_or(apo_ctx *c, const uint64_t *keys, uint32_t n, uint64_t *out_dev, cudaStream_t s);
 int radix_sort_init();
 int sort_shape_info(int id, int *threads, int *items, int *bits);

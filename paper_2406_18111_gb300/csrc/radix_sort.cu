@@ -220,13 +220,24 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
   }
 }
 
+// out[0] |= every key, out[1] = max(out[1], every key).
 __global__ void k_key_or(const uint64_t *__restrict__ keys, uint32_t n, unsigned long long *out) {
-  uint64_t acc = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    acc |= keys[i];
+  uint64_t acc = 0, mx = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    acc |= k;
+    mx = k > mx ? k : mx;
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicOr(out, (unsigned long long)acc);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    const uint64_t m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && acc) {
+    atomicOr(out, (unsigned long long)acc);
+    atomicMax(out + 1, (unsigned long long)mx);
+  }
 }
 
 // Synthetic trial pairs: keys uniform over `bits` bits (splitmix64 of the

@@ -527,21 +527,23 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   // distinct tokens is filled in the same round trip)
   uint32_t *misc = c->ps.counters + kCtrMisc;
   uint64_t *kor = reinterpret_cast<uint64_t *>(misc + kMiscKeyOr);
-  APO_CUDA_TRY(cudaMemsetAsync(kor, 0, sizeof(uint64_t), s));
+  APO_CUDA_TRY(cudaMemsetAsync(kor, 0, 2 * sizeof(uint64_t), s));
   launch_key_or(c, b.keys[0], n, kor, s);
   DictCodes dict;
   const bool dict_early = tb == 8 && n >= 4096;
   if (dict_early) APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
-  uint64_t orv = 0;
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, kor, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  uint64_t orv = 0, maxv = 0;
+  // (pinned words 8..11: words 2..3 may be receiving the dictionary's size)
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 8, kor, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
-  memcpy(&orv, c->host_pinned, sizeof(uint64_t));
+  memcpy(&orv, c->host_pinned + 8, sizeof(uint64_t));
+  memcpy(&maxv, c->host_pinned + 10, sizeof(uint64_t));
 
   // codes for the packed first keys: token + 1, or dictionary ranks when
   // that packs more tokens per key
   const int wb = st.win.count > 1 ? bits_for(st.win.count - 1) : 0;
   const int tbits = bits_for(orv);
-  int cb = tbits <= 32 ? bits_for(orv + 1) : 0;
+  int cb = tbits <= 32 ? bits_for(maxv + 1) : 0;  // codes token + 1 <= max + 1
   uint32_t h0 = cb ? (uint32_t)((64 - wb) / cb) : 0;
   const uint32_t *codes = nullptr;
   if (h0 < 4 && n >= 4096) {
