@@ -336,6 +336,23 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
     prof = apo.profile_read()
     apo.profile(False)
 
+    # the same call replayed as a CUDA graph (apo_graph_mode): the first
+    # call records and captures, the timed ones replay
+    ga = Apo(local)
+    ga.sort_tuning(args.sort_tuning)
+    ga.graph_mode(True)
+    for _ in range(max(2, args.warmup)):
+        ga.find_repeats_batched(t, off, MIN_LEN, stages=False, reuse=True)
+    torch.cuda.synchronize()
+    st0 = ga.graph_stats()
+    ms_graph = timed(lambda: ga.find_repeats_batched(t, off, MIN_LEN, stages=False, reuse=True), args.steps)
+    st1 = ga.graph_stats()
+    graph = {"value": total * world / (ms_graph / 1e3), "unit": UNIT, "ms_per_step": ms_graph,
+             "replays_in_timed_steps": st1["replays"] - st0["replays"], "captures": st1["captures"],
+             "discarded": st1["discarded"],
+             "form": "the whole batched call as one CUDA graph launch (recorded host reads, checked on the device)"}
+    ga.close()
+
     def plain():
         for w in range(args.windows):
             a, b = int(off[w]), int(off[w + 1])
@@ -371,7 +388,7 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
                        "l2": "flushed between steps"},
             "plain": {"value": total / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                       "form": "one apo_find_repeats call per window, same stream", "steps": plain_steps},
-            "batched_over_plain": ms_plain / ms,
+            "batched_over_plain": ms_plain / ms, "graph": graph,
             "gpu_launches": n_launch, "roofline": roof, "sa_lcp_roofline": sa_lcp, "clocks": clk,
             "kernels": kernels, "sort_tuning": tuning_summary(apo)})
     if emit and rank == 0:
@@ -966,7 +983,7 @@ def main():
         a2.steps, a2.warmup = min(args.steps, 5), 2
         bt = run_batched(a2, rank, world, local, emit=False, plain_steps=1)
         line["batched"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "config", "plain",
-                                               "batched_over_plain", "roofline", "sa_lcp_roofline")}
+                                               "batched_over_plain", "graph", "roofline", "sa_lcp_roofline")}
         a3 = copy.copy(args)
         a3.duration = 2.0
         sv = run_served(a3, rank, world, local, emit=False)

@@ -191,6 +191,23 @@ typedef struct {
 int apo_find_repeats_batched(apo_ctx *ctx, const apo_windows *windows,
                              const apo_repeats_params *params, apo_repeats_out *out, void *stream);
 
+/* Graph mode for apo_find_repeats_batched (off by default).  The first call
+ * with given arguments (token pointer and width, window offsets, min_len,
+ * output pointers and capacities) runs as usual while the values the host
+ * reads back between its kernels are recorded; the call is then captured
+ * into a CUDA graph that takes those values as given and checks each on the
+ * device where it would have been read.  Later calls with the same arguments
+ * replay the graph, one launch for the whole call; when a check fails (the
+ * token contents led to other counts) the replay is discarded and the call
+ * runs as usual and is recorded again.  Results are the same either way.
+ * Calls with one window, and calls while the context's workspace has moved
+ * since the capture, run as usual.  enable = 0 turns it off and frees the
+ * graphs. */
+int apo_graph_mode(apo_ctx *ctx, int enable);
+/* Since graph mode was turned on: calls answered by a graph replay, graphs
+ * captured, replays discarded because a check failed (HOST outputs). */
+int apo_graph_stats(apo_ctx *ctx, uint64_t *replays, uint64_t *captures, uint64_t *discarded);
+
 /* ------------------------------------------------------------------------
  * Served repeat finding -- Alg. 1 launches an asynchronous FindRepeats for
  * each history slice while the application keeps issuing tasks, and ingests

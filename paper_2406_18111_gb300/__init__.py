@@ -35,7 +35,7 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
            "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read", "apo_finder_create",
            "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy",
-           "apo_replay", "apo_optimum_batched")
+           "apo_replay", "apo_optimum_batched", "apo_graph_mode", "apo_graph_stats")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -156,6 +156,8 @@ def lib():
         L.apo_finder_poll.argtypes = [_P, ctypes.c_int, ctypes.POINTER(apo_finder_result)]
         L.apo_finder_stats.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
         L.apo_finder_destroy.argtypes = [_P]
+        L.apo_graph_mode.argtypes = [_P, ctypes.c_int]
+        L.apo_graph_stats.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
         L.apo_optimum_batched.argtypes = [_P, ctypes.POINTER(apo_windows), _U32, _P, _P, _P, _P, _P]
         L.apo_replay.argtypes = [_P, _P, _U64, ctypes.c_int, ctypes.POINTER(apo_replay_traces),
                                  ctypes.POINTER(apo_replay_params), ctypes.POINTER(apo_replay_out), _P]
@@ -301,9 +303,12 @@ class Apo:
                        ss[:k], sl[:k], st[:k], tl[:t], ts[:t], rounds)
 
     def find_repeats_batched(self, tokens, win_off, min_len: int, stages: bool = True,
-                             stream=None) -> "BatchRepeats":
+                             stream=None, reuse: bool = False) -> "BatchRepeats":
         """Alg. 2 on many windows at once: tokens holds the windows back to
-        back, window w = tokens[win_off[w]:win_off[w+1]] (win_off on the host)."""
+        back, window w = tokens[win_off[w]:win_off[w+1]] (win_off on the host).
+        With reuse, the output buffers are kept for the next call of the same
+        sizes (the returned tensors are then overwritten by it), so that
+        repeated calls hand the library the same arguments (graph mode)."""
         import torch
         wo = np.ascontiguousarray(np.asarray(win_off, dtype=np.uint64))
         W = wo.shape[0] - 1
@@ -312,13 +317,21 @@ class Apo:
         u32 = torch.int32
         M = max(1, 2 * n)
         K = max(1, n // max(1, min_len))
-        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
-        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages else None
-        cl = torch.empty(M, dtype=u32, device=dev) if stages else None
-        ci = torch.empty(M, dtype=u32, device=dev) if stages else None
-        cs = torch.empty(M, dtype=u32, device=dev) if stages else None
-        ca = torch.empty(M, dtype=torch.uint8, device=dev) if stages else None
-        ss, sl, st, tl, ts = (torch.empty(K, dtype=u32, device=dev) for _ in range(5))
+        bkey = (n, W, int(min_len), bool(stages), str(dev))
+        bufs = getattr(self, "_bufs", {}).get(bkey) if reuse else None
+        if bufs is None:
+            bufs = (torch.empty(max(1, n), dtype=u32, device=dev) if stages else None,
+                    torch.empty(max(1, n), dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=torch.uint8, device=dev) if stages else None,
+                    *(torch.empty(K, dtype=u32, device=dev) for _ in range(5)))
+            if reuse:
+                if not hasattr(self, "_bufs"):
+                    self._bufs = {}
+                self._bufs[bkey] = bufs
+        sa, lcp, cl, ci, cs, ca, ss, sl, st, tl, ts = bufs
         counts = (ctypes.c_uint64 * 4)()
         offs = [np.zeros(W + 1, dtype=np.uint64) for _ in range(3)]
         o = apo_repeats_out(_ptr(sa), _ptr(lcp), _ptr(cl), _ptr(ci), _ptr(cs), _ptr(ca),
@@ -413,6 +426,16 @@ class Apo:
         _check(lib().apo_optimum_batched(self._h, ctypes.byref(w), min_len, _ptr(best), _ptr(ws_), _ptr(wl),
                                          _ptr(wc), _stream_handle(stream)))
         return best[:W], ws_[:n], wl[:n], wc[:W]
+
+    def graph_mode(self, enable: bool = True):
+        """Replay batched calls with unchanged arguments as CUDA graphs
+        (apo_graph_mode); results are the same as without."""
+        _check(lib().apo_graph_mode(self._h, int(bool(enable))))
+
+    def graph_stats(self) -> dict:
+        a, b, c = _U64(0), _U64(0), _U64(0)
+        _check(lib().apo_graph_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"replays": int(a.value), "captures": int(b.value), "discarded": int(c.value)}
 
     # -------------------------------------------------------------- sort tuning
     def sort_tuning(self, mode: int):

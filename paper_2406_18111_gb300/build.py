@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libapo.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["capi.cu", "radix_sort.cu", "suffix.cu", "repeats.cu", "hash.cu", "ac.cu", "noalloc.cu", "serve.cu", "finder.cu", "replay.cu", "optimum.cu"]
+SOURCES = ["capi.cu", "radix_sort.cu", "suffix.cu", "repeats.cu", "hash.cu", "ac.cu", "noalloc.cu", "serve.cu", "finder.cu", "replay.cu", "optimum.cu", "graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

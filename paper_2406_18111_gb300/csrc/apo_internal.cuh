@@ -48,6 +48,7 @@ struct Arena {
   char *base = nullptr;
   size_t cap = 0;
   size_t used = 0;
+  uint64_t moves = 0;  // reallocations so far
   int reserve(size_t bytes);
   void reset() { used = 0; }
   void *take(size_t bytes);
@@ -116,14 +117,6 @@ struct Profiler {
   void release();
 };
 
-// ---------------------------------------------------------------- trace replay
-int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
-                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
-
-// ---------------------------------------------------------------- Sec. 3 optimum
-int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
-                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
-
 }  // namespace apo
 
 namespace apo {
@@ -155,14 +148,29 @@ struct SortTuner {
   static int size_class(uint32_t n);
 };
 
-// ---------------------------------------------------------------- trace replay
-int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
-                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
+}  // namespace apo
 
-// ---------------------------------------------------------------- Sec. 3 optimum
-int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
-                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
-
+namespace apo {
+// Host reads of a call, for replaying the call as a CUDA graph.  While a call
+// is recorded, every value the host reads back from the device (a count, a
+// code width, the error word) is appended to `vals`; while the same call is
+// captured into a graph, those reads take the recorded values in the same
+// order and queue a check of the device words at that point of the stream
+// instead (a difference counts into the device word `bad`: the replay's
+// results are then discarded).  `stage` (pinned) receives the per-window
+// output offsets a capture copies back, `upload` (pinned) holds the window
+// offsets a capture copies in.
+struct Tape {
+  int mode = 0;
+  std::vector<uint32_t> vals;
+  size_t pos = 0;
+  uint32_t *dev_vals = nullptr;
+  uint32_t *bad = nullptr;
+  uint32_t *stage = nullptr;
+  uint32_t *upload = nullptr;
+};
+enum : int { kTapeOff = 0, kTapeRecord = 1, kTapeCapture = 2 };
+struct GraphCache;
 }  // namespace apo
 
 struct apo_ctx {
@@ -179,6 +187,10 @@ struct apo_ctx {
   void *rp[3] = {nullptr, nullptr, nullptr};     // trace replay buffers (grow-only)
   size_t rp_bytes[3] = {0, 0, 0};
   uint64_t rp_cap = 0;                            // occurrences the replay buffers hold
+  apo::Tape *tape = nullptr;                      // active tape of a recorded or captured call
+  uint64_t gen = 0;                               // bumped when a workspace buffer moves
+  int graph_mode = 0;                             // replay batched calls as CUDA graphs
+  apo::GraphCache *graphs = nullptr;
 };
 
 namespace apo {
@@ -208,14 +220,6 @@ class Launch {
   cudaStream_t s_;
   cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
-
-// ---------------------------------------------------------------- trace replay
-int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,
-                  const apo_replay_params *prm, apo_replay_out *out, cudaStream_t s);
-
-// ---------------------------------------------------------------- Sec. 3 optimum
-int optimum_batched(apo_ctx *c, const apo_windows *ws, uint32_t min_len, uint32_t *best, uint32_t *wstart,
-                    uint32_t *wlen, uint32_t *wcount, cudaStream_t s);
 
 }  // namespace apo
 
@@ -343,6 +347,23 @@ int server_token_bytes(apo_server *s);
 int match_patterns(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,
                    uint32_t *match_end, uint32_t *match_id, uint64_t cap, uint64_t *count,
                    cudaStream_t s, uint32_t *aux_order = nullptr, uint32_t *aux_slcp = nullptr);
+
+// ---------------------------------------------------------------- call tapes
+inline bool capturing(const apo_ctx *c) { return c->tape && c->tape->mode == kTapeCapture; }
+inline bool recording(const apo_ctx *c) { return c->tape && c->tape->mode == kTapeRecord; }
+// Recording: append `words` values the host has read.
+void tape_put(apo_ctx *c, const uint32_t *vals, int words);
+// Capturing: the next `words` recorded values into host[], and a check that
+// the device words at `dev` hold them at this point of the stream.
+int tape_take(apo_ctx *c, const uint32_t *dev, uint32_t *host, int words, cudaStream_t s);
+void graph_cache_free(apo_ctx *c);
+void graph_stats(apo_ctx *c, uint64_t *replays, uint64_t *captures, uint64_t *discarded);
+namespace drv {
+int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total, const uint64_t *win_off,
+                        uint32_t nwin, const apo_repeats_params *p, apo_repeats_out *out, cudaStream_t s);
+}
+int graph_batched(apo_ctx *c, const apo_windows *ws, const apo_repeats_params *p, apo_repeats_out *out,
+                  cudaStream_t s);
 
 // ---------------------------------------------------------------- trace replay
 int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int token_bytes, const apo_replay_traces *tr,

@@ -31,6 +31,7 @@ int Arena::reserve(size_t bytes) {
     cap = 0;
   }
   const size_t want = std::max<size_t>(bytes, (size_t)1 << 24);
+  ++moves;
   if (cudaMalloc(&base, want) != cudaSuccess) {
     cudaGetLastError();
     base = nullptr;
@@ -59,6 +60,7 @@ int ensure_lookback(apo_ctx *c, size_t words) {
   APO_CUDA_TRY(cudaMalloc(&c->ps.lookback, w * sizeof(uint64_t)));
   APO_CUDA_TRY(cudaMemset(c->ps.lookback, 0, w * sizeof(uint64_t)));
   c->ps.lookback_words = w;
+  ++c->gen;
   return APO_OK;
 }
 
@@ -71,6 +73,7 @@ int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s) {
   const size_t want = std::max<size_t>(bytes + bytes / 4, (size_t)1 << 20);
   APO_CUDA_TRY(cudaMalloc(&c->side, want));
   c->side_bytes = want;
+  ++c->gen;
   return APO_OK;
 }
 
@@ -118,7 +121,7 @@ Launch::Launch(apo_ctx *c, int id, uint64_t units, cudaStream_t s)
     : c_(c), id_(id + c->prof.scope * kKCount), s_(s) {
   c->prof.launches[id_] += 1;
   c->prof.units[id_] += units;
-  if (c->prof.timing) {
+  if (c->prof.timing && !capturing(c)) {
     if (c->prof.pending.size() > 8192) c->prof.resolve();
     a_ = c->prof.get();
     b_ = c->prof.get();
@@ -217,6 +220,7 @@ int apo_destroy(apo_ctx *c) {
   if (!c) return APO_OK;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  graph_cache_free(c);
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->ps.err) cudaFree(c->ps.err);
   if (c->ps.lookback) cudaFree(c->ps.lookback);
@@ -330,12 +334,17 @@ int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total,
       h[w] = (uint32_t)win_off[w];
       if (w) maxlen = std::max(maxlen, h[w] - h[w - 1]);
     }
-    APO_CUDA_TRY(cudaMemcpyAsync(off, h.data(), (nwin + 1) * 4, cudaMemcpyHostToDevice, s));
+    if (capturing(c)) {  // a graph copies from a pinned buffer that outlives this call
+      memcpy(c->tape->upload, h.data(), (nwin + 1) * 4);
+      APO_CUDA_TRY(cudaMemcpyAsync(off, c->tape->upload, (nwin + 1) * 4, cudaMemcpyHostToDevice, s));
+    } else {
+      APO_CUDA_TRY(cudaMemcpyAsync(off, h.data(), (nwin + 1) * 4, cudaMemcpyHostToDevice, s));
+    }
     {
       Launch lp_(c, kKInitKeys, n, s);
       k_fill_windows<<<std::min<uint32_t>(nwin, 4096), 256, 0, s>>>(off, nwin, wid, wend);
     }
-    APO_CUDA_TRY(cudaStreamSynchronize(s));  // h goes out of scope
+    if (!capturing(c)) APO_CUDA_TRY(cudaStreamSynchronize(s));  // h goes out of scope
     st.win.wid = wid;
     st.win.wend = wend;
     st.win.off_host = win_off;
@@ -363,8 +372,16 @@ int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total,
   const int r = find_repeats_from_sa(c, tokens, tb, st, lcp, p->min_len, out, &boff, s);
   out->counts[3] = rounds;
   if (r == APO_OK) {
+    if (capturing(c)) {  // the error word must still be clear at the end of a replay
+      uint32_t e = 0;
+      return tape_take(c, c->ps.err, &e, 1, s);
+    }
     APO_CUDA_TRY(cudaStreamSynchronize(s));
-    return check_device_error(c, s);
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (recording(c)) tape_put(c, c->host_pinned + kPinnedErr, 1);
+    return device_error_status(c, s);
   }
   return r;
 }
@@ -405,8 +422,29 @@ int apo_find_repeats_batched(apo_ctx *c, const apo_windows *ws, const apo_repeat
       return APO_EINVAL;
     }
   }
+  if (c->graph_mode) return graph_batched(c, ws, p, out, static_cast<cudaStream_t>(stream));
   return drv::find_repeats_driver(c, ws->tokens, ws->token_bytes, ws->win_off[ws->n_windows], ws->win_off,
                              (uint32_t)ws->n_windows, p, out, static_cast<cudaStream_t>(stream));
+}
+
+int apo_graph_stats(apo_ctx *c, uint64_t *replays, uint64_t *captures, uint64_t *discarded) {
+  if (!c || !replays || !captures || !discarded) {
+    set_error("apo_graph_stats: null argument");
+    return APO_EINVAL;
+  }
+  graph_stats(c, replays, captures, discarded);
+  return APO_OK;
+}
+
+int apo_graph_mode(apo_ctx *c, int enable) {
+  if (!c) {
+    set_error("apo_graph_mode: null context");
+    return APO_EINVAL;
+  }
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  c->graph_mode = enable != 0;
+  if (!enable) graph_cache_free(c);
+  return APO_OK;
 }
 
 int apo_match_candidates(apo_ctx *c, const apo_patterns *p, const void *stream_tokens, uint64_t n,

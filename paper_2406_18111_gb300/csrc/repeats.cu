@@ -509,12 +509,22 @@ inline int grid_for(uint64_t n, int threads, int sms) {
   return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
 }
 
-// A device count and the error word in one synchronisation.
+// A device count and the error word in one synchronisation (a captured call
+// takes both from its tape).
 int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {
+  if (capturing(c)) {
+    uint32_t e = 0;
+    APO_TRY(tape_take(c, dev, host, 1, s));
+    return tape_take(c, c->ps.err, &e, 1, s);
+  }
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
+  if (recording(c)) {
+    tape_put(c, c->host_pinned, 1);
+    tape_put(c, c->host_pinned + kPinnedErr, 1);
+  }
   APO_TRY(device_error_status(c, s));
   *host = c->host_pinned[0];
   return APO_OK;
@@ -845,7 +855,20 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_TRY(copy_out(out->sel_trace, sq, K, out->sel_cap, &over, s));
   APO_TRY(copy_out(out->trace_len, tl, Tn, out->trace_cap, &over, s));
   APO_TRY(copy_out(out->trace_start, ts, Tn, out->trace_cap, &over, s));
-  if (boff && W.count > 1) {
+  if (boff && W.count > 1 && capturing(c)) {
+    // a replay copies the offsets to the tape's pinned stage (zeros where
+    // there is nothing), the host reads them after the replay
+    uint32_t *h = c->tape->stage;
+    const size_t wb = (size_t)(W.count + 1) * 4;
+    if (m) APO_CUDA_TRY(cudaMemcpyAsync(h, cand_off, wb, cudaMemcpyDeviceToHost, s));
+    else memset(h, 0, wb);
+    if (K) {
+      APO_CUDA_TRY(cudaMemcpyAsync(h + (W.count + 1), sel_off, wb, cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaMemcpyAsync(h + 2 * (W.count + 1), trace_off, wb, cudaMemcpyDeviceToHost, s));
+    } else {
+      memset(h + (W.count + 1), 0, 2 * wb);
+    }
+  } else if (boff && W.count > 1) {
     std::vector<uint32_t> h(3 * (size_t)(W.count + 1), 0);
     if (m) APO_CUDA_TRY(cudaMemcpyAsync(h.data(), cand_off, (W.count + 1) * 4, cudaMemcpyDeviceToHost, s));
     if (K) {
@@ -865,8 +888,17 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     if (boff->sel_off) boff->sel_off[1] = K;
     if (boff->trace_off) boff->trace_off[1] = Tn;
   }
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
+  if (capturing(c)) {
+    uint32_t e = 0;
+    APO_TRY(tape_take(c, c->ps.err, &e, 1, s));
+  } else {
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (recording(c)) tape_put(c, c->host_pinned + kPinnedErr, 1);
+    APO_TRY(device_error_status(c, s));
+  }
   counts[0] = m;
   counts[1] = K;
   counts[2] = Tn;

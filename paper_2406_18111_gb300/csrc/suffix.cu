@@ -450,16 +450,26 @@ int dictionary_begin(apo_ctx *c, const void *tokens, int tb, uint32_t n, DictCod
     k_dict_tokens<<<grid_for(n, 256, c->num_sms), 256, 0, s>>>(tokens, tb, n, d->keys, d->cap - 1, limit,
                                                                misc + kMiscDict, misc + kMiscDict + 1);
   }
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, misc + kMiscDict, 8, cudaMemcpyDeviceToHost, s));
+  if (!capturing(c))  // read in dictionary_finish (a captured call takes it from its tape there)
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, misc + kMiscDict, 8, cudaMemcpyDeviceToHost, s));
   return APO_OK;
 }
 
 int dictionary_finish(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tbits, DictCodes *d,
                       uint32_t **codes_out, int *cb_out, cudaStream_t s) {
   *codes_out = nullptr;
-  const uint32_t sigma = c->host_pinned[2];
-  if (!d->ok || c->host_pinned[3] || sigma > d->cap / 2) return APO_OK;
   uint32_t *misc = c->ps.counters + kCtrMisc;
+  if (!d->ok) return APO_OK;
+  uint32_t sv[2];  // distinct tokens, overflow flag
+  if (capturing(c)) {
+    APO_TRY(tape_take(c, misc + kMiscDict, sv, 2, s));
+  } else {
+    sv[0] = c->host_pinned[2];
+    sv[1] = c->host_pinned[3];
+    if (recording(c)) tape_put(c, sv, 2);
+  }
+  const uint32_t sigma = sv[0];
+  if (sv[1] || sigma > d->cap / 2) return APO_OK;
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscDict, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKSaDict, d->cap, s);
@@ -534,8 +544,13 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   if (dict_early) APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
   uint64_t orv = 0, maxv = 0;
   // (pinned words 8..11: words 2..3 may be receiving the dictionary's size)
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 8, kor, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  if (capturing(c)) {
+    APO_TRY(tape_take(c, reinterpret_cast<const uint32_t *>(kor), c->host_pinned + 8, 4, s));
+  } else {
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 8, kor, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (recording(c)) tape_put(c, c->host_pinned + 8, 4);
+  }
   memcpy(&orv, c->host_pinned + 8, sizeof(uint64_t));
   memcpy(&maxv, c->host_pinned + 10, sizeof(uint64_t));
 
@@ -551,7 +566,7 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     int cb_dict = 0;
     if (!dict_early) {
       APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
-      APO_CUDA_TRY(cudaStreamSynchronize(s));
+      if (!capturing(c)) APO_CUDA_TRY(cudaStreamSynchronize(s));
     }
     APO_TRY(dictionary_finish(c, tokens, tb, n, tbits, &dict, &code_arr, &cb_dict, s));
     if (code_arr && (uint32_t)((64 - wb) / cb_dict) > h0) {
@@ -635,18 +650,38 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[st.levels], st.rank, (size_t)n * 4,
                                  cudaMemcpyDeviceToDevice, s));
     ++st.levels;
-    if (r == 0)  // round 0's input count, also unknown on the host so far
-      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 6, in, 4, cudaMemcpyDeviceToHost, s));
-    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 4 + (r & 1), out, 4, cudaMemcpyDeviceToHost, s));
-    APO_CUDA_TRY(cudaEventRecord(c->round_ev[r & 1], s));
+    const bool cap = capturing(c);
+    if (!cap) {
+      if (r == 0)  // round 0's input count, also unknown on the host so far
+        APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 6, in, 4, cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 4 + (r & 1), out, 4, cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaEventRecord(c->round_ev[r & 1], s));
+    }
     if (r > 0) {
-      APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
-      if (r == 1 && c->host_pinned[6] == 0) {  // the first sort left no group: rounds 0 and 1 idle
-        st.levels -= 2;
-        rounds = 0;
-        break;
+      // (a captured call takes the counts from its tape, checked against the
+      // device words -- still unchanged at this point of the stream)
+      uint32_t first = 0, a = 0;
+      if (r == 1) {
+        if (cap) {
+          APO_TRY(tape_take(c, misc + kMiscRefreshCount, &first, 1, s));
+        } else {
+          APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
+          first = c->host_pinned[6];
+          if (recording(c)) tape_put(c, &first, 1);
+        }
+        if (first == 0) {  // the first sort left no group: rounds 0 and 1 idle
+          st.levels -= 2;
+          rounds = 0;
+          break;
+        }
       }
-      const uint32_t a = c->host_pinned[4 + ((r - 1) & 1)];  // round r's input count
+      if (cap) {
+        APO_TRY(tape_take(c, rc + ((r - 1) & 1), &a, 1, s));
+      } else {
+        if (r > 1) APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
+        a = c->host_pinned[4 + ((r - 1) & 1)];  // round r's input count
+        if (recording(c)) tape_put(c, &a, 1);
+      }
       if (a == 0) {  // round r had nothing to do
         --st.levels;
         break;

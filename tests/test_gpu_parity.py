@@ -673,3 +673,48 @@ def test_optimum_limits(apo):
         apo.optimum_batched(t[:20], [0, 20], 1)
     with pytest.raises(ApoError):
         apo.optimum_batched(t[:4], [0, 4], 0)
+
+
+# ---------------------------------------------------------------- graph mode
+def test_graph_mode_results_equal_eager(apo):
+    """Batched calls replayed as CUDA graphs give the same bytes as the plain
+    path: on a repeated batch (the replay is valid), on a batch of the same
+    shape whose contents changed (the replay's checks fail and the call runs
+    as usual), and back on the first batch."""
+    import torch
+    from paper_2406_18111_gb300 import Apo, as_u32
+    toks, off, _ = W.config3_windows(48, 1024, 16384, seed0=31)
+    other = toks.copy()
+    rng = np.random.default_rng(3)
+    pos = rng.integers(0, len(other), size=len(other) // 50)
+    other[pos] = rng.integers(0, 1000, size=len(pos)).astype(np.uint32)
+    names = ("sa", "lcp", "cand_len", "cand_id", "cand_start", "sel_start", "sel_len", "sel_trace",
+             "trace_len", "trace_start")
+
+    def snap(r):
+        d = {k: as_u32(getattr(r, k)).copy() for k in names}
+        d["acc"] = r.cand_accepted.cpu().numpy().copy()
+        d["rounds"] = r.rounds
+        for k in ("cand_off", "sel_off", "trace_off"):
+            d[k] = np.asarray(getattr(r, k)).copy()
+        return d
+
+    want = {}
+    for name, t in (("a", toks), ("b", other)):
+        want[name] = snap(apo.find_repeats_batched(dev(t, np.int32), off, 5))
+    g = Apo(0)
+    try:
+        g.graph_mode(True)
+        buf = torch.empty(len(toks), dtype=torch.int32, device="cuda")
+        for name in ("a", "a", "a", "b", "b", "a"):
+            buf.copy_(torch.from_numpy((toks if name == "a" else other).view(np.int32)))
+            got = snap(g.find_repeats_batched(buf, off, 5, reuse=True))
+            for k, v in want[name].items():
+                assert np.array_equal(np.asarray(got[k]), np.asarray(v)), (name, k)
+        st = g.graph_stats()
+        # a: captured, replayed twice; b: the replay discarded, recaptured,
+        # replayed; a again: discarded (the graph is b's), recaptured
+        assert st["replays"] >= 3 and st["captures"] >= 2 and st["discarded"] >= 1, st
+        g.graph_mode(False)
+    finally:
+        g.close()
