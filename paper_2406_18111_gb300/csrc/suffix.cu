@@ -397,19 +397,6 @@ int refresh_launch(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32
   return APO_OK;
 }
 
-// Refresh with the count read back at once (the first rounds).
-int refresh(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *actpos,
-            int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next, uint32_t *pos_next, uint32_t n,
-            uint32_t *count_host, cudaStream_t s) {
-  uint32_t *cnt = c->ps.counters + kCtrMisc + kMiscRefreshCount;
-  APO_TRY(refresh_launch(c, keys, idx, A, nullptr, actpos, old_sh, sa, rank, act_next, pos_next, n, cnt, s));
-  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
-  *count_host = c->host_pinned[0];
-  return APO_OK;
-}
-
 uint64_t dict_capacity(uint32_t n) {
   uint64_t cap = 1;
   while (cap < 2ull * n && cap < (1ull << kDictMaxLog)) cap <<= 1;
