@@ -118,6 +118,104 @@ __global__ void k_piece_write(const uint32_t *__restrict__ start, const uint32_t
   }
 }
 
+// ---------------------------------------------------------------- equal pieces
+// Equal strings (the same trace found by several analyses) are matched once:
+// pieces are sorted by a hash of their string, each piece is compared with
+// the first piece of its hash run, and equal ones merge into it, keeping the
+// smallest piece number and the earliest ingestion (all that need() and the
+// reported trace number use).  A piece that differs from its run's first
+// (a hash collision) stays on its own; equal strings left apart that way are
+// still told apart later (k_need's runs).
+__device__ __forceinline__ uint64_t mix_rp(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_piece_hash(const T *__restrict__ tok, const uint32_t *__restrict__ pstart,
+                             const uint32_t *__restrict__ plen, uint32_t Q, uint64_t *__restrict__ keys,
+                             uint32_t *__restrict__ vals) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; q < Q; q += warps) {
+    const uint32_t a = pstart[q], L = plen[q];
+    uint64_t h = 0;
+    for (uint32_t k = lane; k < L; k += 32) h += mix_rp((uint64_t)tok[a + k] * 0x9e3779b97f4a7c15ull + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) {
+      keys[q] = mix_rp(h ^ ((uint64_t)L << 40)) >> 24;  // 40 bits
+      vals[q] = (uint32_t)q;
+    }
+  }
+}
+
+// One warp per sorted position: rep[piece] = the run's first piece if the
+// strings are equal, else the piece itself; the representative keeps the
+// smallest piece number and ingestion task of its members.
+template <class T>
+__global__ void k_piece_dups(const T *__restrict__ tok, const uint32_t *__restrict__ pstart,
+                             const uint32_t *__restrict__ plen, const uint32_t *__restrict__ ptau,
+                             const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t Q,
+                             uint32_t *__restrict__ rep, uint32_t *tau_min, uint32_t *pid_min) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t j = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; j < Q; j += warps) {
+    const uint64_t key = keys[j];
+    uint32_t lo = 0, hi = (uint32_t)j;  // the run's first position
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (keys[mid] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    const uint32_t a = vals[j], b = vals[lo];
+    bool same = plen[a] == plen[b];
+    if (same && a != b) {
+      const uint32_t L = plen[a], sa = pstart[a], sb = pstart[b];
+      for (uint32_t k0 = 0; k0 < L && same; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        same = __all_sync(0xffffffffu, k >= L || tok[sa + k] == tok[sb + k]);
+      }
+    }
+    if (lane == 0) {
+      const uint32_t r = same ? b : a;
+      rep[a] = r;
+      atomicMin(&tau_min[r], ptau[a]);
+      atomicMin(&pid_min[r], a);
+    }
+  }
+}
+
+struct SrcIsRep {
+  const uint32_t *rep;
+  __device__ __forceinline__ uint32_t operator()(uint32_t k) const { return rep[k] == k ? 1u : 0u; }
+};
+struct DstRepOffset {
+  const uint32_t *rep;
+  uint32_t *out;
+  uint32_t n;
+  __device__ __forceinline__ void operator()(uint32_t k, uint32_t s) const {
+    out[k] = s - (rep[k] == k ? 1u : 0u);
+    if (k == n - 1) out[n] = s;
+  }
+};
+
+__global__ void k_unique_write(const uint32_t *__restrict__ rep, const uint32_t *__restrict__ uoff, uint32_t Q,
+                               const uint32_t *__restrict__ pstart, const uint32_t *__restrict__ plen,
+                               const uint32_t *__restrict__ tau_min, const uint32_t *__restrict__ pid_min,
+                               uint32_t *__restrict__ ust, uint32_t *__restrict__ uln, uint32_t *__restrict__ uta,
+                               uint32_t *__restrict__ upi) {
+  RP_FOR(q, Q) {
+    if (rep[q] != q) continue;
+    const uint32_t i = uoff[q];
+    ust[i] = pstart[q];
+    uln[i] = plen[q];
+    uta[i] = tau_min[q];
+    upi[i] = pid_min[q];
+  }
+}
+
 // ---------------------------------------------------------------- need(t)
 // Sparse tables of minima over windows ending at j (clipped at 0): level 0
 // is slcp (the lcp with the previous piece in string order) and the
@@ -174,11 +272,11 @@ __device__ __forceinline__ uint32_t right_bound(const Tables &T, uint32_t hi, ui
 }
 
 // One thread per string position; the first position of each run of equal
-// pieces handles the run: its smallest piece id becomes the canonical id of
-// every piece in it, and the canonical piece gets need().
+// strings handles the run: its entry with the smallest piece number becomes
+// the canonical one of every entry in it, and gets need().
 __global__ void k_need(Tables T, const uint32_t *__restrict__ sp, const uint32_t *__restrict__ plen,
-                       const uint32_t *__restrict__ tau_sorted, uint32_t *__restrict__ canon,
-                       uint32_t *__restrict__ need) {
+                       const uint32_t *__restrict__ upid, const uint32_t *__restrict__ tau_sorted,
+                       uint32_t *__restrict__ canon, uint32_t *__restrict__ need) {
   const uint32_t Q = T.Q;
   const uint32_t *slcp = T.lcp[0];
   RP_FOR(h64, Q) {
@@ -188,7 +286,7 @@ __global__ void k_need(Tables T, const uint32_t *__restrict__ sp, const uint32_t
     uint32_t r = h, cmin = sp[h], tb = tau_sorted[h];
     while (r + 1 < Q && slcp[r + 1] >= L && plen[sp[r + 1]] == L) {
       ++r;
-      cmin = min(cmin, sp[r]);
+      if (upid[sp[r]] < upid[cmin]) cmin = sp[r];  // the entry with the smallest piece number
       tb = min(tb, tau_sorted[r]);
     }
     for (uint32_t j = h; j <= r; ++j) canon[sp[j]] = cmin;
@@ -471,7 +569,8 @@ __global__ void __launch_bounds__(kSelectThreads)
 // ---------------------------------------------------------------- outputs
 // One warp per replay: the replay record, the traced tasks, the traced total.
 __global__ void k_replay_out(uint32_t R, const uint32_t *__restrict__ chain, const uint32_t *__restrict__ winner,
-                             const uint32_t *__restrict__ plen, uint32_t *rep_end, uint32_t *rep_len,
+                             const uint32_t *__restrict__ plen, const uint32_t *__restrict__ upid,
+                             uint32_t *rep_end, uint32_t *rep_len,
                              uint32_t *rep_trace, uint64_t rcap, uint8_t *traced,
                              unsigned long long *traced_total, uint32_t *err) {
   const uint32_t lane = threadIdx.x & 31;
@@ -487,7 +586,7 @@ __global__ void k_replay_out(uint32_t R, const uint32_t *__restrict__ chain, con
       if (r < rcap) {
         rep_end[r] = e;
         rep_len[r] = L;
-        rep_trace[r] = w;
+        rep_trace[r] = upid[w];
       }
       atomicAdd(traced_total, (unsigned long long)L);
     }
@@ -537,6 +636,8 @@ struct Carve {
 
 struct Ws1 {
   uint32_t *pstart, *plen, *ptau, *sp, *slcp, *tau_sorted, *lev, *canon, *need, *first_dec, *fu;
+  uint64_t *hk0, *hk1;
+  uint32_t *hv0, *hv1, *rep, *tmin, *pmin, *uoff, *ust, *uln, *uta, *upi;
   uint32_t *ms1, *pm, *first, *J, *la, *lb, *acnt, *aoff, *winner, *und, *wcur, *wnew, *pre, *small;
   uint8_t *traced;
 };
@@ -554,6 +655,18 @@ Ws1 carve1(Carve &cv, uint64_t n, uint32_t Q, int nlev, int K) {
   w.need = cv.take<uint32_t>(Q);
   w.first_dec = cv.take<uint32_t>(Q);
   w.fu = cv.take<uint32_t>(Q);
+  w.hk0 = cv.take<uint64_t>(Q);
+  w.hk1 = cv.take<uint64_t>(Q);
+  w.hv0 = cv.take<uint32_t>(Q);
+  w.hv1 = cv.take<uint32_t>(Q);
+  w.rep = cv.take<uint32_t>(Q);
+  w.tmin = cv.take<uint32_t>(Q);
+  w.pmin = cv.take<uint32_t>(Q);
+  w.uoff = cv.take<uint32_t>((size_t)Q + 1);
+  w.ust = cv.take<uint32_t>(Q);
+  w.uln = cv.take<uint32_t>(Q);
+  w.uta = cv.take<uint32_t>(Q);
+  w.upi = cv.take<uint32_t>(Q);
   w.ms1 = cv.take<uint32_t>(n + 1);
   w.pm = cv.take<uint32_t>(n + 1);
   w.first = cv.take<uint32_t>(n + 1);
@@ -655,14 +768,57 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
   }
   APO_CUDA_TRY(cudaGetLastError());
 
-  // occurrences of the pieces, and the pieces in string order
+  // one entry per distinct string
+  {
+    const int hb = grid_for((uint64_t)Q * 32, 256, sms);
+    Launch lp_(c, kKRpPieces, Q, s);
+    if (tb == 4)
+      k_piece_hash<<<hb, 256, 0, s>>>(static_cast<const uint32_t *>(tokens), w.pstart, w.plen, Q, w.hk0, w.hv0);
+    else
+      k_piece_hash<<<hb, 256, 0, s>>>(static_cast<const uint64_t *>(tokens), w.pstart, w.plen, Q, w.hk0, w.hv0);
+  }
+  SortBuffers hb;
+  hb.keys[0] = w.hk0;
+  hb.keys[1] = w.hk1;
+  hb.vals[0] = w.hv0;
+  hb.vals[1] = w.hv1;
+  hb.cur = 0;
+  {
+    const DigitRange hr{0, 40, false};
+    APO_TRY(radix_sort_pairs(c, hb, Q, &hr, 1, s));
+  }
+  APO_CUDA_TRY(cudaMemsetAsync(w.tmin, 0xff, (size_t)Q * 4, s));
+  APO_CUDA_TRY(cudaMemsetAsync(w.pmin, 0xff, (size_t)Q * 4, s));
+  {
+    const int db = grid_for((uint64_t)Q * 32, 256, sms);
+    Launch lp_(c, kKRpPieces, Q, s);
+    if (tb == 4)
+      k_piece_dups<<<db, 256, 0, s>>>(static_cast<const uint32_t *>(tokens), w.pstart, w.plen, w.ptau,
+                                      hb.keys[hb.cur], hb.vals[hb.cur], Q, w.rep, w.tmin, w.pmin);
+    else
+      k_piece_dups<<<db, 256, 0, s>>>(static_cast<const uint64_t *>(tokens), w.pstart, w.plen, w.ptau,
+                                      hb.keys[hb.cur], hb.vals[hb.cur], Q, w.rep, w.tmin, w.pmin);
+  }
+  APO_TRY(seg_scan<false>(c, SrcIsRep{w.rep}, DstRepOffset{w.rep, w.uoff, Q}, Q, OpSum(), 0u, s));
+  {
+    Launch lp_(c, kKRpPieces, Q, s);
+    k_unique_write<<<grid_for(Q, 256, sms), 256, 0, s>>>(w.rep, w.uoff, Q, w.pstart, w.plen, w.tmin, w.pmin, w.ust,
+                                                         w.uln, w.uta, w.upi);
+  }
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, w.uoff + Q, 4, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaStreamSynchronize(s));
+  const uint32_t Qd = c->host_pinned[0];  // distinct strings (entries from here on)
+  const uint32_t *plen = w.uln, *ptau = w.uta, *upid = w.upi;
+  const int nlevd = std::max(1, bits_for(Qd));
+
+  // occurrences of the entries, and the entries in string order
   apo_patterns pp;
   memset(&pp, 0, sizeof(pp));
-  pp.n_patterns = Q;
+  pp.n_patterns = Qd;
   pp.tokens = tokens;
   pp.token_bytes = tb;
-  pp.pat_start = w.pstart;
-  pp.pat_len = w.plen;
+  pp.pat_start = w.ust;
+  pp.pat_len = w.uln;
   uint64_t cap = std::max<uint64_t>(c->rp_cap, std::max<uint64_t>(1 << 20, n));
   uint64_t O = 0;
   Ws2 v;
@@ -690,31 +846,32 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
 
   // need(t) and canonical piece ids
   Tables T;
-  T.nlev = nlev;
-  T.Q = Q;
+  T.nlev = nlevd;
+  T.Q = Qd;
   T.lcp[0] = w.slcp;
   T.tau[0] = w.tau_sorted;
   {
-    Launch lp_(c, kKRpNeed, Q, s);
-    k_tables0<<<grid_for(Q, 256, sms), 256, 0, s>>>(w.sp, w.ptau, Q, w.tau_sorted);
+    Launch lp_(c, kKRpNeed, Qd, s);
+    k_tables0<<<grid_for(Qd, 256, sms), 256, 0, s>>>(w.sp, ptau, Qd, w.tau_sorted);
   }
-  for (int l = 1; l < nlev; ++l) {
-    uint32_t *lb = w.lev + (size_t)(2 * (l - 1)) * Q, *tbv = lb + Q;
-    Launch lp_(c, kKRpNeed, Q, s);
-    k_tables_level<<<grid_for(Q, 256, sms), 256, 0, s>>>(T.lcp[l - 1], T.tau[l - 1], Q, 1u << (l - 1), lb, tbv);
+  for (int l = 1; l < nlevd; ++l) {
+    uint32_t *lb = w.lev + (size_t)(2 * (l - 1)) * Qd, *tbv = lb + Qd;
+    Launch lp_(c, kKRpNeed, Qd, s);
+    k_tables_level<<<grid_for(Qd, 256, sms), 256, 0, s>>>(T.lcp[l - 1], T.tau[l - 1], Qd, 1u << (l - 1), lb,
+                                                             tbv);
     T.lcp[l] = lb;
     T.tau[l] = tbv;
   }
   {
-    Launch lp_(c, kKRpNeed, Q, s);
-    k_need<<<grid_for(Q, 128, sms), 128, 0, s>>>(T, w.sp, w.plen, w.tau_sorted, w.canon, w.need);
+    Launch lp_(c, kKRpNeed, Qd, s);
+    k_need<<<grid_for(Qd, 128, sms), 128, 0, s>>>(T, w.sp, plen, upid, w.tau_sorted, w.canon, w.need);
   }
 
   // replay ends
   APO_CUDA_TRY(cudaMemsetAsync(w.ms1, 0, n * 4, s));
   if (O32) {
     Launch lp_(c, kKRpChain, O32, s);
-    k_valid_ends<<<grid_for(O32, 256, sms), 256, 0, s>>>(v.oend, v.oid, O32, w.canon, w.need, w.plen, w.ms1,
+    k_valid_ends<<<grid_for(O32, 256, sms), 256, 0, s>>>(v.oend, v.oid, O32, w.canon, w.need, plen, w.ms1,
                                                          w.first);
   }
   APO_TRY(seg_scan<false>(c, SrcU32{w.ms1}, DstU32{w.pm}, nn, OpMax(), 0u, s));
@@ -757,14 +914,14 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
     {
       Launch lp_(c, kKRpAppear, R, s);
       k_appear<false><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, w.first, v.oend, v.oid, O32, w.canon, w.need,
-                                                            w.plen,
+                                                            plen,
                                                             w.acnt, nullptr, nullptr, nullptr);
     }
     APO_TRY(seg_scan<false>(c, SrcU32{w.acnt}, DstExclusive{w.acnt, w.aoff, R}, R, OpSum(), 0u, s));
     {
       Launch lp_(c, kKRpAppear, R, s);
       k_appear<true><<<grid_for(R, 128, sms), 128, 0, s>>>(chain, R, w.first, v.oend, v.oid, O32, w.canon, w.need,
-                                                           w.plen,
+                                                           plen,
                                                            nullptr, w.aoff, v.app_t, v.app_r);
     }
     // count and previous appearance per trace: stable sort by trace
@@ -779,30 +936,30 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
     b.vals[0] = v.vals0;
     b.vals[1] = v.vals1;
     b.cur = 0;
-    const DigitRange rg{0, std::max(1, bits_for(Q - 1)), false};
+    const DigitRange rg{0, std::max(1, bits_for(Qd - 1)), false};
     APO_TRY(radix_sort_pairs(c, b, O32, &rg, 1, s, A_dev));
     {
       Launch lp_(c, kKRpAppear, O32, s);
       k_app_score<<<grid_for(O32, 256, sms), 256, 0, s>>>(b.keys[b.cur], b.vals[b.cur], A_dev, v.app_r, chain,
-                                                          w.plen, sp, v.app_x, v.app_sh);
+                                                          plen, sp, v.app_x, v.app_sh);
     }
     // selection
-    APO_CUDA_TRY(cudaMemsetAsync(w.first_dec, 0xff, (size_t)Q * 4, s));
-    APO_CUDA_TRY(cudaMemsetAsync(w.fu, 0xff, (size_t)Q * 4, s));
+    APO_CUDA_TRY(cudaMemsetAsync(w.first_dec, 0xff, (size_t)Qd * 4, s));
+    APO_CUDA_TRY(cudaMemsetAsync(w.fu, 0xff, (size_t)Qd * 4, s));
     {
       Launch lp_(c, kKRpSelect, R, s);
-      k_decide<<<grid_for(R, 128, sms), 128, 0, s>>>(R, w.aoff, v.app_t, v.app_x, v.app_sh, w.plen, sp, w.winner,
+      k_decide<<<grid_for(R, 128, sms), 128, 0, s>>>(R, w.aoff, v.app_t, v.app_x, v.app_sh, plen, sp, w.winner,
                                                      w.first_dec, w.und, w.small + kSmUcnt);
     }
     {
       Launch lp_(c, kKRpSelect, R, s);
-      k_select<<<1, kSelectThreads, 0, s>>>(w.und, w.small + kSmUcnt, w.aoff, v.app_t, v.app_x, v.app_sh, w.plen,
+      k_select<<<1, kSelectThreads, 0, s>>>(w.und, w.small + kSmUcnt, w.aoff, v.app_t, v.app_x, v.app_sh, plen,
                                             w.first_dec, w.fu, w.wcur, w.wnew, sp, w.winner, w.small + kSmRounds,
                                             c->ps.err);
     }
     {
       Launch lp_(c, kKRpOut, R, s);
-      k_replay_out<<<grid_for((uint64_t)R * 32, 256, sms), 256, 0, s>>>(R, chain, w.winner, w.plen, out->rep_end,
+      k_replay_out<<<grid_for((uint64_t)R * 32, 256, sms), 256, 0, s>>>(R, chain, w.winner, plen, upid, out->rep_end,
                                                                         out->rep_len, out->rep_trace, out->rep_cap,
                                                                         traced, traced_total, c->ps.err);
     }
