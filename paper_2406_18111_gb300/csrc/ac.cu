@@ -950,11 +950,6 @@ __global__ void k_ac_fill(const uint32_t *__restrict__ state, uint32_t n, const 
   }
 }
 
-inline int grid_for(uint64_t n, int threads, int sms) {
-  long long b = (long long)((n + threads - 1) / threads);
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
-}
-
 }  // namespace
 
 int match_init(int sms) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -241,6 +242,12 @@ constexpr int kPinnedErr = 15;
 int device_error_status(apo_ctx *c, cudaStream_t s);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+// Blocks for a grid-stride loop over n elements: enough for one element per
+// thread, at most 16 blocks per SM.
+inline int grid_for(uint64_t n, int threads, int sms) {
+  long long b = (long long)((n + threads - 1) / threads);
+  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
+}
 inline int bits_for(uint64_t v) {  // number of bits to represent values 0..v
   int b = 0;
   while (b < 64 && (v >> b) != 0) ++b;

@@ -504,11 +504,6 @@ __global__ void k_relativize(uint32_t *__restrict__ start, uint32_t *__restrict_
 
 int g_greedy_smem_max = 0;  // dynamic shared memory available to k_greedy<*, true>
 
-inline int grid_for(uint64_t n, int threads, int sms) {
-  long long b = (long long)((n + threads - 1) / threads);
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
-}
-
 // A device count and the error word in one synchronisation (a captured call
 // takes both from its tape).
 int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {

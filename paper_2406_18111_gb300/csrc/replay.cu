@@ -60,11 +60,6 @@ namespace {
 constexpr uint32_t kNone = 0xffffffffu;
 constexpr int kSelectThreads = 1024;
 
-inline int grid_for(uint64_t n, int threads, int sms) {
-  long long b = (long long)((n + threads - 1) / threads);
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
-}
-
 #define RP_FOR(i, n) \
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); i += (uint64_t)gridDim.x * blockDim.x)
 

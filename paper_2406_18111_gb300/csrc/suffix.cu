@@ -370,11 +370,6 @@ __global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__re
     lcp[k] = (k + 1 < n && win_id(W, sa[k + 1]) == win_id(W, sa[k])) ? plcp[sa[k + 1]] : 0u;
 }
 
-inline int grid_for(uint64_t n, int threads, int sms) {
-  long long b = (long long)((n + threads - 1) / threads);
-  return (int)std::max<long long>(1, std::min<long long>(b, (long long)sms * 16));
-}
-
 // Launches the refresh of the (at most A, exactly *A_dev when given) sorted
 // active suffixes; the number still active lands in *count_dev (zeroed
 // first, so a launch with nothing to do leaves 0).
