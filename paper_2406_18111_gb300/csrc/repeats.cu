@@ -737,7 +737,9 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
       // Phases: the one block settles a prefix of the list; then every
       // remaining candidate with a marked end is dropped by the whole GPU
       // and the survivors form the next list.  Long candidates come first,
-      // so a short prefix marks most of the window.
+      // so a short prefix marks most of the window; each prefix is twice the
+      // last (a drop costs far less than the block's rounds over candidates
+      // that a drop would have removed).
       if (smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
       const uint32_t *pl = cl, *ps = cs, *po = nullptr;
       uint32_t len = m, prefix = kGreedyFirstPhase;
@@ -770,7 +772,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
         ps = s2;
         po = o2;
         len = kept;
-        prefix *= 4;
+        prefix *= 2;
       }
     } else {
       Launch lp_(c, kKGreedy, m, s);
