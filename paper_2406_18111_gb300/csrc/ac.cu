@@ -853,7 +853,7 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
   }
 }
 
-// Pass A2 (repeated until nothing changes), one warp per group of kGroup
+// Pass A2 (repeated until nothing changes), one warp per group of `group`
 // consecutive first-pass chunks: the group restarts from the state stored at
 // its predecessor's last position, and each of its chunks re-runs until its
 // state equals the stored one (the rest of that chunk was stored by a
@@ -862,14 +862,13 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
 // is still rewriting it; then the predecessor's end state changes in this
 // pass and the host runs another.  When no group's end state changes, every
 // group continues its predecessor exactly and all states are exact.
-constexpr int kGroup = 4;
 __global__ void __launch_bounds__(32 * kStateWarps)
-    k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, Automaton A,
+    k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, uint32_t group, Automaton A,
              uint32_t *__restrict__ state, uint32_t *changed) {
   const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t g0 = t * chunk * kGroup;
+  const uint64_t g0 = t * chunk * group;
   if (g0 >= n) return;
-  const uint64_t ce = min(n, g0 + chunk * kGroup);
+  const uint64_t ce = min(n, g0 + chunk * group);
   const uint64_t cs = g0 == 0 ? chunk : g0;  // the first chunk of all is exact
   if (cs >= ce) return;
   const uint32_t rec_end = state[ce - 1];
@@ -1327,7 +1326,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   // exact states one group of chunks further
   const uint64_t chunk = std::max<uint64_t>(64, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
   const uint64_t nch = (n + chunk - 1) / chunk;
-  const uint64_t nch2 = (nch + kGroup - 1) / kGroup;
+  // chunks per repair warp: longer groups settle in fewer passes, shorter
+  // ones keep more warps busy on a short stream
+  const uint32_t group = n >= (1ull << 22) ? 8u : 4u;
+  const uint64_t nch2 = (nch + group - 1) / group;
   if (!state || !off) return APO_ENOMEM;
   {
     Launch lp_(c, kKAcStates, n, s);
@@ -1337,7 +1339,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     {
       Launch lp_(c, kKAcFix, n, s);
-      k_ac_fix<<<ceil_div(nch2, kStateWarps), 32 * kStateWarps, 0, s>>>(ssym, n, chunk, A, state,
+      k_ac_fix<<<ceil_div(nch2, kStateWarps), 32 * kStateWarps, 0, s>>>(ssym, n, chunk, group, A, state,
                                                                           misc + kMiscAccCount);
     }
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
