@@ -919,11 +919,14 @@ __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restric
   __syncthreads();
   uint32_t r = s_pre + ex;
 #pragma unroll
-  for (int i = 0; i < kSI; ++i) {
-    const uint64_t x = base + (uint64_t)tid * kSI + i;
-    if (x < n) off[x] = r;
-    r += sv[tid * kSI + i];
+  for (int i = 0; i < kSI; ++i) {  // exclusive offsets back into the tile, then written coalesced
+    const uint32_t v = sv[tid * kSI + i];
+    sv[tid * kSI + i] = r;
+    r += v;
   }
+  __syncthreads();
+  for (int q = tid; q < kSTile; q += kST)
+    if (base + q < n) off[base + q] = sv[q];
 }
 
 // Pass B: the matches of position x, down the output chain from its state
