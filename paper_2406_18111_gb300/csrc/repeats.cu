@@ -175,7 +175,7 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
 
 // ---------------------------------------------------------------- greedy
 constexpr int kGI = 4;  // candidates per thread per round
-constexpr uint32_t kGreedyFirstPhase = 1u << 15;  // candidates settled before the first drop
+constexpr uint32_t kGreedyFirstPhase = 1u << 16;  // candidates settled before the first drop
 constexpr int glist_bytes(int threads) { return threads * kGI * 16; }
 
 template <bool kSmem>
