@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
   acc += cb;
   m = ce - cb;
   uint32_t *sl = gsm + words, *ss = sl + kGRound, *sk = ss + kGRound, *sov = sk + kGRound;
-  __shared__ uint32_t s_cnt[kGI][32], s_off[kGI][32], s_total;
+  __shared__ uint32_t s_cnt[2][kGI][32];  // survivors per (item, warp), by round parity
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (kSmem)
     for (uint32_t x = tid; x < words; x += kGT) gsm[x] = persist ? gbits[x] : 0u;
@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
     ns[i] = k < m ? cs[k] : 0u;
   }
   __syncthreads();
-  for (uint32_t base = 0; base < m; base += kGRound) {
+  uint32_t par = 0;
+  for (uint32_t base = 0; base < m; base += kGRound, par ^= 1u) {
     uint32_t l[kGI], s[kGI], bal[kGI];
     bool surv[kGI];
 #pragma unroll
@@ -263,26 +264,27 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
         }
       }
       bal[i] = __ballot_sync(0xffffffffu, surv[i]);
-      if (lane == 0) s_cnt[i][warp] = __popc(bal[i]);
+      if (lane == 0) s_cnt[par][i][warp] = __popc(bal[i]);
     }
     __syncthreads();
-    if (warp == 0) {  // survivor offsets in (item, warp) order = candidate order
-      uint32_t carry = 0;
+    // Survivor offsets in (item, warp) order = candidate order, scanned by
+    // every warp for itself.  The counts are double-buffered by round
+    // parity: a round without survivors skips the barriers below, and a
+    // warp may write the next round's counts while another still reads these.
+    uint32_t off[kGI], s_total = 0;
 #pragma unroll
-      for (int i = 0; i < kGI; ++i) {
-        const uint32_t c = lane < kGT / 32 ? s_cnt[i][lane] : 0u;
-        const uint32_t inc = warp_inclusive(c, OpSum());
-        s_off[i][lane] = carry + inc - c;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-      }
-      if (lane == 0) s_total = carry;
+    for (int i = 0; i < kGI; ++i) {
+      const uint32_t c = lane < kGT / 32 ? s_cnt[par][i][lane] : 0u;
+      const uint32_t inc = warp_inclusive(c, OpSum());
+      off[i] = s_total + __shfl_sync(0xffffffffu, inc - c, warp);
+      s_total += __shfl_sync(0xffffffffu, inc, 31);
     }
-    __syncthreads();
+    if (s_total == 0) continue;  // the same in every warp; no mark changes
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kGI; ++i) {
       if (surv[i]) {
-        const uint32_t q = s_off[i][warp] + __popc(bal[i] & lt);
+        const uint32_t q = off[i] + __popc(bal[i] & lt);
         sl[q] = l[i];
         ss[q] = s[i];
         sk[q] = corig ? corig[base + i * kGT + tid] : base + i * kGT + tid;
