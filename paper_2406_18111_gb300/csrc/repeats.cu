@@ -229,26 +229,29 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
   if (kSmem)
     for (uint32_t x = tid; x < words; x += kGT) gsm[x] = persist ? gbits[x] : 0u;
   uint32_t nacc = 0;
-  uint32_t nl[kGI], ns[kGI];
+  uint32_t nl[kGI], ns[kGI], no[kGI];  // the next round's candidates, loaded a round ahead
 #pragma unroll
   for (int i = 0; i < kGI; ++i) {
     const uint32_t k = i * kGT + tid;
     nl[i] = k < m ? cl[k] : 0u;
     ns[i] = k < m ? cs[k] : 0u;
+    no[i] = corig && k < m ? corig[k] : k;
   }
   __syncthreads();
   uint32_t par = 0;
   for (uint32_t base = 0; base < m; base += kGRound, par ^= 1u) {
-    uint32_t l[kGI], s[kGI], bal[kGI];
+    uint32_t l[kGI], s[kGI], o[kGI], bal[kGI];
     bool surv[kGI];
 #pragma unroll
     for (int i = 0; i < kGI; ++i) {
       l[i] = nl[i];
       s[i] = ns[i];
+      o[i] = no[i];
       const uint64_t kn = (uint64_t)base + kGRound + i * kGT + tid;  // prefetch the next round
       if (kn < m) {
         nl[i] = cl[kn];
         ns[i] = cs[kn];
+        no[i] = corig ? corig[kn] : (uint32_t)kn;
       }
     }
 #pragma unroll
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
         const uint32_t q = off[i] + __popc(bal[i] & lt);
         sl[q] = l[i];
         ss[q] = s[i];
-        sk[q] = corig ? corig[base + i * kGT + tid] : base + i * kGT + tid;
+        sk[q] = o[i];
       }
     }
     __syncthreads();
