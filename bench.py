@@ -260,6 +260,36 @@ def cpu_baseline(n_tasks: int) -> dict:
                       f"the same structure; {len(e)} matches; {dt:.2f} s single-threaded"}
 
 
+def batched_cpu_baseline(toks, off) -> dict:
+    """The oracle, as it stands, over the batched workload's windows: every
+    host core through a thread pool over independent windows (the oracle is
+    a C library called through ctypes, which releases the GIL), and one
+    core on a prefix of the windows."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    wins = [toks[int(off[w]):int(off[w + 1])] for w in range(len(off) - 1)]
+    t0 = time.perf_counter()
+    one, k = 0, 0
+    while k < len(wins) and one < (1 << 21):
+        oracle.find_repeats(wins[k], MIN_LEN)
+        one += len(wins[k])
+        k += 1
+    dt1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda x: oracle.find_repeats(x, MIN_LEN), wins))
+    dt = time.perf_counter() - t0
+    total = int(off[-1])
+    return {"value": total / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"SA, LCP and Alg. 2 repeats of all {len(wins)} windows ({total} tokens), one window per "
+                      f"task on a pool of {cores} threads: {dt:.2f} s",
+            "one_core": {"value": one / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"the first {k} windows ({one} tokens): {dt1:.2f} s"}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -393,6 +423,8 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
             "batched_over_plain": ms_plain / ms, "graph": graph,
             "gpu_launches": n_launch, "roofline": roof, "sa_lcp_roofline": sa_lcp, "clocks": clk,
             "kernels": kernels, "sort_tuning": tuning_summary(apo)})
+    if emit and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = batched_cpu_baseline(toks, off)
     if emit and rank == 0:
         print(json.dumps(out))
     return out
