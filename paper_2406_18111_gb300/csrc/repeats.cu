@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
           atomicExch(err, kDevRange);
         } else {
           s[i] -= shift;
-          surv[i] = !marked<kSmem>(bits, s[i]) && !marked<kSmem>(bits, s[i] + l[i] - 1);
+          surv[i] = !(marked<kSmem>(bits, s[i]) | marked<kSmem>(bits, s[i] + l[i] - 1));
         }
       }
       bal[i] = __ballot_sync(0xffffffffu, surv[i]);
@@ -316,18 +316,28 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
       // accepted or undecided, and rejected once one that overlaps it is
       // accepted (the batch's greedy order, settled a few ballots at a time).
       const uint32_t total = s_total;
+      // the lane's survivor of the next batch, read one batch ahead (the
+      // survivor lists do not change during the settle; only the marks do)
+      uint32_t ps = 0, pl = 1, pov = 0, pk = 0;
+      if (lane < total) {
+        ps = ss[lane];
+        pl = sl[lane];
+        pov = sov[lane];
+        pk = sk[lane];
+      }
       for (uint32_t q0 = 0; q0 < total; q0 += 32) {
         const uint32_t q = q0 + lane;
-        uint32_t qs = 0, qe = 0;
-        bool free = false;
-        if (q < total) {
-          qs = ss[q];
-          qe = qs + sl[q] - 1;
-          free = !marked<kSmem>(bits, qs) && !marked<kSmem>(bits, qe);
+        const uint32_t qs = ps, qe = ps + pl - 1;
+        const uint32_t ov = pov, qk = pk;  // ov: earlier lanes of the batch meeting this one
+        if (q + 32 < total) {
+          ps = ss[q + 32];
+          pl = sl[q + 32];
+          pov = sov[q + 32];
+          pk = sk[q + 32];
         }
+        const bool free = q < total && !(marked<kSmem>(bits, qs) | marked<kSmem>(bits, qe));
         uint32_t und = __ballot_sync(0xffffffffu, free), accm = 0;
         if (und == 0) continue;  // every survivor of the batch met an accepted interval meanwhile
-        const uint32_t ov = q < total ? sov[q] : 0u;  // earlier lanes of the batch meeting this one
         while (und) {
           const bool mine = (und >> lane) & 1u;
           const uint32_t take = __ballot_sync(0xffffffffu, mine && (ov & (und | accm)) == 0);
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
         const bool mine = (accm >> lane) & 1u;
         bool lng = false;
         if (mine) {
-          acc[sk[q]] = 1;
+          acc[qk] = 1;
           const uint32_t w0 = qs >> 5, w1 = qe >> 5;
           if (w1 - w0 < 8) {
             for (uint32_t w = w0; w <= w1; ++w) {
