@@ -1029,8 +1029,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     }
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscMaxLen, 8, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, cnt64, 8, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaStreamSynchronize(s));
-    if (check_device_error(c, s) != APO_OK) {
+    if (device_error_status(c, s) != APO_OK) {
       set_error("match_candidates: empty pattern");
       return APO_EINVAL;
     }
@@ -1314,10 +1316,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
                                                                   firstrec, rec, c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
-  if (n == 0) {
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    return check_device_error(c, s);
-  }
+  if (n == 0) return check_device_error(c, s);  // synchronises
 
   // pass A: states, chunked without a halo, then repaired until stable
   Automaton A{tsym, g, skip, root};
@@ -1362,8 +1361,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscCompactCount, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 1, misc + kMiscTraceCount, 4, cudaMemcpyDeviceToHost, s));
+  APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
-  APO_TRY(check_device_error(c, s));
+  APO_TRY(device_error_status(c, s));
   const uint64_t total_m = c->host_pinned[0];
   *count = total_m;
   if (total_m > cap) {
@@ -1408,8 +1409,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     }
   }
   APO_CUDA_TRY(cudaGetLastError());
-  APO_CUDA_TRY(cudaStreamSynchronize(s));
-  return check_device_error(c, s);
+  return check_device_error(c, s);  // synchronises
 }
 
 }  // namespace apo

@@ -369,20 +369,10 @@ int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total,
     }
   }
   if (out->lcp) APO_CUDA_TRY(cudaMemcpyAsync(out->lcp, lcp, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  // find_repeats_from_sa ends by reading the device error word (a replay
+  // checks that it is still clear)
   const int r = find_repeats_from_sa(c, tokens, tb, st, lcp, p->min_len, out, &boff, s);
   out->counts[3] = rounds;
-  if (r == APO_OK) {
-    if (capturing(c)) {  // the error word must still be clear at the end of a replay
-      uint32_t e = 0;
-      return tape_take(c, c->ps.err, &e, 1, s);
-    }
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, s));
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    if (recording(c)) tape_put(c, c->host_pinned + kPinnedErr, 1);
-    return device_error_status(c, s);
-  }
   return r;
 }
 

@@ -648,7 +648,20 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     }
   };
   zero_offsets();
-  if (n < 2) return APO_OK;
+  // The call's last step: the device error word, read behind everything
+  // queued so far (one synchronisation), or checked against the tape.
+  auto err_check = [&]() -> int {
+    if (capturing(c)) {
+      uint32_t e = 0;
+      return tape_take(c, c->ps.err, &e, 1, s);
+    }
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (recording(c)) tape_put(c, c->host_pinned + kPinnedErr, 1);
+    return device_error_status(c, s);
+  };
+  if (n < 2) return err_check();
   uint32_t *misc = c->ps.counters + kCtrMisc;
   const int g = grid_for(n, 256, c->num_sms);
 
@@ -900,17 +913,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     if (boff->sel_off) boff->sel_off[1] = K;
     if (boff->trace_off) boff->trace_off[1] = Tn;
   }
-  if (capturing(c)) {
-    uint32_t e = 0;
-    APO_TRY(tape_take(c, c->ps.err, &e, 1, s));
-  } else {
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, s));
-    APO_CUDA_TRY(cudaStreamSynchronize(s));
-    if (recording(c)) tape_put(c, c->host_pinned + kPinnedErr, 1);
-    APO_TRY(device_error_status(c, s));
-  }
+  APO_TRY(err_check());
   counts[0] = m;
   counts[1] = K;
   counts[2] = Tn;
