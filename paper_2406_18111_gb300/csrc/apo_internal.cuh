@@ -70,6 +70,7 @@ enum : int {
   kMiscKeyOr = 16,        // two u64 (four words): OR and maximum of keys
   kMiscRound = 20,        // two words: active-suffix counts of consecutive doubling rounds
   kMiscDict = 22,         // two words: distinct tokens, dictionary overflow flag
+  kMiscPhaseLen = 24,     // two words: list lengths of consecutive greedy phases
   kMiscCount = 64,
 };
 

@@ -120,16 +120,22 @@ struct PredFlag {
 };
 
 template <class Pred>
-__global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, uint32_t *__restrict__ out,
-                                                 uint32_t *count_out, uint64_t *status,
-                                                 uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+__global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const uint32_t *m_dev, uint32_t m_sub,
+                                                 uint32_t *__restrict__ out, uint32_t *count_out,
+                                                 uint64_t *status, uint32_t *tile_ctr, uint32_t epoch,
+                                                 uint32_t *err) {
   __shared__ uint32_t s_tile, s_pre;
   __shared__ uint32_t scr[kCT / 32];
   const int tid = threadIdx.x;
+  if (m_dev) {  // the launch is sized for an upper bound; the count is *m_dev - m_sub
+    const uint32_t v = *m_dev;
+    m = min(m, v > m_sub ? v - m_sub : 0u);
+  }
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * kCTile;
+  if (t > 0 && base >= m) return;  // past the count (no earlier tile looks at it)
   const uint64_t e0 = base + (uint64_t)tid * kCI;
   uint32_t fb = 0;
 #pragma unroll
@@ -208,11 +214,12 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
                                                const uint32_t *__restrict__ woff, uint32_t n,
                                                uint32_t *gbits, uint8_t *acc, uint32_t *acc_count,
                                                const uint32_t *__restrict__ corig, int persist,
-                                               uint32_t *err) {
+                                               const uint32_t *m_dev, uint32_t *err) {
   constexpr int kGT = kT;
   constexpr int kGRound = kT * kGI;
   extern __shared__ __align__(16) uint32_t gsm[];
   const uint32_t w = blockIdx.x;
+  if (m_dev) m = min(m, *m_dev);  // single window: m bounds the list, *m_dev is its length
   const uint32_t cb = cand_off ? cand_off[w] : 0u, ce = cand_off ? cand_off[w + 1] : m;
   const uint32_t ws = woff ? woff[w] : 0u, we = woff ? woff[w + 1] : n;
   const uint32_t shift = kSmem ? ws : 0u;  // bitmap coordinate = position - shift
@@ -401,11 +408,13 @@ struct PredUnmarked {
   }
 };
 
-// New list = the kept remainder entries, in order.
-__global__ void k_list_gather(const uint32_t *__restrict__ keep, uint32_t cnt, uint32_t from,
-                              const uint32_t *__restrict__ l, const uint32_t *__restrict__ st,
+// New list = the kept remainder entries, in order (cnt: an upper bound of
+// their number, *cnt_dev the number).
+__global__ void k_list_gather(const uint32_t *__restrict__ keep, uint32_t cnt, const uint32_t *cnt_dev,
+                              uint32_t from, const uint32_t *__restrict__ l, const uint32_t *__restrict__ st,
                               const uint32_t *__restrict__ orig, uint32_t *__restrict__ l2,
                               uint32_t *__restrict__ s2, uint32_t *__restrict__ o2) {
+  cnt = min(cnt, *cnt_dev);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
     const uint32_t k = from + keep[q];
     l2[q] = l[k];
@@ -540,8 +549,11 @@ int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {
   return APO_OK;
 }
 
+// Compacts the k < m (or, with m_dev, k < min(m, *m_dev - m_sub)) for which
+// pred(k) holds into out, in order; their number lands in *count_dev.
 template <class Pred>
-int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_dev, cudaStream_t s) {
+int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_dev, cudaStream_t s,
+            const uint32_t *m_dev = nullptr, uint32_t m_sub = 0) {
   const int tiles = std::max(1, ceil_div(m, kCTile));
   APO_TRY(ensure_lookback(c, tiles));
   uint32_t *tctr = c->ps.counters + kCtrMisc + kMiscCompactTiles;
@@ -549,8 +561,8 @@ int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_de
   APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKCompact, m, s);
-    k_compact<<<tiles, kCT, 0, s>>>(pred, m, out, count_dev, c->ps.lookback, tctr, next_epoch(c),
-                                    c->ps.err);
+    k_compact<<<tiles, kCT, 0, s>>>(pred, m, m_dev, m_sub, out, count_dev, c->ps.lookback, tctr,
+                                    next_epoch(c), c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
@@ -767,39 +779,43 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
       // and the survivors form the next list.  Long candidates come first,
       // so a short prefix marks most of the window; each prefix is twice the
       // last (a drop costs far less than the block's rounds over candidates
-      // that a drop would have removed).
+      // that a drop would have removed).  The list lengths after the drops
+      // stay on the device (two alternating words): the host sizes every
+      // launch for an upper bound -- the list before its drops -- and queues
+      // phases until that bound is used up; a phase past the real end finds
+      // an empty list and returns at once.
       if (smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
       const uint32_t *pl = cl, *ps = cs, *po = nullptr;
-      uint32_t len = m, prefix = kGreedyFirstPhase;
+      const uint32_t *len_dev = nullptr;  // the current list's length (null: exactly len)
+      uint32_t len = m, prefix = kGreedyFirstPhase;  // len: an upper bound of that length
       for (int phase = 0;; ++phase) {
         const uint32_t take = std::min(prefix, len);
         {
           Launch lp_(c, kKGreedy, take, s);
           if (smem)
             k_greedy<1024, true><<<1, 1024, bm_bytes + list, s>>>(pl, ps, nullptr, take, W.off_dev, n, gbits,
-                                                                  acc, misc + kMiscAccCount, po, 1,
+                                                                  acc, misc + kMiscAccCount, po, 1, len_dev,
                                                                   c->ps.err);
           else
             k_greedy<1024, false><<<1, 1024, list, s>>>(pl, ps, nullptr, take, W.off_dev, n, gbits, acc,
-                                                         misc + kMiscAccCount, po, 0, c->ps.err);
+                                                         misc + kMiscAccCount, po, 0, len_dev, c->ps.err);
         }
         APO_CUDA_TRY(cudaGetLastError());
         if (take == len) break;
+        uint32_t *kept_dev = misc + kMiscPhaseLen + (phase & 1);
         PredUnmarked pu{pl, ps, gbits, take};
-        APO_TRY(compact(c, pu, len - take, keep, misc + kMiscCompactCount, s));
-        uint32_t kept = 0;
-        APO_TRY(read_u32(c, misc + kMiscCompactCount, &kept, s));
-        if (kept == 0) break;
+        APO_TRY(compact(c, pu, len - take, keep, kept_dev, s, len_dev, take));
         uint32_t *l2 = glist[phase & 1][0], *s2 = glist[phase & 1][1], *o2 = glist[phase & 1][2];
         {
-          Launch lp_(c, kKCandGather, kept, s);
-          k_list_gather<<<grid_for(kept, 256, c->num_sms), 256, 0, s>>>(keep, kept, take, pl, ps, po, l2, s2,
-                                                                        o2);
+          Launch lp_(c, kKCandGather, len - take, s);
+          k_list_gather<<<grid_for(len - take, 256, c->num_sms), 256, 0, s>>>(keep, len - take, kept_dev, take,
+                                                                              pl, ps, po, l2, s2, o2);
         }
         pl = l2;
         ps = s2;
         po = o2;
-        len = kept;
+        len -= take;
+        len_dev = kept_dev;
         prefix *= 2;
       }
     } else {
@@ -807,10 +823,10 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
       if (smem)
         k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n,
                                                                   nullptr, acc, misc + kMiscAccCount,
-                                                                  nullptr, 0, c->ps.err);
+                                                                  nullptr, 0, nullptr, c->ps.err);
       else
         k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
-                                                        misc + kMiscAccCount, nullptr, 0, c->ps.err);
+                                                        misc + kMiscAccCount, nullptr, 0, nullptr, c->ps.err);
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
