@@ -639,11 +639,12 @@ struct DstRecord {
 
 // Flattened output chains: record r's chain (all its matches, in report
 // order) is flat[flat_off[r] .. + rtot[r]).  rtot[r] = the match total of
-// the record's node.
-__global__ void k_rec_totals(const uint4 *__restrict__ rec, const uint32_t *__restrict__ total, uint32_t R,
-                             uint32_t *rtot) {
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
-    rtot[r] = total[rec[r].w];
+// the record's node for r < *R_dev, 0 for the rest of the P-entry bound.
+__global__ void k_rec_totals(const uint4 *__restrict__ rec, const uint32_t *__restrict__ total, uint32_t P,
+                             const uint32_t *R_dev, uint32_t *rtot) {
+  const uint32_t R = min(P, *R_dev);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x)
+    rtot[r] = r < R ? total[rec[r].w] : 0u;
 }
 
 struct SrcU32 {
@@ -864,7 +865,9 @@ __global__ void k_ac_states(const uint32_t *__restrict__ ssym, uint64_t n, uint6
 // group continues its predecessor exactly and all states are exact.
 __global__ void __launch_bounds__(32 * kStateWarps)
     k_ac_fix(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t chunk, uint32_t group, Automaton A,
-             uint32_t *__restrict__ state, uint32_t *changed) {
+             uint32_t *__restrict__ state, const uint32_t *prev_changed, uint32_t *changed) {
+  // a pass queued behind one that changed nothing has nothing to do
+  if (prev_changed && *(volatile const uint32_t *)prev_changed == 0) return;
   const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t g0 = t * chunk * group;
   if (g0 >= n) return;
@@ -978,7 +981,8 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
   // pattern text (symbols, sort tokens, pattern ids, reach) and the per-node arrays
   uint64_t bytes = N * (8 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * (16 + 8) +
-                   tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + 96 * 256;
+                   tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + 96 * 256 +
+                   P * 8;  // record totals and flattened-chain offsets
   if (src_n)  // source ranks, start lengths, both interval scans, the LCP min-tree
     bytes += src_n * 16 + (src_n / 31 + 1) * 4 + kMaxTree * 256;
   else  // the suffix array, LCP and nearest-start scans of the pattern text
@@ -1318,6 +1322,20 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   APO_CUDA_TRY(cudaGetLastError());
   if (n == 0) return check_device_error(c, s);  // synchronises
 
+  // record totals and flattened-chain offsets: they depend on the automaton
+  // only, so they are queued now over the bound P >= records, and their
+  // total is read with the match total below
+  uint32_t *rtot = c->arena.take_n<uint32_t>(P), *flat_off = c->arena.take_n<uint32_t>(P);
+  const bool flat_ok = rtot && flat_off;
+  if (flat_ok) {
+    {
+      Launch lp_(c, kKMarkEnds, P, s);
+      k_rec_totals<<<grid_for(P, 256, sms), 256, 0, s>>>(rec, mtotal, P, misc + kMiscTraceCount, rtot);
+    }
+    APO_TRY(seg_scan<false>(c, SrcU32{rtot}, DstExclusive{rtot, flat_off, misc + kMiscFlatTotal, P}, P, OpSum(),
+                            0u, s));
+  }
+
   // pass A: states, chunked without a halo, then repaired until stable
   Automaton A{tsym, g, skip, root};
   uint32_t *state = c->arena.take_n<uint32_t>(n);
@@ -1337,14 +1355,19 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     Launch lp_(c, kKAcStates, n, s);
     k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state);
   }
-  for (uint64_t pass = 0; pass < nch2; ++pass) {
-    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
-    {
+  // Repair passes two at a time: pass p counts its changes in word p & 1,
+  // and a pass after one without changes returns at once, so the host reads
+  // a count only after every second pass.
+  uint32_t *chg = misc + kMiscFixChanged;
+  for (uint64_t pass = 0; pass < nch2;) {
+    const uint64_t last = std::min<uint64_t>(pass + 2, nch2);
+    for (; pass < last; ++pass) {
+      APO_CUDA_TRY(cudaMemsetAsync(chg + (pass & 1), 0, sizeof(uint32_t), s));
       Launch lp_(c, kKAcFix, n, s);
-      k_ac_fix<<<ceil_div(nch2, kStateWarps), 32 * kStateWarps, 0, s>>>(ssym, n, chunk, group, A, state,
-                                                                          misc + kMiscAccCount);
+      k_ac_fix<<<ceil_div(nch2, kStateWarps), 32 * kStateWarps, 0, s>>>(
+          ssym, n, chunk, group, A, state, pass ? chg + ((pass - 1) & 1) : nullptr, chg + (pass & 1));
     }
-    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, chg + ((pass - 1) & 1), 4, cudaMemcpyDeviceToHost, s));
     APO_CUDA_TRY(cudaStreamSynchronize(s));
     if (c->host_pinned[0] == 0) break;
   }
@@ -1361,6 +1384,8 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   APO_CUDA_TRY(cudaGetLastError());
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscCompactCount, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 1, misc + kMiscTraceCount, 4, cudaMemcpyDeviceToHost, s));
+  if (flat_ok)
+    APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 2, misc + kMiscFlatTotal, 4, cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1376,19 +1401,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     // chain lengths, usually far below the match count), then copy chains
     // per position; very long flattened chains fall back to walking
     const uint32_t R = c->host_pinned[1];
-    uint32_t *rtot = c->arena.take_n<uint32_t>(R), *flat_off = c->arena.take_n<uint32_t>(R);
-    uint64_t flat_total = ~0ull;
-    if (rtot && flat_off && R) {
-      {
-        Launch lp_(c, kKMarkEnds, R, s);
-        k_rec_totals<<<grid_for(R, 256, sms), 256, 0, s>>>(rec, mtotal, R, rtot);
-      }
-      APO_TRY(seg_scan<false>(c, SrcU32{rtot}, DstExclusive{rtot, flat_off, misc + kMiscAccCount, R}, R, OpSum(),
-                              0u, s));
-      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, misc + kMiscAccCount, 4, cudaMemcpyDeviceToHost, s));
-      APO_CUDA_TRY(cudaStreamSynchronize(s));
-      flat_total = c->host_pinned[0];
-    }
+    const uint64_t flat_total = flat_ok && R ? c->host_pinned[2] : ~0ull;
     uint32_t *flat = nullptr;
     if (flat_total <= kMaxFlat) {
       APO_TRY(ensure_side(c, std::max<uint64_t>(flat_total, 1) * 4, s));

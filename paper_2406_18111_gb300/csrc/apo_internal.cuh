@@ -71,6 +71,8 @@ enum : int {
   kMiscRound = 20,        // two words: active-suffix counts of consecutive doubling rounds
   kMiscDict = 22,         // two words: distinct tokens, dictionary overflow flag
   kMiscPhaseLen = 24,     // two words: list lengths of consecutive greedy phases
+  kMiscFixChanged = 26,   // two words: changes of consecutive automaton repair passes
+  kMiscFlatTotal = 28,    // length of the flattened output chains
   kMiscCount = 64,
 };
 
