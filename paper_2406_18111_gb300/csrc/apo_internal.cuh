@@ -73,6 +73,7 @@ enum : int {
   kMiscPhaseLen = 24,     // two words: list lengths of consecutive greedy phases
   kMiscFixChanged = 26,   // two words: changes of consecutive automaton repair passes
   kMiscFlatTotal = 28,    // length of the flattened output chains
+  kMiscCandUnique = 29,   // candidates left after deduplication
   kMiscCount = 64,
 };
 

@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const ui
   }
 }
 
-__global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m,
+__global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m, const uint32_t *m_dev,
                               const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                               int bi, int bl, uint32_t lmax, int ks, const uint32_t *__restrict__ woff,
                               uint32_t *__restrict__ cl, uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
+  m = min(m, *m_dev);  // m: an upper bound
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
@@ -504,7 +505,8 @@ __global__ void k_sel_out(const uint64_t *__restrict__ keys, const uint32_t *__r
 // First index of each window in a list sorted by window (the window of entry
 // k is the window of position pos[k]); out[count] = m.
 __global__ void k_window_bounds(const uint32_t *__restrict__ pos, uint32_t m, Windows W,
-                                uint32_t *__restrict__ out) {
+                                uint32_t *__restrict__ out, const uint32_t *m_dev = nullptr) {
+  if (m_dev) m = min(m, *m_dev);  // m: an upper bound
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= W.count; w += gridDim.x * blockDim.x) {
     uint32_t lo = 0, hi = m;
     while (lo < hi) {
@@ -528,23 +530,28 @@ __global__ void k_relativize(uint32_t *__restrict__ start, uint32_t *__restrict_
 
 int g_greedy_smem_max = 0;  // dynamic shared memory available to k_greedy<*, true>
 
-// A device count and the error word in one synchronisation (a captured call
-// takes both from its tape).
-int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s) {
+// A device count (and optionally a second one) and the error word in one
+// synchronisation (a captured call takes them from its tape).
+int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s, const uint32_t *dev2 = nullptr,
+             uint32_t *host2 = nullptr) {
   if (capturing(c)) {
     uint32_t e = 0;
     APO_TRY(tape_take(c, dev, host, 1, s));
+    if (dev2) APO_TRY(tape_take(c, dev2, host2, 1, s));
     return tape_take(c, c->ps.err, &e, 1, s);
   }
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned, dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (dev2) APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 1, dev2, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + kPinnedErr, c->ps.err, sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s));
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   if (recording(c)) {
     tape_put(c, c->host_pinned, 1);
+    if (dev2) tape_put(c, c->host_pinned + 1, 1);
     tape_put(c, c->host_pinned + kPinnedErr, 1);
   }
   APO_TRY(device_error_status(c, s));
+  if (dev2) *host2 = c->host_pinned[1];
   *host = c->host_pinned[0];
   return APO_OK;
 }
@@ -728,7 +735,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   APO_CUDA_TRY(cudaGetLastError());
   uint32_t mraw = 0;
   APO_TRY(read_u32(c, misc + kMiscCandCount, &mraw, s));
-  uint32_t m = 0;
+  // m, the candidates left after deduplication, stays on the device (m_dev)
+  // until it is read with the greedy's count; launches before that are sized
+  // by mu = mraw >= m
+  uint32_t m = 0, mu = 0;
+  const uint32_t *m_dev = misc + kMiscCandUnique;
   if (mraw) {
     // (window, length, id, start): one key, or start digits (the value)
     // first and then the (window, length, id) key
@@ -740,25 +751,25 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     else
       APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
     PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
-    APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCompactCount, s));
-    APO_TRY(read_u32(c, misc + kMiscCompactCount, &m, s));
+    APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCandUnique, s));
+    mu = mraw;
     {
-      Launch lp_(c, kKCandGather, m, s);
-      k_cand_gather<<<grid_for(m, 256, c->num_sms), 256, 0, s>>>(sel, m, b.keys[b.cur], b.vals[b.cur],
-                                                                 bi, bl, lmax, ks, W.count > 1 ? W.off_dev : nullptr,
-                                                                 cl, cid, cs);
+      Launch lp_(c, kKCandGather, mu, s);
+      k_cand_gather<<<grid_for(mu, 256, c->num_sms), 256, 0, s>>>(sel, mu, m_dev, b.keys[b.cur], b.vals[b.cur],
+                                                                  bi, bl, lmax, ks, W.count > 1 ? W.off_dev : nullptr,
+                                                                  cl, cid, cs);
     }
   }
 
   // greedy selection, one block per window
   uint32_t K = 0;
-  if (m) {
+  if (mu) {
     {
       Launch lp_(c, kKSlices, W.count + 1, s);
-      k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(cs, m, W, cand_off);
+      k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(cs, mu, W, cand_off, m_dev);
     }
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
-    APO_CUDA_TRY(cudaMemsetAsync(acc, 0, m, s));
+    APO_CUDA_TRY(cudaMemsetAsync(acc, 0, mu, s));
     const uint32_t maxw = W.count > 1 ? W.max_len : n;
     const size_t bm_bytes = (size_t)((((maxw + 31) / 32) + 3) & ~3u) * 4;
     const bool big = W.count == 1;  // one window: one wide block
@@ -768,9 +779,9 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     if (!smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
     uint32_t *keep = nullptr, *glist[2][3] = {};
     if (big) {
-      keep = c->arena.take_n<uint32_t>(m);
+      keep = c->arena.take_n<uint32_t>(mu);
       for (auto &g : glist)
-        for (auto &a : g) a = c->arena.take_n<uint32_t>(m);
+        for (auto &a : g) a = c->arena.take_n<uint32_t>(mu);
       if (!keep || !glist[1][2]) return APO_ENOMEM;
     }
     if (big) {
@@ -786,8 +797,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
       // an empty list and returns at once.
       if (smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
       const uint32_t *pl = cl, *ps = cs, *po = nullptr;
-      const uint32_t *len_dev = nullptr;  // the current list's length (null: exactly len)
-      uint32_t len = m, prefix = kGreedyFirstPhase;  // len: an upper bound of that length
+      const uint32_t *len_dev = m_dev;  // the current list's length
+      uint32_t len = mu, prefix = kGreedyFirstPhase;  // len: an upper bound of that length
       for (int phase = 0;; ++phase) {
         const uint32_t take = std::min(prefix, len);
         {
@@ -819,17 +830,17 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
         prefix *= 2;
       }
     } else {
-      Launch lp_(c, kKGreedy, m, s);
+      Launch lp_(c, kKGreedy, mu, s);
       if (smem)
-        k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, m, W.off_dev, n,
+        k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, mu, W.off_dev, n,
                                                                   nullptr, acc, misc + kMiscAccCount,
                                                                   nullptr, 0, nullptr, c->ps.err);
       else
-        k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, m, W.off_dev, n, gbits, acc,
+        k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, mu, W.off_dev, n, gbits, acc,
                                                         misc + kMiscAccCount, nullptr, 0, nullptr, c->ps.err);
     }
     APO_CUDA_TRY(cudaGetLastError());
-    APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s));
+    APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s, m_dev, &m));
   }
 
   // R and the selected intervals
