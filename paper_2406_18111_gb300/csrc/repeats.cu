@@ -119,11 +119,16 @@ struct PredFlag {
   __device__ bool operator()(uint32_t k) const { return f[k] != 0; }
 };
 
-template <class Pred>
+// Where the r-th kept k goes: out[r] = k.
+struct PutIndex {
+  uint32_t *out;
+  __device__ __forceinline__ void operator()(uint32_t r, uint32_t k) const { out[r] = k; }
+};
+
+template <class Pred, class Put>
 __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const uint32_t *m_dev, uint32_t m_sub,
-                                                 uint32_t *__restrict__ out, uint32_t *count_out,
-                                                 uint64_t *status, uint32_t *tile_ctr, uint32_t epoch,
-                                                 uint32_t *err) {
+                                                 Put put, uint32_t *count_out, uint64_t *status,
+                                                 uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
   __shared__ uint32_t s_tile, s_pre;
   __shared__ uint32_t scr[kCT / 32];
   const int tid = threadIdx.x;
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const ui
 #pragma unroll
   for (int i = 0; i < kCI; ++i) {
     if ((fb >> i) & 1u) {
-      if (r < m) out[r] = (uint32_t)(e0 + i); else atomicExch(err, kDevRange);
+      if (r < m) put(r, (uint32_t)(e0 + i)); else atomicExch(err, kDevRange);
       ++r;
     }
   }
@@ -409,20 +414,19 @@ struct PredUnmarked {
   }
 };
 
-// New list = the kept remainder entries, in order (cnt: an upper bound of
-// their number, *cnt_dev the number).
-__global__ void k_list_gather(const uint32_t *__restrict__ keep, uint32_t cnt, const uint32_t *cnt_dev,
-                              uint32_t from, const uint32_t *__restrict__ l, const uint32_t *__restrict__ st,
-                              const uint32_t *__restrict__ orig, uint32_t *__restrict__ l2,
-                              uint32_t *__restrict__ s2, uint32_t *__restrict__ o2) {
-  cnt = min(cnt, *cnt_dev);
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
-    const uint32_t k = from + keep[q];
-    l2[q] = l[k];
-    s2[q] = st[k];
-    o2[q] = orig ? orig[k] : k;
+// The drop's output: the r-th kept remainder entry k (list position from + k)
+// becomes entry r of the next list.
+struct PutList {
+  const uint32_t *l, *st, *orig;
+  uint32_t from;
+  uint32_t *l2, *s2, *o2;
+  __device__ __forceinline__ void operator()(uint32_t r, uint32_t k) const {
+    const uint32_t q = from + k;
+    l2[r] = l[q];
+    s2[r] = st[q];
+    o2[r] = orig ? orig[q] : q;
   }
-}
+};
 
 // Accepted candidates (compacted, in order) -> R and the keys of the
 // selected intervals.  A new trace starts wherever (length, id) changes; the
@@ -557,10 +561,11 @@ int read_u32(apo_ctx *c, const uint32_t *dev, uint32_t *host, cudaStream_t s, co
 }
 
 // Compacts the k < m (or, with m_dev, k < min(m, *m_dev - m_sub)) for which
-// pred(k) holds into out, in order; their number lands in *count_dev.
-template <class Pred>
-int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_dev, cudaStream_t s,
-            const uint32_t *m_dev = nullptr, uint32_t m_sub = 0) {
+// pred(k) holds: the r-th of them goes to put(r, k) (out[r] = k with an
+// index array); their number lands in *count_dev.
+template <class Pred, class Put>
+int compact_to(apo_ctx *c, Pred pred, Put put, uint32_t m, uint32_t *count_dev, cudaStream_t s,
+               const uint32_t *m_dev = nullptr, uint32_t m_sub = 0) {
   const int tiles = std::max(1, ceil_div(m, kCTile));
   APO_TRY(ensure_lookback(c, tiles));
   uint32_t *tctr = c->ps.counters + kCtrMisc + kMiscCompactTiles;
@@ -568,11 +573,16 @@ int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_de
   APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKCompact, m, s);
-    k_compact<<<tiles, kCT, 0, s>>>(pred, m, m_dev, m_sub, out, count_dev, c->ps.lookback, tctr,
+    k_compact<<<tiles, kCT, 0, s>>>(pred, m, m_dev, m_sub, put, count_dev, c->ps.lookback, tctr,
                                     next_epoch(c), c->ps.err);
   }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
+}
+
+template <class Pred>
+int compact(apo_ctx *c, Pred pred, uint32_t m, uint32_t *out, uint32_t *count_dev, cudaStream_t s) {
+  return compact_to(c, pred, PutIndex{out}, m, count_dev, s);
 }
 
 template <class T>
@@ -643,7 +653,7 @@ size_t repeats_workspace_bytes(uint64_t n, uint64_t windows) {
   const uint64_t M = n ? 2 * (n - 1) : 0;
   return (size_t)M * (2 * 8 + 2 * 4)  // sort buffers
          + (size_t)M * (4 * 3 + 4 + 1)  // candidate arrays, compaction indices, flags
-         + (size_t)M * (4 * 7)           // single window: greedy lists (two of three arrays) and drops
+         + (size_t)M * (4 * 6)           // single window: greedy lists (two sets of three arrays)
          + (size_t)n * 20                // R and the selected intervals (5 arrays of <= n)
          + (size_t)n * 4 / 16 + (size_t)n / 8 + 16 + (size_t)(windows + 1) * 12 + 64 * 256;
 }
@@ -777,12 +787,11 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     const uint32_t *coff = W.count > 1 ? cand_off : nullptr;
     const bool smem = (long long)(bm_bytes + list) <= g_greedy_smem_max;
     if (!smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
-    uint32_t *keep = nullptr, *glist[2][3] = {};
+    uint32_t *glist[2][3] = {};
     if (big) {
-      keep = c->arena.take_n<uint32_t>(mu);
       for (auto &g : glist)
         for (auto &a : g) a = c->arena.take_n<uint32_t>(mu);
-      if (!keep || !glist[1][2]) return APO_ENOMEM;
+      if (!glist[1][2]) return APO_ENOMEM;
     }
     if (big) {
       // Phases: the one block settles a prefix of the list; then every
@@ -814,14 +823,10 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
         APO_CUDA_TRY(cudaGetLastError());
         if (take == len) break;
         uint32_t *kept_dev = misc + kMiscPhaseLen + (phase & 1);
-        PredUnmarked pu{pl, ps, gbits, take};
-        APO_TRY(compact(c, pu, len - take, keep, kept_dev, s, len_dev, take));
         uint32_t *l2 = glist[phase & 1][0], *s2 = glist[phase & 1][1], *o2 = glist[phase & 1][2];
-        {
-          Launch lp_(c, kKCandGather, len - take, s);
-          k_list_gather<<<grid_for(len - take, 256, c->num_sms), 256, 0, s>>>(keep, len - take, kept_dev, take,
-                                                                              pl, ps, po, l2, s2, o2);
-        }
+        PredUnmarked pu{pl, ps, gbits, take};
+        APO_TRY(compact_to(c, pu, PutList{pl, ps, po, take, l2, s2, o2}, len - take, kept_dev, s, len_dev,
+                           take));
         pl = l2;
         ps = s2;
         po = o2;
