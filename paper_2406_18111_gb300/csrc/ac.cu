@@ -298,6 +298,20 @@ __global__ void k_sparse_level(const uint32_t *__restrict__ prev, uint32_t P, ui
     next[j] = j >= half ? min(prev[j], prev[j - half]) : prev[j];
 }
 
+// All levels 1 .. nlev-1 in one block (level l at base + l * P), for a short
+// table: one launch instead of one per level.
+constexpr uint32_t kSparseOneBlock = 1u << 15;
+__global__ void __launch_bounds__(1024) k_sparse_all(uint32_t *base, uint32_t P, int nlev) {
+  for (int l = 1; l < nlev; ++l) {
+    const uint32_t *prev = base + (size_t)(l - 1) * P;
+    uint32_t *next = base + (size_t)l * P;
+    const uint32_t half = 1u << (l - 1);
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x)
+      next[j] = j >= half ? min(prev[j], prev[j - half]) : prev[j];
+    __syncthreads();
+  }
+}
+
 constexpr int kMaxSparse = 33;
 struct Sparse {
   const uint32_t *lev[kMaxSparse];
@@ -1250,11 +1264,19 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   Sparse S;
   S.nlev = nsparse;
   S.lev[0] = sparse;
-  for (int l = 1; l < nsparse; ++l) {
-    uint32_t *lv = sparse + (size_t)l * P;
-    Launch lp_(c, kKSparse, P, s);
-    k_sparse_level<<<grid_for(P, 256, sms), 256, 0, s>>>(S.lev[l - 1], P, 1u << (l - 1), lv);
-    S.lev[l] = lv;
+  if (P <= kSparseOneBlock) {
+    if (nsparse > 1) {
+      Launch lp_(c, kKSparse, P, s);
+      k_sparse_all<<<1, 1024, 0, s>>>(sparse, P, nsparse);
+    }
+    for (int l = 1; l < nsparse; ++l) S.lev[l] = sparse + (size_t)l * P;
+  } else {
+    for (int l = 1; l < nsparse; ++l) {
+      uint32_t *lv = sparse + (size_t)l * P;
+      Launch lp_(c, kKSparse, P, s);
+      k_sparse_level<<<grid_for(P, 256, sms), 256, 0, s>>>(S.lev[l - 1], P, 1u << (l - 1), lv);
+      S.lev[l] = lv;
+    }
   }
 
   // nodes: failure links, branch edges, pattern ends
