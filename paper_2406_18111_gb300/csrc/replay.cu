@@ -233,6 +233,34 @@ __global__ void k_tables_level(const uint32_t *__restrict__ la, const uint32_t *
   }
 }
 
+// Level 0's ingestion times and every level above in one block (level l's
+// arrays at lev + 2 (l - 1) Q), for a short table: one launch instead of one
+// per level.
+constexpr uint32_t kTablesOneBlock = 1u << 15;
+__global__ void __launch_bounds__(1024) k_tables_all(const uint32_t *__restrict__ sp,
+                                                     const uint32_t *__restrict__ ptau, const uint32_t *slcp,
+                                                     uint32_t Q, int nlev, uint32_t *tau_sorted, uint32_t *lev) {
+  for (uint32_t j = threadIdx.x; j < Q; j += blockDim.x) tau_sorted[j] = ptau[sp[j]];
+  __syncthreads();
+  const uint32_t *la = slcp, *ta = tau_sorted;
+  for (int l = 1; l < nlev; ++l) {
+    uint32_t *lb = lev + (size_t)(2 * (l - 1)) * Q, *tb = lb + Q;
+    const uint32_t half = 1u << (l - 1);
+    for (uint32_t j = threadIdx.x; j < Q; j += blockDim.x) {
+      uint32_t x = la[j], y = ta[j];
+      if (j >= half) {
+        x = min(x, la[j - half]);
+        y = min(y, ta[j - half]);
+      }
+      lb[j] = x;
+      tb[j] = y;
+    }
+    __syncthreads();
+    la = lb;
+    ta = tb;
+  }
+}
+
 struct Tables {
   const uint32_t *lcp[32];  // window minima of slcp, level l covers 2^l entries
   const uint32_t *tau[32];  // window minima of the ingestion times
@@ -845,17 +873,28 @@ int replay_stream(apo_ctx *c, const void *tokens, uint64_t n, int tb, const apo_
   T.Q = Qd;
   T.lcp[0] = w.slcp;
   T.tau[0] = w.tau_sorted;
-  {
-    Launch lp_(c, kKRpNeed, Qd, s);
-    k_tables0<<<grid_for(Qd, 256, sms), 256, 0, s>>>(w.sp, ptau, Qd, w.tau_sorted);
-  }
-  for (int l = 1; l < nlevd; ++l) {
-    uint32_t *lb = w.lev + (size_t)(2 * (l - 1)) * Qd, *tbv = lb + Qd;
-    Launch lp_(c, kKRpNeed, Qd, s);
-    k_tables_level<<<grid_for(Qd, 256, sms), 256, 0, s>>>(T.lcp[l - 1], T.tau[l - 1], Qd, 1u << (l - 1), lb,
-                                                             tbv);
-    T.lcp[l] = lb;
-    T.tau[l] = tbv;
+  if (Qd <= kTablesOneBlock) {
+    {
+      Launch lp_(c, kKRpNeed, Qd, s);
+      k_tables_all<<<1, 1024, 0, s>>>(w.sp, ptau, w.slcp, Qd, nlevd, w.tau_sorted, w.lev);
+    }
+    for (int l = 1; l < nlevd; ++l) {
+      T.lcp[l] = w.lev + (size_t)(2 * (l - 1)) * Qd;
+      T.tau[l] = T.lcp[l] + Qd;
+    }
+  } else {
+    {
+      Launch lp_(c, kKRpNeed, Qd, s);
+      k_tables0<<<grid_for(Qd, 256, sms), 256, 0, s>>>(w.sp, ptau, Qd, w.tau_sorted);
+    }
+    for (int l = 1; l < nlevd; ++l) {
+      uint32_t *lb = w.lev + (size_t)(2 * (l - 1)) * Qd, *tbv = lb + Qd;
+      Launch lp_(c, kKRpNeed, Qd, s);
+      k_tables_level<<<grid_for(Qd, 256, sms), 256, 0, s>>>(T.lcp[l - 1], T.tau[l - 1], Qd, 1u << (l - 1), lb,
+                                                               tbv);
+      T.lcp[l] = lb;
+      T.tau[l] = tbv;
+    }
   }
   {
     Launch lp_(c, kKRpNeed, Qd, s);
