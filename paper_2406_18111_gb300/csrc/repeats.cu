@@ -14,17 +14,22 @@
 //              32-ary min-tree over LCP (up one level until a block with a
 //              smaller minimum lies to the left, then down into it).
 //  sort        (length desc, id asc, start asc): the onesweep radix sort over
-//              the start digits (value) then the (length, id) digits (key).
+//              one (window, length, id, start) key when it fits 64 bits, else
+//              over the start digits (value) then the (window, length, id)
+//              digits (key).
 //  dedup       identical (length, start) pairs are adjacent after the sort and
 //              are kept once (order-preserving compaction).
 //  greedy      the second loop of Alg. 2 is sequential by definition; it runs
-//              in one 1024-thread block with the mark array of Sec. 4.2 as a
-//              bitmap (in shared memory when the window fits).  Because the
-//              candidates come in non-increasing length, a candidate meets an
-//              accepted interval iff its first or last position is marked.
-//              Each round loads 1024 candidates, drops in parallel those whose
-//              ends are already marked, and one warp settles the few
-//              survivors in order, marking the accepted intervals.
+//              in one block (1024 threads for a single window, 256 per window
+//              in a batch) with the mark array of Sec. 4.2 as a bitmap (in
+//              shared memory when the window fits).  Because the candidates
+//              come in non-increasing length, a candidate meets an accepted
+//              interval iff its first or last position is marked.  Each round
+//              takes 4 candidates per thread, drops in parallel those whose
+//              ends are already marked, and warp 0 settles the survivors 32
+//              at a time, in order, marking the accepted intervals.  A single
+//              window runs in phases of growing length; between them the
+//              whole GPU drops the remaining candidates with a marked end.
 //  R           accepted candidates in order; a new trace starts where (length,
 //              id) changes; selected intervals are re-sorted by start.
 #include <algorithm>
