@@ -41,15 +41,18 @@
 //
 // Match.  The stream is cut into short chunks and each thread runs the
 // automaton over its chunk from the root, writing the state of every
-// position (only the first chunk is exact).  Repair passes then restart each
-// chunk from its predecessor's end state and stop at the first position whose
-// state agrees with the recorded one -- from there on the deterministic
-// automaton repeats the recorded run.  When a pass changes no end state all
-// states are exact (after k passes chunks 0..k are, by induction).  The
-// per-node match totals turn the output offsets into one prefix sum over
-// positions; a final kernel per position writes its matches.  Output order:
-// end ascending, then pattern length descending (the output chain's order),
-// then pattern id ascending.
+// position (only the first chunk is exact).  Repair passes then give each
+// group of chunks (4, or 8 on streams of 2^22 tokens and more) one warp that
+// restarts from the predecessor's end state and stops at the first position
+// whose state agrees with the recorded one -- from there on the
+// deterministic automaton repeats the recorded run.  When a pass changes no
+// end state all states are exact (after k passes groups 0..k are, by
+// induction); passes are queued two at a time, and one behind a pass without
+// changes returns at once.  The per-node match totals turn the output
+// offsets into one prefix sum over positions; each output record's chain is
+// flattened once, and a final kernel per position copies its matches.
+// Output order: end ascending, then pattern length descending (the output
+// chain's order), then pattern id ascending.
 #include <algorithm>
 #include <cstring>
 #include <vector>
