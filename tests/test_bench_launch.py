@@ -30,3 +30,20 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_batched_oracle_baseline_on_every_core():
+    """The batched workload's CPU baseline: the oracle over every window on a
+    thread pool, and on one core over a prefix of the windows; both rates
+    positive and the core counts stated."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import workloads as W
+    toks, off, _ = W.config3_windows(6, lo=1024, hi=4096)
+    r = bench.batched_cpu_baseline(toks, off)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert r["one_core"]["cores"] == 1 and r["one_core"]["value"] > 0
+    assert f"all 6 windows ({int(off[-1])} tokens)" in r["sample"]
+    assert np.all(np.diff(off.astype(np.int64)) >= 1024)
