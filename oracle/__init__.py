@@ -53,12 +53,14 @@ def lib():
         for f in ("ora_lcp_direct", "ora_lcp_kasai"):
             getattr(L, f).restype = None
             getattr(L, f).argtypes = [P, U64, P, P]
+        L.ora_lce.restype = None
+        L.ora_lce.argtypes = [P, P, U64, P, P, U64, P]
         L.ora_candidates_raw.restype = U64
         L.ora_candidates_raw.argtypes = [U64, P, P, P, P]
         L.ora_greedy.restype = None
         L.ora_greedy.argtypes = [U64, U64, P, P, P, ctypes.c_int]
         L.ora_find_repeats.restype = None
-        L.ora_find_repeats.argtypes = [P, U64, P, P, ctypes.c_uint32, ctypes.c_int] + [P] * 10
+        L.ora_find_repeats.argtypes = [P, U64, P, P, ctypes.c_uint32, ctypes.c_int, ctypes.c_int] + [P] * 10
         L.ora_match.restype = U64
         L.ora_match.argtypes = [P, P, U64, P, U64, ctypes.c_int, P, P, U64]
         L.ora_optimum.restype = U64
@@ -119,6 +121,17 @@ def lcp(S, sa, method: str = "kasai") -> np.ndarray:
     return out
 
 
+def lce(sa, lcp_arr, a, b) -> np.ndarray:
+    """lcp of the suffixes at a[k] and b[k] by range minima over the LCP array."""
+    sa = np.ascontiguousarray(sa, dtype=np.uint32)
+    lcp_arr = np.ascontiguousarray(lcp_arr, dtype=np.uint32)
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    b = np.ascontiguousarray(b, dtype=np.uint32)
+    out = np.zeros(max(1, a.shape[0]), np.uint64)
+    lib().ora_lce(_p(sa), _p(lcp_arr), sa.shape[0], _p(a), _p(b), a.shape[0], _p(out))
+    return out[:a.shape[0]]
+
+
 def candidates_raw(sa, lcp_arr):
     sa = np.ascontiguousarray(sa, dtype=np.uint32)
     lcp_arr = np.ascontiguousarray(lcp_arr, dtype=np.uint32)
@@ -152,9 +165,16 @@ class Repeats:
     trace_start: np.ndarray
 
 
+_CMP = {"direct": 0, "lce": 1, "auto": 2}
+
+
 def find_repeats(S, min_len: int, greedy_variant: int = 0, sa_method: str = "direct",
-                 sa=None, lcp_arr=None) -> Repeats:
-    """Alg. 2 end to end on one window (SA, LCP, candidates, greedy, R)."""
+                 sa=None, lcp_arr=None, cmp: str = "auto") -> Repeats:
+    """Alg. 2 end to end on one window (SA, LCP, candidates, greedy, R).
+
+    ``cmp`` selects how the candidate sort and the id search compare
+    sub-strings: "direct" token by token, "lce" by LCE queries over the SA
+    and LCP, "auto" token by token up to 2^16 tokens and by LCE above."""
     S = _tok(S)
     n = S.shape[0]
     if sa is None:
@@ -168,7 +188,7 @@ def find_repeats(S, min_len: int, greedy_variant: int = 0, sa_method: str = "dir
     acc = np.zeros(cap, np.uint8)
     ss, sl, st, tl, tst = (np.zeros(max(1, n), np.uint32) for _ in range(5))
     counts = np.zeros(3, np.uint64)
-    lib().ora_find_repeats(_p(S), n, _p(sa), _p(lcp_arr), min_len, greedy_variant,
+    lib().ora_find_repeats(_p(S), n, _p(sa), _p(lcp_arr), min_len, greedy_variant, _CMP[cmp],
                            _p(cl), _p(ci), _p(cs), _p(acc), _p(ss), _p(sl), _p(st), _p(tl), _p(tst),
                            _p(counts))
     m, k, t = (int(c) for c in counts)

@@ -18,7 +18,10 @@
 //                                  and by Kasai et al. (CPM 2001).
 //   ora_find_repeats               Alg. 2 "FindRepeats": candidate loop, sort by
 //                                  (length desc, sub-string asc, start asc),
-//                                  greedy non-overlapping selection, dedup.
+//                                  greedy non-overlapping selection, dedup;
+//                                  sub-strings compared token by token or, for
+//                                  long windows, by LCE queries (range minima
+//                                  of the LCP array).
 //   ora_match                      every occurrence of every candidate trace in
 //                                  a stream (Sec. 4.3: a pointer that reaches the
 //                                  end of a trace in the trie is a match).
@@ -91,6 +94,50 @@ bool prefix_less(const uint64_t *S, uint64_t n, uint64_t j, uint64_t r, uint64_t
 struct Cand {
   uint64_t l, s;
 };
+
+// Longest common extension of two suffixes from the LCP array: the LCP of
+// suffixes a and b is the minimum of LCP over the SA positions between them
+// (a range-minimum query), answered by a sparse table of minima over
+// power-of-two ranges (Bender & Farach-Colton 2000, the O(n log n) table).
+struct Lce {
+  uint64_t n = 0;
+  std::vector<uint32_t> isa;
+  std::vector<std::vector<uint32_t>> tab;  // tab[k][i] = min LCP[i .. i + 2^k)
+  Lce(const uint32_t *sa, const uint32_t *lcp, uint64_t n_) : n(n_), isa(n_) {
+    for (uint64_t k = 0; k < n; ++k) isa[sa[k]] = (uint32_t)k;
+    tab.emplace_back(lcp, lcp + n);
+    for (uint64_t w = 1; 2 * w <= n; w *= 2) {
+      const std::vector<uint32_t> &prev = tab.back();
+      std::vector<uint32_t> next(n - 2 * w + 1);
+      for (uint64_t i = 0; i + 2 * w <= n; ++i) next[i] = std::min(prev[i], prev[i + w]);
+      tab.push_back(std::move(next));
+    }
+  }
+  // lcp of the suffixes starting at a and b
+  uint64_t operator()(uint64_t a, uint64_t b) const {
+    if (a == b) return n - a;
+    uint64_t x = isa[a], y = isa[b];
+    if (x > y) std::swap(x, y);
+    // min LCP[x .. y - 1]: LCP[k] pairs SA[k] with SA[k + 1]
+    uint64_t len = y - x, k = 0;
+    while ((2ull << k) <= len) ++k;
+    return std::min(tab[k][x], tab[k][y - (1ull << k)]);
+  }
+};
+
+// substr_cmp and prefix_less through LCE queries instead of token loops.
+int substr_cmp_lce(const uint64_t *S, const Lce &E, uint64_t a, uint64_t b, uint64_t l) {
+  const uint64_t e = E(a, b);
+  if (e >= l) return 0;
+  return S[a + e] < S[b + e] ? -1 : 1;
+}
+
+bool prefix_less_lce(const uint64_t *S, uint64_t n, const Lce &E, uint64_t j, uint64_t r, uint64_t l) {
+  const uint64_t e = E(j, r);
+  if (e >= l) return false;
+  if (j + e >= n) return true;  // suffix j ends first: a proper prefix is smaller
+  return S[j + e] < S[r + e];
+}
 
 }  // namespace
 
@@ -228,6 +275,15 @@ uint64_t ora_candidates_raw(uint64_t n, const uint32_t *sa, const uint32_t *lcp,
   return m;
 }
 
+// LCE queries (for the tests): out[k] = lcp of the suffixes at a[k] and b[k],
+// through the sparse table over the given SA and LCP.
+void ora_lce(const uint32_t *sa, const uint32_t *lcp, uint64_t n, const uint32_t *a, const uint32_t *b,
+             uint64_t q, uint64_t *out) {
+  if (n == 0) return;
+  Lce E(sa, lcp, n);
+  for (uint64_t k = 0; k < q; ++k) out[k] = E(a[k], b[k]);
+}
+
 // Greedy selection over candidates already in priority order (Alg. 2's second
 // loop).  variant 0: an ordered set of the accepted intervals; 1: the literal
 // scan over every accepted interval; 2: the mark array of Sec. 4.2 (mark every
@@ -281,8 +337,12 @@ void ora_greedy(uint64_t n, uint64_t m, const uint32_t *l, const uint32_t *s,
 //   trace_len/start         R: distinct accepted sub-strings in the order the
 //                           loop first took them; start = smallest accepted start
 //   counts[0..2]            #candidates, #accepted, |R|
+// cmp_method: how sub-strings are compared in the sort and the id search:
+// 0 token by token, 1 by LCE queries over the given SA and LCP (O(1) per
+// comparison, for windows whose long repeats make token loops quadratic),
+// 2 token by token up to 2^16 tokens and by LCE above.
 void ora_find_repeats(const uint64_t *S, uint64_t n, const uint32_t *sa, const uint32_t *lcp,
-                      uint32_t min_len, int greedy_variant, uint32_t *cand_l, uint32_t *cand_id,
+                      uint32_t min_len, int greedy_variant, int cmp_method, uint32_t *cand_l, uint32_t *cand_id,
                       uint32_t *cand_s, uint8_t *accepted, uint32_t *sel_start, uint32_t *sel_len,
                       uint32_t *sel_trace, uint32_t *trace_len, uint32_t *trace_start,
                       uint64_t *counts) {
@@ -293,10 +353,13 @@ void ora_find_repeats(const uint64_t *S, uint64_t n, const uint32_t *sa, const u
   std::vector<Cand> C;
   for (uint64_t k = 0; k < m_raw; ++k)
     if (rl[k] >= min_len && rl[k] > 0) C.push_back({rl[k], rs[k]});
+  const bool use_lce = cmp_method == 1 || (cmp_method == 2 && n > (1u << 16));
+  Lce *E = nullptr;
+  if (use_lce) E = new Lce(sa, lcp, n);
   // Sort by decreasing length, then increasing sub-string, then increasing start.
   std::sort(C.begin(), C.end(), [&](const Cand &a, const Cand &b) {
     if (a.l != b.l) return a.l > b.l;
-    int c = substr_cmp(S, a.s, b.s, a.l);
+    int c = E ? substr_cmp_lce(S, *E, a.s, b.s, a.l) : substr_cmp(S, a.s, b.s, a.l);
     if (c != 0) return c < 0;
     return a.s < b.s;
   });
@@ -311,10 +374,13 @@ void ora_find_repeats(const uint64_t *S, uint64_t n, const uint32_t *sa, const u
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
       uint64_t mid = (lo + hi) / 2;
-      if (prefix_less(S, n, sa[mid], D[k].s, D[k].l)) lo = mid + 1; else hi = mid;
+      const bool less = E ? prefix_less_lce(S, n, *E, sa[mid], D[k].s, D[k].l)
+                          : prefix_less(S, n, sa[mid], D[k].s, D[k].l);
+      if (less) lo = mid + 1; else hi = mid;
     }
     cand_id[k] = (uint32_t)lo;
   }
+  delete E;
   ora_greedy(n, m, cand_l, cand_s, accepted, greedy_variant);
   // R: distinct accepted sub-strings, keyed by their tokens, in first-acceptance order.
   std::map<std::vector<uint64_t>, uint32_t> Rix;

@@ -224,6 +224,58 @@ def test_sa_methods_and_lcp_methods_agree(kind):
     assert np.array_equal(oracle.lcp(S, sa, "kasai"), oracle.lcp(S, sa, "direct"))
 
 
+def _lce_strings():
+    """Strings up to 2^16 tokens whose long repeats stress the LCE path:
+    constant, period-2 and period-3 runs (up to 2^14 alone, at 2^16 as the
+    three thirds of config 4's adversarial window), periodic
+    windows with noise, random strings over small and large alphabets."""
+    out = []
+    for n in (1, 2, 7, 64, 1000, 4099, 1 << 14):
+        out.append(np.zeros(n, np.uint64))
+        out.append((np.arange(n) % 2).astype(np.uint64))
+        out.append((np.arange(n) % 3).astype(np.uint64))
+    a, _ = W.config4_windows(1 << 16)
+    out.append(a.astype(np.uint64))
+    out.append(np.asarray(W.config1_window(4096, seed=17), np.uint64))
+    out.append(np.asarray(W.periodic_window(1 << 16, 37, 0.02, 50, 19), np.uint64))
+    out.append(W.uniform_int(23, 1 << 16, 0, 1).astype(np.uint64))
+    out.append(W.uniform_int(24, 5000, 0, 1 << 40).astype(np.uint64))
+    return out
+
+
+def test_lce_queries_equal_direct_comparison():
+    """The sparse-table LCE equals the common prefix counted token by token
+    (sampled pairs, every window; the equal-suffix case a == b included)."""
+    for k, S in enumerate(_lce_strings()):
+        n = S.shape[0]
+        sa = oracle.suffix_array(S, "doubling")
+        lc = oracle.lcp(S, sa)
+        q = min(400, n * n)
+        a = W.uniform_int(300 + k, q, 0, n - 1).astype(np.uint32)
+        b = W.uniform_int(400 + k, q, 0, n - 1).astype(np.uint32)
+        b[::17] = a[::17]
+        got = oracle.lce(sa, lc, a, b)
+        for x, y, g in zip(a.tolist(), b.tolist(), got.tolist()):
+            m = min(n - x, n - y)
+            eq = S[x:x + m] == S[y:y + m]
+            want = m if eq.all() else int(np.argmin(eq))
+            assert g == want, (k, x, y, g, want)
+
+
+def test_candidate_order_lce_equals_direct():
+    """Alg. 2's sort and the candidate ids are the same with sub-strings
+    compared token by token and through LCE queries."""
+    for k, S in enumerate(_lce_strings()):
+        sa = oracle.suffix_array(S, "doubling")
+        lc = oracle.lcp(S, sa)
+        for ml in ((1, 5) if S.shape[0] < (1 << 14) else (5,)):
+            d = oracle.find_repeats(S, ml, sa=sa, lcp_arr=lc, cmp="direct")
+            e = oracle.find_repeats(S, ml, sa=sa, lcp_arr=lc, cmp="lce")
+            for f in ("cand_len", "cand_id", "cand_start", "accepted", "sel_start", "sel_len", "sel_trace",
+                      "trace_len", "trace_start"):
+                assert np.array_equal(getattr(d, f), getattr(e, f)), (k, ml, f)
+
+
 def test_greedy_variants_agree_on_config1():
     S = W.config1_window()
     r = oracle.find_repeats(S, 5)
