@@ -191,6 +191,36 @@ typedef struct {
 int apo_find_repeats_batched(apo_ctx *ctx, const apo_windows *windows,
                              const apo_repeats_params *params, apo_repeats_out *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Workspace of the repeat-finding calls (the scratch of Alg. 2's stages:
+ * sort buffers, doubling-round lists, level ranks, candidate arrays).
+ *
+ * apo_find_repeats_workspace: *bytes (HOST) receives the device bytes that
+ * apo_find_repeats (one window: n_windows = 1, win_off = {0, n}) or
+ * apo_find_repeats_batched needs for `windows` -- an upper bound that depends
+ * only on the total token count and the window count.  It allocates and
+ * launches nothing and needs no GPU (ctx may be NULL).  APO_EINVAL for a
+ * null windows or bytes pointer, no windows, or more than 2^31 - 1 tokens.
+ *
+ * apo_set_workspace: from now on the context takes all scratch of its repeat
+ * calls from `workspace` (DEVICE, `bytes` long, 256-byte aligned, at least
+ * 4096 bytes, owned by the caller and not freed by the library) instead of
+ * growing its own with cudaMalloc; a call that needs more than is attached
+ * fails with APO_ENOMEM before it launches anything, with the size it needs
+ * in apo_last_error().  Radix-sort shapes are not tuned by trial runs while a
+ * workspace is attached (the default shape, or a choice made earlier in the
+ * process).  workspace = NULL returns to the context's own scratch.  The
+ * caller makes sure that the context's earlier work has finished before it
+ * attaches, replaces or detaches a workspace (the call does not wait), and
+ * does not reuse the workspace's memory while calls on the context may still
+ * run.
+ * Calls that need scratch of another kind (matching's flattened output
+ * chains, the replayer, the optimum) fail with APO_ENOMEM while a workspace
+ * is attached.
+ * ---------------------------------------------------------------------- */
+int apo_find_repeats_workspace(apo_ctx *ctx, const apo_windows *windows, uint64_t *bytes);
+int apo_set_workspace(apo_ctx *ctx, void *workspace, uint64_t bytes);
+
 /* Graph mode for apo_find_repeats_batched (off by default).  The first call
  * with given arguments (token pointer and width, window offsets, min_len,
  * output pointers and capacities) runs as usual while the values the host
@@ -214,21 +244,31 @@ int apo_graph_stats(apo_ctx *ctx, uint64_t *replays, uint64_t *captures, uint64_
  * each result when it completes (Sec. 4.2, 4.3).  A server accepts such
  * analysis requests at any time and batches them continuously: each of its
  * `lanes` (a context and a stream of its own) repeatedly takes the requests
- * that are waiting, in arrival order, up to max_batch_tokens tokens (the
- * admission budget: a batch's device footprint grows with its tokens) and
- * max_batch_windows requests, runs apo_find_repeats_batched on them and
- * publishes each request's results.  Batches of different lanes overlap on
- * the device; requests that arrive meanwhile join the next batch a lane forms.
- * A request's results are the ones apo_find_repeats gives its window alone.
+ * that are waiting, in arrival order, runs apo_find_repeats_batched on them
+ * and publishes each request's results.  Batches of different lanes overlap
+ * on the device; requests that arrive meanwhile join the next batch a lane
+ * forms.  A request's results are the ones apo_find_repeats gives its window
+ * alone.
+ *
+ * Admission is by device-memory footprint: the server holds one pool of
+ * hbm_budget bytes, and a batch takes a slice of it for its tokens, outputs
+ * and analysis scratch (apo_find_repeats_workspace of its windows).  A lane
+ * adds waiting requests to its batch while the larger footprint still fits
+ * in a free slice, within max_batch_tokens and max_batch_windows; when not
+ * even the first waiting request fits beside the batches in flight, it waits
+ * until one of them finishes and returns its slice.  A request whose
+ * footprint exceeds the whole budget completes with status APO_ECAPACITY.
  * ---------------------------------------------------------------------- */
 typedef struct apo_server apo_server;
 
 typedef struct {
   uint32_t min_len;            /* as apo_repeats_params */
   int token_bytes;             /* 4 or 8 */
-  uint64_t max_batch_tokens;   /* admission budget per batch (a larger request runs alone) */
+  uint64_t max_batch_tokens;   /* most tokens per batch (a larger request runs alone) */
   uint32_t max_batch_windows;  /* most requests per batch */
   uint32_t lanes;              /* batches in flight at once, >= 1 */
+  uint64_t hbm_budget;         /* device bytes all batches in flight may hold together (one pool,
+                                  allocated at creation); 0 = 16 GiB */
 } apo_server_config;
 
 typedef struct {
@@ -257,6 +297,9 @@ int apo_server_wait(apo_server *srv, uint64_t id, apo_request_result *out);
 int apo_server_release(apo_server *srv, uint64_t id);
 /* Seconds on the server's steady clock (the clock of the t_* fields). */
 double apo_server_now(apo_server *srv);
+/* The pool's size, the bytes batches in flight hold now, and the most they
+ * have held at once (HOST outputs; NULL skips one). */
+int apo_server_memory(apo_server *srv, uint64_t *budget, uint64_t *held, uint64_t *held_max);
 /* Finish the queued requests, stop the lanes and free everything. */
 int apo_server_destroy(apo_server *srv);
 
@@ -452,12 +495,18 @@ int apo_optimum_batched(apo_ctx *ctx, const apo_windows *windows, uint32_t min_l
  * pool, or on a latency-critical path that must not pay for cudaMalloc /
  * cudaFree (which may synchronise the whole device).  It needs no context.
  *
- * It runs Alg. 2's second loop on candidates already in greedy order (the
- * cand_len / cand_start outputs of apo_find_repeats for a window of n
- * tokens): accepted[k] = 1 iff [cand_start[k], cand_start[k] + cand_len[k])
- * meets no interval accepted before it, and *accepted_count (DEVICE u32)
- * receives the number accepted.  All arguments are device pointers owned by
- * the caller; the call only enqueues work on `stream` and returns.
+ * Contract: the m candidates are visited in the order given, and
+ * accepted[k] = 1 iff [cand_start[k], cand_start[k] + cand_len[k]) meets no
+ * interval accepted before it (else 0).  cand_len must not increase along
+ * the order -- apo_find_repeats's candidate order (length descending)
+ * satisfies this -- because the test that a candidate meets an accepted
+ * interval looks only at its first and last position, which is exact only
+ * then.  When a length does increase, the flags are undefined and
+ * *accepted_count is set to 0xffffffff; otherwise *accepted_count (DEVICE
+ * u32) receives the number accepted.  Intervals must lie in [0, n); one that
+ * does not is never accepted.  All arguments are device pointers owned by the
+ * caller (cand_len, cand_start and accepted with m entries); the call only
+ * enqueues work on `stream` and returns.  m = 0 writes *accepted_count = 0.
  *
  * Its scratch is a fixed bitmap of APO_NOALLOC_MAX_WINDOW bits (512 KiB)
  * compiled into the library as a static device array, which every GPU that

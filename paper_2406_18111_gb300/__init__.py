@@ -35,7 +35,8 @@ EXPORTS = ("apo_create", "apo_destroy", "apo_last_error", "apo_version", "apo_ha
            "apo_server_poll", "apo_server_wait", "apo_server_release", "apo_server_now",
            "apo_server_destroy", "apo_sort_tuning", "apo_sort_tuning_read", "apo_finder_create",
            "apo_finder_push", "apo_finder_poll", "apo_finder_stats", "apo_finder_destroy",
-           "apo_replay", "apo_optimum_batched", "apo_graph_mode", "apo_graph_stats")
+           "apo_replay", "apo_optimum_batched", "apo_graph_mode", "apo_graph_stats",
+           "apo_find_repeats_workspace", "apo_set_workspace", "apo_server_memory")
 
 # Largest window apo_greedy_select_noalloc accepts (positions of its fixed bitmap).
 NOALLOC_MAX_WINDOW = 1 << 22
@@ -74,7 +75,7 @@ class apo_repeats_out(ctypes.Structure):
 
 class apo_server_config(ctypes.Structure):
     _fields_ = [("min_len", _U32), ("token_bytes", ctypes.c_int), ("max_batch_tokens", _U64),
-                ("max_batch_windows", _U32), ("lanes", _U32)]
+                ("max_batch_windows", _U32), ("lanes", _U32), ("hbm_budget", _U64)]
 
 
 class apo_request_result(ctypes.Structure):
@@ -139,12 +140,15 @@ def lib():
                                        ctypes.POINTER(_U64), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(_U64)]
         L.apo_greedy_select_noalloc.argtypes = [_P, _P, _U64, _U64, _P, _P, _P]
+        L.apo_find_repeats_workspace.argtypes = [_P, ctypes.POINTER(apo_windows), ctypes.POINTER(_U64)]
+        L.apo_set_workspace.argtypes = [_P, _P, _U64]
         L.apo_server_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(apo_server_config)]
         L.apo_server_submit.argtypes = [_P, _P, _U64, ctypes.POINTER(_U64)]
         L.apo_server_poll.argtypes = [_P, _U64, ctypes.POINTER(apo_request_result)]
         L.apo_server_wait.argtypes = [_P, _U64, ctypes.POINTER(apo_request_result)]
         L.apo_server_release.argtypes = [_P, _U64]
         L.apo_server_now.argtypes = [_P]
+        L.apo_server_memory.argtypes = [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]
         L.apo_server_destroy.argtypes = [_P]
         L.apo_sort_tuning.argtypes = [_P, ctypes.c_int]
         _I = ctypes.POINTER(ctypes.c_int)
@@ -256,6 +260,25 @@ class Apo:
             self.close()
         except Exception:
             pass
+
+    # -------------------------------------------------------------- workspace
+    def find_repeats_workspace(self, win_off) -> int:
+        """Device bytes a repeat call over these windows needs (win_off on
+        the host; [0, n] for one window of n tokens)."""
+        wo = np.ascontiguousarray(np.asarray(win_off, dtype=np.uint64))
+        ws = apo_windows(wo.shape[0] - 1, None, 4, wo.ctypes.data)
+        out = _U64()
+        _check(lib().apo_find_repeats_workspace(self._h, ctypes.byref(ws), ctypes.byref(out)))
+        return int(out.value)
+
+    def set_workspace(self, buf=None):
+        """Take the repeat calls' scratch from a caller-owned device buffer
+        (a uint8 tensor, kept alive by the caller), or from the context's own
+        scratch again (None)."""
+        if buf is None:
+            _check(lib().apo_set_workspace(self._h, None, 0))
+        else:
+            _check(lib().apo_set_workspace(self._h, _ptr(buf), int(buf.numel() * buf.element_size())))
 
     # -------------------------------------------------------------- Alg. 1 Hash
     def hash_tasks(self, task_id, arg_off, region, field_mask, priv, out=None, stream=None):
@@ -585,13 +608,31 @@ class Server:
     the GPU, several batches in flight at once."""
 
     def __init__(self, device: int = 0, min_len: int = 5, token_bytes: int = 4,
-                 max_batch_tokens: int = 1 << 24, max_batch_windows: int = 512, lanes: int = 2):
+                 max_batch_tokens: int = 1 << 24, max_batch_windows: int = 512, lanes: int = 2,
+                 hbm_budget: int = 0):
         self.token_bytes = token_bytes
         self._dt = np.uint32 if token_bytes == 4 else np.uint64
         h = _P()
-        cfg = apo_server_config(min_len, token_bytes, max_batch_tokens, max_batch_windows, lanes)
+        cfg = apo_server_config(min_len, token_bytes, max_batch_tokens, max_batch_windows, lanes, hbm_budget)
         _check(lib().apo_server_create(ctypes.byref(h), device, ctypes.byref(cfg)))
         self._h = h
+
+    def memory(self) -> dict:
+        """The pool's size and the bytes batches in flight hold (now, most at once)."""
+        b, h, m = _U64(), _U64(), _U64()
+        _check(lib().apo_server_memory(self._h, ctypes.byref(b), ctypes.byref(h), ctypes.byref(m)))
+        return {"budget": int(b.value), "held": int(h.value), "held_max": int(m.value)}
+
+    @staticmethod
+    def footprint(n_tokens: int, token_bytes: int = 4, min_len: int = 5) -> int:
+        """Bytes one request of n_tokens takes from the pool when it is
+        batched alone (tokens, outputs, analysis scratch)."""
+        wo = np.array([0, n_tokens], dtype=np.uint64)
+        ws = apo_windows(1, None, token_bytes, wo.ctypes.data)
+        out = _U64()
+        _check(lib().apo_find_repeats_workspace(None, ctypes.byref(ws), ctypes.byref(out)))
+        al = lambda b: (b + 255) & ~255  # noqa: E731
+        return al(n_tokens * token_bytes + 16) + al(5 * (n_tokens // max(min_len, 1) + 1) * 4) + al(int(out.value))
 
     def submit(self, tokens) -> int:
         a = np.ascontiguousarray(np.asarray(tokens).astype(self._dt, copy=False))
@@ -643,14 +684,48 @@ class Server:
 
 
 def greedy_select_noalloc(cand_len, cand_start, n: int, accepted, accepted_count, stream=None):
-    """apo_greedy_select_noalloc: Alg. 2's greedy loop with no device
-    allocation, for callers that cannot allocate (see include/apo.h).  All
-    tensors are caller-owned device buffers: cand_len / cand_start (int32,
-    m entries, greedy order), accepted (uint8, m) and accepted_count (int32,
-    1).  Only enqueues the work on `stream`."""
+    """apo_greedy_select_noalloc, for callers that cannot allocate device
+    memory (see include/apo.h): accepted[k] = 1 iff the interval
+    [cand_start[k], cand_start[k] + cand_len[k]) meets no interval accepted
+    before it, visiting the m candidates in the order given; cand_len must not
+    increase along that order (apo_find_repeats's candidate order satisfies
+    this), and *accepted_count receives the number accepted, or 0xffffffff
+    (-1 as int32) when a length increases.
+
+    All tensors are caller-owned buffers on one CUDA device: cand_len and
+    cand_start int32 with m entries each, accepted uint8 with at least m,
+    accepted_count int32 with at least 1, all contiguous.  Anything else is
+    refused with ValueError before the library is called, so that no kernel
+    reads or writes past a buffer.  The call runs with that device current and
+    only enqueues the work on `stream`."""
+    import torch
+    named = (("cand_len", cand_len), ("cand_start", cand_start), ("accepted", accepted),
+             ("accepted_count", accepted_count))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"greedy_select_noalloc: {name} must be a torch.Tensor")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"greedy_select_noalloc: {name} must be a contiguous 1-D tensor")
+    want = {"cand_len": torch.int32, "cand_start": torch.int32, "accepted": torch.uint8,
+            "accepted_count": torch.int32}
+    for name, t in named:
+        if t.dtype != want[name]:
+            raise ValueError(f"greedy_select_noalloc: {name} must be {want[name]}, got {t.dtype}")
     m = int(cand_len.shape[0])
-    _check(lib().apo_greedy_select_noalloc(_ptr(cand_len), _ptr(cand_start), m, int(n), _ptr(accepted),
-                                           _ptr(accepted_count), _stream_handle(stream)))
+    if int(cand_start.shape[0]) != m:
+        raise ValueError(f"greedy_select_noalloc: cand_start has {cand_start.shape[0]} entries, cand_len {m}")
+    if int(accepted.shape[0]) < m:
+        raise ValueError(f"greedy_select_noalloc: accepted holds {accepted.shape[0]} entries, need {m}")
+    if int(accepted_count.shape[0]) < 1:
+        raise ValueError("greedy_select_noalloc: accepted_count needs one entry")
+    if int(n) < 0:
+        raise ValueError("greedy_select_noalloc: n must be >= 0")
+    devs = {t.device for _, t in named}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError(f"greedy_select_noalloc: all tensors must be on one CUDA device, got {sorted(map(str, devs))}")
+    with torch.cuda.device(next(iter(devs))):
+        _check(lib().apo_greedy_select_noalloc(_ptr(cand_len), _ptr(cand_start), m, int(n), _ptr(accepted),
+                                               _ptr(accepted_count), _stream_handle(stream)))
 
 
 def as_u32(t) -> np.ndarray:

@@ -50,6 +50,7 @@ struct Arena {
   size_t cap = 0;
   size_t used = 0;
   uint64_t moves = 0;  // reallocations so far
+  bool external = false;  // base/cap lie in a caller-owned workspace: never reallocated
   int reserve(size_t bytes);
   void reset() { used = 0; }
   void *take(size_t bytes);
@@ -74,6 +75,8 @@ enum : int {
   kMiscFixChanged = 26,   // two words: changes of consecutive automaton repair passes
   kMiscFlatTotal = 28,    // length of the flattened output chains
   kMiscCandUnique = 29,   // candidates left after deduplication
+  kMiscRoundTiles = 30,   // tile tickets of a doubling round
+  kMiscRoundW = 32,       // 2 x 4 words of consecutive doubling rounds (see build_suffix_array)
   kMiscCount = 64,
 };
 
@@ -93,7 +96,7 @@ enum KernelId : int {
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
   kKAcNodes, kKAcJump, kKRsTune, kKRpPieces, kKRpNeed, kKRpChain, kKRpAppear, kKRpSelect, kKRpOut,
-  kKOptimum, kKSaDict, kKCount
+  kKOptimum, kKSaDict, kKRound, kKSplit, kKWsb, kKListCompact, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 
@@ -196,6 +199,15 @@ struct apo_ctx {
   uint64_t gen = 0;                               // bumped when a workspace buffer moves
   int graph_mode = 0;                             // replay batched calls as CUDA graphs
   apo::GraphCache *graphs = nullptr;
+  // A caller-owned workspace (apo_set_workspace): look-back words at its
+  // start (zeroed up to ext_lb_bytes), the arena after them.  While one is
+  // attached the context's own arena and look-back array are set aside here.
+  char *ext = nullptr;
+  size_t ext_bytes = 0, ext_lb_bytes = 0;
+  char *own_base = nullptr;
+  size_t own_cap = 0;
+  uint64_t *own_lookback = nullptr;
+  size_t own_lookback_words = 0;
 };
 
 namespace apo {
@@ -238,6 +250,11 @@ inline uint32_t next_epoch(apo_ctx *c) {
 }
 
 int ensure_lookback(apo_ctx *c, size_t words);
+// Sizes the call's scratch: an arena of arena_bytes and a look-back array of
+// lb_words (grown with cudaMalloc, or laid out in the caller's workspace).
+int reserve_workspace(apo_ctx *c, size_t arena_bytes, size_t lb_words, cudaStream_t s);
+// Scratch of apo_find_repeats / _batched over n tokens in `windows` windows.
+void find_repeats_need(uint64_t n, uint64_t windows, size_t *arena_bytes, size_t *lb_words);
 // Grows the context's side buffer to `bytes` (waits for the stream first).
 int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s);
 int check_device_error(apo_ctx *c, cudaStream_t s);
@@ -323,10 +340,13 @@ struct SuffixState {
   uint32_t n;        // positions over all windows
   uint32_t *sa;      // global SA: window w's suffixes occupy [off[w], off[w+1])
   uint32_t *rank;
-  uint32_t **snaps;  // host array of device pointers: rank after level k
-  int levels;        // number of snapshots written
+  uint32_t **snaps;  // host array of device pointers, snaps[k] = snaps[0] + k * n: level-k ranks
+                     // of the suffixes still grouped at the start of round k (fin >= k)
+  int levels;        // number of levels written
   Windows win;
   uint32_t h0 = 1;   // tokens per initial key: level k ranks are equal iff h0 * 2^k tokens are
+  uint8_t *fin = nullptr;    // level at which each suffix became final (0xff: not yet)
+  uint32_t *wsb = nullptr;   // window-start bits (bit n set), null for one window
 };
 int build_suffix_array(apo_ctx *c, const void *tokens, int token_bytes, uint32_t n,
                        SuffixState &st, int max_levels, uint32_t *rounds_out, cudaStream_t s);

@@ -24,6 +24,11 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 int Arena::reserve(size_t bytes) {
   used = 0;
   if (bytes <= cap) return APO_OK;
+  if (external) {
+    set_error("workspace: the call needs " + std::to_string(bytes) + " bytes of scratch, the attached "
+              "workspace leaves " + std::to_string(cap));
+    return APO_ENOMEM;
+  }
   if (base) {
     cudaDeviceSynchronize();
     cudaFree(base);
@@ -51,6 +56,11 @@ void *Arena::take(size_t bytes) {
 
 int ensure_lookback(apo_ctx *c, size_t words) {
   if (words <= c->ps.lookback_words) return APO_OK;
+  if (c->ext) {
+    set_error("workspace: a launch needs " + std::to_string(words) + " look-back words, the attached "
+              "workspace's reservation holds " + std::to_string(c->ps.lookback_words));
+    return APO_ENOMEM;
+  }
   // Growing frees the old array: wait for launches that may still read it.
   APO_CUDA_TRY(cudaDeviceSynchronize());
   if (c->ps.lookback) cudaFree(c->ps.lookback);
@@ -64,8 +74,47 @@ int ensure_lookback(apo_ctx *c, size_t words) {
   return APO_OK;
 }
 
+int reserve_workspace(apo_ctx *c, size_t arena_bytes, size_t lb_words, cudaStream_t s) {
+  if (!c->ext) {
+    APO_TRY(ensure_lookback(c, lb_words));
+    return c->arena.reserve(arena_bytes);
+  }
+  const size_t lb_bytes = (lb_words * 8 + 255) & ~(size_t)255;
+  if (lb_bytes + arena_bytes > c->ext_bytes) {
+    set_error("workspace: the call needs " + std::to_string(lb_bytes + arena_bytes) + " bytes, " +
+              std::to_string(c->ext_bytes) + " are attached (apo_find_repeats_workspace gives the size)");
+    return APO_ENOMEM;
+  }
+  if (lb_bytes > c->ext_lb_bytes) {
+    // the look-back words must start out clear (earlier calls may have used
+    // these bytes as arena); queued ahead of the call's kernels
+    APO_CUDA_TRY(cudaMemsetAsync(c->ext, 0, lb_bytes, s));
+    c->ext_lb_bytes = lb_bytes;
+    ++c->gen;
+  }
+  c->ps.lookback = reinterpret_cast<uint64_t *>(c->ext);
+  c->ps.lookback_words = c->ext_lb_bytes / 8;
+  c->arena.base = c->ext + c->ext_lb_bytes;
+  c->arena.cap = c->ext_bytes - c->ext_lb_bytes;
+  c->arena.used = 0;
+  return arena_bytes <= c->arena.cap ? APO_OK : c->arena.reserve(arena_bytes);
+}
+
+void find_repeats_need(uint64_t n, uint64_t windows, size_t *arena_bytes, size_t *lb_words) {
+  *arena_bytes = suffix_workspace_bytes(n) + repeats_workspace_bytes(n, windows) + (size_t)n * 24 +
+                 (size_t)(windows + 1) * 4 + ((size_t)1 << 20);  // + slack for 256-byte alignment
+  // the widest look-back of the call: a radix pass over at most 2n pairs in
+  // tiles of at least 1024 with 512 digits
+  *lb_words = ((size_t)(2 * n + 1023) / 1024 + 2) * 512 + ((size_t)1 << 16);
+}
+
 int ensure_side(apo_ctx *c, size_t bytes, cudaStream_t s) {
   if (bytes <= c->side_bytes) return APO_OK;
+  if (c->ext) {
+    set_error("workspace: this call needs scratch outside the attached workspace (" + std::to_string(bytes) +
+              " bytes); detach it with apo_set_workspace(ctx, NULL, 0)");
+    return APO_ENOMEM;
+  }
   APO_CUDA_TRY(cudaStreamSynchronize(s));
   if (c->side) cudaFree(c->side);
   c->side = nullptr;
@@ -86,7 +135,7 @@ const char *const kKernelNames[kKCount] = {
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
-    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict"};
+    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {
@@ -193,7 +242,7 @@ int apo_create(apo_ctx **out, int device) {
   }
   if (cudaMalloc(&c->ps.err, sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&c->ps.counters, kCtrWords * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMallocHost(&c->host_pinned, 64) != cudaSuccess) {
+      cudaMallocHost(&c->host_pinned, 256) != cudaSuccess) {
     cudaGetLastError();
     apo_destroy(c);
     set_error("apo_create: device allocation failed");
@@ -221,6 +270,7 @@ int apo_destroy(apo_ctx *c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   graph_cache_free(c);
+  if (c->ext) apo_set_workspace(c, nullptr, 0);  // frees the context's own buffers, not the caller's
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->ps.err) cudaFree(c->ps.err);
   if (c->ps.lookback) cudaFree(c->ps.lookback);
@@ -234,6 +284,59 @@ int apo_destroy(apo_ctx *c) {
     if (e) cudaEventDestroy(e);
   c->prof.release();
   delete c;
+  return APO_OK;
+}
+
+int apo_find_repeats_workspace(apo_ctx *c, const apo_windows *ws, uint64_t *bytes) {
+  (void)c;  // the size depends on the windows only
+  if (!ws || !bytes || !ws->win_off || ws->n_windows == 0) {
+    set_error("apo_find_repeats_workspace: null argument or no windows");
+    return APO_EINVAL;
+  }
+  const uint64_t n = ws->win_off[ws->n_windows];
+  if (n > 0x7fffffffull) {
+    set_error("apo_find_repeats_workspace: at most 2^31 - 1 tokens per call");
+    return APO_EINVAL;
+  }
+  size_t arena_bytes = 0, lb_words = 0;
+  find_repeats_need(n, ws->n_windows, &arena_bytes, &lb_words);
+  *bytes = ((lb_words * 8 + 255) & ~(size_t)255) + arena_bytes;
+  return APO_OK;
+}
+
+int apo_set_workspace(apo_ctx *c, void *workspace, uint64_t bytes) {
+  if (!c || (workspace && bytes < 4096) || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+    set_error("apo_set_workspace: null context, a workspace under 4096 bytes or not 256-byte aligned");
+    return APO_EINVAL;
+  }
+  APO_CUDA_TRY(cudaSetDevice(c->device));
+  if (!c->ext && workspace) {  // set the context's own buffers aside
+    c->own_base = c->arena.base;
+    c->own_cap = c->arena.cap;
+    c->own_lookback = c->ps.lookback;
+    c->own_lookback_words = c->ps.lookback_words;
+  }
+  if (c->ext && !workspace) {  // back to the context's own buffers
+    c->arena.base = c->own_base;
+    c->arena.cap = c->own_cap;
+    c->ps.lookback = c->own_lookback;
+    c->ps.lookback_words = c->own_lookback_words;
+    c->own_base = nullptr;
+    c->own_lookback = nullptr;
+  }
+  c->ext = static_cast<char *>(workspace);
+  c->ext_bytes = workspace ? bytes : 0;
+  c->ext_lb_bytes = 0;
+  c->arena.external = workspace != nullptr;
+  if (workspace) {
+    c->arena.base = c->ext;
+    c->arena.cap = c->ext_bytes;
+    c->ps.lookback = nullptr;
+    c->ps.lookback_words = 0;
+  }
+  c->arena.used = 0;
+  ++c->arena.moves;
+  ++c->gen;
   return APO_OK;
 }
 
@@ -309,8 +412,11 @@ int find_repeats_driver(apo_ctx *c, const void *tokens, int tb, uint64_t total,
     return APO_OK;
   }
   APO_CUDA_TRY(cudaSetDevice(c->device));
-  APO_TRY(c->arena.reserve(suffix_workspace_bytes(n) + repeats_workspace_bytes(n, nwin) +
-                           (size_t)n * 24 + (size_t)(nwin + 1) * 4));
+  {
+    size_t arena_bytes = 0, lb_words = 0;
+    find_repeats_need(n, nwin, &arena_bytes, &lb_words);
+    APO_TRY(reserve_workspace(c, arena_bytes, lb_words, s));
+  }
   SuffixState st;
   st.n = n;
   st.sa = c->arena.take_n<uint32_t>(n);

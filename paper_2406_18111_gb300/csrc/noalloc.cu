@@ -39,14 +39,18 @@ __device__ __forceinline__ bool is_marked(const uint32_t *bits, uint32_t x) {
 // One block visits the candidates in order, 1024 at a time: those whose first
 // or last position is already marked are rejected in parallel (lengths never
 // increase along the order, so that test is exact), and one warp settles the
-// remaining ones in order, marking each accepted interval.
+// remaining ones in order, marking each accepted interval.  A length that
+// increases along the order breaks that exactness; it is detected and
+// reported as a count of 0xffffffff.
 __global__ void __launch_bounds__(kT, 1) k_greedy_noalloc(const uint32_t *__restrict__ cl,
                                                           const uint32_t *__restrict__ cs,
                                                           uint32_t m, uint32_t n, uint32_t *bits,
                                                           uint8_t *acc, uint32_t *count) {
   __shared__ uint32_t s_l[kT], s_s[kT], s_k[kT];
   __shared__ uint32_t s_wc[32], s_off[32], s_total;
+  __shared__ int s_rising;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_rising = 0;
   for (uint32_t w = tid; w < (n + 31) / 32; w += kT) bits[w] = 0;  // left over from the last call
   uint32_t nacc = 0;
   __syncthreads();
@@ -58,6 +62,7 @@ __global__ void __launch_bounds__(kT, 1) k_greedy_noalloc(const uint32_t *__rest
       l = cl[k];
       s = cs[k];
       acc[k] = 0;
+      if (k > 0 && l > cl[k - 1]) s_rising = 1;
       surv = l > 0 && (uint64_t)s + l <= n && !is_marked(bits, s) && !is_marked(bits, s + l - 1);
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, surv);
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(kT, 1) k_greedy_noalloc(const uint32_t *__rest
     }
     __syncthreads();
   }
-  if (tid == 0) *count = nacc;
+  if (tid == 0) *count = s_rising ? 0xffffffffu : nacc;
 }
 
 }  // namespace

@@ -438,7 +438,9 @@ int sort_plan(apo_ctx *c, uint32_t n, const DigitRange *ranges, int nranges, Sor
       std::lock_guard<std::mutex> lk(g_table_mu);
       id = tb.choice[cls][bits];
     }
-    if (id < 0) {
+    if (id < 0 && c->ext) {
+      id = 0;  // a caller workspace: no trial buffers, the default shape until the class is tuned
+    } else if (id < 0) {
       APO_TRY(tune(c, n, bits, cls, s));
       std::lock_guard<std::mutex> lk(g_table_mu);
       id = tb.choice[cls][bits];

@@ -1,20 +1,32 @@
-// The served form: continuous batching of repeat-finding requests.
+// The served form: continuous batching of repeat-finding requests, admitted
+// by device-memory footprint.
 //
 // Alg. 1 hands each history slice to an asynchronous FindRepeats while the
 // application keeps issuing tasks, and ingests results as they complete.
 // Here requests arrive through apo_server_submit at any time.  Each lane (a
 // worker thread with its own context and stream) repeatedly takes the
-// requests waiting at that moment, in arrival order, up to the admission
-// budget (tokens per batch, which bounds the batch's device footprint) and a
-// window count, concatenates them into pinned memory, runs the batched
-// analysis and publishes each request's slice of the results.  With several
-// lanes, one batch computes while the next is being formed and copied, and
-// their kernels overlap on the device; a request arriving while batches run
-// joins the next batch any lane forms.
+// requests waiting at that moment, in arrival order, concatenates them into
+// pinned memory, runs the batched analysis and publishes each request's slice
+// of the results.  With several lanes, one batch computes while the next is
+// being formed and copied, and their kernels overlap on the device; a request
+// arriving while batches run joins the next batch any lane forms.
+//
+// Admission by footprint.  The server owns one device pool of hbm_budget
+// bytes, allocated once.  A batch's footprint is its tokens, its output
+// arrays and the scratch apo_find_repeats_workspace reports for its windows;
+// a lane carves one slice of that size from the pool (first fit) and hands
+// the scratch part to its context with apo_set_workspace, so the batches in
+// flight never hold more than the budget together.  A lane grows its batch
+// request by request while the bigger footprint still fits in a free slice
+// (and within max_batch_tokens / max_batch_windows); when not even the first
+// waiting request fits, the lane waits until a finishing batch returns its
+// slice.  A request whose footprint exceeds the whole budget fails with
+// APO_ECAPACITY.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -38,24 +50,44 @@ struct Request {
   uint64_t batch_windows = 0;
 };
 
-template <class T>
-struct DevBuf {  // grow-only device buffer
-  T *p = nullptr;
-  size_t cap = 0;
-  int ensure(size_t n) {
-    if (n <= cap) return APO_OK;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      return APO_ENOMEM;
-    }
-    cap = n;
-    return APO_OK;
+// First-fit allocator over the pool (offsets, 256-byte granules); free
+// ranges are coalesced with their neighbours.
+struct Pool {
+  uint64_t cap = 0;
+  std::map<uint64_t, uint64_t> free_;  // offset -> size
+  void init(uint64_t bytes) {
+    cap = bytes;
+    free_.clear();
+    if (bytes) free_[0] = bytes;
   }
-  ~DevBuf() {
-    if (p) cudaFree(p);
+  bool take(uint64_t bytes, uint64_t *off) {
+    bytes = (bytes + 255) & ~255ull;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const uint64_t rest = it->second - bytes;
+      const uint64_t at = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[at] = rest;
+      return true;
+    }
+    return false;
+  }
+  void give(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~255ull;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
   }
 };
 
@@ -72,10 +104,28 @@ struct apo_server {
   uint64_t next_id = 1;
   bool stopping = false;
   std::vector<std::thread> lanes;
+  char *pool_base = nullptr;
+  Pool pool;
+  uint64_t in_flight = 0;           // batches holding a slice
+  uint64_t held = 0, held_max = 0;  // bytes held by them (now, most so far)
+  uint64_t pool_gen = 0;            // bumped whenever a slice is returned
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
   void lane_main();
+  uint64_t footprint(const std::vector<uint64_t> &win_off) const;
 };
+
+// Tokens, five output arrays of total / min_len + 1 entries, and the
+// analysis scratch of these windows (each part 256-byte aligned).
+uint64_t apo_server::footprint(const std::vector<uint64_t> &win_off) const {
+  const uint64_t W = win_off.size() - 1, total = win_off[W];
+  const uint64_t K = total / std::max<uint32_t>(cfg.min_len, 1) + 1;
+  apo_windows ws{W, nullptr, cfg.token_bytes, win_off.data()};
+  uint64_t scratch = 0;
+  apo_find_repeats_workspace(nullptr, &ws, &scratch);
+  auto al = [](uint64_t b) { return (b + 255) & ~255ull; };
+  return al(total * cfg.token_bytes + 16) + al(5 * K * 4) + al(scratch);
+}
 
 void apo_server::lane_main() {
   cudaSetDevice(device);
@@ -86,30 +136,89 @@ void apo_server::lane_main() {
   const int tb = cfg.token_bytes;
   uint8_t *host_in = nullptr;
   size_t host_cap = 0;
-  DevBuf<uint8_t> d_tok;
-  DevBuf<uint32_t> d_out;
   std::vector<uint32_t> h_out;
-  std::vector<uint64_t> win_off, sel_off, trace_off;
+  std::vector<uint64_t> win_off, trial, sel_off, trace_off;
   while (true) {
     std::vector<std::shared_ptr<Request>> batch;
+    std::vector<std::shared_ptr<Request>> refused;
+    uint64_t slice_off = 0, slice_bytes = 0;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stopping || !pending.empty(); });
-      if (pending.empty()) break;  // stopping and drained
-      uint64_t tokens = 0;
-      while (!pending.empty() && batch.size() < cfg.max_batch_windows) {
-        const auto &r = pending.front();
-        if (!batch.empty() && tokens + r->n > cfg.max_batch_tokens) break;
-        tokens += r->n;
-        batch.push_back(r);
-        pending.pop_front();
+      while (true) {
+        cv_work.wait(lk, [&] { return stopping || !pending.empty(); });
+        if (pending.empty()) break;  // stopping and drained
+        // grow the batch in arrival order while its footprint still fits
+        win_off.assign(1, 0);
+        uint64_t fit = 0, off = 0;
+        size_t take = 0;
+        while (take < pending.size() && take < cfg.max_batch_windows) {
+          const uint64_t n = pending[take]->n;
+          if (take > 0 && win_off.back() + n > cfg.max_batch_tokens) break;
+          trial = win_off;
+          trial.push_back(win_off.back() + n);
+          const uint64_t need = footprint(trial);
+          if (take == 0 && need > pool.cap) {  // can never fit: refuse it
+            refused.push_back(pending.front());
+            pending.pop_front();
+            continue;
+          }
+          if (take > 0) pool.give(off, fit);  // the larger slice replaces the smaller one
+          uint64_t o = 0;
+          if (!pool.take(need, &o)) {
+            if (take > 0 && !pool.take(fit, &off)) take = 0;  // (cannot fail: that space was just free)
+            break;
+          }
+          off = o;
+          fit = need;
+          win_off.swap(trial);
+          ++take;
+        }
+        if (take == 0) {
+          if (!refused.empty()) break;  // publish the refusals
+          // the first waiting request does not fit next to the batches in
+          // flight: wait until one of them returns its slice
+          const uint64_t g0 = pool_gen;
+          cv_work.wait(lk, [&] { return in_flight == 0 || pool_gen != g0; });
+          continue;
+        }
+        for (size_t k = 0; k < take; ++k) {
+          batch.push_back(pending.front());
+          pending.pop_front();
+        }
+        slice_off = off;
+        slice_bytes = fit;
+        ++in_flight;
+        held += fit;
+        held_max = std::max(held_max, held);
+        break;
       }
+    }
+    if (!refused.empty()) {
+      const double t = now();
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto &r : refused) {
+        r->status = APO_ECAPACITY;
+        r->t_start = r->t_done = t;
+        r->done = true;
+        r->tokens.clear();
+        r->tokens.shrink_to_fit();
+      }
+      cv_done.notify_all();
+    }
+    if (batch.empty()) {
+      if (refused.empty()) break;  // stopping and drained
+      continue;
     }
     const double t_start = now();
     const size_t W = batch.size();
-    win_off.assign(W + 1, 0);
-    for (size_t w = 0; w < W; ++w) win_off[w + 1] = win_off[w] + batch[w]->n;
     const uint64_t total = win_off[W];
+    const uint64_t K = total / std::max<uint32_t>(cfg.min_len, 1) + 1;
+    auto al = [](uint64_t b) { return (b + 255) & ~255ull; };
+    char *slice = pool_base + slice_off;
+    uint8_t *d_tok = reinterpret_cast<uint8_t *>(slice);
+    uint32_t *d_out = reinterpret_cast<uint32_t *>(slice + al(total * tb + 16));
+    char *scratch = slice + al(total * tb + 16) + al(5 * K * 4);
+    const uint64_t scratch_bytes = slice_bytes - (uint64_t)(scratch - slice);
     int st = ctx ? APO_OK : APO_ECUDA;
     if (st == APO_OK && total * tb > host_cap) {
       if (host_in) cudaFreeHost(host_in);
@@ -121,27 +230,25 @@ void apo_server::lane_main() {
         st = APO_ENOMEM;
       }
     }
-    const uint64_t K = total / std::max<uint32_t>(cfg.min_len, 1) + 1;
-    if (st == APO_OK) st = d_tok.ensure(total * tb + 1);
-    if (st == APO_OK) st = d_out.ensure(5 * K);
+    if (st == APO_OK) st = apo_set_workspace(ctx, scratch, scratch_bytes);
     uint64_t counts[4] = {0, 0, 0, 0};
     if (st == APO_OK) {
       for (size_t w = 0; w < W; ++w)
         memcpy(host_in + win_off[w] * tb, batch[w]->tokens.data(), batch[w]->n * tb);
-      if (cudaMemcpyAsync(d_tok.p, host_in, total * tb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      if (cudaMemcpyAsync(d_tok, host_in, total * tb, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         st = APO_ECUDA;
     }
     if (st == APO_OK) {
       sel_off.assign(W + 1, 0);
       trace_off.assign(W + 1, 0);
-      apo_windows ws{W, d_tok.p, tb, win_off.data()};
+      apo_windows ws{W, d_tok, tb, win_off.data()};
       apo_repeats_params pr{cfg.min_len, 0};
       apo_repeats_out o{};
-      o.sel_start = d_out.p;
-      o.sel_len = d_out.p + K;
-      o.sel_trace = d_out.p + 2 * K;
-      o.trace_len = d_out.p + 3 * K;
-      o.trace_start = d_out.p + 4 * K;
+      o.sel_start = d_out;
+      o.sel_len = d_out + K;
+      o.sel_trace = d_out + 2 * K;
+      o.trace_len = d_out + 3 * K;
+      o.trace_start = d_out + 4 * K;
       o.sel_cap = o.trace_cap = K;
       o.counts = counts;
       o.sel_off = sel_off.data();
@@ -151,12 +258,13 @@ void apo_server::lane_main() {
     if (st == APO_OK) {
       h_out.resize(5 * K);
       for (int a = 0; a < 5 && st == APO_OK; ++a)
-        if (cudaMemcpyAsync(h_out.data() + a * K, d_out.p + a * K,
+        if (cudaMemcpyAsync(h_out.data() + a * K, d_out + a * K,
                             (a < 3 ? counts[1] : counts[2]) * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                             stream) != cudaSuccess)
           st = APO_ECUDA;
       if (cudaStreamSynchronize(stream) != cudaSuccess) st = APO_ECUDA;
     }
+    if (ctx) apo_set_workspace(ctx, nullptr, 0);  // the stream is idle: the slice goes back
     const double t_done = now();
     std::lock_guard<std::mutex> lk(mu);
     for (size_t w = 0; w < W; ++w) {
@@ -177,7 +285,12 @@ void apo_server::lane_main() {
       r.tokens.clear();
       r.tokens.shrink_to_fit();
     }
+    pool.give(slice_off, slice_bytes);
+    --in_flight;
+    held -= slice_bytes;
+    ++pool_gen;
     cv_done.notify_all();
+    cv_work.notify_all();  // lanes waiting for memory
   }
   if (host_in) cudaFreeHost(host_in);
   if (stream) cudaStreamDestroy(stream);
@@ -217,9 +330,19 @@ int apo_server_create(apo_server **out, int device, const apo_server_config *cfg
                    "token_bytes 4 or 8)");
     return APO_EINVAL;
   }
+  APO_CUDA_TRY(cudaSetDevice(device));
   auto *s = new apo_server();
   s->device = device;
   s->cfg = *cfg;
+  if (s->cfg.hbm_budget == 0) s->cfg.hbm_budget = (uint64_t)16 << 30;
+  if (cudaMalloc(&s->pool_base, s->cfg.hbm_budget) != cudaSuccess) {
+    cudaGetLastError();
+    apo::set_error("apo_server_create: cudaMalloc of the " + std::to_string(s->cfg.hbm_budget) +
+                   "-byte pool failed");
+    delete s;
+    return APO_ENOMEM;
+  }
+  s->pool.init(s->cfg.hbm_budget);
   s->t0 = Clock::now();
   for (uint32_t l = 0; l < cfg->lanes; ++l) s->lanes.emplace_back([s] { s->lane_main(); });
   *out = s;
@@ -292,6 +415,15 @@ int apo_server_release(apo_server *s, uint64_t id) {
 
 double apo_server_now(apo_server *s) { return s ? s->now() : 0.0; }
 
+int apo_server_memory(apo_server *s, uint64_t *budget, uint64_t *held, uint64_t *held_max) {
+  if (!s) return APO_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (budget) *budget = s->cfg.hbm_budget;
+  if (held) *held = s->held;
+  if (held_max) *held_max = s->held_max;
+  return APO_OK;
+}
+
 int apo_server_destroy(apo_server *s) {
   if (!s) return APO_OK;
   {
@@ -300,6 +432,8 @@ int apo_server_destroy(apo_server *s) {
   }
   s->cv_work.notify_all();
   for (auto &t : s->lanes) t.join();
+  cudaSetDevice(s->device);
+  if (s->pool_base) cudaFree(s->pool_base);
   delete s;
   return APO_OK;
 }

@@ -1,24 +1,45 @@
 // Suffix array by prefix doubling, and the LCP array by Phi / PLCP.
 //
 // Alg. 2 starts with SuffixArray(S) -> SA, LCP.  The suffix array is built
-// by prefix doubling (Manber & Myers 1993) on the GPU in the style of
-// Larsson & Sadakane: a suffix's rank is the SA position where its group of
-// suffixes with an equal 2^r-token prefix starts.  Round r sorts only the
-// suffixes whose group is not yet a singleton, by the key
-// (rank[i], rank[i+h] + 1) with h = 2^r (0 when i + h runs past the end, so
-// a proper prefix sorts first), with the onesweep radix sort.  The active
-// suffixes are kept in SA order, so the k-th sorted key takes the k-th
-// smallest active SA position: no segment bookkeeping is needed.  A single
-// refresh kernel then finds the new group heads, writes SA and ranks, and
-// compacts the suffixes that still share a group (one decoupled look-back
-// max-scan for the head positions, one sum-scan for the compaction).
+// by prefix doubling (Manber & Myers 1993) in the style of Larsson &
+// Sadakane: a suffix's level-L rank is the SA slot where its group of
+// suffixes sharing the first h0 * 2^L tokens starts, and a suffix alone in
+// its group has its final slot.
 //
-// Each round's rank array is kept ("level" r ranks: equal iff the first 2^r
-// tokens are equal).  The LCP array follows Karkkainen, Manzini & Puglisi
-// (CPM 2009): Phi[SA[k]] = SA[k-1]; PLCP[i] = lcp(i, Phi[i]) >= PLCP[i-1] - 1
-// is computed in chunks with direct token comparison, and a match that keeps
-// going is finished in O(levels) steps by binary lifting over the kept ranks;
-// finally LCP[k] = PLCP[SA[k+1]] (LCP[k] pairs SA[k] with SA[k+1]).
+// Level 0 comes from one radix sort of the first h0 tokens of every suffix
+// (dense token codes packed into a 64-bit key under the window id).  Each
+// later round r refines the groups that are not yet singletons by the minor
+// key rank_{r-1}[i + h] + 1 (0 when i + h is past the window's end), h =
+// h0 * 2^(r-1).  The groups are already in order, so a round only has to
+// sort each group by its minor keys:
+//
+//   * The active suffixes form a list of (suffix, group head slot) entries,
+//     each group contiguous.  k_round cuts the list into tiles of kRdT
+//     entries; a tile owns the groups that start in it.  A group of at most
+//     kRdT entries is gathered, sorted by (group, minor) in shared memory and
+//     settled by its owner in one pass over its entries: no key leaves the
+//     chip.  Whether a group is larger than kRdT is read off one entry kRdT
+//     places after its start, so no scan over group sizes is needed.
+//   * Larger groups ("big") are written as (big-group ordinal, minor) keys
+//     and sorted by the onesweep radix sort; k_split then settles them.
+//
+// Settling a sorted group: its subgroups of equal minor keys start at the
+// slots head + (position in the group); a subgroup of one suffix is final
+// (SA, final rank, level recorded in fin[]); the others form the next list.
+//
+// Level ranks for the LCP.  Every round writes the new level rank of each
+// of its active suffixes into that level's snapshot array and nothing else,
+// so snaps[L][i] is valid exactly when suffix i was still grouped at the
+// start of round L (fin[i] >= L); earlier-final suffixes keep their final
+// slot in rank[i].  level_rank(L, i) therefore reads fin[i] first.  A round
+// reads only the previous level and final ranks, which no kernel of the
+// same round writes, so rounds need no copies of the rank array.
+//
+// The LCP array follows Karkkainen, Manzini & Puglisi (CPM 2009):
+// Phi[SA[k]] = SA[k-1]; PLCP[i] = lcp(i, Phi[i]) >= PLCP[i-1] - 1 is
+// computed in chunks by direct token comparison, and a match that keeps
+// going is finished in O(levels) steps by binary lifting over the level
+// ranks; finally LCP[k] = PLCP[SA[k+1]] (LCP[k] pairs SA[k] with SA[k+1]).
 #include <algorithm>
 #include <cstring>
 
@@ -29,11 +50,8 @@ namespace apo {
 
 namespace {
 
-constexpr int kRT = 256;            // refresh threads per block
-constexpr int kRI = 4;              // consecutive elements per thread
-constexpr int kRTile = kRT * kRI;   // 1024
 constexpr uint32_t kNone = 0xffffffffu;
-constexpr size_t kRefreshSmem = (size_t)(kRTile + 2) * 8 + (size_t)kRTile * 8;
+constexpr uint32_t kHole = 0xfffffffeu;  // head of a place in the holed next list that holds no entry
 
 __global__ void k_init_keys(const void *__restrict__ tokens, int tb, uint32_t n,
                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
@@ -44,69 +62,109 @@ __global__ void k_init_keys(const void *__restrict__ tokens, int tb, uint32_t n,
   }
 }
 
-// Sorted (key, suffix) pairs of the active suffixes -> new group heads, SA,
-// ranks and the next active list.  actpos == nullptr means position = index
-// (the first call, where the sorted list is the whole SA).  Only a suffix
-// whose group became a singleton has reached its final SA position, so only
-// it writes SA; a rank is written only when it changed (with old_sh >= 0 the
-// old rank is key >> old_sh; a group's first subgroup keeps its start).
-// Both cut scattered 4-byte writes, each of which costs a whole sector.
-__global__ void __launch_bounds__(kRT) k_refresh(
-    const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx, uint32_t A,
-    const uint32_t *__restrict__ A_dev, const uint32_t *__restrict__ actpos, int old_sh,
-    uint32_t *__restrict__ sa, uint32_t *__restrict__ rank, uint32_t *__restrict__ act_next,
-    uint32_t *__restrict__ pos_next, uint32_t n, uint32_t *count_out, uint64_t *st_max, uint64_t *st_sum,
-    uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint64_t *sk = reinterpret_cast<uint64_t *>(smem);           // [kRTile + 2], key[base-1 ..]
-  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kRTile + 2);  // [kRTile]
-  uint32_t *sp = si + kRTile;                                     // [kRTile]
+// out[0] |= every token, out[1] = max(out[1], every token).
+__global__ void k_token_or(const void *__restrict__ tokens, int tb, uint32_t n, unsigned long long *out) {
+  uint64_t acc = 0, mx = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t k = tb == 4 ? (uint64_t) static_cast<const uint32_t *>(tokens)[i]
+                               : static_cast<const uint64_t *>(tokens)[i];
+    acc |= k;
+    mx = k > mx ? k : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    const uint64_t m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && acc) {
+    atomicOr(out, (unsigned long long)acc);
+    atomicMax(out + 1, (unsigned long long)mx);
+  }
+}
+
+__device__ __forceinline__ bool bit_at(const uint32_t *__restrict__ bits, uint32_t j) {
+  return (__ldg(bits + (j >> 5)) >> (j & 31)) & 1u;
+}
+
+// Level-L rank of suffix j: its final slot when it was settled before level
+// L, else the level's snapshot.
+__device__ __forceinline__ uint32_t level_rank(const uint8_t *__restrict__ fin, const uint32_t *__restrict__ rank,
+                                               const uint32_t *__restrict__ snap, uint32_t L, uint32_t j) {
+  const uint32_t f = fin[j];
+  return f < L ? rank[j] : snap[j];
+}
+
+// ---------------------------------------------------------------- settling sorted groups
+// Sorted (key, suffix) pairs -> groups of equal keys.  Every suffix gets its
+// level rank (the slot where its group starts) in snap; with `finals` a
+// suffix alone in its group is settled (sa, rank, fin = level).
+//   kBig false (the first sort): the slot of sorted element q is q; the
+//   suffixes not alone are appended, group by group, to the list (nid, nhd),
+//   whose length lands in *count_out.
+//   kBig true (big groups sorted by (ordinal o = key >> ord_shift, minor)):
+//   group o's sorted elements start at bg_off[o], its slots at bg_head[o],
+//   and its list entries at bg_pos[o]; a suffix not alone is written in
+//   place to the holed next list (nid, nhd), a singleton's place becomes a
+//   hole.
+// Decoupled look-backs: the last group start (max) and, for kBig false, the
+// list position (sum).
+constexpr int kST = 256, kSI = 4, kSTile = kST * kSI;
+
+template <bool kBig>
+__global__ void __launch_bounds__(kST) k_split(
+    const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, uint32_t ub,
+    const uint32_t *__restrict__ n_dev, int ord_shift, const uint32_t *__restrict__ bg_head,
+    const uint32_t *__restrict__ bg_off, const uint32_t *__restrict__ bg_pos, uint32_t bg_cap, uint32_t level,
+    int finals, uint32_t *__restrict__ snap, uint32_t *__restrict__ sa, uint32_t *__restrict__ rank,
+    uint8_t *__restrict__ fin, uint32_t *__restrict__ nid, uint32_t *__restrict__ nhd, uint32_t list_cap,
+    uint32_t *count_out, uint32_t n, uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr, uint32_t epoch,
+    uint32_t *err) {
+  __shared__ uint64_t sk[kSTile + 2];  // key of element base - 1 + q
+  __shared__ uint32_t sv[kSTile];
   __shared__ uint32_t s_tile, s_pmax, s_psum;
-  __shared__ uint32_t scr[kRT / 32];
+  __shared__ uint32_t scr[kST / 32];
   const int tid = threadIdx.x;
-  if (A_dev) A = min(A, *A_dev);  // the launch is sized for an upper bound
+  const uint32_t N = n_dev ? min(ub, *n_dev) : ub;
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
   const uint32_t t = s_tile;
-  const uint64_t base = (uint64_t)t * kRTile;
-  if (base >= A) return;  // past the device-side count: no later tile looks at it
-  const uint32_t cnt = (A - base) < (uint64_t)kRTile ? (uint32_t)(A - base) : (uint32_t)kRTile;
-  for (uint32_t q = tid; q < cnt + 2; q += kRT) {
+  const uint64_t base = (uint64_t)t * kSTile;
+  if (base >= N) return;  // past the device-side count: no later tile looks at it
+  const uint32_t cnt = (N - base) < (uint64_t)kSTile ? (uint32_t)(N - base) : (uint32_t)kSTile;
+  for (uint32_t q = tid; q < cnt + 2; q += kST) {
     const long long g = (long long)base - 1 + q;
-    sk[q] = (g >= 0 && g < (long long)A) ? keys[g] : 0;
+    sk[q] = (g >= 0 && g < (long long)N) ? keys[g] : 0;
   }
-  for (uint32_t q = tid; q < cnt; q += kRT) {
-    si[q] = idx[base + q];
-    sp[q] = actpos ? actpos[base + q] : (uint32_t)(base + q);
-  }
+  for (uint32_t q = tid; q < cnt; q += kST) sv[q] = vals[base + q];
   __syncthreads();
 
-  const uint32_t e0 = tid * kRI;
-  uint32_t hb = 0;  // bit i: element e0+i starts a group (bit kRI: the element after)
+  const uint32_t e0 = tid * kSI;
+  uint32_t hb = 0;  // bit i: element e0 + i starts a group (bit kSI: the element after)
 #pragma unroll
-  for (int i = 0; i <= kRI; ++i) {
+  for (int i = 0; i <= kSI; ++i) {
     const uint32_t local = e0 + i;
     if (local <= cnt) {
       const uint64_t g = base + local;
-      if (g == 0 || g == A || sk[local + 1] != sk[local]) hb |= 1u << i;
+      if (g == 0 || g == N || sk[local + 1] != sk[local]) hb |= 1u << i;
     }
   }
   uint32_t tmax = 0, tcnt = 0;
   bool thead = false;
 #pragma unroll
-  for (int i = 0; i < kRI; ++i) {
+  for (int i = 0; i < kSI; ++i) {
     if (e0 + i < cnt) {
       const bool h = (hb >> i) & 1u;
       if (h) {
-        tmax = sp[e0 + i];
+        tmax = (uint32_t)(base + e0 + i);
         thead = true;
       }
       if (!(h && ((hb >> (i + 1)) & 1u))) ++tcnt;
     }
   }
   uint32_t tot_max, tot_sum;
-  const uint32_t ex_max = block_exclusive<kRT / 32>(tmax, OpMax(), 0u, scr, &tot_max);
-  const uint32_t ex_sum = block_exclusive<kRT / 32>(tcnt, OpSum(), 0u, scr, &tot_sum);
+  const uint32_t ex_max = block_exclusive<kST / 32>(tmax, OpMax(), 0u, scr, &tot_max);
+  const uint32_t ex_sum = kBig ? 0u : block_exclusive<kST / 32>(tcnt, OpSum(), 0u, scr, &tot_sum);
   const int any_head = __syncthreads_or(thead);
   if (tid == 0) {
     const bool incl = t == 0 || any_head;
@@ -116,7 +174,7 @@ __global__ void __launch_bounds__(kRT) k_refresh(
     if (!incl) lb_store(&st_max[t], lb_pack(kLbInclusive, epoch, max(pm, tot_max)));
     s_pmax = pm;
   }
-  if (tid == 32) {
+  if (!kBig && tid == 32) {
     lb_store(&st_sum[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot_sum));
     uint32_t ps = 0;
     if (t > 0) {
@@ -124,35 +182,54 @@ __global__ void __launch_bounds__(kRT) k_refresh(
       lb_store(&st_sum[t], lb_pack(kLbInclusive, epoch, ps + tot_sum));
     }
     s_psum = ps;
-    if (base + cnt == A) *count_out = ps + tot_sum;
+    if (finals && base + cnt == N) *count_out = ps + tot_sum;
   }
   __syncthreads();
-  uint32_t rm = max(s_pmax, ex_max);
-  uint32_t rs = s_psum + ex_sum;
+  uint32_t hq = max(s_pmax, ex_max);  // index of the current group's first element
+  uint32_t rs = kBig ? 0u : s_psum + ex_sum;
 #pragma unroll
-  for (int i = 0; i < kRI; ++i) {
+  for (int i = 0; i < kSI; ++i) {
     const uint32_t local = e0 + i;
-    if (local < cnt) {
-      const bool h = (hb >> i) & 1u;
-      const uint32_t p = sp[local];
-      if (h) rm = p;
-      const uint32_t id = si[local];
-      if (p >= n || id >= n) {
+    if (local >= cnt) break;
+    const bool h = (hb >> i) & 1u;
+    const uint32_t q = (uint32_t)(base + local);
+    if (h) hq = q;
+    const uint32_t id = sv[local];
+    uint32_t slot = q, head = hq, at = 0;
+    if (kBig) {
+      const uint32_t o = (uint32_t)(sk[local + 1] >> ord_shift);
+      if (o >= bg_cap) {
         atomicExch(err, kDevRange);
         continue;
       }
-      const bool single = h && ((hb >> (i + 1)) & 1u);
-      if (single) sa[p] = id;
-      if (old_sh < 0 || (uint32_t)(sk[local + 1] >> old_sh) != rm) rank[id] = rm;
-      if (!single) {
-        if (rs < A) {
-          act_next[rs] = id;
-          pos_next[rs] = p;
-        } else {
-          atomicExch(err, kDevRange);
-        }
-        ++rs;
+      const uint32_t hs = bg_head[o], bo = bg_off[o];
+      slot = hs + (q - bo);
+      head = hs + (hq - bo);
+      at = bg_pos[o] + (q - bo);
+    }
+    if (id >= n || slot >= n || (kBig && at >= list_cap)) {
+      atomicExch(err, kDevRange);
+      continue;
+    }
+    snap[id] = head;
+    if (!finals) continue;
+    const bool alone = h && ((hb >> (i + 1)) & 1u);
+    if (alone) {
+      sa[slot] = id;
+      rank[id] = slot;
+      fin[id] = (uint8_t)level;
+      if (kBig) nhd[at] = kHole;
+    } else if (kBig) {
+      nid[at] = id;
+      nhd[at] = head;
+    } else {
+      if (rs < list_cap) {
+        nid[rs] = id;
+        nhd[rs] = head;
+      } else {
+        atomicExch(err, kDevRange);
       }
+      ++rs;
     }
   }
 }
@@ -256,106 +333,613 @@ __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t 
   }
 }
 
-// key = (rank[i] << sh) | (i + h < end of i's window ? rank[i + h] + 1 : 0)
-// (the second part relative to the window's SA range with several windows),
-// value = i, with sh = bits of the longest window (the second part is at
-// most its length).
-// Also counts the digits of the sort's first place (key bits [shift,
-// shift + dbits)) into hist, which saves the sort its own pass over the keys.
-__global__ void k_pack(const uint32_t *__restrict__ act, uint32_t A, const uint32_t *__restrict__ A_dev,
-                       const uint32_t *__restrict__ rank, uint32_t n, uint64_t h, int sh, Windows W,
-                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *hist, int shift,
-                       int dbits) {
-  __shared__ uint32_t cnt[512];
-  const uint32_t R = 1u << dbits, lane = threadIdx.x & 31;
-  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) cnt[q] = 0;
+// ---------------------------------------------------------------- a doubling round
+constexpr int kRdT = 1024;                     // list entries per tile
+constexpr int kRdBig = 128;                    // a group with more entries is sorted globally ("big")
+constexpr int kRdThreads = 256, kRdItems = 8;  // items: rows of kRdThreads positions
+constexpr int kRdWarps = kRdThreads / 32;
+constexpr int kRdDigit = 9;                    // digit bits of the warp-level sort
+constexpr int kRdRadix = 1 << kRdDigit;
+constexpr int kRdWin = kRdT + kRdBig + 1;      // positions a tile reads: its span and the next kRdBig + 1
+constexpr int kRdHw0 = kRdBig + 2;             // list heads read before the span
+constexpr int kRdHw = kRdWin + kRdHw0;
+constexpr int kRdGroups = kRdWin / 2 + 2;      // group starts in the window (groups have two entries or more)
+constexpr uint32_t kRdNoGroup = 0xffff;
+static_assert(kRdWin <= kRdItems * kRdThreads, "rows cover the window");
+static_assert(kRdGroups < kRdNoGroup, "group numbers fit 16 bits");
+constexpr size_t kRoundSmem = (size_t)kRdHw * 4               // list heads
+                              + (size_t)kRdWin * 4 * 3         // minor keys (two buffers), suffixes
+                              + (size_t)(kRdGroups + 1) * 4    // group starts
+                              + (size_t)kRdGroups * 4 * 3      // group heads, big indices, first big entries
+                              + (size_t)kRdWin * 2 * 3         // positions (two buffers), group of each position
+                              + (size_t)kRdWarps * kRdRadix * 2;  // per-warp digit counts
+
+struct RoundArgs {
+  const uint32_t *lid, *lhd;   // this round's list: suffix, head slot of its group
+  uint32_t ub;                 // launch bound on the list length
+  const uint32_t *A_dev;       // the list length
+  uint32_t r, h, n;            // round, doubling offset, positions
+  const uint32_t *wsb;         // window-start bits (bit n set), null for one window
+  const uint32_t *wid, *woff;  // window of each position and window offsets (several windows)
+  uint8_t *fin;
+  uint32_t *rank, *sa;
+  const uint32_t *snap_prev;   // level r - 1
+  uint32_t *snap_cur;          // level r
+  uint32_t *hid, *hhd;         // the next list with holes: entry k of a small group settled in place
+  uint64_t *bkeys;             // big entries: (ordinal << mb) | minor relative to the window
+  uint32_t *bvals;
+  uint32_t *bg_head, *bg_off, *bg_pos;  // per big group: head slot, first big entry, first list entry
+  uint32_t bg_cap;
+  int mb;
+  uint32_t *big_hist;          // digit counts of the big keys' lowest hist_bits bits
+  int hist_bits;
+  uint32_t *words;             // [1] big entries, [3] big groups (of the round)
+  uint64_t *st_bc, *st_bs;
+  uint32_t *tile_ctr;
+  uint32_t epoch;
+  uint32_t *err;
+};
+
+__device__ __forceinline__ int bits_for_dev(uint32_t v) { return v ? 32 - __clz(v) : 0; }
+
+// Decoupled look-back in two steps, so that a tile publishes its aggregate
+// as soon as it knows it and waits for its predecessors only when it needs
+// the prefix: lb_publish, later lb_resolve (the sum over tiles < t; also
+// publishes the tile's inclusive prefix).
+__device__ __forceinline__ void lb_publish(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch) {
+  lb_store(&st[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, v));
+}
+__device__ __forceinline__ uint32_t lb_resolve(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
+                                               uint32_t *err) {
+  if (t == 0) return 0;
+  const uint32_t p = lb_exclusive(st, 1, t, epoch, OpSum(), 0u, err);
+  lb_store(&st[t], lb_pack(kLbInclusive, epoch, p + v));
+  return p;
+}
+
+// Exclusive prefix over the tile's items in the strided order p = i *
+// kRdThreads + tid (rows i < rows), from each item's flag or value.  `vals`
+// holds one value per row for this thread; `op` combines (sum or max) with
+// identity 0.  Warp ballots / shuffles inside a row, one shared-memory pass
+// over the (row, warp) totals.  Returns the exclusive prefixes in `ex`.
+template <class Op>
+__device__ __forceinline__ void rows_exclusive(const uint32_t (&vals)[kRdItems], int rows, Op op,
+                                               uint32_t *rowtot /* [kRdItems * kRdWarps + 1] */,
+                                               uint32_t (&ex)[kRdItems], uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc[kRdItems];
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    if (i >= rows) break;
+    inc[i] = warp_inclusive(vals[i], op);
+    if (lane == 31) rowtot[i * kRdWarps + warp] = inc[i];
+  }
   __syncthreads();
-  if (A_dev) A = min(A, *A_dev);
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t k0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < A; k0 += stride) {
-    const uint32_t k = k0 + lane;
-    uint32_t d = R;
-    if (k < A) {
-      const uint32_t i = act[k];
-      const uint64_t j = i + h;
-      // the second rank is only compared within a group, i.e. within one
-      // window, so it is taken relative to the window's SA range
-      uint32_t r2 = 0;
-      if (j < win_end(W, i, n)) r2 = rank[j] + 1u - (W.count > 1 ? W.off_dev[W.wid[i]] : 0u);
-      const uint64_t key = ((uint64_t)rank[i] << sh) | r2;
-      keys[k] = key;
-      vals[k] = i;
-      d = (uint32_t)(key >> shift) & (R - 1);
+  if (threadIdx.x == 0) {  // (row, warp) totals in row-major order -> exclusive prefixes
+    uint32_t run = 0;
+    for (int q = 0; q < rows * kRdWarps; ++q) {
+      const uint32_t v = rowtot[q];
+      rowtot[q] = run;
+      run = op(run, v);
     }
-    const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-    if (__all_sync(0xffffffffu, d == d0 && d0 < R)) {
-      if (lane == 0) atomicAdd(&cnt[d0], 32u);
-    } else if (d < R) {
-      atomicAdd(&cnt[d], 1u);
+    rowtot[kRdItems * kRdWarps] = run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    if (i >= rows) break;
+    const uint32_t before = __shfl_up_sync(0xffffffffu, inc[i], 1);
+    ex[i] = op(rowtot[i * kRdWarps + warp], lane ? before : 0u);
+  }
+  *total = rowtot[kRdItems * kRdWarps];
+  __syncthreads();
+}
+
+// One warp settles one owned group: its entries' minor keys m (u32) and
+// positions are at [q0, q0 + s) of (mA, pA); the group is list entries
+// lbase + q0 ...  Writes every entry's new level rank, settles the
+// singletons, and writes the others in place to the holed next list, in
+// sorted order (a singleton's place becomes a hole).
+__device__ __forceinline__ void settle_group(const RoundArgs &a, uint32_t lbase, uint32_t q0, uint32_t s,
+                                             uint32_t head0, uint32_t *mA, uint16_t *pA, uint32_t *mB,
+                                             uint16_t *pB, uint16_t *wc, const uint32_t *sid) {
+  const uint32_t lane = threadIdx.x & 31, lt = lanemask_lt();
+  // one entry, sorted: its position k in the group, its subgroup's first
+  // position hk, whether it is alone in its subgroup
+  auto put = [&](uint32_t id, uint32_t k, uint32_t hk, bool alone) {
+    const uint32_t slot = head0 + k, head = head0 + hk, at = lbase + q0 + k;
+    if (id >= a.n || slot >= a.n || at >= a.ub) {
+      atomicExch(a.err, kDevRange);
+      return;
+    }
+    a.snap_cur[id] = head;
+    if (alone) {
+      a.sa[slot] = id;
+      a.rank[id] = slot;
+      a.fin[id] = (uint8_t)a.r;
+      a.hhd[at] = kHole;
+    } else {
+      a.hid[at] = id;
+      a.hhd[at] = head;
+    }
+  };
+  if (s <= 32) {
+    // rank by counting: sorted position = #smaller + #equal before
+    const bool v = lane < s;
+    const uint32_t m = v ? mA[q0 + lane] : 0u;
+    uint32_t less = 0, eq = 0, eqb = 0;
+    for (uint32_t j = 0; j < s; ++j) {
+      const uint32_t mj = __shfl_sync(0xffffffffu, m, j);
+      less += mj < m;
+      eq += mj == m;
+      eqb += (mj == m) & (j < lane);
+    }
+    if (v) put(sid[q0 + lane], less + eqb, less, eq == 1);
+    return;
+  }
+  // larger groups: warp-level LSD radix sort of (m - min) with 9-bit digits,
+  // stable (rows of 32 in order), counts in this warp's shared counters
+  const uint32_t rows = (s + 31) / 32;
+  uint32_t mn = 0xffffffffu, mx = 0;
+  for (uint32_t r = 0; r < rows; ++r) {
+    const uint32_t q = q0 + r * 32 + lane;
+    if (q < q0 + s) {
+      mn = min(mn, mA[q]);
+      mx = max(mx, mA[q]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int bits = bits_for_dev(mx - mn);
+  uint32_t *ms = mA, *md = mB;
+  uint16_t *ps = pA, *pd = pB;
+  for (int sh = 0; sh < bits; sh += kRdDigit) {
+    for (int d = lane; d < kRdRadix; d += 32) wc[d] = 0;
+    __syncwarp();
+    // counts
+    for (uint32_t r = 0; r < rows; ++r) {
+      const uint32_t q = q0 + r * 32 + lane;
+      const bool v = q < q0 + s;
+      const uint32_t d = v ? ((ms[q] - mn) >> sh) & (kRdRadix - 1) : (uint32_t)kRdRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (v && (peers & lt) == 0) wc[d] += (uint16_t)__popc(peers);
+      __syncwarp();
+    }
+    // exclusive prefix over the digits (lane owns kRdRadix / 32 consecutive digits)
+    constexpr int kPer = kRdRadix / 32;
+    uint32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) run += wc[lane * kPer + k];
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    uint32_t b = inc - run;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t c = wc[lane * kPer + k];
+      wc[lane * kPer + k] = (uint16_t)b;
+      b += c;
+    }
+    __syncwarp();
+    // scatter in order
+    for (uint32_t r = 0; r < rows; ++r) {
+      const uint32_t q = q0 + r * 32 + lane;
+      const bool v = q < q0 + s;
+      const uint32_t mv = v ? ms[q] : 0u;
+      const uint32_t d = v ? ((mv - mn) >> sh) & (kRdRadix - 1) : (uint32_t)kRdRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t base = 0;
+      if (v) base = wc[d];
+      __syncwarp();
+      if (v) {
+        const uint32_t dst = q0 + base + __popc(peers & lt);
+        md[dst] = mv;
+        pd[dst] = ps[q];
+        if ((peers & lt) == 0) wc[d] = (uint16_t)(base + __popc(peers));
+      }
+      __syncwarp();
+    }
+    uint32_t *xm = ms;
+    ms = md;
+    md = xm;
+    uint16_t *xp = ps;
+    ps = pd;
+    pd = xp;
+  }
+  // settle in sorted order: subgroups of equal m
+  uint32_t hcarry = 0;  // position (in the group) of the last subgroup start so far
+  for (uint32_t r = 0; r < rows; ++r) {
+    const uint32_t k = r * 32 + lane;  // position in the group
+    const bool v = k < s;
+    const uint32_t m = v ? ms[q0 + k] : 0u;
+    const bool st = v && (k == 0 || ms[q0 + k - 1] != m);
+    const bool en = v && (k + 1 == s || ms[q0 + k + 1] != m);
+    // last start at or before this lane
+    const uint32_t sm = __ballot_sync(0xffffffffu, st) & (lt | (1u << lane));
+    const uint32_t hk = sm ? r * 32 + (31 - __clz(sm)) : hcarry;
+    const uint32_t all = __ballot_sync(0xffffffffu, st);
+    if (all) hcarry = r * 32 + (31 - __clz(all));
+    if (v) put(sid[ps[q0 + k]], k, hk, st && en);
+  }
+}
+
+__global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  // positions q of the tile's window are list entries base + q; hw holds the
+  // list heads from base - kRdHw0 on
+  uint32_t *hw = reinterpret_cast<uint32_t *>(smem);  // [kRdHw]
+  uint32_t *mA = hw + kRdHw;                           // [kRdWin] minor keys
+  uint32_t *mB = mA + kRdWin;
+  uint32_t *sid = mB + kRdWin;                         // [kRdWin] suffix by position
+  uint32_t *gst = sid + kRdWin;                        // [kRdGroups + 1] group start positions
+  uint32_t *ghd = gst + kRdGroups + 1;                 // [kRdGroups] group head slots
+  uint32_t *gbx = ghd + kRdGroups;                     // [kRdGroups] big group: its index; small: kNone
+  uint32_t *gbp = gbx + kRdGroups;                     // [kRdGroups] big group: its first big entry
+  uint16_t *pA = reinterpret_cast<uint16_t *>(gbp + kRdGroups);  // [kRdWin] positions
+  uint16_t *pB = pA + kRdWin;
+  uint16_t *gid = pB + kRdWin;                         // [kRdWin] group of each position (kRdNoGroup: covering)
+  uint16_t *wcs = gid + kRdWin;                        // [kRdWarps][kRdRadix] per-warp digit counts
+  __shared__ uint32_t rowtot[kRdItems * kRdWarps + 1];
+  __shared__ uint32_t s_tile, s_G, s_BC, s_BS, s_gnext, s_cov;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(a.tile_ctr, 1u);
+    s_gnext = 0;
+  }
+  const uint32_t A = min(a.ub, *a.A_dev);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base64 = (uint64_t)t * kRdT;
+  if (base64 >= A) return;  // past the list: no later tile looks at it
+  const uint32_t base = (uint32_t)base64;
+  const uint32_t span_end = min(base + (uint32_t)kRdT, A);
+  const uint32_t span = span_end - base;
+  const uint32_t lim = min(A - base, span + (uint32_t)kRdBig + 1);  // positions read: [0, lim)
+  // list heads of entries base - kRdHw0 .. base + lim - 1
+  for (uint32_t q = tid; q < lim + kRdHw0; q += kRdThreads) {
+    const long long k = (long long)base - kRdHw0 + q;
+    hw[q] = k >= 0 ? a.lhd[k] : kNone;
+  }
+  __syncthreads();
+  // group starts among positions [0, lim); their indices by one scan
+  const int rows = (int)((lim + kRdThreads - 1) / kRdThreads);
+  uint32_t st[kRdItems], gex[kRdItems], gall;
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    st[i] = 0;
+    if (i >= rows) break;
+    const uint32_t q = i * kRdThreads + tid;
+    if (q < lim) st[i] = hw[q + kRdHw0] != hw[q + kRdHw0 - 1] ? 1u : 0u;
+  }
+  rows_exclusive(st, rows, OpSum(), rowtot, gex, &gall);
+  gall = min(gall, (uint32_t)kRdGroups);
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    if (i >= rows) break;
+    const uint32_t q = i * kRdThreads + tid;
+    if (q < lim) {
+      if (st[i] && gex[i] < kRdGroups) gst[gex[i]] = q;
+      if (st[i] && gex[i] >= kRdGroups) atomicExch(a.err, kDevRange);  // list groups have two entries or more
+      gid[q] = gex[i] + st[i] == 0 ? (uint16_t)kRdNoGroup : (uint16_t)(gex[i] + st[i] - 1);
     }
   }
   __syncthreads();
-  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
-    if (cnt[q]) atomicAdd(&hist[q], cnt[q]);
+  if (tid == 0) {
+    // groups starting in the span, and where the last of them ends: the next
+    // start, or the list's end when it lies in the window, else unknown
+    uint32_t lo = 0, hi = gall;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (gst[mid] < span) lo = mid + 1; else hi = mid;
+    }
+    s_G = lo;
+    gst[gall] = lim == A - base ? lim : kNone;
+  }
+  __syncthreads();
+  const uint32_t G = s_G;
+  const uint32_t f = G ? gst[0] : span;  // entries before f belong to a group that started earlier
+  // per group starting in the span: head, big or small, big entries in the span
+  uint32_t bflag[kRdItems], bent[kRdItems], bfx[kRdItems], bex[kRdItems], bs_tile, bc_groups;
+  const int grows = (int)((G + kRdThreads - 1) / kRdThreads);
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    bflag[i] = 0;
+    bent[i] = 0;
+    if (i >= grows) break;
+    const uint32_t g = i * kRdThreads + tid;
+    if (g < G) {
+      const uint32_t q0 = gst[g], nx = gst[g + 1];
+      ghd[g] = hw[q0 + kRdHw0];
+      const bool big = nx == kNone || nx - q0 > (uint32_t)kRdBig;
+      bflag[i] = big;
+      bent[i] = big ? min(nx == kNone ? span : nx, span) - q0 : 0u;
+    }
+  }
+  rows_exclusive(bflag, grows, OpSum(), rowtot, bfx, &bs_tile);
+  rows_exclusive(bent, grows, OpSum(), rowtot, bex, &bc_groups);
+  // the covering group [0, f): big iff it has more than kRdBig entries, i.e.
+  // it covers the whole span or the entry kRdBig places before its end is
+  // still in it
+  if (tid == 0) {
+    bool cov = false;
+    if (f > 0) {
+      if (G == 0 && span == (uint32_t)kRdT) {
+        cov = true;
+      } else {
+        const long long x = (long long)(G ? f : A - base) - kRdBig - 1;  // relative to base, >= -kRdBig - 1
+        cov = (long long)base + x >= 0 && hw[x + kRdHw0] == hw[kRdHw0];
+      }
+    }
+    s_cov = cov;
+  }
+#pragma unroll
+  for (int i = 0; i < kRdItems; ++i) {
+    if (i >= grows) break;
+    const uint32_t g = i * kRdThreads + tid;
+    if (g < G) {
+      gbx[g] = bflag[i] ? bfx[i] : kNone;
+      gbp[g] = bex[i];
+    }
+  }
+  __syncthreads();
+  const bool cov_big = s_cov != 0;
+  const uint32_t cov_cnt = cov_big ? f : 0u;
+  const uint32_t bc = cov_cnt + bc_groups;
+  // the tile's big entries and big groups are known: published now, the
+  // prefixes over the tiles before are read at the end
+  if (tid == 0) lb_publish(a.st_bc, t, bc, a.epoch);
+  if (tid == 32) lb_publish(a.st_bs, t, bs_tile, a.epoch);
+  // the positions whose minor keys are needed: the covering group when it is
+  // big, every group starting in the span (a small one to its end)
+  uint32_t gend = span;
+  if (G && gbx[G - 1] == kNone) gend = max(gend, gst[G]);
+  const uint32_t g0 = cov_big ? 0u : f;
+  const int mrows = (int)((gend + kRdThreads - 1) / kRdThreads);
+
+  // ---- gather: suffix, then the level of the suffix h ahead, then its rank
+  {
+    uint32_t id[kRdItems], jj[kRdItems];
+    uint8_t fb[kRdItems];
+#pragma unroll
+    for (int i = 0; i < kRdItems; ++i) {
+      if (i >= mrows) break;
+      const uint32_t q = i * kRdThreads + tid;
+      id[i] = (q >= g0 && q < gend) ? a.lid[base + q] : a.n;
+    }
+#pragma unroll
+    for (int i = 0; i < kRdItems; ++i) {
+      if (i >= mrows) break;
+      const uint32_t j = id[i] < a.n ? id[i] + a.h : a.n;
+      jj[i] = (j >= a.n || (a.wsb && bit_at(a.wsb, j))) ? a.n : j;  // a.n: past the end
+      fb[i] = jj[i] < a.n ? a.fin[jj[i]] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kRdItems; ++i) {
+      if (i >= mrows) break;
+      const uint32_t q = i * kRdThreads + tid;
+      if (q < gend) {
+        mA[q] = jj[i] < a.n ? ((uint32_t)fb[i] < a.r - 1 ? a.rank[jj[i]] : a.snap_prev[jj[i]]) + 1 : 0u;
+        sid[q] = id[i];
+        pA[q] = (uint16_t)q;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- small groups: one warp each, settled in place
+  {
+    uint16_t *wc = wcs + warp * kRdRadix;
+    while (true) {
+      uint32_t g = 0;
+      if (lane == 0) g = atomicAdd(&s_gnext, 1u);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (g >= G) break;
+      if (gbx[g] != kNone) continue;
+      const uint32_t q0 = gst[g], s = gst[g + 1] - q0;
+      if (s == 0 || q0 + s > gend) {  // only after an error reported above
+        if (lane == 0) atomicExch(a.err, kDevRange);
+        continue;
+      }
+      settle_group(a, base, q0, s, ghd[g], mA, pA, mB, pB, wc, sid);
+    }
+  }
+
+  // ---- big entries of the span: (ordinal, minor relative to the window),
+  // and each big group's head, first big entry and first list entry
+  if (tid == 0) s_BC = lb_resolve(a.st_bc, t, bc, a.epoch, a.err);
+  if (tid == 32) s_BS = lb_resolve(a.st_bs, t, bs_tile, a.epoch, a.err);
+  __syncthreads();
+  const uint32_t BC = s_BC, BS = s_BS;
+  if (bc) {
+    uint32_t *hcnt = mB;  // free now: digit counts of the big keys
+    const uint32_t hmask = (1u << a.hist_bits) - 1;
+    for (uint32_t d = tid; d <= hmask; d += kRdThreads) hcnt[d] = 0;
+    __syncthreads();
+    for (uint32_t q = tid; q < span; q += kRdThreads) {
+      uint32_t j, o;
+      if (q < f) {
+        if (!cov_big) continue;
+        j = q;
+        o = BS - 1;
+      } else {
+        const uint32_t g = gid[q];
+        if (g >= G || gbx[g] == kNone) continue;
+        j = cov_cnt + gbp[g] + (q - gst[g]);
+        o = BS + gbx[g];
+      }
+      const uint32_t i = sid[q];
+      uint32_t m = mA[q];
+      if (m && a.woff && i < a.n) m -= a.woff[a.wid[i]];
+      const uint64_t key = ((uint64_t)o << a.mb) | m;
+      if (BC + j < a.ub && o < a.bg_cap) {
+        a.bkeys[BC + j] = key;
+        a.bvals[BC + j] = i;
+        atomicAdd(&hcnt[(uint32_t)key & hmask], 1u);
+      } else {
+        atomicExch(a.err, kDevRange);
+      }
+    }
+    for (uint32_t g = tid; g < G; g += kRdThreads) {
+      if (gbx[g] == kNone) continue;
+      const uint32_t o = BS + gbx[g];
+      if (o < a.bg_cap) {
+        a.bg_head[o] = ghd[g];
+        a.bg_off[o] = BC + cov_cnt + gbp[g];
+        a.bg_pos[o] = base + gst[g];
+      } else {
+        atomicExch(a.err, kDevRange);
+      }
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d <= hmask; d += kRdThreads)
+      if (hcnt[d]) atomicAdd(&a.big_hist[d], hcnt[d]);
+  }
+  if (tid == 0 && span_end == A) {
+    a.words[1] = BC + bc;
+    a.words[3] = BS + bs_tile;
+  }
 }
 
-// Batched first round: key = (window << 32) | rank of the token among all
-// tokens, so that suffixes of different windows never share a group.
-__global__ void k_wkeys(const uint32_t *__restrict__ rank, Windows W, uint32_t n,
+// The holed next list (entries settled in place, holes where a suffix became
+// final) -> the dense next list, order kept; its length lands in *count_out.
+constexpr int kLcT = 256, kLcI = 8, kLcTile = kLcT * kLcI;
+__global__ void __launch_bounds__(kLcT) k_list_compact(const uint32_t *__restrict__ hid,
+                                                       const uint32_t *__restrict__ hhd, uint32_t ub,
+                                                       const uint32_t *__restrict__ A_dev,
+                                                       uint32_t *__restrict__ nid, uint32_t *__restrict__ nhd,
+                                                       uint32_t n, uint32_t *count_out, uint64_t *status,
+                                                       uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
+  __shared__ uint32_t s_tile, s_pre;
+  __shared__ uint32_t scr[kLcT / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  const uint32_t A = min(ub, *A_dev);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kLcTile;
+  if (base >= A) return;
+  uint32_t hd[kLcI], cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kLcI; ++i) {
+    const uint64_t k = base + (uint64_t)tid * kLcI + i;
+    hd[i] = k < A ? hhd[k] : kHole;
+    cnt += hd[i] != kHole;
+  }
+  uint32_t tot;
+  const uint32_t ex = block_exclusive<kLcT / 32>(cnt, OpSum(), 0u, scr, &tot);
+  if (tid == 0) {
+    lb_publish(status, t, tot, epoch);
+    s_pre = lb_resolve(status, t, tot, epoch, err);
+    if (base + kLcTile >= A) *count_out = s_pre + tot;
+  }
+  __syncthreads();
+  uint32_t rs = s_pre + ex;
+#pragma unroll
+  for (int i = 0; i < kLcI; ++i) {
+    if (hd[i] == kHole) continue;
+    const uint64_t k = base + (uint64_t)tid * kLcI + i;
+    if (rs < n) {
+      nid[rs] = hid[k];
+      nhd[rs] = hd[i];
+    } else {
+      atomicExch(err, kDevRange);
+    }
+    ++rs;
+  }
+}
+
+// Window-start bits: bit off[w] for w >= 1, and bit n.
+__global__ void k_wsb(const uint32_t *__restrict__ off, uint32_t count, uint32_t n, uint32_t *bits) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= count; w += gridDim.x * blockDim.x) {
+    const uint32_t j = w < count ? off[w + 1] : n;
+    if (w < count && j >= n) continue;
+    atomicOr(&bits[j >> 5], 1u << (j & 31));
+  }
+}
+
+// Batched first round: key = (window << 32) | level-0 rank of the token among
+// all tokens, so that suffixes of different windows never share a group.
+__global__ void k_wkeys(const uint32_t *__restrict__ r0, Windows W, uint32_t n,
                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    keys[i] = ((uint64_t)win_id(W, i) << 32) | rank[i];
+    keys[i] = ((uint64_t)win_id(W, i) << 32) | r0[i];
     vals[i] = i;
   }
 }
 
-__global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, Windows W,
+// Phi[SA[k]] = SA[k-1] within a window (a window's first slot has none).
+__global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, const uint32_t *__restrict__ wsb,
                       uint32_t *__restrict__ phi) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const uint32_t i = sa[k];
-    phi[i] = (k && win_id(W, sa[k - 1]) == win_id(W, i)) ? sa[k - 1] : kNone;
+    const bool first = k == 0 || (wsb && bit_at(wsb, k));
+    if (i < n) phi[i] = first ? kNone : sa[k - 1];
   }
 }
 
-template <class T>
-__device__ __forceinline__ bool long_match(const T *__restrict__ S, uint32_t n, uint32_t i,
-                                           uint32_t j, uint32_t &l) {
-  // i and j lie in the same window, which ends at n
-  uint32_t steps = 0;
-  while (i + (uint64_t)l < n && j + (uint64_t)l < n && S[i + l] == S[j + l]) {
-    ++l;
-    if (++steps == 32) return true;
-  }
-  return false;
-}
-
-// PLCP[i] = lcp(i, Phi[i]) over chunks of consecutive i, kRChunk per thread.
+// PLCP[i] = lcp(i, Phi[i]) over chunks of kPChunk consecutive i per thread.
+// Tokens are compared directly for up to kPDirect steps; a match that keeps
+// going is finished by lifting over the level ranks: level lev ranks are
+// equal iff the next h0 * 2^lev tokens are, from the top level down (level
+// lev's snapshot at snap0 + lev * n).
 constexpr int kPChunk = 16;
+constexpr uint32_t kPDirect = 256;
+constexpr int kPBlock = 8;
 template <class T>
-__global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W,
-                       const uint32_t *__restrict__ phi, const uint32_t *__restrict__ snaps,
-                       int levels, uint32_t h0, uint32_t *__restrict__ plcp) {
+__global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W, const uint32_t *__restrict__ wsb,
+                       const uint32_t *__restrict__ phi, const uint8_t *__restrict__ fin,
+                       const uint32_t *__restrict__ rank, const uint32_t *__restrict__ snap0, int levels,
+                       uint32_t h0, uint32_t *__restrict__ plcp) {
   const uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kPChunk;
   if (i0 >= n) return;
   const uint32_t iend = (i0 + kPChunk) < (uint64_t)n ? (uint32_t)(i0 + kPChunk) : n;
   uint32_t l = 0;
   for (uint32_t i = (uint32_t)i0; i < iend; ++i) {
     const uint32_t j = phi[i];
-    if (j == kNone) {
+    if (i > i0 && wsb && bit_at(wsb, i)) l = 0;  // a new window starts
+    if (j >= n) {
       plcp[i] = 0;
       l = 0;
       continue;
     }
-    if (i > i0 && win_id(W, i) != win_id(W, i - 1)) l = 0;  // a new window starts
-    const uint32_t we = win_end(W, i, n);
-    if (long_match(S, we, i, j, l)) {
-      // lift: level lev ranks are equal iff the next h0 * 2^lev tokens are
-      // equal; what remains is shorter than h0 and is compared directly
+    const uint32_t we = win_end(W, i, n);  // i and j lie in the same window
+    // blocks of kPBlock tokens are loaded together (independent loads), then
+    // compared; the tail token by token
+    uint32_t steps = 0;
+    bool more = true;
+    while (more && steps < kPDirect && (uint64_t)max(i, j) + l + kPBlock <= we) {
+      T x[kPBlock], y[kPBlock];
+#pragma unroll
+      for (int k = 0; k < kPBlock; ++k) {
+        x[k] = S[i + l + k];
+        y[k] = S[j + l + k];
+      }
+      int eq = 0;
+#pragma unroll
+      for (int k = kPBlock - 1; k >= 0; --k) eq = x[k] == y[k] ? eq + 1 : 0;  // leading equal tokens
+      l += eq;
+      steps += eq;
+      more = eq == kPBlock;
+    }
+    while (more && steps < kPDirect && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]) {
+      ++l;
+      ++steps;
+    }
+    if (steps >= kPDirect) {
       for (int lev = levels - 1; lev >= 0; --lev) {
-        const uint64_t a = (uint64_t)i + l, b = (uint64_t)j + l;
-        if (a < we && b < we && snaps[(size_t)lev * n + a] == snaps[(size_t)lev * n + b])
+        const uint64_t x = (uint64_t)i + l, y = (uint64_t)j + l;
+        if (x < we && y < we &&
+            level_rank(fin, rank, snap0 + (size_t)lev * n, (uint32_t)lev, (uint32_t)x) ==
+                level_rank(fin, rank, snap0 + (size_t)lev * n, (uint32_t)lev, (uint32_t)y))
           l += h0 << lev;
       }
+      // what remains is shorter than h0 tokens
       for (uint32_t k = 1; k < h0 && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]; ++k)
         ++l;
     }
@@ -364,30 +948,38 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W,
   }
 }
 
-__global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ plcp,
-                           uint32_t n, Windows W, uint32_t *__restrict__ lcp) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    lcp[k] = (k + 1 < n && win_id(W, sa[k + 1]) == win_id(W, sa[k])) ? plcp[sa[k + 1]] : 0u;
+__global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ plcp, uint32_t n,
+                           const uint32_t *__restrict__ wsb, uint32_t *__restrict__ lcp) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const bool last = k + 1 >= n || (wsb && bit_at(wsb, k + 1));
+    const uint32_t x = last ? 0u : sa[k + 1];
+    lcp[k] = (last || x >= n) ? 0u : plcp[x];
+  }
 }
 
-// Launches the refresh of the (at most A, exactly *A_dev when given) sorted
-// active suffixes; the number still active lands in *count_dev (zeroed
-// first, so a launch with nothing to do leaves 0).
-int refresh_launch(apo_ctx *c, const uint64_t *keys, const uint32_t *idx, uint32_t A, const uint32_t *A_dev,
-                   const uint32_t *actpos, int old_sh, uint32_t *sa, uint32_t *rank, uint32_t *act_next,
-                   uint32_t *pos_next, uint32_t n, uint32_t *count_dev, cudaStream_t s) {
-  const int tiles = std::max(1, ceil_div(A, kRTile));
+// Launches k_split over ub sorted pairs (exactly *n_dev when given).  With
+// big = false the slot of sorted element q is q and the list length lands in
+// *count_out; with big = true the groups' tables place slots and list entries.
+int split_launch(apo_ctx *c, bool big, const uint64_t *keys, const uint32_t *vals, uint32_t ub,
+                 const uint32_t *n_dev, int ord_shift, const uint32_t *bg_head, const uint32_t *bg_off,
+                 const uint32_t *bg_pos, uint32_t bg_cap, uint32_t level, bool finals, uint32_t *snap,
+                 SuffixState &st, uint32_t *nid, uint32_t *nhd, uint32_t *count_out, cudaStream_t s) {
+  const int tiles = std::max(1, ceil_div(ub, kSTile));
   APO_TRY(ensure_lookback(c, (size_t)2 * tiles));
   uint32_t *misc = c->ps.counters + kCtrMisc;
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRefreshTiles, 0, sizeof(uint32_t), s));
-  APO_CUDA_TRY(cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s));
   const uint32_t ep = next_epoch(c);
-  {
-    Launch lp_(c, kKRefresh, A, s);
-    k_refresh<<<tiles, kRT, kRefreshSmem, s>>>(keys, idx, A, A_dev, actpos, old_sh, sa, rank, act_next, pos_next,
-                                               n, count_dev, c->ps.lookback, c->ps.lookback + tiles,
-                                               misc + kMiscRefreshTiles, ep, c->ps.err);
-  }
+  Launch lp_(c, kKSplit, ub, s);
+  if (big)
+    k_split<true><<<tiles, kST, 0, s>>>(keys, vals, ub, n_dev, ord_shift, bg_head, bg_off, bg_pos, bg_cap, level,
+                                        finals, snap, st.sa, st.rank, st.fin, nid, nhd, st.n, count_out, st.n,
+                                        c->ps.lookback, c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
+                                        c->ps.err);
+  else
+    k_split<false><<<tiles, kST, 0, s>>>(keys, vals, ub, n_dev, 0, nullptr, nullptr, nullptr, 0, level, finals,
+                                         snap, st.sa, st.rank, st.fin, nid, nhd, st.n, count_out, st.n,
+                                         c->ps.lookback, c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
+                                         c->ps.err);
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
 }
@@ -480,15 +1072,19 @@ int dictionary_finish(apo_ctx *c, const void *tokens, int tb, uint32_t n, int tb
 }  // namespace
 
 int suffix_init() {
-  APO_CUDA_TRY(cudaFuncSetAttribute(k_refresh, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kRefreshSmem));
+  APO_CUDA_TRY(cudaFuncSetAttribute(k_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundSmem));
   return APO_OK;
 }
 
 size_t suffix_workspace_bytes(uint64_t n) {
   const int levels = bits_for(n) + 2;
   const uint64_t cap = dict_capacity((uint32_t)std::min<uint64_t>(n, 0xffffffffull));
-  return (size_t)n * (2 * 8 + 2 * 4 + 4 * 4 + 4 + 4) + (size_t)levels * n * 4 + 16 * 256 +
+  return (size_t)n * (2 * 8 + 2 * 4)        // sort pairs
+         + (size_t)n * 4 * 6                // two lists of (suffix, head), the holed list
+         + (size_t)n * (1 + 4 + 4)          // fin; phi and plcp
+         + (size_t)(n / 32 + 2) * 4         // window-start bits
+         + (size_t)(n / (kRdBig + 1) + 2) * 12  // big-group table
+         + (size_t)levels * n * 4 + 16 * 256 +
          (size_t)(cap * 12 + (cap / 2) * 24 + n * 4 + 8 * 256);  // token dictionary
 }
 
@@ -503,24 +1099,39 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   b.keys[1] = c->arena.take_n<uint64_t>(n);
   b.vals[0] = c->arena.take_n<uint32_t>(n);
   b.vals[1] = c->arena.take_n<uint32_t>(n);
-  uint32_t *act[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
-  uint32_t *pos[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
-  if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !act[0] || !act[1] || !pos[0] ||
-      !pos[1]) {
+  uint32_t *lid[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
+  uint32_t *lhd[2] = {c->arena.take_n<uint32_t>(n), c->arena.take_n<uint32_t>(n)};
+  const uint32_t bg_cap = n / (kRdBig + 1) + 2;  // big groups have more than kRdBig entries
+  uint32_t *bg_head = c->arena.take_n<uint32_t>(bg_cap);
+  uint32_t *bg_off = c->arena.take_n<uint32_t>(bg_cap);
+  uint32_t *bg_pos = c->arena.take_n<uint32_t>(bg_cap);
+  uint32_t *hid = c->arena.take_n<uint32_t>(n);  // the holed next list of a round
+  uint32_t *hhd = c->arena.take_n<uint32_t>(n);
+  st.fin = c->arena.take_n<uint8_t>(n);
+  const size_t wsb_words = (size_t)n / 32 + 2;
+  st.wsb = st.win.count > 1 ? c->arena.take_n<uint32_t>(wsb_words) : nullptr;
+  if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !lid[0] || !lid[1] || !lhd[0] || !lhd[1] ||
+      !bg_head || !bg_off || !bg_pos || !hid || !hhd || !st.fin || (st.win.count > 1 && !st.wsb)) {
     set_error("suffix array: workspace too small");
     return APO_ENOMEM;
   }
   const int g = grid_for(n, 256, c->num_sms);
-  {
-    Launch lp_(c, kKInitKeys, n, s);
-    k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
+  APO_CUDA_TRY(cudaMemsetAsync(st.fin, 0xff, n, s));
+  if (st.wsb) {
+    APO_CUDA_TRY(cudaMemsetAsync(st.wsb, 0, wsb_words * 4, s));
+    Launch lp_(c, kKWsb, st.win.count, s);
+    k_wsb<<<grid_for(st.win.count + 1, 256, c->num_sms), 256, 0, s>>>(st.win.off_dev, st.win.count, n, st.wsb);
   }
   // how many token bits are populated (for u64 tokens the dictionary of
   // distinct tokens is filled in the same round trip)
   uint32_t *misc = c->ps.counters + kCtrMisc;
   uint64_t *kor = reinterpret_cast<uint64_t *>(misc + kMiscKeyOr);
   APO_CUDA_TRY(cudaMemsetAsync(kor, 0, 2 * sizeof(uint64_t), s));
-  launch_key_or(c, b.keys[0], n, kor, s);
+  {
+    Launch lp_(c, kKKeyOr, n, s);
+    k_token_or<<<std::min(1024, ceil_div(n, 256 * 8)), 256, 0, s>>>(tokens, tb, n,
+                                                                     reinterpret_cast<unsigned long long *>(kor));
+  }
   DictCodes dict;
   const bool dict_early = tb == 8 && n >= 4096;
   if (dict_early) APO_TRY(dictionary_begin(c, tokens, tb, n, &dict, s));
@@ -557,7 +1168,8 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       h0 = (uint32_t)((64 - wb) / cb);
     }
   }
-  uint32_t A = 0;
+  // level 0: groups of equal first h0 tokens (within a window)
+  uint32_t *first_count = misc + kMiscRefreshCount;
   if (h0 >= 2) {
     h0 = std::min<uint32_t>(h0, 32);
     {
@@ -567,112 +1179,163 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     b.cur = 0;
     const DigitRange r{0, wb + (int)h0 * cb, false};
     APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
-    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
-                           pos[0], n, misc + kMiscRefreshCount, s));
-    A = n;  // an upper bound: the count stays on the device
   } else {
     h0 = 1;
     {
-      const DigitRange r{0, tbits, false};
-      APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
+      Launch lp_(c, kKInitKeys, n, s);
+      k_init_keys<<<g, 256, 0, s>>>(tokens, tb, n, b.keys[0], b.vals[0]);
     }
-    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
-                           pos[0], n, misc + kMiscRefreshCount, s));
-    A = n;  // an upper bound: the count stays on the device
+    b.cur = 0;
+    const DigitRange r{0, tbits, false};
+    APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
     if (st.win.count > 1) {
-      // group by (window, token): re-sort by the window id over the token ranks
+      // group by (window, token): the token's rank among all tokens, then a
+      // re-sort by the window id over those ranks
+      APO_TRY(split_launch(c, false, b.keys[b.cur], b.vals[b.cur], n, nullptr, 0, nullptr, nullptr, nullptr, 0, 0,
+                           false, st.snaps[0], st, lid[0], lhd[0], first_count, s));
       {
         Launch lp_(c, kKInitKeys, n, s);
-        k_wkeys<<<g, 256, 0, s>>>(st.rank, st.win, n, b.keys[0], b.vals[0]);
+        k_wkeys<<<g, 256, 0, s>>>(st.snaps[0], st.win, n, b.keys[0], b.vals[0]);
       }
       b.cur = 0;
-      const DigitRange r[2] = {{0, bits_for(n - 1), false}, {32, 32 + wb, false}};
-      APO_TRY(radix_sort_pairs(c, b, n, r, 2, s));
-      APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], n, nullptr, nullptr, -1, st.sa, st.rank, act[0],
-                           pos[0], n, misc + kMiscRefreshCount, s));
-    A = n;  // an upper bound: the count stays on the device
+      const DigitRange r2[2] = {{0, bits_for(n - 1), false}, {32, 32 + wb, false}};
+      APO_TRY(radix_sort_pairs(c, b, n, r2, 2, s));
     }
   }
+  APO_TRY(split_launch(c, false, b.keys[b.cur], b.vals[b.cur], n, nullptr, 0, nullptr, nullptr, nullptr, 0, 0,
+                       true, st.snaps[0], st, lid[0], lhd[0], first_count, s));
   st.h0 = h0;
-  APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[0], st.rank, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
   st.levels = 1;
-  int cur = 0;
-  uint32_t rounds = 0;
-  // second rank + 1 <= the longest window; first rank < n
-  const int minor_bits = bits_for(st.win.count > 1 ? st.win.max_len : n), major_bits = bits_for(n - 1);
-  // Round r reads its active count from a device word and writes the next
-  // one; the host queues round r+1 before it has read round r's count (an
-  // upper bound sizes the launches), and stops one round after the count
-  // reaches 0 (that round's kernels find nothing to do and return).
-  uint32_t *rc = misc + kMiscRound;
-  uint32_t ub = A;  // upper bound on the current round's input count
-  for (uint32_t r = 0; A > 0; ++r) {
+
+  // Rounds r = 1, 2, ...: round r reads list (r - 1) & 1 and writes the
+  // level-r snapshot and list r & 1: k_round settles the small groups into
+  // the holed list (hid, hhd) and writes the big entries' keys; the big
+  // entries are sorted and k_split settles them into the holed list; then
+  // k_list_compact drops the holes.  The round's device words (next list
+  // length, big entries, -, big groups) alternate between two slots.  The host queues round r + 1 before it has read round r's
+  // length (an upper bound sizes the launches), and stops one round after
+  // the length reaches 0 (that round's kernels find nothing to do).  A round
+  // with no big entries has no big groups after it, so from then on the big
+  // path is not queued.
+  const int mb = bits_for(st.win.count > 1 ? st.win.max_len : n);
+  uint32_t ub = n;      // bound on the current round's list length
+  uint32_t big_ub = n;  // bound on its big entries (a round has no more than the round before)
+  bool big_possible = true;
+  for (uint32_t r = 1;; ++r) {
     if (st.levels >= max_levels) {
       set_error("suffix array: too many doubling rounds");
       return APO_EDEVICE;
     }
-    const uint32_t *in = r == 0 ? misc + kMiscRefreshCount : rc + ((r - 1) & 1);
-    uint32_t *out = rc + (r & 1);
-    const uint64_t h = (uint64_t)h0 << r;
-    b.cur = 0;
-    const DigitRange dr{0, minor_bits + major_bits, false};
+    const int cur = (r - 1) & 1, nxt = r & 1;
+    const uint32_t *in = r == 1 ? first_count : misc + kMiscRoundW + 4 * ((r - 1) & 1);
+    uint32_t *words = misc + kMiscRoundW + 4 * (r & 1);
+    const uint64_t h64 = (uint64_t)h0 << (r - 1);
+    const uint32_t h = (uint32_t)std::min<uint64_t>(h64, n);  // no suffix is active once h reaches n
+    const int tiles = std::max(1, ceil_div(ub, kRdT));
+    const int ctiles = std::max(1, ceil_div(ub, kLcTile));
+    APO_TRY(ensure_lookback(c, std::max<size_t>((size_t)2 * tiles, ctiles)));
     SortPlan sp;
-    APO_TRY(sort_plan(c, ub, &dr, 1, &sp, s));
-    APO_TRY(sort_first_hist_clear(c, s));
-    {
-      Launch lp_(c, kKPack, ub, s);
-      const int blocks = std::max(1, std::min(ceil_div(ub, 256), c->num_sms * 4));
-      k_pack<<<blocks, 256, 0, s>>>(act[cur], ub, in, st.rank, n, h, minor_bits, st.win, b.keys[0], b.vals[0],
-                                    sort_first_hist(c), sp.shape >= 0 ? (sp.place[0] & 255) : 0, sp.bits);
+    big_ub = std::min(big_ub, ub);
+    if (big_possible) {
+      const DigitRange dr{0, bits_for(big_ub / (kRdBig + 1) + 1) + mb, false};
+      APO_TRY(sort_plan(c, big_ub, &dr, 1, &sp, s));
+      APO_TRY(sort_first_hist_clear(c, s));
     }
-    APO_TRY(radix_sort_planned(c, b, ub, sp, s, in, true));
-    APO_TRY(refresh_launch(c, b.keys[b.cur], b.vals[b.cur], ub, in, pos[cur], minor_bits, st.sa, st.rank,
-                           act[cur ^ 1], pos[cur ^ 1], n, out, s));
-    cur ^= 1;
-    APO_CUDA_TRY(cudaMemcpyAsync(st.snaps[st.levels], st.rank, (size_t)n * 4,
-                                 cudaMemcpyDeviceToDevice, s));
+    APO_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(uint32_t), s));
+    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRoundTiles, 0, sizeof(uint32_t), s));
+    {
+      RoundArgs a;
+      a.lid = lid[cur];
+      a.lhd = lhd[cur];
+      a.ub = ub;
+      a.A_dev = in;
+      a.r = r;
+      a.h = h;
+      a.n = n;
+      a.wsb = st.wsb;
+      a.wid = st.win.count > 1 ? st.win.wid : nullptr;
+      a.woff = st.win.count > 1 ? st.win.off_dev : nullptr;
+      a.fin = st.fin;
+      a.rank = st.rank;
+      a.sa = st.sa;
+      a.snap_prev = st.snaps[r - 1];
+      a.snap_cur = st.snaps[r];
+      a.hid = hid;
+      a.hhd = hhd;
+      a.bkeys = b.keys[0];
+      a.bvals = b.vals[0];
+      a.bg_head = bg_head;
+      a.bg_off = bg_off;
+      a.bg_pos = bg_pos;
+      a.bg_cap = bg_cap;
+      a.mb = mb;
+      a.big_hist = sort_first_hist(c);
+      a.hist_bits = big_possible && sp.shape >= 0 ? sp.bits : 8;
+      a.words = words;
+      a.st_bc = c->ps.lookback;
+      a.st_bs = c->ps.lookback + tiles;
+      a.tile_ctr = misc + kMiscRoundTiles;
+      a.epoch = next_epoch(c);
+      a.err = c->ps.err;
+      Launch lp_(c, kKRound, ub, s);
+      k_round<<<tiles, kRdThreads, kRoundSmem, s>>>(a);
+    }
+    APO_CUDA_TRY(cudaGetLastError());
+    if (big_possible && sp.shape >= 0) {
+      b.cur = 0;
+      APO_TRY(radix_sort_planned(c, b, big_ub, sp, s, words + 1, true));
+      APO_TRY(split_launch(c, true, b.keys[b.cur], b.vals[b.cur], big_ub, words + 1, mb, bg_head, bg_off, bg_pos,
+                           bg_cap, r, true, st.snaps[r], st, hid, hhd, nullptr, s));
+    }
+    APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRoundTiles, 0, sizeof(uint32_t), s));
+    {
+      Launch lp_(c, kKListCompact, ub, s);
+      k_list_compact<<<ctiles, kLcT, 0, s>>>(hid, hhd, ub, in, lid[nxt], lhd[nxt], n, words, c->ps.lookback,
+                                             misc + kMiscRoundTiles, next_epoch(c), c->ps.err);
+    }
+    APO_CUDA_TRY(cudaGetLastError());
     ++st.levels;
     const bool cap = capturing(c);
     if (!cap) {
-      if (r == 0)  // round 0's input count, also unknown on the host so far
-        APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 6, in, 4, cudaMemcpyDeviceToHost, s));
-      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 4 + (r & 1), out, 4, cudaMemcpyDeviceToHost, s));
+      if (r == 1) APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 6, first_count, 4, cudaMemcpyDeviceToHost, s));
+      APO_CUDA_TRY(cudaMemcpyAsync(c->host_pinned + 16 + 2 * (r & 1), words, 8, cudaMemcpyDeviceToHost, s));
       APO_CUDA_TRY(cudaEventRecord(c->round_ev[r & 1], s));
     }
-    if (r > 0) {
-      // (a captured call takes the counts from its tape, checked against the
-      // device words -- still unchanged at this point of the stream)
-      uint32_t first = 0, a = 0;
-      if (r == 1) {
-        if (cap) {
-          APO_TRY(tape_take(c, misc + kMiscRefreshCount, &first, 1, s));
-        } else {
-          APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
-          first = c->host_pinned[6];
-          if (recording(c)) tape_put(c, &first, 1);
-        }
-        if (first == 0) {  // the first sort left no group: rounds 0 and 1 idle
-          st.levels -= 2;
-          rounds = 0;
-          break;
-        }
-      }
+    if (r == 1) continue;
+    // round r - 1's results (a captured call takes them from its tape,
+    // checked against the device words -- still unchanged at this point)
+    if (r == 2) {
+      uint32_t first = 0;
       if (cap) {
-        APO_TRY(tape_take(c, rc + ((r - 1) & 1), &a, 1, s));
+        APO_TRY(tape_take(c, first_count, &first, 1, s));
       } else {
-        if (r > 1) APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
-        a = c->host_pinned[4 + ((r - 1) & 1)];  // round r's input count
-        if (recording(c)) tape_put(c, &a, 1);
+        APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[1]));
+        first = c->host_pinned[6];
+        if (recording(c)) tape_put(c, &first, 1);
       }
-      if (a == 0) {  // round r had nothing to do
-        --st.levels;
+      if (first == 0) {  // the first sort left no group: rounds 1 and 2 idle
+        st.levels = 1;
         break;
       }
-      ub = a;
     }
-    ++rounds;
+    uint32_t w2[2];
+    if (cap) {
+      APO_TRY(tape_take(c, misc + kMiscRoundW + 4 * ((r - 1) & 1), w2, 2, s));
+    } else {
+      if (r > 2) APO_CUDA_TRY(cudaEventSynchronize(c->round_ev[(r - 1) & 1]));
+      w2[0] = c->host_pinned[16 + 2 * ((r - 1) & 1)];
+      w2[1] = c->host_pinned[17 + 2 * ((r - 1) & 1)];
+      if (recording(c)) tape_put(c, w2, 2);
+    }
+    if (w2[0] == 0) {  // round r had nothing to do: levels 0 .. r - 1
+      st.levels = (int)r;
+      break;
+    }
+    ub = w2[0];
+    big_ub = std::min(big_ub, w2[1]);
+    if (w2[1] == 0) big_possible = false;
   }
-  *rounds_out = rounds;
+  *rounds_out = (uint32_t)(st.levels - 1);
   return APO_OK;
 }
 
@@ -689,26 +1352,21 @@ int build_lcp(apo_ctx *c, const void *tokens, int tb, const SuffixState &st, uin
   const int g = grid_for(n, 256, c->num_sms);
   {
     Launch lp_(c, kKPhi, n, s);
-    k_phi<<<g, 256, 0, s>>>(st.sa, n, st.win, phi);
+    k_phi<<<g, 256, 0, s>>>(st.sa, n, st.wsb, phi);
   }
   const int pb = ceil_div(ceil_div(n, kPChunk), 128);
-  if (tb == 4)
-    {
-      Launch lp_(c, kKPlcp, n, s);
-      k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, st.win, phi,
-                                          st.snaps[0],
-                                          st.levels, st.h0, plcp);
-    }
-  else
-    {
-      Launch lp_(c, kKPlcp, n, s);
-      k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, st.win, phi,
-                                          st.snaps[0],
-                                          st.levels, st.h0, plcp);
-    }
+  {
+    Launch lp_(c, kKPlcp, n, s);
+    if (tb == 4)
+      k_plcp<uint32_t><<<pb, 128, 0, s>>>(static_cast<const uint32_t *>(tokens), n, st.win, st.wsb, phi, st.fin,
+                                          st.rank, st.snaps[0], st.levels, st.h0, plcp);
+    else
+      k_plcp<uint64_t><<<pb, 128, 0, s>>>(static_cast<const uint64_t *>(tokens), n, st.win, st.wsb, phi, st.fin,
+                                          st.rank, st.snaps[0], st.levels, st.h0, plcp);
+  }
   {
     Launch lp_(c, kKLcpPerm, n, s);
-    k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, st.win, lcp);
+    k_lcp_perm<<<g, 256, 0, s>>>(st.sa, plcp, n, st.wsb, lcp);
   }
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;

@@ -142,57 +142,27 @@ def test_config4_scaled(apo):
 
 
 def test_config4_full(apo):
-    """2^24 tokens: the random window bit-exact; the adversarial window against
-    invariants and sampled direct checks (the oracle's direct comparison is
-    quadratic on a constant run of 5.6M tokens)."""
-    from paper_2406_18111_gb300 import as_u32
+    """2^24 tokens, both windows, every field element by element: the random
+    window against the direct oracle, the adversarial window (a constant run
+    of 5.59M tokens, then period-2 and period-3 runs; 23 doubling rounds)
+    against the oracle's Manber-Myers suffix array and LCE comparisons."""
     a, b = W.config4_windows()
     compare(apo, b, 5)
-    r = apo.find_repeats(tokens_dev(a, 4), 5)
-    n = a.shape[0]
-    sa = as_u32(r.sa).astype(np.int64)
-    lcp = as_u32(r.lcp).astype(np.int64)
-    assert np.array_equal(np.sort(sa), np.arange(n))
-    A64 = a.astype(np.uint64)
-    rng = W.uniform_int(44, 400, 0, n - 2)
-    sub_sa = []
-    for k in rng:
-        x, y = int(sa[k]), int(sa[k + 1])
-        # direct LCP via block comparison, then the order of the next token
-        L = 0
-        step = 1 << 16
-        while x + L < n and y + L < n:
-            m = min(step, n - x - L, n - y - L)
-            eq = A64[x + L:x + L + m] == A64[y + L:y + L + m]
-            if eq.all():
-                L += m
-                continue
-            L += int(np.argmin(eq))
-            break
-        assert lcp[k] == L, (k, x, y, lcp[k], L)
-        if x + L < n and y + L < n:
-            assert A64[x + L] < A64[y + L]
-        else:
-            assert x + L == n  # a proper prefix comes first
-        sub_sa.append(k)
-    # candidates and the greedy selection: structure that holds at any size
-    cl = as_u32(r.cand_len).astype(np.int64)
-    cs = as_u32(r.cand_start).astype(np.int64)
-    acc = r.cand_accepted.cpu().numpy().astype(bool)
-    assert np.all(np.diff(cl) <= 0)
-    assert acc[0] and cl[0] == cl.max()
-    ss = as_u32(r.sel_start).astype(np.int64)
-    sl = as_u32(r.sel_len).astype(np.int64)
-    assert np.all(ss[1:] >= ss[:-1] + sl[:-1])
-    assert sorted(zip(cs[acc].tolist(), cl[acc].tolist())) == list(zip(ss.tolist(), sl.tolist()))
-    # every rejected candidate meets an accepted interval (sampled)
-    cover = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(cover, ss, 1)
-    np.add.at(cover, ss + sl, -1)
-    covered = np.cumsum(cover)[:n] > 0
-    rej = np.nonzero(~acc)[0]
-    for k in rej[:: max(1, len(rej) // 2000)]:
-        assert covered[cs[k]] or covered[cs[k] + cl[k] - 1]
+    r, o = compare(apo, a, 5, sa_method="doubling")
+    assert r.rounds >= 18  # h0 = 21 tokens per first key (3-bit codes): log2(5592405 / 21) > 18
+
+
+def test_batched_config3_full(apo):
+    """All 512 windows of config 3 (23.3M tokens) in one batched call, every
+    window's fields against the oracle (run on a pool of host threads)."""
+    import concurrent.futures as cf
+    import os
+    toks, off, periods = W.config3_windows()
+    wins = [toks[int(off[w]):int(off[w + 1])] for w in range(len(off) - 1)]
+    res = apo.find_repeats_batched(tokens_dev(toks, 4), off, 5)
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        want = list(ex.map(lambda S: oracle.find_repeats(np.asarray(S, np.uint64), 5), wins))
+    _check_batch_against(res, wins, lambda w, S: want[w])
 
 
 # ---------------------------------------------------------------- matching
@@ -403,6 +373,41 @@ def test_batched_equals_plain_and_u64(apo):
     _check_batch_against(res, wins, lambda w, S: oracle.find_repeats(S, 5))
 
 
+def _tile_cases():
+    """Windows whose doubling groups straddle the round kernel's tile span
+    (1024 list entries): periodic strings whose level groups hold about
+    n / p suffixes, with and without noise."""
+    cases = []
+    k = 0
+    for p in (1, 2, 3, 5):
+        for g in (1023, 1024, 1025, 1026, 2047, 2049, 4100):
+            n = p * g + (k % 3)
+            S = (np.arange(n) % p).astype(np.uint32)
+            if k % 2:
+                pos = W.uniform_int(700 + k, max(1, n // 200), 0, n - 1)
+                S[pos] = W.uniform_int(800 + k, len(pos), 0, 7).astype(np.uint32)
+            cases.append(S)
+            k += 1
+    return cases
+
+
+def test_doubling_tile_boundaries(apo):
+    """Group sizes around the tile span, one window per call and all of them
+    in one batched call, SA and LCP against the oracle."""
+    from paper_2406_18111_gb300 import as_u32
+    cases = _tile_cases()
+    for S in cases[::3]:
+        compare(apo, S, 5, sa_method="doubling")
+    wins = cases + [np.zeros(0, np.uint32), np.zeros(3000, np.uint32)]
+    cat, off = _concat(wins)
+    res = apo.find_repeats_batched(tokens_dev(cat, 4), off, 5)
+    for w, S in enumerate(wins):
+        a, b = int(res.win_off[w]), int(res.win_off[w + 1])
+        sa = oracle.suffix_array(np.asarray(S, np.uint64), "doubling")
+        assert np.array_equal(as_u32(res.sa[a:b]), sa), ("sa", w)
+        assert np.array_equal(as_u32(res.lcp[a:b]), oracle.lcp(np.asarray(S, np.uint64), sa)), ("lcp", w)
+
+
 # ---------------------------------------------------------------- sort shapes
 def test_sort_shapes_give_identical_results(apo):
     """Every radix-sort shape the tuner may pick gives the same bytes: the
@@ -444,6 +449,37 @@ def test_served_results_equal_alone(apo):
         for f in ("sel_start", "sel_len", "sel_trace", "trace_len", "trace_start"):
             assert np.array_equal(getattr(got, f), as_u32(getattr(alone, f))), f
             assert np.array_equal(getattr(got, f), getattr(o, f)), f
+
+
+def test_served_admission_by_footprint(apo):
+    """A pool that holds one request's footprint at a time: the second and
+    third requests wait for the one before to return its slice, never more
+    than the budget is held, results equal the plain call and the oracle,
+    and a request larger than the whole pool is refused."""
+    from paper_2406_18111_gb300 import ApoError, Server, as_u32
+    n = 1 << 18
+    fp = Server.footprint(n, 4, 5)
+    srv = Server(0, min_len=5, token_bytes=4, max_batch_tokens=1 << 24, max_batch_windows=8, lanes=2,
+                 hbm_budget=int(fp * 1.6))
+    wins = [W.periodic_window(n, 97 + 13 * k, 0.05, 1000, seed=500 + k) for k in range(3)]
+    ids = [srv.submit(S) for S in wins]
+    res = [srv.wait(i) for i in ids]
+    assert all(r.batch_windows == 1 for r in res)
+    order = sorted(res, key=lambda r: r.t_start)
+    for x, y in zip(order, order[1:]):
+        assert y.t_start >= x.t_done  # admitted only once the slice before it came back
+    mem = srv.memory()
+    assert mem["held"] == 0 and fp <= mem["held_max"] <= mem["budget"]
+    for S, got in zip(wins, res):
+        alone = apo.find_repeats(tokens_dev(S, 4), 5, stages=False)
+        o = oracle.find_repeats(S.astype(np.uint64), 5)
+        for f in ("sel_start", "sel_len", "sel_trace", "trace_len", "trace_start"):
+            assert np.array_equal(getattr(got, f), as_u32(getattr(alone, f))), f
+            assert np.array_equal(getattr(got, f), getattr(o, f)), f
+    big = srv.submit(np.zeros(2 * n, np.uint32))
+    with pytest.raises(ApoError, match="APO_ECAPACITY"):
+        srv.wait(big)
+    srv.close()
 
 
 def test_match_config5_full(apo):

@@ -47,6 +47,62 @@ def test_noalloc_greedy_matches_find_repeats(apo):
         assert int(cnt.item()) == int(r.cand_accepted.sum().item()) == int(r.sel_start.shape[0])
 
 
+def _noalloc(cl, cs, n):
+    import torch
+    from paper_2406_18111_gb300 import greedy_select_noalloc
+    m = int(cl.shape[0])
+    acc = torch.full((max(m, 1),), 7, dtype=torch.uint8, device="cuda")
+    cnt = torch.full((1,), -2, dtype=torch.int32, device="cuda")
+    greedy_select_noalloc(cl, cs, n, acc[:m], cnt)
+    torch.cuda.synchronize()
+    return acc[:m], int(cnt.item())
+
+
+def test_noalloc_window_sizes_in_sequence(apo):
+    """A window at the fixed maximum, then a small one, then the large one
+    again: no marks left from a larger window leak into a smaller one, and
+    the full bitmap is used correctly."""
+    from paper_2406_18111_gb300 import NOALLOC_MAX_WINDOW
+    big = W.periodic_window(NOALLOC_MAX_WINDOW, 4999, 0.05, 1000, seed=37)
+    small = W.config1_window()
+    for S in (big, small, big):
+        t = _window(S)
+        r = apo.find_repeats(t, 5)
+        acc, cnt = _noalloc(r.cand_len, r.cand_start, int(S.shape[0]))
+        assert acc.equal(r.cand_accepted)
+        assert cnt == int(r.cand_accepted.sum().item()) == int(r.sel_start.shape[0])
+
+
+def test_noalloc_batch_boundary_and_empty(apo):
+    """Hand-built candidate lists of exactly 1024 and 1025 entries (the
+    kernel's batch size and one past it) against the oracle's greedy; no
+    candidates at all gives a count of 0."""
+    import torch
+    import oracle
+    n = 5000
+    for m in (1024, 1025, 1):
+        ln = np.sort(W.uniform_int(60 + m, m, 1, 40))[::-1].astype(np.uint32)
+        st = (W.uniform_int(70 + m, m, 0, n - 41)).astype(np.uint32)
+        want = oracle.greedy(n, ln, st)
+        cl = torch.from_numpy(ln.view(np.int32).copy()).cuda()
+        cs = torch.from_numpy(st.view(np.int32).copy()).cuda()
+        acc, cnt = _noalloc(cl, cs, n)
+        assert np.array_equal(acc.cpu().numpy(), want), m
+        assert cnt == int(want.sum())
+    z = torch.zeros(0, dtype=torch.int32, device="cuda")
+    acc, cnt = _noalloc(z, z, n)
+    assert cnt == 0
+
+
+def test_noalloc_flags_increasing_length(apo):
+    """A list whose lengths increase breaks the precondition; the count says so."""
+    import torch
+    cl = torch.tensor([3, 5, 2], dtype=torch.int32, device="cuda")
+    cs = torch.tensor([0, 10, 20], dtype=torch.int32, device="cuda")
+    _, cnt = _noalloc(cl, cs, 100)
+    assert cnt == -1
+
+
 def test_noalloc_rejects_oversized_window(apo):
     import torch
     from paper_2406_18111_gb300 import NOALLOC_MAX_WINDOW, ApoError, greedy_select_noalloc
