@@ -135,7 +135,7 @@ const char *const kKernelNames[kKCount] = {
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
-    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact"};
+    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact", "minor"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {

@@ -70,6 +70,51 @@ __device__ uint32_t lb_exclusive(const uint64_t *status, int stride, uint32_t t,
   return acc;
 }
 
+// The same walk by a whole warp, for a commutative operator: lane l reads
+// the word of tile hi - l, so 32 predecessors are combined per step instead
+// of one.  Every lane of the warp must call it; all receive the result.
+// The words nearer than the first inclusive one must all be published
+// before the step is taken; otherwise the warp polls them again (bounded as
+// above, then kDevTimeout).
+template <class Op>
+__device__ uint32_t lb_exclusive_warp(const uint64_t *status, int stride, uint32_t t, uint32_t epoch, Op op,
+                                      uint32_t identity, uint32_t *err) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t acc = identity;
+  long long hi = (long long)t - 1;  // the nearest tile not combined yet
+  uint32_t spins = 0;
+  while (hi >= 0) {
+    const long long j = hi - (long long)lane;
+    bool ready = true, incl = true;  // past tile 0: nothing to combine, the walk ends
+    uint32_t val = identity;
+    if (j >= 0) {
+      const uint64_t w = lb_load(status + (size_t)j * stride);
+      const uint32_t st = (uint32_t)(w >> 62), ep = (uint32_t)(w >> 32) & 0x3fffffffu;
+      ready = ep == epoch && st != kLbNone;
+      incl = ready && st == kLbInclusive;
+      val = (uint32_t)w;
+    }
+    const uint32_t incl_mask = __ballot_sync(0xffffffffu, incl);
+    const uint32_t first = incl_mask ? (uint32_t)(__ffs(incl_mask) - 1) : 32u;  // nearest inclusive word
+    const uint32_t need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (__ballot_sync(0xffffffffu, !ready) & need) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicExch(err, kDevTimeout);
+        break;
+      }
+      if (spins > 32) __nanosleep(128);
+      continue;
+    }
+    uint32_t v = (lane <= first && j >= 0) ? val : identity;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    acc = op(acc, v);
+    if (first < 32) break;
+    hi -= 32;
+  }
+  return acc;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -95,6 +95,35 @@ __device__ __forceinline__ uint32_t level_rank(const uint8_t *__restrict__ fin, 
   return f < L ? rank[j] : snap[j];
 }
 
+// Decoupled look-back: lb_publish stores the tile's aggregate, lb_resolve
+// walks back to the sum over tiles < t and stores the tile's inclusive
+// prefix; lb_sum does both.  A tile should resolve right after it publishes:
+// a walk back only ends at an inclusive prefix, so tiles that resolve late
+// make their successors' walks long.
+__device__ __forceinline__ void lb_publish(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch) {
+  lb_store(&st[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, v));
+}
+__device__ __forceinline__ uint32_t lb_resolve(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
+                                               uint32_t *err) {
+  if (t == 0) return 0;
+  const uint32_t p = lb_exclusive(st, 1, t, epoch, OpSum(), 0u, err);
+  lb_store(&st[t], lb_pack(kLbInclusive, epoch, p + v));
+  return p;
+}
+__device__ __forceinline__ uint32_t lb_sum(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch, uint32_t *err) {
+  lb_publish(st, t, v, epoch);
+  return lb_resolve(st, t, v, epoch, err);
+}
+// The same by a whole warp (every lane calls it; all get the prefix).
+__device__ __forceinline__ uint32_t lb_sum_warp(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
+                                                uint32_t *err) {
+  if ((threadIdx.x & 31) == 0) lb_publish(st, t, v, epoch);
+  if (t == 0) return 0;
+  const uint32_t p = lb_exclusive_warp(st, 1, t, epoch, OpSum(), 0u, err);
+  if ((threadIdx.x & 31) == 0) lb_store(&st[t], lb_pack(kLbInclusive, epoch, p + v));
+  return p;
+}
+
 // ---------------------------------------------------------------- settling sorted groups
 // Sorted (key, suffix) pairs -> groups of equal keys.  Every suffix gets its
 // level rank (the slot where its group starts) in snap; with `finals` a
@@ -166,23 +195,21 @@ __global__ void __launch_bounds__(kST) k_split(
   const uint32_t ex_max = block_exclusive<kST / 32>(tmax, OpMax(), 0u, scr, &tot_max);
   const uint32_t ex_sum = kBig ? 0u : block_exclusive<kST / 32>(tcnt, OpSum(), 0u, scr, &tot_sum);
   const int any_head = __syncthreads_or(thead);
-  if (tid == 0) {
-    const bool incl = t == 0 || any_head;
-    lb_store(&st_max[t], lb_pack(incl ? kLbInclusive : kLbAggregate, epoch, tot_max));
+  if (tid < 32) {
+    const bool incl = t == 0 || any_head;  // a tile with a group start knows its maximum
+    if (tid == 0) lb_store(&st_max[t], lb_pack(incl ? kLbInclusive : kLbAggregate, epoch, tot_max));
     uint32_t pm = 0;
-    if (t > 0) pm = lb_exclusive(st_max, 1, t, epoch, OpMax(), 0u, err);
-    if (!incl) lb_store(&st_max[t], lb_pack(kLbInclusive, epoch, max(pm, tot_max)));
-    s_pmax = pm;
-  }
-  if (!kBig && tid == 32) {
-    lb_store(&st_sum[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot_sum));
-    uint32_t ps = 0;
-    if (t > 0) {
-      ps = lb_exclusive(st_sum, 1, t, epoch, OpSum(), 0u, err);
-      lb_store(&st_sum[t], lb_pack(kLbInclusive, epoch, ps + tot_sum));
+    if (t > 0) pm = lb_exclusive_warp(st_max, 1, t, epoch, OpMax(), 0u, err);
+    if (tid == 0) {
+      if (!incl) lb_store(&st_max[t], lb_pack(kLbInclusive, epoch, max(pm, tot_max)));
+      s_pmax = pm;
     }
-    s_psum = ps;
-    if (finals && base + cnt == N) *count_out = ps + tot_sum;
+  } else if (!kBig && tid < 64) {
+    const uint32_t ps = lb_sum_warp(st_sum, t, tot_sum, epoch, err);
+    if (tid == 32) {
+      s_psum = ps;
+      if (finals && base + cnt == N) *count_out = ps + tot_sum;
+    }
   }
   __syncthreads();
   uint32_t hq = max(s_pmax, ex_max);  // index of the current group's first element
@@ -336,26 +363,31 @@ __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t 
 // ---------------------------------------------------------------- a doubling round
 constexpr int kRdT = 1024;                     // list entries per tile
 constexpr int kRdBig = 128;                    // a group with more entries is sorted globally ("big")
-constexpr int kRdThreads = 256, kRdItems = 8;  // items: rows of kRdThreads positions
+constexpr int kRdThreads = 256;
 constexpr int kRdWarps = kRdThreads / 32;
-constexpr int kRdDigit = 9;                    // digit bits of the warp-level sort
+constexpr int kRdDigit = 9;                    // digit bits of the in-tile sort
 constexpr int kRdRadix = 1 << kRdDigit;
 constexpr int kRdWin = kRdT + kRdBig + 1;      // positions a tile reads: its span and the next kRdBig + 1
+constexpr int kRdRows = (kRdWin + kRdThreads - 1) / kRdThreads;  // rows of kRdThreads positions
+constexpr int kRdPosBits = 11;                 // bits of a position in a sort key
 constexpr int kRdHw0 = kRdBig + 2;             // list heads read before the span
 constexpr int kRdHw = kRdWin + kRdHw0;
 constexpr int kRdGroups = kRdWin / 2 + 2;      // group starts in the window (groups have two entries or more)
 constexpr uint32_t kRdNoGroup = 0xffff;
-static_assert(kRdWin <= kRdItems * kRdThreads, "rows cover the window");
+static_assert(kRdWin <= (1 << kRdPosBits), "positions fit the key");
 static_assert(kRdGroups < kRdNoGroup, "group numbers fit 16 bits");
-constexpr size_t kRoundSmem = (size_t)kRdHw * 4               // list heads
-                              + (size_t)kRdWin * 4 * 3         // minor keys (two buffers), suffixes
-                              + (size_t)(kRdGroups + 1) * 4    // group starts
-                              + (size_t)kRdGroups * 4 * 3      // group heads, big indices, first big entries
-                              + (size_t)kRdWin * 2 * 3         // positions (two buffers), group of each position
+static_assert(kRdRadix % kRdThreads == 0, "each thread owns whole digits");
+constexpr size_t kRoundSmem = (size_t)kRdWin * 8 * 2           // sort keys (two buffers)
+                              + (size_t)kRdHw * 4               // list heads
+                              + (size_t)kRdWin * 4 * 2          // minor keys, suffixes by position
+                              + (size_t)(kRdGroups + 1) * 4     // group starts
+                              + (size_t)kRdGroups * 4 * 3       // group heads, big indices, first entries
+                              + (size_t)kRdWin * 2              // group of each position
                               + (size_t)kRdWarps * kRdRadix * 2;  // per-warp digit counts
 
 struct RoundArgs {
   const uint32_t *lid, *lhd;   // this round's list: suffix, head slot of its group
+  const uint32_t *mkey;        // minor key of each entry (k_minor)
   uint32_t ub;                 // launch bound on the list length
   const uint32_t *A_dev;       // the list length
   uint32_t r, h, n;            // round, doubling offset, positions
@@ -382,215 +414,95 @@ struct RoundArgs {
 
 __device__ __forceinline__ int bits_for_dev(uint32_t v) { return v ? 32 - __clz(v) : 0; }
 
-// Decoupled look-back in two steps, so that a tile publishes its aggregate
-// as soon as it knows it and waits for its predecessors only when it needs
-// the prefix: lb_publish, later lb_resolve (the sum over tiles < t; also
-// publishes the tile's inclusive prefix).
-__device__ __forceinline__ void lb_publish(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch) {
-  lb_store(&st[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, v));
-}
-__device__ __forceinline__ uint32_t lb_resolve(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
-                                               uint32_t *err) {
-  if (t == 0) return 0;
-  const uint32_t p = lb_exclusive(st, 1, t, epoch, OpSum(), 0u, err);
-  lb_store(&st[t], lb_pack(kLbInclusive, epoch, p + v));
-  return p;
-}
-
-// Exclusive prefix over the tile's items in the strided order p = i *
-// kRdThreads + tid (rows i < rows), from each item's flag or value.  `vals`
-// holds one value per row for this thread; `op` combines (sum or max) with
-// identity 0.  Warp ballots / shuffles inside a row, one shared-memory pass
-// over the (row, warp) totals.  Returns the exclusive prefixes in `ex`.
-template <class Op>
-__device__ __forceinline__ void rows_exclusive(const uint32_t (&vals)[kRdItems], int rows, Op op,
-                                               uint32_t *rowtot /* [kRdItems * kRdWarps + 1] */,
-                                               uint32_t (&ex)[kRdItems], uint32_t *total) {
+// Exclusive counts of flags over the tile's rows (item (i, tid) is number
+// i * kRdThreads + tid; bit i of `bits` is row i's flag): warp ballots, one
+// pass of warp 0 over the (row, warp) counts.  ex[i] receives the flags
+// before item (i, tid); *total all of them.
+__device__ __forceinline__ void flags_exclusive(uint32_t bits, int rows, uint32_t *rowtot,
+                                                uint32_t (&ex)[kRdRows], uint32_t *total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t inc[kRdItems];
+  const uint32_t lt = lanemask_lt();
+  uint32_t pre[kRdRows];
 #pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
+  for (int i = 0; i < kRdRows; ++i) {
     if (i >= rows) break;
-    inc[i] = warp_inclusive(vals[i], op);
-    if (lane == 31) rowtot[i * kRdWarps + warp] = inc[i];
+    const uint32_t b = __ballot_sync(0xffffffffu, (bits >> i) & 1u);
+    pre[i] = __popc(b & lt);
+    if (lane == 0) rowtot[i * kRdWarps + warp] = __popc(b);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {  // (row, warp) totals in row-major order -> exclusive prefixes
-    uint32_t run = 0;
-    for (int q = 0; q < rows * kRdWarps; ++q) {
-      const uint32_t v = rowtot[q];
-      rowtot[q] = run;
-      run = op(run, v);
-    }
-    rowtot[kRdItems * kRdWarps] = run;
+  if (warp == 0) {  // (row, warp) counts in row-major order: 2 per lane
+    const int m = rows * kRdWarps;
+    const uint32_t c0 = 2 * lane < m ? rowtot[2 * lane] : 0u, c1 = 2 * lane + 1 < m ? rowtot[2 * lane + 1] : 0u;
+    const uint32_t inc = warp_inclusive(c0 + c1, OpSum());
+    if (2 * lane < m) rowtot[2 * lane] = inc - c0 - c1;
+    if (2 * lane + 1 < m) rowtot[2 * lane + 1] = inc - c1;
+    if (lane == 31) rowtot[kRdRows * kRdWarps] = inc;
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
+  for (int i = 0; i < kRdRows; ++i) {
     if (i >= rows) break;
-    const uint32_t before = __shfl_up_sync(0xffffffffu, inc[i], 1);
-    ex[i] = op(rowtot[i * kRdWarps + warp], lane ? before : 0u);
+    ex[i] = rowtot[i * kRdWarps + warp] + pre[i];
   }
-  *total = rowtot[kRdItems * kRdWarps];
+  *total = rowtot[kRdRows * kRdWarps];
   __syncthreads();
 }
 
-// One warp settles one owned group: its entries' minor keys m (u32) and
-// positions are at [q0, q0 + s) of (mA, pA); the group is list entries
-// lbase + q0 ...  Writes every entry's new level rank, settles the
-// singletons, and writes the others in place to the holed next list, in
-// sorted order (a singleton's place becomes a hole).
-__device__ __forceinline__ void settle_group(const RoundArgs &a, uint32_t lbase, uint32_t q0, uint32_t s,
-                                             uint32_t head0, uint32_t *mA, uint16_t *pA, uint32_t *mB,
-                                             uint16_t *pB, uint16_t *wc, const uint32_t *sid) {
-  const uint32_t lane = threadIdx.x & 31, lt = lanemask_lt();
-  // one entry, sorted: its position k in the group, its subgroup's first
-  // position hk, whether it is alone in its subgroup
-  auto put = [&](uint32_t id, uint32_t k, uint32_t hk, bool alone) {
-    const uint32_t slot = head0 + k, head = head0 + hk, at = lbase + q0 + k;
-    if (id >= a.n || slot >= a.n || at >= a.ub) {
-      atomicExch(a.err, kDevRange);
-      return;
-    }
-    a.snap_cur[id] = head;
-    if (alone) {
-      a.sa[slot] = id;
-      a.rank[id] = slot;
-      a.fin[id] = (uint8_t)a.r;
-      a.hhd[at] = kHole;
-    } else {
-      a.hid[at] = id;
-      a.hhd[at] = head;
-    }
-  };
-  if (s <= 32) {
-    // rank by counting: sorted position = #smaller + #equal before
-    const bool v = lane < s;
-    const uint32_t m = v ? mA[q0 + lane] : 0u;
-    uint32_t less = 0, eq = 0, eqb = 0;
-    for (uint32_t j = 0; j < s; ++j) {
-      const uint32_t mj = __shfl_sync(0xffffffffu, m, j);
-      less += mj < m;
-      eq += mj == m;
-      eqb += (mj == m) & (j < lane);
-    }
-    if (v) put(sid[q0 + lane], less + eqb, less, eq == 1);
-    return;
-  }
-  // larger groups: warp-level LSD radix sort of (m - min) with 9-bit digits,
-  // stable (rows of 32 in order), counts in this warp's shared counters
-  const uint32_t rows = (s + 31) / 32;
-  uint32_t mn = 0xffffffffu, mx = 0;
-  for (uint32_t r = 0; r < rows; ++r) {
-    const uint32_t q = q0 + r * 32 + lane;
-    if (q < q0 + s) {
-      mn = min(mn, mA[q]);
-      mx = max(mx, mA[q]);
-    }
-  }
+// Minor key of every list entry of round r: rank_{r-1}[i + h] + 1, or 0
+// when i + h is past the window's end (absolute slots).  A streaming pass
+// with independent loads in flight, so that the round kernel reads the keys
+// in order instead of chasing three dependent loads per entry.
+__global__ void __launch_bounds__(256) k_minor(const uint32_t *__restrict__ lid, uint32_t ub,
+                                               const uint32_t *__restrict__ A_dev, uint32_t r, uint32_t h,
+                                               uint32_t n, const uint32_t *__restrict__ wsb,
+                                               const uint8_t *__restrict__ fin, const uint32_t *__restrict__ rank,
+                                               const uint32_t *__restrict__ snap_prev, uint32_t *__restrict__ mout) {
+  constexpr int kI = 4;
+  const uint32_t A = min(ub, *A_dev);
+  for (uint64_t k0 = ((uint64_t)blockIdx.x * blockDim.x) * kI + threadIdx.x; k0 < A;
+       k0 += (uint64_t)gridDim.x * blockDim.x * kI) {
+    uint32_t j[kI];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  const int bits = bits_for_dev(mx - mn);
-  uint32_t *ms = mA, *md = mB;
-  uint16_t *ps = pA, *pd = pB;
-  for (int sh = 0; sh < bits; sh += kRdDigit) {
-    for (int d = lane; d < kRdRadix; d += 32) wc[d] = 0;
-    __syncwarp();
-    // counts
-    for (uint32_t r = 0; r < rows; ++r) {
-      const uint32_t q = q0 + r * 32 + lane;
-      const bool v = q < q0 + s;
-      const uint32_t d = v ? ((ms[q] - mn) >> sh) & (kRdRadix - 1) : (uint32_t)kRdRadix;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (v && (peers & lt) == 0) wc[d] += (uint16_t)__popc(peers);
-      __syncwarp();
+    for (int u = 0; u < kI; ++u) {
+      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
+      const uint32_t i = k < A ? lid[k] : n;
+      const uint32_t x = i < n ? i + h : n;
+      j[u] = (x >= n || (wsb && bit_at(wsb, x))) ? n : x;  // n: past the end
     }
-    // exclusive prefix over the digits (lane owns kRdRadix / 32 consecutive digits)
-    constexpr int kPer = kRdRadix / 32;
-    uint32_t run = 0;
+    uint8_t fb[kI];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) run += wc[lane * kPer + k];
-    uint32_t inc = run;
+    for (int u = 0; u < kI; ++u) fb[u] = j[u] < n ? fin[j[u]] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= (uint32_t)o) inc += y;
+    for (int u = 0; u < kI; ++u) {
+      const uint64_t k = k0 + (uint64_t)u * blockDim.x;
+      if (k < A) mout[k] = j[u] < n ? ((uint32_t)fb[u] < r - 1 ? rank[j[u]] : snap_prev[j[u]]) + 1 : 0u;
     }
-    uint32_t b = inc - run;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const uint32_t c = wc[lane * kPer + k];
-      wc[lane * kPer + k] = (uint16_t)b;
-      b += c;
-    }
-    __syncwarp();
-    // scatter in order
-    for (uint32_t r = 0; r < rows; ++r) {
-      const uint32_t q = q0 + r * 32 + lane;
-      const bool v = q < q0 + s;
-      const uint32_t mv = v ? ms[q] : 0u;
-      const uint32_t d = v ? ((mv - mn) >> sh) & (kRdRadix - 1) : (uint32_t)kRdRadix;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      uint32_t base = 0;
-      if (v) base = wc[d];
-      __syncwarp();
-      if (v) {
-        const uint32_t dst = q0 + base + __popc(peers & lt);
-        md[dst] = mv;
-        pd[dst] = ps[q];
-        if ((peers & lt) == 0) wc[d] = (uint16_t)(base + __popc(peers));
-      }
-      __syncwarp();
-    }
-    uint32_t *xm = ms;
-    ms = md;
-    md = xm;
-    uint16_t *xp = ps;
-    ps = pd;
-    pd = xp;
-  }
-  // settle in sorted order: subgroups of equal m
-  uint32_t hcarry = 0;  // position (in the group) of the last subgroup start so far
-  for (uint32_t r = 0; r < rows; ++r) {
-    const uint32_t k = r * 32 + lane;  // position in the group
-    const bool v = k < s;
-    const uint32_t m = v ? ms[q0 + k] : 0u;
-    const bool st = v && (k == 0 || ms[q0 + k - 1] != m);
-    const bool en = v && (k + 1 == s || ms[q0 + k + 1] != m);
-    // last start at or before this lane
-    const uint32_t sm = __ballot_sync(0xffffffffu, st) & (lt | (1u << lane));
-    const uint32_t hk = sm ? r * 32 + (31 - __clz(sm)) : hcarry;
-    const uint32_t all = __ballot_sync(0xffffffffu, st);
-    if (all) hcarry = r * 32 + (31 - __clz(all));
-    if (v) put(sid[ps[q0 + k]], k, hk, st && en);
   }
 }
 
 __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  // positions q of the tile's window are list entries base + q; hw holds the
-  // list heads from base - kRdHw0 on
-  uint32_t *hw = reinterpret_cast<uint32_t *>(smem);  // [kRdHw]
-  uint32_t *mA = hw + kRdHw;                           // [kRdWin] minor keys
-  uint32_t *mB = mA + kRdWin;
-  uint32_t *sid = mB + kRdWin;                         // [kRdWin] suffix by position
+  // positions q of the tile's window are list entries base + q
+  uint64_t *ka = reinterpret_cast<uint64_t *>(smem);  // [kRdWin] sort keys of the small groups' entries
+  uint64_t *kb = ka + kRdWin;
+  uint32_t *hw = reinterpret_cast<uint32_t *>(kb + kRdWin);  // [kRdHw] list heads from base - kRdHw0
+  uint32_t *mv = hw + kRdHw;                           // [kRdWin] minor key by position
+  uint32_t *sid = mv + kRdWin;                         // [kRdWin] suffix by position
   uint32_t *gst = sid + kRdWin;                        // [kRdGroups + 1] group start positions
   uint32_t *ghd = gst + kRdGroups + 1;                 // [kRdGroups] group head slots
   uint32_t *gbx = ghd + kRdGroups;                     // [kRdGroups] big group: its index; small: kNone
-  uint32_t *gbp = gbx + kRdGroups;                     // [kRdGroups] big group: its first big entry
-  uint16_t *pA = reinterpret_cast<uint16_t *>(gbp + kRdGroups);  // [kRdWin] positions
-  uint16_t *pB = pA + kRdWin;
-  uint16_t *gid = pB + kRdWin;                         // [kRdWin] group of each position (kRdNoGroup: covering)
+  uint32_t *gfs = gbx + kRdGroups;                     // [kRdGroups] big: first big entry; small: first sorted entry
+  uint16_t *gid = reinterpret_cast<uint16_t *>(gfs + kRdGroups);  // [kRdWin] group of each position
   uint16_t *wcs = gid + kRdWin;                        // [kRdWarps][kRdRadix] per-warp digit counts
-  __shared__ uint32_t rowtot[kRdItems * kRdWarps + 1];
-  __shared__ uint32_t s_tile, s_G, s_BC, s_BS, s_gnext, s_cov;
+  __shared__ uint32_t rowtot[kRdRows * kRdWarps + 1];
+  __shared__ uint32_t s_tile, s_G, s_BC, s_BS, s_cov, s_mmin, s_mmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
   if (tid == 0) {
     s_tile = atomicAdd(a.tile_ctr, 1u);
-    s_gnext = 0;
+    s_mmin = kNone;
+    s_mmax = 0;
   }
   const uint32_t A = min(a.ub, *a.A_dev);
   __syncthreads();
@@ -601,32 +513,58 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
   const uint32_t span_end = min(base + (uint32_t)kRdT, A);
   const uint32_t span = span_end - base;
   const uint32_t lim = min(A - base, span + (uint32_t)kRdBig + 1);  // positions read: [0, lim)
-  // list heads of entries base - kRdHw0 .. base + lim - 1
-  for (uint32_t q = tid; q < lim + kRdHw0; q += kRdThreads) {
-    const long long k = (long long)base - kRdHw0 + q;
-    hw[q] = k >= 0 ? a.lhd[k] : kNone;
+  // list heads of entries base - kRdHw0 .. base + lim - 1; suffixes and
+  // minor keys of entries base .. base + lim - 1 (all loads at once)
+  {
+    constexpr int kHr = (kRdHw + kRdThreads - 1) / kRdThreads;
+    uint32_t rh[kHr], ri[kRdRows], rm[kRdRows];
+#pragma unroll
+    for (int i = 0; i < kHr; ++i) {
+      const uint32_t q = i * kRdThreads + tid;
+      const long long k = (long long)base - kRdHw0 + q;
+      rh[i] = (q < lim + kRdHw0 && k >= 0) ? a.lhd[k] : kNone;
+    }
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      const uint32_t q = i * kRdThreads + tid;
+      ri[i] = q < lim ? a.lid[base + q] : 0u;
+      rm[i] = q < lim ? a.mkey[base + q] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kHr; ++i) {
+      const uint32_t q = i * kRdThreads + tid;
+      if (q < lim + kRdHw0) hw[q] = rh[i];
+    }
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      const uint32_t q = i * kRdThreads + tid;
+      if (q < lim) {
+        sid[q] = ri[i];
+        mv[q] = rm[i];
+      }
+    }
   }
   __syncthreads();
-  // group starts among positions [0, lim); their indices by one scan
+  // group starts among positions [0, lim), numbered in order
   const int rows = (int)((lim + kRdThreads - 1) / kRdThreads);
-  uint32_t st[kRdItems], gex[kRdItems], gall;
+  uint32_t stb = 0, gex[kRdRows], gall;
 #pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
-    st[i] = 0;
+  for (int i = 0; i < kRdRows; ++i) {
     if (i >= rows) break;
     const uint32_t q = i * kRdThreads + tid;
-    if (q < lim) st[i] = hw[q + kRdHw0] != hw[q + kRdHw0 - 1] ? 1u : 0u;
+    if (q < lim && hw[q + kRdHw0] != hw[q + kRdHw0 - 1]) stb |= 1u << i;
   }
-  rows_exclusive(st, rows, OpSum(), rowtot, gex, &gall);
+  flags_exclusive(stb, rows, rowtot, gex, &gall);
   gall = min(gall, (uint32_t)kRdGroups);
 #pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
+  for (int i = 0; i < kRdRows; ++i) {
     if (i >= rows) break;
     const uint32_t q = i * kRdThreads + tid;
     if (q < lim) {
-      if (st[i] && gex[i] < kRdGroups) gst[gex[i]] = q;
-      if (st[i] && gex[i] >= kRdGroups) atomicExch(a.err, kDevRange);  // list groups have two entries or more
-      gid[q] = gex[i] + st[i] == 0 ? (uint16_t)kRdNoGroup : (uint16_t)(gex[i] + st[i] - 1);
+      const uint32_t s = (stb >> i) & 1u;
+      if (s && gex[i] < kRdGroups) gst[gex[i]] = q;
+      if (s && gex[i] >= kRdGroups) atomicExch(a.err, kDevRange);  // list groups have two entries or more
+      gid[q] = gex[i] + s == 0 ? (uint16_t)kRdNoGroup : (uint16_t)min(gex[i] + s - 1, (uint32_t)kRdGroups - 1);
     }
   }
   __syncthreads();
@@ -640,146 +578,283 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
     }
     s_G = lo;
     gst[gall] = lim == A - base ? lim : kNone;
-  }
-  __syncthreads();
-  const uint32_t G = s_G;
-  const uint32_t f = G ? gst[0] : span;  // entries before f belong to a group that started earlier
-  // per group starting in the span: head, big or small, big entries in the span
-  uint32_t bflag[kRdItems], bent[kRdItems], bfx[kRdItems], bex[kRdItems], bs_tile, bc_groups;
-  const int grows = (int)((G + kRdThreads - 1) / kRdThreads);
-#pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
-    bflag[i] = 0;
-    bent[i] = 0;
-    if (i >= grows) break;
-    const uint32_t g = i * kRdThreads + tid;
-    if (g < G) {
-      const uint32_t q0 = gst[g], nx = gst[g + 1];
-      ghd[g] = hw[q0 + kRdHw0];
-      const bool big = nx == kNone || nx - q0 > (uint32_t)kRdBig;
-      bflag[i] = big;
-      bent[i] = big ? min(nx == kNone ? span : nx, span) - q0 : 0u;
-    }
-  }
-  rows_exclusive(bflag, grows, OpSum(), rowtot, bfx, &bs_tile);
-  rows_exclusive(bent, grows, OpSum(), rowtot, bex, &bc_groups);
-  // the covering group [0, f): big iff it has more than kRdBig entries, i.e.
-  // it covers the whole span or the entry kRdBig places before its end is
-  // still in it
-  if (tid == 0) {
+    // the group covering [0, f): big iff it has more than kRdBig entries, i.e.
+    // it covers the whole span or the entry kRdBig places before its end is
+    // still in it
+    const uint32_t f = lo ? gst[0] : span;
     bool cov = false;
     if (f > 0) {
-      if (G == 0 && span == (uint32_t)kRdT) {
+      if (lo == 0 && span == (uint32_t)kRdT) {
         cov = true;
       } else {
-        const long long x = (long long)(G ? f : A - base) - kRdBig - 1;  // relative to base, >= -kRdBig - 1
+        const long long x = (long long)(lo ? f : A - base) - kRdBig - 1;  // relative to base, >= -kRdBig - 1
         cov = (long long)base + x >= 0 && hw[x + kRdHw0] == hw[kRdHw0];
       }
     }
     s_cov = cov;
   }
+  __syncthreads();
+  const uint32_t G = s_G;
+  const uint32_t f = G ? gst[0] : span;  // entries before f belong to a group that started earlier
+  const bool cov_big = s_cov != 0;
+  // big groups: more than kRdBig entries (or not ending in the window)
+  const int grows = (int)((G + kRdThreads - 1) / kRdThreads);
+  uint32_t gbb = 0, gbxe[kRdRows], bs_tile;
 #pragma unroll
-  for (int i = 0; i < kRdItems; ++i) {
+  for (int i = 0; i < kRdRows; ++i) {
     if (i >= grows) break;
     const uint32_t g = i * kRdThreads + tid;
     if (g < G) {
-      gbx[g] = bflag[i] ? bfx[i] : kNone;
-      gbp[g] = bex[i];
+      const uint32_t q0 = gst[g], nx = gst[g + 1];
+      ghd[g] = hw[q0 + kRdHw0];
+      if (nx == kNone || nx - q0 > (uint32_t)kRdBig) gbb |= 1u << i;
     }
   }
+  flags_exclusive(gbb, grows, rowtot, gbxe, &bs_tile);
+#pragma unroll
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= grows) break;
+    const uint32_t g = i * kRdThreads + tid;
+    if (g < G) gbx[g] = ((gbb >> i) & 1u) ? gbxe[i] : kNone;
+  }
   __syncthreads();
-  const bool cov_big = s_cov != 0;
-  const uint32_t cov_cnt = cov_big ? f : 0u;
-  const uint32_t bc = cov_cnt + bc_groups;
-  // the tile's big entries and big groups are known: published now, the
-  // prefixes over the tiles before are read at the end
-  if (tid == 0) lb_publish(a.st_bc, t, bc, a.epoch);
-  if (tid == 32) lb_publish(a.st_bs, t, bs_tile, a.epoch);
-  // the positions whose minor keys are needed: the covering group when it is
-  // big, every group starting in the span (a small one to its end)
+  // per position: in a small group of this tile (sorted here), or a big
+  // entry of the span (keyed for the global sort); their numbers in order
   uint32_t gend = span;
   if (G && gbx[G - 1] == kNone) gend = max(gend, gst[G]);
-  const uint32_t g0 = cov_big ? 0u : f;
   const int mrows = (int)((gend + kRdThreads - 1) / kRdThreads);
-
-  // ---- gather: suffix, then the level of the suffix h ahead, then its rank
-  {
-    uint32_t id[kRdItems], jj[kRdItems];
-    uint8_t fb[kRdItems];
+  uint32_t smb = 0, bgb = 0;
 #pragma unroll
-    for (int i = 0; i < kRdItems; ++i) {
-      if (i >= mrows) break;
-      const uint32_t q = i * kRdThreads + tid;
-      id[i] = (q >= g0 && q < gend) ? a.lid[base + q] : a.n;
-    }
-#pragma unroll
-    for (int i = 0; i < kRdItems; ++i) {
-      if (i >= mrows) break;
-      const uint32_t j = id[i] < a.n ? id[i] + a.h : a.n;
-      jj[i] = (j >= a.n || (a.wsb && bit_at(a.wsb, j))) ? a.n : j;  // a.n: past the end
-      fb[i] = jj[i] < a.n ? a.fin[jj[i]] : 0;
-    }
-#pragma unroll
-    for (int i = 0; i < kRdItems; ++i) {
-      if (i >= mrows) break;
-      const uint32_t q = i * kRdThreads + tid;
-      if (q < gend) {
-        mA[q] = jj[i] < a.n ? ((uint32_t)fb[i] < a.r - 1 ? a.rank[jj[i]] : a.snap_prev[jj[i]]) + 1 : 0u;
-        sid[q] = id[i];
-        pA[q] = (uint16_t)q;
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= mrows) break;
+    const uint32_t q = i * kRdThreads + tid;
+    if (q < gend) {
+      if (q < f) {
+        if (cov_big) bgb |= 1u << i;
+      } else {
+        const uint32_t g = gid[q];
+        if (g < G && gbx[g] == kNone) smb |= 1u << i;
+        else if (g < G && q < span) bgb |= 1u << i;
       }
+    }
+  }
+  uint32_t sx[kRdRows], bx[kRdRows], S, bc;
+  flags_exclusive(smb, mrows, rowtot, sx, &S);
+  flags_exclusive(bgb, mrows, rowtot, bx, &bc);
+  // the tile's big entries and big groups are known: their prefixes over the
+  // tiles before, resolved at once so that inclusive prefixes spread through
+  // the tiles in flight and every walk back stays short
+  if (warp == 0) {
+    const uint32_t p = lb_sum_warp(a.st_bc, t, bc, a.epoch, a.err);
+    if (lane == 0) s_BC = p;
+  } else if (warp == 1) {
+    const uint32_t p = lb_sum_warp(a.st_bs, t, bs_tile, a.epoch, a.err);
+    if (lane == 0) s_BS = p;
+  }
+  // a group's first small or big entry
+#pragma unroll
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= mrows) break;
+    const uint32_t q = i * kRdThreads + tid;
+    if (q >= f && q < gend && ((stb >> i) & 1u)) {
+      const uint32_t g = gid[q];
+      if (g < G) gfs[g] = ((smb >> i) & 1u) ? sx[i] : bx[i];
+    }
+  }
+
+  // the small groups' minor key range
+  {
+    uint32_t lmin = kNone, lmax = 0;
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      if (i >= mrows) break;
+      if ((smb >> i) & 1u) {
+        const uint32_t m = mv[i * kRdThreads + tid];
+        lmin = min(lmin, m);
+        lmax = max(lmax, m);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+      lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    }
+    if (lane == 0 && lmin != kNone) {
+      atomicMin(&s_mmin, lmin);
+      atomicMax(&s_mmax, lmax);
     }
   }
   __syncthreads();
 
-  // ---- small groups: one warp each, settled in place
+  // ---- the small groups' entries sorted by (group, minor), block-wide LSD
+  // radix with kRdDigit-bit digits, stable: warp w ranks the contiguous
+  // entries [w * R, (w + 1) * R) in order
+  const uint32_t mmin = s_mmin;
+  const int mbits = S ? bits_for_dev(s_mmax - mmin) : 0;
+  const int gbits = bits_for_dev(G ? G - 1 : 0);
+  const int B = gbits + mbits;
+#pragma unroll
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= mrows) break;
+    const uint32_t q = i * kRdThreads + tid;
+    if ((smb >> i) & 1u)
+      ka[sx[i]] = ((((uint64_t)gid[q] << mbits) | (uint64_t)(mv[q] - mmin)) << kRdPosBits) | q;
+  }
+  __syncthreads();
+  uint64_t *src = ka, *dst = kb;
+  const int srows = (int)((S + kRdThreads - 1) / kRdThreads);  // rows of 32 per warp
+  const uint32_t R = (uint32_t)srows * 32;
+  for (int sh = kRdPosBits; sh < kRdPosBits + B && S > 1; sh += kRdDigit) {
+    uint16_t *mywc = wcs + warp * kRdRadix;
+    for (int d = lane; d < kRdRadix; d += 32) mywc[d] = 0;
+    __syncwarp();
+    uint32_t rk[kRdRows], dg[kRdRows];
+    uint64_t kr[kRdRows];
+#pragma unroll
+    for (int j = 0; j < kRdRows; ++j) {
+      if (j >= srows) break;
+      const uint32_t p = warp * R + j * 32 + lane;
+      const bool v = p < S;
+      kr[j] = v ? src[p] : 0ull;
+      const uint32_t d = v ? (uint32_t)(kr[j] >> sh) & (kRdRadix - 1) : (uint32_t)kRdRadix;
+      dg[j] = d;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t b = 0;
+      if (v) b = mywc[d];
+      __syncwarp();
+      rk[j] = 0;
+      if (v) {
+        rk[j] = b + __popc(peers & lt);
+        if ((peers & lt) == 0) mywc[d] = (uint16_t)(b + __popc(peers));
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    // thread tid owns digits 2 tid, 2 tid + 1: warp-major prefixes, then the bases
+    uint32_t run = 0;
+#pragma unroll
+    for (int dd = 0; dd < kRdRadix / kRdThreads; ++dd) {
+      const int d = tid * (kRdRadix / kRdThreads) + dd;
+#pragma unroll
+      for (int w = 0; w < kRdWarps; ++w) {
+        const uint32_t c = wcs[w * kRdRadix + d];
+        wcs[w * kRdRadix + d] = (uint16_t)run;
+        run += c;
+      }
+    }
+    uint32_t tot;
+    const uint32_t dbase = block_exclusive<kRdWarps>(run, OpSum(), 0u, rowtot, &tot);
+#pragma unroll
+    for (int dd = 0; dd < kRdRadix / kRdThreads; ++dd) {
+      const int d = tid * (kRdRadix / kRdThreads) + dd;
+#pragma unroll
+      for (int w = 0; w < kRdWarps; ++w) wcs[w * kRdRadix + d] += (uint16_t)dbase;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kRdRows; ++j) {
+      if (j >= srows) break;
+      const uint32_t p = warp * R + j * 32 + lane;
+      if (p < S) dst[mywc[dg[j]] + rk[j]] = kr[j];
+    }
+    __syncthreads();
+    uint64_t *x = src;
+    src = dst;
+    dst = x;
+  }
+
+  // ---- settle the sorted entries: subgroups of equal (group, minor)
   {
-    uint16_t *wc = wcs + warp * kRdRadix;
-    while (true) {
-      uint32_t g = 0;
-      if (lane == 0) g = atomicAdd(&s_gnext, 1u);
-      g = __shfl_sync(0xffffffffu, g, 0);
-      if (g >= G) break;
-      if (gbx[g] != kNone) continue;
-      const uint32_t q0 = gst[g], s = gst[g + 1] - q0;
-      if (s == 0 || q0 + s > gend) {  // only after an error reported above
-        if (lane == 0) atomicExch(a.err, kDevRange);
+    const int csh = kRdPosBits;
+    uint32_t stf = 0, enf = 0;
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      if (i >= srows) break;
+      const uint32_t p = i * kRdThreads + tid;
+      if (p < S) {
+        const uint64_t c = src[p] >> csh;
+        const uint32_t g = (uint32_t)(c >> mbits);
+        if (p == 0 || (src[p - 1] >> csh) != c || gfs[g] == p) stf |= 1u << i;
+        if (p + 1 == S || (src[p + 1] >> csh) != c) enf |= 1u << i;
+      }
+    }
+    // the last subgroup start at or before each entry: ballots in a row, the
+    // (row, warp) carry through warp 0
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      if (i >= srows) break;
+      const uint32_t b = __ballot_sync(0xffffffffu, (stf >> i) & 1u);
+      if (lane == 0) rowtot[i * kRdWarps + warp] = b ? i * kRdThreads + warp * 32 + (31 - __clz(b)) + 1 : 0u;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int m = srows * kRdWarps;
+      uint32_t c0 = 2 * lane < m ? rowtot[2 * lane] : 0u, c1 = 2 * lane + 1 < m ? rowtot[2 * lane + 1] : 0u;
+      const uint32_t inc = warp_inclusive(max(c0, c1), OpMax());
+      const uint32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
+      const uint32_t ex0 = lane ? before : 0u;
+      if (2 * lane < m) rowtot[2 * lane] = ex0;
+      if (2 * lane + 1 < m) rowtot[2 * lane + 1] = max(ex0, c0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      if (i >= srows) break;
+      const uint32_t p = i * kRdThreads + tid;
+      const uint32_t b = __ballot_sync(0xffffffffu, (stf >> i) & 1u) & (lt | (1u << lane));
+      if (p >= S) continue;
+      const uint32_t hp = b ? i * kRdThreads + warp * 32 + (31 - __clz(b)) : rowtot[i * kRdWarps + warp] - 1;
+      const uint64_t key = src[p];
+      const uint32_t q = (uint32_t)key & ((1u << kRdPosBits) - 1);
+      const uint32_t g = (uint32_t)(key >> (csh + mbits));
+      if (g >= G) {
+        atomicExch(a.err, kDevRange);
         continue;
       }
-      settle_group(a, base, q0, s, ghd[g], mA, pA, mB, pB, wc, sid);
+      const uint32_t id = sid[q], k = p - gfs[g], hk = hp - gfs[g];
+      const uint32_t slot = ghd[g] + k, head = ghd[g] + hk, at = base + gst[g] + k;
+      if (id >= a.n || slot >= a.n || at >= a.ub) {
+        atomicExch(a.err, kDevRange);
+        continue;
+      }
+      a.snap_cur[id] = head;
+      if (((stf >> i) & 1u) && ((enf >> i) & 1u)) {  // alone in its subgroup: final
+        a.sa[slot] = id;
+        a.rank[id] = slot;
+        a.fin[id] = (uint8_t)a.r;
+        a.hhd[at] = kHole;
+      } else {
+        a.hid[at] = id;
+        a.hhd[at] = head;
+      }
     }
   }
 
   // ---- big entries of the span: (ordinal, minor relative to the window),
   // and each big group's head, first big entry and first list entry
-  if (tid == 0) s_BC = lb_resolve(a.st_bc, t, bc, a.epoch, a.err);
-  if (tid == 32) s_BS = lb_resolve(a.st_bs, t, bs_tile, a.epoch, a.err);
-  __syncthreads();
-  const uint32_t BC = s_BC, BS = s_BS;
+  const uint32_t BC = s_BC, BS = s_BS;  // (read after the barriers since they were set)
   if (bc) {
-    uint32_t *hcnt = mB;  // free now: digit counts of the big keys
+    // kb may hold the sorted keys the settle just read: every warp is done
+    // with them before it becomes the digit counts of the big keys
+    __syncthreads();
+    uint32_t *hcnt = reinterpret_cast<uint32_t *>(kb);
     const uint32_t hmask = (1u << a.hist_bits) - 1;
     for (uint32_t d = tid; d <= hmask; d += kRdThreads) hcnt[d] = 0;
     __syncthreads();
-    for (uint32_t q = tid; q < span; q += kRdThreads) {
-      uint32_t j, o;
-      if (q < f) {
-        if (!cov_big) continue;
-        j = q;
-        o = BS - 1;
-      } else {
-        const uint32_t g = gid[q];
-        if (g >= G || gbx[g] == kNone) continue;
-        j = cov_cnt + gbp[g] + (q - gst[g]);
-        o = BS + gbx[g];
-      }
-      const uint32_t i = sid[q];
-      uint32_t m = mA[q];
-      if (m && a.woff && i < a.n) m -= a.woff[a.wid[i]];
+#pragma unroll
+    for (int i = 0; i < kRdRows; ++i) {
+      if (i >= mrows) break;
+      if (!((bgb >> i) & 1u)) continue;
+      const uint32_t q = i * kRdThreads + tid;
+      const uint32_t o = q < f ? BS - 1 : BS + gbx[gid[q]];
+      const uint32_t i2 = sid[q];
+      uint32_t m = mv[q];
+      if (m && a.woff && i2 < a.n) m -= a.woff[a.wid[i2]];
       const uint64_t key = ((uint64_t)o << a.mb) | m;
-      if (BC + j < a.ub && o < a.bg_cap) {
-        a.bkeys[BC + j] = key;
-        a.bvals[BC + j] = i;
+      const uint32_t j = BC + bx[i];
+      if (j < a.ub && o < a.bg_cap) {
+        a.bkeys[j] = key;
+        a.bvals[j] = i2;
         atomicAdd(&hcnt[(uint32_t)key & hmask], 1u);
       } else {
         atomicExch(a.err, kDevRange);
@@ -790,7 +865,7 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
       const uint32_t o = BS + gbx[g];
       if (o < a.bg_cap) {
         a.bg_head[o] = ghd[g];
-        a.bg_off[o] = BC + cov_cnt + gbp[g];
+        a.bg_off[o] = BC + gfs[g];
         a.bg_pos[o] = base + gst[g];
       } else {
         atomicExch(a.err, kDevRange);
@@ -833,10 +908,12 @@ __global__ void __launch_bounds__(kLcT) k_list_compact(const uint32_t *__restric
   }
   uint32_t tot;
   const uint32_t ex = block_exclusive<kLcT / 32>(cnt, OpSum(), 0u, scr, &tot);
-  if (tid == 0) {
-    lb_publish(status, t, tot, epoch);
-    s_pre = lb_resolve(status, t, tot, epoch, err);
-    if (base + kLcTile >= A) *count_out = s_pre + tot;
+  if (tid < 32) {
+    const uint32_t p = lb_sum_warp(status, t, tot, epoch, err);
+    if (tid == 0) {
+      s_pre = p;
+      if (base + kLcTile >= A) *count_out = p + tot;
+    }
   }
   __syncthreads();
   uint32_t rs = s_pre + ex;
@@ -890,7 +967,6 @@ __global__ void k_phi(const uint32_t *__restrict__ sa, uint32_t n, const uint32_
 // lev's snapshot at snap0 + lev * n).
 constexpr int kPChunk = 16;
 constexpr uint32_t kPDirect = 256;
-constexpr int kPBlock = 8;
 template <class T>
 __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W, const uint32_t *__restrict__ wsb,
                        const uint32_t *__restrict__ phi, const uint8_t *__restrict__ fin,
@@ -909,25 +985,8 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W, const uin
       continue;
     }
     const uint32_t we = win_end(W, i, n);  // i and j lie in the same window
-    // blocks of kPBlock tokens are loaded together (independent loads), then
-    // compared; the tail token by token
     uint32_t steps = 0;
-    bool more = true;
-    while (more && steps < kPDirect && (uint64_t)max(i, j) + l + kPBlock <= we) {
-      T x[kPBlock], y[kPBlock];
-#pragma unroll
-      for (int k = 0; k < kPBlock; ++k) {
-        x[k] = S[i + l + k];
-        y[k] = S[j + l + k];
-      }
-      int eq = 0;
-#pragma unroll
-      for (int k = kPBlock - 1; k >= 0; --k) eq = x[k] == y[k] ? eq + 1 : 0;  // leading equal tokens
-      l += eq;
-      steps += eq;
-      more = eq == kPBlock;
-    }
-    while (more && steps < kPDirect && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]) {
+    while (steps < kPDirect && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]) {
       ++l;
       ++steps;
     }
@@ -1105,13 +1164,14 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   uint32_t *bg_head = c->arena.take_n<uint32_t>(bg_cap);
   uint32_t *bg_off = c->arena.take_n<uint32_t>(bg_cap);
   uint32_t *bg_pos = c->arena.take_n<uint32_t>(bg_cap);
+  uint32_t *mkey = c->arena.take_n<uint32_t>(n);  // minor keys of a round's list
   uint32_t *hid = c->arena.take_n<uint32_t>(n);  // the holed next list of a round
   uint32_t *hhd = c->arena.take_n<uint32_t>(n);
   st.fin = c->arena.take_n<uint8_t>(n);
   const size_t wsb_words = (size_t)n / 32 + 2;
   st.wsb = st.win.count > 1 ? c->arena.take_n<uint32_t>(wsb_words) : nullptr;
   if (!b.keys[0] || !b.keys[1] || !b.vals[0] || !b.vals[1] || !lid[0] || !lid[1] || !lhd[0] || !lhd[1] ||
-      !bg_head || !bg_off || !bg_pos || !hid || !hhd || !st.fin || (st.win.count > 1 && !st.wsb)) {
+      !bg_head || !bg_off || !bg_pos || !mkey || !hid || !hhd || !st.fin || (st.win.count > 1 && !st.wsb)) {
     set_error("suffix array: workspace too small");
     return APO_ENOMEM;
   }
@@ -1223,6 +1283,9 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   bool big_possible = true;
   for (uint32_t r = 1;; ++r) {
     if (st.levels >= max_levels) {
+      // a device wait that gave up or an index out of range leaves counts
+      // that never reach 0: report that first
+      if (!capturing(c)) APO_TRY(check_device_error(c, s));
       set_error("suffix array: too many doubling rounds");
       return APO_EDEVICE;
     }
@@ -1244,7 +1307,13 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     APO_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(uint32_t), s));
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRoundTiles, 0, sizeof(uint32_t), s));
     {
+      Launch lp_(c, kKMinor, ub, s);
+      k_minor<<<std::max(1, std::min(ceil_div(ub, 256 * 4), c->num_sms * 8)), 256, 0, s>>>(
+          lid[cur], ub, in, r, h, n, st.wsb, st.fin, st.rank, st.snaps[r - 1], mkey);
+    }
+    {
       RoundArgs a;
+      a.mkey = mkey;
       a.lid = lid[cur];
       a.lhd = lhd[cur];
       a.ub = ub;
