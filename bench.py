@@ -48,19 +48,21 @@ WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/30
 
 # Algorithmic bytes moved per unit of work, per kernel (unit = the element
 # count the library records for each launch).  rs_pass: read and write one
-# (u64 key, u32 value) pair; refresh: read key, suffix, position, write SA,
-# rank, next active suffix and position; pack: read suffix and two ranks,
-# write a pair; hash: descriptor bytes in, 8 out (per task, at the
-# workload's mean of 4.5 arguments).  The greedy loop and the automaton
+# (u64 key, u32 value) pair; round (a doubling round over its list entries):
+# the survey's 36 bytes per active suffix and round (read the entry, gather
+# the rank h ahead, write the new rank, the key traffic of a sort); split
+# (settling sorted pairs): read a pair, write a rank and a list entry; hash:
+# descriptor bytes in, 8 out (per task, at the workload's mean of 4.5
+# arguments).  The greedy loop and the automaton
 # passes are chains of dependent accesses (latency-bound) and have no entry.
-BYTES_PER_UNIT = {"rs_pass": 24, "refresh": 32, "pack": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
+BYTES_PER_UNIT = {"rs_pass": 24, "round": 36, "split": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
                   "plcp": 24, "rep.cand_gen": 36, "rep.compact": 16}
 
 
 # The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
 # with their radix sorts and rank refreshes) and the Phi/PLCP LCP.
-SA_LCP_KERNELS = ("init_keys", "key_or", "sa_dict", "rs_hist", "rs_offsets", "rs_pass", "refresh", "pack",
-                  "phi", "plcp", "lcp_perm")
+SA_LCP_KERNELS = ("init_keys", "key_or", "sa_dict", "wsb", "rs_hist", "rs_offsets", "rs_pass", "round", "split",
+                  "list_compact", "minor", "phi", "plcp", "lcp_perm")
 
 
 def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:
@@ -167,7 +169,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n-tasks", type=int, default=N_TASKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder", "replay", "quality"],
+    ap.add_argument("--workload", default="window", choices=["window", "batched", "served", "match", "finder", "replay", "quality",
+                                                     "config4"],
                     help="window: the full path on one 2^20-task window (default); batched: "
                          "SA+LCP+repeats over 512 uneven windows in one call vs one call per window")
     ap.add_argument("--windows", type=int, default=512)
@@ -238,26 +241,29 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n_tasks: int) -> dict:
-    """The oracle, as it stands, on a bounded sample of the workload (one
-    full step on a smaller window of the same structure), single-threaded."""
-    import numpy as np
-
+def oracle_window_step(ts):
+    """The oracle, as it stands, on one window: hash the descriptors, then
+    SA, LCP and Alg. 2's repeats (the metric's stages).  Returns the seconds
+    taken and the number of traces."""
     import oracle
-    import workloads as W
-    ts = W.config2_tasks(n_tasks, seed=2)
     t0 = time.perf_counter()
     tok = oracle.hash_tasks(ts)
     r = oracle.find_repeats(tok, MIN_LEN)
-    st, tl = r.trace_start.astype(np.int64), r.trace_len.astype(np.int64)
-    off = np.zeros(len(tl) + 1, dtype=np.uint64)
-    off[1:] = np.cumsum(tl)
-    pt = np.concatenate([tok[s:s + l] for s, l in zip(st, tl)]) if len(tl) else np.zeros(1, np.uint64)
-    e, _ = oracle.match(pt, off, tok) if len(tl) else (np.zeros(0), None)
-    dt = time.perf_counter() - t0
-    return {"value": n_tasks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full step (hash, SA, LCP, repeats, match) on a {n_tasks}-task window of "
-                      f"the same structure; {len(e)} matches; {dt:.2f} s single-threaded"}
+    return time.perf_counter() - t0, int(r.trace_len.shape[0])
+
+
+def cpu_baseline(n_tasks: int) -> dict:
+    """The oracle, as it stands, single-threaded, on the bench's own window
+    (same seed and size): one step of hashing, SA, LCP and repeats.  The
+    GPU step also matches the traces against the window; the oracle's naive
+    matching of the same traces takes over a minute per window, so it is
+    left out of the sample (the GPU side does more work than this sample)."""
+    import workloads as W
+    ts = W.config2_tasks(n_tasks, seed=2)
+    dt, nt = oracle_window_step(ts)
+    return {"value": n_tasks / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "same_config": True,
+            "sample": f"one step (hash, SA, LCP, Alg. 2 repeats: {nt} traces) on the bench's own {n_tasks}-task "
+                      f"window, {dt:.2f} s single-threaded; the GPU step's matching stage is not in the sample"}
 
 
 def batched_cpu_baseline(toks, off) -> dict:
@@ -291,35 +297,32 @@ def batched_cpu_baseline(toks, off) -> dict:
 
 
 def run_reference(args, rank, world):
+    """The oracle on the bench's own window (2^20 tasks, same seed), one
+    window per step: hashing, SA, LCP and Alg. 2's repeats, single-threaded
+    (about 4-5 s per step).  The GPU step also matches the traces it found
+    against the window; the oracle's naive matching of those traces alone
+    takes over a minute, so the reference step leaves it out."""
     if rank != 0:
         return
-    import oracle
     import workloads as W
-    n = 1 << 16  # bounded sample per step so that warmup + steps end within minutes
+    n = args.n_tasks
+    ts = W.config2_tasks(n, seed=2)
     times = []
     for k in range(args.warmup + args.steps):
-        ts = W.config2_tasks(n, seed=2)
-        t0 = time.perf_counter()
-        tok = oracle.hash_tasks(ts)
-        r = oracle.find_repeats(tok, MIN_LEN)
-        import numpy as np
-        st, tl = r.trace_start.astype(np.int64), r.trace_len.astype(np.int64)
-        off = np.zeros(len(tl) + 1, dtype=np.uint64)
-        off[1:] = np.cumsum(tl)
-        if len(tl):
-            pt = np.concatenate([tok[s:s + l] for s, l in zip(st, tl)])
-            oracle.match(pt, off, tok)
+        dt, _ = oracle_window_step(ts)
         if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(dt)
     tot = sum(times)
     value = n * len(times) / tot
-    sample = (f"each step: one full step (hash, SA, LCP, repeats, match) on a {n}-task window of "
-              f"the workload's structure, single-threaded oracle")
+    sample = (f"each step: hash, SA, LCP and Alg. 2 repeats of the bench's own {n}-task window "
+              "(the GPU step also matches the traces; not in the oracle step), single-threaded oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tokens": n, "min_len": MIN_LEN},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tokens": n, "min_len": MIN_LEN,
+                                        "same_config": True,
+                                        "stages": "hash, SA, LCP, repeats (the GPU step adds matching)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -423,7 +426,7 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
             "batched_over_plain": ms_plain / ms, "graph": graph,
             "gpu_launches": n_launch, "roofline": roof, "sa_lcp_roofline": sa_lcp, "clocks": clk,
             "kernels": kernels, "sort_tuning": tuning_summary(apo)})
-    if emit and rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = batched_cpu_baseline(toks, off)
     if emit and rank == 0:
         print(json.dumps(out))
@@ -752,6 +755,63 @@ def run_quality(args, rank, world, local, emit=True):
     return out
 
 
+def run_config4(args, rank, world, local, emit=True):
+    """The adversarial pair at 2^24 tokens each: window A (a constant run, a
+    period-2 run and a period-3 run in equal thirds: 23 doubling rounds) and
+    window B (uniform random u32): SA, LCP and Alg. 2 repeats per window,
+    device-resident tokens, L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2406_18111_gb300 import Apo
+    dev = torch.device("cuda", local)
+    apo = Apo(local)
+    apo.sort_tuning(args.sort_tuning)
+    a_np, b_np = W.config4_windows(1 << 24, seed=4 + rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = peaks()
+    out = {"config": {"workload": "config 4: two windows of 2^24 u32 tokens: A = constant / period-2 / "
+                                  "period-3 thirds, B = uniform random; SA+LCP+repeats (min_len 5)",
+                      "l2": "flushed between steps"}}
+    steps = max(1, min(args.steps, 3))
+    for name, S in (("A", a_np), ("B", b_np)):
+        t = torch.from_numpy(S.view(np.int32)).to(dev)
+        for _ in range(max(1, min(args.warmup, 2))):
+            r = apo.find_repeats(t, MIN_LEN, stages=False)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = apo.find_repeats(t, MIN_LEN, stages=False)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / steps
+        apo.profile_reset()
+        apo.profile(True)
+        for _ in range(steps):
+            flush.zero_()
+            apo.find_repeats(t, MIN_LEN, stages=False)
+        torch.cuda.synchronize()
+        prof = apo.profile_read()
+        apo.profile(False)
+        full = apo.find_repeats(t, MIN_LEN, stages=True)
+        b_alg, a_r = sa_lcp_bytes(full.lcp, None, 4)
+        rounds = full.rounds
+        del full
+        out[name] = {"value": S.shape[0] * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "rounds": rounds, "selected": int(r.sel_start.shape[0]),
+                     "sa_lcp_roofline": sa_lcp_roofline(prof, steps, b_alg, a_r, peak, peak_kind)}
+        del t
+    if emit and rank == 0:
+        print(json.dumps(out))
+    return out
+
+
 def run_match(args, rank, world, local, emit=True):
     """Aho-Corasick matching (Sec. 4.3) of 10,000 candidate traces (lengths
     log-uniform 5..2000; half copied from the stream, half random) against a
@@ -820,7 +880,7 @@ def main():
     rank, world, local = env_ranks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload in ("batched", "served", "match", "finder", "replay", "quality"):
+    if args.workload in ("batched", "served", "match", "finder", "replay", "quality", "config4"):
         import torch
         torch.cuda.set_device(local)
         if world > 1:
@@ -841,6 +901,8 @@ def main():
             return run_replay(args, rank, world, local)
         if args.workload == "quality":
             return run_quality(args, rank, world, local)
+        if args.workload == "config4":
+            return run_config4(args, rank, world, local)
         return run_batched(args, rank, world, local)
     import numpy as np
     import torch
@@ -1028,7 +1090,7 @@ def main():
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(1 << 18)
+        cpu = cpu_baseline(n)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -1068,6 +1130,11 @@ def main():
                                               "mean_batch_windows")}
         fd = run_finder(args, rank, world, local, emit=False)
         line["finder"] = {k: fd[k] for k in ("metric", "value", "unit", "p50_ms", "p99_ms", "config")}
+        line["batched"]["cpu_baseline"] = bt.get("cpu_baseline")
+        c4 = run_config4(a2, rank, world, local, emit=False)
+        line["config4"] = c4
+        mt = run_match(a2, rank, world, local, emit=False)
+        line["match"] = {k: mt[k] for k in ("metric", "value", "unit", "ms_per_step", "config")}
         rp = run_replay(a2, rank, world, local, emit=False, cpu_leg=False)
         line["replay"] = {k: rp[k] for k in ("metric", "value", "unit", "ms_per_step", "e2e", "replays",
                                               "traced_fraction", "top_kernel", "config")}
