@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kHistThreads) k_rs_hist(const uint64_t *__rest
   for (uint64_t b0 = (uint64_t)blockIdx.x * kHistThreads + (threadIdx.x & ~31u); b0 < n; b0 += stride) {
     const uint64_t i = b0 + lane;
     const bool valid = i < n;
-    const uint32_t d = valid ? digit_of<BITS>(keys[i], vals[i], place) : (uint32_t)R;
+    const uint32_t d = valid ? digit_of<BITS>(keys[i], vals ? vals[i] : 0u, place) : (uint32_t)R;
     const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
     if (__all_sync(0xffffffffu, d == d0 && d0 < (uint32_t)R)) {
       if (lane == 0) atomicAdd(&sh[d0], 32u);
@@ -90,7 +90,10 @@ struct PassShape {
 // One digit place.  `gcnt` is this place's global digit histogram (the
 // tile turns it into digit offsets itself); when next_place >= 0 the tile
 // also counts the next place's digits of its keys into next_cnt, so no
-// separate histogram read is needed for any place but the first.
+// separate histogram read is needed for any place but the first.  A full
+// tile arrives in shared memory by two bulk copies (keys, values) that one
+// thread issues while the others clear the counters; the ragged last tile
+// is loaded by the threads.  vin == nullptr: keys only (no value digits).
 template <int TPB, int ITEMS, int BITS>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
@@ -109,31 +112,54 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
   __shared__ uint32_t s_tile;
   __shared__ uint32_t scratch[NW];
   __shared__ uint32_t s_next[R];
+  __shared__ __align__(8) uint64_t s_bar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < NW * R; i += TPB) wc[i] = 0;
-  if (tid < R) s_next[tid] = 0;
-  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  const bool hv = vin != nullptr;
+  if (tid == 0) {
+    s_tile = atomicAdd(tile_ctr, 1u);
+    mbar_init(&s_bar, 1);
+  }
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * TILE;
   if (base >= n) return;  // a tile past the device-side count (no later tile looks at it)
+  const bool bulk = n - base >= (uint64_t)TILE &&
+                    ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(vin)) & 15) == 0;
+  if (bulk && tid == 0) {
+    mbar_arrive_expect(&s_bar, TILE * (hv ? 12u : 8u));
+    bulk_load(sk, kin + base, TILE * 8u, &s_bar);
+    if (hv) bulk_load(sv, vin + base, TILE * 4u, &s_bar);
+  }
+  for (int i = tid; i < NW * R; i += TPB) wc[i] = 0;
+  if (tid < R) s_next[tid] = 0;
   const uint64_t seg = base + (uint64_t)warp * (ITEMS * 32);
+  const uint32_t wseg = (uint32_t)warp * (ITEMS * 32);
 
   uint64_t k[ITEMS];
   uint32_t v[ITEMS];
   uint32_t rk[ITEMS];
+  if (bulk) {
+    mbar_wait(&s_bar, 0, err);
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) {
-    const uint64_t idx = seg + j * 32 + lane;
-    if (idx < n) {
-      k[j] = kin[idx];
-      v[j] = vin[idx];
-    } else {
-      k[j] = 0;
-      v[j] = 0;
+    for (int j = 0; j < ITEMS; ++j) {
+      k[j] = sk[wseg + j * 32 + lane];
+      v[j] = hv ? sv[wseg + j * 32 + lane] : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint64_t idx = seg + j * 32 + lane;
+      if (idx < n) {
+        k[j] = kin[idx];
+        v[j] = hv ? vin[idx] : 0u;
+      } else {
+        k[j] = 0;
+        v[j] = 0;
+      }
     }
   }
+  __syncthreads();  // the counters are clear
   uint32_t *mywc = wc + warp * R;
   const uint32_t lt = lanemask_lt();
   if (next_place >= 0) {
@@ -202,18 +228,18 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
       const uint32_t dd = digit_of<BITS>(k[j], v[j], place);
       const uint32_t lp = tex[dd] + wc[warp * R + dd] + rk[j];
       sk[lp] = k[j];
-      sv[lp] = v[j];
+      if (hv) sv[lp] = v[j];
     }
   }
   __syncthreads();
   const uint32_t cnt = (n - base) < (uint64_t)TILE ? (uint32_t)(n - base) : (uint32_t)TILE;
   for (uint32_t q = tid; q < cnt; q += TPB) {
     const uint64_t kk = sk[q];
-    const uint32_t vv = sv[q];
+    const uint32_t vv = hv ? sv[q] : 0u;
     const uint32_t pos = gof[digit_of<BITS>(kk, vv, place)] + q;
     if (pos < n) {
       kout[pos] = kk;
-      vout[pos] = vv;
+      if (hv) vout[pos] = vv;
     } else {
       atomicExch(err, kDevRange);  // only after a failed look-back
     }

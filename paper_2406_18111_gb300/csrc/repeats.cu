@@ -50,6 +50,25 @@ namespace {
 // with the start in the low ks bits when everything fits one 64-bit key
 // (ks = 0 otherwise: the start is sorted as the value).  Pairs that straddle
 // two windows have LCP 0 and are dropped with the other short candidates.
+// Alg. 2's candidates of the SA pair (s1, s2) with common prefix p: length
+// l and the two starts a, b.
+__device__ __forceinline__ void pair_cand(uint32_t s1, uint32_t s2, uint32_t p, uint32_t *l, uint32_t *a,
+                                          uint32_t *b) {
+  const uint32_t lo = min(s1, s2), hi = max(s1, s2);
+  if (hi - lo >= p) {  // [s1, s1+p) and [s2, s2+p) are disjoint
+    *l = p;
+    *a = s1;
+    *b = s2;
+  } else {             // the common prefix is a run of S[lo, lo + d)
+    const uint32_t d = hi - lo;
+    uint64_t h = ((uint64_t)p + d) / 2;
+    h -= h % d;
+    *l = (uint32_t)h;
+    *a = lo;
+    *b = lo + *l;
+  }
+}
+
 __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ lcp,
                            uint32_t n, uint32_t min_len, MinTree T, int bi, int bl, uint32_t lmax, int ks,
                            Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
@@ -58,24 +77,19 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n - 1; base += stride) {
     const uint32_t k = base + threadIdx.x;
-    bool ok = false;
+    bool ok = false, ok_b = false;
     uint32_t l = 0, a = 0, b = 0;
     if (k < n - 1) {
-      const uint32_t s1 = sa[k], s2 = sa[k + 1], p = lcp[k];
-      const uint32_t lo = min(s1, s2), hi = max(s1, s2);
-      if (hi - lo >= p) {  // [s1, s1+p) and [s2, s2+p) are disjoint
-        l = p;
-        a = s1;
-        b = s2;
-      } else {             // the common prefix is a run of S[lo, lo + d)
-        const uint32_t d = hi - lo;
-        uint64_t h = ((uint64_t)p + d) / 2;
-        h -= h % d;
-        l = (uint32_t)h;
-        a = lo;
-        b = lo + l;
-      }
+      pair_cand(sa[k], sa[k + 1], lcp[k], &l, &a, &b);
       ok = l >= min_len && l > 0;
+      // pair k + 1's first candidate is often this pair's second one (equal
+      // LCPs along a run of the SA): leave it to pair k + 1
+      ok_b = ok;
+      if (ok && k + 1 < n - 1) {
+        uint32_t l2, a2, b2;
+        pair_cand(sa[k + 1], sa[k + 2], lcp[k + 1], &l2, &a2, &b2);
+        if (l2 == l && a2 == b) ok_b = false;
+      }
     }
     uint64_t key = 0;
     if (ok) {
@@ -88,22 +102,25 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
       a -= wbase;
       b -= wbase;
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+    const uint32_t bal = __ballot_sync(0xffffffffu, ok), bal_b = __ballot_sync(0xffffffffu, ok_b);
     if (bal == 0) continue;
     const int leader = __ffs(bal) - 1;
     uint32_t slot0 = 0;
-    if ((int)lane == leader) slot0 = atomicAdd(count, 2u * __popc(bal));
+    if ((int)lane == leader) slot0 = atomicAdd(count, __popc(bal) + __popc(bal_b));
     slot0 = __shfl_sync(0xffffffffu, slot0, leader);
     if (ok) {
-      const uint32_t slot = slot0 + 2u * __popc(bal & lanemask_lt());
-      if (slot + 1 >= 2 * (n - 1)) {
+      const uint32_t lt = lanemask_lt();
+      const uint32_t slot = slot0 + __popc(bal & lt) + __popc(bal_b & lt);
+      if (slot + (ok_b ? 1u : 0u) >= 2 * (n - 1)) {
         atomicExch(err, kDevRange);
         continue;
       }
       keys[slot] = ks ? (key << ks) | a : key;
-      vals[slot] = a;
-      keys[slot + 1] = ks ? (key << ks) | b : key;
-      vals[slot + 1] = b;
+      if (ok_b) keys[slot + 1] = ks ? (key << ks) | b : key;
+      if (!ks) {  // the start is the value (otherwise it is the key's low digits)
+        vals[slot] = a;
+        if (ok_b) vals[slot + 1] = b;
+      }
     }
   }
 }
@@ -112,11 +129,11 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
 // decoupled look-back sum-scan).
 constexpr int kCT = 256, kCI = 8, kCTile = kCT * kCI;
 
-struct PredFirstOfRun {  // k starts a run of identical (key, value) pairs
+struct PredFirstOfRun {  // k starts a run of identical (key, value) pairs (vals == nullptr: keys)
   const uint64_t *keys;
   const uint32_t *vals;
   __device__ bool operator()(uint32_t k) const {
-    return k == 0 || keys[k] != keys[k - 1] || vals[k] != vals[k - 1];
+    return k == 0 || keys[k] != keys[k - 1] || (vals && vals[k] != vals[k - 1]);
   }
 };
 struct PredFlag {
@@ -182,11 +199,11 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m, cons
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
-    const uint64_t key = keys[k] >> ks;
+    const uint64_t full = keys[k], key = full >> ks;
     const uint32_t base = woff ? woff[(uint32_t)(key >> (bl + bi))] : 0u;  // back to global positions
     cl[q] = lmax - (uint32_t)((key >> bi) & lmax);
     cid[q] = (uint32_t)(key & idmask) + base;
-    cs[q] = vals[k] + base;
+    cs[q] = (ks ? (uint32_t)(full & ((1ull << ks) - 1)) : vals[k]) + base;
   }
 }
 
@@ -761,11 +778,15 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     const DigitRange r[2] = {{0, bs, true}, {0, bw + bl + bi, false}};
     const DigitRange rk{0, bw + bl + bi + bs, false};
     b.cur = 0;
-    if (ks)
-      APO_TRY(radix_sort_pairs(c, b, mraw, &rk, 1, s));
-    else
+    if (ks) {  // the key holds every field: a keys-only sort (two thirds of the bytes per pass)
+      SortBuffers kb = b;
+      kb.vals[0] = kb.vals[1] = nullptr;
+      APO_TRY(radix_sort_pairs(c, kb, mraw, &rk, 1, s));
+      b.cur = kb.cur;
+    } else {
       APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
-    PredFirstOfRun pr{b.keys[b.cur], b.vals[b.cur]};
+    }
+    PredFirstOfRun pr{b.keys[b.cur], ks ? nullptr : b.vals[b.cur]};
     APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCandUnique, s));
     mu = mraw;
     {

@@ -15,13 +15,19 @@
 //
 //   * The active suffixes form a list of (suffix, group head slot) entries,
 //     each group contiguous.  k_round cuts the list into tiles of kRdT
-//     entries; a tile owns the groups that start in it.  A group of at most
-//     kRdT entries is gathered, sorted by (group, minor) in shared memory and
-//     settled by its owner in one pass over its entries: no key leaves the
-//     chip.  Whether a group is larger than kRdT is read off one entry kRdT
-//     places after its start, so no scan over group sizes is needed.
+//     entries; a tile owns the groups that start in it.  The groups of at
+//     most kRdBig entries ("small") are sorted together by (group, minor) in
+//     shared memory with a block-wide LSD radix sort and settled by the
+//     owner in one pass: no key leaves the chip.  Whether a group is small is
+//     read off the entry kRdBig places after its start, so no scan over
+//     group sizes is needed.  The minor keys come from k_minor, a streaming
+//     pass that keeps many of its dependent gathers in flight.
 //   * Larger groups ("big") are written as (big-group ordinal, minor) keys
 //     and sorted by the onesweep radix sort; k_split then settles them.
+//   * Settled entries go to a holed copy of the list (a suffix that became
+//     final leaves a hole), which k_list_compact squeezes into the next
+//     round's list.  Every prefix a tile needs from the tiles before it (big
+//     entries, big groups, list positions) is a decoupled look-back.
 //
 // Settling a sorted group: its subgroups of equal minor keys start at the
 // slots head + (position in the group); a subgroup of one suffix is final
