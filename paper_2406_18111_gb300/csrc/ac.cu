@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(kST) k_match_offsets(const uint32_t *__restric
     lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
     uint32_t pre = 0;
     if (t > 0) {
-      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      pre = lb_exclusive_k<8>(status, 1, t, epoch, OpSum(), 0u, err);
       lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
     }
     s_pre = pre;

@@ -70,6 +70,50 @@ __device__ uint32_t lb_exclusive(const uint64_t *status, int stride, uint32_t t,
   return acc;
 }
 
+// The same walk with K predecessor words loaded at once (K loads in flight
+// instead of one dependent load per step).  The words nearer than the first
+// one that is not ready are combined and the walk moves past them; it ends at
+// the first inclusive word.
+template <int K, class Op>
+__device__ uint32_t lb_exclusive_k(const uint64_t *status, int stride, uint32_t t, uint32_t epoch, Op op,
+                                   uint32_t identity, uint32_t *err) {
+  uint32_t acc = identity;
+  long long hi = (long long)t - 1;
+  uint32_t spins = 0;
+  while (hi >= 0) {
+    uint64_t w[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = hi - i >= 0 ? lb_load(status + (size_t)(hi - i) * stride) : 0ull;
+    uint32_t part = identity;
+    int used = 0;
+    bool done = false;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if (done || used < i) continue;  // stop at the first word not ready
+      if (hi - i < 0) {
+        done = true;
+        continue;
+      }
+      const uint32_t st = (uint32_t)(w[i] >> 62), ep = (uint32_t)(w[i] >> 32) & 0x3fffffffu;
+      if (ep != epoch || st == kLbNone) continue;
+      part = op((uint32_t)w[i], part);  // tile hi - i precedes the tiles in part
+      used = i + 1;
+      if (st == kLbInclusive) done = true;
+    }
+    acc = op(part, acc);
+    if (done) break;
+    hi -= used;
+    if (used == 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(err, kDevTimeout);
+        break;
+      }
+      if (spins > 32) __nanosleep(128);
+    }
+  }
+  return acc;
+}
+
 // The same walk by a whole warp, for a commutative operator: lane l reads
 // the word of tile hi - l, so 32 predecessors are combined per step instead
 // of one.  Every lane of the warp must call it; all receive the result.

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const ui
     lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
     uint32_t pre = 0;
     if (t > 0) {
-      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      pre = lb_exclusive_k<8>(status, 1, t, epoch, OpSum(), 0u, err);
       lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
     }
     s_pre = pre;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kCT) k_traces(const uint32_t *__restrict__ acc
     lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
     uint32_t pre = 0;
     if (t > 0) {
-      pre = lb_exclusive(status, 1, t, epoch, OpSum(), 0u, err);
+      pre = lb_exclusive_k<8>(status, 1, t, epoch, OpSum(), 0u, err);
       lb_store(&status[t], lb_pack(kLbInclusive, epoch, pre + tot));
     }
     s_pre = pre;

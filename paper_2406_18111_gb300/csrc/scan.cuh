@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kGT) k_seg_scan(Src src, Dst dst, uint32_t n, 
     lb_store(&status[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, tot));
     uint32_t pre = ident;
     if (t > 0) {
-      pre = lb_exclusive(status, 1, t, epoch, op, ident, err);
+      pre = lb_exclusive_k<8>(status, 1, t, epoch, op, ident, err);
       lb_store(&status[t], lb_pack(kLbInclusive, epoch, op(pre, tot)));
     }
     s_pre = pre;

@@ -101,26 +101,15 @@ __device__ __forceinline__ uint32_t level_rank(const uint8_t *__restrict__ fin, 
   return f < L ? rank[j] : snap[j];
 }
 
-// Decoupled look-back: lb_publish stores the tile's aggregate, lb_resolve
-// walks back to the sum over tiles < t and stores the tile's inclusive
-// prefix; lb_sum does both.  A tile should resolve right after it publishes:
-// a walk back only ends at an inclusive prefix, so tiles that resolve late
-// make their successors' walks long.
+// Decoupled look-back: lb_publish stores the tile's aggregate, lb_sum_warp
+// publishes it and resolves the sum over tiles < t with one warp, then stores
+// the tile's inclusive prefix.  A tile should resolve right after it
+// publishes: a walk back only ends at an inclusive prefix, so tiles that
+// resolve late make their successors' walks long.
 __device__ __forceinline__ void lb_publish(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch) {
   lb_store(&st[t], lb_pack(t == 0 ? kLbInclusive : kLbAggregate, epoch, v));
 }
-__device__ __forceinline__ uint32_t lb_resolve(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
-                                               uint32_t *err) {
-  if (t == 0) return 0;
-  const uint32_t p = lb_exclusive(st, 1, t, epoch, OpSum(), 0u, err);
-  lb_store(&st[t], lb_pack(kLbInclusive, epoch, p + v));
-  return p;
-}
-__device__ __forceinline__ uint32_t lb_sum(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch, uint32_t *err) {
-  lb_publish(st, t, v, epoch);
-  return lb_resolve(st, t, v, epoch, err);
-}
-// The same by a whole warp (every lane calls it; all get the prefix).
+// Every lane of the warp calls it; all get the prefix.
 __device__ __forceinline__ uint32_t lb_sum_warp(uint64_t *st, uint32_t t, uint32_t v, uint32_t epoch,
                                                 uint32_t *err) {
   if ((threadIdx.x & 31) == 0) lb_publish(st, t, v, epoch);
