@@ -78,13 +78,14 @@ __global__ void __launch_bounds__(kHistThreads) k_rs_hist(const uint64_t *__rest
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-template <int TPB, int ITEMS, int BITS>
+template <int TPB, int ITEMS, int BITS, bool KO>
 struct PassShape {
   static constexpr int kRadix = 1 << BITS;
   static constexpr int kWarps = TPB / 32;
   static constexpr int kTile = TPB * ITEMS;
-  static constexpr size_t kSmem = (size_t)kTile * 12 + (size_t)kWarps * kRadix * 4 + 2 * kRadix * 4;
+  static constexpr size_t kSmem = (size_t)kTile * (KO ? 8 : 12) + (size_t)kWarps * kRadix * 2 + 2 * kRadix * 4;
   static_assert(kRadix <= TPB, "each digit needs an owner thread");
+  static_assert(kTile <= 65535, "per-warp digit prefixes are 16-bit");
 };
 
 // One digit place.  `gcnt` is this place's global digit histogram (the
@@ -93,21 +94,24 @@ struct PassShape {
 // separate histogram read is needed for any place but the first.  A full
 // tile arrives in shared memory by two bulk copies (keys, values) that one
 // thread issues while the others clear the counters; the ragged last tile
-// is loaded by the threads.  vin == nullptr: keys only (no value digits).
-template <int TPB, int ITEMS, int BITS>
-__global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
+// is loaded by the threads.  KO: keys only (vin, vout unused; no value
+// digits).  Without values a thread needs fewer registers and a tile less
+// shared memory, so three blocks of 512 threads fit an SM instead of two.
+template <int TPB, int ITEMS, int BITS, bool KO>
+__global__ void __launch_bounds__(TPB, (KO ? 1536 : 1024) / TPB) k_rs_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, const uint32_t *__restrict__ n_dev, int place,
     const uint32_t *__restrict__ gcnt, int next_place, uint32_t *__restrict__ next_cnt, uint64_t *status,
     uint32_t *tile_ctr, uint32_t epoch, uint32_t *err) {
-  using S = PassShape<TPB, ITEMS, BITS>;
+  using S = PassShape<TPB, ITEMS, BITS, KO>;
   if (n_dev) n = min(n, *n_dev);  // the launch is sized for an upper bound
   constexpr int R = S::kRadix, NW = S::kWarps, TILE = S::kTile;
   extern __shared__ __align__(16) uint8_t smem[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
-  uint32_t *sv = reinterpret_cast<uint32_t *>(sk + TILE);
-  uint32_t *wc = sv + TILE;            // [NW][R] per-warp digit counts, then prefixes
-  uint32_t *tex = wc + NW * R;         // [R] exclusive digit prefix within the tile
+  uint32_t *sv = reinterpret_cast<uint32_t *>(sk + TILE);  // (pairs only)
+  uint16_t *wc = reinterpret_cast<uint16_t *>(KO ? reinterpret_cast<uint8_t *>(sk + TILE)
+                                                 : reinterpret_cast<uint8_t *>(sv + TILE));  // [NW][R] per-warp digit counts, then prefixes
+  uint32_t *tex = reinterpret_cast<uint32_t *>(wc + NW * R);  // [R] exclusive digit prefix within the tile
   uint32_t *gof = tex + R;             // [R] global offset of the tile's digit run, minus tex
   __shared__ uint32_t s_tile;
   __shared__ uint32_t scratch[NW];
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
   __shared__ __align__(8) uint64_t s_bar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool hv = vin != nullptr;
+  constexpr bool hv = !KO;
   if (tid == 0) {
     s_tile = atomicAdd(tile_ctr, 1u);
     mbar_init(&s_bar, 1);
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
     }
   }
   __syncthreads();  // the counters are clear
-  uint32_t *mywc = wc + warp * R;
+  uint16_t *mywc = wc + warp * R;
   const uint32_t lt = lanemask_lt();
   if (next_place >= 0) {
 #pragma unroll
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
     __syncwarp();
     if (valid) {
       rk[j] = b + __popc(peers & lt);
-      if ((peers & lt) == 0) mywc[d] = b + __popc(peers);
+      if ((peers & lt) == 0) mywc[d] = (uint16_t)(b + __popc(peers));
     }
     __syncwarp();
   }
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) k_rs_pass(
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
       const uint32_t c = wc[w * R + d];
-      wc[w * R + d] = tcnt;
+      wc[w * R + d] = (uint16_t)tcnt;
       tcnt += c;
     }
   }
@@ -287,15 +291,15 @@ using HistFn = void (*)(const uint64_t *, const uint32_t *, uint32_t, const uint
 
 struct Shape {
   int threads, items, bits;
-  PassFn pass;
+  PassFn pass, pass_keys;  // (key, value) pairs; keys only
   HistFn hist;
-  size_t smem;
+  size_t smem, smem_keys;
 };
 
 template <int TPB, int ITEMS, int BITS>
 constexpr Shape shape() {
-  return Shape{TPB, ITEMS, BITS, k_rs_pass<TPB, ITEMS, BITS>, k_rs_hist<BITS>,
-               PassShape<TPB, ITEMS, BITS>::kSmem};
+  return Shape{TPB, ITEMS, BITS, k_rs_pass<TPB, ITEMS, BITS, false>, k_rs_pass<TPB, ITEMS, BITS, true>,
+               k_rs_hist<BITS>, PassShape<TPB, ITEMS, BITS, false>::kSmem, PassShape<TPB, ITEMS, BITS, true>::kSmem};
 }
 
 // Shape 0 is the default (and the only one used with tuning off).
@@ -337,7 +341,9 @@ int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const uin
     const int nxt = p + 1 < pl.n ? pl.p[p + 1] : -1;
     {
       Launch lp_(c, count ? kKRsPass : kKRsTune, n, s);
-      sh.pass<<<tiles, sh.threads, sh.smem, s>>>(b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
+      const bool ko = b.vals[b.cur] == nullptr;
+      (ko ? sh.pass_keys : sh.pass)<<<tiles, sh.threads, ko ? sh.smem_keys : sh.smem, s>>>(
+          b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
                                                  b.vals[b.cur ^ 1], n, n_dev, pl.p[p], hist + p * kMaxRadix, nxt,
                                                  hist + (p + 1) * kMaxRadix, c->ps.lookback, tctr + p, ep,
                                                  c->ps.err);
@@ -351,9 +357,12 @@ int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const uin
 }  // namespace
 
 int radix_sort_init() {
-  for (int i = 0; i < kNumShapes; ++i)
+  for (int i = 0; i < kNumShapes; ++i) {
     APO_CUDA_TRY(cudaFuncSetAttribute((const void *)kShapes[i].pass,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kShapes[i].smem));
+    APO_CUDA_TRY(cudaFuncSetAttribute((const void *)kShapes[i].pass_keys,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kShapes[i].smem_keys));
+  }
   return APO_OK;
 }
 
