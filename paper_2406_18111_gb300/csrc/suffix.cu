@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(kST) k_split(
     int finals, uint32_t *__restrict__ snap, uint32_t *__restrict__ sa, uint32_t *__restrict__ rank,
     uint8_t *__restrict__ fin, uint32_t *__restrict__ nid, uint32_t *__restrict__ nhd, uint32_t list_cap,
     uint32_t *count_out, uint32_t n, uint64_t *st_max, uint64_t *st_sum, uint32_t *tile_ctr, uint32_t epoch,
-    uint32_t *err) {
-  __shared__ uint64_t sk[kSTile + 2];  // key of element base - 1 + q
+    uint32_t *err, int id_bits) {
+  __shared__ uint64_t sk[kSTile + 2];  // key of element base - 1 + q (without the suffix bits)
   __shared__ uint32_t sv[kSTile];
   __shared__ uint32_t s_tile, s_pmax, s_psum;
   __shared__ uint32_t scr[kST / 32];
@@ -156,11 +156,16 @@ __global__ void __launch_bounds__(kST) k_split(
   const uint64_t base = (uint64_t)t * kSTile;
   if (base >= N) return;  // past the device-side count: no later tile looks at it
   const uint32_t cnt = (N - base) < (uint64_t)kSTile ? (uint32_t)(N - base) : (uint32_t)kSTile;
+  // id_bits > 0: the suffix is the key's low id_bits bits (keys-only sort)
+  const uint64_t idmask = id_bits ? (1ull << id_bits) - 1 : 0ull;
   for (uint32_t q = tid; q < cnt + 2; q += kST) {
     const long long g = (long long)base - 1 + q;
-    sk[q] = (g >= 0 && g < (long long)N) ? keys[g] : 0;
+    const uint64_t kv = (g >= 0 && g < (long long)N) ? keys[g] : 0;
+    sk[q] = kv >> id_bits;
+    if (id_bits && q >= 1 && q <= cnt) sv[q - 1] = (uint32_t)(kv & idmask);
   }
-  for (uint32_t q = tid; q < cnt; q += kST) sv[q] = vals[base + q];
+  if (!id_bits)
+    for (uint32_t q = tid; q < cnt; q += kST) sv[q] = vals[base + q];
   __syncthreads();
 
   const uint32_t e0 = tid * kSI;
@@ -398,6 +403,7 @@ struct RoundArgs {
   uint32_t *bg_head, *bg_off, *bg_pos;  // per big group: head slot, first big entry, first list entry
   uint32_t bg_cap;
   int mb;
+  int id_bits;                 // > 0: big keys carry the suffix in their low id_bits bits (no values)
   uint32_t *big_hist;          // digit counts of the big keys' lowest hist_bits bits
   int hist_bits;
   uint32_t *words;             // [1] big entries, [3] big groups (of the round)
@@ -847,9 +853,13 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
       if (m && a.woff && i2 < a.n) m -= a.woff[a.wid[i2]];
       const uint64_t key = ((uint64_t)o << a.mb) | m;
       const uint32_t j = BC + bx[i];
-      if (j < a.ub && o < a.bg_cap) {
-        a.bkeys[j] = key;
-        a.bvals[j] = i2;
+      if (j < a.ub && o < a.bg_cap && i2 < a.n) {
+        if (a.id_bits) {
+          a.bkeys[j] = (key << a.id_bits) | i2;
+        } else {
+          a.bkeys[j] = key;
+          a.bvals[j] = i2;
+        }
         atomicAdd(&hcnt[(uint32_t)key & hmask], 1u);
       } else {
         atomicExch(a.err, kDevRange);
@@ -1017,7 +1027,8 @@ __global__ void k_lcp_perm(const uint32_t *__restrict__ sa, const uint32_t *__re
 int split_launch(apo_ctx *c, bool big, const uint64_t *keys, const uint32_t *vals, uint32_t ub,
                  const uint32_t *n_dev, int ord_shift, const uint32_t *bg_head, const uint32_t *bg_off,
                  const uint32_t *bg_pos, uint32_t bg_cap, uint32_t level, bool finals, uint32_t *snap,
-                 SuffixState &st, uint32_t *nid, uint32_t *nhd, uint32_t *count_out, cudaStream_t s) {
+                 SuffixState &st, uint32_t *nid, uint32_t *nhd, uint32_t *count_out, cudaStream_t s,
+                 int id_bits = 0) {
   const int tiles = std::max(1, ceil_div(ub, kSTile));
   APO_TRY(ensure_lookback(c, (size_t)2 * tiles));
   uint32_t *misc = c->ps.counters + kCtrMisc;
@@ -1028,12 +1039,12 @@ int split_launch(apo_ctx *c, bool big, const uint64_t *keys, const uint32_t *val
     k_split<true><<<tiles, kST, 0, s>>>(keys, vals, ub, n_dev, ord_shift, bg_head, bg_off, bg_pos, bg_cap, level,
                                         finals, snap, st.sa, st.rank, st.fin, nid, nhd, st.n, count_out, st.n,
                                         c->ps.lookback, c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
-                                        c->ps.err);
+                                        c->ps.err, id_bits);
   else
     k_split<false><<<tiles, kST, 0, s>>>(keys, vals, ub, n_dev, 0, nullptr, nullptr, nullptr, 0, level, finals,
                                          snap, st.sa, st.rank, st.fin, nid, nhd, st.n, count_out, st.n,
                                          c->ps.lookback, c->ps.lookback + tiles, misc + kMiscRefreshTiles, ep,
-                                         c->ps.err);
+                                         c->ps.err, 0);
   APO_CUDA_TRY(cudaGetLastError());
   return APO_OK;
 }
@@ -1273,6 +1284,7 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   // with no big entries has no big groups after it, so from then on the big
   // path is not queued.
   const int mb = bits_for(st.win.count > 1 ? st.win.max_len : n);
+  const int idb = std::max(1, bits_for(n - 1));  // bits of a suffix index
   uint32_t ub = n;      // bound on the current round's list length
   uint32_t big_ub = n;  // bound on its big entries (a round has no more than the round before)
   bool big_possible = true;
@@ -1294,8 +1306,12 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     APO_TRY(ensure_lookback(c, std::max<size_t>((size_t)2 * tiles, ctiles)));
     SortPlan sp;
     big_ub = std::min(big_ub, ub);
+    // the big keys carry the suffix in their low bits when it fits: a
+    // keys-only sort moves 16 instead of 24 bytes per entry and pass
+    const int kbits = bits_for(big_ub / (kRdBig + 1) + 1) + mb;
+    const int id_bits = idb + kbits <= 64 ? idb : 0;
     if (big_possible) {
-      const DigitRange dr{0, bits_for(big_ub / (kRdBig + 1) + 1) + mb, false};
+      const DigitRange dr{id_bits, id_bits + kbits, false};
       APO_TRY(sort_plan(c, big_ub, &dr, 1, &sp, s));
       APO_TRY(sort_first_hist_clear(c, s));
     }
@@ -1333,6 +1349,7 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       a.bg_pos = bg_pos;
       a.bg_cap = bg_cap;
       a.mb = mb;
+      a.id_bits = id_bits;
       a.big_hist = sort_first_hist(c);
       a.hist_bits = big_possible && sp.shape >= 0 ? sp.bits : 8;
       a.words = words;
@@ -1346,10 +1363,12 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
     }
     APO_CUDA_TRY(cudaGetLastError());
     if (big_possible && sp.shape >= 0) {
-      b.cur = 0;
-      APO_TRY(radix_sort_planned(c, b, big_ub, sp, s, words + 1, true));
-      APO_TRY(split_launch(c, true, b.keys[b.cur], b.vals[b.cur], big_ub, words + 1, mb, bg_head, bg_off, bg_pos,
-                           bg_cap, r, true, st.snaps[r], st, hid, hhd, nullptr, s));
+      SortBuffers bb = b;
+      bb.cur = 0;
+      if (id_bits) bb.vals[0] = bb.vals[1] = nullptr;
+      APO_TRY(radix_sort_planned(c, bb, big_ub, sp, s, words + 1, true));
+      APO_TRY(split_launch(c, true, bb.keys[bb.cur], bb.vals[bb.cur], big_ub, words + 1, mb, bg_head, bg_off,
+                           bg_pos, bg_cap, r, true, st.snaps[r], st, hid, hhd, nullptr, s, id_bits));
     }
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscRoundTiles, 0, sizeof(uint32_t), s));
     {
