@@ -990,10 +990,35 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W, const uin
       continue;
     }
     const uint32_t we = win_end(W, i, n);  // i and j lie in the same window
+    const uint32_t lim = we - max(i, j);    // tokens left to compare in both suffixes
     uint32_t steps = 0;
-    while (steps < kPDirect && i + (uint64_t)l < we && j + (uint64_t)l < we && S[i + l] == S[j + l]) {
-      ++l;
-      ++steps;
+    // four token pairs per step (eight independent loads in flight), then
+    // one at a time near the window's end
+    for (bool more = true; more && steps < kPDirect;) {
+      if (l + 4 <= lim) {
+        const T a0 = S[i + l], a1 = S[i + l + 1], a2 = S[i + l + 2], a3 = S[i + l + 3];
+        const T b0 = S[j + l], b1 = S[j + l + 1], b2 = S[j + l + 2], b3 = S[j + l + 3];
+        if (a0 != b0) {
+          more = false;
+        } else if (a1 != b1) {
+          l += 1;
+          more = false;
+        } else if (a2 != b2) {
+          l += 2;
+          more = false;
+        } else if (a3 != b3) {
+          l += 3;
+          more = false;
+        } else {
+          l += 4;
+          steps += 4;
+        }
+      } else if (l < lim && S[i + l] == S[j + l]) {
+        ++l;
+        ++steps;
+      } else {
+        more = false;
+      }
     }
     if (steps >= kPDirect) {
       for (int lev = levels - 1; lev >= 0; --lev) {
