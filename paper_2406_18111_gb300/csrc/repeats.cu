@@ -96,7 +96,9 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
       // with several windows, the id and the start are relative to the
       // window (its suffixes occupy a contiguous SA range starting at its
       // offset), which keeps the key and value digits to the longest window
-      const uint32_t w = win_id(W, a), wbase = W.off_dev ? W.off_dev[w] : 0u;
+      // (the pair's SA slots and suffixes lie in the same window: its id is
+      // read at slot k, next to the other threads' reads)
+      const uint32_t w = win_id(W, k), wbase = W.off_dev ? W.off_dev[w] : 0u;
       const long long j = prev_less(T, k, l, err);
       key = ((uint64_t)w << (bl + bi)) | ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1 - wbase);
       a -= wbase;

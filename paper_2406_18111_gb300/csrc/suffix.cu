@@ -450,6 +450,45 @@ __device__ __forceinline__ void flags_exclusive(uint32_t bits, int rows, uint32_
   __syncthreads();
 }
 
+// Two flag sets at once (their counts packed in 16-bit halves: a tile's
+// totals stay below 2^16): the exclusive counts of both, one scan.
+__device__ __forceinline__ void flags_exclusive2(uint32_t bits_a, uint32_t bits_b, int rows, uint32_t *rowtot,
+                                                 uint32_t (&ex_a)[kRdRows], uint32_t (&ex_b)[kRdRows],
+                                                 uint32_t *total_a, uint32_t *total_b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  uint32_t pre[kRdRows];
+#pragma unroll
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= rows) break;
+    const uint32_t ba = __ballot_sync(0xffffffffu, (bits_a >> i) & 1u);
+    const uint32_t bb = __ballot_sync(0xffffffffu, (bits_b >> i) & 1u);
+    pre[i] = __popc(ba & lt) | (__popc(bb & lt) << 16);
+    if (lane == 0) rowtot[i * kRdWarps + warp] = __popc(ba) | (__popc(bb) << 16);
+  }
+  __syncthreads();
+  if (warp == 0) {  // (row, warp) counts in row-major order: 2 per lane
+    const int m = rows * kRdWarps;
+    const uint32_t c0 = 2 * lane < m ? rowtot[2 * lane] : 0u, c1 = 2 * lane + 1 < m ? rowtot[2 * lane + 1] : 0u;
+    const uint32_t inc = warp_inclusive(c0 + c1, OpSum());
+    if (2 * lane < m) rowtot[2 * lane] = inc - c0 - c1;
+    if (2 * lane + 1 < m) rowtot[2 * lane + 1] = inc - c1;
+    if (lane == 31) rowtot[kRdRows * kRdWarps] = inc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kRdRows; ++i) {
+    if (i >= rows) break;
+    const uint32_t e = rowtot[i * kRdWarps + warp] + pre[i];
+    ex_a[i] = e & 0xffffu;
+    ex_b[i] = e >> 16;
+  }
+  const uint32_t t = rowtot[kRdRows * kRdWarps];
+  *total_a = t & 0xffffu;
+  *total_b = t >> 16;
+  __syncthreads();
+}
+
 // Minor key of every list entry of round r: rank_{r-1}[i + h] + 1, or 0
 // when i + h is past the window's end (absolute slots).  A streaming pass
 // with independent loads in flight, so that the round kernel reads the keys
@@ -640,8 +679,7 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
     }
   }
   uint32_t sx[kRdRows], bx[kRdRows], S, bc;
-  flags_exclusive(smb, mrows, rowtot, sx, &S);
-  flags_exclusive(bgb, mrows, rowtot, bx, &bc);
+  flags_exclusive2(smb, bgb, mrows, rowtot, sx, bx, &S, &bc);
   // the tile's big entries and big groups are known: their prefixes over the
   // tiles before, resolved at once so that inclusive prefixes spread through
   // the tiles in flight and every walk back stays short
