@@ -221,8 +221,9 @@ int apo_find_repeats_batched(apo_ctx *ctx, const apo_windows *windows,
 int apo_find_repeats_workspace(apo_ctx *ctx, const apo_windows *windows, uint64_t *bytes);
 int apo_set_workspace(apo_ctx *ctx, void *workspace, uint64_t bytes);
 
-/* Graph mode for apo_find_repeats_batched (off by default).  The first call
- * with given arguments (token pointer and width, window offsets, min_len,
+/* Graph mode for apo_find_repeats and apo_find_repeats_batched (off by
+ * default).  The first call with given arguments (token pointer and width,
+ * window offsets, min_len,
  * output pointers and capacities) runs as usual while the values the host
  * reads back between its kernels are recorded; the call is then captured
  * into a CUDA graph that takes those values as given and checks each on the
@@ -230,8 +231,8 @@ int apo_set_workspace(apo_ctx *ctx, void *workspace, uint64_t bytes);
  * replay the graph, one launch for the whole call; when a check fails (the
  * token contents led to other counts) the replay is discarded and the call
  * runs as usual and is recorded again.  Results are the same either way.
- * Calls with one window, and calls while the context's workspace has moved
- * since the capture, run as usual.  enable = 0 turns it off and frees the
+ * Calls while the context's workspace has moved since the capture run as
+ * usual (and are recorded again).  enable = 0 turns it off and frees the
  * graphs. */
 int apo_graph_mode(apo_ctx *ctx, int enable);
 /* Since graph mode was turned on: calls answered by a graph replay, graphs

@@ -293,23 +293,34 @@ class Apo:
 
     # -------------------------------------------------------------- Alg. 2
     def find_repeats(self, tokens, min_len: int, stages: bool = True, stream=None,
-                     sa_lcp: bool = False) -> Repeats:
+                     sa_lcp: bool = False, reuse: bool = False) -> Repeats:
         """Alg. 2 on one window of device tokens (int32 = u32, int64 = u64).
         stages: also return SA, LCP and the candidates; sa_lcp: SA and LCP
-        only (what match_candidates can reuse)."""
+        only (what match_candidates can reuse).  With reuse, the output
+        buffers are kept for the next call of the same sizes (the returned
+        tensors are then overwritten by it), so that repeated calls hand the
+        library the same arguments (graph mode)."""
         import torch
         n = int(tokens.shape[0])
         dev = tokens.device
         u32 = torch.int32
         M = max(1, 2 * (n - 1))
         K = max(1, n // max(1, min_len))
-        sa = torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None
-        lcp = torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None
-        cl = torch.empty(M, dtype=u32, device=dev) if stages else None
-        ci = torch.empty(M, dtype=u32, device=dev) if stages else None
-        cs = torch.empty(M, dtype=u32, device=dev) if stages else None
-        ca = torch.empty(M, dtype=torch.uint8, device=dev) if stages else None
-        ss, sl, st, tl, ts = (torch.empty(K, dtype=u32, device=dev) for _ in range(5))
+        bkey = ("one", n, int(min_len), bool(stages), bool(sa_lcp), str(dev))
+        bufs = getattr(self, "_bufs", {}).get(bkey) if reuse else None
+        if bufs is None:
+            bufs = (torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None,
+                    torch.empty(max(1, n), dtype=u32, device=dev) if stages or sa_lcp else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=u32, device=dev) if stages else None,
+                    torch.empty(M, dtype=torch.uint8, device=dev) if stages else None,
+                    *(torch.empty(K, dtype=u32, device=dev) for _ in range(5)))
+            if reuse:
+                if not hasattr(self, "_bufs"):
+                    self._bufs = {}
+                self._bufs[bkey] = bufs
+        sa, lcp, cl, ci, cs, ca, ss, sl, st, tl, ts = bufs
         counts = (ctypes.c_uint64 * 4)()
         o = apo_repeats_out(_ptr(sa), _ptr(lcp), _ptr(cl), _ptr(ci), _ptr(cs), _ptr(ca),
                             M if stages else 0, _ptr(ss), _ptr(sl), _ptr(st), K, _ptr(tl), _ptr(ts), K,

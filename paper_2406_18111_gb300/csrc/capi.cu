@@ -496,8 +496,14 @@ int apo_find_repeats(apo_ctx *c, const apo_window *w, const apo_repeats_params *
   const uint64_t off[2] = {0, w->n};
   apo_repeats_out o = *out;
   o.cand_off = o.sel_off = o.trace_off = nullptr;
-  const int r = drv::find_repeats_driver(c, w->tokens, w->token_bytes, w->n, off, 1, p, &o,
-                                    static_cast<cudaStream_t>(stream));
+  int r;
+  if (c->graph_mode) {  // a repeated call on the same buffers replays as one graph
+    const apo_windows ws{1, w->tokens, w->token_bytes, off};
+    r = graph_batched(c, &ws, p, &o, static_cast<cudaStream_t>(stream));
+  } else {
+    r = drv::find_repeats_driver(c, w->tokens, w->token_bytes, w->n, off, 1, p, &o,
+                                 static_cast<cudaStream_t>(stream));
+  }
   for (int k = 0; k < 4; ++k) out->counts[k] = o.counts[k];
   return r;
 }

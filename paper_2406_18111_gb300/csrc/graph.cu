@@ -163,7 +163,7 @@ int graph_batched(apo_ctx *c, const apo_windows *ws, const apo_repeats_params *p
   auto eager = [&]() {
     return drv::find_repeats_driver(c, ws->tokens, ws->token_bytes, total, ws->win_off, W, p, out, s);
   };
-  if (W < 2 || total == 0) return eager();  // one window: the plain path
+  if (total == 0) return eager();
   APO_TRY(ensure_cache(c));
   GraphCache *g = c->graphs;
   std::vector<uint32_t> win;

@@ -712,6 +712,54 @@ def test_optimum_limits(apo):
 
 
 # ---------------------------------------------------------------- graph mode
+@pytest.mark.parametrize("kind", ["u32", "u64"])
+def test_graph_mode_single_window(apo, kind):
+    """One window replayed as a CUDA graph (apo_find_repeats in graph mode)
+    gives the same bytes as the plain call: on repeats of the same window,
+    after its contents change (the replay's checks fail and it is
+    recorded again), and back; u64 windows take the token dictionary."""
+    import torch
+    from paper_2406_18111_gb300 import Apo, as_u32
+    n = 1 << 15
+    if kind == "u32":
+        a = W.periodic_window(n, 113, 0.03, 1000, seed=41)
+        dt, tdt = np.int32, torch.int32
+    else:
+        ts = W.config2_tasks(n, seed=42)
+        a = oracle.hash_tasks(ts)
+        dt, tdt = np.int64, torch.int64
+    b = a.copy()
+    rng = np.random.default_rng(5)
+    pos = rng.integers(0, n, size=n // 40)
+    b[pos] = a[rng.integers(0, n, size=len(pos))]
+    names = ("sa", "lcp", "cand_len", "cand_id", "cand_start", "sel_start", "sel_len", "sel_trace",
+             "trace_len", "trace_start")
+
+    def snap(r):
+        d = {k: as_u32(getattr(r, k)).copy() for k in names}
+        d["acc"] = r.cand_accepted.cpu().numpy().copy()
+        d["rounds"] = r.rounds
+        return d
+
+    want = {name: snap(apo.find_repeats(dev(t, dt), 5)) for name, t in (("a", a), ("b", b))}
+    o = oracle.find_repeats(a.astype(np.uint64), 5)
+    assert np.array_equal(want["a"]["sel_start"], o.sel_start)
+    g = Apo(0)
+    try:
+        g.graph_mode(True)
+        buf = torch.empty(n, dtype=tdt, device="cuda")
+        for name in ("a", "a", "a", "b", "b", "a"):
+            buf.copy_(torch.from_numpy((a if name == "a" else b).view(dt)))
+            got = snap(g.find_repeats(buf, 5, reuse=True))
+            for k, v in want[name].items():
+                assert np.array_equal(np.asarray(got[k]), np.asarray(v)), (name, k)
+        st = g.graph_stats()
+        assert st["replays"] >= 3 and st["captures"] >= 2 and st["discarded"] >= 1, st
+        g.graph_mode(False)
+    finally:
+        g.close()
+
+
 def test_graph_mode_results_equal_eager(apo):
     """Batched calls replayed as CUDA graphs give the same bytes as the plain
     path: on a repeated batch (the replay is valid), on a batch of the same
