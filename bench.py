@@ -55,14 +55,15 @@ WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/30
 # descriptor bytes in, 8 out (per task, at the workload's mean of 4.5
 # arguments).  The greedy loop and the automaton
 # passes are chains of dependent accesses (latency-bound) and have no entry.
-BYTES_PER_UNIT = {"rs_pass": 24, "round": 36, "split": 24, "rs_hist": 12, "hash_tasks": 16 + 4.5 * 13,
+BYTES_PER_UNIT = {"rs_pass": 24, "rs_pass_keys": 16, "round": 36, "split": 24, "rs_hist": 12,
+                  "hash_tasks": 16 + 4.5 * 13,
                   "plcp": 24, "rep.cand_gen": 36, "rep.compact": 16}
 
 
 # The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
 # with their radix sorts and rank refreshes) and the Phi/PLCP LCP.
-SA_LCP_KERNELS = ("init_keys", "key_or", "sa_dict", "wsb", "rs_hist", "rs_offsets", "rs_pass", "round", "split",
-                  "list_compact", "minor", "phi", "plcp", "lcp_perm")
+SA_LCP_KERNELS = ("init_keys", "key_or", "sa_dict", "wsb", "rs_hist", "rs_offsets", "rs_pass", "rs_pass_keys",
+                  "round", "split", "list_compact", "minor", "phi", "plcp", "lcp_perm")
 
 
 def sa_lcp_bytes(lcp, win_off, w: int) -> tuple[float, list]:

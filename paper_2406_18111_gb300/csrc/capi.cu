@@ -135,7 +135,8 @@ const char *const kKernelNames[kKCount] = {
     "traces", "sel_out", "pat_layout", "table_init", "end_pairs", "mark_ends", "ac_fix",
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
-    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact", "minor"};
+    "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact", "minor",
+    "rs_pass_keys"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {

@@ -340,8 +340,8 @@ int sort_with(apo_ctx *c, const Shape &sh, SortBuffers &b, uint32_t n, const uin
     const uint32_t ep = next_epoch(c);
     const int nxt = p + 1 < pl.n ? pl.p[p + 1] : -1;
     {
-      Launch lp_(c, count ? kKRsPass : kKRsTune, n, s);
       const bool ko = b.vals[b.cur] == nullptr;
+      Launch lp_(c, count ? (ko ? kKRsPassKeys : kKRsPass) : kKRsTune, n, s);
       (ko ? sh.pass_keys : sh.pass)<<<tiles, sh.threads, ko ? sh.smem_keys : sh.smem, s>>>(
           b.keys[b.cur], b.vals[b.cur], b.keys[b.cur ^ 1],
                                                  b.vals[b.cur ^ 1], n, n_dev, pl.p[p], hist + p * kMaxRadix, nxt,
