@@ -451,6 +451,39 @@ def test_served_results_equal_alone(apo):
             assert np.array_equal(getattr(got, f), getattr(o, f)), f
 
 
+def test_served_config5_mix(apo):
+    """Config 5's request mix (window lengths log-uniform 4,096..2^20, the
+    first 0.1 s of its Poisson arrivals: about 200 requests) submitted in
+    bursts while earlier batches run: every result equals the plain call on
+    its window, and every tenth one also the oracle (on a thread pool)."""
+    import time
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2406_18111_gb300 import Server, as_u32
+    t_arr, L, P = W.served_requests(0.1, 2000.0, seed=77)
+    wins = [W.served_window(k, int(L[k]), int(P[k]), seed=77) for k in range(len(L))]
+    assert len(wins) >= 150
+    srv = Server(0, min_len=5, token_bytes=4, max_batch_tokens=1 << 24, max_batch_windows=64, lanes=2)
+    ids = []
+    for k, S in enumerate(wins):
+        ids.append(srv.submit(S))
+        if k % 25 == 24:
+            time.sleep(0.002)  # let lanes start batches while more requests arrive
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    assert max(x.batch_windows for x in res) > 1
+    fields = ("sel_start", "sel_len", "sel_trace", "trace_len", "trace_start")
+    for S, got in zip(wins, res):
+        alone = apo.find_repeats(tokens_dev(S, 4), 5, stages=False)
+        for f in fields:
+            assert np.array_equal(getattr(got, f), as_u32(getattr(alone, f))), f
+    sample = list(range(0, len(wins), 10))
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        ors = list(ex.map(lambda k: oracle.find_repeats(wins[k].astype(np.uint64), 5), sample))
+    for k, o in zip(sample, ors):
+        for f in fields:
+            assert np.array_equal(getattr(res[k], f), getattr(o, f)), (k, f)
+
+
 def test_served_admission_by_footprint(apo):
     """A pool that holds one request's footprint at a time: the second and
     third requests wait for the one before to return its slice, never more
