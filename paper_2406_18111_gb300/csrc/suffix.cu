@@ -1028,7 +1028,10 @@ __global__ void k_plcp(const T *__restrict__ S, uint32_t n, Windows W, const uin
       continue;
     }
     const uint32_t we = win_end(W, i, n);  // i and j lie in the same window
-    const uint32_t lim = we - max(i, j);    // tokens left to compare in both suffixes
+    // tokens left to compare in both suffixes (0 if j is not before the
+    // window's end: only a suffix array from a replay whose checks failed,
+    // and whose results are discarded, can hold such a pair)
+    const uint32_t lim = max(i, j) < we ? we - max(i, j) : 0u;
     uint32_t steps = 0;
     // four token pairs per step (eight independent loads in flight), then
     // one at a time near the window's end
