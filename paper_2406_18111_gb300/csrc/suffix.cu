@@ -34,10 +34,11 @@
 // (SA, final rank, level recorded in fin[]); the others form the next list.
 //
 // Level ranks for the LCP.  Every round writes the new level rank of each
-// of its active suffixes into that level's snapshot array and nothing else,
-// so snaps[L][i] is valid exactly when suffix i was still grouped at the
-// start of round L (fin[i] >= L); earlier-final suffixes keep their final
-// slot in rank[i].  level_rank(L, i) therefore reads fin[i] first.  A round
+// of its active suffixes that stay grouped into that level's snapshot array
+// and nothing else, so snaps[L][i] is valid exactly when suffix i is still
+// grouped after round L (fin[i] > L); a suffix final at level L or before
+// has its level rank -- its final slot -- in rank[i] (a group of one starts
+// at its own slot).  level_rank(L, i) therefore reads fin[i] first.  A round
 // reads only the previous level and final ranks, which no kernel of the
 // same round writes, so rounds need no copies of the rank array.
 //
@@ -93,12 +94,12 @@ __device__ __forceinline__ bool bit_at(const uint32_t *__restrict__ bits, uint32
   return (__ldg(bits + (j >> 5)) >> (j & 31)) & 1u;
 }
 
-// Level-L rank of suffix j: its final slot when it was settled before level
-// L, else the level's snapshot.
+// Level-L rank of suffix j: its final slot when it was settled at level L
+// or before, else the level's snapshot.
 __device__ __forceinline__ uint32_t level_rank(const uint8_t *__restrict__ fin, const uint32_t *__restrict__ rank,
                                                const uint32_t *__restrict__ snap, uint32_t L, uint32_t j) {
   const uint32_t f = fin[j];
-  return f < L ? rank[j] : snap[j];
+  return f <= L ? rank[j] : snap[j];
 }
 
 // Decoupled look-back: lb_publish stores the tile's aggregate, lb_sum_warp
@@ -238,9 +239,9 @@ __global__ void __launch_bounds__(kST) k_split(
       atomicExch(err, kDevRange);
       continue;
     }
-    snap[id] = head;
+    const bool alone = finals && h && ((hb >> (i + 1)) & 1u);
+    if (!alone) snap[id] = head;  // (a final suffix's level rank is its rank[])
     if (!finals) continue;
-    const bool alone = h && ((hb >> (i + 1)) & 1u);
     if (alone) {
       sa[slot] = id;
       rank[id] = slot;
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(256) k_minor(const uint32_t *__restrict__ lid,
 #pragma unroll
     for (int u = 0; u < kI; ++u) {
       const uint64_t k = k0 + (uint64_t)u * blockDim.x;
-      if (k < A) mout[k] = j[u] < n ? ((uint32_t)fb[u] < r - 1 ? rank[j[u]] : snap_prev[j[u]]) + 1 : 0u;
+      if (k < A) mout[k] = j[u] < n ? ((uint32_t)fb[u] <= r - 1 ? rank[j[u]] : snap_prev[j[u]]) + 1 : 0u;
     }
   }
 }
@@ -856,13 +857,13 @@ __global__ void __launch_bounds__(kRdThreads, 4) k_round(const RoundArgs a) {
         atomicExch(a.err, kDevRange);
         continue;
       }
-      a.snap_cur[id] = head;
       if (((stf >> i) & 1u) && ((enf >> i) & 1u)) {  // alone in its subgroup: final
         a.sa[slot] = id;
         a.rank[id] = slot;
         a.fin[id] = (uint8_t)a.r;
         a.hhd[at] = kHole;
       } else {
+        a.snap_cur[id] = head;
         a.hid[at] = id;
         a.hhd[at] = head;
       }
