@@ -72,7 +72,13 @@ __device__ __forceinline__ void pair_cand(uint32_t s1, uint32_t s2, uint32_t p, 
 __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ lcp,
                            uint32_t n, uint32_t min_len, MinTree T, int bi, int bl, uint32_t lmax, int ks,
                            Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                           uint32_t *count, uint32_t *err) {
+                           uint32_t *count, uint32_t *err, uint32_t *__restrict__ hist, int hist_bits) {
+  // the sort's first digit place (the key's lowest hist_bits bits when the
+  // key holds the start, else the value's): counted here for the sort
+  __shared__ uint32_t sh[512];
+  const uint32_t hmask = (1u << hist_bits) - 1;
+  for (uint32_t d = threadIdx.x; d <= hmask; d += blockDim.x) sh[d] = 0;
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n - 1; base += stride) {
@@ -117,14 +123,21 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
         atomicExch(err, kDevRange);
         continue;
       }
-      keys[slot] = ks ? (key << ks) | a : key;
-      if (ok_b) keys[slot + 1] = ks ? (key << ks) | b : key;
+      const uint64_t ka = ks ? (key << ks) | a : key, kb = ks ? (key << ks) | b : key;
+      keys[slot] = ka;
+      if (ok_b) keys[slot + 1] = kb;
+      // the first digit: of the key when it holds the start, else of the value
+      atomicAdd(&sh[(ks ? (uint32_t)ka : a) & hmask], 1u);
+      if (ok_b) atomicAdd(&sh[(ks ? (uint32_t)kb : b) & hmask], 1u);
       if (!ks) {  // the start is the value (otherwise it is the key's low digits)
         vals[slot] = a;
         if (ok_b) vals[slot + 1] = b;
       }
     }
   }
+  __syncthreads();
+  for (uint32_t d = threadIdx.x; d <= hmask; d += blockDim.x)
+    if (sh[d]) atomicAdd(&hist[d], sh[d]);
 }
 
 // Order-preserving compaction of the indices k < m with pred(k) (one
@@ -760,11 +773,22 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     set_error("repeats: workspace too small");
     return APO_ENOMEM;
   }
+  // the candidate sort is planned for the bound M, so that candidate
+  // generation can count its first digit place (the start's low digits)
+  const DigitRange r[2] = {{0, bs, true}, {0, bw + bl + bi, false}};
+  const DigitRange rk{0, bw + bl + bi + bs, false};
+  SortPlan sp;
+  if (ks)
+    APO_TRY(sort_plan(c, (uint32_t)M, &rk, 1, &sp, s));
+  else
+    APO_TRY(sort_plan(c, (uint32_t)M, r, 2, &sp, s));
+  APO_TRY(sort_first_hist_clear(c, s));
   APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscCandCount, 0, sizeof(uint32_t), s));
   {
     Launch lp_(c, kKCandGen, n, s);
     k_cand_gen<<<g, 256, 0, s>>>(st.sa, lcp, n, min_len, T, bi, bl, lmax, ks, W, b.keys[0], b.vals[0],
-                                 misc + kMiscCandCount, c->ps.err);
+                                 misc + kMiscCandCount, c->ps.err, sort_first_hist(c),
+                                 sp.shape >= 0 ? sp.bits : 8);
   }
   APO_CUDA_TRY(cudaGetLastError());
   uint32_t mraw = 0;
@@ -777,16 +801,14 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   if (mraw) {
     // (window, length, id, start): one key, or start digits (the value)
     // first and then the (window, length, id) key
-    const DigitRange r[2] = {{0, bs, true}, {0, bw + bl + bi, false}};
-    const DigitRange rk{0, bw + bl + bi + bs, false};
     b.cur = 0;
     if (ks) {  // the key holds every field: a keys-only sort (two thirds of the bytes per pass)
       SortBuffers kb = b;
       kb.vals[0] = kb.vals[1] = nullptr;
-      APO_TRY(radix_sort_pairs(c, kb, mraw, &rk, 1, s));
+      APO_TRY(radix_sort_planned(c, kb, mraw, sp, s, nullptr, true));
       b.cur = kb.cur;
     } else {
-      APO_TRY(radix_sort_pairs(c, b, mraw, r, 2, s));
+      APO_TRY(radix_sort_planned(c, b, mraw, sp, s, nullptr, true));
     }
     PredFirstOfRun pr{b.keys[b.cur], ks ? nullptr : b.vals[b.cur]};
     APO_TRY(compact(c, pr, mraw, sel, misc + kMiscCandUnique, s));

@@ -345,8 +345,15 @@ __global__ void k_code_map(const void *__restrict__ tokens, int tb, uint32_t n, 
 }
 
 // key(i) = (window << (h0 * cb)) | code(i) code(i+1) .. code(i+h0-1), value i.
+// The keys' lowest hist_bits bits are counted into hist (the sort's first
+// digit place), so that the sort needs no histogram read of its own.
 __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t *__restrict__ codes, uint32_t n,
-                        uint32_t h0, int cb, Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                        uint32_t h0, int cb, Windows W, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                        uint32_t *__restrict__ hist, int hist_bits) {
+  __shared__ uint32_t sh[512];
+  const uint32_t hmask = (1u << hist_bits) - 1;
+  for (uint32_t d = threadIdx.x; d <= hmask; d += blockDim.x) sh[d] = 0;
+  __syncthreads();
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t we = win_end(W, i, n);
     uint64_t key = 0;
@@ -358,7 +365,11 @@ __global__ void k_pack0(const void *__restrict__ tokens, int tb, const uint32_t 
     if (W.count > 1) key |= (uint64_t)win_id(W, i) << (h0 * cb);
     keys[i] = key;
     vals[i] = i;
+    atomicAdd(&sh[(uint32_t)key & hmask], 1u);
   }
+  __syncthreads();
+  for (uint32_t d = threadIdx.x; d <= hmask; d += blockDim.x)
+    if (sh[d]) atomicAdd(&hist[d], sh[d]);
 }
 
 // ---------------------------------------------------------------- a doubling round
@@ -1305,13 +1316,17 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   uint32_t *first_count = misc + kMiscRefreshCount;
   if (h0 >= 2) {
     h0 = std::min<uint32_t>(h0, 32);
+    const DigitRange r{0, wb + (int)h0 * cb, false};
+    SortPlan sp;
+    APO_TRY(sort_plan(c, n, &r, 1, &sp, s));
+    APO_TRY(sort_first_hist_clear(c, s));
     {
       Launch lp_(c, kKInitKeys, n, s);
-      k_pack0<<<g, 256, 0, s>>>(tokens, tb, codes, n, h0, cb, st.win, b.keys[0], b.vals[0]);
+      k_pack0<<<g, 256, 0, s>>>(tokens, tb, codes, n, h0, cb, st.win, b.keys[0], b.vals[0], sort_first_hist(c),
+                                sp.shape >= 0 ? sp.bits : 8);
     }
     b.cur = 0;
-    const DigitRange r{0, wb + (int)h0 * cb, false};
-    APO_TRY(radix_sort_pairs(c, b, n, &r, 1, s));
+    APO_TRY(radix_sort_planned(c, b, n, sp, s, nullptr, true));
   } else {
     h0 = 1;
     {
