@@ -105,6 +105,12 @@ __global__ void k_cand_gen(const uint32_t *__restrict__ sa, const uint32_t *__re
       // (the pair's SA slots and suffixes lie in the same window: its id is
       // read at slot k, next to the other threads' reads)
       const uint32_t w = win_id(W, k), wbase = W.off_dev ? W.off_dev[w] : 0u;
+      const uint32_t wlen = (W.off_dev ? W.off_dev[w + 1] : n) - wbase;
+      if (a < wbase || b < wbase || a - wbase + (uint64_t)l > wlen || b - wbase + (uint64_t)l > wlen) {
+        // (only a suffix array or LCP from a replay whose checks failed)
+        atomicExch(err, kDevRange);
+        ok = ok_b = false;
+      }
       const long long j = prev_less(T, k, l, err);
       key = ((uint64_t)w << (bl + bi)) | ((uint64_t)(lmax - l) << bi) | (uint64_t)(j + 1 - wbase);
       a -= wbase;
@@ -209,13 +215,19 @@ __global__ void __launch_bounds__(kCT) k_compact(Pred pred, uint32_t m, const ui
 __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m, const uint32_t *m_dev,
                               const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                               int bi, int bl, uint32_t lmax, int ks, const uint32_t *__restrict__ woff,
-                              uint32_t *__restrict__ cl, uint32_t *__restrict__ cid, uint32_t *__restrict__ cs) {
+                              uint32_t nwin, uint32_t *__restrict__ cl, uint32_t *__restrict__ cid,
+                              uint32_t *__restrict__ cs, uint32_t *err) {
   m = min(m, *m_dev);  // m: an upper bound
   const uint64_t idmask = (bi >= 64) ? ~0ull : ((1ull << bi) - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
     const uint32_t k = sel[q];
     const uint64_t full = keys[k], key = full >> ks;
-    const uint32_t base = woff ? woff[(uint32_t)(key >> (bl + bi))] : 0u;  // back to global positions
+    const uint64_t w = key >> (bl + bi);
+    if (woff && w >= nwin) {  // (only keys of a replay whose checks failed)
+      atomicExch(err, kDevRange);
+      continue;
+    }
+    const uint32_t base = woff ? woff[(uint32_t)w] : 0u;  // back to global positions
     cl[q] = lmax - (uint32_t)((key >> bi) & lmax);
     cid[q] = (uint32_t)(key & idmask) + base;
     cs[q] = (ks ? (uint32_t)(full & ((1ull << ks) - 1)) : vals[k]) + base;
@@ -545,14 +557,15 @@ __global__ void k_sel_out(const uint64_t *__restrict__ keys, const uint32_t *__r
 
 // First index of each window in a list sorted by window (the window of entry
 // k is the window of position pos[k]); out[count] = m.
-__global__ void k_window_bounds(const uint32_t *__restrict__ pos, uint32_t m, Windows W,
+__global__ void k_window_bounds(const uint32_t *__restrict__ pos, uint32_t m, Windows W, uint32_t n,
                                 uint32_t *__restrict__ out, const uint32_t *m_dev = nullptr) {
   if (m_dev) m = min(m, *m_dev);  // m: an upper bound
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= W.count; w += gridDim.x * blockDim.x) {
     uint32_t lo = 0, hi = m;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (win_id(W, pos[mid]) < w) lo = mid + 1; else hi = mid;
+      const uint32_t p = pos[mid];
+      if ((p < n ? win_id(W, p) : W.count) < w) lo = mid + 1; else hi = mid;
     }
     out[w] = lo;
   }
@@ -817,7 +830,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
       Launch lp_(c, kKCandGather, mu, s);
       k_cand_gather<<<grid_for(mu, 256, c->num_sms), 256, 0, s>>>(sel, mu, m_dev, b.keys[b.cur], b.vals[b.cur],
                                                                   bi, bl, lmax, ks, W.count > 1 ? W.off_dev : nullptr,
-                                                                  cl, cid, cs);
+                                                                  W.count, cl, cid, cs, c->ps.err);
     }
   }
 
@@ -826,7 +839,7 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
   if (mu) {
     {
       Launch lp_(c, kKSlices, W.count + 1, s);
-      k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(cs, mu, W, cand_off, m_dev);
+      k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(cs, mu, W, n, cand_off, m_dev);
     }
     APO_CUDA_TRY(cudaMemsetAsync(misc + kMiscAccCount, 0, sizeof(uint32_t), s));
     APO_CUDA_TRY(cudaMemsetAsync(acc, 0, mu, s));
@@ -936,8 +949,8 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
     if (W.count > 1) {  // per-window offsets, then window-relative values
       {
         Launch lp_(c, kKSlices, W.count + 1, s);
-        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ss, K, W, sel_off);
-        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ts, Tn, W, trace_off);
+        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ss, K, W, n, sel_off);
+        k_window_bounds<<<ceil_div(W.count + 1, 256), 256, 0, s>>>(ts, Tn, W, n, trace_off);
       }
       {
         Launch lp_(c, kKSelOut, K, s);
