@@ -530,7 +530,7 @@ int apo_greedy_select_noalloc(const uint32_t *cand_len, const uint32_t *cand_sta
  * enabled, each launch is also bracketed by two CUDA events recorded on its
  * launch stream, and the elapsed device time is accumulated when the entry
  * is read.  `units` accumulates the elements each launch processed (keys for
- * a radix-sort pass, suffixes for a refresh, tokens for a match), from which
+ * a radix-sort pass, list entries for a doubling round, tokens for a match), from which
  * a caller derives algorithmic bytes.  The same kernel on different stages
  * is kept in separate entries: everything the matcher launches (including
  * the suffix array of its pattern text) carries the prefix "ac.", the
