@@ -192,6 +192,8 @@ struct apo_ctx {
   void *side = nullptr;             // grow-only buffer for sizes known only mid-call
   size_t side_bytes = 0;
   cudaEvent_t round_ev[2] = {nullptr, nullptr};  // doubling-round count read-backs
+  cudaStream_t aux = nullptr;                     // a second stream for independent launches
+  cudaEvent_t fork_ev[2] = {nullptr, nullptr};    // fork to it, join back
   void *rp[3] = {nullptr, nullptr, nullptr};     // trace replay buffers (grow-only)
   size_t rp_bytes[3] = {0, 0, 0};
   uint64_t rp_cap = 0;                            // occurrences the replay buffers hold

@@ -250,7 +250,10 @@ int apo_create(apo_ctx **out, int device) {
     return APO_ENOMEM;
   }
   if (cudaEventCreateWithFlags(&c->round_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->round_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->round_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     apo_destroy(c);
     set_error("apo_create: event creation failed");
@@ -283,6 +286,9 @@ int apo_destroy(apo_ctx *c) {
     if (p) cudaFree(p);
   for (auto e : c->round_ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : c->fork_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->aux) cudaStreamDestroy(c->aux);
   c->prof.release();
   delete c;
   return APO_OK;

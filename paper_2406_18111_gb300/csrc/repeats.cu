@@ -237,6 +237,7 @@ __global__ void k_cand_gather(const uint32_t *__restrict__ sel, uint32_t m, cons
 // ---------------------------------------------------------------- greedy
 constexpr int kGI = 4;  // candidates per thread per round
 constexpr uint32_t kGreedyFirstPhase = 1u << 16;  // candidates settled before the first drop
+constexpr uint32_t kGWideWin = 1u << 16;  // batched windows of this many tokens or more: 1024-thread blocks
 constexpr int glist_bytes(int threads) { return threads * kGI * 16; }
 
 template <bool kSmem>
@@ -269,7 +270,8 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
                                                const uint32_t *__restrict__ woff, uint32_t n,
                                                uint32_t *gbits, uint8_t *acc, uint32_t *acc_count,
                                                const uint32_t *__restrict__ corig, int persist,
-                                               const uint32_t *m_dev, uint32_t *err) {
+                                               const uint32_t *m_dev, uint32_t *err, uint32_t len_lo = 0,
+                                               uint32_t len_hi = 0xffffffffu) {
   constexpr int kGT = kT;
   constexpr int kGRound = kT * kGI;
   extern __shared__ __align__(16) uint32_t gsm[];
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(kT) k_greedy(const uint32_t *__restrict__ cl,
   if (m_dev) m = min(m, *m_dev);  // single window: m bounds the list, *m_dev is its length
   const uint32_t cb = cand_off ? cand_off[w] : 0u, ce = cand_off ? cand_off[w + 1] : m;
   const uint32_t ws = woff ? woff[w] : 0u, we = woff ? woff[w + 1] : n;
+  if (we - ws < len_lo || we - ws >= len_hi) return;  // a window for the other launch
   const uint32_t shift = kSmem ? ws : 0u;  // bitmap coordinate = position - shift
   const uint32_t words = kSmem ? ((we - ws + 31) / 32 + 3) & ~3u : 0;
   uint32_t *bits = kSmem ? gsm : gbits;
@@ -898,14 +901,44 @@ int find_repeats_from_sa(apo_ctx *c, const void *tokens, int tb, const SuffixSta
         prefix *= 2;
       }
     } else {
-      Launch lp_(c, kKGreedy, mu, s);
-      if (smem)
-        k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, mu, W.off_dev, n,
-                                                                  nullptr, acc, misc + kMiscAccCount,
-                                                                  nullptr, 0, nullptr, c->ps.err);
-      else
-        k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, mu, W.off_dev, n, gbits, acc,
-                                                        misc + kMiscAccCount, nullptr, 0, nullptr, c->ps.err);
+      // windows of kGWideWin tokens and more get blocks of 1024 threads (4x
+      // the candidates per round: their long sequences of rounds bound the
+      // launch), the others blocks of 256; each launch skips the other's
+      const bool wide = W.max_len >= kGWideWin;
+      const uint32_t hi = wide ? kGWideWin : 0xffffffffu;
+      if (wide) {  // on the context's second stream, beside the narrow windows' launch
+        const size_t list_w = glist_bytes(1024);
+        const bool smem_w = (long long)(bm_bytes + list_w) <= g_greedy_smem_max;
+        if (!smem_w && smem) APO_CUDA_TRY(cudaMemsetAsync(gbits, 0, gwords * 4, s));
+        cudaStream_t s2 = c->aux;
+        APO_CUDA_TRY(cudaEventRecord(c->fork_ev[0], s));
+        APO_CUDA_TRY(cudaStreamWaitEvent(s2, c->fork_ev[0], 0));
+        {
+          Launch lp_(c, kKGreedy, mu, s2);
+          if (smem_w)
+            k_greedy<1024, true><<<W.count, 1024, bm_bytes + list_w, s2>>>(cl, cs, coff, mu, W.off_dev, n,
+                                                                          nullptr, acc, misc + kMiscAccCount,
+                                                                          nullptr, 0, nullptr, c->ps.err, hi);
+          else
+            k_greedy<1024, false><<<W.count, 1024, list_w, s2>>>(cl, cs, coff, mu, W.off_dev, n, gbits, acc,
+                                                                misc + kMiscAccCount, nullptr, 0, nullptr,
+                                                                c->ps.err, hi);
+        }
+        APO_CUDA_TRY(cudaGetLastError());
+        APO_CUDA_TRY(cudaEventRecord(c->fork_ev[1], s2));
+      }
+      {
+        Launch lp_(c, kKGreedy, mu, s);
+        if (smem)
+          k_greedy<256, true><<<W.count, 256, bm_bytes + list, s>>>(cl, cs, coff, mu, W.off_dev, n,
+                                                                    nullptr, acc, misc + kMiscAccCount,
+                                                                    nullptr, 0, nullptr, c->ps.err, 0u, hi);
+        else
+          k_greedy<256, false><<<W.count, 256, list, s>>>(cl, cs, coff, mu, W.off_dev, n, gbits, acc,
+                                                          misc + kMiscAccCount, nullptr, 0, nullptr, c->ps.err,
+                                                          0u, hi);
+      }
+      if (wide) APO_CUDA_TRY(cudaStreamWaitEvent(s, c->fork_ev[1], 0));  // join
     }
     APO_CUDA_TRY(cudaGetLastError());
     APO_TRY(read_u32(c, misc + kMiscAccCount, &K, s, m_dev, &m));
