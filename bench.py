@@ -58,11 +58,9 @@ WORKLOAD = ("one window of 2^20 hashed task descriptors (nested periods 7/120/30
 BYTES_PER_UNIT = {"rs_pass": 24, "rs_pass_keys": 16, "round": 36, "split": 24, "rs_hist": 12,
                   "hash_tasks": 16 + 4.5 * 13,
                   "plcp": 24, "rep.cand_gen": 36, "rep.compact": 16}
-# Kernels launched for a host-side upper bound of their work (the doubling
-# rounds, their big-group sorts and splits: the exact counts stay on the
-# device): their recorded units overstate the work, so they are not chosen
-# for the `roofline` object, whose achieved bytes must be exact.
-UPPER_BOUND_UNITS = {"rs_pass_keys", "round", "split"}
+# (Launches sized for an upper bound -- the doubling rounds, their big-group
+# sorts and splits -- have their recorded units corrected by the library to
+# the exact counts once those are read, so every entry's units are exact.)
 
 
 # The suffix-array + LCP path: prefix doubling (rank init, doubling rounds
@@ -119,10 +117,11 @@ class _Range:
             torch.cuda.nvtx.range_pop()
 
 
-def traffic_for(workload: str, kernel: str, units_per_launch: float):
+def traffic_for(workload: str, kernel: str, launches_per_step: float):
     """DRAM bytes per launch of `kernel` from the committed ncu figures
-    (profiles/traffic.txt), or None when there are none or the kernel's
-    source changed since they were taken."""
+    (profiles/traffic.txt: bytes per step of the kernel's launches), or None
+    when there are none or the kernel's source changed since they were
+    taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -139,7 +138,7 @@ def traffic_for(workload: str, kernel: str, units_per_launch: float):
             h.update(open(src, "rb").read())
         if h.hexdigest() != f[4]:
             return None
-        return float(f[2]) * units_per_launch
+        return float(f[2]) / launches_per_step if launches_per_step else None
     return None
 
 
@@ -408,14 +407,14 @@ def run_batched(args, rank, world, local, emit=True, plain_steps=3):
         bpu = BYTES_PER_UNIT.get(name)
         r = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
              "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof,
-             "traffic": traffic_for("batched", name, units / la) if la else None,
+             "traffic": traffic_for("batched", name, la / args.steps) if la else None,
              "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
         if bpu is not None and kms > 0:
             ach = bpu * units / (kms / 1e3) / 1e9
             r.update({"achieved": ach, "frac": ach / peak, "algorithmic_bytes_per_launch": bpu * units / la,
                       "ms_per_launch": kms / la})
         return r
-    name = max((k for k in prof if k in BYTES_PER_UNIT and k not in UPPER_BOUND_UNITS), key=lambda k: prof[k][1])
+    name = max((k for k in prof if k in BYTES_PER_UNIT), key=lambda k: prof[k][1])
     roof = kernel_roof(name)
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -1174,13 +1173,12 @@ def main():
     # one are latency-bound chains: the greedy loop, automaton passes)
     peak, peak_kind = peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1])
-    dom = max(((k, v) for k, v in prof.items() if k in BYTES_PER_UNIT and k not in UPPER_BOUND_UNITS),
-              key=lambda kv: kv[1][1])
+    dom = max(((k, v) for k, v in prof.items() if k in BYTES_PER_UNIT), key=lambda kv: kv[1][1])
     name, (la, kms, units) = dom
     bpu = BYTES_PER_UNIT.get(name)
     roof = {"kernel": name, "bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
             "launches_per_step": la / args.steps, "share_of_step": kms / args.steps / ms_prof,
-            "traffic": traffic_for("window", name, units / la) if la else None,
+            "traffic": traffic_for("window", name, la / args.steps) if la else None,
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"}
     if bpu is not None and kms > 0:
         ach = bpu * units / (kms / 1e3) / 1e9

@@ -120,6 +120,9 @@ struct Profiler {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  // A launch sized for an upper bound records the bound as its units; once
+  // the exact count is known the difference is taken off again.
+  void adjust(int id, int64_t delta) { units[id + scope * kKCount] += (uint64_t)delta; }
   cudaEvent_t get();
   int resolve();
   void release();

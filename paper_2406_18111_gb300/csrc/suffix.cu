@@ -1370,6 +1370,24 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
   uint32_t ub = n;      // bound on the current round's list length
   uint32_t big_ub = n;  // bound on its big entries (a round has no more than the round before)
   bool big_possible = true;
+  // per round: the bounds its launches were sized for (units recorded by
+  // the profiler), corrected to the exact counts when those are read
+  struct RoundBounds {
+    uint32_t ub = 0, big_ub = 0;
+    int places = 0;
+    bool keys = false;
+  };
+  std::vector<RoundBounds> rb(2);
+  auto exact_list = [&](uint32_t rr, uint32_t len) {  // round rr's list held len entries
+    const int64_t d = (int64_t)len - (int64_t)rb[rr].ub;
+    for (int id : {(int)kKMinor, (int)kKRound, (int)kKListCompact}) c->prof.adjust(id, d);
+  };
+  auto exact_big = [&](uint32_t rr, uint32_t cnt) {  // round rr had cnt big entries
+    if (!rb[rr].places) return;
+    const int64_t d = (int64_t)cnt - (int64_t)rb[rr].big_ub;
+    c->prof.adjust(rb[rr].keys ? kKRsPassKeys : kKRsPass, d * rb[rr].places);
+    c->prof.adjust(kKSplit, d);
+  };
   for (uint32_t r = 1;; ++r) {
     if (st.levels >= max_levels) {
       // a device wait that gave up or an index out of range leaves counts
@@ -1444,7 +1462,12 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       k_round<<<tiles, kRdThreads, kRoundSmem, s>>>(a);
     }
     APO_CUDA_TRY(cudaGetLastError());
+    rb.resize(r + 1);
+    rb[r].ub = ub;
     if (big_possible && sp.shape >= 0) {
+      rb[r].big_ub = big_ub;
+      rb[r].places = sp.places;
+      rb[r].keys = id_bits != 0;
       SortBuffers bb = b;
       bb.cur = 0;
       if (id_bits) bb.vals[0] = bb.vals[1] = nullptr;
@@ -1478,7 +1501,13 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
         first = c->host_pinned[6];
         if (recording(c)) tape_put(c, &first, 1);
       }
+      if (!cap) exact_list(1, first);
       if (first == 0) {  // the first sort left no group: rounds 1 and 2 idle
+        if (!cap) {
+          exact_list(2, 0);
+          exact_big(1, 0);
+          exact_big(2, 0);
+        }
         st.levels = 1;
         break;
       }
@@ -1492,7 +1521,12 @@ int build_suffix_array(apo_ctx *c, const void *tokens, int tb, uint32_t n, Suffi
       w2[1] = c->host_pinned[17 + 2 * ((r - 1) & 1)];
       if (recording(c)) tape_put(c, w2, 2);
     }
+    if (!cap) {
+      exact_list(r, w2[0]);
+      exact_big(r - 1, w2[1]);
+    }
     if (w2[0] == 0) {  // round r had nothing to do: levels 0 .. r - 1
+      if (!cap) exact_big(r, 0);
       st.levels = (int)r;
       break;
     }
