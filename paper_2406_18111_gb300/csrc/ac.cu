@@ -51,6 +51,11 @@
 // changes returns at once.  The per-node match totals turn the output
 // offsets into one prefix sum over positions; each output record's chain is
 // flattened once, and a final kernel per position copies its matches.
+// Where the patterns are slices of the stream itself and long (deep
+// states over much of the stream), one exact pass replaces the chunks and
+// repairs: a warp per segment starts its walk one longest-pattern length
+// before the segment, from the root, and follows failure chains 32 nodes
+// at a time through lifting tables of the skip links.
 // Output order: end ascending, then pattern length descending (the output
 // chain's order), then pattern id ascending.
 #include <algorithm>
@@ -332,6 +337,17 @@ __device__ __forceinline__ uint32_t rep_of(const Sparse &S, uint32_t j, uint32_t
   return (uint32_t)max(0ll, y);
 }
 
+// The end of the block of sorted patterns that share d symbols with pattern
+// j: the smallest j' > j with slcp[j'] < d, or P.
+__device__ __forceinline__ uint32_t block_end(const Sparse &S, uint32_t j, uint32_t d, uint32_t P) {
+  uint32_t x = j + 1;  // every entry in (j, x) is >= d
+  for (int l = S.nlev - 1; l >= 0; --l) {
+    const uint64_t e = (uint64_t)x + (1u << l) - 1;
+    if (e < P && S.lev[l][e] >= d) x += 1u << l;
+  }
+  return x;
+}
+
 // ---------------------------------------------------------------- source mode
 // The patterns are slices of a source whose suffix array and LCP array are
 // given.  A pattern's key is (left end of its string's LCP interval in the
@@ -447,6 +463,7 @@ struct NodeArgs {
   Table g;
   uint32_t *fail, *own, *end_node;
   uint8_t *has_branch;  // [nodes] 1 if a branch-table edge leaves the node
+  unsigned long long *pref;  // [nodes] preferred child (null: not wanted), zeroed
   uint32_t *err;
   // source mode (the patterns are slices of a source with a known suffix
   // array): failure nodes are found through the source's LCP intervals
@@ -482,7 +499,12 @@ __device__ __forceinline__ uint32_t node_of(const NodeArgs &a, uint32_t j, uint3
 // One warp per pattern, one lane per depth d = 1 .. len + 1 (len + 1 is the
 // separator after the pattern).  A depth-d prefix that is its own node gets
 // its failure link, and the branch edge into it when it hangs off another
-// pattern's node; the pattern's end node counts one more pattern end.
+// pattern's node; the pattern's end node counts one more pattern end.  With
+// `pref`, every node also gets its preferred child: the one that the most
+// patterns pass through (for slices of the stream itself, the way the stream
+// most likely continues; ties to the larger node id).  The preferred
+// children are wanted by the halo pass only, which is when kPref is set.
+template <bool kPref>
 __global__ void k_ac_nodes(NodeArgs a) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -535,7 +557,11 @@ __global__ void k_ac_nodes(NodeArgs a) {
           const uint32_t parent = d == 1 ? a.root : node_of(a, j, d - 1);
           table_insert(a.g, parent, a.tsym[v], v, a.err);
           a.has_branch[parent] = 1;
+          if (kPref && d > 1)  // v as a child of parent, weighed by the patterns through it
+            atomicMax(&a.pref[parent], ((unsigned long long)(block_end(a.S, j, d, a.P) - j) << 32) | v);
         }
+        if (kPref && d < len)  // v's own next position as its child
+          atomicMax(&a.pref[v], ((unsigned long long)(block_end(a.S, j, d + 1, a.P) - j) << 32) | (v + 1));
       }
       a.fail[v] = f;
       if (d == len) {
@@ -747,11 +773,16 @@ __global__ void k_ac_fill_flat(const uint32_t *__restrict__ state, uint32_t n, c
 // symbols with the 32 symbols of T after the current state at once and
 // takes the whole agreeing run in one step; a mismatch is settled by one
 // lane with the goto table and the failure chain.
+constexpr int kLift = 5;  // skip^(2^k), k < kLift: 32 chain nodes per warp-wide step
 struct Automaton {
   const uint32_t *tsym;  // padded with kTsymPad separators past the text
+  const uint8_t *has_branch;
   Table g;
   const uint32_t *skip;  // failure steps taken after the primary edge did not match
   uint32_t root;
+  const uint32_t *lift[kLift];  // lift[k][u] = skip^(2^k)(u) (warp-wide walks only)
+  uint32_t batches;             // bound on the 32-node steps of one walk (chains end at the root)
+  const uint32_t *heavy[kLift];  // heavy[k][u] = hc^(2^k)(u), hc = preferred child (halo pass)
 };
 constexpr int kStateWarps = 4;
 
@@ -903,6 +934,144 @@ __global__ void __launch_bounds__(32 * kStateWarps)
   if ((threadIdx.x & 31) == 0 && v != rec_end) atomicAdd(changed, 1u);
 }
 
+// Pass A with a halo (exact in one pass).  The state at x is the longest
+// suffix of the stream up to x that is a trie node, so its depth is at most
+// the longest pattern length H.  A walk from the root that starts H
+// positions before g0 has read every symbol that state can span, and from
+// g0 on its states are the exact ones: each warp takes a segment [g0, g0 +
+// seg), starts at g0 - H and writes the states of its segment only.  The
+// halo costs H extra positions per segment; it pays where states are deep
+// (long patterns that the stream contains), which makes the chunked first
+// pass wrong over most positions and its repairs long.
+
+// The transition from v (not the root) on c after v's preferred child did
+// not match: v's next position in T or a branch edge of v, else the first
+// node on v's skip chain with an edge on c (the root, with or without one,
+// ends every chain).  The chain is taken 32 nodes at a time: lane j gets
+// skip^j(u0) in five doubling rounds (lanes [2^k, 2^(k+1)) apply
+// skip^(2^k) to the node of lane j - 2^k), the lanes test their nodes at
+// once and the first hit in chain order wins.
+__device__ __forceinline__ uint32_t fail_walk_warp(const Automaton &A, uint32_t v, uint32_t c,
+                                                   uint32_t *err) {
+  const uint32_t lane = threadIdx.x & 31, root = A.root;
+  uint32_t u0 = A.skip[v];
+  if (A.tsym[v + 1] == c) return v + 1;  // when the preferred child was another one
+  if (A.has_branch[v]) {
+    const uint32_t r = table_lookup(A.g, v, c);
+    if (r != kNil) return r;
+  }
+  for (uint32_t step = 0; step < A.batches; ++step) {
+    uint32_t u = u0;
+#pragma unroll
+    for (int k = 0; k < kLift; ++k) {
+      const uint32_t from = __shfl_up_sync(0xffffffffu, u, 1u << k);
+      if (lane >= (1u << k) && lane < (2u << k)) u = A.lift[k][from];
+    }
+    uint32_t r = kNil;
+    bool hit = false;
+    if (u == root) {
+      r = table_lookup(A.g, root, c);
+      if (r == kNil) r = root;
+      hit = true;
+    } else {
+      const uint32_t p = A.tsym[u + 1];
+      const uint8_t b = A.has_branch[u];
+      if (p == c) {
+        r = u + 1;
+        hit = true;
+      } else if (b) {
+        r = table_lookup(A.g, u, c);
+        hit = r != kNil;
+      }
+    }
+    const uint32_t h = __ballot_sync(0xffffffffu, hit);
+    if (h) return __shfl_sync(0xffffffffu, r, __ffs(h) - 1);
+    u0 = A.skip[__shfl_sync(0xffffffffu, u, 31)];  // skip^32 of this step's first node
+  }
+  if (lane == 0) atomicExch(err, kDevRange);  // a chain longer than the deepest node
+  return root;
+}
+
+// One warp runs positions [x, x1) from the root and writes the states of
+// [wfrom, x1): along a primary edge 32 positions per step, from the root the
+// positions that start no pattern 32 at a time, a mismatch by the warp-wide
+// failure walk.
+__device__ __forceinline__ void run_exact(const uint32_t *__restrict__ ssym, uint64_t x, uint64_t wfrom,
+                                          uint64_t x1, const Automaton &A, uint32_t *__restrict__ state,
+                                          uint32_t *err) {
+  const uint32_t lane = threadIdx.x & 31, root = A.root;
+  uint32_t v = root;
+  while (x < x1) {
+    const uint64_t xi = x + lane;
+    const uint32_t sy = xi < x1 ? ssym[xi] : kNil;
+    if (v != root) {
+      // down the path of preferred children: lane j tests node hc^(j+1)(v)
+      // (doubling rounds as in the failure walk), whose own symbol is the
+      // one that leads into it
+      uint32_t u = A.heavy[0][v];
+#pragma unroll
+      for (int k = 0; k < kLift; ++k) {
+        const uint32_t from = __shfl_up_sync(0xffffffffu, u, 1u << k);
+        if (lane >= (1u << k) && lane < (2u << k)) u = A.heavy[k][from];
+      }
+      const bool ok = xi < x1 && sy == A.tsym[u];
+      const uint32_t miss = __ballot_sync(0xffffffffu, !ok);
+      const uint32_t m = miss ? (uint32_t)(__ffs(miss) - 1) : 32u;
+      if (m > 0) {
+        if (lane < m && xi >= wfrom) state[xi] = u;
+        v = __shfl_sync(0xffffffffu, u, m - 1);
+        x += m;
+        continue;
+      }
+      v = fail_walk_warp(A, v, __shfl_sync(0xffffffffu, sy, 0), err);
+    } else {
+      const uint32_t r = xi < x1 ? table_lookup(A.g, root, sy) : kNil;
+      const uint32_t hit = __ballot_sync(0xffffffffu, r != kNil || xi >= x1);
+      const uint32_t h = hit ? (uint32_t)(__ffs(hit) - 1) : 32u;  // positions staying at the root
+      if (h > 0) {
+        if (lane < h && xi >= wfrom) state[xi] = root;
+        x += h;
+        continue;
+      }
+      v = __shfl_sync(0xffffffffu, r, 0);
+    }
+    if (lane == 0 && x >= wfrom) state[x] = v;
+    ++x;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kStateWarps)
+    k_ac_halo(const uint32_t *__restrict__ ssym, uint64_t n, uint64_t seg, uint64_t halo, Automaton A,
+              uint32_t *__restrict__ state, uint32_t *err) {
+  const uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the same in the warp
+  const uint64_t g0 = t * seg;
+  if (g0 >= n) return;
+  run_exact(ssym, g0 > halo ? g0 - halo : 0, g0, min(n, g0 + seg), A, state, err);
+}
+
+// hc[t] over T positions and the root: a node's preferred child (its next
+// position in T when no preference was recorded), a separator and the root
+// map to themselves -- a separator's symbol matches no stream symbol, so a
+// walk down the path stops there.
+__global__ void k_heavy_init(const uint32_t *__restrict__ tsym, const unsigned long long *__restrict__ pref,
+                             uint32_t N, uint32_t *__restrict__ hc) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= N; t += gridDim.x * blockDim.x) {
+    uint32_t h = t;
+    if (t < N && tsym[t] != kSep) h = pref[t] ? (uint32_t)pref[t] : t + 1;
+    hc[t] = h;
+  }
+}
+
+// next[v] = prev[prev[v]] for two tables at once: the lifting tables of the
+// skip links and of the preferred children, one doubling each
+__global__ void k_lift(const uint32_t *__restrict__ prev_a, uint32_t *__restrict__ next_a,
+                       const uint32_t *__restrict__ prev_b, uint32_t *__restrict__ next_b, uint32_t nodes) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nodes; v += gridDim.x * blockDim.x) {
+    next_a[v] = prev_a[prev_a[v]];
+    next_b[v] = prev_b[prev_b[v]];
+  }
+}
+
 // Exclusive prefix sum of total[state[x]] over stream positions (the first
 // output slot of each position), decoupled look-back.
 constexpr int kST = 256, kSI = 8, kSTile = kST * kSI;
@@ -996,8 +1165,10 @@ size_t match_workspace_bytes(uint64_t total_tokens, uint64_t P, uint64_t n, uint
   const uint64_t tbl = pow2_at_least(2 * (P + 1));
   const uint64_t dct = pow2_at_least(2 * (extent + 1));
   const uint64_t sparse = (uint64_t)(bits_for(P) + 1) * P;
-  // pattern text (symbols, sort tokens, pattern ids, reach) and the per-node arrays
-  uint64_t bytes = N * (8 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1) + P * (16 + 8) +
+  // pattern text (symbols, sort tokens, pattern ids, reach) and the per-node
+  // arrays (with the halo pass's preferred children and lifting tables)
+  uint64_t bytes = N * (8 + 4 + 4) + (N + kTsymPad) * (4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 1 + 16 + 8 + 20) +
+                   P * (16 + 8) +
                    tbl * 16 + dct * 8 + P * (4 * 8 + 24) + sparse * 4 + (extent + n) * 4 + n * 8 + 96 * 256 +
                    P * 8;  // record totals and flattened-chain offsets
   if (src_n)  // source ranks, start lengths, both interval scans, the LCP min-tree
@@ -1075,6 +1246,26 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   if (srcm && maxlen >= 0xffff) srcm = false;  // the interval scans hold lengths in 16 bits
   const uint32_t src_n = srcm ? (uint32_t)pp->src_n : 0u;
+  // Pass A's shape.  A chunk per lane in the first pass, about 64 per SM; a
+  // repair pass moves exact states one group of chunks further (chunks of 32
+  // positions and 256 lanes per SM on the 2^20-token window: first pass 0.28
+  // -> about 0.1 ms, repairs 0.45 -> 0.79 ms).
+  const uint64_t chunk = std::max<uint64_t>(64, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
+  const uint64_t nch = (n + chunk - 1) / chunk;
+  // chunks per repair warp: longer groups settle in fewer passes, shorter
+  // ones keep more warps busy on a short stream
+  const uint32_t group = n >= (1ull << 22) ? 8u : 4u;
+  const uint64_t nch2 = (nch + group - 1) / group;
+  // The halo pass instead where states are deep: the patterns are slices of
+  // the stream itself (each occurs at least at its own slice), they cover a
+  // quarter of it or more, and the longest is longer than a chunk -- so the
+  // chunked pass would be wrong over most covered positions -- but at most
+  // four segments long (the halo's extra walk).  Segments of 128 to 1024
+  // positions, about 24 warps per SM.
+  uint64_t seg = 128;
+  while (seg < 1024 && seg * 2 * 24 * (uint64_t)sms <= n) seg *= 2;
+  const bool self_slices = !pp->pat_off && pp->tokens == stream;
+  const bool halo = n && self_slices && 4 * total >= n && maxlen > chunk && maxlen <= 4 * seg;
   APO_TRY(c->arena.reserve(match_workspace_bytes(total, P, n, extent, maxlen, src_n)));
   const uint32_t N = (uint32_t)(total + P);  // pattern text with separators
   const uint32_t root = N;                   // node ids are T positions; the root is N
@@ -1108,6 +1299,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   uint32_t *mtotal = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint32_t *skip = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint8_t *has_branch = c->arena.take_n<uint8_t>((size_t)N + 1);
+  unsigned long long *pref = halo ? c->arena.take_n<unsigned long long>((size_t)N + 1) : nullptr;
   uint32_t *recidx = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint32_t *firstrec = c->arena.take_n<uint32_t>((size_t)N + 1);
   uint4 *rec = c->arena.take_n<uint4>(P);
@@ -1131,7 +1323,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   const bool src_mode_ok = !srcm || (src_rank && startlen && fl && mw);
   if (!g.keys || !d.keys || (pp->pat_off && !pbuf) || !tstart || !tsym || !tkey || !tpid || !reach ||
       !sa_mode_ok || !src_mode_ok || !fail || !own || !wj || !jl || !mtotal || !skip || !has_branch || !recidx ||
-      !firstrec || !rec || !sr || !jpos || !end_node || !sparse || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
+      !firstrec || (halo && !pref) || !rec || !sr || !jpos || !end_node || !sparse || !b.keys[0] || !b.keys[1] || !b.vals[0] ||
       !b.vals[1] || !be.keys[0] || !be.keys[1] || !be.vals[0] || !be.vals[1]) {
     set_error("match: workspace too small");
     return APO_ENOMEM;
@@ -1289,6 +1481,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   }
   APO_CUDA_TRY(cudaMemsetAsync(own, 0, ((size_t)N + 1) * sizeof(uint32_t), s));
   APO_CUDA_TRY(cudaMemsetAsync(has_branch, 0, (size_t)N + 1, s));
+  if (pref) APO_CUDA_TRY(cudaMemsetAsync(pref, 0, ((size_t)N + 1) * sizeof(unsigned long long), s));
   {
     NodeArgs a;
     a.tstart = tstart;
@@ -1308,6 +1501,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.own = own;
     a.end_node = end_node;
     a.has_branch = has_branch;
+    a.pref = pref;
     a.err = c->ps.err;
     a.src = srcm;
     a.pstart = pstart;
@@ -1316,7 +1510,10 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
     a.T = src_tree;
     a.lenbits = lenbits;
     Launch lp_(c, kKAcNodes, N, s);
-    k_ac_nodes<<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
+    if (pref)
+      k_ac_nodes<true><<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
+    else
+      k_ac_nodes<false><<<std::max(1, std::min(ceil_div(P, 8), sms * 16)), 256, 0, s>>>(a);
   }
   // pattern ids grouped by end node
   {
@@ -1361,22 +1558,33 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
                             0u, s));
   }
 
-  // pass A: states, chunked without a halo, then repaired until stable
-  Automaton A{tsym, g, skip, root};
+  // pass A: the state of every stream position (pass shape chosen above)
+  Automaton A{tsym, has_branch, g, skip, root, {skip}, (uint32_t)(maxlen / 32 + 2), {}};
   uint32_t *state = c->arena.take_n<uint32_t>(n);
   uint32_t *off = c->arena.take_n<uint32_t>(n);
-  // a chunk per lane in the first pass, about 64 per SM; a repair pass
-  // moves exact states one group of chunks further (chunks of 32 positions
-  // and 256 lanes per SM on the 2^20-token window: first pass 0.28 -> about
-  // 0.1 ms, repairs 0.45 -> 0.79 ms)
-  const uint64_t chunk = std::max<uint64_t>(64, std::min<uint64_t>(512, n / ((uint64_t)sms * 64)));
-  const uint64_t nch = (n + chunk - 1) / chunk;
-  // chunks per repair warp: longer groups settle in fewer passes, shorter
-  // ones keep more warps busy on a short stream
-  const uint32_t group = n >= (1ull << 22) ? 8u : 4u;
-  const uint64_t nch2 = (nch + group - 1) / group;
   if (!state || !off) return APO_ENOMEM;
-  {
+  if (halo) {
+    // lifting tables of the skip links and of the preferred children
+    uint32_t *hc = c->arena.take_n<uint32_t>((size_t)N + 1);
+    if (!hc) return APO_ENOMEM;
+    {
+      Launch lp_(c, kKAcJump, (uint64_t)N + 1, s);
+      k_heavy_init<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(tsym, pref, N, hc);
+    }
+    A.heavy[0] = hc;
+    for (int k = 1; k < kLift; ++k) {
+      uint32_t *t = c->arena.take_n<uint32_t>((size_t)N + 1), *h = c->arena.take_n<uint32_t>((size_t)N + 1);
+      if (!t || !h) return APO_ENOMEM;
+      Launch lp_(c, kKAcJump, 2 * ((uint64_t)N + 1), s);
+      k_lift<<<grid_for((uint64_t)N + 1, 256, sms), 256, 0, s>>>(A.lift[k - 1], t, A.heavy[k - 1], h, N + 1);
+      A.lift[k] = t;
+      A.heavy[k] = h;
+    }
+    const uint64_t nseg = (n + seg - 1) / seg;
+    Launch lp_(c, kKAcHalo, n, s);
+    k_ac_halo<<<ceil_div(nseg, kStateWarps), 32 * kStateWarps, 0, s>>>(ssym, n, seg, maxlen, A, state,
+                                                                        c->ps.err);
+  } else {
     Launch lp_(c, kKAcStates, n, s);
     k_ac_states<<<ceil_div(nch, 64), 64, 0, s>>>(ssym, n, chunk, A, state);
   }
@@ -1384,7 +1592,7 @@ int match_patterns(apo_ctx *c, const apo_patterns *pp, const void *stream, uint6
   // and a pass after one without changes returns at once, so the host reads
   // a count only after every second pass.
   uint32_t *chg = misc + kMiscFixChanged;
-  for (uint64_t pass = 0; pass < nch2;) {
+  for (uint64_t pass = 0; !halo && pass < nch2;) {
     const uint64_t last = std::min<uint64_t>(pass + 2, nch2);
     for (; pass < last; ++pass) {
       APO_CUDA_TRY(cudaMemsetAsync(chg + (pass & 1), 0, sizeof(uint32_t), s));

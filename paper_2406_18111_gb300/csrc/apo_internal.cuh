@@ -96,7 +96,7 @@ enum KernelId : int {
   kKSelOut, kKPatLayout, kKTableInit, kKEndPairs, kKMarkEnds, kKAcFix, kKAcStates,
   kKAcFill, kKDictInsert, kKDictMap, kKSlices, kKMatchOffsets, kKSegScan, kKStarts, kKSparse,
   kKAcNodes, kKAcJump, kKRsTune, kKRpPieces, kKRpNeed, kKRpChain, kKRpAppear, kKRpSelect, kKRpOut,
-  kKOptimum, kKSaDict, kKRound, kKSplit, kKWsb, kKListCompact, kKMinor, kKRsPassKeys, kKCount
+  kKOptimum, kKSaDict, kKRound, kKSplit, kKWsb, kKListCompact, kKMinor, kKRsPassKeys, kKAcHalo, kKCount
 };
 extern const char *const kKernelNames[kKCount];
 

@@ -136,7 +136,7 @@ const char *const kKernelNames[kKCount] = {
     "ac_states", "ac_fill", "dict_insert", "dict_map", "slices", "match_offsets", "seg_scan",
     "starts", "sparse", "ac_nodes", "ac_jump", "rs_tune", "rp_pieces", "rp_need", "rp_chain",
     "rp_appear", "rp_select", "rp_out", "optimum", "sa_dict", "round", "split", "wsb", "list_compact", "minor",
-    "rs_pass_keys"};
+    "rs_pass_keys", "ac_halo"};
 
 cudaEvent_t Profiler::get() {
   if (!pool.empty()) {

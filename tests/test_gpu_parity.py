@@ -119,9 +119,27 @@ def test_config2_tokens_scaled(apo, n):
 
 
 def test_config2_full(apo):
+    """The window of 2^20 hashed tasks end to end, as the bench runs it: the
+    repeats, then their traces matched against the window with the window's
+    suffix and LCP arrays (long self-slices: the exact halo pass)."""
+    from paper_2406_18111_gb300 import as_u32
     tok = oracle.hash_tasks(W.config2_tasks(1 << 20))
     r, o = compare(apo, tok, 5, tb=8)
     assert r.rounds >= 1
+    t = tokens_dev(tok, 8)
+    rs = apo.find_repeats(t, 5, stages=False, sa_lcp=True)
+    apo.profile_reset()
+    e, i = apo.match_candidates(t, None, t, pat_start=rs.trace_start, pat_len=rs.trace_len, src_sa=rs.sa,
+                                src_lcp=rs.lcp)
+    prof = apo.profile_read()
+    assert "ac.ac_halo" in prof and "ac.ac_states" not in prof and "ac.ac_fix" not in prof
+    st, tl = o.trace_start.astype(np.int64), o.trace_len.astype(np.int64)
+    off = np.zeros(len(tl) + 1, np.uint64)
+    off[1:] = np.cumsum(tl)
+    pt = np.concatenate([tok[a:a + b] for a, b in zip(st, tl)])
+    oe, oi = oracle.match(pt, off, tok)
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
 
 
 def test_config3_windows(apo):
@@ -202,7 +220,10 @@ def test_match_config5_scaled(apo, n, P):
     from paper_2406_18111_gb300 import as_u32
     stream = W.match_stream(n, seed=7)
     pt, off = W.match_patterns(stream, P, 5, 2000, seed=7)
+    apo.profile_reset()
     e, i = apo.match_candidates(tokens_dev(pt, 4), off, tokens_dev(stream, 4))
+    prof = apo.profile_read()
+    assert "ac.ac_states" in prof and "ac.ac_halo" not in prof  # chunks and repairs
     oe, oi = oracle.match(pt, off, stream)
     assert len(oe) > 0
     assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
@@ -267,6 +288,40 @@ def test_match_traces_slice_form(apo):
     oe, oi = oracle.match(pt, off, tok)
     assert len(oe) > 0
     assert np.array_equal(as_u32(e), oe) and np.array_equal(as_u32(i), oi)
+
+
+@pytest.mark.parametrize("n,period,tb", [(1000, 7, 4), (3 * 4096 + 77, 300, 8), (50000, 1500, 4)])
+def test_match_halo_pass(apo, n, period, tb):
+    """Long slices of the stream matched against the stream itself (the
+    exact pass that starts each segment one longest-pattern length early):
+    ragged segments, segments nearer the start than that length, a pattern
+    ending at the stream's end, long failure chains in a noisy periodic
+    stream.  The same
+    matches as the oracle and as the chunked pass (the patterns as CSR)."""
+    from paper_2406_18111_gb300 import as_u32
+    S = W.periodic_window(n, period, 0.02, 50, seed=n)
+    rng = np.random.default_rng(period)
+    k = max(8, n // 100)
+    lens = rng.integers(65, min(512, n) + 1, k)
+    starts = rng.integers(0, n - lens + 1)
+    lens[0], starts[0] = min(512, n), n - min(512, n)  # a pattern ending at the stream's end
+    assert 4 * lens.sum() >= n
+    t = tokens_dev(S, tb)
+    apo.profile_reset()
+    e1, i1 = apo.match_candidates(t, None, t, pat_start=dev(starts.astype(np.uint32), np.int32),
+                                  pat_len=dev(lens.astype(np.uint32), np.int32))
+    prof = apo.profile_read()
+    assert "ac.ac_halo" in prof and "ac.ac_states" not in prof
+    off = np.zeros(k + 1, np.uint64)
+    off[1:] = np.cumsum(lens)
+    pt = np.concatenate([S[a:a + b] for a, b in zip(starts, lens)])
+    apo.profile_reset()
+    e2, i2 = apo.match_candidates(tokens_dev(pt, tb), off, t)
+    assert "ac.ac_states" in apo.profile_read()
+    oe, oi = oracle.match(pt.astype(np.uint64), off, S.astype(np.uint64))
+    assert len(oe) > 0
+    assert np.array_equal(as_u32(e1), oe) and np.array_equal(as_u32(i1), oi)
+    assert np.array_equal(as_u32(e2), oe) and np.array_equal(as_u32(i2), oi)
 
 
 @pytest.mark.parametrize("n,tb", [(1 << 14, 8), ((1 << 16) + 77, 8), (20000, 4)])
