@@ -393,7 +393,12 @@ typedef struct {
  * matches to match_end/match_id (device, `cap` entries each) and their total
  * number to *count (HOST).  Synchronises `stream`.  APO_ECAPACITY if the total
  * exceeds cap (*count is exact, the arrays' contents are then unspecified).
- * APO_EINVAL for an empty pattern, P = 0, or token_bytes not 4 or 8. */
+ * APO_EINVAL for an empty pattern, P = 0, or token_bytes not 4 or 8.
+ * Performance only, the results are the same either way: when the slices are
+ * taken from the stream itself (patterns->tokens == stream_tokens) and are
+ * long, the automaton's states are computed in one exact pass that starts
+ * each segment of the stream one longest-pattern length early; otherwise in
+ * short chunks from the root, repaired until they agree. */
 int apo_match_candidates(apo_ctx *ctx, const apo_patterns *patterns, const void *stream_tokens,
                          uint64_t n, uint32_t *match_end, uint32_t *match_id, uint64_t cap,
                          uint64_t *count, void *stream);
