@@ -993,9 +993,9 @@ __device__ __forceinline__ uint32_t fail_walk_warp(const Automaton &A, uint32_t 
 }
 
 // One warp runs positions [x, x1) from the root and writes the states of
-// [wfrom, x1): along a primary edge 32 positions per step, from the root the
-// positions that start no pattern 32 at a time, a mismatch by the warp-wide
-// failure walk.
+// [wfrom, x1): down the path of preferred children 32 positions per step,
+// from the root the positions that start no pattern 32 at a time, a
+// mismatch by the warp-wide failure walk.
 __device__ __forceinline__ void run_exact(const uint32_t *__restrict__ ssym, uint64_t x, uint64_t wfrom,
                                           uint64_t x1, const Automaton &A, uint32_t *__restrict__ state,
                                           uint32_t *err) {
